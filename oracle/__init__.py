@@ -1,0 +1,252 @@
+"""FP64 CPU oracle of the k-shell renderer -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA path:
+it is a separate C++ library (``vs_oracle.cpp``) reached through ``ctypes``,
+fed by the seeded generators of the ``synth`` package.
+
+Every function states the paper passage it follows; the discrete readings of
+the silent parts (snapping, fill rule, depth key, addressing) are listed at
+the top of ``vs_oracle.cpp``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from .build import LIB_PATH, build_oracle
+
+FMT_RGBA_F32 = 0
+FMT_SH_F16 = 1
+
+_lib = None
+
+
+class OCam(ctypes.Structure):
+    _fields_ = [("w2c", ctypes.c_float * 12), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("znear", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class OShell(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("tris", ctypes.c_void_p),
+                ("nv", ctypes.c_int32), ("nt", ctypes.c_int32), ("tex", ctypes.c_void_p),
+                ("tw", ctypes.c_int32), ("th", ctypes.c_int32), ("fmt", ctypes.c_int32),
+                ("degree", ctypes.c_int32), ("pitch", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+
+
+_DTYPES = {np.dtype(np.float32): 0, np.dtype(np.float16): 1, np.dtype(np.float64): 2}
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = os.environ.get("VS_ORACLE_LIB", LIB_PATH)   # e.g. a mutated copy
+        if path == LIB_PATH and not os.path.exists(LIB_PATH):
+            build_oracle()
+        _lib = ctypes.CDLL(path)
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def ocam(cam) -> OCam:
+    c = OCam()
+    w2c = np.ascontiguousarray(cam.world_to_cam, dtype=np.float32).reshape(-1)
+    for i in range(12):
+        c.w2c[i] = float(w2c[i])
+    c.fx, c.fy, c.cx, c.cy, c.znear = cam.fx, cam.fy, cam.cx, cam.cy, cam.znear
+    c.width, c.height = cam.width, cam.height
+    return c
+
+
+class _ShellRefs:
+    """Keeps contiguous copies alive while the C side holds pointers."""
+
+    def __init__(self, shells):
+        self.keep = []
+        self.arr = (OShell * len(shells))()
+        for i, s in enumerate(shells):
+            pos = np.ascontiguousarray(s.pos, np.float32)
+            uv = np.ascontiguousarray(s.uv, np.float32)
+            tris = np.ascontiguousarray(s.tris, np.int32)
+            tex = np.ascontiguousarray(s.tex)
+            self.keep += [pos, uv, tris, tex]
+            o = self.arr[i]
+            o.pos, o.uv, o.tris = _ptr(pos).value, _ptr(uv).value, _ptr(tris).value
+            o.nv, o.nt = pos.shape[0], tris.shape[0]
+            o.tex = _ptr(tex).value
+            o.th, o.tw, o.pitch = tex.shape[0], tex.shape[1], tex.shape[2]
+            o.fmt, o.degree = s.fmt, s.degree
+            o.dtype = _DTYPES[tex.dtype]
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+# --- vertex stage -------------------------------------------------------------
+
+def setup_vertices(pos: np.ndarray, cam):
+    """Pinned FP32 transform + 1/256 px snap + depth key, per vertex.
+
+    Returns (xy int64 [V,2], invw float32 [V], q uint32 [V], flags int32 [V])
+    with flags bit 0 = nearer than znear, bit 1 = outside the guard band.
+    """
+    pos = np.ascontiguousarray(pos, np.float32)
+    n = pos.shape[0]
+    xy = np.zeros((n, 2), np.int64)
+    invw = np.zeros(n, np.float32)
+    q = np.zeros(n, np.uint32)
+    flags = np.zeros(n, np.int32)
+    c = ocam(cam)
+    lib().oracle_setup_vertices(_ptr(pos), ctypes.c_int32(n), ctypes.byref(c), _ptr(xy), _ptr(invw),
+                                _ptr(q), _ptr(flags))
+    return xy, invw, q, flags
+
+
+# --- raster (per shell nearest hit) ---------------------------------------------
+
+def raster(pos, tris, cam, brute: bool = False, threads: Optional[int] = None,
+           coverage: bool = False):
+    """Per-shell nearest-hit raster (Fig. 3c: first intersection per surface).
+
+    Returns (keys uint64 [H,W], cover int32 [H,W] or None, stats int64 [4]).
+    keys = (depth key << 32) | (2^32 - 1 - triangle); 0 = miss.
+    """
+    pos = np.ascontiguousarray(pos, np.float32)
+    tris = np.ascontiguousarray(tris, np.int32)
+    H, W = cam.height, cam.width
+    keys = np.zeros((H, W), np.uint64)
+    cover = np.zeros((H, W), np.int32) if coverage else None
+    stats = np.zeros(4, np.int64)
+    c = ocam(cam)
+    lib().oracle_raster(_ptr(pos), ctypes.c_int32(pos.shape[0]), _ptr(tris),
+                        ctypes.c_int32(tris.shape[0]), ctypes.byref(c), ctypes.c_int32(int(brute)),
+                        ctypes.c_int32(threads or default_threads()), _ptr(keys),
+                        _ptr(cover) if cover is not None else None, _ptr(stats))
+    return keys, cover, stats
+
+
+def hits_from_keys(keys: np.ndarray) -> np.ndarray:
+    low = (keys & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    return np.where(keys == 0, -1, 0xFFFFFFFF - low).astype(np.int32)
+
+
+def raster_scene(scene, cam, threads: Optional[int] = None, brute: bool = False):
+    """hits int32 [k,H,W] (-1 = miss), keys uint64 [k,H,W], stats [k,4]."""
+    hs, ks, st = [], [], []
+    for s in scene.shells:
+        keys, _, stats = raster(s.pos, s.tris, cam, brute=brute, threads=threads)
+        ks.append(keys)
+        hs.append(hits_from_keys(keys))
+        st.append(stats)
+    return np.stack(hs), np.stack(ks), np.stack(st)
+
+
+# --- shading / compositing ----------------------------------------------------------
+
+def shade(scene, cam, hits: np.ndarray, bg=(0.0, 0.0, 0.0), threads: Optional[int] = None):
+    """Bilinear texel fetch, SH decode and front-to-back compositing (Eq. 6).
+
+    Returns (rgba float64 [H,W,4] = (C + T bg, 1 - T), fragments per shell).
+    """
+    refs = _ShellRefs(scene.shells)
+    H, W = cam.height, cam.width
+    hits = np.ascontiguousarray(hits, np.int32)
+    assert hits.shape == (scene.k, H, W)
+    out = np.zeros((H, W, 4), np.float64)
+    bgv = np.ascontiguousarray(bg, np.float64)
+    frags = np.zeros(scene.k, np.int64)
+    c = ocam(cam)
+    lib().oracle_shade(refs.arr, ctypes.c_int32(scene.k), ctypes.byref(c), _ptr(bgv), _ptr(hits),
+                       _ptr(out), ctypes.c_int32(threads or default_threads()), _ptr(frags))
+    return out, frags
+
+
+def render(scene, cam, bg=(0.0, 0.0, 0.0), threads: Optional[int] = None):
+    """Full oracle render: (rgba [H,W,4] f64, hits [k,H,W] i32, frags [k])."""
+    hits, _, _ = raster_scene(scene, cam, threads=threads)
+    rgba, frags = shade(scene, cam, hits, bg=bg, threads=threads)
+    return rgba, hits, frags
+
+
+def backward(scene, cam, hits: np.ndarray, grad_rgb: np.ndarray, bg=(0.0, 0.0, 0.0)) -> List[np.ndarray]:
+    """dL/d(texel values) given dL/d(output rgb) -- the texture-fitting
+    gradient of Sec. 3 "Texturing Meshes".  Returns one FP64 array per shell,
+    shaped like its texture."""
+    refs = _ShellRefs(scene.shells)
+    H, W = cam.height, cam.width
+    hits = np.ascontiguousarray(hits, np.int32)
+    g = np.ascontiguousarray(grad_rgb, np.float64)
+    assert g.shape == (H, W, 3)
+    grads = [np.zeros(s.tex.shape, np.float64) for s in scene.shells]
+    ptrs = (ctypes.c_void_p * scene.k)(*[gr.ctypes.data for gr in grads])
+    bgv = np.ascontiguousarray(bg, np.float64)
+    c = ocam(cam)
+    lib().oracle_backward(refs.arr, ctypes.c_int32(scene.k), ctypes.byref(c), _ptr(bgv), _ptr(hits),
+                          _ptr(g), ptrs)
+    return grads
+
+
+def l2_loss_grad(rgba: np.ndarray, target_rgb: np.ndarray):
+    """L = mean over pixels and RGB channels of (C - target)^2; returns (L, dL/dC)."""
+    d = rgba[..., :3] - target_rgb
+    n = d.size
+    return float((d * d).sum() / n), 2.0 * d / n
+
+
+def footprint_texels(scene, cam, hits: np.ndarray) -> np.ndarray:
+    """Distinct texels read by each shell's bilinear footprints."""
+    refs = _ShellRefs(scene.shells)
+    hits = np.ascontiguousarray(hits, np.int32)
+    out = np.zeros(scene.k, np.int64)
+    c = ocam(cam)
+    lib().oracle_footprint_texels(refs.arr, ctypes.c_int32(scene.k), ctypes.byref(c), _ptr(hits),
+                                  _ptr(out))
+    return out
+
+
+# --- single steps, for the pins -------------------------------------------------------
+
+def sh_basis(degree: int, v: Sequence[float]) -> np.ndarray:
+    vv = np.ascontiguousarray(v, np.float64)
+    out = np.zeros(16, np.float64)
+    lib().oracle_sh_basis(ctypes.c_int32(degree), _ptr(vv), _ptr(out))
+    return out[: (degree + 1) ** 2]
+
+
+def sample(tex: np.ndarray, u: float, v: float, nch: Optional[int] = None) -> np.ndarray:
+    """Bilinear sample of the raw texel values at UV (u, v) (Fig. 5)."""
+    tex = np.ascontiguousarray(tex)
+    th, tw, pitch = tex.shape
+    nch = pitch if nch is None else nch
+    out = np.zeros(nch, np.float64)
+    lib().oracle_sample(_ptr(tex), ctypes.c_int32(_DTYPES[tex.dtype]), ctypes.c_int32(tw), ctypes.c_int32(th),
+                        ctypes.c_int32(pitch), ctypes.c_int32(nch), ctypes.c_double(u),
+                        ctypes.c_double(v), _ptr(out))
+    return out
+
+
+def interp_uv(X, Y, invw, uv, px: int, py: int) -> np.ndarray:
+    Xa = np.ascontiguousarray(X, np.int64)
+    Ya = np.ascontiguousarray(Y, np.int64)
+    iw = np.ascontiguousarray(invw, np.float64)
+    uva = np.ascontiguousarray(uv, np.float32).reshape(-1)
+    out = np.zeros(2, np.float64)
+    lib().oracle_interp_uv(_ptr(Xa), _ptr(Ya), _ptr(iw), _ptr(uva), ctypes.c_int64(px),
+                           ctypes.c_int64(py), _ptr(out))
+    return out
+
+
+def ray_dir(cam, x: int, y: int) -> np.ndarray:
+    out = np.zeros(3, np.float64)
+    c = ocam(cam)
+    lib().oracle_ray_dir(ctypes.byref(c), ctypes.c_int32(x), ctypes.c_int32(y), _ptr(out))
+    return out

@@ -1,0 +1,596 @@
+// FP64 CPU oracle of the k-shell ("Volumetric Surfaces") renderer.
+//
+// TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+// baseline leg of the benchmark load this library; the product path never
+// does.  It shares no code, header, table or constant with the CUDA path.
+//
+// What it computes, step by step, in the paper's order:
+//   * Sec. 3 "Baking Textures" / Sec. 4 real-time renderer: every shell is a
+//     triangle mesh, rasterized in a fixed outer-to-inner order, each with
+//     its own nearest-hit test ("only sampling the first intersection with
+//     each surface", Fig. 3c).
+//   * Sec. 3 "Texturing Meshes", Fig. 5: the texture value at a UV point is
+//     the bilinear mix of the four surrounding texel centers, like an OpenGL
+//     fragment shader; SH coefficients are decoded with the view direction v
+//     (the ray direction of Sec. 2, r(t) = o + v t) into RGBA.
+//   * Eq. 6 with the transmittance of Eq. 1 (products over *earlier* layers
+//     only): C = sum_i c_i a_i prod_{j<i} (1 - a_j), front to back.
+//   * Sec. 3 "Texturing Meshes": texture fitting differentiates the renderer
+//     with respect to texel values; the adjoint below is that derivative.
+//
+// Discrete rules the paper leaves open (readings of the silent parts):
+//   * vertices go through an FP32 world->camera->screen transform in a fixed
+//     operation order (each op rounded to float, no fused multiply-add; this
+//     file must be compiled with -ffp-contract=off), are snapped to 1/256 px
+//     with round-half-even, and carry a depth key q = rint(2^30 znear / w);
+//   * pixel centers (x + 1/2, y + 1/2), one sample per pixel;
+//   * integer edge functions, top-left fill rule, front faces only
+//     (counter-clockwise seen from outside), zero-area faces culled,
+//     faces with a vertex nearer than znear or beyond +-32768 px culled;
+//   * depth key at a pixel K = floor(sum_j e_j q_j / sum_j e_j) in exact
+//     integer arithmetic; the nearest (largest K) wins, ties go to the lower
+//     triangle index;
+//   * perspective-correct barycentrics, texel (x, y) centred at
+//     ((x+1/2)/W, (y+1/2)/H), clamp-to-edge, no mipmaps;
+//   * SH_F16: alpha = sigmoid(a), rgb = sigmoid(sum_m sh_m Y_m(v));
+//     RGBA_F32: values used as they are;
+//   * output (C + T bg, 1 - T).
+// Everything after the snapped integers and the FP32 1/w is FP64.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+struct OShell {
+  const float* pos;        // [nv, 3]
+  const float* uv;         // [nv, 2]
+  const int32_t* tris;     // [nt, 3]
+  int32_t nv, nt;
+  const void* tex;         // [th, tw, pitch] texel values
+  int32_t tw, th, fmt, degree, pitch;
+  int32_t dtype;           // storage of tex: 0 float32, 1 float16, 2 float64
+};
+
+struct OCam {
+  float w2c[12];           // row-major 3x4 [R | t], world -> camera
+  float fx, fy, cx, cy, znear;
+  int32_t width, height;
+};
+
+enum { FMT_RGBA_F32 = 0, FMT_SH_F16 = 1 };  // value meaning; storage is OShell::dtype
+enum { VF_NEAR = 1, VF_GUARD = 2 };
+
+struct SVert {
+  int64_t X = 0, Y = 0;    // snapped screen position, 1/256 px
+  float invw = 0.f;        // FP32 1/w
+  uint32_t q = 0;          // depth key
+  int flags = 0;
+};
+
+// --- vertex transform (pinned FP32 sequence) --------------------------------
+SVert setup_vertex(const float* p, const OCam& c) {
+  const float* m = c.w2c;
+  float x = p[0], y = p[1], z = p[2];
+  float xc = m[0] * x;
+  xc = xc + m[1] * y;
+  xc = xc + m[2] * z;
+  xc = xc + m[3];
+  float yc = m[4] * x;
+  yc = yc + m[5] * y;
+  yc = yc + m[6] * z;
+  yc = yc + m[7];
+  float zc = m[8] * x;
+  zc = zc + m[9] * y;
+  zc = zc + m[10] * z;
+  zc = zc + m[11];
+  SVert v;
+  if (!(zc >= c.znear)) {
+    v.flags = VF_NEAR;
+    return v;
+  }
+  float iw = 1.0f / zc;
+  float sx = c.fx * xc;
+  sx = sx * iw;
+  sx = sx + c.cx;
+  float sy = c.fy * yc;
+  sy = sy * iw;
+  sy = sy + c.cy;
+  float X = sx * 256.0f, Y = sy * 256.0f;
+  if (!(std::fabs(X) < 8388608.0f && std::fabs(Y) < 8388608.0f)) {
+    v.flags = VF_GUARD;
+    return v;
+  }
+  v.X = (int64_t)std::nearbyint(X);
+  v.Y = (int64_t)std::nearbyint(Y);
+  v.invw = iw;
+  float kq = c.znear * 1073741824.0f;
+  float qf = iw * kq;
+  v.q = (uint32_t)std::nearbyint(qf);
+  return v;
+}
+
+std::vector<SVert> setup_all(const OShell& s, const OCam& c) {
+  std::vector<SVert> v(s.nv);
+  for (int i = 0; i < s.nv; ++i) v[i] = setup_vertex(s.pos + 3 * i, c);
+  return v;
+}
+
+int64_t floor_div(int64_t a, int64_t b) {  // b > 0
+  int64_t q = a / b;
+  if ((a % b) != 0 && a < 0) --q;
+  return q;
+}
+
+// Triangle prepared for rasterization: front-facing, all vertices valid.
+struct Tri {
+  int64_t X[3], Y[3];
+  uint32_t q[3];
+  bool tl[3];              // edge j (opposite vertex j) is a top or left edge
+  int64_t xlo, xhi, ylo, yhi;
+};
+
+// orient(a, b, p) = (bx - ax)(py - ay) - (by - ay)(px - ax); for a
+// front-facing triangle (orient(v0, v1, v2) < 0 in y-down screen space) the
+// weights e_j = orient(v_{j+2}, v_{j+1}, p) are >= 0 inside and e_j is the
+// barycentric weight of vertex j.
+inline void edge_values(const Tri& t, int64_t px, int64_t py, int64_t e[3]) {
+  for (int j = 0; j < 3; ++j) {
+    int a = (j + 2) % 3, b = (j + 1) % 3;
+    e[j] = (t.X[b] - t.X[a]) * (py - t.Y[a]) - (t.Y[b] - t.Y[a]) * (px - t.X[a]);
+  }
+}
+
+inline bool covered(const Tri& t, const int64_t e[3]) {
+  for (int j = 0; j < 3; ++j) {
+    if (e[j] < 0) return false;
+    if (e[j] == 0 && !t.tl[j]) return false;
+  }
+  return true;
+}
+
+// Returns 0 if culled (reason in *why: 1 back/degenerate, 2 near, 3 guard).
+bool prepare_tri(const std::vector<SVert>& sv, const int32_t* idx, const OCam& c,
+                 Tri* t, int* why) {
+  const SVert* v[3] = {&sv[idx[0]], &sv[idx[1]], &sv[idx[2]]};
+  int f = v[0]->flags | v[1]->flags | v[2]->flags;
+  if (f & VF_NEAR) { *why = 2; return false; }
+  if (f & VF_GUARD) { *why = 3; return false; }
+  for (int j = 0; j < 3; ++j) {
+    t->X[j] = v[j]->X; t->Y[j] = v[j]->Y; t->q[j] = v[j]->q;
+  }
+  int64_t a2 = (t->X[1] - t->X[0]) * (t->Y[2] - t->Y[0]) -
+               (t->X[2] - t->X[0]) * (t->Y[1] - t->Y[0]);
+  if (a2 >= 0) { *why = 1; return false; }
+  for (int j = 0; j < 3; ++j) {
+    int a = (j + 2) % 3, b = (j + 1) % 3;
+    // gradient of e_j: d/dpx = -(Yb - Ya), d/dpy = (Xb - Xa); interior on
+    // the positive side.  Left edge: interior to the right (d/dpx > 0).
+    // Top edge: horizontal with the interior below (+y is down).
+    int64_t ax = -(t->Y[b] - t->Y[a]);
+    int64_t by = t->X[b] - t->X[a];
+    t->tl[j] = (ax > 0) || (ax == 0 && by > 0);
+  }
+  int64_t mnx = std::min({t->X[0], t->X[1], t->X[2]});
+  int64_t mxx = std::max({t->X[0], t->X[1], t->X[2]});
+  int64_t mny = std::min({t->Y[0], t->Y[1], t->Y[2]});
+  int64_t mxy = std::max({t->Y[0], t->Y[1], t->Y[2]});
+  // pixel centres 256 x + 128 inside [mn, mx]
+  t->xlo = std::max<int64_t>(0, -floor_div(-(mnx - 128), 256));
+  t->xhi = std::min<int64_t>(c.width - 1, floor_div(mxx - 128, 256));
+  t->ylo = std::max<int64_t>(0, -floor_div(-(mny - 128), 256));
+  t->yhi = std::min<int64_t>(c.height - 1, floor_div(mxy - 128, 256));
+  *why = 0;
+  return true;
+}
+
+inline uint32_t depth_key(const Tri& t, const int64_t e[3]) {
+  __int128 n = (__int128)e[0] * t.q[0] + (__int128)e[1] * t.q[1] + (__int128)e[2] * t.q[2];
+  __int128 s = (__int128)e[0] + e[1] + e[2];
+  return (uint32_t)(n / s);
+}
+
+void raster_rows(const OShell& s, const OCam& c, const std::vector<SVert>& sv, int brute,
+                 int64_t y0, int64_t y1, uint64_t* keys, int32_t* cover, int64_t* stats) {
+  const int64_t W = c.width;
+  for (int32_t ti = 0; ti < s.nt; ++ti) {
+    Tri t;
+    int why;
+    bool ok = prepare_tri(sv, s.tris + 3 * ti, c, &t, &why);
+    if (stats) stats[why] += 1;
+    if (!ok) continue;
+    int64_t xa = t.xlo, xb = t.xhi, ya = std::max(t.ylo, y0), yb = std::min(t.yhi, y1 - 1);
+    if (brute) { xa = 0; xb = W - 1; ya = y0; yb = y1 - 1; }
+    for (int64_t y = ya; y <= yb; ++y) {
+      int64_t py = 256 * y + 128;
+      for (int64_t x = xa; x <= xb; ++x) {
+        int64_t px = 256 * x + 128;
+        int64_t e[3];
+        edge_values(t, px, py, e);
+        if (!covered(t, e)) continue;
+        if (cover) cover[y * W + x] += 1;
+        uint64_t key = ((uint64_t)depth_key(t, e) << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)ti);
+        uint64_t& slot = keys[y * W + x];
+        if (key > slot) slot = key;
+      }
+    }
+  }
+}
+
+template <class F>
+void parallel_rows(int64_t h, int nthreads, F f) {
+  if (nthreads <= 1 || h < 2) { f(0, h, 0); return; }
+  nthreads = (int)std::min<int64_t>(nthreads, h);
+  std::vector<std::thread> th;
+  for (int i = 0; i < nthreads; ++i) {
+    int64_t a = h * i / nthreads, b = h * (i + 1) / nthreads;
+    th.emplace_back([=] { f(a, b, i); });
+  }
+  for (auto& t : th) t.join();
+}
+
+// --- texture sampling ---------------------------------------------------------
+double half_to_double(uint16_t h) {
+  int s = h >> 15, e = (h >> 10) & 31, m = h & 1023;
+  double v;
+  if (e == 0) v = std::ldexp((double)m, -24);
+  else if (e == 31) v = m ? NAN : INFINITY;
+  else v = std::ldexp((double)(m | 1024), e - 25);
+  return s ? -v : v;
+}
+
+inline double texel_value(const OShell& s, int64_t x, int64_t y, int ch) {
+  size_t off = ((size_t)y * s.tw + (size_t)x) * s.pitch + ch;
+  if (s.dtype == 0) return (double)((const float*)s.tex)[off];
+  if (s.dtype == 2) return ((const double*)s.tex)[off];
+  return half_to_double(((const uint16_t*)s.tex)[off]);
+}
+
+struct Footprint {
+  int64_t x[2], y[2];      // clamped tap columns / rows
+  double fx, fy;           // weight of column x[1] / row y[1]
+};
+
+// Bilinear footprint of UV point (u, v): texel centres at ((x+1/2)/W, (y+1/2)/H).
+Footprint footprint(const OShell& s, double u, double v) {
+  double X = u * s.tw - 0.5, Y = v * s.th - 0.5;
+  double fx0 = std::floor(X), fy0 = std::floor(Y);
+  Footprint f;
+  f.fx = X - fx0;
+  f.fy = Y - fy0;
+  int64_t ix = (int64_t)fx0, iy = (int64_t)fy0;
+  f.x[0] = std::clamp<int64_t>(ix, 0, s.tw - 1);
+  f.x[1] = std::clamp<int64_t>(ix + 1, 0, s.tw - 1);
+  f.y[0] = std::clamp<int64_t>(iy, 0, s.th - 1);
+  f.y[1] = std::clamp<int64_t>(iy + 1, 0, s.th - 1);
+  return f;
+}
+
+inline double tap_weight(const Footprint& f, int a, int b) {  // a: column tap, b: row tap
+  return (a ? f.fx : 1.0 - f.fx) * (b ? f.fy : 1.0 - f.fy);
+}
+
+void sample(const OShell& s, const Footprint& f, int nch, double* out) {
+  for (int ch = 0; ch < nch; ++ch) {
+    double acc = 0.0;
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) acc += tap_weight(f, a, b) * texel_value(s, f.x[a], f.y[b], ch);
+    out[ch] = acc;
+  }
+}
+
+// --- real spherical harmonics, l <= 3, orthonormal on the unit sphere ---------
+// Real forms of the complex Y_l^m without the Condon-Shortley sign; the l = 1
+// band is proportional to (y, z, x).  Index l^2 + l + m.
+void sh_basis(int deg, const double v[3], double* Y) {
+  const double pi = 3.14159265358979323846;
+  const double x = v[0], y = v[1], z = v[2];
+  Y[0] = 0.5 * std::sqrt(1.0 / pi);
+  if (deg < 1) return;
+  const double c1 = std::sqrt(3.0 / (4.0 * pi));
+  Y[1] = c1 * y;
+  Y[2] = c1 * z;
+  Y[3] = c1 * x;
+  if (deg < 2) return;
+  const double c2a = 0.5 * std::sqrt(15.0 / pi);
+  const double c2b = 0.25 * std::sqrt(5.0 / pi);
+  const double c2c = 0.25 * std::sqrt(15.0 / pi);
+  Y[4] = c2a * x * y;
+  Y[5] = c2a * y * z;
+  Y[6] = c2b * (3.0 * z * z - 1.0);
+  Y[7] = c2a * x * z;
+  Y[8] = c2c * (x * x - y * y);
+  if (deg < 3) return;
+  const double c3a = 0.25 * std::sqrt(35.0 / (2.0 * pi));
+  const double c3b = 0.5 * std::sqrt(105.0 / pi);
+  const double c3c = 0.25 * std::sqrt(21.0 / (2.0 * pi));
+  const double c3d = 0.25 * std::sqrt(7.0 / pi);
+  const double c3e = 0.25 * std::sqrt(105.0 / pi);
+  Y[9] = c3a * y * (3.0 * x * x - y * y);
+  Y[10] = c3b * x * y * z;
+  Y[11] = c3c * y * (5.0 * z * z - 1.0);
+  Y[12] = c3d * z * (5.0 * z * z - 3.0);
+  Y[13] = c3c * x * (5.0 * z * z - 1.0);
+  Y[14] = c3e * z * (x * x - y * y);
+  Y[15] = c3a * x * (x * x - 3.0 * y * y);
+}
+
+inline double sigmoid(double x) { return 1.0 / (1.0 + std::exp(-x)); }
+
+// Unit world-space direction of the ray through the centre of pixel (x, y).
+void ray_dir(const OCam& c, int64_t x, int64_t y, double v[3]) {
+  double dc[3] = {((double)x + 0.5 - c.cx) / c.fx, ((double)y + 0.5 - c.cy) / c.fy, 1.0};
+  double n = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    v[i] = c.w2c[0 + i] * dc[0] + c.w2c[4 + i] * dc[1] + c.w2c[8 + i] * dc[2];
+    n += v[i] * v[i];
+  }
+  n = std::sqrt(n);
+  for (int i = 0; i < 3; ++i) v[i] /= n;
+}
+
+// Perspective-correct UV at pixel centre (px, py) (1/256 px fixed point).
+void interp_uv(const Tri& t, const float* const uv[3], const double invw[3], int64_t px, int64_t py,
+               double out[2]) {
+  int64_t e[3];
+  edge_values(t, px, py, e);
+  double w[3], sw = 0.0;
+  for (int j = 0; j < 3; ++j) { w[j] = (double)e[j] * invw[j]; sw += w[j]; }
+  out[0] = out[1] = 0.0;
+  for (int j = 0; j < 3; ++j) {
+    out[0] += w[j] / sw * uv[j][0];
+    out[1] += w[j] / sw * uv[j][1];
+  }
+}
+
+int num_values(const OShell& s) {
+  return s.fmt == FMT_RGBA_F32 ? 4 : 1 + 3 * (s.degree + 1) * (s.degree + 1);
+}
+
+// One fragment: (pixel, shell, triangle) -> rgb, alpha, plus what the adjoint needs.
+struct Frag {
+  double rgb[3], alpha;
+  Footprint fp;
+  double val[64];          // interpolated texel values
+};
+
+bool shade_fragment(const OShell& s, const OCam& c, const std::vector<SVert>& sv, int32_t tri,
+                    int64_t x, int64_t y, const double* Y, Frag* f) {
+  const int32_t* idx = s.tris + 3 * tri;
+  Tri t;
+  int why;
+  if (!prepare_tri(sv, idx, c, &t, &why)) return false;
+  const float* uvp[3] = {s.uv + 2 * idx[0], s.uv + 2 * idx[1], s.uv + 2 * idx[2]};
+  double invw[3] = {sv[idx[0]].invw, sv[idx[1]].invw, sv[idx[2]].invw};
+  double uv[2];
+  interp_uv(t, uvp, invw, 256 * x + 128, 256 * y + 128, uv);
+  f->fp = footprint(s, uv[0], uv[1]);
+  int nv = num_values(s);
+  sample(s, f->fp, nv, f->val);
+  if (s.fmt == FMT_RGBA_F32) {
+    for (int ch = 0; ch < 3; ++ch) f->rgb[ch] = f->val[ch];
+    f->alpha = f->val[3];
+  } else {
+    int nb = (s.degree + 1) * (s.degree + 1);
+    f->alpha = sigmoid(f->val[0]);
+    for (int ch = 0; ch < 3; ++ch) {
+      double z = 0.0;
+      for (int m = 0; m < nb; ++m) z += f->val[1 + 3 * m + ch] * Y[m];
+      f->rgb[ch] = sigmoid(z);
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int oracle_setup_vertices(const float* pos, int32_t nv, const OCam* cam, int64_t* xy, float* invw,
+                          uint32_t* q, int32_t* flags) {
+  for (int i = 0; i < nv; ++i) {
+    SVert v = setup_vertex(pos + 3 * i, *cam);
+    xy[2 * i] = v.X;
+    xy[2 * i + 1] = v.Y;
+    invw[i] = v.invw;
+    q[i] = v.q;
+    flags[i] = v.flags;
+  }
+  return 0;
+}
+
+// keys: [H*W] zero-initialised by the caller; max of (K << 32 | ~tri).
+// cover (optional): [H*W] zero-initialised, += 1 per covering front triangle.
+// stats (optional): [4] = {front, back or zero-area, near, guard band}.
+int oracle_raster(const float* pos, int32_t nv, const int32_t* tris, int32_t nt, const OCam* cam,
+                  int32_t brute, int32_t nthreads, uint64_t* keys, int32_t* cover, int64_t* stats) {
+  OShell s{};
+  s.pos = pos; s.nv = nv; s.tris = tris; s.nt = nt;
+  std::vector<SVert> sv = setup_all(s, *cam);
+  if (stats) std::memset(stats, 0, 4 * sizeof(int64_t));
+  int nth = std::max(1, nthreads);
+  std::vector<int64_t> st(4 * nth, 0);
+  parallel_rows(cam->height, nth, [&](int64_t y0, int64_t y1, int i) {
+    raster_rows(s, *cam, sv, brute, y0, y1, keys, cover, st.data() + 4 * i);
+  });
+  if (stats) {
+    // every band sees every triangle once: report the counts of band 0
+    for (int j = 0; j < 4; ++j) stats[j] = st[j];
+  }
+  return 0;
+}
+
+// Shade + composite every pixel from per-shell hits [k, H, W] (-1 = miss).
+// out: [H, W, 4] = (C + T bg, 1 - T).  stats (optional): [k] fragments per shell.
+int oracle_shade(const OShell* shells, int32_t k, const OCam* cam, const double* bg,
+                 const int32_t* hits, double* out, int32_t nthreads, int64_t* frags) {
+  const int64_t W = cam->width, H = cam->height;
+  std::vector<std::vector<SVert>> sv(k);
+  int maxdeg = 0;
+  for (int i = 0; i < k; ++i) {
+    sv[i] = setup_all(shells[i], *cam);
+    if (shells[i].fmt == FMT_SH_F16) maxdeg = std::max(maxdeg, (int)shells[i].degree);
+  }
+  int nth = std::max(1, nthreads);
+  std::vector<int64_t> cnt((size_t)nth * k, 0);
+  parallel_rows(H, nth, [&](int64_t y0, int64_t y1, int ti) {
+    for (int64_t y = y0; y < y1; ++y)
+      for (int64_t x = 0; x < W; ++x) {
+        double v[3], Y[16];
+        ray_dir(*cam, x, y, v);
+        sh_basis(maxdeg, v, Y);
+        double C[3] = {0, 0, 0}, T = 1.0;
+        for (int i = 0; i < k; ++i) {
+          int32_t h = hits[(size_t)i * H * W + y * W + x];
+          if (h < 0) continue;
+          Frag f;
+          if (!shade_fragment(shells[i], *cam, sv[i], h, x, y, Y, &f)) continue;
+          cnt[(size_t)ti * k + i] += 1;
+          for (int ch = 0; ch < 3; ++ch) C[ch] += T * f.alpha * f.rgb[ch];
+          T *= (1.0 - f.alpha);
+        }
+        double* o = out + 4 * (y * W + x);
+        for (int ch = 0; ch < 3; ++ch) o[ch] = C[ch] + T * bg[ch];
+        o[3] = 1.0 - T;
+      }
+  });
+  if (frags)
+    for (int i = 0; i < k; ++i) {
+      frags[i] = 0;
+      for (int t = 0; t < nth; ++t) frags[i] += cnt[(size_t)t * k + i];
+    }
+  return 0;
+}
+
+// Adjoint of oracle_shade w.r.t. the texel values.  grad_rgb: [H, W, 3] =
+// dL/d(output rgb).  grad_tex[i]: [th, tw, pitch] FP64, accumulated into.
+int oracle_backward(const OShell* shells, int32_t k, const OCam* cam, const double* bg,
+                    const int32_t* hits, const double* grad_rgb, double* const* grad_tex) {
+  const int64_t W = cam->width, H = cam->height;
+  std::vector<std::vector<SVert>> sv(k);
+  int maxdeg = 0;
+  for (int i = 0; i < k; ++i) {
+    sv[i] = setup_all(shells[i], *cam);
+    if (shells[i].fmt == FMT_SH_F16) maxdeg = std::max(maxdeg, (int)shells[i].degree);
+  }
+  std::vector<Frag> fr(k);
+  std::vector<char> hit(k);
+  std::vector<double> Tin(k);
+  for (int64_t y = 0; y < H; ++y)
+    for (int64_t x = 0; x < W; ++x) {
+      const double* g = grad_rgb + 3 * (y * W + x);
+      double v[3], Y[16];
+      ray_dir(*cam, x, y, v);
+      sh_basis(maxdeg, v, Y);
+      double T = 1.0;
+      for (int i = 0; i < k; ++i) {
+        int32_t h = hits[(size_t)i * H * W + y * W + x];
+        hit[i] = h >= 0 && shade_fragment(shells[i], *cam, sv[i], h, x, y, Y, &fr[i]);
+        Tin[i] = T;
+        if (hit[i]) T *= (1.0 - fr[i].alpha);
+      }
+      // back to front: A = colour seen behind shell i (bg behind the last)
+      double A[3] = {bg[0], bg[1], bg[2]};
+      for (int i = k - 1; i >= 0; --i) {
+        if (!hit[i]) continue;
+        const Frag& f = fr[i];
+        const OShell& s = shells[i];
+        double gc[3], ga = 0.0;
+        for (int ch = 0; ch < 3; ++ch) {
+          gc[ch] = Tin[i] * f.alpha * g[ch];                 // dL/dc_i
+          ga += Tin[i] * (f.rgb[ch] - A[ch]) * g[ch];         // dL/dalpha_i
+        }
+        for (int ch = 0; ch < 3; ++ch) A[ch] = f.alpha * f.rgb[ch] + (1.0 - f.alpha) * A[ch];
+        int nv = num_values(s);
+        double dval[64];
+        if (s.fmt == FMT_RGBA_F32) {
+          dval[0] = gc[0]; dval[1] = gc[1]; dval[2] = gc[2]; dval[3] = ga;
+        } else {
+          int nb = (s.degree + 1) * (s.degree + 1);
+          dval[0] = ga * f.alpha * (1.0 - f.alpha);
+          for (int ch = 0; ch < 3; ++ch) {
+            double dz = gc[ch] * f.rgb[ch] * (1.0 - f.rgb[ch]);
+            for (int m = 0; m < nb; ++m) dval[1 + 3 * m + ch] = dz * Y[m];
+          }
+        }
+        for (int b = 0; b < 2; ++b)
+          for (int a = 0; a < 2; ++a) {
+            double w = tap_weight(f.fp, a, b);
+            double* gt = grad_tex[i] + ((size_t)f.fp.y[b] * s.tw + (size_t)f.fp.x[a]) * s.pitch;
+            for (int ch = 0; ch < nv; ++ch) gt[ch] += w * dval[ch];
+          }
+      }
+    }
+  return 0;
+}
+
+// Number of distinct texels touched by the bilinear footprints of all
+// fragments of each shell (the D of the algorithmic-bytes count).
+int oracle_footprint_texels(const OShell* shells, int32_t k, const OCam* cam, const int32_t* hits,
+                            int64_t* distinct) {
+  const int64_t W = cam->width, H = cam->height;
+  for (int i = 0; i < k; ++i) {
+    const OShell& s = shells[i];
+    std::vector<SVert> sv = setup_all(s, *cam);
+    std::vector<uint8_t> mark((size_t)s.tw * s.th, 0);
+    for (int64_t y = 0; y < H; ++y)
+      for (int64_t x = 0; x < W; ++x) {
+        int32_t h = hits[(size_t)i * H * W + y * W + x];
+        if (h < 0) continue;
+        const int32_t* idx = s.tris + 3 * h;
+        Tri t;
+        int why;
+        if (!prepare_tri(sv, idx, *cam, &t, &why)) continue;
+        const float* uvp[3] = {s.uv + 2 * idx[0], s.uv + 2 * idx[1], s.uv + 2 * idx[2]};
+        double invw[3] = {sv[idx[0]].invw, sv[idx[1]].invw, sv[idx[2]].invw};
+        double uv[2];
+        interp_uv(t, uvp, invw, 256 * x + 128, 256 * y + 128, uv);
+        Footprint f = footprint(s, uv[0], uv[1]);
+        for (int b = 0; b < 2; ++b)
+          for (int a = 0; a < 2; ++a) mark[(size_t)f.y[b] * s.tw + f.x[a]] = 1;
+      }
+    int64_t n = 0;
+    for (uint8_t m : mark) n += m;
+    distinct[i] = n;
+  }
+  return 0;
+}
+
+// --- single-step entry points for the pins --------------------------------------
+int oracle_sh_basis(int32_t deg, const double* v, double* Y) {
+  sh_basis(deg, v, Y);
+  return 0;
+}
+
+// Bilinear sample of all `nch` raw values of a texture at UV (u, v).
+int oracle_sample(const void* tex, int32_t dtype, int32_t tw, int32_t th, int32_t pitch, int32_t nch,
+                  double u, double v, double* out) {
+  OShell s{};
+  s.tex = tex; s.dtype = dtype; s.tw = tw; s.th = th; s.pitch = pitch;
+  Footprint f = footprint(s, u, v);
+  sample(s, f, nch, out);
+  return 0;
+}
+
+// Perspective-correct UV of a (front-facing) triangle with snapped vertices
+// X, Y (1/256 px), per-vertex 1/w and UVs, at fixed-point point (px, py).
+int oracle_interp_uv(const int64_t* X, const int64_t* Y, const double* invw, const float* uv,
+                     int64_t px, int64_t py, double* out) {
+  Tri t{};
+  for (int j = 0; j < 3; ++j) { t.X[j] = X[j]; t.Y[j] = Y[j]; }
+  const float* uvp[3] = {uv, uv + 2, uv + 4};
+  interp_uv(t, uvp, invw, px, py, out);
+  return 0;
+}
+
+// Unit ray direction through pixel (x, y).
+int oracle_ray_dir(const OCam* cam, int32_t x, int32_t y, double* v) {
+  ray_dir(*cam, x, y, v);
+  return 0;
+}
+
+}  // extern "C"

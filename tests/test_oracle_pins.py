@@ -1,0 +1,665 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these recompute the oracle's own formulas: each compares it with an
+independent route (ray casting, a library routine, a closed form, brute
+force, finite differences) chosen so that a plausible slip -- a dropped term,
+a wrong sign or index, a transposed operand -- fails at least one of them.
+The paper prints no worked numeric example, so there is no table to copy.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import FMT_RGBA_F32, FMT_SH_F16, Camera, Scene, Shell
+
+
+# ----------------------------------------------------------------------------
+# independent helpers (FP64, numpy) -- no oracle code
+# ----------------------------------------------------------------------------
+
+def pixel_rays(cam):
+    """Camera centre and unit world ray directions through pixel centres."""
+    R = cam.world_to_cam[:, :3].astype(np.float64)
+    t = cam.world_to_cam[:, 3].astype(np.float64)
+    eye = -R.T @ t
+    ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+    dc = np.stack([(xs + 0.5 - cam.cx) / cam.fx, (ys + 0.5 - cam.cy) / cam.fy,
+                   np.ones(xs.shape)], axis=-1)
+    dw = dc @ R
+    dw /= np.linalg.norm(dw, axis=-1, keepdims=True)
+    return eye, dw
+
+
+def raycast_front(eye, dirs, pos, tris):
+    """Nearest front-facing hit per ray (Moller-Trumbore, FP64).
+
+    Returns (tri id or -1, t, second-nearest t) per ray."""
+    p = pos.astype(np.float64)
+    a, b, c = p[tris[:, 0]], p[tris[:, 1]], p[tris[:, 2]]
+    e1, e2 = b - a, c - a
+    n = np.cross(e1, e2)
+    tvec = eye[None, :] - a
+    qvec = np.cross(tvec, e1)
+    tt_num = np.einsum("ij,ij->i", e2, qvec)
+    d = dirs.reshape(-1, 3)
+    ids = np.full(d.shape[0], -1)
+    t_best = np.full(d.shape[0], np.inf)
+    t_second = np.full(d.shape[0], np.inf)
+    for s in range(0, d.shape[0], 256):
+        dd = d[s:s + 256]
+        pvec = np.cross(dd[:, None, :], e2[None, :, :])
+        det = np.einsum("tj,dtj->dt", e1, pvec)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            inv = 1.0 / det
+            u = np.einsum("tj,dtj->dt", tvec, pvec) * inv
+            v = (dd @ qvec.T) * inv
+            tt = tt_num[None, :] * inv
+        front = (dd @ n.T) < 0
+        ok = front & (u >= 0) & (v >= 0) & (u + v <= 1) & (tt > 0)
+        tm = np.where(ok, tt, np.inf)
+        order = np.argsort(tm, axis=1)[:, :2]
+        best = tm[np.arange(len(dd)), order[:, 0]]
+        ids[s:s + 256] = np.where(np.isfinite(best), order[:, 0], -1)
+        t_best[s:s + 256] = best
+        t_second[s:s + 256] = tm[np.arange(len(dd)), order[:, 1]]
+    return ids, t_best, t_second
+
+
+def project64(pos, cam):
+    R = cam.world_to_cam[:, :3].astype(np.float64)
+    t = cam.world_to_cam[:, 3].astype(np.float64)
+    pc = pos.astype(np.float64) @ R.T + t
+    return np.stack([cam.fx * pc[:, 0] / pc[:, 2] + cam.cx,
+                     cam.fy * pc[:, 1] / pc[:, 2] + cam.cy], axis=1), pc[:, 2]
+
+
+def edge_distance_px(scr, tri, px, py):
+    """Distance (pixels) from point to the three edge lines of a projected tri."""
+    d = []
+    for j in range(3):
+        a, b = scr[tri[j]], scr[tri[(j + 1) % 3]]
+        ab = b - a
+        d.append(abs(ab[0] * (py - a[1]) - ab[1] * (px - a[0])) / max(np.hypot(*ab), 1e-30))
+    return min(d)
+
+
+def real_sh_scipy(degree, v):
+    """Real orthonormal SH from scipy's complex Y_l^m: sqrt(2)(-1)^m Re / Im,
+    index l^2 + l + m."""
+    from scipy.special import sph_harm_y
+    v = np.asarray(v, np.float64)
+    theta = math.acos(max(-1.0, min(1.0, v[2])))
+    phi = math.atan2(v[1], v[0])
+    out = []
+    for l in range(degree + 1):
+        for m in range(-l, l + 1):
+            y = sph_harm_y(l, abs(m), theta, phi)
+            if m > 0:
+                out.append(math.sqrt(2) * (-1) ** m * y.real)
+            elif m < 0:
+                out.append(math.sqrt(2) * (-1) ** m * y.imag)
+            else:
+                out.append(y.real)
+    return np.array(out)
+
+
+def sigmoid(x):
+    return 1.0 / (1.0 + np.exp(-x))
+
+
+def constant_shell(pos, uv, tris, values, fmt=FMT_RGBA_F32, degree=0, size=4, dtype=np.float32):
+    tex = np.broadcast_to(np.asarray(values, dtype), (size, size, len(values))).copy()
+    return Shell(pos, uv, tris, tex, fmt, degree)
+
+
+def inradius(pos, tris):
+    p = pos.astype(np.float64)
+    a, b, c = p[tris[:, 0]], p[tris[:, 1]], p[tris[:, 2]]
+    n = np.cross(b - a, c - a)
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    return float(np.abs(np.einsum("ij,ij->i", n, a)).min())
+
+
+def ray_center_distance(cam):
+    eye, d = pixel_rays(cam)
+    return np.linalg.norm(np.cross(np.broadcast_to(eye, d.shape), d), axis=-1)
+
+
+# ----------------------------------------------------------------------------
+# coverage and depth (Fig. 3c; rasterization of Sec. 3 "Baking Textures")
+# ----------------------------------------------------------------------------
+
+def test_raster_brute_force_equals_bbox():
+    rng = np.random.default_rng(3)
+    # random small mesh with vertices on the half-pixel lattice: edges through
+    # pixel centres, shared edges and vertices, mixed orientations
+    cam = synth.look_at((0.0, -3.0, 0.4), width=24, height=20)
+    pos = rng.normal(size=(30, 3)).astype(np.float32) * 0.5
+    tris = rng.integers(0, 30, size=(60, 3)).astype(np.int32)
+    k_b, c_b, s_b = oracle.raster(pos, tris, cam, brute=True, coverage=True, threads=1)
+    k_x, c_x, s_x = oracle.raster(pos, tris, cam, brute=False, coverage=True, threads=3)
+    assert np.array_equal(k_b, k_x)
+    assert np.array_equal(c_b, c_x)
+    assert (k_x != 0).sum() > 50
+    pos2, uv2, tris2 = synth.displaced_shells(1, 8, seed=5, amp=0.3)[0]
+    cam2 = synth.look_at((2.5, 1.0, 0.5), width=40, height=32)
+    k_b = oracle.raster(pos2, tris2, cam2, brute=True, threads=1)[0]
+    k_x = oracle.raster(pos2, tris2, cam2, brute=False, threads=4)[0]
+    assert np.array_equal(k_b, k_x)
+
+
+@pytest.mark.parametrize("eye", [(0.0, -3.0, 0.0), (2.1, 1.3, 1.7), (0.3, 0.2, 3.2)])
+def test_watertight_convex_icosphere(eye):
+    """Convex closed mesh: each pixel inside the insphere's silhouette is
+    covered by exactly one front triangle; none outside the circumsphere's;
+    never more than one anywhere (no double cover, no holes)."""
+    pos, uv, tris = synth.icosphere(2, 1.0)
+    cam = synth.look_at(eye, width=96, height=80)
+    _, cover, stats = oracle.raster(pos, tris, cam, coverage=True)
+    dist = ray_center_distance(cam)
+    margin = 0.05 * np.linalg.norm(eye) / cam.fx
+    rin = inradius(pos, tris)
+    assert cover.max() <= 1
+    assert np.all(cover[dist < rin - margin] == 1)
+    assert np.all(cover[dist > 1.0 + margin] == 0)
+    assert stats[2] == 0 and stats[3] == 0
+    assert stats[0] + stats[1] == tris.shape[0]
+
+
+def _grid_camera(w, h):
+    # identity pose, focal 256 and z = 1: world x = (s - cx)/256 lands
+    # exactly on screen coordinate s
+    return Camera(world_to_cam=np.concatenate([np.eye(3), np.zeros((3, 1))], 1).astype(np.float32),
+                  fx=256.0, fy=256.0, cx=w / 2.0, cy=h / 2.0, znear=0.1, width=w, height=h)
+
+
+def test_watertight_lattice_triangulation():
+    """Delaunay triangulation of points on pixel centres, pixel corners and
+    edge midpoints: many edges and vertices pass exactly through pixel
+    centres, so only the top-left rule decides; every pixel centre strictly
+    inside the hull is covered exactly once."""
+    from scipy.spatial import ConvexHull, Delaunay
+    w, h = 40, 36
+    cam = _grid_camera(w, h)
+    rng = np.random.default_rng(7)
+    pts = np.unique(rng.integers(4, 2 * min(w, h) - 8, size=(120, 2)) * 0.5, axis=0)
+    tri = Delaunay(pts).simplices.astype(np.int32)
+    pos = np.stack([(pts[:, 0] - cam.cx) / 256.0, (pts[:, 1] - cam.cy) / 256.0,
+                    np.ones(len(pts))], axis=1).astype(np.float32)
+    xy, _, _, _ = oracle.setup_vertices(pos, cam)
+    assert np.array_equal(xy, np.round(pts * 256).astype(np.int64))   # exact placement
+    # make every triangle front-facing (negative signed area in y-down screen space)
+    p = pts[tri]
+    a2 = (p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1]) - \
+         (p[:, 2, 0] - p[:, 0, 0]) * (p[:, 1, 1] - p[:, 0, 1])
+    tri[a2 > 0] = tri[a2 > 0][:, [0, 2, 1]]
+    _, cover, stats = oracle.raster(pos, tri, cam, coverage=True)
+    assert stats[0] == len(tri)
+    eq = ConvexHull(pts).equations
+    ys, xs = np.mgrid[0:h, 0:w]
+    c = np.stack([xs + 0.5, ys + 0.5, np.ones_like(xs, dtype=float)], -1)
+    inside = np.all(c @ eq.T < -1e-9, axis=-1)
+    assert cover.max() <= 1
+    assert np.all(cover[inside] == 1)
+    on_vertex = np.isin((xs + 0.5) * 1000 + (ys + 0.5), pts[:, 0] * 1000 + pts[:, 1])
+    assert on_vertex[inside].sum() > 5            # the case is exercised
+
+
+def test_top_left_rule_shared_edges():
+    """Two triangles sharing a vertical and a horizontal edge through pixel
+    centres: the shared pixels go to the triangle to the right of the
+    vertical edge / below the horizontal edge (top-left rule)."""
+    w, h = 16, 16
+    cam = _grid_camera(w, h)
+    # square [4.5, 10.5]^2 split along the vertical x = 7.5 into two rects of
+    # two triangles each
+    P = {"a": (4.5, 4.5), "b": (7.5, 4.5), "c": (10.5, 4.5),
+         "d": (4.5, 10.5), "e": (7.5, 10.5), "f": (10.5, 10.5)}
+    names = list(P)
+    pts = np.array([P[n] for n in names])
+    ix = {n: i for i, n in enumerate(names)}
+    tris = np.array([[ix["a"], ix["d"], ix["b"]], [ix["b"], ix["d"], ix["e"]],
+                     [ix["b"], ix["e"], ix["c"]], [ix["c"], ix["e"], ix["f"]]], np.int32)
+    pos = np.stack([(pts[:, 0] - cam.cx) / 256.0, (pts[:, 1] - cam.cy) / 256.0,
+                    np.ones(len(pts))], axis=1).astype(np.float32)
+    keys, cover, stats = oracle.raster(pos, tris, cam, coverage=True)
+    hits = oracle.hits_from_keys(keys)
+    assert stats[0] == 4
+    # column x = 7 has centre 7.5 on the shared vertical edge: belongs to the
+    # right half (triangles 2, 3); the top row y = 4 (centre 4.5) is a top
+    # edge -> covered; the bottom row (centre 10.5) is a bottom edge -> not;
+    # left column x = 4 (left edge) covered, right column x = 10 not.
+    assert np.all(cover[4:10, 4:10] == 1)
+    assert np.all(cover[10, :] == 0) and np.all(cover[:, 10] == 0)
+    assert set(np.unique(hits[4:10, 7])) <= {2, 3}
+    assert set(np.unique(hits[4:10, 4:7])) <= {0, 1}
+
+
+def test_projection_matches_fp64_pinhole():
+    """Snapped vertices sit within 1/512 px (+ FP32 rounding) of the exact
+    FP64 pinhole projection; depth keys follow 2^30 znear / z."""
+    pos, _, _ = synth.displaced_shells(1, 12, seed=2)[0]
+    for cam in synth.fibonacci_cameras(3, 4.0, 300, 200):
+        xy, invw, q, flags = oracle.setup_vertices(pos, cam)
+        scr, z = project64(pos, cam)
+        assert np.all(flags == 0)
+        err = np.abs(xy / 256.0 - scr).max()
+        assert err <= 1.0 / 512 + 1e-3
+        assert np.allclose(invw, 1.0 / z, rtol=1e-6)
+        assert np.allclose(q.astype(np.float64), 2.0 ** 30 * cam.znear / z, rtol=1e-6)
+
+
+def test_raycast_agrees_except_near_edges():
+    """Non-convex, self-occluding shell: the nearest front hit of an FP64 ray
+    cast equals the oracle's triangle except where the pixel centre is within
+    a hair of a triangle edge (snapping) or two hits tie in depth."""
+    # one mesh made of a bumpy shell and a second blob in front of it: front
+    # faces overlap on screen, so the nearest-hit rule decides
+    p1, _, t1 = synth.displaced_shells(1, 14, seed=11, amp=0.3)[0]
+    p2, _, t2 = synth.icosphere(2, 0.35)
+    p2 = p2 + np.array([1.2, 0.3, 0.2], np.float32)
+    pos = np.concatenate([p1, p2]).astype(np.float32)
+    tris = np.concatenate([t1, t2 + len(p1)]).astype(np.int32)
+    cam = synth.look_at((3.2, 0.8, 0.35), width=72, height=64)
+    keys, cover, _ = oracle.raster(pos, tris, cam, coverage=True)
+    hits = oracle.hits_from_keys(keys).reshape(-1)
+    assert (cover >= 2).sum() > 10             # overlapping front faces exist
+    eye, dirs = pixel_rays(cam)
+    ids, t1, t2 = raycast_front(eye, dirs, pos, tris)
+    scr, _ = project64(pos, cam)
+    bad = 0
+    for p in np.nonzero(ids != hits)[0]:
+        y, x = divmod(p, cam.width)
+        px, py = x + 0.5, y + 0.5
+        near_edge = any(edge_distance_px(scr, tris[t], px, py) < 0.01
+                        for t in (ids[p], hits[p]) if t >= 0)
+        tie = np.isfinite(t2[p]) and abs(t2[p] - t1[p]) < 1e-6 * t1[p]
+        if not (near_edge or tie):
+            bad += 1
+    assert bad == 0
+    assert (ids == hits).mean() > 0.99
+
+
+def test_nested_shells_keep_depth_order():
+    """Sec. 3 "Support Surfaces as Shells": nested shells are met in order,
+    so per pixel the depth key (larger = nearer) never increases inward."""
+    shells = synth.displaced_shells(4, 20, seed=1, amp=0.15)
+    cam = synth.look_at((2.0, -2.8, 1.1), width=80, height=80)
+    keys = np.stack([oracle.raster(p, t, cam)[0] for (p, uv, t) in shells])
+    K = keys >> np.uint64(32)
+    both = (keys[:-1] != 0) & (keys[1:] != 0)
+    assert both.sum() > 1000
+    assert np.all(K[:-1][both] >= K[1:][both])
+    # inner shells are covered only where outer ones are
+    assert np.all((keys[1:] != 0) <= (keys[:-1] != 0))
+
+
+# ----------------------------------------------------------------------------
+# texture sampling (Fig. 5) and SH decode (Sec. 3 "Texturing Meshes")
+# ----------------------------------------------------------------------------
+
+def test_bilinear_at_texel_centres_returns_texel():
+    rng = np.random.default_rng(0)
+    tex = rng.normal(size=(5, 7, 3))
+    for y in range(5):
+        for x in range(7):
+            out = oracle.sample(tex, (x + 0.5) / 7, (y + 0.5) / 5)
+            assert np.array_equal(out, tex[y, x])
+
+
+def test_bilinear_reproduces_affine_texture():
+    H, W = 6, 9
+    ys, xs = np.mgrid[0:H, 0:W]
+    tex = np.stack([0.3 + 0.7 * xs - 0.2 * ys, -1.0 + 0.05 * xs + 0.9 * ys], -1).astype(np.float64)
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        X, Y = rng.uniform(0, W - 1), rng.uniform(0, H - 1)
+        out = oracle.sample(tex, (X + 0.5) / W, (Y + 0.5) / H)
+        assert np.allclose(out, [0.3 + 0.7 * X - 0.2 * Y, -1.0 + 0.05 * X + 0.9 * Y], atol=1e-12)
+
+
+def test_bilinear_clamps_to_edge():
+    rng = np.random.default_rng(2)
+    tex = rng.normal(size=(4, 6, 2))
+    for v in rng.uniform(0, 1, 20):
+        assert np.allclose(oracle.sample(tex, 0.0, v), oracle.sample(tex, 0.5 / 6, v), atol=1e-15)
+        assert np.allclose(oracle.sample(tex, 1.0, v), oracle.sample(tex, 5.5 / 6, v), atol=1e-15)
+    assert np.allclose(oracle.sample(tex, 0.0, 0.0), tex[0, 0])
+    assert np.allclose(oracle.sample(tex, 1.0, 1.0), tex[3, 5])
+
+
+def test_bilinear_tent_of_single_texel():
+    """A single non-zero texel gives the separable tent (1-|dx|)(1-|dy|)."""
+    tex = np.zeros((8, 8, 1))
+    tex[3, 5, 0] = 1.0
+    rng = np.random.default_rng(4)
+    for _ in range(100):
+        X, Y = rng.uniform(3.2, 6.8), rng.uniform(1.2, 4.8)
+        out = oracle.sample(tex, (X + 0.5) / 8, (Y + 0.5) / 8)[0]
+        assert abs(out - max(0, 1 - abs(X - 5)) * max(0, 1 - abs(Y - 3))) < 1e-12
+
+
+def test_half_precision_values_decode_exactly():
+    vals = np.array([0.0, -0.0, 1.0, -2.5, 0.1, 65504.0, 2.0 ** -24, 3 * 2.0 ** -24,
+                     2.0 ** -14, -0.3333], np.float16)
+    tex = vals.reshape(1, 1, -1)
+    out = oracle.sample(tex, 0.5, 0.5)
+    assert np.array_equal(out, vals.astype(np.float64))
+
+
+def test_sh_basis_orthonormal_by_quadrature():
+    mu, wmu = np.polynomial.legendre.leggauss(16)
+    nphi = 16
+    phis = 2 * np.pi * np.arange(nphi) / nphi
+    G = np.zeros((16, 16))
+    for m_, w_ in zip(mu, wmu):
+        s = math.sqrt(1 - m_ * m_)
+        for ph in phis:
+            Y = oracle.sh_basis(3, [s * math.cos(ph), s * math.sin(ph), m_])
+            G += w_ * (2 * np.pi / nphi) * np.outer(Y, Y)
+    assert np.abs(G - np.eye(16)).max() < 1e-12
+
+
+def test_sh_basis_matches_scipy_real_harmonics():
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        v = rng.normal(size=3)
+        v /= np.linalg.norm(v)
+        assert np.allclose(oracle.sh_basis(3, v), real_sh_scipy(3, v), atol=1e-13)
+    # l = 1 band is (y, z, x) * sqrt(3 / 4 pi); l = 0 is constant
+    v = np.array([0.48, -0.6, 0.64])
+    Y = oracle.sh_basis(1, v)
+    assert np.allclose(Y[1:4], math.sqrt(3 / (4 * math.pi)) * v[[1, 2, 0]], atol=1e-15)
+    assert abs(Y[0] - 0.5 / math.sqrt(math.pi)) < 1e-16
+
+
+def test_perspective_correct_uv_is_ray_plane_intersection():
+    """Barycentrics from snapped screen positions and 1/w reproduce the UV of
+    the true ray-plane intersection (Sec. 3 "Texturing Meshes": the sample
+    point is the surface point seen through the pixel)."""
+    rng = np.random.default_rng(6)
+    f, cx, cy = 300.0, 64.0, 48.0
+    for _ in range(100):
+        while True:
+            X = rng.integers(0, 128 * 256, 3)
+            Y = rng.integers(0, 96 * 256, 3)
+            a2 = (X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0])
+            if a2 < -1e6:
+                break
+        z = rng.uniform(1.0, 9.0, 3)
+        uv = rng.uniform(0, 1, (3, 2)).astype(np.float32)
+        P = np.stack([z * (X / 256.0 - cx) / f, z * (Y / 256.0 - cy) / f, z], 1)
+        # a point inside the triangle in screen space
+        bc = rng.dirichlet([1, 1, 1])
+        px = int(round(bc @ X))
+        py = int(round(bc @ Y))
+        d = np.array([(px / 256.0 - cx) / f, (py / 256.0 - cy) / f, 1.0])
+        n = np.cross(P[1] - P[0], P[2] - P[0])
+        hit = d * (n @ P[0]) / (n @ d)
+        # 3D barycentrics of the hit point
+        A = np.stack([P[0] - P[2], P[1] - P[2]], 1)
+        b01 = np.linalg.lstsq(A, hit - P[2], rcond=None)[0]
+        beta = np.array([b01[0], b01[1], 1 - b01.sum()])
+        want = beta @ uv.astype(np.float64)
+        got = oracle.interp_uv(X, Y, 1.0 / z, uv, px, py)
+        assert np.allclose(got, want, atol=1e-11)
+
+
+def test_ray_direction_matches_pixel_rays():
+    cam = synth.fibonacci_cameras(1, 4.0, 50, 30)[0]
+    _, d = pixel_rays(cam)
+    for (x, y) in [(0, 0), (49, 29), (17, 3), (25, 15)]:
+        assert np.allclose(oracle.ray_dir(cam, x, y), d[y, x], atol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# compositing (Eq. 6 with Eq. 1's transmittance over earlier layers)
+# ----------------------------------------------------------------------------
+
+def _sure_hits(cam, shells_geo, margin_px=0.5):
+    """Per pixel and shell: +1 surely hit, -1 surely missed, 0 ambiguous."""
+    dist = ray_center_distance(cam)
+    eye = np.linalg.norm(pixel_rays(cam)[0])
+    m = margin_px * eye / cam.fx
+    out = []
+    for (pos, uv, tris) in shells_geo:
+        r_in, r_out = inradius(pos, tris), float(np.linalg.norm(pos, axis=1).max())
+        s = np.zeros(dist.shape, np.int8)
+        s[dist < r_in - m] = 1
+        s[dist > r_out + m] = -1
+        out.append(s)
+    return np.stack(out)
+
+
+def _closed_form_composite(colors, alphas, bg, sure):
+    """C = sum_{i<m} c_i a_i prod_{j<i}(1-a_j) + bg prod_{j<m}(1-a_j) where the
+    m covered shells form a prefix (nested shells)."""
+    k = len(alphas)
+    H, W = sure.shape[1:]
+    out = np.zeros((H, W, 4))
+    valid = np.all(sure != 0, axis=0)
+    for y, x in zip(*np.nonzero(valid)):
+        C = np.zeros(3)
+        T = 1.0
+        for i in range(k):
+            if sure[i, y, x] > 0:
+                C += T * alphas[i] * np.asarray(colors[i])
+                T *= 1 - alphas[i]
+        out[y, x, :3] = C + T * np.asarray(bg)
+        out[y, x, 3] = 1 - T
+    return out, valid
+
+
+def test_composite_closed_form_concentric_shells():
+    geo = synth.concentric_icospheres([1.0, 0.9, 0.8], subdiv=3)
+    colors = [(0.9, 0.2, 0.1), (0.1, 0.8, 0.3), (0.2, 0.3, 0.95)]
+    alphas = [0.35, 0.6, 0.8]
+    shells = [constant_shell(p, u, t, list(c) + [a], dtype=np.float64)
+              for (p, u, t), c, a in zip(geo, colors, alphas)]
+    cam = synth.look_at((1.5, -2.4, 0.9), width=96, height=96)
+    bg = (0.25, 0.5, 0.75)
+    rgba, hits, _ = oracle.render(Scene(shells), cam, bg=bg)
+    sure = _sure_hits(cam, geo)
+    want, valid = _closed_form_composite(colors, alphas, bg, sure)
+    assert valid.sum() > 0.8 * valid.size
+    for i in range(3):                        # every sure hit / miss agrees
+        assert np.all(hits[i][sure[i] > 0] >= 0)
+        assert np.all(hits[i][sure[i] < 0] == -1)
+    assert np.abs(rgba[valid] - want[valid]).max() < 1e-12
+    assert (sure.sum(0) == 3).sum() > 100     # all three layers seen somewhere
+
+
+def test_single_opaque_shell_is_surface_render():
+    """k = 1, alpha = 1: the blend reduces to an opaque surface render
+    (Sec. 2, surface-based representations): output = texture colour."""
+    pos, uv, tris = synth.icosphere(2, 1.0)
+    rng = np.random.default_rng(8)
+    tex = rng.random((16, 16, 4)).astype(np.float32)
+    tex[..., 3] = 1.0
+    sc = Scene([Shell(pos, uv, tris, tex, FMT_RGBA_F32)])
+    cam = synth.look_at((0.4, -2.9, 0.6), width=64, height=64)
+    rgba, hits, _ = oracle.render(sc, cam, bg=(0.3, 0.3, 0.3))
+    h = hits[0] >= 0
+    assert h.sum() > 1000
+    assert np.abs(rgba[h][:, 3] - 1.0).max() < 1e-14
+    assert np.all(rgba[~h] == [0.3, 0.3, 0.3, 0.0])
+    # the background no longer shows through anywhere the shell is hit
+    rgba0, _, _ = oracle.render(sc, cam, bg=(0, 0, 0))
+    assert np.abs(rgba0[h] - rgba[h]).max() < 1e-14
+    # and the colour is the texture seen along the FP64 ray (away from edges,
+    # where snapping can move the sample point by a fraction of a pixel)
+    eye, dirs = pixel_rays(cam)
+    scr, _ = project64(pos, cam)
+    p64 = pos.astype(np.float64)
+    checked = 0
+    for y, x in zip(*np.nonzero(h)):
+        t = tris[hits[0, y, x]]
+        if edge_distance_px(scr, t, x + 0.5, y + 0.5) < 0.05:
+            continue
+        if np.ptp(uv[t], axis=0).max() > 0.5:     # UV-seam faces: huge UV gradient
+            continue
+        a, b, c = p64[t]
+        n = np.cross(b - a, c - a)
+        d = dirs[y, x]
+        pt = eye + d * (n @ (a - eye)) / (n @ d)
+        A = np.stack([a - c, b - c], 1)
+        b01 = np.linalg.lstsq(A, pt - c, rcond=None)[0]
+        beta = np.array([b01[0], b01[1], 1 - b01.sum()])
+        u, v = beta @ uv[t].astype(np.float64)
+        want = oracle.sample(tex, u, v)[:3]
+        assert np.abs(rgba[y, x, :3] - want).max() < 2e-3
+        checked += 1
+    assert checked > 1000
+
+
+def test_transparent_shell_is_invisible():
+    geo = synth.concentric_icospheres([1.0, 0.9, 0.8], subdiv=2)
+    rng = np.random.default_rng(9)
+
+    def tex(alpha=None):
+        t = rng.random((8, 8, 4)).astype(np.float32)
+        if alpha is not None:
+            t[..., 3] = alpha
+        return t
+    t0, t1, t2 = tex(), tex(0.0), tex()
+    full = Scene([Shell(*geo[0], t0, FMT_RGBA_F32), Shell(*geo[1], t1, FMT_RGBA_F32),
+                  Shell(*geo[2], t2, FMT_RGBA_F32)])
+    dropped = Scene([Shell(*geo[0], t0, FMT_RGBA_F32), Shell(*geo[2], t2, FMT_RGBA_F32)])
+    cam = synth.look_at((0.0, -3.0, 0.5), width=48, height=48)
+    a, _, _ = oracle.render(full, cam, bg=(0.1, 0.2, 0.3))
+    b, _, _ = oracle.render(dropped, cam, bg=(0.1, 0.2, 0.3))
+    assert np.abs(a - b).max() < 1e-15
+
+
+def test_constant_sh_textures_closed_form():
+    """Constant SH textures: colour = sigmoid(sum_m sh_m Y_m(v)) with v the
+    pixel's ray direction, alpha = sigmoid(a); layout [a, rgb_0, rgb_1, ...]."""
+    geo = synth.concentric_icospheres([1.0, 0.85], subdiv=3)
+    rng = np.random.default_rng(10)
+    deg = 3
+    coeffs = [np.float16(rng.normal(0, 0.8, synth.sh_channels(deg))) for _ in geo]
+    shells = [constant_shell(p, u, t, c, FMT_SH_F16, deg, dtype=np.float16)
+              for (p, u, t), c in zip(geo, coeffs)]
+    cam = synth.look_at((-1.2, 2.5, 1.3), width=64, height=64)
+    bg = (0.05, 0.1, 0.9)
+    rgba, hits, _ = oracle.render(Scene(shells), cam, bg=bg)
+    sure = _sure_hits(cam, geo)
+    _, dirs = pixel_rays(cam)
+    valid = np.all(sure != 0, axis=0)
+    checked = 0
+    for y, x in zip(*np.nonzero(valid)):
+        Y = real_sh_scipy(deg, dirs[y, x])
+        C, T = np.zeros(3), 1.0
+        for i, c in enumerate(coeffs):
+            if sure[i, y, x] < 0:
+                continue
+            c = c.astype(np.float64)
+            a = sigmoid(c[0])
+            rgb = sigmoid(np.array([c[1 + ch::3][:16] @ Y for ch in range(3)]))
+            C += T * a * rgb
+            T *= 1 - a
+        assert np.allclose(rgba[y, x, :3], C + T * np.asarray(bg), atol=1e-12)
+        assert abs(rgba[y, x, 3] - (1 - T)) < 1e-12
+        checked += 1
+    assert checked > 1000
+
+
+# ----------------------------------------------------------------------------
+# backward (Sec. 3 "Texturing Meshes": fitting texels through the renderer)
+# ----------------------------------------------------------------------------
+
+def _tiny_scene(fmt, degree, seed, size=4):
+    geo = synth.concentric_icospheres([1.0, 0.85], subdiv=1)
+    rng = np.random.default_rng(seed)
+    shells = []
+    for (p, u, t) in geo:
+        if fmt == FMT_RGBA_F32:
+            tex = rng.uniform(0.1, 0.9, (size, size, 4))
+        else:
+            tex = rng.normal(0, 0.5, (size, size, synth.sh_channels(degree)))
+        shells.append(Shell(p, u, t, tex.astype(np.float64), fmt, degree))
+    return Scene(shells)
+
+
+@pytest.mark.parametrize("fmt,degree", [(FMT_RGBA_F32, 0), (FMT_SH_F16, 1), (FMT_SH_F16, 2)])
+def test_backward_matches_central_differences(fmt, degree):
+    sc = _tiny_scene(fmt, degree, seed=20 + degree)
+    cam = synth.look_at((0.7, -2.8, 0.9), width=20, height=18)
+    bg = (0.2, 0.4, 0.6)
+    hits, _, _ = oracle.raster_scene(sc, cam)
+    rng = np.random.default_rng(30)
+    g = rng.normal(size=(cam.height, cam.width, 3))
+    grads = oracle.backward(sc, cam, hits, g, bg=bg)
+
+    def loss():
+        return float((oracle.shade(sc, cam, hits, bg=bg, threads=1)[0][..., :3] * g).sum())
+
+    h = 1e-6
+    worst = 0.0
+    for i, s in enumerate(sc.shells):
+        flat = s.tex.reshape(-1)
+        for j in range(flat.size):
+            v0 = flat[j]
+            flat[j] = v0 + h
+            lp = loss()
+            flat[j] = v0 - h
+            lm = loss()
+            flat[j] = v0
+            fd = (lp - lm) / (2 * h)
+            worst = max(worst, abs(fd - grads[i].reshape(-1)[j]))
+    assert worst < 1e-7
+    assert max(np.abs(gr).max() for gr in grads) > 1e-2
+
+
+def test_backward_constant_texture_closed_form():
+    """Constant RGBA textures: bilinear weights sum to one, so the gradient
+    summed over a shell's texels is sum_pixels T_i a_i g for rgb and
+    sum_pixels T_i (c_i - A_{i+1}) . g for alpha (A = colour behind)."""
+    geo = synth.concentric_icospheres([1.0, 0.9, 0.8], subdiv=2)
+    colors = [np.array([0.9, 0.2, 0.1]), np.array([0.1, 0.8, 0.3]), np.array([0.2, 0.3, 0.95])]
+    alphas = [0.35, 0.6, 0.8]
+    shells = [constant_shell(p, u, t, list(c) + [a], dtype=np.float64)
+              for (p, u, t), c, a in zip(geo, colors, alphas)]
+    sc = Scene(shells)
+    cam = synth.look_at((1.1, -2.6, 0.7), width=40, height=40)
+    bg = np.array([0.3, 0.1, 0.5])
+    hits, _, _ = oracle.raster_scene(sc, cam)
+    g = np.random.default_rng(12).normal(size=(40, 40, 3))
+    grads = oracle.backward(sc, cam, hits, g, bg=bg)
+    want_rgb = np.zeros((3, 3))
+    want_a = np.zeros(3)
+    for y in range(40):
+        for x in range(40):
+            on = [i for i in range(3) if hits[i, y, x] >= 0]
+            T, Ts = 1.0, {}
+            for i in on:
+                Ts[i] = T
+                T *= 1 - alphas[i]
+            A = bg.copy()
+            for i in reversed(on):
+                want_rgb[i] += Ts[i] * alphas[i] * g[y, x]
+                want_a[i] += Ts[i] * (colors[i] - A) @ g[y, x]
+                A = alphas[i] * colors[i] + (1 - alphas[i]) * A
+    for i in range(3):
+        assert np.allclose(grads[i][..., :3].sum((0, 1)), want_rgb[i], atol=1e-10)
+        assert abs(grads[i][..., 3].sum() - want_a[i]) < 1e-10
+
+
+# ----------------------------------------------------------------------------
+# the workloads themselves
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c4", "c5"])
+def test_workloads_cull_nothing_at_near_plane_or_guard_band(name):
+    """Cameras stay outside the shells: no triangle crosses the near plane or
+    leaves the guard band, so culling is back faces only."""
+    objs = synth.config_scene(name, scale=0.002, views=2)
+    for sc, cams in objs[:4]:
+        for cam in cams[:2]:
+            for s in sc.shells:
+                xy, invw, q, flags = oracle.setup_vertices(s.pos, cam)
+                assert np.all(flags == 0)
