@@ -1,0 +1,235 @@
+/*
+ * vs.h -- C ABI of the GB300 (sm_103a) k-shell renderer ("Volumetric
+ * Surfaces", arXiv 2409.02482).
+ *
+ * A baked Volumetric-Surfaces asset is k nested, semi-transparent,
+ * UV-textured triangle meshes ("shells").  A frame rasterizes every shell in
+ * a fixed outer-to-inner order, each with its own nearest-hit test (Fig. 3c:
+ * only the first intersection with each surface is sampled), samples each
+ * hit's texture bilinearly at texel centres (Fig. 5), decodes spherical
+ * harmonics with the view direction (Sec. 3 "Texturing Meshes"), and
+ * alpha-composites the hits front to back (Eq. 6, with the transmittance of
+ * Eq. 1 taken over the *earlier* layers only).  No sorting is involved: the
+ * shell order is the blend order (Sec. 3 "Support Surfaces as Shells").
+ * The backward pass is the texel gradient used by the paper's post-bake
+ * texture fitting (Sec. 3 "Texturing Meshes").
+ *
+ * Conventions shared by all entry points
+ * ---------------------------------------
+ * Memory.  Every pointer named "device" is CUDA device memory owned by the
+ *   caller; the library never allocates device memory.  Its only scratch is
+ *   the caller's `workspace` (size from vs_workspace_size).  A workspace must
+ *   be zero-filled once before its first use; afterwards calls keep it valid.
+ *   Calls that share a workspace must not overlap on the GPU.
+ * Streams.  Work is enqueued asynchronously on `stream` (NULL = the legacy
+ *   default stream); no call synchronizes except vs_read_stats.
+ * Errors.  Every call returns a vs_status; nothing aborts or throws across the
+ *   ABI.  Argument errors are detected on the host before anything is
+ *   enqueued.  Errors found on the device (a bounded wait that ran out,
+ *   a malformed input detected while running) are recorded in the workspace
+ *   and returned by vs_read_stats.  vs_last_error() gives a message for the
+ *   calling thread's last failure.
+ * Layouts.  Row-major, C order.  Shell 0 is the OUTERMOST; the library never
+ *   reorders shells.  Triangles are counter-clockwise seen from outside
+ *   (front faces).  Texel (x, y) is centred at UV ((x+1/2)/W, (y+1/2)/H),
+ *   row 0 at v = 0, clamp-to-edge addressing, no mipmaps.
+ * Cameras.  OpenCV pinhole: x right, y down, z forward; pixel (x, y) is
+ *   sampled once at its centre (x + 1/2, y + 1/2).
+ * Exactness.  Which triangle a pixel sees in each shell is decided in
+ *   integer arithmetic after a fixed FP32 vertex transform (1/256-pixel
+ *   snapping, top-left fill rule, exact depth-key interpolation, ties to the
+ *   lower triangle index), so hit IDs are reproducible bit for bit.  Colours
+ *   and gradients are FP32 (no FP64 on the GPU).
+ */
+#ifndef VS_H_
+#define VS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t vs_status;
+#define VS_OK 0
+#define VS_ERR_INVALID_ARG (-1) /* bad pointer, size, format or range     */
+#define VS_ERR_CUDA (-2)        /* a CUDA runtime call failed              */
+#define VS_ERR_UNSUPPORTED (-3) /* valid but not implemented combination   */
+#define VS_ERR_WORKSPACE (-4)   /* workspace NULL, too small or misaligned */
+#define VS_ERR_OVERFLOW (-5)    /* a size exceeds a documented limit       */
+#define VS_ERR_TIMEOUT (-6)     /* a bounded device wait ran out           */
+
+/* cudaStream_t without including the CUDA headers. */
+typedef struct CUstream_st* vs_stream_t;
+
+typedef struct vs_ctx vs_ctx;       /* opaque: device id and its properties */
+typedef struct vs_object vs_object; /* opaque: k shells (non-owning views)  */
+
+/* Texel formats.
+ * VS_TEX_RGBA_F32: float32 (r, g, b, alpha), used as stored.
+ * VS_TEX_SH_F16:   float16 [a, r0, g0, b0, r1, g1, b1, ...]: one alpha logit
+ *   and the (d+1)^2 RGB spherical-harmonic coefficients of degree d <= 3,
+ *   coefficient-major with channels interleaved (the paper's baked layout
+ *   stores coefficient i of every channel in image i, Sec. 3 "Baking
+ *   Textures").  alpha = sigmoid(a), rgb = sigmoid(sum_m sh_m Y_m(v)) with v
+ *   the unit ray direction and Y_m the real orthonormal SH (l = 1 band
+ *   proportional to (y, z, x)), index m = l^2 + l + m'.
+ *   C = 1 + 3 (d+1)^2 values: 4, 13, 28, 49 for d = 0..3.
+ */
+#define VS_TEX_RGBA_F32 0
+#define VS_TEX_SH_F16 1
+
+/* One shell.  All pointers are device memory, kept alive by the caller until
+ * vs_free_shells. */
+typedef struct {
+  const float* pos;      /* [num_verts, 3] object = world space          */
+  int32_t num_verts;     /* 3 <= num_verts <= 2^30                       */
+  const float* uv;       /* [num_verts, 2]                                */
+  const int32_t* tris;   /* [num_tris, 3] vertex indices, CCW = front    */
+  int32_t num_tris;      /* 1 <= num_tris <= 2^31 - 2                    */
+  const void* texels;    /* [tex_h, tex_w, texel_pitch] of the format's type */
+  int32_t tex_w, tex_h;  /* 1 .. 65536 each                               */
+  int32_t format;        /* VS_TEX_*                                      */
+  int32_t sh_degree;     /* 0..3 for VS_TEX_SH_F16, ignored otherwise     */
+  int32_t texel_pitch;   /* values per texel in memory, >= C (padding ok) */
+} vs_shell_desc;
+
+typedef struct {
+  float world_to_cam[12]; /* row-major 3x4 [R | t]                        */
+  float fx, fy, cx, cy;   /* pinhole intrinsics in pixels                  */
+  float znear;            /* > 0; faces with a vertex nearer are culled   */
+  int32_t width, height;  /* 1 .. 8192 each                                */
+} vs_camera;
+
+/* Flags (bitwise OR). */
+#define VS_FLAG_LOSS_L2 (1u << 0)
+/* Backward only: `grad_rgb` holds the TARGET image [H, W, 3] instead of a
+ * gradient; the kernel uses dL/dC = 2 (C - target) / (3 H W), i.e. the
+ * gradient of the mean squared error over pixels and RGB channels, computing
+ * C itself from the hits, and adds L to `loss` when that pointer is set. */
+#define VS_FLAG_TEST_STALL (1u << 30)
+/* Test hook for failure detection: the persistent batch kernel's first
+ * shading unit waits for a counter that nothing increments, with a short
+ * spin limit, so the call ends with VS_ERR_TIMEOUT recorded in the
+ * workspace.  The wait is bounded; the context stays usable. */
+
+/* Limits. */
+#define VS_MAX_SHELLS 16
+#define VS_MAX_IMAGE_SIDE 8192
+
+/* --- context ------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device` (queries its properties; makes
+ * no allocation).  Errors: VS_ERR_INVALID_ARG (ctx NULL), VS_ERR_CUDA (no
+ * such device). */
+vs_status vs_create(vs_ctx** ctx, int device);
+vs_status vs_destroy(vs_ctx* ctx);
+
+/* Message of the calling thread's last failed call ("" if none).  Valid
+ * until the thread's next call into the library. */
+const char* vs_last_error(void);
+
+/* --- assets ---------------------------------------------------------------- */
+
+/* Wraps k shells (index 0 = outermost) into an object.  Copies the
+ * descriptors (host memory only); the device arrays stay the caller's.
+ * Errors: VS_ERR_INVALID_ARG for k outside [1, VS_MAX_SHELLS], NULL
+ * pointers, sizes out of range, unknown format, texel_pitch < C, SH degree
+ * outside [0, 3]. */
+vs_status vs_load_shells(vs_ctx* ctx, const vs_shell_desc* shells, int32_t k, vs_object** out);
+vs_status vs_free_shells(vs_ctx* ctx, vs_object* obj);
+
+/* --- scratch ------------------------------------------------------------------ */
+
+/* Bytes of workspace needed to render (and differentiate) the n_items
+ * (object, camera) pairs in ONE vs_render_batch call; for n_items = 1 it
+ * also covers vs_render / vs_render_backward of that pair.  Dominant terms
+ * per item: 8 * k * H * W (per-shell visibility words) + 16 * sum(V) +
+ * 4 * sum(T).  Pure host arithmetic.  Errors: VS_ERR_INVALID_ARG. */
+vs_status vs_workspace_size(vs_ctx* ctx, const vs_object* const* objs, const vs_camera* cams,
+                            int32_t n_items, uint32_t flags, size_t* bytes);
+
+/* --- forward ------------------------------------------------------------------ */
+
+/* Renders one object from one camera.
+ *   bg        host float[3], background colour (NULL = black)
+ *   out_rgba  device float32 [H, W, 4] = (C + T bg, 1 - T), T the
+ *             transmittance left after the last shell
+ *   hits      device int32 [k, H, W] shell-local triangle index of each
+ *             shell's nearest front-facing hit, -1 = miss; may be NULL.
+ *             The only state vs_render_backward needs.
+ *   workspace device, >= vs_workspace_size(obj, cam, 1), 256-byte aligned
+ * Launches, in order: clear + vertex setup, small-triangle raster, large-
+ * triangle raster, shade + composite. */
+vs_status vs_render(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, const float* bg,
+                    float* out_rgba, int32_t* hits, void* workspace, size_t ws_bytes,
+                    uint32_t flags, vs_stream_t stream);
+
+/* --- backward ------------------------------------------------------------------- */
+
+/* Accumulates dL/d(texel values) into grad_texels given dL/d(output rgb).
+ *   hits         device int32 [k, H, W] as written by vs_render for the same
+ *                object, camera and texels
+ *   grad_rgb     device float32 [H, W, 3] (or the target image with
+ *                VS_FLAG_LOSS_L2)
+ *   grad_texels  host array of k device pointers, each float32
+ *                [tex_h, tex_w, texel_pitch]; ADDED to (zero them first);
+ *                padding values receive nothing
+ *   loss         device float32 scalar, L added (VS_FLAG_LOSS_L2 only; may
+ *                be NULL)
+ * Transmittance is recomputed from the hits, not stored.  Gradients use
+ * float atomics: summation order, hence the last bits, vary run to run. */
+vs_status vs_render_backward(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam,
+                             const float* bg, const int32_t* hits, const float* grad_rgb,
+                             float* const* grad_texels, float* loss, void* workspace,
+                             size_t ws_bytes, uint32_t flags, vs_stream_t stream);
+
+/* --- batch ------------------------------------------------------------------------ */
+
+typedef struct {
+  const vs_object* obj;
+  vs_camera cam;
+  float* out_rgba;            /* device [H, W, 4]; required               */
+  int32_t* hits;              /* device [k, H, W] or NULL                 */
+  const float* grad_rgb;      /* device [H, W, 3] (do_backward only)      */
+  float* const* grad_texels;  /* host array of k device pointers (bwd)    */
+  float* loss;                /* device scalar or NULL (VS_FLAG_LOSS_L2)  */
+} vs_batch_item;
+
+/* Renders n items -- any mix of objects, shell counts, triangle counts and
+ * resolutions -- in ONE persistent kernel launch (after small launches that
+ * copy the item table into the workspace).  Work units are handed out in a
+ * fixed global order (all vertex setup, then raster, then shading); a unit
+ * waits, with a bounded spin, only for units handed out before it, so the
+ * launch cannot deadlock.  With do_backward, each pixel's forward result is
+ * differentiated in the same unit (fused forward + backward) using
+ * grad_rgb -- with VS_FLAG_LOSS_L2, the target image.  Forward outputs are
+ * bit-identical to vs_render of each item.  All enqueued work is
+ * capturable in a CUDA graph (the item table travels in kernel parameters).
+ * Errors: as vs_render; VS_ERR_INVALID_ARG for n < 1. */
+vs_status vs_render_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, const float* bg,
+                          int32_t do_backward, void* workspace, size_t ws_bytes, uint32_t flags,
+                          vs_stream_t stream);
+
+/* --- status and counters --------------------------------------------------------- */
+
+typedef struct {
+  vs_status device_status;   /* first error recorded on the device, or VS_OK  */
+  uint64_t fragments;        /* (pixel, shell) pairs shaded (hits)            */
+  uint64_t tris_front;       /* triangles rasterized (front-facing, valid)    */
+  uint64_t tris_culled_back; /* back-facing or zero-area                       */
+  uint64_t tris_culled_near; /* a vertex nearer than znear                    */
+  uint64_t tris_culled_guard;/* a vertex beyond +-32768 px                    */
+  uint64_t tris_large;       /* rasterized cooperatively by a whole block     */
+} vs_stats;
+
+/* Synchronizes `stream`, copies the counters accumulated in `workspace`
+ * since the last reset into *out, and (reset != 0) zeroes them and the
+ * device status.  The only call that synchronizes. */
+vs_status vs_read_stats(void* workspace, vs_stream_t stream, int32_t reset, vs_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VS_H_ */

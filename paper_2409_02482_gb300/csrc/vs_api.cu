@@ -1,0 +1,427 @@
+// Host side of the C ABI declared in include/vs.h: argument checking,
+// workspace layout, the item table and kernel launches.  No device memory is
+// ever allocated here; the caller's workspace is the only scratch.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vs.h"
+#include "vs_device.cuh"
+#include "vs_kernels.h"
+
+using namespace vsd;
+
+struct vs_ctx {
+  int device;
+  int num_sms;
+  int persist_blocks_per_sm;
+};
+
+struct vs_object {
+  int32_t k;
+  vs_shell_desc shells[VS_MAX_SHELLS];
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+vs_status fail(vs_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+vs_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(VS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int nch_of(const vs_shell_desc& s) {
+  return s.format == VS_TEX_RGBA_F32 ? 4 : 1 + 3 * (s.sh_degree + 1) * (s.sh_degree + 1);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int gcd_pow2(uint64_t a, int cap) {  // largest power of two <= cap dividing a
+  int g = 1;
+  while (g < cap && (a % (uint64_t)(2 * g)) == 0) g *= 2;
+  return g;
+}
+
+vs_status check_shell(const vs_shell_desc& s, int i) {
+  if (!s.pos || !s.uv || !s.tris || !s.texels) return fail(VS_ERR_INVALID_ARG, "shell %d: NULL array", i);
+  if (s.num_verts < 3 || s.num_verts > (1 << 30)) return fail(VS_ERR_INVALID_ARG, "shell %d: num_verts %d out of [3, 2^30]", i, s.num_verts);
+  if (s.num_tris < 1 || s.num_tris > 0x7FFFFFFE) return fail(VS_ERR_INVALID_ARG, "shell %d: num_tris %d out of range", i, s.num_tris);
+  if (s.tex_w < 1 || s.tex_h < 1 || s.tex_w > 65536 || s.tex_h > 65536)
+    return fail(VS_ERR_INVALID_ARG, "shell %d: texture %dx%d out of [1, 65536]", i, s.tex_w, s.tex_h);
+  if (s.format != VS_TEX_RGBA_F32 && s.format != VS_TEX_SH_F16) return fail(VS_ERR_INVALID_ARG, "shell %d: unknown format %d", i, s.format);
+  if (s.format == VS_TEX_SH_F16 && (s.sh_degree < 0 || s.sh_degree > 3)) return fail(VS_ERR_INVALID_ARG, "shell %d: SH degree %d out of [0, 3]", i, s.sh_degree);
+  if (s.texel_pitch < nch_of(s)) return fail(VS_ERR_INVALID_ARG, "shell %d: texel_pitch %d < %d values", i, s.texel_pitch, nch_of(s));
+  size_t esz = s.format == VS_TEX_RGBA_F32 ? 4 : 2;
+  if ((uintptr_t)s.pos % 4 || (uintptr_t)s.uv % 8 || (uintptr_t)s.tris % 4 || (uintptr_t)s.texels % esz)
+    return fail(VS_ERR_INVALID_ARG, "shell %d: misaligned array (pos 4 B, uv 8 B, tris 4 B, texels %zu B)", i, esz);
+  return VS_OK;
+}
+
+vs_status check_camera(const vs_camera* c) {
+  if (!c) return fail(VS_ERR_INVALID_ARG, "camera is NULL");
+  if (c->width < 1 || c->height < 1 || c->width > VS_MAX_IMAGE_SIDE || c->height > VS_MAX_IMAGE_SIDE)
+    return fail(VS_ERR_INVALID_ARG, "image %dx%d out of [1, %d]", c->width, c->height, VS_MAX_IMAGE_SIDE);
+  if (!(c->znear > 0.0f) || !(c->fx != 0.0f) || !(c->fy != 0.0f))
+    return fail(VS_ERR_INVALID_ARG, "camera needs znear > 0 and nonzero focal lengths");
+  for (int i = 0; i < 12; ++i)
+    if (!(c->world_to_cam[i] == c->world_to_cam[i])) return fail(VS_ERR_INVALID_ARG, "camera matrix has NaN");
+  return VS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// planning: workspace layout + the host copy of the item table
+// ---------------------------------------------------------------------------
+struct ItemReq {
+  const vs_object* obj;
+  const vs_camera* cam;
+  float* out;
+  int32_t* hits;
+  const float* grad_rgb;
+  float* const* grad_tex;
+  float* loss;
+};
+
+struct Plan {
+  size_t off_items, off_shells, off_done, off_pre, table_end, total;
+  std::vector<DItem> items;
+  std::vector<DShell> shells;
+  std::vector<int> pre;          // [4][n+1]
+  int phase_total[NPH];
+  int phase_start[NPH];
+  int total_units;
+};
+
+// Fills the plan; with ws == nullptr only sizes are computed.
+vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool clear_vis, uint32_t flags,
+                    char* ws, Plan& P) {
+  size_t off = sizeof(WsHeader);
+  int S = 0;
+  for (int j = 0; j < n; ++j) S += req[j].obj->k;
+  P.off_items = off;
+  off = align256(off + sizeof(DItem) * (size_t)n);
+  P.off_shells = off;
+  off = align256(off + sizeof(DShell) * (size_t)S);
+  P.off_done = off;
+  off = align256(off + sizeof(int) * (size_t)n * NPH);
+  P.off_pre = off;
+  off = align256(off + sizeof(int) * (size_t)NPH * (n + 1));
+  P.table_end = off;
+  P.items.assign(n, DItem{});
+  P.shells.assign(S, DShell{});
+  P.pre.assign((size_t)NPH * (n + 1), 0);
+  int sidx = 0;
+  for (int j = 0; j < n; ++j) {
+    const vs_object& o = *req[j].obj;
+    const vs_camera& c = *req[j].cam;
+    DItem& it = P.items[j];
+    std::memcpy(it.cam.m, c.world_to_cam, sizeof it.cam.m);
+    it.cam.fx = c.fx; it.cam.fy = c.fy; it.cam.cx = c.cx; it.cam.cy = c.cy; it.cam.znear = c.znear;
+    it.cam.W = c.width; it.cam.H = c.height;
+    it.out = reinterpret_cast<float4*>(req[j].out);
+    it.hits = req[j].hits;
+    it.grad_rgb = req[j].grad_rgb;
+    it.loss = req[j].loss;
+    it.k = o.k;
+    it.shell0 = sidx;
+    it.flags = (int)flags;
+    it.do_bwd = do_bwd;
+    it.stall = (flags & VS_FLAG_TEST_STALL) ? 1 : 0;
+    it.bg[0] = bg ? bg[0] : 0.f; it.bg[1] = bg ? bg[1] : 0.f; it.bg[2] = bg ? bg[2] : 0.f;
+    it.maxdeg = -1;
+    const size_t HW = (size_t)c.width * c.height;
+    // per-item workspace regions
+    it.large_count = reinterpret_cast<int32_t*>(ws ? ws + off : nullptr);
+    off = align256(off + sizeof(int32_t) * o.k);
+    it.setup_pre[0] = 0;
+    it.raster_pre[0] = 0;
+    for (int i = 0; i < o.k; ++i) {
+      const vs_shell_desc& d = o.shells[i];
+      DShell& s = P.shells[sidx + i];
+      s.pos = d.pos; s.uv = reinterpret_cast<const float2*>(d.uv); s.tris = d.tris; s.tex = d.texels;
+      s.grad = (do_bwd && req[j].grad_tex) ? req[j].grad_tex[i] : nullptr;
+      s.nv = d.num_verts; s.nt = d.num_tris; s.tw = d.tex_w; s.th = d.tex_h;
+      s.fmt = d.format; s.degree = d.format == VS_TEX_SH_F16 ? d.sh_degree : 0; s.pitch = d.texel_pitch;
+      const int esz = d.format == VS_TEX_RGBA_F32 ? 4 : 2;
+      const uint64_t tex_align = (uint64_t)(uintptr_t)d.texels | (uint64_t)d.texel_pitch * esz;
+      s.vec = d.format == VS_TEX_RGBA_F32 ? (gcd_pow2(tex_align, 16) >= 16 ? 4 : 1) : gcd_pow2(tex_align, 16) / 2;
+      if (s.grad) {
+        const uint64_t ga = (uint64_t)(uintptr_t)s.grad | (uint64_t)d.texel_pitch * 4;
+        s.gvec = gcd_pow2(ga, 16) / 4;
+        if (s.gvec < 1) s.gvec = 1;
+      } else {
+        s.gvec = 1;
+      }
+      if (d.format == VS_TEX_SH_F16) it.maxdeg = std::max(it.maxdeg, (int)d.sh_degree);
+      s.vsetup = reinterpret_cast<int4*>(ws ? ws + off : nullptr);
+      off = align256(off + sizeof(int4) * (size_t)d.num_verts);
+      s.large = reinterpret_cast<int32_t*>(ws ? ws + off : nullptr);
+      off = align256(off + sizeof(int32_t) * (size_t)d.num_tris);
+      it.setup_pre[i + 1] = it.setup_pre[i] + (d.num_verts + kSetupPerUnit - 1) / kSetupPerUnit;
+      it.raster_pre[i + 1] = it.raster_pre[i] + (d.num_tris + kRasterPerUnit - 1) / kRasterPerUnit;
+    }
+    it.vis = reinterpret_cast<unsigned long long*>(ws ? ws + off : nullptr);
+    if (clear_vis) off = align256(off + sizeof(unsigned long long) * o.k * HW);
+    const size_t vis_words = (size_t)o.k * HW;
+    it.clear_units = clear_vis ? (int)((vis_words + kClearPerUnit - 1) / kClearPerUnit) : 0;
+    it.units[PH_SETUP] = it.clear_units + it.setup_pre[o.k];
+    it.units[PH_RASTER] = clear_vis ? it.raster_pre[o.k] : 0;
+    it.units[PH_LARGE] = clear_vis ? kLargeUnits : 0;
+    it.units[PH_SHADE] = (int)((HW + kShadePerUnit - 1) / kShadePerUnit);
+    sidx += o.k;
+  }
+  P.total = align256(off);
+  int g = 0;
+  for (int ph = 0; ph < NPH; ++ph) {
+    int* pre = P.pre.data() + ph * (n + 1);
+    pre[0] = 0;
+    for (int j = 0; j < n; ++j) pre[j + 1] = pre[j] + P.items[j].units[ph];
+    P.phase_total[ph] = pre[n];
+    P.phase_start[ph] = g;
+    g += pre[n];
+  }
+  P.total_units = g;
+  return VS_OK;
+}
+
+TableRef table_ref(const Plan& P, char* ws) {
+  TableRef t;
+  t.hdr = reinterpret_cast<WsHeader*>(ws);
+  t.items = reinterpret_cast<DItem*>(ws + P.off_items);
+  t.shells = reinterpret_cast<DShell*>(ws + P.off_shells);
+  t.done = reinterpret_cast<int*>(ws + P.off_done);
+  t.unit_pre = reinterpret_cast<const int*>(ws + P.off_pre);
+  t.n = (int)P.items.size();
+  t.total = P.total_units;
+  for (int i = 0; i < NPH; ++i) t.phase_start[i] = P.phase_start[i];
+  return t;
+}
+
+// Copies the table (items, shells, zeroed completion counters, unit
+// prefixes) into the workspace through kernel parameters.
+vs_status upload_table(const Plan& P, char* ws, cudaStream_t st) {
+  std::vector<char> blob(P.table_end - P.off_items, 0);
+  std::memcpy(blob.data(), P.items.data(), sizeof(DItem) * P.items.size());
+  std::memcpy(blob.data() + (P.off_shells - P.off_items), P.shells.data(), sizeof(DShell) * P.shells.size());
+  std::memcpy(blob.data() + (P.off_pre - P.off_items), P.pre.data(), sizeof(int) * P.pre.size());
+  static thread_local UploadChunk chunk;
+  size_t pos = 0;
+  bool first = true;
+  while (pos < blob.size() || first) {
+    const size_t nb = std::min(blob.size() - pos, (size_t)kUploadBytes);
+    chunk.dst_off = (uint32_t)(P.off_items + pos);
+    chunk.nbytes = (uint32_t)nb;
+    chunk.reset = first ? 1 : 0;
+    std::memcpy(chunk.data, blob.data() + pos, nb);
+    cudaError_t e = vsk::upload(ws, chunk, st);
+    if (e != cudaSuccess) return cuda_fail(e, "table upload launch");
+    pos += nb;
+    first = false;
+  }
+  return VS_OK;
+}
+
+vs_status check_ws(const Plan& P, void* ws, size_t ws_bytes) {
+  if (!ws) return fail(VS_ERR_WORKSPACE, "workspace is NULL");
+  if ((uintptr_t)ws % 256) return fail(VS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (ws_bytes < P.total) return fail(VS_ERR_WORKSPACE, "workspace has %zu bytes, needs %zu", ws_bytes, P.total);
+  if (P.table_end - P.off_items > ((size_t)1 << 31)) return fail(VS_ERR_OVERFLOW, "item table too large");
+  if ((long long)P.total_units > 0x7FFFFFFFll) return fail(VS_ERR_OVERFLOW, "too many work units");
+  return VS_OK;
+}
+
+vs_status check_item(const vs_ctx* ctx, const vs_object* obj, const vs_camera* cam) {
+  if (!ctx) return fail(VS_ERR_INVALID_ARG, "ctx is NULL");
+  if (!obj) return fail(VS_ERR_INVALID_ARG, "object is NULL");
+  return check_camera(cam);
+}
+
+vs_status set_device(const vs_ctx* ctx) {
+  cudaError_t e = cudaSetDevice(ctx->device);
+  return e == cudaSuccess ? VS_OK : cuda_fail(e, "cudaSetDevice");
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char* vs_last_error(void) { return g_err.c_str(); }
+
+vs_status vs_create(vs_ctx** ctx, int device) {
+  if (!ctx) return fail(VS_ERR_INVALID_ARG, "ctx is NULL");
+  *ctx = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= n) return fail(VS_ERR_CUDA, "device %d not present (%d devices)", device, n);
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  vs_ctx* c = new (std::nothrow) vs_ctx{};
+  if (!c) return fail(VS_ERR_INVALID_ARG, "out of host memory");
+  c->device = device;
+  if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+  if ((e = vsk::persistent_occupancy(&c->persist_blocks_per_sm)) != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "occupancy query");
+  }
+  if (c->persist_blocks_per_sm < 1) c->persist_blocks_per_sm = 1;
+  *ctx = c;
+  g_err.clear();
+  return VS_OK;
+}
+
+vs_status vs_destroy(vs_ctx* ctx) {
+  delete ctx;
+  return VS_OK;
+}
+
+vs_status vs_load_shells(vs_ctx* ctx, const vs_shell_desc* shells, int32_t k, vs_object** out) {
+  if (!ctx || !shells || !out) return fail(VS_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (k < 1 || k > VS_MAX_SHELLS) return fail(VS_ERR_INVALID_ARG, "k = %d out of [1, %d]", k, VS_MAX_SHELLS);
+  for (int i = 0; i < k; ++i) {
+    vs_status s = check_shell(shells[i], i);
+    if (s != VS_OK) return s;
+  }
+  vs_object* o = new (std::nothrow) vs_object{};
+  if (!o) return fail(VS_ERR_INVALID_ARG, "out of host memory");
+  o->k = k;
+  std::memcpy(o->shells, shells, sizeof(vs_shell_desc) * k);
+  *out = o;
+  return VS_OK;
+}
+
+vs_status vs_free_shells(vs_ctx* ctx, vs_object* obj) {
+  (void)ctx;
+  delete obj;
+  return VS_OK;
+}
+
+vs_status vs_workspace_size(vs_ctx* ctx, const vs_object* const* objs, const vs_camera* cams, int32_t n_items,
+                            uint32_t flags, size_t* bytes) {
+  (void)ctx;
+  if (!objs || !cams || !bytes) return fail(VS_ERR_INVALID_ARG, "NULL argument");
+  if (n_items < 1) return fail(VS_ERR_INVALID_ARG, "n_items = %d < 1", n_items);
+  std::vector<ItemReq> req(n_items);
+  for (int j = 0; j < n_items; ++j) {
+    if (!objs[j]) return fail(VS_ERR_INVALID_ARG, "object %d is NULL", j);
+    vs_status s = check_camera(&cams[j]);
+    if (s != VS_OK) return s;
+    req[j] = ItemReq{objs[j], &cams[j], nullptr, nullptr, nullptr, nullptr, nullptr};
+  }
+  Plan P;
+  vs_status s = make_plan(req.data(), n_items, nullptr, 1, true, flags, nullptr, P);
+  if (s != VS_OK) return s;
+  *bytes = P.total;
+  return VS_OK;
+}
+
+vs_status vs_render(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, const float* bg, float* out_rgba,
+                    int32_t* hits, void* workspace, size_t ws_bytes, uint32_t flags, vs_stream_t stream) {
+  vs_status s = check_item(ctx, obj, cam);
+  if (s != VS_OK) return s;
+  if (!out_rgba) return fail(VS_ERR_INVALID_ARG, "out_rgba is NULL");
+  if ((uintptr_t)out_rgba % 16) return fail(VS_ERR_INVALID_ARG, "out_rgba must be 16-byte aligned");
+  ItemReq r{obj, cam, out_rgba, hits, nullptr, nullptr, nullptr};
+  Plan P;
+  char* ws = static_cast<char*>(workspace);
+  if ((s = make_plan(&r, 1, bg, 0, true, flags & ~VS_FLAG_TEST_STALL, ws, P)) != VS_OK) return s;
+  if ((s = check_ws(P, workspace, ws_bytes)) != VS_OK) return s;
+  if ((s = set_device(ctx)) != VS_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if ((s = upload_table(P, ws, st)) != VS_OK) return s;
+  cudaError_t e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, st);
+  return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render launch");
+}
+
+vs_status vs_render_backward(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, const float* bg,
+                             const int32_t* hits, const float* grad_rgb, float* const* grad_texels, float* loss,
+                             void* workspace, size_t ws_bytes, uint32_t flags, vs_stream_t stream) {
+  vs_status s = check_item(ctx, obj, cam);
+  if (s != VS_OK) return s;
+  if (!hits || !grad_rgb || !grad_texels) return fail(VS_ERR_INVALID_ARG, "hits, grad_rgb and grad_texels are required");
+  for (int i = 0; i < obj->k; ++i)
+    if (!grad_texels[i] || (uintptr_t)grad_texels[i] % 4) return fail(VS_ERR_INVALID_ARG, "grad_texels[%d] NULL or misaligned", i);
+  ItemReq r{obj, cam, nullptr, const_cast<int32_t*>(hits), grad_rgb, grad_texels, loss};
+  Plan P;
+  char* ws = static_cast<char*>(workspace);
+  if ((s = make_plan(&r, 1, bg, 1, false, flags & ~VS_FLAG_TEST_STALL, ws, P)) != VS_OK) return s;
+  if ((s = check_ws(P, workspace, ws_bytes)) != VS_OK) return s;
+  if ((s = set_device(ctx)) != VS_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if ((s = upload_table(P, ws, st)) != VS_OK) return s;
+  cudaError_t e = vsk::plain_backward(table_ref(P, ws), P.items[0].units, st);
+  return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_backward launch");
+}
+
+vs_status vs_render_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, const float* bg, int32_t do_backward,
+                          void* workspace, size_t ws_bytes, uint32_t flags, vs_stream_t stream) {
+  if (!ctx || !items) return fail(VS_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1) return fail(VS_ERR_INVALID_ARG, "n = %d < 1", n);
+  std::vector<ItemReq> req(n);
+  for (int j = 0; j < n; ++j) {
+    const vs_batch_item& b = items[j];
+    vs_status s = check_item(ctx, b.obj, &b.cam);
+    if (s != VS_OK) return fail(s, "item %d: %s", j, g_err.c_str());
+    if (!b.out_rgba || (uintptr_t)b.out_rgba % 16) return fail(VS_ERR_INVALID_ARG, "item %d: out_rgba NULL or not 16-byte aligned", j);
+    if (do_backward) {
+      if (!b.grad_rgb || !b.grad_texels) return fail(VS_ERR_INVALID_ARG, "item %d: backward needs grad_rgb and grad_texels", j);
+      for (int i = 0; i < b.obj->k; ++i)
+        if (!b.grad_texels[i] || (uintptr_t)b.grad_texels[i] % 4) return fail(VS_ERR_INVALID_ARG, "item %d: grad_texels[%d] NULL or misaligned", j, i);
+    }
+    req[j] = ItemReq{b.obj, &b.cam, b.out_rgba, b.hits, b.grad_rgb, b.grad_texels, b.loss};
+  }
+  Plan P;
+  char* ws = static_cast<char*>(workspace);
+  vs_status s = make_plan(req.data(), n, bg, do_backward ? 1 : 0, true, flags, ws, P);
+  if (s != VS_OK) return s;
+  if ((s = check_ws(P, workspace, ws_bytes)) != VS_OK) return s;
+  if ((s = set_device(ctx)) != VS_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if ((s = upload_table(P, ws, st)) != VS_OK) return s;
+  const int grid = ctx->num_sms * ctx->persist_blocks_per_sm;
+  const long long spin_limit = 1ll << 24;   // ~ seconds with 200 ns sleeps
+  cudaError_t e = vsk::persistent(table_ref(P, ws), grid, spin_limit, st);
+  return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_batch launch");
+}
+
+vs_status vs_read_stats(void* workspace, vs_stream_t stream, int32_t reset, vs_stats* out) {
+  if (!workspace || !out) return fail(VS_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  WsHeader h;
+  if ((e = cudaMemcpy(&h, workspace, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  out->device_status = h.status;
+  out->fragments = h.frags;
+  out->tris_front = h.front;
+  out->tris_culled_back = h.back;
+  out->tris_culled_near = h.nearc;
+  out->tris_culled_guard = h.guard;
+  out->tris_large = h.large;
+  if (reset) {
+    if ((e = cudaMemset(workspace, 0, sizeof h)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+  }
+  return VS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,505 @@
+// Device-side building blocks of the k-shell renderer (sm_103a).
+//
+// Everything a kernel needs is here as __device__ functions so that the
+// per-phase kernels of vs_render and the persistent kernel of
+// vs_render_batch run the very same arithmetic (batched forward output is
+// bit-identical to the plain launches).  The file is compiled with
+// --fmad=false: no multiply-add is fused unless written as fmaf(), so the
+// arithmetic does not depend on where a function gets inlined.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "vs.h"
+
+namespace vsd {
+
+// ----------------------------------------------------------------------------
+// tuning constants and table layout
+// ----------------------------------------------------------------------------
+constexpr int kThreads = 256;          // threads per block, all kernels
+constexpr int kSetupPerUnit = 1024;    // vertices per setup unit
+constexpr int kRasterPerUnit = 256;    // triangles per raster unit (1 / thread)
+constexpr int kClearPerUnit = 65536;   // visibility words cleared per unit
+constexpr int kShadePerUnit = 256;     // pixels per shading unit (1 / thread)
+constexpr int kLargeUnits = 8;         // large-triangle units per item
+constexpr int kSmallMaxPixels = 64;    // bbox pixels one thread rasterizes
+constexpr int kMaxShells = VS_MAX_SHELLS;
+
+enum { PH_SETUP = 0, PH_RASTER = 1, PH_LARGE = 2, PH_SHADE = 3, NPH = 4 };
+
+constexpr int kInvalidX = -2147483647 - 1;   // vertex marker: culled
+enum { VTX_NEAR = 1, VTX_GUARD = 2 };
+
+struct alignas(16) DCam {
+  float m[12];                 // world -> camera [R | t], row-major
+  float fx, fy, cx, cy, znear;
+  int32_t W, H;
+  int32_t pad;
+};
+
+struct alignas(16) DShell {
+  const float* pos;            // [nv, 3]
+  const float2* uv;            // [nv]
+  const int32_t* tris;         // [nt, 3]
+  const void* tex;             // [th, tw, pitch]
+  float* grad;                 // [th, tw, pitch] FP32 (backward) or null
+  int4* vsetup;                // [nv] (X, Y, bits(1/w), q) -- workspace
+  int32_t* large;              // [nt] large-triangle list -- workspace
+  int32_t nv, nt, tw, th;
+  int32_t fmt, degree, pitch;
+  int32_t vec;                 // texel load width in values (1, 2, 4, 8)
+  int32_t gvec;                // gradient atomic width in floats (1, 2, 4)
+  int32_t pad0, pad1, pad2;
+};
+
+struct alignas(16) DItem {
+  DCam cam;
+  float4* out;                 // [H*W]
+  int32_t* hits;               // [k, H*W] or null
+  const float* grad_rgb;       // [H*W, 3] gradient or target, or null
+  float* loss;                 // scalar or null
+  unsigned long long* vis;     // [k, H*W] -- workspace
+  int32_t* large_count;        // [k] -- workspace
+  int32_t k, shell0, maxdeg, clear_units;
+  int32_t flags, do_bwd, stall, pad;
+  int32_t units[NPH];
+  int32_t setup_pre[kMaxShells + 1];
+  int32_t raster_pre[kMaxShells + 1];
+  float bg[4];
+};
+
+// Workspace header (first 256 bytes).  status and the counters persist
+// across calls until vs_read_stats resets them; next_unit and abort are
+// reset by every call's table upload.
+struct alignas(16) WsHeader {
+  int32_t status;
+  int32_t abort;
+  uint32_t next_unit;
+  int32_t pad;
+  unsigned long long frags, front, back, nearc, guard, large;
+  unsigned long long reserved[24];
+};
+static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
+
+// ----------------------------------------------------------------------------
+// small helpers
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void record_error(WsHeader* h, int code) {
+  atomicCAS(&h->status, 0, code);
+}
+
+__device__ __forceinline__ void warp_count(unsigned long long* ctr, unsigned v) {
+  v = __reduce_add_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(ctr, (unsigned long long)v);
+}
+
+// ----------------------------------------------------------------------------
+// vertex stage: fixed FP32 transform, 1/256 px snap, depth key
+// ----------------------------------------------------------------------------
+// Each product and sum is rounded to FP32 in this order; the CPU oracle runs
+// the same sequence, so the snapped integers agree bit for bit.
+__device__ __forceinline__ int4 setup_vertex(const float* p, const DCam& c) {
+  const float x = p[0], y = p[1], z = p[2];
+  float xc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.m[0], x), __fmul_rn(c.m[1], y)),
+                                 __fmul_rn(c.m[2], z)), c.m[3]);
+  float yc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.m[4], x), __fmul_rn(c.m[5], y)),
+                                 __fmul_rn(c.m[6], z)), c.m[7]);
+  float zc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.m[8], x), __fmul_rn(c.m[9], y)),
+                                 __fmul_rn(c.m[10], z)), c.m[11]);
+  if (!(zc >= c.znear)) return make_int4(kInvalidX, 0, 0, VTX_NEAR);
+  const float iw = __frcp_rn(zc);
+  const float sx = __fadd_rn(__fmul_rn(__fmul_rn(c.fx, xc), iw), c.cx);
+  const float sy = __fadd_rn(__fmul_rn(__fmul_rn(c.fy, yc), iw), c.cy);
+  const float X = __fmul_rn(sx, 256.0f), Y = __fmul_rn(sy, 256.0f);
+  if (!(fabsf(X) < 8388608.0f && fabsf(Y) < 8388608.0f)) return make_int4(kInvalidX, 0, 0, VTX_GUARD);
+  const float qf = __fmul_rn(iw, __fmul_rn(c.znear, 1073741824.0f));
+  return make_int4(__float2int_rn(X), __float2int_rn(Y), __float_as_int(iw),
+                   (int)__float2uint_rn(qf));
+}
+
+// ----------------------------------------------------------------------------
+// triangle stage: integer edge functions, top-left rule, exact depth key
+// ----------------------------------------------------------------------------
+struct Tri {
+  int X[3], Y[3];
+  unsigned q[3];
+  float iw[3];
+  int tl[3];        // 1 if edge j (opposite vertex j) is a top or left edge
+  int xlo, xhi, ylo, yhi;
+};
+
+// 0 = front-facing and valid; 1 = back-facing or zero area; 2 = near; 3 = guard.
+__device__ __forceinline__ int make_tri(const int4 v0, const int4 v1, const int4 v2, int W, int H,
+                                        Tri& t) {
+  if (v0.x == kInvalidX || v1.x == kInvalidX || v2.x == kInvalidX) {
+    const int f = (v0.x == kInvalidX ? v0.w : 0) | (v1.x == kInvalidX ? v1.w : 0) |
+                  (v2.x == kInvalidX ? v2.w : 0);
+    return (f & VTX_NEAR) ? 2 : 3;
+  }
+  t.X[0] = v0.x; t.X[1] = v1.x; t.X[2] = v2.x;
+  t.Y[0] = v0.y; t.Y[1] = v1.y; t.Y[2] = v2.y;
+  const long long a2 = (long long)(t.X[1] - t.X[0]) * (t.Y[2] - t.Y[0]) -
+                       (long long)(t.X[2] - t.X[0]) * (t.Y[1] - t.Y[0]);
+  if (a2 >= 0) return 1;
+  t.q[0] = (unsigned)v0.w; t.q[1] = (unsigned)v1.w; t.q[2] = (unsigned)v2.w;
+  t.iw[0] = __int_as_float(v0.z); t.iw[1] = __int_as_float(v1.z); t.iw[2] = __int_as_float(v2.z);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int a = (j + 2) % 3, b = (j + 1) % 3;
+    const int gx = t.Y[a] - t.Y[b];   // d e_j / d px
+    const int gy = t.X[b] - t.X[a];   // d e_j / d py
+    t.tl[j] = (gx > 0) || (gx == 0 && gy > 0);
+  }
+  const int mnx = min(t.X[0], min(t.X[1], t.X[2])), mxx = max(t.X[0], max(t.X[1], t.X[2]));
+  const int mny = min(t.Y[0], min(t.Y[1], t.Y[2])), mxy = max(t.Y[0], max(t.Y[1], t.Y[2]));
+  // pixel centres 256 x + 128 within [mn, mx]
+  t.xlo = max(0, -((128 - mnx) >> 8));
+  t.xhi = min(W - 1, (mxx - 128) >> 8);
+  t.ylo = max(0, -((128 - mny) >> 8));
+  t.yhi = min(H - 1, (mxy - 128) >> 8);
+  return 0;
+}
+
+__device__ __forceinline__ void edge_values(const Tri& t, int px, int py, long long e[3]) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int a = (j + 2) % 3, b = (j + 1) % 3;
+    e[j] = (long long)(t.X[b] - t.X[a]) * (py - t.Y[a]) - (long long)(t.Y[b] - t.Y[a]) * (px - t.X[a]);
+  }
+}
+
+__device__ __forceinline__ bool covered(const Tri& t, const long long e[3]) {
+  return (e[0] + t.tl[0] > 0) && (e[1] + t.tl[1] > 0) && (e[2] + t.tl[2] > 0);
+}
+
+// floor(sum_j e_j q_j / sum_j e_j) exactly, for e_j >= 0 (sum > 0, < 2^51)
+// and q_j < 2^31.  The quotient lies between min q and max q, so it fits in
+// 32 bits; an FP32 estimate is within ~2^10 of it, which bounds the residual
+// R = N - Q S below 2^62 and lets R be computed exactly in wrapping 64-bit
+// arithmetic; two correction steps make it exact.
+__device__ __forceinline__ unsigned depth_key(const Tri& t, const long long e[3]) {
+  const unsigned long long S = (unsigned long long)(e[0] + e[1] + e[2]);
+  const unsigned long long N = (unsigned long long)e[0] * t.q[0] + (unsigned long long)e[1] * t.q[1] +
+                               (unsigned long long)e[2] * t.q[2];   // mod 2^64
+  const float fS = (float)S;
+  const float est = (fmaf((float)e[0], (float)t.q[0],
+                     fmaf((float)e[1], (float)t.q[1], (float)e[2] * (float)t.q[2]))) / fS;
+  const unsigned qmin = min(t.q[0], min(t.q[1], t.q[2])), qmax = max(t.q[0], max(t.q[1], t.q[2]));
+  unsigned Q = (unsigned)fminf(fmaxf(est, (float)qmin), (float)qmax);
+  Q = min(max(Q, qmin), qmax);
+  long long R = (long long)(N - (unsigned long long)Q * S);
+  Q = (unsigned)((long long)Q + (long long)floorf((float)R / fS));
+  R = (long long)(N - (unsigned long long)Q * S);
+#pragma unroll 1
+  for (int i = 0; i < 4 && R < 0; ++i) { --Q; R += (long long)S; }
+#pragma unroll 1
+  for (int i = 0; i < 4 && R >= (long long)S; ++i) { ++Q; R -= (long long)S; }
+  return Q;
+}
+
+__device__ __forceinline__ unsigned long long vis_key(unsigned K, int tri) {
+  return ((unsigned long long)K << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)tri);
+}
+
+__device__ __forceinline__ int vis_tri(unsigned long long key) {
+  return key ? (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull)) : -1;
+}
+
+// ----------------------------------------------------------------------------
+// float-float arithmetic (Dekker 1971 / Knuth TAOCP 4.2.2): used for UV
+// interpolation over triangles that span many texels
+// ----------------------------------------------------------------------------
+struct ff { float hi, lo; };
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff quick_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.hi, b.hi);
+  ff t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = quick_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  ff p = two_prod(a.hi, b.hi);
+  p.lo = __fadd_rn(p.lo, __fadd_rn(__fmul_rn(a.hi, b.lo), __fmul_rn(a.lo, b.hi)));
+  return quick_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  ff p = two_prod(a.hi, b);
+  p.lo = __fadd_rn(p.lo, __fmul_rn(a.lo, b));
+  return quick_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  ff r = ff_add(a, ff_mul_f({-b.hi, -b.lo}, q1));
+  const float q2 = __fdiv_rn(r.hi, b.hi);
+  r = ff_add(r, ff_mul_f({-b.hi, -b.lo}, q2));
+  const float q3 = __fdiv_rn(r.hi, b.hi);
+  ff q = quick_two_sum(q1, q2);
+  return ff_add(q, {q3, 0.0f});
+}
+__device__ __forceinline__ ff ll_to_ff(long long v) {
+  const float hi = __ll2float_rn(v);
+  const float lo = __ll2float_rn(v - __float2ll_rn(hi));
+  return {hi, lo};
+}
+
+// ----------------------------------------------------------------------------
+// attribute interpolation and the bilinear footprint
+// ----------------------------------------------------------------------------
+struct Footprint {
+  int x0, x1, y0, y1;  // clamped tap columns / rows
+  float fx, fy;        // weight of column x1 / row y1
+};
+
+// Integer part and fraction of (X0 - 1/2) + delta, with delta given as a
+// float-float; the fraction is returned rounded to FP32.
+__device__ __forceinline__ void split_coord(float X0, ff delta, int& i, float& f) {
+  const float a = __fsub_rn(X0, 0.5f);
+  const float base = floorf(a);
+  const float frac0 = __fsub_rn(a, base);          // exact, in [0, 1)
+  ff s = ff_add({frac0, 0.0f}, delta);
+  float fl = floorf(s.hi);
+  if (s.hi == fl && s.lo < 0.0f) fl = __fsub_rn(fl, 1.0f);
+  f = __fadd_rn(__fsub_rn(s.hi, fl), s.lo);
+  if (f >= 1.0f) { f = __fsub_rn(f, 1.0f); fl = __fadd_rn(fl, 1.0f); }
+  if (f < 0.0f) f = 0.0f;
+  i = (int)base + (int)fl;
+}
+
+// Perspective-correct UV of pixel centre (px, py) mapped to texel space
+// (x = u W - 1/2, y = v H - 1/2), interpolated relative to vertex 0.  For
+// triangles spanning at most 8 texels plain FP32 keeps the texel-space
+// error near 1e-6 texel; wider ones go through float-float.
+__device__ __forceinline__ Footprint footprint(const Tri& t, const float2 uv[3], int tw, int th,
+                                               int px, int py) {
+  long long e[3];
+  edge_values(t, px, py, e);
+  const float W = (float)tw, H = (float)th;
+  const float X0 = __fmul_rn(uv[0].x, W), X1 = __fmul_rn(uv[1].x, W), X2 = __fmul_rn(uv[2].x, W);
+  const float Y0 = __fmul_rn(uv[0].y, H), Y1 = __fmul_rn(uv[1].y, H), Y2 = __fmul_rn(uv[2].y, H);
+  const float d1x = __fsub_rn(X1, X0), d2x = __fsub_rn(X2, X0);
+  const float d1y = __fsub_rn(Y1, Y0), d2y = __fsub_rn(Y2, Y0);
+  const float span = fmaxf(fmaxf(fabsf(d1x), fabsf(d2x)), fmaxf(fabsf(d1y), fabsf(d2y)));
+  ff dx, dy;
+  if (span <= 8.0f) {
+    const float w0 = __fmul_rn((float)e[0], t.iw[0]);
+    const float w1 = __fmul_rn((float)e[1], t.iw[1]);
+    const float w2 = __fmul_rn((float)e[2], t.iw[2]);
+    const float rD = __frcp_rn(__fadd_rn(__fadd_rn(w0, w1), w2));
+    const float l1 = __fmul_rn(w1, rD), l2 = __fmul_rn(w2, rD);
+    dx = {__fmaf_rn(l1, d1x, __fmul_rn(l2, d2x)), 0.0f};
+    dy = {__fmaf_rn(l1, d1y, __fmul_rn(l2, d2y)), 0.0f};
+  } else {
+    const ff w0 = ff_mul_f(ll_to_ff(e[0]), t.iw[0]);
+    const ff w1 = ff_mul_f(ll_to_ff(e[1]), t.iw[1]);
+    const ff w2 = ff_mul_f(ll_to_ff(e[2]), t.iw[2]);
+    const ff D = ff_add(ff_add(w0, w1), w2);
+    const ff ex1 = two_sum(X1, -X0), ex2 = two_sum(X2, -X0);
+    const ff ey1 = two_sum(Y1, -Y0), ey2 = two_sum(Y2, -Y0);
+    dx = ff_div(ff_add(ff_mul(w1, ex1), ff_mul(w2, ex2)), D);
+    dy = ff_div(ff_add(ff_mul(w1, ey1), ff_mul(w2, ey2)), D);
+  }
+  Footprint f;
+  int ix, iy;
+  split_coord(X0, dx, ix, f.fx);
+  split_coord(Y0, dy, iy, f.fy);
+  f.x0 = min(max(ix, 0), tw - 1);
+  f.x1 = min(max(ix + 1, 0), tw - 1);
+  f.y0 = min(max(iy, 0), th - 1);
+  f.y1 = min(max(iy + 1, 0), th - 1);
+  return f;
+}
+
+// ----------------------------------------------------------------------------
+// real spherical harmonics, l <= 3 (orthonormal; l = 1 band ~ (y, z, x))
+// Constants are the closed-form normalisations:
+//   0.2820947917738782 = 1/(2 sqrt(pi))        0.4886025119029199 = sqrt(3/(4 pi))
+//   1.0925484305920792 = sqrt(15/pi)/2          0.31539156525252005 = sqrt(5/pi)/4
+//   0.5462742152960396 = sqrt(15/pi)/4          0.5900435899266435 = sqrt(35/(2 pi))/4
+//   2.890611442640554  = sqrt(105/pi)/2         0.4570457994644658 = sqrt(21/(2 pi))/4
+//   0.3731763325901154 = sqrt(7/pi)/4           1.445305721320277  = sqrt(105/pi)/4
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float Y[16]) {
+  Y[0] = 0.2820947917738782f;
+  if (deg < 1) return;
+  Y[1] = 0.4886025119029199f * y;
+  Y[2] = 0.4886025119029199f * z;
+  Y[3] = 0.4886025119029199f * x;
+  if (deg < 2) return;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = 1.0925484305920792f * (x * y);
+  Y[5] = 1.0925484305920792f * (y * z);
+  Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
+  Y[7] = 1.0925484305920792f * (x * z);
+  Y[8] = 0.5462742152960396f * (xx - yy);
+  if (deg < 3) return;
+  Y[9] = 0.5900435899266435f * y * (3.0f * xx - yy);
+  Y[10] = 2.890611442640554f * (x * y) * z;
+  Y[11] = 0.4570457994644658f * y * (4.0f * zz - xx - yy);
+  Y[12] = 0.3731763325901154f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+  Y[13] = 0.4570457994644658f * x * (4.0f * zz - xx - yy);
+  Y[14] = 1.445305721320277f * z * (xx - yy);
+  Y[15] = 0.5900435899266435f * x * (xx - 3.0f * yy);
+}
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + __expf(-x)); }
+
+// Unit world-space ray direction through pixel (x, y).
+__device__ __forceinline__ float3 ray_dir(const DCam& c, int x, int y) {
+  const float a = ((float)x + 0.5f - c.cx) / c.fx;
+  const float b = ((float)y + 0.5f - c.cy) / c.fy;
+  // world = R^T (a, b, 1)
+  float vx = c.m[0] * a + c.m[4] * b + c.m[8];
+  float vy = c.m[1] * a + c.m[5] * b + c.m[9];
+  float vz = c.m[2] * a + c.m[6] * b + c.m[10];
+  const float r = rsqrtf(vx * vx + vy * vy + vz * vz);
+  return make_float3(vx * r, vy * r, vz * r);
+}
+
+// ----------------------------------------------------------------------------
+// texel fetch + decode.  NCH values per texel, loaded VEC at a time.
+// ----------------------------------------------------------------------------
+template <int VEC>
+__device__ __forceinline__ void load_halves(const __half* p, float* out) {
+  if constexpr (VEC == 8) {
+    const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
+    const __half2* h = reinterpret_cast<const __half2*>(&r);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { float2 f = __half22float2(h[i]); out[2 * i] = f.x; out[2 * i + 1] = f.y; }
+  } else if constexpr (VEC == 4) {
+    const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+    const __half2* h = reinterpret_cast<const __half2*>(&r);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) { float2 f = __half22float2(h[i]); out[2 * i] = f.x; out[2 * i + 1] = f.y; }
+  } else if constexpr (VEC == 2) {
+    const unsigned r = __ldg(reinterpret_cast<const unsigned*>(p));
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&r));
+    out[0] = f.x; out[1] = f.y;
+  } else {
+    out[0] = __half2float(__ldg(p));
+  }
+}
+
+// Bilinear mix of the 4 taps' NCH values (fp16 storage), FP32 accumulate.
+template <int NCH, int VEC>
+__device__ __forceinline__ void bilinear_f16(const __half* tex, int tw, int pitch, const Footprint& f,
+                                             float val[NCH]) {
+  const float w00 = (1.0f - f.fx) * (1.0f - f.fy), w10 = f.fx * (1.0f - f.fy);
+  const float w01 = (1.0f - f.fx) * f.fy, w11 = f.fx * f.fy;
+  const __half* p00 = tex + ((size_t)f.y0 * tw + f.x0) * pitch;
+  const __half* p10 = tex + ((size_t)f.y0 * tw + f.x1) * pitch;
+  const __half* p01 = tex + ((size_t)f.y1 * tw + f.x0) * pitch;
+  const __half* p11 = tex + ((size_t)f.y1 * tw + f.x1) * pitch;
+  constexpr int NL = (NCH + VEC - 1) / VEC;
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    float a[VEC], b[VEC], c[VEC], d[VEC];
+    load_halves<VEC>(p00 + l * VEC, a);
+    load_halves<VEC>(p10 + l * VEC, b);
+    load_halves<VEC>(p01 + l * VEC, c);
+    load_halves<VEC>(p11 + l * VEC, d);
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) {
+      const int ch = l * VEC + i;
+      if (ch < NCH) val[ch] = fmaf(w11, d[i], fmaf(w01, c[i], fmaf(w10, b[i], w00 * a[i])));
+    }
+  }
+}
+
+template <int VEC>
+__device__ __forceinline__ void bilinear_rgba(const float* tex, int tw, int pitch, const Footprint& f,
+                                              float val[4]) {
+  const float w00 = (1.0f - f.fx) * (1.0f - f.fy), w10 = f.fx * (1.0f - f.fy);
+  const float w01 = (1.0f - f.fx) * f.fy, w11 = f.fx * f.fy;
+  const float* p[4] = {tex + ((size_t)f.y0 * tw + f.x0) * pitch, tex + ((size_t)f.y0 * tw + f.x1) * pitch,
+                       tex + ((size_t)f.y1 * tw + f.x0) * pitch, tex + ((size_t)f.y1 * tw + f.x1) * pitch};
+  float t[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if constexpr (VEC == 4) {
+      const float4 r = __ldg(reinterpret_cast<const float4*>(p[q]));
+      t[q][0] = r.x; t[q][1] = r.y; t[q][2] = r.z; t[q][3] = r.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) t[q][i] = __ldg(p[q] + i);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) val[i] = fmaf(w11, t[3][i], fmaf(w01, t[2][i], fmaf(w10, t[1][i], w00 * t[0][i])));
+}
+
+// Fragment colour and opacity.
+struct Frag {
+  float r, g, b, a;
+};
+
+template <int DEG>
+__device__ __forceinline__ Frag decode_sh(const float* val, const float Y[16]) {
+  constexpr int NB = (DEG + 1) * (DEG + 1);
+  float z[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int m = 0; m < NB; ++m) {
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) z[ch] = fmaf(val[1 + 3 * m + ch], Y[m], z[ch]);
+  }
+  return {sigmoidf_(z[0]), sigmoidf_(z[1]), sigmoidf_(z[2]), sigmoidf_(val[0])};
+}
+
+// ----------------------------------------------------------------------------
+// gradient scatter: dval (NCH values) * tap weight into 4 texels
+// ----------------------------------------------------------------------------
+template <int NCH, int GV>
+__device__ __forceinline__ void scatter_grad(float* grad, int tw, int pitch, const Footprint& f,
+                                             const float* dval) {
+  const float w[4] = {(1.0f - f.fx) * (1.0f - f.fy), f.fx * (1.0f - f.fy), (1.0f - f.fx) * f.fy,
+                      f.fx * f.fy};
+  const int xs[4] = {f.x0, f.x1, f.x0, f.x1}, ys[4] = {f.y0, f.y0, f.y1, f.y1};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float* g = grad + ((size_t)ys[q] * tw + xs[q]) * pitch;
+    constexpr int NL = (NCH + GV - 1) / GV;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      if constexpr (GV == 4) {
+        float4 v;
+        v.x = w[q] * dval[4 * l];
+        v.y = (4 * l + 1 < NCH) ? w[q] * dval[4 * l + 1] : 0.0f;
+        v.z = (4 * l + 2 < NCH) ? w[q] * dval[4 * l + 2] : 0.0f;
+        v.w = (4 * l + 3 < NCH) ? w[q] * dval[4 * l + 3] : 0.0f;
+        atomicAdd(reinterpret_cast<float4*>(g + 4 * l), v);
+      } else if constexpr (GV == 2) {
+        float2 v;
+        v.x = w[q] * dval[2 * l];
+        v.y = (2 * l + 1 < NCH) ? w[q] * dval[2 * l + 1] : 0.0f;
+        atomicAdd(reinterpret_cast<float2*>(g + 2 * l), v);
+      } else {
+        atomicAdd(g + l, w[q] * dval[l]);
+      }
+    }
+  }
+}
+
+}  // namespace vsd

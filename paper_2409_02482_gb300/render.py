@@ -1,0 +1,234 @@
+"""Python binding of the k-shell renderer: the C-ABI names, torch tensors in.
+
+PyTorch only supplies device memory and streams here; all rendering and
+differentiation runs in libvs.so's CUDA kernels (see include/vs.h).
+"""
+
+from __future__ import annotations
+
+import ctypes
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import _abi
+from ._abi import (VS_FLAG_LOSS_L2, VS_TEX_RGBA_F32, VS_TEX_SH_F16, check, vs_batch_item,
+                   vs_camera, vs_shell_desc, vs_stats)
+
+__all__ = ["Context", "ShellObject", "camera_struct", "workspace_size", "make_workspace",
+           "render", "render_backward", "render_batch", "read_stats", "VSRender",
+           "VS_FLAG_LOSS_L2", "VS_TEX_RGBA_F32", "VS_TEX_SH_F16"]
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def camera_struct(cam) -> vs_camera:
+    """vs_camera from any object with world_to_cam (3x4), fx, fy, cx, cy,
+    znear, width, height (e.g. synth.Camera)."""
+    c = vs_camera()
+    m = torch.as_tensor(cam.world_to_cam, dtype=torch.float32).reshape(-1).tolist()
+    for i in range(12):
+        c.world_to_cam[i] = m[i]
+    c.fx, c.fy, c.cx, c.cy, c.znear = (float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy),
+                                       float(cam.znear))
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+class Context:
+    """vs_create / vs_destroy."""
+
+    def __init__(self, device: int = 0):
+        self.lib = _abi.load()
+        self.device = device
+        self.handle = ctypes.c_void_p()
+        check(self.lib.vs_create(ctypes.byref(self.handle), device))
+
+    def close(self):
+        if self.handle:
+            self.lib.vs_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ShellObject:
+    """vs_load_shells over device tensors (kept alive by this object).
+
+    Each shell: dict(pos=[V,3] f32, uv=[V,2] f32, tris=[T,3] i32,
+    tex=[H,W,pitch] f32 (RGBA) or f16 (SH), fmt, degree)."""
+
+    def __init__(self, ctx: Context, shells: Sequence[dict]):
+        self.ctx = ctx
+        self.shells = [dict(s) for s in shells]
+        k = len(self.shells)
+        arr = (vs_shell_desc * k)()
+        for i, s in enumerate(self.shells):
+            for key in ("pos", "uv", "tris", "tex"):
+                t = s[key]
+                if not (t.is_cuda and t.is_contiguous()):
+                    raise ValueError(f"shell {i}: {key} must be a contiguous CUDA tensor")
+            d = arr[i]
+            d.pos, d.num_verts = s["pos"].data_ptr(), s["pos"].shape[0]
+            d.uv = s["uv"].data_ptr()
+            d.tris, d.num_tris = s["tris"].data_ptr(), s["tris"].shape[0]
+            d.texels = s["tex"].data_ptr()
+            d.tex_h, d.tex_w, d.texel_pitch = s["tex"].shape
+            d.format = int(s["fmt"])
+            d.sh_degree = int(s.get("degree", 0))
+        self.handle = ctypes.c_void_p()
+        check(ctx.lib.vs_load_shells(ctx.handle, arr, k, ctypes.byref(self.handle)))
+
+    @property
+    def k(self) -> int:
+        return len(self.shells)
+
+    @property
+    def textures(self) -> List[torch.Tensor]:
+        return [s["tex"] for s in self.shells]
+
+    @classmethod
+    def from_scene(cls, ctx: Context, scene, device="cuda") -> "ShellObject":
+        """Upload a synth.Scene (numpy arrays) to the device."""
+        shells = []
+        for s in scene.shells:
+            shells.append(dict(pos=torch.from_numpy(s.pos).to(device).contiguous(),
+                               uv=torch.from_numpy(s.uv).to(device).contiguous(),
+                               tris=torch.from_numpy(s.tris).to(device).contiguous(),
+                               tex=torch.from_numpy(s.tex).to(device).contiguous(),
+                               fmt=s.fmt, degree=s.degree))
+        return cls(ctx, shells)
+
+    def free(self):
+        if self.handle:
+            self.ctx.lib.vs_free_shells(self.ctx.handle, self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def workspace_size(ctx: Context, objs: Sequence[ShellObject], cams: Sequence, flags: int = 0) -> int:
+    n = len(objs)
+    oarr = (ctypes.c_void_p * n)(*[o.handle.value for o in objs])
+    carr = (vs_camera * n)(*[camera_struct(c) for c in cams])
+    out = ctypes.c_size_t()
+    check(ctx.lib.vs_workspace_size(ctx.handle, oarr, carr, n, flags, ctypes.byref(out)))
+    return out.value
+
+
+def make_workspace(ctx: Context, objs, cams, flags: int = 0, device="cuda") -> torch.Tensor:
+    """Zero-filled workspace tensor of the required size."""
+    return torch.zeros(workspace_size(ctx, objs, cams, flags), dtype=torch.uint8, device=device)
+
+
+def render(ctx: Context, obj: ShellObject, cam, ws: torch.Tensor, bg=(0.0, 0.0, 0.0),
+           out: Optional[torch.Tensor] = None, hits: Optional[torch.Tensor] = None,
+           want_hits: bool = True, flags: int = 0, stream=None):
+    """vs_render: returns (rgba [H,W,4] f32, hits [k,H,W] i32 or None)."""
+    H, W = int(cam.height), int(cam.width)
+    dev = ws.device
+    if out is None:
+        out = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    if hits is None and want_hits:
+        hits = torch.empty((obj.k, H, W), dtype=torch.int32, device=dev)
+    c = camera_struct(cam)
+    bgv = (ctypes.c_float * 3)(*bg)
+    check(ctx.lib.vs_render(ctx.handle, obj.handle, ctypes.byref(c), bgv, _ptr(out), _ptr(hits),
+                            _ptr(ws), ws.numel(), flags, _stream(stream)))
+    return out, hits
+
+
+def render_backward(ctx: Context, obj: ShellObject, cam, ws: torch.Tensor, hits: torch.Tensor,
+                    grad_rgb: torch.Tensor, grads: Optional[List[torch.Tensor]] = None,
+                    bg=(0.0, 0.0, 0.0), loss: Optional[torch.Tensor] = None, flags: int = 0,
+                    stream=None) -> List[torch.Tensor]:
+    """vs_render_backward: accumulates into (and returns) FP32 texel grads."""
+    if grads is None:
+        grads = [torch.zeros(t.shape, dtype=torch.float32, device=t.device) for t in obj.textures]
+    c = camera_struct(cam)
+    bgv = (ctypes.c_float * 3)(*bg)
+    gptrs = (ctypes.c_void_p * obj.k)(*[g.data_ptr() for g in grads])
+    check(ctx.lib.vs_render_backward(ctx.handle, obj.handle, ctypes.byref(c), bgv, _ptr(hits),
+                                     _ptr(grad_rgb.contiguous()), gptrs, _ptr(loss), _ptr(ws),
+                                     ws.numel(), flags, _stream(stream)))
+    return grads
+
+
+class BatchItems:
+    """Host-side vs_batch_item array (built once, reusable across calls)."""
+
+    def __init__(self, items: Sequence[dict]):
+        n = len(items)
+        self.arr = (vs_batch_item * n)()
+        self.keep = []
+        for j, it in enumerate(items):
+            b = self.arr[j]
+            b.obj = it["obj"].handle.value
+            b.cam = camera_struct(it["cam"])
+            b.out_rgba = it["out"].data_ptr()
+            b.hits = it["hits"].data_ptr() if it.get("hits") is not None else None
+            b.grad_rgb = it["grad_rgb"].data_ptr() if it.get("grad_rgb") is not None else None
+            if it.get("grads") is not None:
+                g = (ctypes.c_void_p * len(it["grads"]))(*[t.data_ptr() for t in it["grads"]])
+                self.keep.append(g)
+                b.grad_texels = ctypes.cast(g, ctypes.POINTER(ctypes.c_void_p))
+            b.loss = it["loss"].data_ptr() if it.get("loss") is not None else None
+        self.n = n
+
+
+def render_batch(ctx: Context, items, ws: torch.Tensor, bg=(0.0, 0.0, 0.0), do_backward: bool = False,
+                 flags: int = 0, stream=None):
+    """vs_render_batch over a BatchItems (or a list of item dicts: obj, cam,
+    out, hits, grad_rgb, grads, loss)."""
+    if not isinstance(items, BatchItems):
+        items = BatchItems(items)
+    bgv = (ctypes.c_float * 3)(*bg)
+    check(ctx.lib.vs_render_batch(ctx.handle, items.arr, items.n, bgv, int(do_backward), _ptr(ws),
+                                  ws.numel(), flags, _stream(stream)))
+    return items
+
+
+def read_stats(ws: torch.Tensor, reset: bool = False, stream=None) -> dict:
+    st = vs_stats()
+    check(_abi.load().vs_read_stats(_ptr(ws), _stream(stream), int(reset), ctypes.byref(st)))
+    return st.as_dict()
+
+
+class VSRender(torch.autograd.Function):
+    """Differentiable render w.r.t. the texel arrays.
+
+    forward(ctx_, obj, cam, ws, bg, *textures) -> rgba [H,W,4]; the hit
+    buffer is saved and the backward recomputes transmittance from it
+    (vs_render_backward).  Gradients come back in FP32 and autograd casts
+    them to each texture's dtype.
+    """
+
+    @staticmethod
+    def forward(fctx, vctx: Context, obj: ShellObject, cam, ws: torch.Tensor, bg, *textures):
+        out, hits = render(vctx, obj, cam, ws, bg=bg)
+        fctx.vctx, fctx.obj, fctx.cam, fctx.ws, fctx.bg = vctx, obj, cam, ws, bg
+        fctx.save_for_backward(hits)
+        return out
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        (hits,) = fctx.saved_tensors
+        g = grad_out[..., :3].contiguous().float()
+        grads = render_backward(fctx.vctx, fctx.obj, fctx.cam, fctx.ws, hits, g, bg=fctx.bg)
+        return (None, None, None, None, None, *grads)

@@ -1,0 +1,142 @@
+"""The C-ABI library on the host: it loads, exports every function
+include/vs.h declares, and rejects bad arguments before touching a GPU.
+No compute call is made here."""
+
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+from paper_2409_02482_gb300 import _abi
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(_abi.LIB_PATH):
+        from paper_2409_02482_gb300 import build
+        build.build()
+    return _abi.load()
+
+
+def test_exports_every_declared_function(lib):
+    declared = _abi.header_functions()
+    assert len(declared) >= 10
+    for name in declared:
+        assert hasattr(lib, name), name
+    nm = subprocess.run(["nm", "-D", "--defined-only", _abi.LIB_PATH], capture_output=True, text=True)
+    if nm.returncode == 0:
+        exported = {line.split()[-1] for line in nm.stdout.splitlines() if " T " in line}
+        assert set(declared) <= exported
+    # the binding covers exactly what the header declares
+    assert set(_abi.SIGNATURES) == set(declared)
+
+
+def test_struct_layouts_match_header_sizes():
+    # sizes implied by the C declarations on LP64
+    assert ctypes.sizeof(_abi.vs_camera) == 76
+    assert ctypes.sizeof(_abi.vs_shell_desc) == 72
+    assert ctypes.sizeof(_abi.vs_stats) == 56
+
+
+def test_create_without_gpu_reports_cuda_error(lib):
+    h = ctypes.c_void_p()
+    st = lib.vs_create(ctypes.byref(h), 0)
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if has_gpu:
+        assert st == _abi.VS_OK
+        lib.vs_destroy(h)
+    else:
+        assert st == _abi.VS_ERR_CUDA
+        assert lib.vs_last_error()
+    assert lib.vs_create(None, 0) == _abi.VS_ERR_INVALID_ARG
+
+
+def _fake_ctx():
+    # the host-only calls check ctx for NULL but never dereference it
+    return ctypes.c_void_p(ctypes.addressof(ctypes.c_int(0)))
+
+
+def _desc(nv=100, nt=150, tw=64, th=32, fmt=_abi.VS_TEX_SH_F16, deg=2, pitch=None):
+    d = _abi.vs_shell_desc()
+    d.pos, d.uv, d.tris, d.texels = 0x10000, 0x20000, 0x30000, 0x40000   # never dereferenced
+    d.num_verts, d.num_tris, d.tex_w, d.tex_h = nv, nt, tw, th
+    d.format, d.sh_degree = fmt, deg
+    nch = 4 if fmt == _abi.VS_TEX_RGBA_F32 else 1 + 3 * (deg + 1) ** 2
+    d.texel_pitch = nch if pitch is None else pitch
+    return d
+
+
+def _load(lib, descs):
+    arr = (_abi.vs_shell_desc * len(descs))(*descs)
+    out = ctypes.c_void_p()
+    st = lib.vs_load_shells(_fake_ctx(), arr, len(descs), ctypes.byref(out))
+    return st, out
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nv=2), dict(nt=0), dict(tw=0), dict(fmt=7), dict(deg=4), dict(pitch=27), dict(th=70000),
+])
+def test_load_shells_rejects_bad_descriptors(lib, bad):
+    st, out = _load(lib, [_desc(**bad)])
+    assert st == _abi.VS_ERR_INVALID_ARG
+    assert not out.value
+    assert lib.vs_last_error()
+
+
+def test_load_shells_rejects_bad_k_and_nulls(lib):
+    arr = (_abi.vs_shell_desc * 17)(*[_desc() for _ in range(17)])
+    out = ctypes.c_void_p()
+    assert lib.vs_load_shells(_fake_ctx(), arr, 0, ctypes.byref(out)) == _abi.VS_ERR_INVALID_ARG
+    assert lib.vs_load_shells(_fake_ctx(), arr, 17, ctypes.byref(out)) == _abi.VS_ERR_INVALID_ARG
+    assert lib.vs_load_shells(None, arr, 1, ctypes.byref(out)) == _abi.VS_ERR_INVALID_ARG
+    d = _desc()
+    d.pos = None
+    st, _ = _load(lib, [d])
+    assert st == _abi.VS_ERR_INVALID_ARG
+
+
+def _cam(w=800, h=600):
+    c = _abi.vs_camera()
+    for i, v in enumerate([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 4]):
+        c.world_to_cam[i] = v
+    c.fx = c.fy = 500.0
+    c.cx, c.cy, c.znear = w / 2, h / 2, 0.1
+    c.width, c.height = w, h
+    return c
+
+
+def test_workspace_size_covers_the_dominant_terms(lib):
+    descs = [_desc(nv=1000 + 10 * i, nt=2000 + 7 * i) for i in range(5)]
+    st, obj = _load(lib, descs)
+    assert st == 0
+    objs = (ctypes.c_void_p * 1)(obj.value)
+    cams = (_abi.vs_camera * 1)(_cam())
+    size = ctypes.c_size_t()
+    assert lib.vs_workspace_size(_fake_ctx(), objs, cams, 1, 0, ctypes.byref(size)) == 0
+    need = 8 * 5 * 800 * 600 + sum(16 * d.num_verts + 4 * d.num_tris for d in descs)
+    assert need <= size.value <= need + 64 * 1024
+    # batch of 3 items ~ three times one item
+    objs3 = (ctypes.c_void_p * 3)(obj.value, obj.value, obj.value)
+    cams3 = (_abi.vs_camera * 3)(_cam(), _cam(320, 200), _cam(1024, 1024))
+    size3 = ctypes.c_size_t()
+    assert lib.vs_workspace_size(_fake_ctx(), objs3, cams3, 3, 0, ctypes.byref(size3)) == 0
+    assert size3.value > 8 * 5 * (800 * 600 + 320 * 200 + 1024 * 1024)
+    lib.vs_free_shells(_fake_ctx(), obj)
+
+
+@pytest.mark.parametrize("w,h,znear", [(0, 10, 0.1), (10, 9000, 0.1), (64, 64, 0.0), (64, 64, -1.0)])
+def test_workspace_size_rejects_bad_cameras(lib, w, h, znear):
+    st, obj = _load(lib, [_desc()])
+    assert st == 0
+    c = _cam(w, h)
+    c.znear = znear
+    objs = (ctypes.c_void_p * 1)(obj.value)
+    cams = (_abi.vs_camera * 1)(c)
+    size = ctypes.c_size_t()
+    assert lib.vs_workspace_size(_fake_ctx(), objs, cams, 1, 0, ctypes.byref(size)) == _abi.VS_ERR_INVALID_ARG
+    lib.vs_free_shells(_fake_ctx(), obj)

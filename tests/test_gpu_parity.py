@@ -1,0 +1,379 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: hit IDs bit-exact; colours within 1e-5 max-abs for FP32 texels and
+2e-3 for FP16 texel storage (against the oracle fed the same FP16 values --
+the compute error -- and, separately reported, the FP32 values before
+rounding -- the storage error); gradients within the same relative bars;
+batched forward bit-identical to the per-view launches.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from synth import FMT_RGBA_F32, FMT_SH_F16, Scene, Shell
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-5
+TOL_F16 = 2e-3
+
+
+@pytest.fixture(scope="module")
+def vs():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2409_02482_gb300 as vs
+    return vs
+
+
+@pytest.fixture(scope="module")
+def ctx(vs):
+    return vs.Context(0)
+
+
+def tol_of(scene):
+    return TOL_F32 if all(s.fmt == FMT_RGBA_F32 for s in scene.shells) else TOL_F16
+
+
+def gpu_render(vs, ctx, scene, cam, bg=(0.0, 0.0, 0.0), obj=None):
+    obj = obj or vs.ShellObject.from_scene(ctx, scene)
+    ws = vs.make_workspace(ctx, [obj], [cam])
+    out, hits = vs.render(ctx, obj, cam, ws, bg=bg)
+    st = vs.read_stats(ws)
+    assert st["device_status"] == 0
+    return out.cpu().numpy(), hits.cpu().numpy(), st, obj, ws
+
+
+def check_forward(vs, ctx, scene, cam, bg=(0.0, 0.0, 0.0), tol=None):
+    out, hits, st, obj, ws = gpu_render(vs, ctx, scene, cam, bg)
+    ref, ref_hits, frags = oracle.render(scene, cam, bg=bg)
+    mism = (hits != ref_hits).sum()
+    assert mism == 0, f"{mism} hit IDs differ"
+    err = np.abs(out - ref).max()
+    assert err <= (tol or tol_of(scene)), f"max colour error {err}"
+    assert st["fragments"] == frags.sum()
+    assert st["tris_culled_near"] == 0 and st["tris_culled_guard"] == 0
+    return err, obj, ws, hits
+
+
+# ----------------------------------------------------------------------------
+# forward
+# ----------------------------------------------------------------------------
+
+def test_c1_full_size_rgba_f32(vs, ctx):
+    (scene, cams), = synth.config_scene("c1")
+    err, *_ = check_forward(vs, ctx, scene, cams[0], bg=(0.3, 0.2, 0.1), tol=TOL_F32)
+    print(f"c1 max err {err:.3e}")
+
+
+@pytest.mark.parametrize("w,h", [(77, 53), (256, 1), (1, 200), (131, 257)])
+def test_ragged_images(vs, ctx, w, h):
+    (scene, _), = synth.config_scene("c1", scale=0.25)
+    cam = synth.look_at((2.0, -2.0, 1.0), width=w, height=h)
+    check_forward(vs, ctx, scene, cam, tol=TOL_F32)
+
+
+@pytest.mark.parametrize("name,scale", [("c2", 0.01), ("c3", 0.004), ("c5", 0.0005)])
+def test_sh_configs_scaled(vs, ctx, name, scale):
+    (scene, cams), = synth.config_scene(name, scale=scale, views=3)
+    errs = []
+    for cam in cams:
+        err, *_ = check_forward(vs, ctx, scene, cam, bg=(0.2, 0.2, 0.2))
+        errs.append(err)
+    print(f"{name} compute error vs oracle on the same FP16 values: {max(errs):.3e}")
+    assert max(errs) < 1e-4      # FP32 compute error is far below the FP16 bar
+
+
+def test_fp16_storage_error_is_within_bar(vs, ctx):
+    """The error against the FP32 values before FP16 rounding (storage
+    error) stays within 2e-3."""
+    (scene, cams), = synth.config_scene("c2", scale=0.01, views=2)
+    rng = np.random.default_rng(0)
+    master = []
+    for s in scene.shells:
+        m = (0.3 * rng.standard_normal(s.tex.shape)).astype(np.float32)
+        master.append(m)
+        s.tex = m.astype(np.float16)
+    for cam in cams:
+        out, hits, st, obj, ws = gpu_render(vs, ctx, scene, cam)
+        ref32 = Scene([Shell(s.pos, s.uv, s.tris, m, s.fmt, s.degree) for s, m in zip(scene.shells, master)])
+        ref, _ = oracle.shade(ref32, cam, hits)
+        err = np.abs(out - ref).max()
+        print(f"storage error {err:.3e}")
+        assert err <= TOL_F16
+
+
+@pytest.mark.parametrize("k", [1, 2, 9, 16])
+def test_many_and_few_shells(vs, ctx, k):
+    shells = []
+    rng = np.random.default_rng(k)
+    geo = synth.displaced_shells(k, 10, seed=3, spacing=0.03)
+    for i, (p, u, t) in enumerate(geo):
+        if i % 2:
+            shells.append(Shell(p, u, t, synth.sh_texture(32, 32, i % 4, rng), FMT_SH_F16, i % 4))
+        else:
+            shells.append(Shell(p, u, t, synth.rgba_texture(16, 16, rng), FMT_RGBA_F32))
+    cam = synth.look_at((2.5, -1.5, 1.0), width=96, height=72)
+    check_forward(vs, ctx, Scene(shells), cam, bg=(0.5, 0.5, 0.5))
+
+
+def test_texel_pitch_padding_and_vector_widths(vs, ctx):
+    """Padded texel pitches select wider loads; results do not change."""
+    scene, cams = synth.config_scene("c4", scale=0.002, views=1)[0]
+    cam = cams[0]
+    base, *_ = gpu_render(vs, ctx, scene, cam)
+    for pitch in (14, 16, 20):
+        padded = Scene([Shell(s.pos, s.uv, s.tris,
+                              np.concatenate([s.tex, np.zeros(s.tex.shape[:2] + (pitch - s.tex.shape[2],),
+                                                              np.float16)], axis=2),
+                              s.fmt, s.degree) for s in scene.shells])
+        out, *_ = gpu_render(vs, ctx, padded, cam)
+        assert np.array_equal(out, base)
+
+
+def test_nothing_visible(vs, ctx):
+    (scene, _), = synth.config_scene("c1", scale=0.25)
+    cam = synth.look_at((0.0, -3.0, 0.0), target=(0.0, -6.0, 0.0), width=64, height=48)
+    out, hits, st, *_ = gpu_render(vs, ctx, scene, cam, bg=(0.25, 0.5, 1.0))
+    assert np.all(hits == -1)
+    assert np.all(out == np.array([0.25, 0.5, 1.0, 0.0], np.float32))
+    assert st["fragments"] == 0
+
+
+def test_degenerate_and_back_facing_triangles(vs, ctx):
+    pos, uv, tris = synth.icosphere(2, 1.0)
+    extra = np.array([[0, 0, 0], [1, 1, 2], [5, 5, 5]], np.int32)          # zero-area
+    flipped = tris[:40][:, [0, 2, 1]]                                        # back-facing copies
+    t2 = np.concatenate([tris, extra, flipped]).astype(np.int32)
+    rng = np.random.default_rng(0)
+    scene = Scene([Shell(pos, uv, t2, synth.rgba_texture(32, 32, rng), FMT_RGBA_F32)])
+    cam = synth.look_at((0.5, -2.5, 0.8), width=80, height=80)
+    err, obj, ws, hits = check_forward(vs, ctx, scene, cam, tol=TOL_F32)
+
+
+def test_large_triangles_take_the_cooperative_path(vs, ctx):
+    """A few triangles that cover most of the image (screen boxes far above
+    the per-thread limit) next to tiny ones."""
+    pos, uv, tris = synth.icosphere(0, 1.0)     # 20 faces, each hundreds of pixels
+    rng = np.random.default_rng(1)
+    geo2 = synth.icosphere(3, 0.7)
+    scene = Scene([Shell(pos, uv, tris, synth.rgba_texture(64, 64, rng), FMT_RGBA_F32),
+                   Shell(*geo2, synth.rgba_texture(64, 64, rng), FMT_RGBA_F32)])
+    cam = synth.look_at((0.3, -2.2, 0.5), width=640, height=480)
+    err, obj, ws, hits = check_forward(vs, ctx, scene, cam, tol=TOL_F32)
+    st = vs.read_stats(ws)
+    assert st["device_status"] == 0
+
+
+def test_bad_triangle_indices_are_reported_not_faulted(vs, ctx):
+    pos, uv, tris = synth.icosphere(1, 1.0)
+    bad = tris.copy()
+    bad[3, 1] = 10_000_000
+    rng = np.random.default_rng(0)
+    scene = Scene([Shell(pos, uv, bad, synth.rgba_texture(8, 8, rng), FMT_RGBA_F32)])
+    cam = synth.look_at((0.0, -3.0, 0.0), width=32, height=32)
+    obj = vs.ShellObject.from_scene(ctx, scene)
+    ws = vs.make_workspace(ctx, [obj], [cam])
+    vs.render(ctx, obj, cam, ws)
+    st = vs.read_stats(ws, reset=True)
+    assert st["device_status"] == -1       # VS_ERR_INVALID_ARG
+    # the context is still usable afterwards
+    (scene2, cams2), = synth.config_scene("c1", scale=0.1)
+    check_forward(vs, ctx, scene2, cams2[0], tol=TOL_F32)
+
+
+def test_host_side_errors(vs, ctx):
+    from paper_2409_02482_gb300._abi import VSError
+    (scene, cams), = synth.config_scene("c1", scale=0.1)
+    obj = vs.ShellObject.from_scene(ctx, scene)
+    ws = vs.make_workspace(ctx, [obj], cams)
+    with pytest.raises(VSError, match="WORKSPACE"):
+        vs.render(ctx, obj, cams[0], ws[: ws.numel() // 2])
+    with pytest.raises(VSError, match="WORKSPACE"):
+        vs.render(ctx, obj, cams[0], ws[1:])
+
+
+# ----------------------------------------------------------------------------
+# backward
+# ----------------------------------------------------------------------------
+
+def check_backward(vs, ctx, scene, cam, bg, rel):
+    obj = vs.ShellObject.from_scene(ctx, scene)
+    ws = vs.make_workspace(ctx, [obj], [cam])
+    out, hits = vs.render(ctx, obj, cam, ws, bg=bg)
+    g = torch.randn((cam.height, cam.width, 3), device="cuda",
+                    generator=torch.Generator("cuda").manual_seed(1))
+    grads = vs.render_backward(ctx, obj, cam, ws, hits, g, bg=bg)
+    ref = oracle.backward(scene, cam, hits.cpu().numpy(), g.cpu().numpy().astype(np.float64), bg=bg)
+    worst = 0.0
+    for gg, rg in zip(grads, ref):
+        scale = max(np.abs(rg).max(), 1e-30)
+        worst = max(worst, np.abs(gg.cpu().numpy() - rg).max() / scale)
+    assert worst <= rel, f"relative gradient error {worst}"
+    assert vs.read_stats(ws)["device_status"] == 0
+    return worst, obj, ws, hits, grads
+
+
+def test_backward_rgba_matches_oracle(vs, ctx):
+    (scene, cams), = synth.config_scene("c1", scale=0.25)
+    w, *_ = check_backward(vs, ctx, scene, cams[0], (0.2, 0.3, 0.4), TOL_F32)
+    print(f"rgba grad rel err {w:.2e}")
+
+
+@pytest.mark.parametrize("name,scale", [("c2", 0.005), ("c4", 0.001), ("c5", 0.0004)])
+def test_backward_sh_matches_oracle(vs, ctx, name, scale):
+    sc, cams = synth.config_scene(name, scale=scale, views=1)[0]
+    w, *_ = check_backward(vs, ctx, sc, cams[0], (0.1, 0.1, 0.1), 1e-4)
+    print(f"{name} sh grad rel err {w:.2e}")
+
+
+def test_backward_l2_loss_flag(vs, ctx):
+    (scene, cams), = synth.config_scene("c3", scale=0.002, views=1)
+    cam = cams[0]
+    (target_scene, _), = synth.config_scene("c3", scale=0.002, views=1, tex_seed=1)
+    target, _, _ = oracle.render(target_scene, cam)
+    obj = vs.ShellObject.from_scene(ctx, scene)
+    ws = vs.make_workspace(ctx, [obj], [cam])
+    out, hits = vs.render(ctx, obj, cam, ws)
+    tgt = torch.from_numpy(target[..., :3].astype(np.float32)).cuda()
+    loss = torch.zeros(1, device="cuda")
+    grads = vs.render_backward(ctx, obj, cam, ws, hits, tgt, loss=loss, flags=vs.VS_FLAG_LOSS_L2)
+    ref_rgba, ref_hits, _ = oracle.render(scene, cam)
+    L, dL = oracle.l2_loss_grad(ref_rgba, target[..., :3].astype(np.float32).astype(np.float64))
+    ref = oracle.backward(scene, cam, ref_hits, dL)
+    assert abs(loss.item() - L) <= 1e-5 * L + 1e-9
+    for gg, rg in zip(grads, ref):
+        assert np.abs(gg.cpu().numpy() - rg).max() <= 1e-4 * np.abs(rg).max()
+
+
+def test_autograd_function(vs, ctx):
+    (scene, cams), = synth.config_scene("c1", scale=0.25)
+    cam = cams[0]
+    obj = vs.ShellObject.from_scene(ctx, scene)
+    ws = vs.make_workspace(ctx, [obj], [cam])
+    tex = [t.clone().requires_grad_(True) for t in obj.textures]
+    obj2 = vs.ShellObject(ctx, [dict(s, tex=t) for s, t in zip(obj.shells, tex)])
+    out = vs.VSRender.apply(ctx, obj2, cam, ws, (0.0, 0.0, 0.0), *tex)
+    w = torch.randn_like(out[..., :3])
+    (out[..., :3] * w).sum().backward()
+    out2, hits = vs.render(ctx, obj, cam, ws)
+    ref = vs.render_backward(ctx, obj, cam, ws, hits, w)
+    for t, r in zip(tex, ref):
+        assert torch.allclose(t.grad, r, rtol=1e-5, atol=1e-7)
+
+
+# ----------------------------------------------------------------------------
+# batch
+# ----------------------------------------------------------------------------
+
+def _batch_setup(vs, ctx, objs_cams, do_bwd, with_targets=False):
+    items, objs = [], []
+    for sc, cams in objs_cams:
+        obj = vs.ShellObject.from_scene(ctx, sc)
+        objs.append(obj)
+        grads = [torch.zeros(t.shape, dtype=torch.float32, device="cuda") for t in obj.textures] if do_bwd else None
+        for cam in cams:
+            it = dict(obj=obj, cam=cam, scene=sc,
+                      out=torch.empty((cam.height, cam.width, 4), device="cuda"),
+                      hits=torch.empty((obj.k, cam.height, cam.width), dtype=torch.int32, device="cuda"),
+                      grads=grads)
+            if do_bwd:
+                it["grad_rgb"] = torch.randn((cam.height, cam.width, 3), device="cuda",
+                                             generator=torch.Generator("cuda").manual_seed(len(items)))
+                it["loss"] = torch.zeros(1, device="cuda")
+            items.append(it)
+    ws = vs.make_workspace(ctx, [it["obj"] for it in items], [it["cam"] for it in items])
+    return items, objs, ws
+
+
+def test_batch_forward_bit_identical_to_plain(vs, ctx):
+    objs_cams = synth.config_scene("c4", scale=0.003, views=2)[:6]
+    items, objs, ws = _batch_setup(vs, ctx, objs_cams, False)
+    bg = (0.1, 0.2, 0.3)
+    vs.render_batch(ctx, items, ws, bg=bg)
+    st = vs.read_stats(ws, reset=True)
+    assert st["device_status"] == 0
+    total = 0
+    for it in items:
+        ws1 = vs.make_workspace(ctx, [it["obj"]], [it["cam"]])
+        out, hits = vs.render(ctx, it["obj"], it["cam"], ws1, bg=bg)
+        assert torch.equal(out, it["out"])
+        assert torch.equal(hits, it["hits"])
+        total += vs.read_stats(ws1)["fragments"]
+    assert st["fragments"] == total
+    # and against the oracle for two of them
+    for it in items[:2]:
+        ref, ref_hits, _ = oracle.render(it["scene"], it["cam"], bg=bg)
+        assert np.array_equal(it["hits"].cpu().numpy(), ref_hits)
+        assert np.abs(it["out"].cpu().numpy() - ref).max() <= TOL_F16
+
+
+def test_batch_fused_backward_matches_plain(vs, ctx):
+    objs_cams = synth.config_scene("c4", scale=0.002, views=2)[:4]
+    items, objs, ws = _batch_setup(vs, ctx, objs_cams, True)
+    vs.render_batch(ctx, items, ws, do_backward=True)
+    assert vs.read_stats(ws)["device_status"] == 0
+    for obj, (sc, cams) in zip(objs, objs_cams):
+        its = [it for it in items if it["obj"] is obj]
+        plain = [torch.zeros_like(g) for g in its[0]["grads"]]
+        for it in its:
+            ws1 = vs.make_workspace(ctx, [obj], [it["cam"]])
+            out, hits = vs.render(ctx, obj, it["cam"], ws1)
+            assert torch.equal(out, it["out"])
+            vs.render_backward(ctx, obj, it["cam"], ws1, hits, it["grad_rgb"], grads=plain)
+        for a, b in zip(its[0]["grads"], plain):
+            assert torch.allclose(a, b, rtol=1e-4, atol=1e-6 * b.abs().max().item())
+
+
+def test_batch_stall_hook_times_out_and_context_survives(vs, ctx):
+    objs_cams = synth.config_scene("c4", scale=0.001, views=1)[:2]
+    items, objs, ws = _batch_setup(vs, ctx, objs_cams, False)
+    vs.render_batch(ctx, items, ws, flags=1 << 30)
+    st = vs.read_stats(ws, reset=True)
+    assert st["device_status"] == -6          # VS_ERR_TIMEOUT
+    vs.render_batch(ctx, items, ws)
+    st = vs.read_stats(ws, reset=True)
+    assert st["device_status"] == 0
+    ref, ref_hits, _ = oracle.render(items[0]["scene"], items[0]["cam"])
+    assert np.array_equal(items[0]["hits"].cpu().numpy(), ref_hits)
+
+
+def test_batch_graph_capture_replays(vs, ctx):
+    objs_cams = synth.config_scene("c4", scale=0.001, views=2)[:3]
+    items, objs, ws = _batch_setup(vs, ctx, objs_cams, False)
+    bi = vs.BatchItems(items)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        vs.render_batch(ctx, bi, ws, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    first = [it["out"].clone() for it in items]
+    for it in items:
+        it["out"].zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        vs.render_batch(ctx, bi, ws, stream=torch.cuda.current_stream())
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, it in zip(first, items):
+        assert torch.equal(a, it["out"])
+    assert vs.read_stats(ws)["device_status"] == 0
+
+
+# ----------------------------------------------------------------------------
+# full-size workloads (the launch configuration the benchmark times)
+# ----------------------------------------------------------------------------
+
+def test_c2_full_size_views(vs, ctx):
+    (scene, cams), = synth.config_scene("c2", views=100)
+    obj = vs.ShellObject.from_scene(ctx, scene)
+    for cam in (cams[0], cams[57]):
+        err, *_ = check_forward(vs, ctx, scene, cam, bg=(0.0, 0.0, 0.0), tol=TOL_F16)
+        print(f"c2 full view err {err:.3e}")
