@@ -1,0 +1,427 @@
+"""Benchmark of the k-shell renderer hot path on GB300.
+
+Workload (N = 1): 7 nested noise-displaced shells of ~200k triangles each,
+2048^2 FP16 textures of one alpha logit + degree-2 RGB SH coefficients
+(28 values = 56 B per texel), 100 views of 800x800 on a hemisphere at
+distance 4 (the synthetic stand-in for the paper's object scenes).
+
+One step = one texture-fitting pass over all 100 views in ONE persistent
+launch (vs_render_batch, do_backward=1, VS_FLAG_LOSS_L2): rasterize every
+shell with its nearest-hit test, shade and composite (forward), and
+accumulate the FP32 texel gradients of the mean-squared error against
+per-view target images (backward) -- every row of the hot path.  Inputs are
+resident in HBM and larger than L2 (1.6 GB texels, 3.3 GB gradients, 0.8 GB
+targets), so no L2 flush is needed between steps.
+
+Printed: ONE JSON line (rank 0).  `value` = fragments composited per second
+(pixel-shell pairs with a hit) over the whole job.  Extras: forward-only
+batched throughput, the plain per-view launch loop and the batched/plain
+ratio, images/s, the roofline of the persistent kernel, the oracle timed on
+the host cores, an end-to-end number with host<->device copies, clocks.
+
+--impl reference times the FP64 CPU oracle (the reference arm for this
+build) on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fragments composited/s and fwd+bwd images/s, batched vs plain, at ≤1e-5 err"
+WORKLOAD = ("k=7 noise-displaced shells x ~200k tris, 2048^2 FP16 alpha+SH2 textures, "
+            "100 views 800x800 on a hemisphere at r=4")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--views", type=int, default=100)
+    p.add_argument("--scale", type=float, default=1.0, help="shrink the workload (testing only)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-profile", action="store_true", help="skip the CUPTI launch count (use under ncu)")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = []
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            rows.append(parts)
+        os.unlink(self.f.name)
+        return rows
+
+    @staticmethod
+    def summarize(rows):
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        pw = [float(r[4]) for r in rows if r[4].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+def build_workload(args, device):
+    import torch
+    import synth
+    import paper_2409_02482_gb300 as vs
+    (scene, cams), = synth.config_scene("c2", scale=args.scale, views=args.views)
+    ctx = vs.Context(device.index or 0)
+    obj = vs.ShellObject.from_scene(ctx, scene, device=device)
+    H, W = cams[0].height, cams[0].width
+    g = torch.Generator(device=device).manual_seed(1)
+    targets = torch.rand((len(cams), H, W, 3), device=device, generator=g)
+    outs = torch.empty((len(cams), H, W, 4), device=device)
+    losses = torch.zeros(len(cams), device=device)
+    grads = [torch.zeros(t.shape, dtype=torch.float32, device=device) for t in obj.textures]
+    items = [dict(obj=obj, cam=c, out=outs[i], grad_rgb=targets[i], grads=grads, loss=losses[i:i + 1])
+             for i, c in enumerate(cams)]
+    ws = vs.make_workspace(ctx, [obj] * len(cams), cams, device=device)
+    return dict(scene=scene, cams=cams, ctx=ctx, obj=obj, targets=targets, outs=outs, losses=losses,
+                grads=grads, items=vs.BatchItems(items), ws=ws, H=H, W=W)
+
+
+def count_launches(fn):
+    """Kernels launched by fn() whose names come from libvs.so (CUPTI via
+    torch.profiler); None if the profiler is unavailable."""
+    import torch
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        names = [e.name for e in prof.events() if e.device_type.name == "CUDA"]
+        ours = [n for n in names if "vsd::" in n or n.startswith("_ZN3vsd")]
+        return len(ours), sorted(set(ours))
+    except Exception as e:   # pragma: no cover - depends on CUPTI on the box
+        return None, [f"profiler unavailable: {e}"]
+
+
+def timed(fn, steps, warmup, stream, barrier):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        fn()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return t0.elapsed_time(t1) / steps   # ms per step
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(wl, frags_per_view, d_per_frag, with_bwd):
+    """Bytes the method itself must move per step (implementation scratch
+    such as the per-shell visibility words excluded):
+      texels D*s (+ FP32 gradient read-modify-write D*C*8 with backward),
+      geometry read once per view (pos 12 B + uv 8 B per vertex, 12 B per
+      triangle), image write 16 B/px, target read 12 B/px (backward)."""
+    scene = wl["scene"]
+    n = len(wl["cams"])
+    s = [sh.tex.shape[2] * sh.tex.itemsize for sh in scene.shells]
+    C = [sh.channels for sh in scene.shells]
+    D_total = d_per_frag * frags_per_view * n           # distinct texels over all (view, shell)
+    tex = D_total * (sum(s) / len(s))
+    grad = D_total * (sum(C) / len(C)) * 8 if with_bwd else 0
+    geo = n * sum(20 * sh.pos.shape[0] + 12 * sh.tris.shape[0] for sh in scene.shells)
+    img = n * wl["H"] * wl["W"] * (16 + (12 if with_bwd else 0))
+    return tex + grad + geo + img, dict(texels=tex, grads=grad, geometry=geo, image=img)
+
+
+def texels_per_fragment(wl, n_views=3, threads=None):
+    """Distinct texels per fragment from the oracle on a few views (the D of
+    the algorithmic bytes; the footprints of neighbouring pixels overlap)."""
+    import oracle
+    cams = wl["cams"]
+    idx = np.linspace(0, len(cams) - 1, n_views).astype(int)
+    D = F = 0
+    for i in idx:
+        hits, _, _ = oracle.raster_scene(wl["scene"], cams[i], threads=threads)
+        D += int(oracle.footprint_texels(wl["scene"], cams[i], hits).sum())
+        F += int((hits >= 0).sum())
+    return D / max(F, 1), [int(i) for i in idx]
+
+
+def cpu_baseline(wl, budget_s=20.0):
+    """The oracle, as it stands, on a bounded sample of the workload: full
+    fused step (raster, shade, L2 loss gradient, adjoint) for as many views
+    as fit in ~budget_s."""
+    import oracle
+    threads = os.cpu_count() or 1
+    t_start = time.perf_counter()
+    frags = 0
+    views = 0
+    targets = wl["targets"].cpu().numpy().astype(np.float64)
+    for i, cam in enumerate(wl["cams"]):
+        rgba, hits, fr = oracle.render(wl["scene"], cam, threads=threads)
+        _, dL = oracle.l2_loss_grad(rgba, targets[i])
+        oracle.backward(wl["scene"], cam, hits, dL)
+        frags += int(fr.sum())
+        views += 1
+        if time.perf_counter() - t_start > budget_s:
+            break
+    dt = time.perf_counter() - t_start
+    return {"value": frags / dt, "unit": "fragments/s", "cores": threads, "kind": "oracle",
+            "sample": f"{views} of {len(wl['cams'])} views, full fused step (raster+shade on {threads} "
+                      f"threads, adjoint on 1), {dt:.1f} s",
+            "images_per_s": views / dt}
+
+
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_2409_02482_gb300 as vs
+    ws_n, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if ws_n > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+        def barrier():
+            dist.barrier()
+    else:
+        def barrier():
+            pass
+    stream = torch.cuda.current_stream()
+    wl = build_workload(args, device)
+    ctx, ws, items = wl["ctx"], wl["ws"], wl["items"]
+    flags = vs.VS_FLAG_LOSS_L2
+
+    def step():
+        vs.render_batch(ctx, items, ws, do_backward=True, flags=flags, stream=stream)
+
+    def step_fwd():
+        vs.render_batch(ctx, items, ws, do_backward=False, stream=stream)
+
+    # fragments per step (device counter), status check
+    vs.read_stats(ws, reset=True)
+    step()
+    st = vs.read_stats(ws, reset=True)
+    assert st["device_status"] == 0, st
+    frags = st["fragments"]
+    n_views = len(wl["cams"])
+
+    launches, kernel_names = (None, ["not counted"]) if args.no_profile else count_launches(step)
+
+    sampler = ClockSampler(local)
+    ms = timed(step, args.steps, args.warmup, stream, barrier)
+    clock_rows = sampler.stop()
+    ms_fwd = timed(step_fwd, max(3, args.steps // 2), 2, stream, barrier)
+
+    # end to end through the public API with host buffers: targets copied in
+    # from pinned host memory, per-view losses read back, every step
+    host_t = wl["targets"].cpu().pin_memory()
+    host_loss = torch.empty(n_views, dtype=torch.float32).pin_memory()
+
+    def step_e2e():
+        wl["targets"].copy_(host_t, non_blocking=True)
+        wl["losses"].zero_()
+        step()
+        host_loss.copy_(wl["losses"], non_blocking=True)
+
+    ms_e2e = timed(step_e2e, max(3, args.steps // 3), 2, stream, barrier)
+
+    if ws_n > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, ms_fwd, ms_e2e], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_fwd, ms_e2e = t.tolist()
+    e2e = {"value": frags * ws_n / (ms_e2e * 1e-3), "unit": "fragments/s",
+           "h2d_bytes_per_step": host_t.numel() * 4, "d2h_bytes_per_step": n_views * 4,
+           "ms_per_step": ms_e2e}
+
+    res = {}
+    # plain per-view launch loop (vs_render + vs_render_backward with the L2 flag)
+    if not args.no_plain and rank == 0:
+        ws1 = vs.make_workspace(ctx, [wl["obj"]], wl["cams"][:1], device=device)
+        hits = torch.empty((wl["obj"].k, wl["H"], wl["W"]), dtype=torch.int32, device=device)
+
+        def plain():
+            for i, cam in enumerate(wl["cams"]):
+                vs.render(ctx, wl["obj"], cam, ws1, out=wl["outs"][i], hits=hits, stream=stream)
+                vs.render_backward(ctx, wl["obj"], cam, ws1, hits, wl["targets"][i], grads=wl["grads"],
+                                   loss=wl["losses"][i:i + 1], flags=flags, stream=stream)
+
+        def plain_fwd():
+            for i, cam in enumerate(wl["cams"]):
+                vs.render(ctx, wl["obj"], cam, ws1, out=wl["outs"][i], want_hits=False, stream=stream)
+
+        ms_plain = timed(plain, 3, 1, stream, lambda: None)
+        ms_plain_fwd = timed(plain_fwd, 3, 1, stream, lambda: None)
+        res["plain_loop"] = {"fwd_bwd_ms_per_step": ms_plain, "fwd_ms_per_step": ms_plain_fwd,
+                             "fwd_bwd_fragments_per_s": frags / (ms_plain * 1e-3),
+                             "fwd_fragments_per_s": frags / (ms_plain_fwd * 1e-3)}
+        res["batched_vs_plain"] = {"fwd_bwd": ms_plain / ms, "fwd": ms_plain_fwd / ms_fwd}
+
+    if rank != 0:
+        if ws_n > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    # roofline of the persistent kernel (the only compute kernel of a step)
+    peak, peak_kind = peaks()
+    d_per_frag, sampled = texels_per_fragment(wl)
+    b_alg, parts = algorithmic_bytes(wl, frags / n_views, d_per_frag, True)
+    b_fwd, _ = algorithmic_bytes(wl, frags / n_views, d_per_frag, False)
+    achieved = b_alg / (ms * 1e-3) / 1e9
+    achieved_fwd = b_fwd / (ms_fwd * 1e-3) / 1e9
+
+    out = {
+        "metric": METRIC,
+        "value": frags * ws_n / (ms * 1e-3),
+        "unit": "fragments/s",
+        "n_gpus": ws_n,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": "batched fused fwd+bwd, L2 loss vs target images, "
+                   "one persistent launch", "texel_storage": "f16", "views": n_views,
+                   "image": f"{wl['W']}x{wl['H']}", "shells": wl["obj"].k,
+                   "tris_per_shell": [int(s.tris.shape[0]) for s in wl["scene"].shells],
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws_n}"},
+        "images_per_s": n_views * ws_n / (ms * 1e-3),
+        "fragments_per_step": frags,
+        "fwd_only": {"fragments_per_s": frags * ws_n / (ms_fwd * 1e-3), "images_per_s": n_views * ws_n / (ms_fwd * 1e-3),
+                     "ms_per_step": ms_fwd,
+                     "roofline_frac": achieved_fwd / peak, "achieved_gbs": achieved_fwd},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs",
+                     "kernel": "vsd::k_persistent", "algorithmic_bytes_per_launch": b_alg,
+                     "bytes_breakdown": parts, "distinct_texels_per_fragment": d_per_frag,
+                     "d_sampled_views": sampled},
+        "gpu_launches": None if launches is None else launches * args.steps,
+        "launches_per_step": launches,
+        "kernels": kernel_names,
+        "e2e": e2e,
+        "clocks": ClockSampler.summarize(clock_rows),
+    }
+    out.update(res)
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(out))
+    if ws_n > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on this machine's host cores, same
+    metric/unit/config, each step a bounded sample (one view's fused step)."""
+    ws_n, rank, local = dist_env()
+    if rank != 0:
+        return
+    import synth
+    import oracle
+    (scene, cams), = synth.config_scene("c2", scale=args.scale, views=args.views)
+    H, W = cams[0].height, cams[0].width
+    rng = np.random.default_rng(1)
+    threads = os.cpu_count() or 1
+
+    def one(i):
+        cam = cams[i % len(cams)]
+        rgba, hits, fr = oracle.render(scene, cam, threads=threads)
+        _, dL = oracle.l2_loss_grad(rgba, rng.random((H, W, 3)))
+        oracle.backward(scene, cam, hits, dL)
+        return int(fr.sum())
+
+    for i in range(args.warmup):
+        one(i)
+    t0 = time.perf_counter()
+    frags = sum(one(args.warmup + i) for i in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = frags / dt
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "fragments/s", "n_gpus": ws_n,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "step": "one view's fused fwd+bwd per step (bounded sample)"},
+           "cpu_baseline": {"value": v, "unit": "fragments/s", "cores": threads, "kind": "oracle",
+                            "sample": f"{args.steps} views, one per step"},
+           "e2e": {"value": v, "unit": "fragments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        if a.steps == 30 and "--steps" not in sys.argv:
+            a.steps = 5
+        run_reference(a)
+    else:
+        run_ours(a)
