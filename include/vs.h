@@ -160,8 +160,8 @@ vs_status vs_workspace_size(vs_ctx* ctx, const vs_object* const* objs, const vs_
  *             shell's nearest front-facing hit, -1 = miss; may be NULL.
  *             The only state vs_render_backward needs.
  *   workspace device, >= vs_workspace_size(obj, cam, 1), 256-byte aligned
- * Launches, in order: clear + vertex setup, small-triangle raster, large-
- * triangle raster, shade + composite. */
+ * Launches, in order: the item-table upload, clear + vertex setup, raster,
+ * shade + composite. */
 vs_status vs_render(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, const float* bg,
                     float* out_rgba, int32_t* hits, void* workspace, size_t ws_bytes,
                     uint32_t flags, vs_stream_t stream);
@@ -200,9 +200,9 @@ typedef struct {
 /* Renders n items -- any mix of objects, shell counts, triangle counts and
  * resolutions -- in ONE persistent kernel launch (after small launches that
  * copy the item table into the workspace).  Work units are handed out in a
- * fixed global order (all vertex setup, then raster, then shading); a unit
- * waits, with a bounded spin, only for units handed out before it, so the
- * launch cannot deadlock.  With do_backward, each pixel's forward result is
+ * fixed, skewed global order (stage s: vertex setup of item s, raster of
+ * item s-1, shading of item s-2); a unit waits, with a bounded spin, only
+ * for units handed out before it, so the launch cannot deadlock.  With do_backward, each pixel's forward result is
  * differentiated in the same unit (fused forward + backward) using
  * grad_rgb -- with VS_FLAG_LOSS_L2, the target image.  Forward outputs are
  * bit-identical to vs_render of each item.  All enqueued work is
@@ -222,6 +222,8 @@ typedef struct {
   uint64_t tris_culled_near; /* a vertex nearer than znear                    */
   uint64_t tris_culled_guard;/* a vertex beyond +-32768 px                    */
   uint64_t tris_large;       /* rasterized cooperatively by a whole block     */
+  uint64_t launches;         /* kernels enqueued by the calls (table uploads
+                                included), as declared by the host side      */
 } vs_stats;
 
 /* Synchronizes `stream`, copies the counters accumulated in `workspace`

@@ -21,7 +21,7 @@ using namespace vsd;
 struct vs_ctx {
   int device;
   int num_sms;
-  int persist_blocks_per_sm;
+  int persist_blocks_per_sm[2];   // forward-only, forward + backward
 };
 
 struct vs_object {
@@ -99,12 +99,10 @@ struct ItemReq {
 };
 
 struct Plan {
-  size_t off_items, off_shells, off_done, off_pre, table_end, total;
+  size_t off_items, off_shells, off_done, off_stage, table_end, total;
   std::vector<DItem> items;
   std::vector<DShell> shells;
-  std::vector<int> pre;          // [4][n+1]
-  int phase_total[NPH];
-  int phase_start[NPH];
+  std::vector<int> stage_pre;    // [n + 3]
   int total_units;
 };
 
@@ -120,12 +118,12 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
   off = align256(off + sizeof(DShell) * (size_t)S);
   P.off_done = off;
   off = align256(off + sizeof(int) * (size_t)n * NPH);
-  P.off_pre = off;
-  off = align256(off + sizeof(int) * (size_t)NPH * (n + 1));
+  P.off_stage = off;
+  off = align256(off + sizeof(int) * (size_t)(n + NPH));
   P.table_end = off;
   P.items.assign(n, DItem{});
   P.shells.assign(S, DShell{});
-  P.pre.assign((size_t)NPH * (n + 1), 0);
+  P.stage_pre.assign((size_t)n + NPH, 0);
   int sidx = 0;
   for (int j = 0; j < n; ++j) {
     const vs_object& o = *req[j].obj;
@@ -146,9 +144,9 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
     it.bg[0] = bg ? bg[0] : 0.f; it.bg[1] = bg ? bg[1] : 0.f; it.bg[2] = bg ? bg[2] : 0.f;
     it.maxdeg = -1;
     const size_t HW = (size_t)c.width * c.height;
-    // per-item workspace regions
-    it.large_count = reinterpret_cast<int32_t*>(ws ? ws + off : nullptr);
-    off = align256(off + sizeof(int32_t) * o.k);
+    int ls = 0;
+    while ((1 << ls) < o.k) ++ls;
+    it.lane_shift = ls;
     it.setup_pre[0] = 0;
     it.raster_pre[0] = 0;
     for (int i = 0; i < o.k; ++i) {
@@ -171,8 +169,6 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
       if (d.format == VS_TEX_SH_F16) it.maxdeg = std::max(it.maxdeg, (int)d.sh_degree);
       s.vsetup = reinterpret_cast<int4*>(ws ? ws + off : nullptr);
       off = align256(off + sizeof(int4) * (size_t)d.num_verts);
-      s.large = reinterpret_cast<int32_t*>(ws ? ws + off : nullptr);
-      off = align256(off + sizeof(int32_t) * (size_t)d.num_tris);
       it.setup_pre[i + 1] = it.setup_pre[i] + (d.num_verts + kSetupPerUnit - 1) / kSetupPerUnit;
       it.raster_pre[i + 1] = it.raster_pre[i] + (d.num_tris + kRasterPerUnit - 1) / kRasterPerUnit;
     }
@@ -182,21 +178,23 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
     it.clear_units = clear_vis ? (int)((vis_words + kClearPerUnit - 1) / kClearPerUnit) : 0;
     it.units[PH_SETUP] = it.clear_units + it.setup_pre[o.k];
     it.units[PH_RASTER] = clear_vis ? it.raster_pre[o.k] : 0;
-    it.units[PH_LARGE] = clear_vis ? kLargeUnits : 0;
-    it.units[PH_SHADE] = (int)((HW + kShadePerUnit - 1) / kShadePerUnit);
+    const size_t slots = HW << ls;
+    it.units[PH_SHADE] = (int)((slots + kShadeSlots - 1) / kShadeSlots);
     sidx += o.k;
   }
   P.total = align256(off);
-  int g = 0;
-  for (int ph = 0; ph < NPH; ++ph) {
-    int* pre = P.pre.data() + ph * (n + 1);
-    pre[0] = 0;
-    for (int j = 0; j < n; ++j) pre[j + 1] = pre[j] + P.items[j].units[ph];
-    P.phase_total[ph] = pre[n];
-    P.phase_start[ph] = g;
-    g += pre[n];
+  // skewed stages: stage s = SETUP(s), RASTER(s-1), SHADE(s-2)
+  long long g = 0;
+  for (int st = 0; st < n + NPH - 1; ++st) {
+    P.stage_pre[st] = (int)std::min<long long>(g, 0x7FFFFFFF);
+    for (int ph = 0; ph < NPH; ++ph) {
+      const int j = st - ph;
+      if (j >= 0 && j < n) g += P.items[j].units[ph];
+    }
   }
-  P.total_units = g;
+  P.stage_pre[n + NPH - 1] = (int)std::min<long long>(g, 0x7FFFFFFF);
+  P.total_units = (int)std::min<long long>(g, 0x7FFFFFFF);
+  if (g > 0x7FFFFFFF) return fail(VS_ERR_OVERFLOW, "too many work units (%lld)", g);
   return VS_OK;
 }
 
@@ -206,33 +204,38 @@ TableRef table_ref(const Plan& P, char* ws) {
   t.items = reinterpret_cast<DItem*>(ws + P.off_items);
   t.shells = reinterpret_cast<DShell*>(ws + P.off_shells);
   t.done = reinterpret_cast<int*>(ws + P.off_done);
-  t.unit_pre = reinterpret_cast<const int*>(ws + P.off_pre);
+  t.stage_pre = reinterpret_cast<const int*>(ws + P.off_stage);
   t.n = (int)P.items.size();
   t.total = P.total_units;
-  for (int i = 0; i < NPH; ++i) t.phase_start[i] = P.phase_start[i];
   return t;
 }
 
-// Copies the table (items, shells, zeroed completion counters, unit
-// prefixes) into the workspace through kernel parameters.
-vs_status upload_table(const Plan& P, char* ws, cudaStream_t st) {
+size_t upload_chunks(const Plan& P) {
+  const size_t bytes = P.table_end - P.off_items;
+  return std::max<size_t>(1, (bytes + kUploadBytes - 1) / kUploadBytes);
+}
+
+// Copies the table (items, shells, zeroed completion counters, stage
+// prefixes) into the workspace through kernel parameters; `kernels` is the
+// number of compute kernels the call enqueues after the upload.
+vs_status upload_table(const Plan& P, char* ws, int kernels, cudaStream_t st) {
   std::vector<char> blob(P.table_end - P.off_items, 0);
   std::memcpy(blob.data(), P.items.data(), sizeof(DItem) * P.items.size());
   std::memcpy(blob.data() + (P.off_shells - P.off_items), P.shells.data(), sizeof(DShell) * P.shells.size());
-  std::memcpy(blob.data() + (P.off_pre - P.off_items), P.pre.data(), sizeof(int) * P.pre.size());
+  std::memcpy(blob.data() + (P.off_stage - P.off_items), P.stage_pre.data(), sizeof(int) * P.stage_pre.size());
   static thread_local UploadChunk chunk;
+  const size_t nchunks = upload_chunks(P);
   size_t pos = 0;
-  bool first = true;
-  while (pos < blob.size() || first) {
+  for (size_t c = 0; c < nchunks; ++c) {
     const size_t nb = std::min(blob.size() - pos, (size_t)kUploadBytes);
     chunk.dst_off = (uint32_t)(P.off_items + pos);
     chunk.nbytes = (uint32_t)nb;
-    chunk.reset = first ? 1 : 0;
+    chunk.reset = c == 0 ? 1 : 0;
+    chunk.launches = c == 0 ? (int32_t)(nchunks + kernels) : 0;
     std::memcpy(chunk.data, blob.data() + pos, nb);
     cudaError_t e = vsk::upload(ws, chunk, st);
     if (e != cudaSuccess) return cuda_fail(e, "table upload launch");
     pos += nb;
-    first = false;
   }
   return VS_OK;
 }
@@ -279,11 +282,13 @@ vs_status vs_create(vs_ctx** ctx, int device) {
     delete c;
     return cuda_fail(e, "cudaDeviceGetAttribute");
   }
-  if ((e = vsk::persistent_occupancy(&c->persist_blocks_per_sm)) != cudaSuccess) {
-    delete c;
-    return cuda_fail(e, "occupancy query");
+  for (int b = 0; b < 2; ++b) {
+    if ((e = vsk::persistent_occupancy(b == 1, &c->persist_blocks_per_sm[b])) != cudaSuccess) {
+      delete c;
+      return cuda_fail(e, "occupancy query");
+    }
+    if (c->persist_blocks_per_sm[b] < 1) c->persist_blocks_per_sm[b] = 1;
   }
-  if (c->persist_blocks_per_sm < 1) c->persist_blocks_per_sm = 1;
   *ctx = c;
   g_err.clear();
   return VS_OK;
@@ -348,7 +353,7 @@ vs_status vs_render(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, con
   if ((s = check_ws(P, workspace, ws_bytes)) != VS_OK) return s;
   if ((s = set_device(ctx)) != VS_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if ((s = upload_table(P, ws, st)) != VS_OK) return s;
+  if ((s = upload_table(P, ws, vsk::plain_forward_launches(P.items[0].units), st)) != VS_OK) return s;
   cudaError_t e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render launch");
 }
@@ -368,7 +373,7 @@ vs_status vs_render_backward(vs_ctx* ctx, const vs_object* obj, const vs_camera*
   if ((s = check_ws(P, workspace, ws_bytes)) != VS_OK) return s;
   if ((s = set_device(ctx)) != VS_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if ((s = upload_table(P, ws, st)) != VS_OK) return s;
+  if ((s = upload_table(P, ws, vsk::plain_backward_launches(P.items[0].units), st)) != VS_OK) return s;
   cudaError_t e = vsk::plain_backward(table_ref(P, ws), P.items[0].units, st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_backward launch");
 }
@@ -397,10 +402,10 @@ vs_status vs_render_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, co
   if ((s = check_ws(P, workspace, ws_bytes)) != VS_OK) return s;
   if ((s = set_device(ctx)) != VS_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if ((s = upload_table(P, ws, st)) != VS_OK) return s;
-  const int grid = ctx->num_sms * ctx->persist_blocks_per_sm;
+  if ((s = upload_table(P, ws, 1, st)) != VS_OK) return s;
+  const int grid = ctx->num_sms * ctx->persist_blocks_per_sm[do_backward ? 1 : 0];
   const long long spin_limit = 1ll << 24;   // ~ seconds with 200 ns sleeps
-  cudaError_t e = vsk::persistent(table_ref(P, ws), grid, spin_limit, st);
+  cudaError_t e = vsk::persistent(table_ref(P, ws), do_backward != 0, grid, spin_limit, st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_batch launch");
 }
 
@@ -418,6 +423,7 @@ vs_status vs_read_stats(void* workspace, vs_stream_t stream, int32_t reset, vs_s
   out->tris_culled_near = h.nearc;
   out->tris_culled_guard = h.guard;
   out->tris_large = h.large;
+  out->launches = h.launches;
   if (reset) {
     if ((e = cudaMemset(workspace, 0, sizeof h)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
   }

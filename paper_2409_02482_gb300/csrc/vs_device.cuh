@@ -22,12 +22,13 @@ constexpr int kThreads = 256;          // threads per block, all kernels
 constexpr int kSetupPerUnit = 1024;    // vertices per setup unit
 constexpr int kRasterPerUnit = 256;    // triangles per raster unit (1 / thread)
 constexpr int kClearPerUnit = 65536;   // visibility words cleared per unit
-constexpr int kShadePerUnit = 256;     // pixels per shading unit (1 / thread)
-constexpr int kLargeUnits = 8;         // large-triangle units per item
+constexpr int kShadeSlots = 2048;      // (pixel, shell-lane) slots per shading unit
 constexpr int kSmallMaxPixels = 64;    // bbox pixels one thread rasterizes
 constexpr int kMaxShells = VS_MAX_SHELLS;
 
-enum { PH_SETUP = 0, PH_RASTER = 1, PH_LARGE = 2, PH_SHADE = 3, NPH = 4 };
+// Phases of one item.  Large triangles are rasterized by the whole block
+// inside the raster unit that met them.
+enum { PH_SETUP = 0, PH_RASTER = 1, PH_SHADE = 2, NPH = 3 };
 
 constexpr int kInvalidX = -2147483647 - 1;   // vertex marker: culled
 enum { VTX_NEAR = 1, VTX_GUARD = 2 };
@@ -46,7 +47,6 @@ struct alignas(16) DShell {
   const void* tex;             // [th, tw, pitch]
   float* grad;                 // [th, tw, pitch] FP32 (backward) or null
   int4* vsetup;                // [nv] (X, Y, bits(1/w), q) -- workspace
-  int32_t* large;              // [nt] large-triangle list -- workspace
   int32_t nv, nt, tw, th;
   int32_t fmt, degree, pitch;
   int32_t vec;                 // texel load width in values (1, 2, 4, 8)
@@ -61,10 +61,10 @@ struct alignas(16) DItem {
   const float* grad_rgb;       // [H*W, 3] gradient or target, or null
   float* loss;                 // scalar or null
   unsigned long long* vis;     // [k, H*W] -- workspace
-  int32_t* large_count;        // [k] -- workspace
   int32_t k, shell0, maxdeg, clear_units;
-  int32_t flags, do_bwd, stall, pad;
-  int32_t units[NPH];
+  int32_t flags, do_bwd, stall;
+  int32_t lane_shift;          // log2 of the lanes per pixel (>= k)
+  int32_t units[4];            // per phase (3 used)
   int32_t setup_pre[kMaxShells + 1];
   int32_t raster_pre[kMaxShells + 1];
   float bg[4];
@@ -79,7 +79,8 @@ struct alignas(16) WsHeader {
   uint32_t next_unit;
   int32_t pad;
   unsigned long long frags, front, back, nearc, guard, large;
-  unsigned long long reserved[24];
+  unsigned long long launches;  // kernels enqueued by the calls (host-declared)
+  unsigned long long reserved[23];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 

@@ -8,14 +8,16 @@
 // (Sec. 3 "Texturing Meshes"):
 //   SETUP  clear the per-shell visibility words; transform + snap vertices
 //   RASTER one thread per triangle: cull, edge functions, exact depth key,
-//          64-bit atomicMax (key << 32 | ~triangle) per (shell, pixel):
-//          nearest hit per shell, ties to the lower triangle (Fig. 3c);
-//          triangles with large screen boxes are queued for LARGE
-//   LARGE  one warp per queued triangle, lanes over its box
-//   SHADE  one thread per pixel: per shell in order, perspective-correct UV,
-//          bilinear fetch at texel centres (Fig. 5), SH decode with the ray
-//          direction, front-to-back over (Eq. 6 with Eq. 1's
-//          transmittance); optionally the adjoint w.r.t. texels.
+//          64-bit atomicMax (key << 32 | ~triangle) per (shell, pixel) --
+//          the nearest hit of each shell, ties to the lower triangle
+//          (Fig. 3c); triangles with large screen boxes are rasterized by
+//          the whole block afterwards
+//   SHADE  one lane per (pixel, shell): perspective-correct UV, bilinear
+//          fetch at texel centres (Fig. 5), SH decode with the ray
+//          direction; the lanes of a pixel then composite front to back
+//          with a segmented warp scan (Eq. 6 with Eq. 1's transmittance)
+//          and, for the adjoint, a segmented suffix scan of the colour
+//          seen behind each shell.
 
 #include <cuda_runtime.h>
 
@@ -36,7 +38,6 @@ __device__ void unit_setup(const DItem& it, const DShell* sh, int u) {
     const size_t n2 = (end - beg) >> 1;
     for (size_t i = threadIdx.x; i < n2; i += blockDim.x) p[i] = make_uint4(0, 0, 0, 0);
     if (((end - beg) & 1) && threadIdx.x == 0) it.vis[end - 1] = 0ull;
-    if (u == 0 && (int)threadIdx.x < it.k) it.large_count[threadIdx.x] = 0;
     return;
   }
   u -= it.clear_units;
@@ -49,15 +50,18 @@ __device__ void unit_setup(const DItem& it, const DShell* sh, int u) {
 }
 
 // ----------------------------------------------------------------------------
-// RASTER / LARGE
+// RASTER
 // ----------------------------------------------------------------------------
 // Loads triangle t of shell s; 0 = front-facing and rasterizable, 1..3 =
 // culled (back/zero-area, near, guard band), 4 = index out of range.
-__device__ __forceinline__ int load_tri(const DShell& s, const DCam& c, int t, Tri& T) {
+__device__ __forceinline__ int load_tri(const DShell& s, const DCam& c, int t, Tri& T, int idx[3]) {
   const int* ip = s.tris + 3 * (size_t)t;
-  const int i0 = __ldg(ip), i1 = __ldg(ip + 1), i2 = __ldg(ip + 2);
-  if ((unsigned)i0 >= (unsigned)s.nv || (unsigned)i1 >= (unsigned)s.nv || (unsigned)i2 >= (unsigned)s.nv) return 4;
-  return make_tri(__ldcg(s.vsetup + i0), __ldcg(s.vsetup + i1), __ldcg(s.vsetup + i2), c.W, c.H, T);
+  idx[0] = __ldg(ip);
+  idx[1] = __ldg(ip + 1);
+  idx[2] = __ldg(ip + 2);
+  if ((unsigned)idx[0] >= (unsigned)s.nv || (unsigned)idx[1] >= (unsigned)s.nv || (unsigned)idx[2] >= (unsigned)s.nv)
+    return 4;
+  return make_tri(__ldcg(s.vsetup + idx[0]), __ldcg(s.vsetup + idx[1]), __ldcg(s.vsetup + idx[2]), c.W, c.H, T);
 }
 
 __device__ __forceinline__ void raster_pixel(const Tri& T, int t, int x, int y, int W, unsigned long long* vis) {
@@ -67,27 +71,31 @@ __device__ __forceinline__ void raster_pixel(const Tri& T, int t, int x, int y, 
 }
 
 __device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* hdr) {
+  __shared__ int s_nlarge;
+  __shared__ int s_large[kRasterPerUnit];
   int i = 0;
   while (i + 1 < it.k && u >= it.raster_pre[i + 1]) ++i;
   const DShell& s = sh[i];
   const int t = (u - it.raster_pre[i]) * kRasterPerUnit + threadIdx.x;
   const int W = it.cam.W, H = it.cam.H;
+  unsigned long long* vis = it.vis + (size_t)i * W * H;
+  if (threadIdx.x == 0) s_nlarge = 0;
+  __syncthreads();
   unsigned front = 0, back = 0, nearc = 0, guard = 0, large = 0, bad = 0;
   if (t < s.nt) {
     Tri T;
-    const int why = load_tri(s, it.cam, t, T);
+    int idx[3];
+    const int why = load_tri(s, it.cam, t, T, idx);
     if (why == 0) {
       front = 1;
       const int bw = T.xhi - T.xlo + 1, bh = T.yhi - T.ylo + 1;
       if (bw > 0 && bh > 0) {
-        unsigned long long* vis = it.vis + (size_t)i * W * H;
         if (bw * bh <= kSmallMaxPixels) {
           for (int y = T.ylo; y <= T.yhi; ++y)
             for (int x = T.xlo; x <= T.xhi; ++x) raster_pixel(T, t, x, y, W, vis);
         } else {
           large = 1;
-          const int slot = atomicAdd(it.large_count + i, 1);
-          if (slot < s.nt) s.large[slot] = t;
+          s_large[atomicAdd(&s_nlarge, 1)] = t;
         }
       }
     } else if (why == 1) back = 1;
@@ -101,24 +109,19 @@ __device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* 
   warp_count(&hdr->guard, guard);
   warp_count(&hdr->large, large);
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) record_error(hdr, VS_ERR_INVALID_ARG);
-}
-
-__device__ void unit_large(const DItem& it, const DShell* sh, int u) {
-  const int NW = kLargeUnits * (kThreads / 32);
-  const int gw = u * (kThreads / 32) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  const int W = it.cam.W, H = it.cam.H;
-  for (int i = 0; i < it.k; ++i) {
-    const DShell& s = sh[i];
-    const int n = min(__ldcg(it.large_count + i), s.nt);
-    unsigned long long* vis = it.vis + (size_t)i * W * H;
-    for (int b = gw; b < n; b += NW) {
-      const int t = __ldcg(s.large + b);
-      Tri T;
-      if (load_tri(s, it.cam, t, T) != 0) continue;
-      const int bw = T.xhi - T.xlo + 1, bh = T.yhi - T.ylo + 1;
-      const int npx = bw * bh;
-      for (int p = lane; p < npx; p += 32) raster_pixel(T, t, T.xlo + p % bw, T.ylo + p / bw, W, vis);
+  __syncthreads();
+  // large triangles: the whole block strides over each one's screen box
+  const int nl = s_nlarge;
+  for (int q = 0; q < nl; ++q) {
+    const int tq = s_large[q];
+    Tri T;
+    int idx[3];
+    if (load_tri(s, it.cam, tq, T, idx) != 0) continue;
+    const int bw = T.xhi - T.xlo + 1, bh = T.yhi - T.ylo + 1;
+    const int npx = bw * bh;
+    for (int p = threadIdx.x; p < npx; p += blockDim.x) {
+      const int yy = p / bw;
+      raster_pixel(T, tq, T.xlo + (p - yy * bw), T.ylo + yy, W, vis);
     }
   }
 }
@@ -127,22 +130,25 @@ __device__ void unit_large(const DItem& it, const DShell* sh, int u) {
 // SHADE (+ adjoint)
 // ----------------------------------------------------------------------------
 template <int DEG, int VEC>
-__device__ __forceinline__ Frag fetch_sh(const DShell& s, const Footprint& f, const float Y[16]) {
+__device__ __forceinline__ Frag fetch_sh(const DShell& s, const Footprint& f, const float3 v) {
   constexpr int NCH = 1 + 3 * (DEG + 1) * (DEG + 1);
+  float Y[16];
+  sh_basis(DEG, v.x, v.y, v.z, Y);
   float val[NCH];
   bilinear_f16<NCH, VEC>(reinterpret_cast<const __half*>(s.tex), s.tw, s.pitch, f, val);
   return decode_sh<DEG>(val, Y);
 }
 
-__device__ __noinline__ Frag fetch_frag(const DShell& s, const Footprint& f, const float Y[16]) {
+// Colour and opacity of one fragment; v = unit ray direction (SH only).
+__device__ __forceinline__ Frag fetch_frag(const DShell& s, const Footprint& f, const float3 v) {
   if (s.fmt == VS_TEX_RGBA_F32) {
-    float v[4];
-    if (s.vec == 4) bilinear_rgba<4>(reinterpret_cast<const float*>(s.tex), s.tw, s.pitch, f, v);
-    else bilinear_rgba<1>(reinterpret_cast<const float*>(s.tex), s.tw, s.pitch, f, v);
-    return {v[0], v[1], v[2], v[3]};
+    float c[4];
+    if (s.vec == 4) bilinear_rgba<4>(reinterpret_cast<const float*>(s.tex), s.tw, s.pitch, f, c);
+    else bilinear_rgba<1>(reinterpret_cast<const float*>(s.tex), s.tw, s.pitch, f, c);
+    return {c[0], c[1], c[2], c[3]};
   }
 #define VS_CASE(D, V) \
-  case D * 16 + V: return fetch_sh<D, V>(s, f, Y);
+  case D * 16 + V: return fetch_sh<D, V>(s, f, v);
   switch (s.degree * 16 + s.vec) {
     VS_CASE(0, 1) VS_CASE(0, 2) VS_CASE(0, 4) VS_CASE(0, 8)
     VS_CASE(1, 1) VS_CASE(1, 2) VS_CASE(1, 4) VS_CASE(1, 8)
@@ -155,10 +161,12 @@ __device__ __noinline__ Frag fetch_frag(const DShell& s, const Footprint& f, con
 
 // dL/d(values) of one fragment, scattered into its 4 texels.
 template <int DEG, int GV>
-__device__ __forceinline__ void adjoint_sh(const DShell& s, const Footprint& f, const float Y[16],
+__device__ __forceinline__ void adjoint_sh(const DShell& s, const Footprint& f, const float3 v,
                                            const Frag& fr, float gcr, float gcg, float gcb, float ga) {
   constexpr int NB = (DEG + 1) * (DEG + 1);
   constexpr int NCH = 1 + 3 * NB;
+  float Y[16];
+  sh_basis(DEG, v.x, v.y, v.z, Y);
   float dval[NCH];
   dval[0] = ga * fr.a * (1.0f - fr.a);
   const float dz[3] = {gcr * fr.r * (1.0f - fr.r), gcg * fr.g * (1.0f - fr.g), gcb * fr.b * (1.0f - fr.b)};
@@ -169,8 +177,8 @@ __device__ __forceinline__ void adjoint_sh(const DShell& s, const Footprint& f, 
   scatter_grad<NCH, GV>(s.grad, s.tw, s.pitch, f, dval);
 }
 
-__device__ __noinline__ void adjoint_frag(const DShell& s, const Footprint& f, const float Y[16],
-                                          const Frag& fr, float gcr, float gcg, float gcb, float ga) {
+__device__ __forceinline__ void adjoint_frag(const DShell& s, const Footprint& f, const float3 v,
+                                             const Frag& fr, float gcr, float gcg, float gcb, float ga) {
   if (s.fmt == VS_TEX_RGBA_F32) {
     const float dval[4] = {gcr, gcg, gcb, ga};
     if (s.gvec == 4) scatter_grad<4, 4>(s.grad, s.tw, s.pitch, f, dval);
@@ -179,7 +187,7 @@ __device__ __noinline__ void adjoint_frag(const DShell& s, const Footprint& f, c
     return;
   }
 #define VS_CASE(D, V) \
-  case D * 16 + V: adjoint_sh<D, V>(s, f, Y, fr, gcr, gcg, gcb, ga); return;
+  case D * 16 + V: adjoint_sh<D, V>(s, f, v, fr, gcr, gcg, gcb, ga); return;
   switch (s.degree * 16 + s.gvec) {
     VS_CASE(0, 1) VS_CASE(0, 2) VS_CASE(0, 4)
     VS_CASE(1, 1) VS_CASE(1, 2) VS_CASE(1, 4)
@@ -190,94 +198,116 @@ __device__ __noinline__ void adjoint_frag(const DShell& s, const Footprint& f, c
 #undef VS_CASE
 }
 
-// One thread per pixel.  FROM_HITS: the hits come from the public int32
-// buffer (standalone backward) instead of the visibility words.
+// Shading unit: kShadeSlots (pixel, lane) slots; L = 2^lane_shift lanes per
+// pixel, lane i handles shell i (lanes >= k idle but join the scans).
+// FROM_HITS: hits come from the public int32 buffer (standalone backward)
+// instead of the visibility words.
 template <bool BWD, bool FROM_HITS>
 __device__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* hdr) {
+  const unsigned FULL = 0xffffffffu;
   const int W = it.cam.W, H = it.cam.H;
   const int HW = W * H;
-  const int p = u * kShadePerUnit + threadIdx.x;
+  const int ls = it.lane_shift;
+  const int L = 1 << ls;
+  const int i = threadIdx.x & (L - 1);            // shell of this lane
+  const int ppass = kThreads >> ls;               // pixels per pass
+  const int npass = kShadeSlots / kThreads;
+  const int pix0 = u * (kShadeSlots >> ls);
   unsigned nfrag = 0, bad = 0;
   float loss = 0.0f;
-  if (p < HW) {
-    const int y = p / W, x = p - y * W;
-    const int px = 256 * x + 128, py = 256 * y + 128;
-    float Y[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) Y[m] = 0.0f;
-    if (it.maxdeg >= 0) {
-      const float3 v = ray_dir(it.cam, x, y);
-      sh_basis(it.maxdeg, v.x, v.y, v.z, Y);
-    }
-    float Cr = 0.f, Cg = 0.f, Cb = 0.f, T = 1.0f;
-    // per-shell state kept for the adjoint
-    Frag sf[BWD ? kMaxShells : 1];
-    Footprint sfp[BWD ? kMaxShells : 1];
-    float sT[BWD ? kMaxShells : 1];
-    unsigned mask = 0;
-    for (int i = 0; i < it.k; ++i) {
-      const DShell& s = sh[i];
-      int tri;
+  for (int pass = 0; pass < npass; ++pass) {
+    const int p = pix0 + pass * ppass + (threadIdx.x >> ls);
+    const bool pix_ok = p < HW;
+    const bool act = pix_ok && i < it.k;
+    int tri = -1;
+    if (act) {
       if (FROM_HITS) {
         tri = __ldg(it.hits + (size_t)i * HW + p);
       } else {
         tri = vis_tri(__ldcg(it.vis + (size_t)i * HW + p));
         if (it.hits) it.hits[(size_t)i * HW + p] = tri;
       }
-      if (tri < 0) continue;
-      Tri Tr;
-      if (tri >= s.nt || load_tri(s, it.cam, tri, Tr) != 0) { bad = 1; continue; }
-      const int* ip = s.tris + 3 * (size_t)tri;
-      const float2 uv[3] = {__ldg(s.uv + __ldg(ip)), __ldg(s.uv + __ldg(ip + 1)), __ldg(s.uv + __ldg(ip + 2))};
-      const Footprint f = footprint(Tr, uv, s.tw, s.th, px, py);
-      const Frag fr = fetch_frag(s, f, Y);
-      ++nfrag;
-      const float ta = T * fr.a;
-      Cr = fmaf(ta, fr.r, Cr);
-      Cg = fmaf(ta, fr.g, Cg);
-      Cb = fmaf(ta, fr.b, Cb);
-      if constexpr (BWD) {
-        sf[i] = fr;
-        sfp[i] = f;
-        sT[i] = T;
-        mask |= 1u << i;
-      }
-      T = T * (1.0f - fr.a);
     }
-    const float outr = fmaf(T, it.bg[0], Cr), outg = fmaf(T, it.bg[1], Cg), outb = fmaf(T, it.bg[2], Cb);
-    if (it.out) it.out[p] = make_float4(outr, outg, outb, 1.0f - T);
+    Frag fr = {0.f, 0.f, 0.f, 0.f};
+    Footprint f;
+    float3 v = make_float3(0.f, 0.f, 1.f);
+    bool hit = false;
+    if (tri >= 0) {
+      const DShell& s = sh[i];
+      Tri Tr;
+      int idx[3];
+      if (tri >= s.nt || load_tri(s, it.cam, tri, Tr, idx) != 0) {
+        bad = 1;
+      } else {
+        const int y = p / W, x = p - y * W;
+        const float2 uv[3] = {__ldg(s.uv + idx[0]), __ldg(s.uv + idx[1]), __ldg(s.uv + idx[2])};
+        f = footprint(Tr, uv, s.tw, s.th, 256 * x + 128, 256 * y + 128);
+        if (s.fmt == VS_TEX_SH_F16) v = ray_dir(it.cam, x, y);
+        fr = fetch_frag(s, f, v);
+        hit = true;
+        ++nfrag;
+      }
+    }
+    // front-to-back over across the lanes of the pixel:
+    // T_i = prod_{j<i} (1 - a_j) by a segmented exclusive product scan
+    float incl = 1.0f - fr.a;
+    for (int o = 1; o < L; o <<= 1) {
+      const float v = __shfl_up_sync(FULL, incl, o, L);
+      if (i >= o) incl *= v;
+    }
+    float Ti = __shfl_up_sync(FULL, incl, 1, L);
+    if (i == 0) Ti = 1.0f;
+    const float Tk = __shfl_sync(FULL, incl, L - 1, L);
+    const float ta = Ti * fr.a;
+    float cr = ta * fr.r, cg = ta * fr.g, cb = ta * fr.b;
+    for (int o = L >> 1; o > 0; o >>= 1) {
+      cr += __shfl_xor_sync(FULL, cr, o, L);
+      cg += __shfl_xor_sync(FULL, cg, o, L);
+      cb += __shfl_xor_sync(FULL, cb, o, L);
+    }
+    const float outr = fmaf(Tk, it.bg[0], cr), outg = fmaf(Tk, it.bg[1], cg), outb = fmaf(Tk, it.bg[2], cb);
+    if (i == 0 && pix_ok && it.out) it.out[p] = make_float4(outr, outg, outb, 1.0f - Tk);
     if constexpr (BWD) {
-      const float* gp = it.grad_rgb + 3 * (size_t)p;
-      float gr = __ldg(gp), gg = __ldg(gp + 1), gb = __ldg(gp + 2);
-      if (it.flags & VS_FLAG_LOSS_L2) {
-        const float dr = outr - gr, dg = outg - gg, db = outb - gb;
-        const float inv = 1.0f / (3.0f * (float)HW);
-        loss = (dr * dr + dg * dg + db * db) * inv;
-        gr = 2.0f * inv * dr;
-        gg = 2.0f * inv * dg;
-        gb = 2.0f * inv * db;
+      float gr = 0.f, gg = 0.f, gb = 0.f;
+      if (pix_ok) {
+        const float* gp = it.grad_rgb + 3 * (size_t)p;
+        gr = __ldg(gp);
+        gg = __ldg(gp + 1);
+        gb = __ldg(gp + 2);
+        if (it.flags & VS_FLAG_LOSS_L2) {
+          const float dr = outr - gr, dg = outg - gg, db = outb - gb;
+          const float inv = 1.0f / (3.0f * (float)HW);
+          if (i == 0) loss += (dr * dr + dg * dg + db * db) * inv;
+          gr = 2.0f * inv * dr;
+          gg = 2.0f * inv * dg;
+          gb = 2.0f * inv * db;
+        }
       }
-      float Ar = it.bg[0], Ag = it.bg[1], Ab = it.bg[2];
-      for (int i = it.k - 1; i >= 0; --i) {
-        if (!((mask >> i) & 1u)) continue;
-        const Frag fr = sf[i];
-        const float Ti = sT[i];
-        const float ta = Ti * fr.a;
-        const float ga = Ti * ((fr.r - Ar) * gr + (fr.g - Ag) * gg + (fr.b - Ab) * gb);
-        Ar = fmaf(fr.a, fr.r - Ar, Ar);
-        Ag = fmaf(fr.a, fr.g - Ag, Ag);
-        Ab = fmaf(fr.a, fr.b - Ab, Ab);
-        adjoint_frag(sh[i], sfp[i], Y, fr, ta * gr, ta * gg, ta * gb, ga);
+      // B_i = A_i . g with A_i the colour seen from in front of shell i:
+      // B_i = a_i + b_i B_{i+1}, a_i = alpha_i (c_i . g), b_i = 1 - alpha_i,
+      // B_k = bg . g; segmented suffix composition of the affine maps.
+      const float cgd = fr.r * gr + fr.g * gg + fr.b * gb;
+      float a = fr.a * cgd, b = 1.0f - fr.a;
+      for (int o = 1; o < L; o <<= 1) {
+        const float a2 = __shfl_down_sync(FULL, a, o, L), b2 = __shfl_down_sync(FULL, b, o, L);
+        if (i + o < L) {
+          a = fmaf(b, a2, a);
+          b = b * b2;
+        }
       }
+      float an = __shfl_down_sync(FULL, a, 1, L), bn = __shfl_down_sync(FULL, b, 1, L);
+      if (i == L - 1) { an = 0.0f; bn = 1.0f; }
+      const float Bnext = fmaf(bn, it.bg[0] * gr + it.bg[1] * gg + it.bg[2] * gb, an);
+      if (hit) adjoint_frag(sh[i], f, v, fr, ta * gr, ta * gg, ta * gb, Ti * (cgd - Bnext));
     }
   }
   if (!FROM_HITS) warp_count(&hdr->frags, nfrag);
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) record_error(hdr, VS_ERR_INVALID_ARG);
+  if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) record_error(hdr, VS_ERR_INVALID_ARG);
   if constexpr (BWD) {
     if (it.loss && (it.flags & VS_FLAG_LOSS_L2)) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
-      if ((threadIdx.x & 31) == 0) atomicAdd(it.loss, loss);
+      for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(FULL, loss, o);
+      if ((threadIdx.x & 31) == 0 && loss != 0.0f) atomicAdd(it.loss, loss);
     }
   }
 }
@@ -292,6 +322,7 @@ __global__ void __launch_bounds__(kThreads) k_upload(char* ws, const __grid_cons
     WsHeader* h = reinterpret_cast<WsHeader*>(ws);
     h->next_unit = 0;
     h->abort = 0;
+    h->launches += (unsigned long long)c.launches;
   }
 }
 
@@ -305,13 +336,8 @@ __global__ void __launch_bounds__(kThreads) k_raster(TableRef tb, int item) {
   unit_raster(it, tb.shells + it.shell0, blockIdx.x, tb.hdr);
 }
 
-__global__ void __launch_bounds__(kThreads) k_large(TableRef tb, int item) {
-  const DItem& it = tb.items[item];
-  unit_large(it, tb.shells + it.shell0, blockIdx.x);
-}
-
 template <bool BWD, bool FROM_HITS>
-__global__ void __launch_bounds__(kThreads) k_shade(TableRef tb, int item) {
+__global__ void __launch_bounds__(kThreads, BWD ? 2 : 4) k_shade(TableRef tb, int item) {
   const DItem& it = tb.items[item];
   unit_shade<BWD, FROM_HITS>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr);
 }
@@ -332,11 +358,15 @@ __device__ bool wait_done(const int* ctr, int target, long long limit, WsHeader*
   }
 }
 
-// Persistent kernel over all items.  Units are dispensed in the global order
-// (phase, item, unit); a unit of phase p > 0 waits only for the phase p-1
-// units of its own item, all of which were dispensed earlier to blocks that
-// are already running, so the wait always ends (and is bounded anyway).
-__global__ void __launch_bounds__(kThreads) k_persistent(TableRef tb, long long spin_limit) {
+// Persistent kernel over all items.  Units are dispensed in a skewed global
+// order: stage s holds the SETUP units of item s, the RASTER units of item
+// s-1 and the SHADE units of item s-2, so that an item's visibility words
+// are written, resolved and read within a few stages (while still in L2).
+// A unit waits only for the previous phase of its own item, whose units were
+// all dispensed in an earlier stage to blocks that are already running, so
+// the wait always ends (and is bounded anyway).
+template <bool BWD>
+__global__ void __launch_bounds__(kThreads, BWD ? 2 : 4) k_persistent(TableRef tb, long long spin_limit) {
   __shared__ int s_unit, s_ok;
   WsHeader* hdr = tb.hdr;
   for (;;) {
@@ -346,18 +376,22 @@ __global__ void __launch_bounds__(kThreads) k_persistent(TableRef tb, long long 
     __syncthreads();
     const int g = s_unit;
     if (g >= tb.total) break;
-    int ph = 0;
-    while (ph + 1 < NPH && g >= tb.phase_start[ph + 1]) ++ph;
-    const int* pre = tb.unit_pre + ph * (tb.n + 1);
-    const int rel = g - tb.phase_start[ph];
-    int lo = 0, hi = tb.n - 1;   // last item with pre[item] <= rel
+    // stage: last s with stage_pre[s] <= g
+    int lo = 0, hi = tb.n + NPH - 2;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (__ldg(pre + mid) <= rel) lo = mid; else hi = mid - 1;
+      if (__ldg(tb.stage_pre + mid) <= g) lo = mid; else hi = mid - 1;
     }
-    const int j = lo;
-    const int u = rel - __ldg(pre + j);
+    int rel = g - __ldg(tb.stage_pre + lo);
+    int ph = 0, j = lo;
+    for (ph = 0; ph < NPH; ++ph) {
+      j = lo - ph;
+      const int cnt = (j >= 0 && j < tb.n) ? tb.items[j].units[ph] : 0;
+      if (rel < cnt) break;
+      rel -= cnt;
+    }
     const DItem& it = tb.items[j];
+    const int u = rel;
     if (threadIdx.x == 0) {
       bool ok = true;
       if (ph > 0) {
@@ -374,10 +408,8 @@ __global__ void __launch_bounds__(kThreads) k_persistent(TableRef tb, long long 
     switch (ph) {
       case PH_SETUP: unit_setup(it, sh, u); break;
       case PH_RASTER: unit_raster(it, sh, u, hdr); break;
-      case PH_LARGE: unit_large(it, sh, u); break;
       default:
-        if (it.do_bwd) unit_shade<true, false>(it, sh, u, hdr);
-        else unit_shade<false, false>(it, sh, u, hdr);
+        unit_shade<BWD, false>(it, sh, u, hdr);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -399,27 +431,31 @@ cudaError_t upload(char* ws, const UploadChunk& c, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+int plain_forward_launches(const int units[4]) { return (units[0] > 0) + (units[1] > 0) + (units[2] > 0); }
+int plain_backward_launches(const int units[4]) { return (units[0] > 0) + (units[2] > 0); }
+
 cudaError_t plain_forward(const TableRef& tb, const int units[4], cudaStream_t st) {
   if (units[0]) vsd::k_setup<<<units[0], vsd::kThreads, 0, st>>>(tb, 0);
   if (units[1]) vsd::k_raster<<<units[1], vsd::kThreads, 0, st>>>(tb, 0);
-  if (units[2]) vsd::k_large<<<units[2], vsd::kThreads, 0, st>>>(tb, 0);
-  if (units[3]) vsd::k_shade<false, false><<<units[3], vsd::kThreads, 0, st>>>(tb, 0);
+  if (units[2]) vsd::k_shade<false, false><<<units[2], vsd::kThreads, 0, st>>>(tb, 0);
   return cudaGetLastError();
 }
 
 cudaError_t plain_backward(const TableRef& tb, const int units[4], cudaStream_t st) {
   if (units[0]) vsd::k_setup<<<units[0], vsd::kThreads, 0, st>>>(tb, 0);
-  if (units[3]) vsd::k_shade<true, true><<<units[3], vsd::kThreads, 0, st>>>(tb, 0);
+  if (units[2]) vsd::k_shade<true, true><<<units[2], vsd::kThreads, 0, st>>>(tb, 0);
   return cudaGetLastError();
 }
 
-cudaError_t persistent(const TableRef& tb, int grid, long long spin_limit, cudaStream_t st) {
-  vsd::k_persistent<<<grid, vsd::kThreads, 0, st>>>(tb, spin_limit);
+cudaError_t persistent(const TableRef& tb, bool bwd, int grid, long long spin_limit, cudaStream_t st) {
+  if (bwd) vsd::k_persistent<true><<<grid, vsd::kThreads, 0, st>>>(tb, spin_limit);
+  else vsd::k_persistent<false><<<grid, vsd::kThreads, 0, st>>>(tb, spin_limit);
   return cudaGetLastError();
 }
 
-cudaError_t persistent_occupancy(int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, vsd::k_persistent, vsd::kThreads, 0);
+cudaError_t persistent_occupancy(bool bwd, int* blocks_per_sm) {
+  if (bwd) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, vsd::k_persistent<true>, vsd::kThreads, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, vsd::k_persistent<false>, vsd::kThreads, 0);
 }
 
 }  // namespace vsk

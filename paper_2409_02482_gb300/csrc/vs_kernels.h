@@ -15,11 +15,10 @@ struct TableRef {
   vsd::WsHeader* hdr;
   vsd::DItem* items;        // [n]
   vsd::DShell* shells;      // [sum of k]
-  int* done;                // [n * 4] completed units per (item, phase)
-  const int* unit_pre;      // [4][n + 1] unit prefix per phase
+  int* done;                // [n * 3] completed units per (item, phase)
+  const int* stage_pre;     // [n + 3] first global unit of each stage (+ total)
   int n;
   int total;                // all units
-  int phase_start[4];       // first global unit of each phase
 };
 
 // A slice of the host-built table carried to the device in kernel
@@ -28,15 +27,17 @@ constexpr int kUploadBytes = 24576;
 struct UploadChunk {
   uint32_t dst_off;
   uint32_t nbytes;          // multiple of 16
-  int32_t reset;            // reset next_unit / abort in the header
-  int32_t pad;
+  int32_t reset;            // first chunk: reset next_unit / abort, count launches
+  int32_t launches;         // kernels this call enqueues (added to the header)
   uint4 data[kUploadBytes / 16];
 };
 
 namespace vsk {
 cudaError_t upload(char* ws, const UploadChunk& c, cudaStream_t st);
+int plain_forward_launches(const int units[4]);
+int plain_backward_launches(const int units[4]);
 cudaError_t plain_forward(const TableRef& tb, const int units[4], cudaStream_t st);
 cudaError_t plain_backward(const TableRef& tb, const int units[4], cudaStream_t st);
-cudaError_t persistent(const TableRef& tb, int grid, long long spin_limit, cudaStream_t st);
-cudaError_t persistent_occupancy(int* blocks_per_sm);
+cudaError_t persistent(const TableRef& tb, bool bwd, int grid, long long spin_limit, cudaStream_t st);
+cudaError_t persistent_occupancy(bool bwd, int* blocks_per_sm);
 }  // namespace vsk
