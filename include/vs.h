@@ -145,8 +145,8 @@ vs_status vs_free_shells(vs_ctx* ctx, vs_object* obj);
 /* Bytes of workspace needed to render (and differentiate) the n_items
  * (object, camera) pairs in ONE vs_render_batch call; for n_items = 1 it
  * also covers vs_render / vs_render_backward of that pair.  Dominant terms
- * per item: 8 * k * H * W (per-shell visibility words) + 16 * sum(V) +
- * 4 * sum(T).  Pure host arithmetic.  Errors: VS_ERR_INVALID_ARG. */
+ * per item: 8 * k * H * W (per-shell visibility words) + 16 * sum(V)
+ * (snapped vertices).  Pure host arithmetic.  Errors: VS_ERR_INVALID_ARG. */
 vs_status vs_workspace_size(vs_ctx* ctx, const vs_object* const* objs, const vs_camera* cams,
                             int32_t n_items, uint32_t flags, size_t* bytes);
 
