@@ -132,6 +132,7 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
     std::memcpy(it.cam.m, c.world_to_cam, sizeof it.cam.m);
     it.cam.fx = c.fx; it.cam.fy = c.fy; it.cam.cx = c.cx; it.cam.cy = c.cy; it.cam.znear = c.znear;
     it.cam.W = c.width; it.cam.H = c.height;
+    it.cam.rfx = 1.0f / c.fx; it.cam.rfy = 1.0f / c.fy;
     it.out = reinterpret_cast<float4*>(req[j].out);
     it.hits = req[j].hits;
     it.grad_rgb = req[j].grad_rgb;

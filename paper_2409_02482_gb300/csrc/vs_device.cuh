@@ -37,7 +37,8 @@ struct alignas(16) DCam {
   float m[12];                 // world -> camera [R | t], row-major
   float fx, fy, cx, cy, znear;
   int32_t W, H;
-  int32_t pad;
+  float rfx, rfy;              // 1 / fx, 1 / fy (ray directions only)
+  int32_t pad[3];
 };
 
 struct alignas(16) DShell {
@@ -91,6 +92,22 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+// Fire-and-forget reductions (no value returned, so no wait on the result).
+__device__ __forceinline__ void red_max_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_f32(float* p, float v) {
+  asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_v2f32(float* p, float a, float b) {
+  asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+__device__ __forceinline__ void red_add_v4f32(float* p, float a, float b, float c, float d) {
+  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
 }
 
 __device__ __forceinline__ void record_error(WsHeader* h, int code) {
@@ -181,29 +198,34 @@ __device__ __forceinline__ bool covered(const Tri& t, const long long e[3]) {
   return (e[0] + t.tl[0] > 0) && (e[1] + t.tl[1] > 0) && (e[2] + t.tl[2] > 0);
 }
 
-// floor(sum_j e_j q_j / sum_j e_j) exactly, for e_j >= 0 (sum > 0, < 2^51)
-// and q_j < 2^31.  The quotient lies between min q and max q, so it fits in
-// 32 bits; an FP32 estimate is within ~2^10 of it, which bounds the residual
-// R = N - Q S below 2^62 and lets R be computed exactly in wrapping 64-bit
-// arithmetic; two correction steps make it exact.
-__device__ __forceinline__ unsigned depth_key(const Tri& t, const long long e[3]) {
-  const unsigned long long S = (unsigned long long)(e[0] + e[1] + e[2]);
-  const unsigned long long N = (unsigned long long)e[0] * t.q[0] + (unsigned long long)e[1] * t.q[1] +
-                               (unsigned long long)e[2] * t.q[2];   // mod 2^64
-  const float fS = (float)S;
-  const float est = (fmaf((float)e[0], (float)t.q[0],
-                     fmaf((float)e[1], (float)t.q[1], (float)e[2] * (float)t.q[2]))) / fS;
-  const unsigned qmin = min(t.q[0], min(t.q[1], t.q[2])), qmax = max(t.q[0], max(t.q[1], t.q[2]));
+// floor(sum_j e_j q_j / S) exactly, S = sum_j e_j, for e_j >= 0 (S > 0,
+// S < 2^51) and q_j < 2^31; rS ~ 1/S in FP32.  The quotient lies between min
+// q and max q, so it fits in 32 bits; the FP32 estimate (a sum of positive
+// terms, relative error ~6 ulp) is within ~2^10 of it, which bounds the
+// residual R = N - Q S below 2^62 and lets R be computed exactly in
+// wrapping 64-bit arithmetic; two correction steps make the quotient exact.
+__device__ __forceinline__ unsigned depth_key_r(const unsigned q[3], const long long e[3],
+                                                unsigned long long S, float rS) {
+  const unsigned long long N = (unsigned long long)e[0] * q[0] + (unsigned long long)e[1] * q[1] +
+                               (unsigned long long)e[2] * q[2];   // mod 2^64
+  const float est = fmaf((float)e[0], (float)q[0],
+                         fmaf((float)e[1], (float)q[1], (float)e[2] * (float)q[2])) * rS;
+  const unsigned qmin = min(q[0], min(q[1], q[2])), qmax = max(q[0], max(q[1], q[2]));
   unsigned Q = (unsigned)fminf(fmaxf(est, (float)qmin), (float)qmax);
   Q = min(max(Q, qmin), qmax);
   long long R = (long long)(N - (unsigned long long)Q * S);
-  Q = (unsigned)((long long)Q + (long long)floorf((float)R / fS));
+  Q = (unsigned)((long long)Q + (long long)floorf((float)R * rS));
   R = (long long)(N - (unsigned long long)Q * S);
 #pragma unroll 1
   for (int i = 0; i < 4 && R < 0; ++i) { --Q; R += (long long)S; }
 #pragma unroll 1
   for (int i = 0; i < 4 && R >= (long long)S; ++i) { ++Q; R -= (long long)S; }
   return Q;
+}
+
+__device__ __forceinline__ unsigned depth_key(const Tri& t, const long long e[3]) {
+  const unsigned long long S = (unsigned long long)(e[0] + e[1] + e[2]);
+  return depth_key_r(t.q, e, S, 1.0f / (float)S);
 }
 
 __device__ __forceinline__ unsigned long long vis_key(unsigned K, int tri) {
@@ -290,6 +312,17 @@ __device__ __forceinline__ void split_coord(float X0, ff delta, int& i, float& f
   i = (int)base + (int)fl;
 }
 
+// Same for a plain FP32 delta of a few texels at most: the sum with the
+// fraction in [0, 1) keeps an absolute error below 2^-20 texel.
+__device__ __forceinline__ void split_coord_f(float X0, float delta, int& i, float& f) {
+  const float a = __fsub_rn(X0, 0.5f);
+  const float base = floorf(a);
+  const float s = __fadd_rn(__fsub_rn(a, base), delta);
+  const float fl = floorf(s);
+  f = __fsub_rn(s, fl);
+  i = (int)base + (int)fl;
+}
+
 // Perspective-correct UV of pixel centre (px, py) mapped to texel space
 // (x = u W - 1/2, y = v H - 1/2), interpolated relative to vertex 0.  For
 // triangles spanning at most 8 texels plain FP32 keeps the texel-space
@@ -304,15 +337,16 @@ __device__ __forceinline__ Footprint footprint(const Tri& t, const float2 uv[3],
   const float d1x = __fsub_rn(X1, X0), d2x = __fsub_rn(X2, X0);
   const float d1y = __fsub_rn(Y1, Y0), d2y = __fsub_rn(Y2, Y0);
   const float span = fmaxf(fmaxf(fabsf(d1x), fabsf(d2x)), fmaxf(fabsf(d1y), fabsf(d2y)));
-  ff dx, dy;
+  Footprint f;
+  int ix, iy;
   if (span <= 8.0f) {
     const float w0 = __fmul_rn((float)e[0], t.iw[0]);
     const float w1 = __fmul_rn((float)e[1], t.iw[1]);
     const float w2 = __fmul_rn((float)e[2], t.iw[2]);
-    const float rD = __frcp_rn(__fadd_rn(__fadd_rn(w0, w1), w2));
+    const float rD = __fdividef(1.0f, __fadd_rn(__fadd_rn(w0, w1), w2));
     const float l1 = __fmul_rn(w1, rD), l2 = __fmul_rn(w2, rD);
-    dx = {__fmaf_rn(l1, d1x, __fmul_rn(l2, d2x)), 0.0f};
-    dy = {__fmaf_rn(l1, d1y, __fmul_rn(l2, d2y)), 0.0f};
+    split_coord_f(X0, __fmaf_rn(l1, d1x, __fmul_rn(l2, d2x)), ix, f.fx);
+    split_coord_f(Y0, __fmaf_rn(l1, d1y, __fmul_rn(l2, d2y)), iy, f.fy);
   } else {
     const ff w0 = ff_mul_f(ll_to_ff(e[0]), t.iw[0]);
     const ff w1 = ff_mul_f(ll_to_ff(e[1]), t.iw[1]);
@@ -320,13 +354,9 @@ __device__ __forceinline__ Footprint footprint(const Tri& t, const float2 uv[3],
     const ff D = ff_add(ff_add(w0, w1), w2);
     const ff ex1 = two_sum(X1, -X0), ex2 = two_sum(X2, -X0);
     const ff ey1 = two_sum(Y1, -Y0), ey2 = two_sum(Y2, -Y0);
-    dx = ff_div(ff_add(ff_mul(w1, ex1), ff_mul(w2, ex2)), D);
-    dy = ff_div(ff_add(ff_mul(w1, ey1), ff_mul(w2, ey2)), D);
+    split_coord(X0, ff_div(ff_add(ff_mul(w1, ex1), ff_mul(w2, ex2)), D), ix, f.fx);
+    split_coord(Y0, ff_div(ff_add(ff_mul(w1, ey1), ff_mul(w2, ey2)), D), iy, f.fy);
   }
-  Footprint f;
-  int ix, iy;
-  split_coord(X0, dx, ix, f.fx);
-  split_coord(Y0, dy, iy, f.fy);
   f.x0 = min(max(ix, 0), tw - 1);
   f.x1 = min(max(ix + 1, 0), tw - 1);
   f.y0 = min(max(iy, 0), th - 1);
@@ -366,12 +396,12 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
   Y[15] = 0.5900435899266435f * x * (xx - 3.0f * yy);
 }
 
-__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + __expf(-x)); }
+__device__ __forceinline__ float sigmoidf_(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
 
 // Unit world-space ray direction through pixel (x, y).
 __device__ __forceinline__ float3 ray_dir(const DCam& c, int x, int y) {
-  const float a = ((float)x + 0.5f - c.cx) / c.fx;
-  const float b = ((float)y + 0.5f - c.cy) / c.fy;
+  const float a = ((float)x + 0.5f - c.cx) * c.rfx;
+  const float b = ((float)y + 0.5f - c.cy) * c.rfy;
   // world = R^T (a, b, 1)
   float vx = c.m[0] * a + c.m[4] * b + c.m[8];
   float vy = c.m[1] * a + c.m[5] * b + c.m[9];
@@ -485,19 +515,14 @@ __device__ __forceinline__ void scatter_grad(float* grad, int tw, int pitch, con
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
       if constexpr (GV == 4) {
-        float4 v;
-        v.x = w[q] * dval[4 * l];
-        v.y = (4 * l + 1 < NCH) ? w[q] * dval[4 * l + 1] : 0.0f;
-        v.z = (4 * l + 2 < NCH) ? w[q] * dval[4 * l + 2] : 0.0f;
-        v.w = (4 * l + 3 < NCH) ? w[q] * dval[4 * l + 3] : 0.0f;
-        atomicAdd(reinterpret_cast<float4*>(g + 4 * l), v);
+        red_add_v4f32(g + 4 * l, w[q] * dval[4 * l],
+                      (4 * l + 1 < NCH) ? w[q] * dval[4 * l + 1] : 0.0f,
+                      (4 * l + 2 < NCH) ? w[q] * dval[4 * l + 2] : 0.0f,
+                      (4 * l + 3 < NCH) ? w[q] * dval[4 * l + 3] : 0.0f);
       } else if constexpr (GV == 2) {
-        float2 v;
-        v.x = w[q] * dval[2 * l];
-        v.y = (2 * l + 1 < NCH) ? w[q] * dval[2 * l + 1] : 0.0f;
-        atomicAdd(reinterpret_cast<float2*>(g + 2 * l), v);
+        red_add_v2f32(g + 2 * l, w[q] * dval[2 * l], (2 * l + 1 < NCH) ? w[q] * dval[2 * l + 1] : 0.0f);
       } else {
-        atomicAdd(g + l, w[q] * dval[l]);
+        red_add_f32(g + l, w[q] * dval[l]);
       }
     }
   }

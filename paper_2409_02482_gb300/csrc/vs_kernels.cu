@@ -67,21 +67,67 @@ __device__ __forceinline__ int load_tri(const DShell& s, const DCam& c, int t, T
 __device__ __forceinline__ void raster_pixel(const Tri& T, int t, int x, int y, int W, unsigned long long* vis) {
   long long e[3];
   edge_values(T, 256 * x + 128, 256 * y + 128, e);
-  if (covered(T, e)) atomicMax(vis + (size_t)y * W + x, vis_key(depth_key(T, e), t));
+  if (covered(T, e)) red_max_u64(vis + (size_t)y * W + x, vis_key(depth_key(T, e), t));
 }
 
+// Triangle record shared by the lanes of a warp during the raster walk.
+// Small boxes (<= kSmallMaxPixels pixel centres) keep every edge function
+// value within +-2^30, so the walk runs in 32-bit integers: e_j(dx, dy) =
+// c_j + gx_j dx + gy_j dy for pixel (xlo + dx, ylo + dy).
+struct TriS {
+  int c[3], gx[3], gy[3];
+  unsigned q[3];
+  int tl_bw;           // bits 0-2: top-left edges; bits 8+: box width
+  float rbw;           // 1 / box width
+  float rS;            // 1 / S, S = sum of the edge values = twice the area
+  int t;
+};
+struct TriPos {        // box origin of a record
+  int xlo, ylo;
+};
+
+// floor(sum_j e_j q_j / S) for the 32-bit edge values of a small box; same
+// estimate-and-correct scheme as depth_key_r.
+__device__ __forceinline__ unsigned depth_key32(const unsigned q[3], const int e[3], int S, float rS) {
+  const unsigned long long N = (unsigned long long)(unsigned)e[0] * q[0] +
+                               (unsigned long long)(unsigned)e[1] * q[1] +
+                               (unsigned long long)(unsigned)e[2] * q[2];
+  const float est = fmaf((float)e[0], (float)q[0], fmaf((float)e[1], (float)q[1], (float)e[2] * (float)q[2])) * rS;
+  const unsigned qmin = min(q[0], min(q[1], q[2])), qmax = max(q[0], max(q[1], q[2]));
+  unsigned Q = (unsigned)fminf(fmaxf(est, (float)qmin), (float)qmax);
+  Q = min(max(Q, qmin), qmax);
+  long long R = (long long)(N - (unsigned long long)Q * (unsigned)S);
+  Q = (unsigned)((long long)Q + (long long)floorf((float)R * rS));
+  R = (long long)(N - (unsigned long long)Q * (unsigned)S);
+#pragma unroll 1
+  for (int i = 0; i < 4 && R < 0; ++i) { --Q; R += S; }
+#pragma unroll 1
+  for (int i = 0; i < 4 && R >= S; ++i) { ++Q; R -= S; }
+  return Q;
+}
+
+// Raster unit: kRasterPerUnit triangles of one shell.  Each lane sets up one
+// triangle; then each warp walks all (triangle, box pixel) pairs of its 32
+// triangles together: window by window, a warp-wide OR of the triangles'
+// start bits tells every lane which triangle owns its pair, so lanes do not
+// idle on small or culled boxes.  Larger boxes are rasterized by the whole
+// warp, one triangle at a time.
 __device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* hdr) {
-  __shared__ int s_nlarge;
-  __shared__ int s_large[kRasterPerUnit];
+  __shared__ TriS s_tri[kRasterPerUnit];
+  __shared__ TriPos s_pos[kRasterPerUnit];
+  __shared__ int s_start[kRasterPerUnit];
+  const unsigned FULL = 0xffffffffu;
   int i = 0;
   while (i + 1 < it.k && u >= it.raster_pre[i + 1]) ++i;
   const DShell& s = sh[i];
   const int t = (u - it.raster_pre[i]) * kRasterPerUnit + threadIdx.x;
   const int W = it.cam.W, H = it.cam.H;
   unsigned long long* vis = it.vis + (size_t)i * W * H;
-  if (threadIdx.x == 0) s_nlarge = 0;
-  __syncthreads();
+  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
   unsigned front = 0, back = 0, nearc = 0, guard = 0, large = 0, bad = 0;
+  int npx = 0;
+  TriS r;
+  TriPos pos;
   if (t < s.nt) {
     Tri T;
     int idx[3];
@@ -91,11 +137,29 @@ __device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* 
       const int bw = T.xhi - T.xlo + 1, bh = T.yhi - T.ylo + 1;
       if (bw > 0 && bh > 0) {
         if (bw * bh <= kSmallMaxPixels) {
-          for (int y = T.ylo; y <= T.yhi; ++y)
-            for (int x = T.xlo; x <= T.xhi; ++x) raster_pixel(T, t, x, y, W, vis);
+          npx = bw * bh;
+          const int ox = 256 * T.xlo + 128, oy = 256 * T.ylo + 128;
+          int S = 0;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const int a = (j + 2) % 3, b = (j + 1) % 3;
+            const int ax = T.X[a] - ox, ay = T.Y[a] - oy;
+            const int ex = T.X[b] - T.X[a], ey = T.Y[b] - T.Y[a];
+            r.c[j] = ex * (0 - ay) - ey * (0 - ax);
+            r.gx[j] = -ey * 256;
+            r.gy[j] = ex * 256;
+            r.q[j] = T.q[j];
+            S += r.c[j];
+          }
+          // S = e_0 + e_1 + e_2 is the same at every point
+          r.tl_bw = T.tl[0] | (T.tl[1] << 1) | (T.tl[2] << 2) | (bw << 8);
+          r.rbw = 1.0f / (float)bw;
+          r.rS = 1.0f / (float)S;
+          r.t = t;
+          pos.xlo = T.xlo;
+          pos.ylo = T.ylo;
         } else {
           large = 1;
-          s_large[atomicAdd(&s_nlarge, 1)] = t;
         }
       }
     } else if (why == 1) back = 1;
@@ -103,23 +167,65 @@ __device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* 
     else if (why == 3) guard = 1;
     else bad = 1;
   }
+  // compact the non-empty boxes and take the exclusive prefix of their sizes
+  const unsigned ne = __ballot_sync(FULL, npx > 0);
+  int pre = npx;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(FULL, pre, o);
+    if (lane >= o) pre += v;
+  }
+  const int total = __shfl_sync(FULL, pre, 31);
+  const int start = pre - npx;
+  if (npx > 0) {
+    const int cpos = __popc(ne & ((1u << lane) - 1u));
+    s_tri[wbase + cpos] = r;
+    s_pos[wbase + cpos] = pos;
+    s_start[wbase + cpos] = start;
+  }
+  __syncwarp();
+  const unsigned le = (lane == 31) ? FULL : ((2u << lane) - 1u);
+  int carry = 0;
+  for (int w0 = 0; w0 < total; w0 += 32) {
+    const unsigned b = (npx > 0 && start >= w0 && start < w0 + 32) ? (1u << (start - w0)) : 0u;
+    const unsigned bits = __reduce_or_sync(FULL, b);
+    const int slot = w0 + lane;
+    if (slot < total) {
+      const int o = carry + __popc(bits & le) - 1;
+      const TriS& q = s_tri[wbase + o];
+      const int local = slot - s_start[wbase + o];
+      const int bwq = q.tl_bw >> 8;
+      const int dy = (int)(((float)local + 0.5f) * q.rbw);
+      const int dx = local - dy * bwq;
+      int e[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) e[j] = q.c[j] + q.gx[j] * dx + q.gy[j] * dy;
+      if ((e[0] + (q.tl_bw & 1) > 0) && (e[1] + ((q.tl_bw >> 1) & 1) > 0) && (e[2] + ((q.tl_bw >> 2) & 1) > 0)) {
+        const TriPos p = s_pos[wbase + o];
+        const int S = e[0] + e[1] + e[2];
+        red_max_u64(vis + (size_t)(p.ylo + dy) * W + (p.xlo + dx), vis_key(depth_key32(q.q, e, S, q.rS), q.t));
+      }
+    }
+    carry += __popc(bits);
+  }
   warp_count(&hdr->front, front);
   warp_count(&hdr->back, back);
   warp_count(&hdr->nearc, nearc);
   warp_count(&hdr->guard, guard);
   warp_count(&hdr->large, large);
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) record_error(hdr, VS_ERR_INVALID_ARG);
-  __syncthreads();
-  // large triangles: the whole block strides over each one's screen box
-  const int nl = s_nlarge;
-  for (int q = 0; q < nl; ++q) {
-    const int tq = s_large[q];
+  if (__any_sync(FULL, bad) && lane == 0) record_error(hdr, VS_ERR_INVALID_ARG);
+  // large boxes: the warp strides over each one's screen box
+  unsigned lm = __ballot_sync(FULL, large);
+  while (lm) {
+    const int l = __ffs(lm) - 1;
+    lm &= lm - 1;
+    const int tq = __shfl_sync(FULL, t, l);
     Tri T;
     int idx[3];
     if (load_tri(s, it.cam, tq, T, idx) != 0) continue;
     const int bw = T.xhi - T.xlo + 1, bh = T.yhi - T.ylo + 1;
-    const int npx = bw * bh;
-    for (int p = threadIdx.x; p < npx; p += blockDim.x) {
+    const int npq = bw * bh;
+    for (int p = lane; p < npq; p += 32) {
       const int yy = p / bw;
       raster_pixel(T, tq, T.xlo + (p - yy * bw), T.ylo + yy, W, vis);
     }
@@ -129,6 +235,28 @@ __device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* 
 // ----------------------------------------------------------------------------
 // SHADE (+ adjoint)
 // ----------------------------------------------------------------------------
+// The part of triangle setup shading needs: snapped positions and 1/w,
+// after the same validity checks as the raster (0 = usable).
+__device__ __forceinline__ int load_tri_shade(const DShell& s, int t, Tri& T, int idx[3]) {
+  const int* ip = s.tris + 3 * (size_t)t;
+  idx[0] = __ldg(ip);
+  idx[1] = __ldg(ip + 1);
+  idx[2] = __ldg(ip + 2);
+  if ((unsigned)idx[0] >= (unsigned)s.nv || (unsigned)idx[1] >= (unsigned)s.nv || (unsigned)idx[2] >= (unsigned)s.nv)
+    return 4;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int4 v = __ldcg(s.vsetup + idx[j]);
+    if (v.x == kInvalidX) return 2;
+    T.X[j] = v.x;
+    T.Y[j] = v.y;
+    T.iw[j] = __int_as_float(v.z);
+  }
+  const long long a2 = (long long)(T.X[1] - T.X[0]) * (T.Y[2] - T.Y[0]) -
+                       (long long)(T.X[2] - T.X[0]) * (T.Y[1] - T.Y[0]);
+  return a2 < 0 ? 0 : 1;
+}
+
 template <int DEG, int VEC>
 __device__ __forceinline__ Frag fetch_sh(const DShell& s, const Footprint& f, const float3 v) {
   constexpr int NCH = 1 + 3 * (DEG + 1) * (DEG + 1);
@@ -236,7 +364,7 @@ __device__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* h
       const DShell& s = sh[i];
       Tri Tr;
       int idx[3];
-      if (tri >= s.nt || load_tri(s, it.cam, tri, Tr, idx) != 0) {
+      if (tri >= s.nt || load_tri_shade(s, tri, Tr, idx) != 0) {
         bad = 1;
       } else {
         const int y = p / W, x = p - y * W;
