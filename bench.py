@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--views", type=int, default=100)
     p.add_argument("--scale", type=float, default=1.0, help="shrink the workload (testing only)")
+    p.add_argument("--pitch", type=int, default=32,
+                   help="FP16 values per texel in memory (28 used; 32 = 64-byte texels)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     return p.parse_args()
@@ -120,7 +122,7 @@ def build_workload(args, device):
     import torch
     import synth
     import paper_2409_02482_gb300 as vs
-    (scene, cams), = synth.config_scene("c2", scale=args.scale, views=args.views)
+    (scene, cams), = synth.config_scene("c2", scale=args.scale, views=args.views, pitch=args.pitch)
     ctx = vs.Context(device.index or 0)
     obj = vs.ShellObject.from_scene(ctx, scene, device=device)
     H, W = cams[0].height, cams[0].width

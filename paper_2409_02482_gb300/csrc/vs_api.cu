@@ -21,7 +21,7 @@ using namespace vsd;
 struct vs_ctx {
   int device;
   int num_sms;
-  int persist_blocks_per_sm[2];   // forward-only, forward + backward
+  int persist_blocks[2][VS_MAX_SHELLS + 1];   // [backward][most shells] blocks per SM
 };
 
 struct vs_object {
@@ -62,7 +62,7 @@ int gcd_pow2(uint64_t a, int cap) {  // largest power of two <= cap dividing a
 vs_status check_shell(const vs_shell_desc& s, int i) {
   if (!s.pos || !s.uv || !s.tris || !s.texels) return fail(VS_ERR_INVALID_ARG, "shell %d: NULL array", i);
   if (s.num_verts < 3 || s.num_verts > (1 << 30)) return fail(VS_ERR_INVALID_ARG, "shell %d: num_verts %d out of [3, 2^30]", i, s.num_verts);
-  if (s.num_tris < 1 || s.num_tris > 0x7FFFFFFE) return fail(VS_ERR_INVALID_ARG, "shell %d: num_tris %d out of range", i, s.num_tris);
+  if (s.num_tris < 1 || s.num_tris >= kMaxTris) return fail(VS_ERR_INVALID_ARG, "shell %d: num_tris %d out of [1, 2^27)", i, s.num_tris);
   if (s.tex_w < 1 || s.tex_h < 1 || s.tex_w > 65536 || s.tex_h > 65536)
     return fail(VS_ERR_INVALID_ARG, "shell %d: texture %dx%d out of [1, 65536]", i, s.tex_w, s.tex_h);
   if (s.format != VS_TEX_RGBA_F32 && s.format != VS_TEX_SH_F16) return fail(VS_ERR_INVALID_ARG, "shell %d: unknown format %d", i, s.format);
@@ -145,9 +145,6 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
     it.bg[0] = bg ? bg[0] : 0.f; it.bg[1] = bg ? bg[1] : 0.f; it.bg[2] = bg ? bg[2] : 0.f;
     it.maxdeg = -1;
     const size_t HW = (size_t)c.width * c.height;
-    int ls = 0;
-    while ((1 << ls) < o.k) ++ls;
-    it.lane_shift = ls;
     it.setup_pre[0] = 0;
     it.raster_pre[0] = 0;
     for (int i = 0; i < o.k; ++i) {
@@ -179,8 +176,7 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
     it.clear_units = clear_vis ? (int)((vis_words + kClearPerUnit - 1) / kClearPerUnit) : 0;
     it.units[PH_SETUP] = it.clear_units + it.setup_pre[o.k];
     it.units[PH_RASTER] = clear_vis ? it.raster_pre[o.k] : 0;
-    const size_t slots = HW << ls;
-    it.units[PH_SHADE] = (int)((slots + kShadeSlots - 1) / kShadeSlots);
+    it.units[PH_SHADE] = (int)((HW + kShadePixels - 1) / kShadePixels);
     sidx += o.k;
   }
   P.total = align256(off);
@@ -208,6 +204,8 @@ TableRef table_ref(const Plan& P, char* ws) {
   t.stage_pre = reinterpret_cast<const int*>(ws + P.off_stage);
   t.n = (int)P.items.size();
   t.total = P.total_units;
+  t.kmax = 1;
+  for (const DItem& it : P.items) t.kmax = std::max(t.kmax, (int)it.k);
   return t;
 }
 
@@ -283,13 +281,18 @@ vs_status vs_create(vs_ctx** ctx, int device) {
     delete c;
     return cuda_fail(e, "cudaDeviceGetAttribute");
   }
-  for (int b = 0; b < 2; ++b) {
-    if ((e = vsk::persistent_occupancy(b == 1, &c->persist_blocks_per_sm[b])) != cudaSuccess) {
-      delete c;
-      return cuda_fail(e, "occupancy query");
-    }
-    if (c->persist_blocks_per_sm[b] < 1) c->persist_blocks_per_sm[b] = 1;
+  if ((e = vsk::configure_kernels()) != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "kernel configuration");
   }
+  for (int b = 0; b < 2; ++b)
+    for (int K = 1; K <= VS_MAX_SHELLS; ++K) {
+      if ((e = vsk::persistent_occupancy(b == 1, K, &c->persist_blocks[b][K])) != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "occupancy query");
+      }
+      if (c->persist_blocks[b][K] < 1) c->persist_blocks[b][K] = 1;
+    }
   *ctx = c;
   g_err.clear();
   return VS_OK;
@@ -404,7 +407,9 @@ vs_status vs_render_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, co
   if ((s = set_device(ctx)) != VS_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if ((s = upload_table(P, ws, 1, st)) != VS_OK) return s;
-  const int grid = ctx->num_sms * ctx->persist_blocks_per_sm[do_backward ? 1 : 0];
+  int kmax = 1;
+  for (int j = 0; j < n; ++j) kmax = std::max(kmax, (int)items[j].obj->k);
+  const int grid = ctx->num_sms * ctx->persist_blocks[do_backward ? 1 : 0][kmax];
   const long long spin_limit = 1ll << 24;   // ~ seconds with 200 ns sleeps
   cudaError_t e = vsk::persistent(table_ref(P, ws), do_backward != 0, grid, spin_limit, st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_batch launch");

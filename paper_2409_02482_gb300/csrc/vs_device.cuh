@@ -22,9 +22,23 @@ constexpr int kThreads = 256;          // threads per block, all kernels
 constexpr int kSetupPerUnit = 1024;    // vertices per setup unit
 constexpr int kRasterPerUnit = 256;    // triangles per raster unit (1 / thread)
 constexpr int kClearPerUnit = 65536;   // visibility words cleared per unit
-constexpr int kShadeSlots = 2048;      // (pixel, shell-lane) slots per shading unit
+constexpr int kShadePixels = 256;      // pixels per shading unit (32 per warp)
 constexpr int kSmallMaxPixels = 64;    // bbox pixels one thread rasterizes
 constexpr int kMaxShells = VS_MAX_SHELLS;
+
+constexpr int kTriBits = 27;           // triangle index bits in a packed fragment
+constexpr int kMaxTris = 1 << kTriBits;
+
+// Dynamic shared memory of a shading warp for up to K shells: N = 32 K
+// fragments; [frag float4 N][T, B float2 N][g float4 32][entry int N][lane u8 N].
+__host__ __device__ constexpr size_t shade_warp_bytes(int K) {
+  return (29 * (size_t)(32 * K) + 512 + 15) & ~(size_t)15;
+}
+constexpr size_t kRasterSmemBytes = 256 * (64 + 8 + 4);   // TriS, TriPos, start per triangle
+__host__ __device__ constexpr size_t block_smem_bytes(int K) {
+  return shade_warp_bytes(K) * (kThreads / 32) > kRasterSmemBytes ? shade_warp_bytes(K) * (kThreads / 32)
+                                                                   : kRasterSmemBytes;
+}
 
 // Phases of one item.  Large triangles are rasterized by the whole block
 // inside the raster unit that met them.
@@ -64,7 +78,7 @@ struct alignas(16) DItem {
   unsigned long long* vis;     // [k, H*W] -- workspace
   int32_t k, shell0, maxdeg, clear_units;
   int32_t flags, do_bwd, stall;
-  int32_t lane_shift;          // log2 of the lanes per pixel (>= k)
+  int32_t pad1;
   int32_t units[4];            // per phase (3 used)
   int32_t setup_pre[kMaxShells + 1];
   int32_t raster_pre[kMaxShells + 1];

@@ -7,22 +7,29 @@
 // fixed order and blend in the frame buffer) and of its texture fitting
 // (Sec. 3 "Texturing Meshes"):
 //   SETUP  clear the per-shell visibility words; transform + snap vertices
-//   RASTER one thread per triangle: cull, edge functions, exact depth key,
-//          64-bit atomicMax (key << 32 | ~triangle) per (shell, pixel) --
+//   RASTER per triangle: cull, integer edge functions, exact depth key,
+//          64-bit max-reduction (key << 32 | ~triangle) per (shell, pixel) --
 //          the nearest hit of each shell, ties to the lower triangle
-//          (Fig. 3c); triangles with large screen boxes are rasterized by
-//          the whole block afterwards
-//   SHADE  one lane per (pixel, shell): perspective-correct UV, bilinear
+//          (Fig. 3c); each warp walks the pixels of its triangles' boxes
+//          together, larger boxes one triangle at a time
+//   SHADE  per warp of 32 pixels: compact the hits into a fragment list,
+//          shade it 32 fragments at a time (perspective-correct UV, bilinear
 //          fetch at texel centres (Fig. 5), SH decode with the ray
-//          direction; the lanes of a pixel then composite front to back
-//          with a segmented warp scan (Eq. 6 with Eq. 1's transmittance)
-//          and, for the adjoint, a segmented suffix scan of the colour
-//          seen behind each shell.
+//          direction), composite each pixel front to back (Eq. 6 with
+//          Eq. 1's transmittance) and, for the adjoint, scatter the texel
+//          gradients 32 fragments at a time.
 
 #include <cuda_runtime.h>
 
 #include "vs_device.cuh"
 #include "vs_kernels.h"
+
+#ifndef VS_BWD_BLOCKS
+#define VS_BWD_BLOCKS 3   // resident 256-thread blocks per SM for kernels with the adjoint
+#endif
+#ifndef VS_FWD_BLOCKS
+#define VS_FWD_BLOCKS 3   // ... and for forward-only kernels
+#endif
 
 namespace vsd {
 
@@ -112,10 +119,10 @@ __device__ __forceinline__ unsigned depth_key32(const unsigned q[3], const int e
 // start bits tells every lane which triangle owns its pair, so lanes do not
 // idle on small or culled boxes.  Larger boxes are rasterized by the whole
 // warp, one triangle at a time.
-__device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* hdr) {
-  __shared__ TriS s_tri[kRasterPerUnit];
-  __shared__ TriPos s_pos[kRasterPerUnit];
-  __shared__ int s_start[kRasterPerUnit];
+__device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* smem) {
+  TriS* s_tri = reinterpret_cast<TriS*>(smem);
+  TriPos* s_pos = reinterpret_cast<TriPos*>(smem + sizeof(TriS) * kRasterPerUnit);
+  int* s_start = reinterpret_cast<int*>(smem + (sizeof(TriS) + sizeof(TriPos)) * kRasterPerUnit);
   const unsigned FULL = 0xffffffffu;
   int i = 0;
   while (i + 1 < it.k && u >= it.raster_pre[i + 1]) ++i;
@@ -326,118 +333,193 @@ __device__ __forceinline__ void adjoint_frag(const DShell& s, const Footprint& f
 #undef VS_CASE
 }
 
-// Shading unit: kShadeSlots (pixel, lane) slots; L = 2^lane_shift lanes per
-// pixel, lane i handles shell i (lanes >= k idle but join the scans).
+// Shading unit: kShadePixels pixels, 32 per warp (lane = pixel).
+//  1. each lane reads its pixel's k visibility words (independent loads)
+//     and the warp compacts the hits into a fragment list in shared memory,
+//     pixel-major with shells ascending;
+//  2. the warp shades the list 32 fragments at a time, every lane busy:
+//     perspective-correct UV, bilinear fetch at texel centres (Fig. 5), SH
+//     decode with the ray direction;
+//  3. each lane composites its pixel front to back from shared memory
+//     (Eq. 6 with Eq. 1's transmittance); for the adjoint it also runs the
+//     back-to-front recurrence of B_i = A_i . g, A_i the colour seen from in
+//     front of shell i (B_i = alpha_i (c_i . g) + (1 - alpha_i) B_{i+1},
+//     B_k = bg . g);
+//  4. (adjoint) the warp scatters dL/d(texel) 32 fragments at a time:
+//     dL/dc_i = T_i alpha_i g, dL/dalpha_i = T_i (c_i . g - B_{i+1}).
 // FROM_HITS: hits come from the public int32 buffer (standalone backward)
 // instead of the visibility words.
 template <bool BWD, bool FROM_HITS>
-__device__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* hdr) {
+__device__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* smem, int K) {
   const unsigned FULL = 0xffffffffu;
   const int W = it.cam.W, H = it.cam.H;
   const int HW = W * H;
-  const int ls = it.lane_shift;
-  const int L = 1 << ls;
-  const int i = threadIdx.x & (L - 1);            // shell of this lane
-  const int ppass = kThreads >> ls;               // pixels per pass
-  const int npass = kShadeSlots / kThreads;
-  const int pix0 = u * (kShadeSlots >> ls);
-  unsigned nfrag = 0, bad = 0;
-  float loss = 0.0f;
-  for (int pass = 0; pass < npass; ++pass) {
-    const int p = pix0 + pass * ppass + (threadIdx.x >> ls);
-    const bool pix_ok = p < HW;
-    const bool act = pix_ok && i < it.k;
-    int tri = -1;
-    if (act) {
-      if (FROM_HITS) {
-        tri = __ldg(it.hits + (size_t)i * HW + p);
-      } else {
-        tri = vis_tri(__ldcg(it.vis + (size_t)i * HW + p));
-        if (it.hits) it.hits[(size_t)i * HW + p] = tri;
+  const int k = it.k;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int N = 32 * K;
+  char* wb = smem + (size_t)warp * shade_warp_bytes(K);
+  float4* sfrag = reinterpret_cast<float4*>(wb);
+  float2* stb = reinterpret_cast<float2*>(wb + 16 * (size_t)N);
+  float4* sg = reinterpret_cast<float4*>(wb + 24 * (size_t)N);
+  int* sent = reinterpret_cast<int*>(wb + 24 * (size_t)N + 512);
+  unsigned char* spl = reinterpret_cast<unsigned char*>(wb + 28 * (size_t)N + 512);
+  const int pbase = u * kShadePixels + warp * 32;
+  const int p = pbase + lane;
+  const bool pix_ok = p < HW;
+
+  // 1. hits of this pixel (triangle ids parked in the fragment area, which
+  //    step 2 overwrites only after the list is built)
+  int* scratch = reinterpret_cast<int*>(sfrag);
+  unsigned mask = 0;
+  // eight shells at a time: all loads of a group are in flight together
+  for (int i0 = 0; i0 < k; i0 += 8) {
+    int tt[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const int i = i0 + d;
+      tt[d] = -1;
+      if (i < k && pix_ok) {
+        if (FROM_HITS) tt[d] = __ldg(it.hits + (size_t)i * HW + p);
+        else tt[d] = vis_tri(__ldcg(it.vis + (size_t)i * HW + p));
       }
     }
-    Frag fr = {0.f, 0.f, 0.f, 0.f};
-    Footprint f;
-    float3 v = make_float3(0.f, 0.f, 1.f);
-    bool hit = false;
-    if (tri >= 0) {
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const int i = i0 + d;
+      if (i < k) {
+        if (!FROM_HITS && it.hits && pix_ok) it.hits[(size_t)i * HW + p] = tt[d];
+        scratch[i * 32 + lane] = tt[d];
+        if (tt[d] >= 0) mask |= 1u << i;
+      }
+    }
+  }
+  const int cnt = __popc(mask);
+  int pre = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(FULL, pre, o);
+    if (lane >= o) pre += v;
+  }
+  const int total = __shfl_sync(FULL, pre, 31);
+  const int start = pre - cnt;
+  {
+    unsigned m = mask;
+    int c = start;
+    while (m) {
+      const int i = __ffs(m) - 1;
+      m &= m - 1;
+      sent[c] = (i << kTriBits) | (scratch[i * 32 + lane] & (kMaxTris - 1));
+      spl[c] = (unsigned char)lane;
+      ++c;
+    }
+  }
+  __syncwarp();
+
+  // 2. fragments, 32 at a time
+  unsigned nfrag = 0, bad = 0;
+  for (int j0 = 0; j0 < total; j0 += 32) {
+    const int j = j0 + lane;
+    if (j < total) {
+      const int e = sent[j];
+      const int i = e >> kTriBits, t = e & (kMaxTris - 1);
+      const int pp = pbase + spl[j];
       const DShell& s = sh[i];
+      Frag fr = {0.f, 0.f, 0.f, 0.f};
       Tri Tr;
       int idx[3];
-      if (tri >= s.nt || load_tri_shade(s, tri, Tr, idx) != 0) {
+      if (t >= s.nt || load_tri_shade(s, t, Tr, idx) != 0) {
         bad = 1;
       } else {
-        const int y = p / W, x = p - y * W;
+        const int y = pp / W, x = pp - y * W;
         const float2 uv[3] = {__ldg(s.uv + idx[0]), __ldg(s.uv + idx[1]), __ldg(s.uv + idx[2])};
-        f = footprint(Tr, uv, s.tw, s.th, 256 * x + 128, 256 * y + 128);
+        const Footprint f = footprint(Tr, uv, s.tw, s.th, 256 * x + 128, 256 * y + 128);
+        float3 v = make_float3(0.f, 0.f, 1.f);
         if (s.fmt == VS_TEX_SH_F16) v = ray_dir(it.cam, x, y);
         fr = fetch_frag(s, f, v);
-        hit = true;
         ++nfrag;
       }
+      sfrag[j] = make_float4(fr.r, fr.g, fr.b, fr.a);
     }
-    // front-to-back over across the lanes of the pixel:
-    // T_i = prod_{j<i} (1 - a_j) by a segmented exclusive product scan
-    float incl = 1.0f - fr.a;
-    for (int o = 1; o < L; o <<= 1) {
-      const float v = __shfl_up_sync(FULL, incl, o, L);
-      if (i >= o) incl *= v;
+  }
+  __syncwarp();
+
+  // 3. composite this pixel
+  float T = 1.0f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
+  for (int c = 0; c < cnt; ++c) {
+    const float4 f = sfrag[start + c];
+    if constexpr (BWD) stb[start + c].x = T;
+    const float ta = T * f.w;
+    Cr = fmaf(ta, f.x, Cr);
+    Cg = fmaf(ta, f.y, Cg);
+    Cb = fmaf(ta, f.z, Cb);
+    T = T * (1.0f - f.w);
+  }
+  const float outr = fmaf(T, it.bg[0], Cr), outg = fmaf(T, it.bg[1], Cg), outb = fmaf(T, it.bg[2], Cb);
+  if (pix_ok && it.out) it.out[p] = make_float4(outr, outg, outb, 1.0f - T);
+  float loss = 0.0f;
+  if constexpr (BWD) {
+    float gr = 0.f, gg = 0.f, gb = 0.f;
+    if (pix_ok) {
+      const float* gp = it.grad_rgb + 3 * (size_t)p;
+      gr = __ldg(gp);
+      gg = __ldg(gp + 1);
+      gb = __ldg(gp + 2);
+      if (it.flags & VS_FLAG_LOSS_L2) {
+        const float dr = outr - gr, dg = outg - gg, db = outb - gb;
+        const float inv = 1.0f / (3.0f * (float)HW);
+        loss = (dr * dr + dg * dg + db * db) * inv;
+        gr = 2.0f * inv * dr;
+        gg = 2.0f * inv * dg;
+        gb = 2.0f * inv * db;
+      }
     }
-    float Ti = __shfl_up_sync(FULL, incl, 1, L);
-    if (i == 0) Ti = 1.0f;
-    const float Tk = __shfl_sync(FULL, incl, L - 1, L);
-    const float ta = Ti * fr.a;
-    float cr = ta * fr.r, cg = ta * fr.g, cb = ta * fr.b;
-    for (int o = L >> 1; o > 0; o >>= 1) {
-      cr += __shfl_xor_sync(FULL, cr, o, L);
-      cg += __shfl_xor_sync(FULL, cg, o, L);
-      cb += __shfl_xor_sync(FULL, cb, o, L);
+    float B = it.bg[0] * gr + it.bg[1] * gg + it.bg[2] * gb;
+    for (int c = cnt - 1; c >= 0; --c) {
+      stb[start + c].y = B;
+      const float4 f = sfrag[start + c];
+      B = fmaf(f.w, f.x * gr + f.y * gg + f.z * gb - B, B);
     }
-    const float outr = fmaf(Tk, it.bg[0], cr), outg = fmaf(Tk, it.bg[1], cg), outb = fmaf(Tk, it.bg[2], cb);
-    if (i == 0 && pix_ok && it.out) it.out[p] = make_float4(outr, outg, outb, 1.0f - Tk);
-    if constexpr (BWD) {
-      float gr = 0.f, gg = 0.f, gb = 0.f;
-      if (pix_ok) {
-        const float* gp = it.grad_rgb + 3 * (size_t)p;
-        gr = __ldg(gp);
-        gg = __ldg(gp + 1);
-        gb = __ldg(gp + 2);
-        if (it.flags & VS_FLAG_LOSS_L2) {
-          const float dr = outr - gr, dg = outg - gg, db = outb - gb;
-          const float inv = 1.0f / (3.0f * (float)HW);
-          if (i == 0) loss += (dr * dr + dg * dg + db * db) * inv;
-          gr = 2.0f * inv * dr;
-          gg = 2.0f * inv * dg;
-          gb = 2.0f * inv * db;
+    sg[lane] = make_float4(gr, gg, gb, 0.0f);
+    __syncwarp();
+
+    // 4. adjoint, 32 fragments at a time
+    for (int j0 = 0; j0 < total; j0 += 32) {
+      const int j = j0 + lane;
+      if (j < total) {
+        const int e = sent[j];
+        const int i = e >> kTriBits, t = e & (kMaxTris - 1);
+        const int pl = spl[j];
+        const int pp = pbase + pl;
+        const DShell& s = sh[i];
+        Tri Tr;
+        int idx[3];
+        if (t < s.nt && load_tri_shade(s, t, Tr, idx) == 0) {
+          const int y = pp / W, x = pp - y * W;
+          const float2 uv[3] = {__ldg(s.uv + idx[0]), __ldg(s.uv + idx[1]), __ldg(s.uv + idx[2])};
+          const Footprint f = footprint(Tr, uv, s.tw, s.th, 256 * x + 128, 256 * y + 128);
+          float3 v = make_float3(0.f, 0.f, 1.f);
+          if (s.fmt == VS_TEX_SH_F16) v = ray_dir(it.cam, x, y);
+          const float4 q = sfrag[j];
+          const Frag fr = {q.x, q.y, q.z, q.w};
+          const float2 tbv = stb[j];
+          const float4 g = sg[pl];
+          const float ta = tbv.x * fr.a;
+          const float ga = tbv.x * (fr.r * g.x + fr.g * g.y + fr.b * g.z - tbv.y);
+          adjoint_frag(s, f, v, fr, ta * g.x, ta * g.y, ta * g.z, ga);
         }
       }
-      // B_i = A_i . g with A_i the colour seen from in front of shell i:
-      // B_i = a_i + b_i B_{i+1}, a_i = alpha_i (c_i . g), b_i = 1 - alpha_i,
-      // B_k = bg . g; segmented suffix composition of the affine maps.
-      const float cgd = fr.r * gr + fr.g * gg + fr.b * gb;
-      float a = fr.a * cgd, b = 1.0f - fr.a;
-      for (int o = 1; o < L; o <<= 1) {
-        const float a2 = __shfl_down_sync(FULL, a, o, L), b2 = __shfl_down_sync(FULL, b, o, L);
-        if (i + o < L) {
-          a = fmaf(b, a2, a);
-          b = b * b2;
-        }
-      }
-      float an = __shfl_down_sync(FULL, a, 1, L), bn = __shfl_down_sync(FULL, b, 1, L);
-      if (i == L - 1) { an = 0.0f; bn = 1.0f; }
-      const float Bnext = fmaf(bn, it.bg[0] * gr + it.bg[1] * gg + it.bg[2] * gb, an);
-      if (hit) adjoint_frag(sh[i], f, v, fr, ta * gr, ta * gg, ta * gb, Ti * (cgd - Bnext));
     }
   }
   if (!FROM_HITS) warp_count(&hdr->frags, nfrag);
-  if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) record_error(hdr, VS_ERR_INVALID_ARG);
+  if (__any_sync(FULL, bad) && lane == 0) record_error(hdr, VS_ERR_INVALID_ARG);
   if constexpr (BWD) {
     if (it.loss && (it.flags & VS_FLAG_LOSS_L2)) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(FULL, loss, o);
-      if ((threadIdx.x & 31) == 0 && loss != 0.0f) atomicAdd(it.loss, loss);
+      if (lane == 0 && loss != 0.0f) atomicAdd(it.loss, loss);
     }
   }
+  __syncwarp();
 }
 
 // ----------------------------------------------------------------------------
@@ -459,15 +541,17 @@ __global__ void __launch_bounds__(kThreads) k_setup(TableRef tb, int item) {
   unit_setup(it, tb.shells + it.shell0, blockIdx.x);
 }
 
+extern __shared__ __align__(16) char vs_smem[];
+
 __global__ void __launch_bounds__(kThreads) k_raster(TableRef tb, int item) {
   const DItem& it = tb.items[item];
-  unit_raster(it, tb.shells + it.shell0, blockIdx.x, tb.hdr);
+  unit_raster(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, vs_smem);
 }
 
 template <bool BWD, bool FROM_HITS>
-__global__ void __launch_bounds__(kThreads, BWD ? 2 : 4) k_shade(TableRef tb, int item) {
+__global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS) k_shade(TableRef tb, int item) {
   const DItem& it = tb.items[item];
-  unit_shade<BWD, FROM_HITS>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr);
+  unit_shade<BWD, FROM_HITS>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, vs_smem, tb.kmax);
 }
 
 // Bounded wait (one thread) for `target` completions; false on timeout or
@@ -494,7 +578,7 @@ __device__ bool wait_done(const int* ctr, int target, long long limit, WsHeader*
 // all dispensed in an earlier stage to blocks that are already running, so
 // the wait always ends (and is bounded anyway).
 template <bool BWD>
-__global__ void __launch_bounds__(kThreads, BWD ? 2 : 4) k_persistent(TableRef tb, long long spin_limit) {
+__global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS) k_persistent(TableRef tb, long long spin_limit) {
   __shared__ int s_unit, s_ok;
   WsHeader* hdr = tb.hdr;
   for (;;) {
@@ -535,9 +619,9 @@ __global__ void __launch_bounds__(kThreads, BWD ? 2 : 4) k_persistent(TableRef t
     const DShell* sh = tb.shells + it.shell0;
     switch (ph) {
       case PH_SETUP: unit_setup(it, sh, u); break;
-      case PH_RASTER: unit_raster(it, sh, u, hdr); break;
+      case PH_RASTER: unit_raster(it, sh, u, hdr, vs_smem); break;
       default:
-        unit_shade<BWD, false>(it, sh, u, hdr);
+        unit_shade<BWD, false>(it, sh, u, hdr, vs_smem, tb.kmax);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -564,26 +648,40 @@ int plain_backward_launches(const int units[4]) { return (units[0] > 0) + (units
 
 cudaError_t plain_forward(const TableRef& tb, const int units[4], cudaStream_t st) {
   if (units[0]) vsd::k_setup<<<units[0], vsd::kThreads, 0, st>>>(tb, 0);
-  if (units[1]) vsd::k_raster<<<units[1], vsd::kThreads, 0, st>>>(tb, 0);
-  if (units[2]) vsd::k_shade<false, false><<<units[2], vsd::kThreads, 0, st>>>(tb, 0);
+  if (units[1]) vsd::k_raster<<<units[1], vsd::kThreads, vsd::kRasterSmemBytes, st>>>(tb, 0);
+  if (units[2])
+    vsd::k_shade<false, false><<<units[2], vsd::kThreads, vsd::block_smem_bytes(tb.kmax), st>>>(tb, 0);
   return cudaGetLastError();
 }
 
 cudaError_t plain_backward(const TableRef& tb, const int units[4], cudaStream_t st) {
   if (units[0]) vsd::k_setup<<<units[0], vsd::kThreads, 0, st>>>(tb, 0);
-  if (units[2]) vsd::k_shade<true, true><<<units[2], vsd::kThreads, 0, st>>>(tb, 0);
+  if (units[2])
+    vsd::k_shade<true, true><<<units[2], vsd::kThreads, vsd::block_smem_bytes(tb.kmax), st>>>(tb, 0);
   return cudaGetLastError();
 }
 
 cudaError_t persistent(const TableRef& tb, bool bwd, int grid, long long spin_limit, cudaStream_t st) {
-  if (bwd) vsd::k_persistent<true><<<grid, vsd::kThreads, 0, st>>>(tb, spin_limit);
-  else vsd::k_persistent<false><<<grid, vsd::kThreads, 0, st>>>(tb, spin_limit);
+  const size_t smem = vsd::block_smem_bytes(tb.kmax);
+  if (bwd) vsd::k_persistent<true><<<grid, vsd::kThreads, smem, st>>>(tb, spin_limit);
+  else vsd::k_persistent<false><<<grid, vsd::kThreads, smem, st>>>(tb, spin_limit);
   return cudaGetLastError();
 }
 
-cudaError_t persistent_occupancy(bool bwd, int* blocks_per_sm) {
-  if (bwd) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, vsd::k_persistent<true>, vsd::kThreads, 0);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, vsd::k_persistent<false>, vsd::kThreads, 0);
+cudaError_t persistent_occupancy(bool bwd, int kmax, int* blocks_per_sm) {
+  const size_t smem = vsd::block_smem_bytes(kmax);
+  if (bwd) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, vsd::k_persistent<true>, vsd::kThreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, vsd::k_persistent<false>, vsd::kThreads, smem);
+}
+
+cudaError_t configure_kernels() {
+  const int most = (int)vsd::block_smem_bytes(vsd::kMaxShells);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(vsd::k_raster, cudaFuncAttributeMaxDynamicSharedMemorySize, most)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(vsd::k_shade<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(vsd::k_shade<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(vsd::k_persistent<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(vsd::k_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
 }
 
 }  // namespace vsk

@@ -19,6 +19,7 @@ struct TableRef {
   const int* stage_pre;     // [n + 3] first global unit of each stage (+ total)
   int n;
   int total;                // all units
+  int kmax;                 // most shells of any item (sizes shared memory)
 };
 
 // A slice of the host-built table carried to the device in kernel
@@ -39,5 +40,6 @@ int plain_backward_launches(const int units[4]);
 cudaError_t plain_forward(const TableRef& tb, const int units[4], cudaStream_t st);
 cudaError_t plain_backward(const TableRef& tb, const int units[4], cudaStream_t st);
 cudaError_t persistent(const TableRef& tb, bool bwd, int grid, long long spin_limit, cudaStream_t st);
-cudaError_t persistent_occupancy(bool bwd, int* blocks_per_sm);
+cudaError_t persistent_occupancy(bool bwd, int kmax, int* blocks_per_sm);
+cudaError_t configure_kernels();
 }  // namespace vsk

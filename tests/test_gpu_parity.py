@@ -264,7 +264,8 @@ def test_autograd_function(vs, ctx):
     out2, hits = vs.render(ctx, obj, cam, ws)
     ref = vs.render_backward(ctx, obj, cam, ws, hits, w)
     for t, r in zip(tex, ref):
-        assert torch.allclose(t.grad, r, rtol=1e-5, atol=1e-7)
+        # same kernel, same hits: only the order of the float atomics differs
+        assert (t.grad - r).abs().max().item() <= 1e-5 * r.abs().max().item()
 
 
 # ----------------------------------------------------------------------------
