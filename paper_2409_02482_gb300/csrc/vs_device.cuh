@@ -19,13 +19,13 @@ namespace vsd {
 // tuning constants and table layout
 // ----------------------------------------------------------------------------
 constexpr int kThreads = 256;          // threads per block, all kernels
+constexpr int kWarps = kThreads / 32;  // a work unit is run by one warp
 constexpr int kSetupPerUnit = 1024;    // vertices per setup unit
-constexpr int kRasterPerUnit = 256;    // triangles per raster unit (1 / thread)
-constexpr int kClearPerUnit = 65536;   // visibility words cleared per unit
-constexpr int kShadePixels = 256;      // pixels per shading unit (32 per warp)
-constexpr int kSmallMaxPixels = 64;    // bbox pixels one thread rasterizes
+constexpr int kRasterPerUnit = 256;    // triangles per raster unit (rounds of 32)
+constexpr int kClearPerUnit = 16384;   // visibility words cleared per unit
+constexpr int kShadePixels = 256;      // pixels per shading unit (rounds of 32)
+constexpr int kSmallMaxPixels = 64;    // bbox pixels walked by the warp's pair loop
 constexpr int kMaxShells = VS_MAX_SHELLS;
-
 constexpr int kTriBits = 27;           // triangle index bits in a packed fragment
 constexpr int kMaxTris = 1 << kTriBits;
 
@@ -34,11 +34,11 @@ constexpr int kMaxTris = 1 << kTriBits;
 __host__ __device__ constexpr size_t shade_warp_bytes(int K) {
   return (29 * (size_t)(32 * K) + 512 + 15) & ~(size_t)15;
 }
-constexpr size_t kRasterSmemBytes = 256 * (64 + 8 + 4);   // TriS, TriPos, start per triangle
-__host__ __device__ constexpr size_t block_smem_bytes(int K) {
-  return shade_warp_bytes(K) * (kThreads / 32) > kRasterSmemBytes ? shade_warp_bytes(K) * (kThreads / 32)
-                                                                   : kRasterSmemBytes;
+constexpr size_t kRasterWarpBytes = 32 * (64 + 8 + 4);   // TriS, TriPos, start per triangle
+__host__ __device__ constexpr size_t warp_slice_bytes(int K) {
+  return shade_warp_bytes(K) > kRasterWarpBytes ? shade_warp_bytes(K) : kRasterWarpBytes;
 }
+__host__ __device__ constexpr size_t block_smem_bytes(int K) { return warp_slice_bytes(K) * kWarps; }
 
 // Phases of one item.  Large triangles are rasterized by the whole block
 // inside the raster unit that met them.

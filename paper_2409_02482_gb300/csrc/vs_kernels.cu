@@ -36,6 +36,7 @@ namespace vsd {
 // ----------------------------------------------------------------------------
 // SETUP
 // ----------------------------------------------------------------------------
+// One warp per unit.
 __device__ void unit_setup(const DItem& it, const DShell* sh, int u) {
   if (u < it.clear_units) {
     const size_t total = (size_t)it.k * it.cam.W * it.cam.H;
@@ -43,8 +44,8 @@ __device__ void unit_setup(const DItem& it, const DShell* sh, int u) {
     const size_t end = min(total, beg + (size_t)kClearPerUnit);
     uint4* p = reinterpret_cast<uint4*>(it.vis + beg);
     const size_t n2 = (end - beg) >> 1;
-    for (size_t i = threadIdx.x; i < n2; i += blockDim.x) p[i] = make_uint4(0, 0, 0, 0);
-    if (((end - beg) & 1) && threadIdx.x == 0) it.vis[end - 1] = 0ull;
+    for (size_t i = threadIdx.x & 31; i < n2; i += 32) p[i] = make_uint4(0, 0, 0, 0);
+    if (((end - beg) & 1) && (threadIdx.x & 31) == 0) it.vis[end - 1] = 0ull;
     return;
   }
   u -= it.clear_units;
@@ -53,7 +54,7 @@ __device__ void unit_setup(const DItem& it, const DShell* sh, int u) {
   const DShell& s = sh[i];
   const int v0 = (u - it.setup_pre[i]) * kSetupPerUnit;
   const int v1 = min(v0 + kSetupPerUnit, s.nv);
-  for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) s.vsetup[v] = setup_vertex(s.pos + 3 * (size_t)v, it.cam);
+  for (int v = v0 + (threadIdx.x & 31); v < v1; v += 32) s.vsetup[v] = setup_vertex(s.pos + 3 * (size_t)v, it.cam);
 }
 
 // ----------------------------------------------------------------------------
@@ -113,24 +114,25 @@ __device__ __forceinline__ unsigned depth_key32(const unsigned q[3], const int e
   return Q;
 }
 
-// Raster unit: kRasterPerUnit triangles of one shell.  Each lane sets up one
-// triangle; then each warp walks all (triangle, box pixel) pairs of its 32
-// triangles together: window by window, a warp-wide OR of the triangles'
-// start bits tells every lane which triangle owns its pair, so lanes do not
-// idle on small or culled boxes.  Larger boxes are rasterized by the whole
-// warp, one triangle at a time.
-__device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* smem) {
+// One round of a raster unit: 32 triangles t0 + lane of one shell.  Each
+// lane sets up one triangle; then the warp walks all (triangle, box pixel)
+// pairs of the 32 triangles together: window by window, a warp-wide OR of
+// the triangles' start bits tells every lane which triangle owns its pair,
+// so lanes do not idle on small or culled boxes.  Larger boxes are
+// rasterized by the whole warp, one triangle at a time.
+struct RasterCounts {
+  unsigned front, back, nearc, guard, large, bad;
+};
+
+__device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, int t0, unsigned long long* vis,
+                                             char* smem, RasterCounts& rc) {
   TriS* s_tri = reinterpret_cast<TriS*>(smem);
-  TriPos* s_pos = reinterpret_cast<TriPos*>(smem + sizeof(TriS) * kRasterPerUnit);
-  int* s_start = reinterpret_cast<int*>(smem + (sizeof(TriS) + sizeof(TriPos)) * kRasterPerUnit);
+  TriPos* s_pos = reinterpret_cast<TriPos*>(smem + sizeof(TriS) * 32);
+  int* s_start = reinterpret_cast<int*>(smem + (sizeof(TriS) + sizeof(TriPos)) * 32);
   const unsigned FULL = 0xffffffffu;
-  int i = 0;
-  while (i + 1 < it.k && u >= it.raster_pre[i + 1]) ++i;
-  const DShell& s = sh[i];
-  const int t = (u - it.raster_pre[i]) * kRasterPerUnit + threadIdx.x;
-  const int W = it.cam.W, H = it.cam.H;
-  unsigned long long* vis = it.vis + (size_t)i * W * H;
-  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+  const int lane = threadIdx.x & 31, wbase = 0;
+  const int t = t0 + lane;
+  const int W = it.cam.W;
   unsigned front = 0, back = 0, nearc = 0, guard = 0, large = 0, bad = 0;
   int npx = 0;
   TriS r;
@@ -215,12 +217,12 @@ __device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* 
     }
     carry += __popc(bits);
   }
-  warp_count(&hdr->front, front);
-  warp_count(&hdr->back, back);
-  warp_count(&hdr->nearc, nearc);
-  warp_count(&hdr->guard, guard);
-  warp_count(&hdr->large, large);
-  if (__any_sync(FULL, bad) && lane == 0) record_error(hdr, VS_ERR_INVALID_ARG);
+  rc.front += front;
+  rc.back += back;
+  rc.nearc += nearc;
+  rc.guard += guard;
+  rc.large += large;
+  rc.bad |= bad;
   // large boxes: the warp strides over each one's screen box
   unsigned lm = __ballot_sync(FULL, large);
   while (lm) {
@@ -237,6 +239,27 @@ __device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* 
       raster_pixel(T, tq, T.xlo + (p - yy * bw), T.ylo + yy, W, vis);
     }
   }
+  __syncwarp();   // the records are reused by the next round
+}
+
+// Raster unit: kRasterPerUnit triangles of one shell in rounds of 32; this
+// warp runs rounds [r0, r1).
+__device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* smem, int r0 = 0,
+                            int r1 = kRasterPerUnit / 32) {
+  int i = 0;
+  while (i + 1 < it.k && u >= it.raster_pre[i + 1]) ++i;
+  const DShell& s = sh[i];
+  const int base = (u - it.raster_pre[i]) * kRasterPerUnit;
+  unsigned long long* vis = it.vis + (size_t)i * it.cam.W * it.cam.H;
+  RasterCounts rc = {0, 0, 0, 0, 0, 0};
+  const int rounds = min(r1, min(kRasterPerUnit, s.nt - base + 31) / 32);
+  for (int r = r0; r < rounds; ++r) raster_round(it, s, base + 32 * r, vis, smem, rc);
+  warp_count(&hdr->front, rc.front);
+  warp_count(&hdr->back, rc.back);
+  warp_count(&hdr->nearc, rc.nearc);
+  warp_count(&hdr->guard, rc.guard);
+  warp_count(&hdr->large, rc.large);
+  if (__any_sync(0xffffffffu, rc.bad) && (threadIdx.x & 31) == 0) record_error(hdr, VS_ERR_INVALID_ARG);
 }
 
 // ----------------------------------------------------------------------------
@@ -350,20 +373,19 @@ __device__ __forceinline__ void adjoint_frag(const DShell& s, const Footprint& f
 // FROM_HITS: hits come from the public int32 buffer (standalone backward)
 // instead of the visibility words.
 template <bool BWD, bool FROM_HITS>
-__device__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* smem, int K) {
+__device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, int pbase, char* wb, int K,
+                                            unsigned& nfrag, unsigned& bad, float& loss_acc) {
   const unsigned FULL = 0xffffffffu;
   const int W = it.cam.W, H = it.cam.H;
   const int HW = W * H;
   const int k = it.k;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int N = 32 * K;
-  char* wb = smem + (size_t)warp * shade_warp_bytes(K);
   float4* sfrag = reinterpret_cast<float4*>(wb);
   float2* stb = reinterpret_cast<float2*>(wb + 16 * (size_t)N);
   float4* sg = reinterpret_cast<float4*>(wb + 24 * (size_t)N);
   int* sent = reinterpret_cast<int*>(wb + 24 * (size_t)N + 512);
   unsigned char* spl = reinterpret_cast<unsigned char*>(wb + 28 * (size_t)N + 512);
-  const int pbase = u * kShadePixels + warp * 32;
   const int p = pbase + lane;
   const bool pix_ok = p < HW;
 
@@ -416,7 +438,6 @@ __device__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* h
   __syncwarp();
 
   // 2. fragments, 32 at a time
-  unsigned nfrag = 0, bad = 0;
   for (int j0 = 0; j0 < total; j0 += 32) {
     const int j = j0 + lane;
     if (j < total) {
@@ -510,6 +531,25 @@ __device__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* h
       }
     }
   }
+  loss_acc += loss;
+  __syncwarp();   // the fragment list is rebuilt by the next round
+}
+
+// Shading unit: kShadePixels consecutive pixels in rounds of 32; this warp
+// runs rounds [r0, r1).  `wb` is the warp's shared-memory slice.
+template <bool BWD, bool FROM_HITS>
+__device__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* wb, int K, int r0 = 0,
+                           int r1 = kShadePixels / 32) {
+  const unsigned FULL = 0xffffffffu;
+  const int HW = it.cam.W * it.cam.H;
+  unsigned nfrag = 0, bad = 0;
+  float loss = 0.0f;
+  for (int r = r0; r < r1; ++r) {
+    const int pbase = u * kShadePixels + 32 * r;
+    if (pbase >= HW) break;
+    shade_round<BWD, FROM_HITS>(it, sh, pbase, wb, K, nfrag, bad, loss);
+  }
+  const int lane = threadIdx.x & 31;
   if (!FROM_HITS) warp_count(&hdr->frags, nfrag);
   if (__any_sync(FULL, bad) && lane == 0) record_error(hdr, VS_ERR_INVALID_ARG);
   if constexpr (BWD) {
@@ -519,7 +559,6 @@ __device__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* h
       if (lane == 0 && loss != 0.0f) atomicAdd(it.loss, loss);
     }
   }
-  __syncwarp();
 }
 
 // ----------------------------------------------------------------------------
@@ -536,27 +575,38 @@ __global__ void __launch_bounds__(kThreads) k_upload(char* ws, const __grid_cons
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_setup(TableRef tb, int item) {
-  const DItem& it = tb.items[item];
-  unit_setup(it, tb.shells + it.shell0, blockIdx.x);
+extern __shared__ __align__(16) char vs_smem[];
+
+// Shared-memory slice of the calling warp (every phase carves the same way).
+__device__ __forceinline__ char* warp_smem(int K) {
+  return vs_smem + (threadIdx.x >> 5) * warp_slice_bytes(K);
 }
 
-extern __shared__ __align__(16) char vs_smem[];
+// Plain per-phase kernels.  Setup: each warp runs one unit (8 per block).
+// Raster and shade: block b runs unit b, its warp w runs round w of it --
+// the same arithmetic as the persistent kernel, spread over more warps.
+__global__ void __launch_bounds__(kThreads) k_setup(TableRef tb, int item) {
+  const DItem& it = tb.items[item];
+  const int u = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (u < it.units[PH_SETUP]) unit_setup(it, tb.shells + it.shell0, u);
+}
 
 __global__ void __launch_bounds__(kThreads) k_raster(TableRef tb, int item) {
   const DItem& it = tb.items[item];
-  unit_raster(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, vs_smem);
+  const int w = threadIdx.x >> 5;
+  unit_raster(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, warp_smem(tb.kmax), w, w + 1);
 }
 
 template <bool BWD, bool FROM_HITS>
 __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS) k_shade(TableRef tb, int item) {
   const DItem& it = tb.items[item];
-  unit_shade<BWD, FROM_HITS>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, vs_smem, tb.kmax);
+  const int w = threadIdx.x >> 5;
+  unit_shade<BWD, FROM_HITS>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, warp_smem(tb.kmax), tb.kmax, w, w + 1);
 }
 
-// Bounded wait (one thread) for `target` completions; false on timeout or
+// Bounded wait (one lane) for `target` completions; false on timeout or
 // abort.  A timeout records VS_ERR_TIMEOUT and raises the abort flag so that
-// every block leaves the persistent loop.
+// every warp leaves the persistent loop.
 __device__ bool wait_done(const int* ctr, int target, long long limit, WsHeader* hdr) {
   for (long long n = 0;; ++n) {
     if (ld_acquire(ctr) >= target) return true;
@@ -570,23 +620,24 @@ __device__ bool wait_done(const int* ctr, int target, long long limit, WsHeader*
   }
 }
 
-// Persistent kernel over all items.  Units are dispensed in a skewed global
-// order: stage s holds the SETUP units of item s, the RASTER units of item
-// s-1 and the SHADE units of item s-2, so that an item's visibility words
-// are written, resolved and read within a few stages (while still in L2).
-// A unit waits only for the previous phase of its own item, whose units were
-// all dispensed in an earlier stage to blocks that are already running, so
-// the wait always ends (and is bounded anyway).
+// Persistent kernel over all items; every WARP takes units on its own, so a
+// slow unit never holds up the other warps of its block.  Units are
+// dispensed in a skewed global order: stage s holds the SETUP units of item
+// s, the RASTER units of item s-1 and the SHADE units of item s-2, so that
+// an item's visibility words are written, resolved and read within a few
+// stages (while still in L2).  A unit waits only for the previous phase of
+// its own item, whose units were all dispensed in an earlier stage to warps
+// that are already running, so the wait always ends (and is bounded anyway).
 template <bool BWD>
 __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS) k_persistent(TableRef tb, long long spin_limit) {
-  __shared__ int s_unit, s_ok;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   WsHeader* hdr = tb.hdr;
+  char* smem = warp_smem(tb.kmax);
   for (;;) {
-    if (threadIdx.x == 0) {
-      s_unit = *(volatile int*)&hdr->abort ? tb.total : (int)atomicAdd(&hdr->next_unit, 1u);
-    }
-    __syncthreads();
-    const int g = s_unit;
+    int g = 0;
+    if (lane == 0) g = *(volatile int*)&hdr->abort ? tb.total : (int)atomicAdd(&hdr->next_unit, 1u);
+    g = __shfl_sync(FULL, g, 0);
     if (g >= tb.total) break;
     // stage: last s with stage_pre[s] <= g
     int lo = 0, hi = tb.n + NPH - 2;
@@ -604,27 +655,25 @@ __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS)
     }
     const DItem& it = tb.items[j];
     const int u = rel;
-    if (threadIdx.x == 0) {
-      bool ok = true;
-      if (ph > 0) {
-        int target = it.units[ph - 1];
-        long long lim = spin_limit;
-        if (ph == PH_SHADE && it.stall && u == 0) { target += 1; lim = 4096; }
-        ok = wait_done(tb.done + j * NPH + ph - 1, target, lim, hdr);
-      }
-      s_ok = ok;
+    int ok = 1;
+    if (lane == 0 && ph > 0) {
+      int target = it.units[ph - 1];
+      long long lim = spin_limit;
+      if (ph == PH_SHADE && it.stall && u == 0) { target += 1; lim = 4096; }
+      ok = wait_done(tb.done + j * NPH + ph - 1, target, lim, hdr) ? 1 : 0;
     }
-    __syncthreads();
-    if (!s_ok) break;
+    ok = __shfl_sync(FULL, ok, 0);
+    __syncwarp();   // orders every lane's reads after lane 0's acquire
+    if (!ok) break;
     const DShell* sh = tb.shells + it.shell0;
     switch (ph) {
       case PH_SETUP: unit_setup(it, sh, u); break;
-      case PH_RASTER: unit_raster(it, sh, u, hdr, vs_smem); break;
+      case PH_RASTER: unit_raster(it, sh, u, hdr, smem); break;
       default:
-        unit_shade<BWD, false>(it, sh, u, hdr, vs_smem, tb.kmax);
+        unit_shade<BWD, false>(it, sh, u, hdr, smem, tb.kmax);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    __syncwarp();
+    if (lane == 0) {
       __threadfence();
       atomicAdd(tb.done + j * NPH + ph, 1);
     }
@@ -647,17 +696,18 @@ int plain_forward_launches(const int units[4]) { return (units[0] > 0) + (units[
 int plain_backward_launches(const int units[4]) { return (units[0] > 0) + (units[2] > 0); }
 
 cudaError_t plain_forward(const TableRef& tb, const int units[4], cudaStream_t st) {
-  if (units[0]) vsd::k_setup<<<units[0], vsd::kThreads, 0, st>>>(tb, 0);
-  if (units[1]) vsd::k_raster<<<units[1], vsd::kThreads, vsd::kRasterSmemBytes, st>>>(tb, 0);
-  if (units[2])
-    vsd::k_shade<false, false><<<units[2], vsd::kThreads, vsd::block_smem_bytes(tb.kmax), st>>>(tb, 0);
+  const int W = vsd::kWarps;
+  const size_t smem = vsd::block_smem_bytes(tb.kmax);
+  if (units[0]) vsd::k_setup<<<(units[0] + W - 1) / W, vsd::kThreads, 0, st>>>(tb, 0);
+  if (units[1]) vsd::k_raster<<<units[1], vsd::kThreads, smem, st>>>(tb, 0);
+  if (units[2]) vsd::k_shade<false, false><<<units[2], vsd::kThreads, smem, st>>>(tb, 0);
   return cudaGetLastError();
 }
 
 cudaError_t plain_backward(const TableRef& tb, const int units[4], cudaStream_t st) {
-  if (units[0]) vsd::k_setup<<<units[0], vsd::kThreads, 0, st>>>(tb, 0);
-  if (units[2])
-    vsd::k_shade<true, true><<<units[2], vsd::kThreads, vsd::block_smem_bytes(tb.kmax), st>>>(tb, 0);
+  const int W = vsd::kWarps;
+  if (units[0]) vsd::k_setup<<<(units[0] + W - 1) / W, vsd::kThreads, 0, st>>>(tb, 0);
+  if (units[2]) vsd::k_shade<true, true><<<units[2], vsd::kThreads, vsd::block_smem_bytes(tb.kmax), st>>>(tb, 0);
   return cudaGetLastError();
 }
 
