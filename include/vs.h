@@ -212,6 +212,30 @@ vs_status vs_render_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, co
                           int32_t do_backward, void* workspace, size_t ws_bytes, uint32_t flags,
                           vs_stream_t stream);
 
+/* --- allocation-free forward ------------------------------------------------- */
+
+/* vs_render for callers that cannot allocate device memory at all, and so
+ * cannot pass a workspace: code running where cudaMalloc is not allowed (a
+ * host callback, a real-time loop under a no-allocation rule) or inside a
+ * framework that owns all device memory and lends none out.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *   Scratch: a fixed 16 MiB array in device memory that every GPU loading the
+ *   library holds until the process exits.  One call needs about
+ *   8 k H W + 16 sum(V) bytes plus a few KB (e.g. k = 3 shells at 512x512
+ *   with up to 300k vertices); larger requests return VS_ERR_OVERFLOW with the
+ *   needed size in vs_last_error(), before anything is enqueued.
+ *   First call: the first call on each device looks up the array's device
+ *   address (cudaGetSymbolAddress); make that first call before any stream
+ *   capture.
+ *   Sharing: every call uses the same array and leaves its contents there;
+ *   each call re-initialises what must start at zero.  Calls that overlap on
+ *   the GPU (e.g. on two streams of one device) race and corrupt each
+ *   other's results: order them.  Device-side counters are not reported.
+ *   Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * Arguments, outputs and errors as vs_render (without the workspace). */
+vs_status vs_render_noalloc(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, const float* bg,
+                            float* out_rgba, int32_t* hits, uint32_t flags, vs_stream_t stream);
+
 /* --- status and counters --------------------------------------------------------- */
 
 typedef struct {

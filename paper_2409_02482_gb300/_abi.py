@@ -80,6 +80,7 @@ SIGNATURES = {
                             ctypes.POINTER(_P), _P, _P, _SZ, _U, _P], _I),
     "vs_render_batch": ([_P, ctypes.POINTER(vs_batch_item), _I, _P, _I, _P, _SZ, _U, _P], _I),
     "vs_read_stats": ([_P, _P, _I, ctypes.POINTER(vs_stats)], _I),
+    "vs_render_noalloc": ([_P, _P, ctypes.POINTER(vs_camera), _P, _P, _P, _U, _P], _I),
 }
 
 _lib = None

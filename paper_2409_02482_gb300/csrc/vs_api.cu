@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -437,3 +438,78 @@ vs_status vs_read_stats(void* workspace, vs_stream_t stream, int32_t reset, vs_s
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free forward (vs_render_noalloc).
+//
+// Some callers cannot allocate device memory: code that runs where
+// cudaMalloc is not allowed (a host callback, a real-time loop under a
+// no-allocation rule) or inside a framework that owns every byte of device
+// memory and lends none out.  They cannot hand vs_render a workspace, so this
+// entry point keeps its scratch in a fixed device array instead.  The array
+// exists once per GPU that loads the library and stays until the process
+// exits; its size is the limit on what one call may render.
+// ===========================================================================
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;   // 16 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+std::mutex g_noalloc_mu;
+char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+}  // namespace
+
+// The scratch itself.  Host code must not use this name as an address: it is
+// a host-side stand-in; the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+// Device address of the scratch on `device` (which must be current); looked
+// up on the first call for that device and remembered.
+vs_status noalloc_scratch(int device, char** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (device < 0 || device >= kNoAllocMaxDevices)
+    return fail(VS_ERR_UNSUPPORTED, "vs_render_noalloc supports devices 0..%d", kNoAllocMaxDevices - 1);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+    g_noalloc_ptr[device] = static_cast<char*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return VS_OK;
+}
+
+}  // namespace
+
+extern "C" vs_status vs_render_noalloc(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, const float* bg,
+                                       float* out_rgba, int32_t* hits, uint32_t flags, vs_stream_t stream) {
+  vs_status s = check_item(ctx, obj, cam);
+  if (s != VS_OK) return s;
+  if (!out_rgba) return fail(VS_ERR_INVALID_ARG, "out_rgba is NULL");
+  if ((uintptr_t)out_rgba % 16) return fail(VS_ERR_INVALID_ARG, "out_rgba must be 16-byte aligned");
+  ItemReq r{obj, cam, out_rgba, hits, nullptr, nullptr, nullptr};
+  const uint32_t fl = flags & ~VS_FLAG_TEST_STALL;
+  Plan P;
+  if ((s = make_plan(&r, 1, bg, 0, true, fl, nullptr, P)) != VS_OK) return s;
+  if (P.total > kNoAllocScratchBytes)
+    return fail(VS_ERR_OVERFLOW,
+                "vs_render_noalloc needs %zu bytes of scratch for this object and camera; its fixed array holds "
+                "%zu (use vs_render with a workspace)",
+                P.total, kNoAllocScratchBytes);
+  if ((s = set_device(ctx)) != VS_OK) return s;
+  char* ws = nullptr;
+  if ((s = noalloc_scratch(ctx->device, &ws)) != VS_OK) return s;
+  if ((s = make_plan(&r, 1, bg, 0, true, fl, ws, P)) != VS_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // the array keeps the previous call's contents: the header (status,
+  // counters, work counter) must start at zero; the visibility words are
+  // cleared by the setup kernel and the table is rewritten below
+  cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-alloc header)");
+  if ((s = upload_table(P, ws, vsk::plain_forward_launches(P.items[0].units), st)) != VS_OK) return s;
+  e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, st);
+  return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_noalloc launch");
+}
