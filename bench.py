@@ -57,6 +57,7 @@ def parse():
                    help="FP16 values per texel in memory (28 used; 32 = 64-byte texels)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-uneven", action="store_true", help="skip the uneven 32-object batch")
     return p.parse_args()
 
 
@@ -136,6 +137,74 @@ def build_workload(args, device):
     ws = vs.make_workspace(ctx, [obj] * len(cams), cams, device=device)
     return dict(scene=scene, cams=cams, ctx=ctx, obj=obj, targets=targets, outs=outs, losses=losses,
                 grads=grads, items=vs.BatchItems(items), ws=ws, H=H, W=W)
+
+
+def uneven_batch(ctx, device, stream, steps):
+    """The uneven batch: 32 objects with k in {3,5,7,9}, 10k-1M faces per
+    shell, 8 views each at 512^2 / 800^2 / 1024^2 / 1920x1080, 1024^2 SH1
+    FP16 textures (pitch 16), fused fwd+bwd with the L2 loss -- one
+    persistent launch vs the plain per-view loop of vs_render +
+    vs_render_backward.  Geometry from the seeded generator; texel values
+    and targets are drawn on the device (only their shape and distribution
+    matter for timing)."""
+    import torch
+    import synth
+    import paper_2409_02482_gb300 as vs
+    objs = synth.config_scene("c4", views=8, pitch=16, textures=False)
+    g = torch.Generator(device=device).manual_seed(4)
+    items, objects = [], []
+    for sc, cams in objs:
+        shells = []
+        for s_ in sc.shells:
+            h, w, pitch = s_.tex.shape
+            tex = torch.zeros((h, w, pitch), dtype=torch.float16, device=device)
+            tex[..., :s_.channels] = (0.3 * torch.randn((h, w, s_.channels), device=device, generator=g)).half()
+            shells.append(dict(pos=torch.from_numpy(s_.pos).to(device), uv=torch.from_numpy(s_.uv).to(device),
+                               tris=torch.from_numpy(s_.tris).to(device), tex=tex, fmt=s_.fmt, degree=s_.degree))
+        obj = vs.ShellObject(ctx, shells)
+        objects.append(obj)
+        grads = [torch.zeros(t.shape, dtype=torch.float32, device=device) for t in obj.textures]
+        for cam in cams:
+            items.append(dict(obj=obj, cam=cam, grads=grads,
+                              out=torch.empty((cam.height, cam.width, 4), device=device),
+                              grad_rgb=torch.rand((cam.height, cam.width, 3), device=device, generator=g),
+                              loss=torch.zeros(1, device=device)))
+    ws = vs.make_workspace(ctx, [it["obj"] for it in items], [it["cam"] for it in items], device=device)
+    bi = vs.BatchItems(items)
+    flags = vs.VS_FLAG_LOSS_L2
+
+    def batched():
+        vs.render_batch(ctx, bi, ws, do_backward=True, flags=flags, stream=stream)
+
+    vs.read_stats(ws, reset=True)
+    batched()
+    st = vs.read_stats(ws, reset=True)
+    assert st["device_status"] == 0, st
+    frags = st["fragments"]
+    ms_b = timed(batched, steps, 2, stream, lambda: None)
+    kmax = max(o.k for o in objects)
+    hmax = max(it["cam"].height * it["cam"].width for it in items)
+    ws1 = torch.zeros(max(vs.workspace_size(ctx, [it["obj"]], [it["cam"]]) for it in items),
+                      dtype=torch.uint8, device=device)
+    hits_buf = torch.empty(kmax * hmax, dtype=torch.int32, device=device)
+
+    def plain():
+        for it in items:
+            c = it["cam"]
+            hits = hits_buf[: it["obj"].k * c.height * c.width].view(it["obj"].k, c.height, c.width)
+            vs.render(ctx, it["obj"], c, ws1, out=it["out"], hits=hits, stream=stream)
+            vs.render_backward(ctx, it["obj"], c, ws1, hits, it["grad_rgb"], grads=it["grads"],
+                               loss=it["loss"], flags=flags, stream=stream)
+
+    ms_p = timed(plain, max(1, steps // 2), 1, stream, lambda: None)
+    out = {"workload": "32 objects x 8 views, k in {3,5,7,9}, 10k-1M faces/shell, 512^2..1920x1080, "
+                       "1024^2 SH1 FP16, fused fwd+bwd, L2 loss",
+           "items": len(items), "triangles": int(sum(sum(s.tris.shape[0] for s in sc.shells) for sc, _ in objs)),
+           "fragments_per_step": frags, "batched_ms": ms_b, "plain_ms": ms_p, "batched_vs_plain": ms_p / ms_b,
+           "batched_fragments_per_s": frags / (ms_b * 1e-3), "batched_images_per_s": len(items) / (ms_b * 1e-3)}
+    del ws, ws1, items, objects, bi
+    torch.cuda.empty_cache()
+    return out
 
 
 def timed(fn, steps, warmup, stream, barrier):
@@ -337,6 +406,8 @@ def run_ours(args):
                              "fwd_bwd_fragments_per_s": frags / (ms_plain * 1e-3),
                              "fwd_fragments_per_s": frags / (ms_plain_fwd * 1e-3)}
         res["batched_vs_plain"] = {"fwd_bwd": ms_plain / ms, "fwd": ms_plain_fwd / ms_fwd}
+    if not args.no_uneven and rank == 0:
+        res["uneven_batch"] = uneven_batch(ctx, device, stream, max(3, args.steps // 10))
 
     if rank != 0:
         if ws_n > 1:

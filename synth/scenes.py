@@ -277,12 +277,12 @@ def sh_texture(h: int, w: int, degree: int, rng: np.random.Generator,
     """
     c = sh_channels(degree)
     pitch = c if pitch is None else pitch
+    vals = rng.standard_normal((h, w, c), dtype=np.float32)
+    vals *= np.float32(sigma)
+    if pitch == c:
+        return vals.astype(np.float16)
     tex = np.zeros((h, w, pitch), dtype=np.float16)
-    rows = max(1, (1 << 24) // (w * c))
-    for r0 in range(0, h, rows):
-        r1 = min(h, r0 + rows)
-        tex[r0:r1, :, :c] = (sigma * rng.standard_normal((r1 - r0, w, c),
-                                                         dtype=np.float32)).astype(np.float16)
+    tex[..., :c] = vals
     return tex
 
 
@@ -346,19 +346,23 @@ CONFIGS = {
 }
 
 
-def _sh_scene(k, n_lat, tex_res, degree, seed, tex_seed, pitch=None, sigma=0.3):
+def _sh_scene(k, n_lat, tex_res, degree, seed, tex_seed, pitch=None, sigma=0.3, textures=True):
     geo = displaced_shells(k, n_lat, seed=seed)
     ss = np.random.SeedSequence(tex_seed).spawn(k)
     shells = []
     for i, (pos, uv, tris) in enumerate(geo):
-        rng = np.random.default_rng(ss[i])
-        tex = sh_texture(tex_res, tex_res, degree, rng, sigma=sigma, pitch=pitch)
+        if textures:
+            rng = np.random.default_rng(ss[i])
+            tex = sh_texture(tex_res, tex_res, degree, rng, sigma=sigma, pitch=pitch)
+        else:   # shape only (zero-strided): the caller makes the values
+            c = sh_channels(degree)
+            tex = np.broadcast_to(np.float16(0), (tex_res, tex_res, c if pitch is None else pitch))
         shells.append(Shell(pos, uv, tris, tex, FMT_SH_F16, degree))
     return Scene(shells)
 
 
 def config_scene(name: str, scale: float = 1.0, views: Optional[int] = None,
-                 tex_seed: int = 0, pitch: Optional[int] = None):
+                 tex_seed: int = 0, pitch: Optional[int] = None, textures: bool = True):
     """Build workload ``name`` ('c1'..'c5').
 
     ``scale`` < 1 shrinks triangle counts (by scale), texture side and image
@@ -403,7 +407,8 @@ def config_scene(name: str, scale: float = 1.0, views: Optional[int] = None,
             k = int(rng.choice([3, 5, 7, 9]))
             tris = np.exp(rng.uniform(np.log(10e3), np.log(1e6), size=k)) * scale
             n_lat = [_n_lat_for_tris(t) for t in tris]
-            sc = _sh_scene(k, n_lat, texres(1024), 1, 100 + o, 1000 * (tex_seed + 1) + o, pitch)
+            sc = _sh_scene(k, n_lat, texres(1024), 1, 100 + o, 1000 * (tex_seed + 1) + o, pitch,
+                           textures=textures)
             cams = []
             for vi in range(n_views):
                 wv, hv = resolutions[int(rng.integers(len(resolutions)))]
