@@ -152,8 +152,12 @@ def raster_scene(scene, cam, threads: Optional[int] = None, brute: bool = False)
 
 # --- shading / compositing ----------------------------------------------------------
 
-def shade(scene, cam, hits: np.ndarray, bg=(0.0, 0.0, 0.0), threads: Optional[int] = None):
-    """Bilinear texel fetch, SH decode and front-to-back compositing (Eq. 6).
+ALPHA_ATTEN = 2   # flag: transparency attenuation (Sec. 3 "Transparency Attenuation")
+
+
+def shade(scene, cam, hits: np.ndarray, bg=(0.0, 0.0, 0.0), threads: Optional[int] = None, flags: int = 0):
+    """Bilinear texel fetch, SH decode and front-to-back compositing (Eq. 6);
+    flags & ALPHA_ATTEN scales each alpha by 2 sigmoid(10 |v . n|) - 1.
 
     Returns (rgba float64 [H,W,4] = (C + T bg, 1 - T), fragments per shell).
     """
@@ -166,18 +170,20 @@ def shade(scene, cam, hits: np.ndarray, bg=(0.0, 0.0, 0.0), threads: Optional[in
     frags = np.zeros(scene.k, np.int64)
     c = ocam(cam)
     lib().oracle_shade(refs.arr, ctypes.c_int32(scene.k), ctypes.byref(c), _ptr(bgv), _ptr(hits),
-                       _ptr(out), ctypes.c_int32(threads or default_threads()), _ptr(frags))
+                       _ptr(out), ctypes.c_int32(threads or default_threads()), _ptr(frags),
+                       ctypes.c_int32(flags))
     return out, frags
 
 
-def render(scene, cam, bg=(0.0, 0.0, 0.0), threads: Optional[int] = None):
+def render(scene, cam, bg=(0.0, 0.0, 0.0), threads: Optional[int] = None, flags: int = 0):
     """Full oracle render: (rgba [H,W,4] f64, hits [k,H,W] i32, frags [k])."""
     hits, _, _ = raster_scene(scene, cam, threads=threads)
-    rgba, frags = shade(scene, cam, hits, bg=bg, threads=threads)
+    rgba, frags = shade(scene, cam, hits, bg=bg, threads=threads, flags=flags)
     return rgba, hits, frags
 
 
-def backward(scene, cam, hits: np.ndarray, grad_rgb: np.ndarray, bg=(0.0, 0.0, 0.0)) -> List[np.ndarray]:
+def backward(scene, cam, hits: np.ndarray, grad_rgb: np.ndarray, bg=(0.0, 0.0, 0.0),
+             flags: int = 0) -> List[np.ndarray]:
     """dL/d(texel values) given dL/d(output rgb) -- the texture-fitting
     gradient of Sec. 3 "Texturing Meshes".  Returns one FP64 array per shell,
     shaped like its texture."""
@@ -191,7 +197,7 @@ def backward(scene, cam, hits: np.ndarray, grad_rgb: np.ndarray, bg=(0.0, 0.0, 0
     bgv = np.ascontiguousarray(bg, np.float64)
     c = ocam(cam)
     lib().oracle_backward(refs.arr, ctypes.c_int32(scene.k), ctypes.byref(c), _ptr(bgv), _ptr(hits),
-                          _ptr(g), ptrs)
+                          _ptr(g), ptrs, ctypes.c_int32(flags))
     return grads
 
 

@@ -353,13 +353,32 @@ int num_values(const OShell& s) {
 
 // One fragment: (pixel, shell, triangle) -> rgb, alpha, plus what the adjoint needs.
 struct Frag {
-  double rgb[3], alpha;
+  double rgb[3], alpha;    // alpha = alpha_raw * atten
+  double alpha_raw;        // opacity from the texels
+  double atten;            // transparency attenuation (1 unless enabled)
   Footprint fp;
   double val[64];          // interpolated texel values
 };
 
+// Sec. 3 "Transparency Attenuation": alpha_w = 2 sigmoid(10 |v . n|) - 1,
+// with v the unit ray direction and n the unit normal of the hit face (the
+// flat geometric normal of the baked triangle).
+double attenuation(const OShell& s, const int32_t* idx, const double v[3]) {
+  double p[3][3];
+  for (int j = 0; j < 3; ++j)
+    for (int d = 0; d < 3; ++d) p[j][d] = s.pos[3 * idx[j] + d];
+  const double a[3] = {p[1][0] - p[0][0], p[1][1] - p[0][1], p[1][2] - p[0][2]};
+  const double b[3] = {p[2][0] - p[0][0], p[2][1] - p[0][1], p[2][2] - p[0][2]};
+  const double n[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+  const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  const double vn = std::fabs(n[0] * v[0] + n[1] * v[1] + n[2] * v[2]) / len;
+  return 2.0 / (1.0 + std::exp(-10.0 * vn)) - 1.0;
+}
+
+enum { OFLAG_ALPHA_ATTEN = 2 };
+
 bool shade_fragment(const OShell& s, const OCam& c, const std::vector<SVert>& sv, int32_t tri,
-                    int64_t x, int64_t y, const double* Y, Frag* f) {
+                    int64_t x, int64_t y, const double* Y, const double* v, int flags, Frag* f) {
   const int32_t* idx = s.tris + 3 * tri;
   Tri t;
   int why;
@@ -383,6 +402,9 @@ bool shade_fragment(const OShell& s, const OCam& c, const std::vector<SVert>& sv
       f->rgb[ch] = sigmoid(z);
     }
   }
+  f->alpha_raw = f->alpha;
+  f->atten = (flags & OFLAG_ALPHA_ATTEN) ? attenuation(s, idx, v) : 1.0;
+  f->alpha = f->alpha_raw * f->atten;
   return true;
 }
 
@@ -427,7 +449,7 @@ int oracle_raster(const float* pos, int32_t nv, const int32_t* tris, int32_t nt,
 // Shade + composite every pixel from per-shell hits [k, H, W] (-1 = miss).
 // out: [H, W, 4] = (C + T bg, 1 - T).  stats (optional): [k] fragments per shell.
 int oracle_shade(const OShell* shells, int32_t k, const OCam* cam, const double* bg,
-                 const int32_t* hits, double* out, int32_t nthreads, int64_t* frags) {
+                 const int32_t* hits, double* out, int32_t nthreads, int64_t* frags, int32_t flags) {
   const int64_t W = cam->width, H = cam->height;
   std::vector<std::vector<SVert>> sv(k);
   int maxdeg = 0;
@@ -448,7 +470,7 @@ int oracle_shade(const OShell* shells, int32_t k, const OCam* cam, const double*
           int32_t h = hits[(size_t)i * H * W + y * W + x];
           if (h < 0) continue;
           Frag f;
-          if (!shade_fragment(shells[i], *cam, sv[i], h, x, y, Y, &f)) continue;
+          if (!shade_fragment(shells[i], *cam, sv[i], h, x, y, Y, v, flags, &f)) continue;
           cnt[(size_t)ti * k + i] += 1;
           for (int ch = 0; ch < 3; ++ch) C[ch] += T * f.alpha * f.rgb[ch];
           T *= (1.0 - f.alpha);
@@ -469,7 +491,7 @@ int oracle_shade(const OShell* shells, int32_t k, const OCam* cam, const double*
 // Adjoint of oracle_shade w.r.t. the texel values.  grad_rgb: [H, W, 3] =
 // dL/d(output rgb).  grad_tex[i]: [th, tw, pitch] FP64, accumulated into.
 int oracle_backward(const OShell* shells, int32_t k, const OCam* cam, const double* bg,
-                    const int32_t* hits, const double* grad_rgb, double* const* grad_tex) {
+                    const int32_t* hits, const double* grad_rgb, double* const* grad_tex, int32_t flags) {
   const int64_t W = cam->width, H = cam->height;
   std::vector<std::vector<SVert>> sv(k);
   int maxdeg = 0;
@@ -489,7 +511,7 @@ int oracle_backward(const OShell* shells, int32_t k, const OCam* cam, const doub
       double T = 1.0;
       for (int i = 0; i < k; ++i) {
         int32_t h = hits[(size_t)i * H * W + y * W + x];
-        hit[i] = h >= 0 && shade_fragment(shells[i], *cam, sv[i], h, x, y, Y, &fr[i]);
+        hit[i] = h >= 0 && shade_fragment(shells[i], *cam, sv[i], h, x, y, Y, v, flags, &fr[i]);
         Tin[i] = T;
         if (hit[i]) T *= (1.0 - fr[i].alpha);
       }
@@ -507,11 +529,12 @@ int oracle_backward(const OShell* shells, int32_t k, const OCam* cam, const doub
         for (int ch = 0; ch < 3; ++ch) A[ch] = f.alpha * f.rgb[ch] + (1.0 - f.alpha) * A[ch];
         int nv = num_values(s);
         double dval[64];
+        // alpha = alpha_raw * atten, atten independent of the texels
         if (s.fmt == FMT_RGBA_F32) {
-          dval[0] = gc[0]; dval[1] = gc[1]; dval[2] = gc[2]; dval[3] = ga;
+          dval[0] = gc[0]; dval[1] = gc[1]; dval[2] = gc[2]; dval[3] = ga * f.atten;
         } else {
           int nb = (s.degree + 1) * (s.degree + 1);
-          dval[0] = ga * f.alpha * (1.0 - f.alpha);
+          dval[0] = ga * f.atten * f.alpha_raw * (1.0 - f.alpha_raw);
           for (int ch = 0; ch < 3; ++ch) {
             double dz = gc[ch] * f.rgb[ch] * (1.0 - f.rgb[ch]);
             for (int m = 0; m < nb; ++m) dval[1 + 3 * m + ch] = dz * Y[m];

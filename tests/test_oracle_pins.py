@@ -569,6 +569,104 @@ def test_constant_sh_textures_closed_form():
 
 
 # ----------------------------------------------------------------------------
+# transparency attenuation (Sec. 3): alpha_w = 2 sigmoid(10 |v . n|) - 1
+# ----------------------------------------------------------------------------
+
+def test_attenuation_tilted_plane_closed_form():
+    """One planar quad with constant colour and alpha, seen at a slant: every
+    covered pixel composites alpha * (2 sigmoid(10 |v . n|) - 1) over the
+    background, v the pixel ray and n the plane normal; head-on rays keep
+    nearly all of alpha, grazing ones lose most of it."""
+    th = math.radians(70.0)
+    ax, az = np.array([1.0, 0.0, 0.0]), np.array([0.0, math.sin(th), math.cos(th)])
+    n = np.cross(ax, az)                     # unit plane normal
+    corners = [-ax - az, ax - az, ax + az, -ax + az]
+    pos = np.array(corners, np.float32)
+    uv = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], np.float32)
+    tris = np.array([[0, 1, 2], [0, 2, 3]], np.int32)
+    view = 0.35 * n + az + 0.2 * ax                # about 18 degrees above the plane
+    eye = 3.0 * view / np.linalg.norm(view)
+    cam = synth.look_at(tuple(eye), target=(0.0, 0.0, 0.0), width=64, height=64)
+    if oracle.raster_scene(Scene([constant_shell(pos, uv, tris, [0, 0, 0, 1])]), cam)[0][0].max() < 0:
+        tris = tris[:, ::-1].copy()          # make the quad face the camera
+    color, a, bg = np.array([0.8, 0.3, 0.1]), 0.7, np.array([0.1, 0.2, 0.9])
+    sc = Scene([constant_shell(pos, uv, tris, list(color) + [a], dtype=np.float64)])
+    rgba, hits, _ = oracle.render(sc, cam, bg=tuple(bg), flags=oracle.ALPHA_ATTEN)
+    plain, _, _ = oracle.render(sc, cam, bg=tuple(bg))
+    _, dirs = pixel_rays(cam)
+    h = hits[0] >= 0
+    assert h.sum() > 500
+    p64 = pos.astype(np.float64)            # the normal of the stored (FP32) plane
+    n = np.cross(p64[1] - p64[0], p64[3] - p64[0])
+    n /= np.linalg.norm(n)
+    aw = 2.0 / (1.0 + np.exp(-10.0 * np.abs(dirs @ n))) - 1.0
+    ae = a * aw
+    want = ae[..., None] * color + (1 - ae[..., None]) * bg
+    assert np.abs(rgba[h][:, :3] - want[h]).max() < 1e-12
+    assert np.abs(rgba[h][:, 3] - ae[h]).max() < 1e-12
+    assert np.all(rgba[~h] == plain[~h])
+    assert np.abs(plain[h][:, 3] - a).max() < 1e-15       # flag off: unchanged
+    assert 0.0 < aw[h].min() < aw[h].max() < 1.0
+
+
+def test_attenuation_grazing_and_head_on_limits():
+    """|v . n| = 1 gives alpha_w = 2 sigmoid(10) - 1 (the sphere's centre
+    pixel, seen head on) and v . n -> 0 gives alpha_w -> 0 (its silhouette)."""
+    pos, uv, tris = synth.icosphere(4, 1.0)
+    sc = Scene([constant_shell(pos, uv, tris, [0.5, 0.5, 0.5, 1.0], dtype=np.float64)])
+    cam = synth.look_at((0.0, -4.0, 0.0), width=96, height=96)
+    rgba, hits, _ = oracle.render(sc, cam, flags=oracle.ALPHA_ATTEN)
+    h = hits[0] >= 0
+    a = rgba[..., 3]
+    # the pixel nearest the sphere's centre sees it almost head on
+    assert abs(a[48, 48] - (2 / (1 + math.exp(-10)) - 1)) < 2e-3
+    # silhouette pixels (hit, with a missed 4-neighbour) are strongly attenuated
+    edge = h & ~(np.roll(h, 1, 0) & np.roll(h, -1, 0) & np.roll(h, 1, 1) & np.roll(h, -1, 1))
+    assert edge.sum() > 50 and a[edge].min() >= 0.0
+    assert a[edge].mean() < 0.7 * a[h].max() and a[edge].max() < a[48, 48]
+    assert np.all(a[h] <= 2 / (1 + math.exp(-10)) - 1 + 1e-15)
+
+
+def test_attenuation_nested_shells_use_each_hit_face_normal():
+    """Nested icospheres, flag on: each layer's alpha is scaled by the weight
+    of its own hit triangle's face normal (the flat normal of the baked mesh,
+    not the radial direction), then the usual front-to-back blend."""
+    geo = synth.concentric_icospheres([1.0, 0.9, 0.8], subdiv=1)
+    colors = [np.array([0.9, 0.2, 0.1]), np.array([0.1, 0.8, 0.3]), np.array([0.2, 0.3, 0.95])]
+    alphas = [0.35, 0.6, 0.8]
+    shells = [constant_shell(p, u, t, list(c) + [a], dtype=np.float64)
+              for (p, u, t), c, a in zip(geo, colors, alphas)]
+    cam = synth.look_at((1.5, -2.4, 0.9), width=64, height=64)
+    bg = np.array([0.25, 0.5, 0.75])
+    rgba, hits, _ = oracle.render(Scene(shells), cam, bg=tuple(bg), flags=oracle.ALPHA_ATTEN)
+    _, dirs = pixel_rays(cam)
+    normals = []
+    for (p, _, t) in geo:
+        p = p.astype(np.float64)
+        nn = np.cross(p[t[:, 1]] - p[t[:, 0]], p[t[:, 2]] - p[t[:, 0]])
+        normals.append(nn / np.linalg.norm(nn, axis=1, keepdims=True))
+    radial_differs = 0
+    for y in range(64):
+        for x in range(64):
+            C, T = np.zeros(3), 1.0
+            for i in range(3):
+                t = hits[i, y, x]
+                if t < 0:
+                    continue
+                vn = abs(dirs[y, x] @ normals[i][t])
+                ae = alphas[i] * (2 / (1 + math.exp(-10 * vn)) - 1)
+                C += T * ae * colors[i]
+                T *= 1 - ae
+            assert np.abs(rgba[y, x, :3] - (C + T * bg)).max() < 1e-12
+            assert abs(rgba[y, x, 3] - (1 - T)) < 1e-12
+            if hits[0, y, x] >= 0:
+                pt = geo[0][0][geo[0][2][hits[0, y, x]]].astype(np.float64).mean(0)
+                vr = abs(dirs[y, x] @ (pt / np.linalg.norm(pt)))
+                radial_differs += abs(vr - abs(dirs[y, x] @ normals[0][hits[0, y, x]])) > 1e-3
+    assert radial_differs > 100
+
+
+# ----------------------------------------------------------------------------
 # backward (Sec. 3 "Texturing Meshes": fitting texels through the renderer)
 # ----------------------------------------------------------------------------
 
@@ -585,18 +683,20 @@ def _tiny_scene(fmt, degree, seed, size=4):
     return Scene(shells)
 
 
-@pytest.mark.parametrize("fmt,degree", [(FMT_RGBA_F32, 0), (FMT_SH_F16, 1), (FMT_SH_F16, 2)])
-def test_backward_matches_central_differences(fmt, degree):
+@pytest.mark.parametrize("fmt,degree,flags", [(FMT_RGBA_F32, 0, 0), (FMT_SH_F16, 1, 0), (FMT_SH_F16, 2, 0),
+                                               (FMT_RGBA_F32, 0, oracle.ALPHA_ATTEN),
+                                               (FMT_SH_F16, 2, oracle.ALPHA_ATTEN)])
+def test_backward_matches_central_differences(fmt, degree, flags):
     sc = _tiny_scene(fmt, degree, seed=20 + degree)
     cam = synth.look_at((0.7, -2.8, 0.9), width=20, height=18)
     bg = (0.2, 0.4, 0.6)
     hits, _, _ = oracle.raster_scene(sc, cam)
     rng = np.random.default_rng(30)
     g = rng.normal(size=(cam.height, cam.width, 3))
-    grads = oracle.backward(sc, cam, hits, g, bg=bg)
+    grads = oracle.backward(sc, cam, hits, g, bg=bg, flags=flags)
 
     def loss():
-        return float((oracle.shade(sc, cam, hits, bg=bg, threads=1)[0][..., :3] * g).sum())
+        return float((oracle.shade(sc, cam, hits, bg=bg, threads=1, flags=flags)[0][..., :3] * g).sum())
 
     h = 1e-6
     worst = 0.0
