@@ -108,6 +108,15 @@ typedef struct {
  * gradient; the kernel uses dL/dC = 2 (C - target) / (3 H W), i.e. the
  * gradient of the mean squared error over pixels and RGB channels, computing
  * C itself from the hits, and adds L to `loss` when that pointer is set. */
+#define VS_FLAG_ALPHA_ATTEN (1u << 1)
+/* Transparency attenuation (Sec. 3 "Transparency Attenuation"): every
+ * fragment's opacity is multiplied by alpha_w = 2 sigmoid(10 |v . n|) - 1,
+ * v the unit ray direction of the pixel and n the unit normal of the hit
+ * triangle, (p1 - p0) x (p2 - p0) of its stored world positions.  Applies to
+ * vs_render, vs_render_backward (pass the same flags as the forward) and
+ * vs_render_batch; the backward treats alpha_w as a constant of the texels.
+ * Off by default: the paper defines it for blending during training and does
+ * not say whether the baked renderer keeps it. */
 #define VS_FLAG_TEST_STALL (1u << 30)
 /* Test hook for failure detection: the persistent batch kernel's first
  * shading unit waits for a counter that nothing increments, with a short

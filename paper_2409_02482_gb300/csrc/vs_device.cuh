@@ -30,9 +30,10 @@ constexpr int kTriBits = 27;           // triangle index bits in a packed fragme
 constexpr int kMaxTris = 1 << kTriBits;
 
 // Dynamic shared memory of a shading warp for up to K shells: N = 32 K
-// fragments; [frag float4 N][T, B float2 N][g float4 32][entry int N][lane u8 N].
+// fragments; [frag float4 N][T, B float2 N][g float4 32][entry int N]
+// [alpha_w float N][lane u8 N].
 __host__ __device__ constexpr size_t shade_warp_bytes(int K) {
-  return (29 * (size_t)(32 * K) + 512 + 15) & ~(size_t)15;
+  return (33 * (size_t)(32 * K) + 512 + 15) & ~(size_t)15;
 }
 constexpr size_t kRasterWarpBytes = 32 * (64 + 8 + 4);   // TriS, TriPos, start per triangle
 __host__ __device__ constexpr size_t warp_slice_bytes(int K) {
@@ -422,6 +423,25 @@ __device__ __forceinline__ float3 ray_dir(const DCam& c, int x, int y) {
   float vz = c.m[2] * a + c.m[6] * b + c.m[10];
   const float r = rsqrtf(vx * vx + vy * vy + vz * vz);
   return make_float3(vx * r, vy * r, vz * r);
+}
+
+// Transparency attenuation (Sec. 3): alpha_w = 2 sigmoid(10 |v . n|) - 1 for
+// unit ray direction v and the unit normal n of the hit face, taken as the
+// flat normal (p1 - p0) x (p2 - p0) of the stored triangle.  Grazing rays
+// (v . n -> 0) give alpha_w -> 0, head-on rays 2 sigmoid(10) - 1.
+__device__ __forceinline__ float alpha_atten(const float* pos, const int idx[3], const float3 v) {
+  float p[3][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) p[j][d] = __ldg(pos + 3 * (size_t)idx[j] + d);
+  const float ax = p[1][0] - p[0][0], ay = p[1][1] - p[0][1], az = p[1][2] - p[0][2];
+  const float bx = p[2][0] - p[0][0], by = p[2][1] - p[0][1], bz = p[2][2] - p[0][2];
+  const float nx = ay * bz - az * by, ny = az * bx - ax * bz, nz = ax * by - ay * bx;
+  const float n2 = nx * nx + ny * ny + nz * nz;
+  // a face with a projected area has a nonzero normal; guard the rounding case
+  const float vn = n2 > 0.0f ? fabsf(nx * v.x + ny * v.y + nz * v.z) * rsqrtf(n2) : 0.0f;
+  return 2.0f * sigmoidf_(10.0f * vn) - 1.0f;
 }
 
 // ----------------------------------------------------------------------------

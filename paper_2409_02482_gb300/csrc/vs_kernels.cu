@@ -356,6 +356,25 @@ __device__ __forceinline__ void adjoint_frag(const DShell& s, const Footprint& f
 #undef VS_CASE
 }
 
+// alpha_w of the fragments [0, total) of a shading round (lane-strided).
+__device__ __noinline__ void atten_pass(const DCam& cam, const DShell* sh, int pbase, const int* sent,
+                                        const unsigned char* spl, float* saw, int total) {
+  const int lane = threadIdx.x & 31;
+  for (int j = lane; j < total; j += 32) {
+    const int e = sent[j];
+    const int i = e >> kTriBits, t = e & (kMaxTris - 1);
+    const DShell& s = sh[i];
+    if (t >= s.nt) continue;
+    const int* ip = s.tris + 3 * (size_t)t;
+    const int idx[3] = {__ldg(ip), __ldg(ip + 1), __ldg(ip + 2)};
+    if ((unsigned)idx[0] >= (unsigned)s.nv || (unsigned)idx[1] >= (unsigned)s.nv || (unsigned)idx[2] >= (unsigned)s.nv)
+      continue;
+    const int pp = pbase + spl[j];
+    const int y = pp / cam.W, x = pp - y * cam.W;
+    saw[j] = alpha_atten(s.pos, idx, ray_dir(cam, x, y));
+  }
+}
+
 // Shading unit: kShadePixels pixels, 32 per warp (lane = pixel).
 //  1. each lane reads its pixel's k visibility words (independent loads)
 //     and the warp compacts the hits into a fragment list in shared memory,
@@ -385,7 +404,8 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
   float2* stb = reinterpret_cast<float2*>(wb + 16 * (size_t)N);
   float4* sg = reinterpret_cast<float4*>(wb + 24 * (size_t)N);
   int* sent = reinterpret_cast<int*>(wb + 24 * (size_t)N + 512);
-  unsigned char* spl = reinterpret_cast<unsigned char*>(wb + 28 * (size_t)N + 512);
+  float* saw = reinterpret_cast<float*>(wb + 28 * (size_t)N + 512);
+  unsigned char* spl = reinterpret_cast<unsigned char*>(wb + 32 * (size_t)N + 512);
   const int p = pbase + lane;
   const bool pix_ok = p < HW;
 
@@ -459,9 +479,14 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
         fr = fetch_frag(s, f, v);
         ++nfrag;
       }
+      // raw opacity here; the composite and the adjoint apply alpha_w
       sfrag[j] = make_float4(fr.r, fr.g, fr.b, fr.a);
+      saw[j] = 1.0f;
     }
   }
+  // 2b. transparency attenuation, in a pass of its own so that the fetch
+  //     loop above keeps its registers
+  if (it.flags & VS_FLAG_ALPHA_ATTEN) atten_pass(it.cam, sh, pbase, sent, spl, saw, total);
   __syncwarp();
 
   // 3. composite this pixel
@@ -469,11 +494,12 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
   for (int c = 0; c < cnt; ++c) {
     const float4 f = sfrag[start + c];
     if constexpr (BWD) stb[start + c].x = T;
-    const float ta = T * f.w;
+    const float a = f.w * saw[start + c];
+    const float ta = T * a;
     Cr = fmaf(ta, f.x, Cr);
     Cg = fmaf(ta, f.y, Cg);
     Cb = fmaf(ta, f.z, Cb);
-    T = T * (1.0f - f.w);
+    T = T * (1.0f - a);
   }
   const float outr = fmaf(T, it.bg[0], Cr), outg = fmaf(T, it.bg[1], Cg), outb = fmaf(T, it.bg[2], Cb);
   if (pix_ok && it.out) it.out[p] = make_float4(outr, outg, outb, 1.0f - T);
@@ -498,7 +524,7 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
     for (int c = cnt - 1; c >= 0; --c) {
       stb[start + c].y = B;
       const float4 f = sfrag[start + c];
-      B = fmaf(f.w, f.x * gr + f.y * gg + f.z * gb - B, B);
+      B = fmaf(f.w * saw[start + c], f.x * gr + f.y * gg + f.z * gb - B, B);
     }
     sg[lane] = make_float4(gr, gg, gb, 0.0f);
     __syncwarp();
@@ -522,10 +548,12 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
           if (s.fmt == VS_TEX_SH_F16) v = ray_dir(it.cam, x, y);
           const float4 q = sfrag[j];
           const Frag fr = {q.x, q.y, q.z, q.w};
+          const float aw = saw[j];
           const float2 tbv = stb[j];
           const float4 g = sg[pl];
-          const float ta = tbv.x * fr.a;
-          const float ga = tbv.x * (fr.r * g.x + fr.g * g.y + fr.b * g.z - tbv.y);
+          // composite opacity alpha = raw * alpha_w; alpha_w is texel-independent
+          const float ta = tbv.x * (fr.a * aw);
+          const float ga = tbv.x * (fr.r * g.x + fr.g * g.y + fr.b * g.z - tbv.y) * aw;
           adjoint_frag(s, f, v, fr, ta * g.x, ta * g.y, ta * g.z, ga);
         }
       }

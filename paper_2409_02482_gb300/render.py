@@ -12,12 +12,12 @@ from typing import List, Optional, Sequence
 import torch
 
 from . import _abi
-from ._abi import (VS_FLAG_LOSS_L2, VS_TEX_RGBA_F32, VS_TEX_SH_F16, check, vs_batch_item,
+from ._abi import (VS_FLAG_ALPHA_ATTEN, VS_FLAG_LOSS_L2, VS_TEX_RGBA_F32, VS_TEX_SH_F16, check, vs_batch_item,
                    vs_camera, vs_shell_desc, vs_stats)
 
 __all__ = ["Context", "ShellObject", "camera_struct", "workspace_size", "make_workspace",
            "render", "render_backward", "render_batch", "read_stats", "VSRender",
-           "VS_FLAG_LOSS_L2", "VS_TEX_RGBA_F32", "VS_TEX_SH_F16"]
+           "VS_FLAG_ALPHA_ATTEN", "VS_FLAG_LOSS_L2", "VS_TEX_RGBA_F32", "VS_TEX_SH_F16"]
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -213,16 +213,16 @@ def read_stats(ws: torch.Tensor, reset: bool = False, stream=None) -> dict:
 class VSRender(torch.autograd.Function):
     """Differentiable render w.r.t. the texel arrays.
 
-    forward(ctx_, obj, cam, ws, bg, *textures) -> rgba [H,W,4]; the hit
-    buffer is saved and the backward recomputes transmittance from it
-    (vs_render_backward).  Gradients come back in FP32 and autograd casts
-    them to each texture's dtype.
+    forward(ctx_, obj, cam, ws, bg, flags, *textures) -> rgba [H,W,4]; the
+    hit buffer is saved and the backward recomputes transmittance from it
+    (vs_render_backward, same flags).  Gradients come back in FP32 and
+    autograd casts them to each texture's dtype.
     """
 
     @staticmethod
-    def forward(fctx, vctx: Context, obj: ShellObject, cam, ws: torch.Tensor, bg, *textures):
-        out, hits = render(vctx, obj, cam, ws, bg=bg)
-        fctx.vctx, fctx.obj, fctx.cam, fctx.ws, fctx.bg = vctx, obj, cam, ws, bg
+    def forward(fctx, vctx: Context, obj: ShellObject, cam, ws: torch.Tensor, bg, flags, *textures):
+        out, hits = render(vctx, obj, cam, ws, bg=bg, flags=flags)
+        fctx.vctx, fctx.obj, fctx.cam, fctx.ws, fctx.bg, fctx.flags = vctx, obj, cam, ws, bg, flags
         fctx.save_for_backward(hits)
         return out
 
@@ -230,5 +230,6 @@ class VSRender(torch.autograd.Function):
     def backward(fctx, grad_out):
         (hits,) = fctx.saved_tensors
         g = grad_out[..., :3].contiguous().float()
-        grads = render_backward(fctx.vctx, fctx.obj, fctx.cam, fctx.ws, hits, g, bg=fctx.bg)
-        return (None, None, None, None, None, *grads)
+        grads = render_backward(fctx.vctx, fctx.obj, fctx.cam, fctx.ws, hits, g, bg=fctx.bg,
+                                flags=fctx.flags)
+        return (None, None, None, None, None, None, *grads)

@@ -40,18 +40,18 @@ def tol_of(scene):
     return TOL_F32 if all(s.fmt == FMT_RGBA_F32 for s in scene.shells) else TOL_F16
 
 
-def gpu_render(vs, ctx, scene, cam, bg=(0.0, 0.0, 0.0), obj=None):
+def gpu_render(vs, ctx, scene, cam, bg=(0.0, 0.0, 0.0), obj=None, flags=0):
     obj = obj or vs.ShellObject.from_scene(ctx, scene)
     ws = vs.make_workspace(ctx, [obj], [cam])
-    out, hits = vs.render(ctx, obj, cam, ws, bg=bg)
+    out, hits = vs.render(ctx, obj, cam, ws, bg=bg, flags=flags)
     st = vs.read_stats(ws)
     assert st["device_status"] == 0
     return out.cpu().numpy(), hits.cpu().numpy(), st, obj, ws
 
 
-def check_forward(vs, ctx, scene, cam, bg=(0.0, 0.0, 0.0), tol=None):
-    out, hits, st, obj, ws = gpu_render(vs, ctx, scene, cam, bg)
-    ref, ref_hits, frags = oracle.render(scene, cam, bg=bg)
+def check_forward(vs, ctx, scene, cam, bg=(0.0, 0.0, 0.0), tol=None, flags=0):
+    out, hits, st, obj, ws = gpu_render(vs, ctx, scene, cam, bg, flags=flags)
+    ref, ref_hits, frags = oracle.render(scene, cam, bg=bg, flags=flags)
     mism = (hits != ref_hits).sum()
     assert mism == 0, f"{mism} hit IDs differ"
     err = np.abs(out - ref).max()
@@ -202,14 +202,15 @@ def test_host_side_errors(vs, ctx):
 # backward
 # ----------------------------------------------------------------------------
 
-def check_backward(vs, ctx, scene, cam, bg, rel):
+def check_backward(vs, ctx, scene, cam, bg, rel, flags=0):
     obj = vs.ShellObject.from_scene(ctx, scene)
     ws = vs.make_workspace(ctx, [obj], [cam])
-    out, hits = vs.render(ctx, obj, cam, ws, bg=bg)
+    out, hits = vs.render(ctx, obj, cam, ws, bg=bg, flags=flags)
     g = torch.randn((cam.height, cam.width, 3), device="cuda",
                     generator=torch.Generator("cuda").manual_seed(1))
-    grads = vs.render_backward(ctx, obj, cam, ws, hits, g, bg=bg)
-    ref = oracle.backward(scene, cam, hits.cpu().numpy(), g.cpu().numpy().astype(np.float64), bg=bg)
+    grads = vs.render_backward(ctx, obj, cam, ws, hits, g, bg=bg, flags=flags)
+    ref = oracle.backward(scene, cam, hits.cpu().numpy(), g.cpu().numpy().astype(np.float64), bg=bg,
+                          flags=flags)
     worst = 0.0
     for gg, rg in zip(grads, ref):
         scale = max(np.abs(rg).max(), 1e-30)
@@ -251,21 +252,48 @@ def test_backward_l2_loss_flag(vs, ctx):
         assert np.abs(gg.cpu().numpy() - rg).max() <= 1e-4 * np.abs(rg).max()
 
 
-def test_autograd_function(vs, ctx):
+@pytest.mark.parametrize("attenuate", [False, True])
+def test_autograd_function(vs, ctx, attenuate):
+    flags = vs.VS_FLAG_ALPHA_ATTEN if attenuate else 0
     (scene, cams), = synth.config_scene("c1", scale=0.25)
     cam = cams[0]
     obj = vs.ShellObject.from_scene(ctx, scene)
     ws = vs.make_workspace(ctx, [obj], [cam])
     tex = [t.clone().requires_grad_(True) for t in obj.textures]
     obj2 = vs.ShellObject(ctx, [dict(s, tex=t) for s, t in zip(obj.shells, tex)])
-    out = vs.VSRender.apply(ctx, obj2, cam, ws, (0.0, 0.0, 0.0), *tex)
+    out = vs.VSRender.apply(ctx, obj2, cam, ws, (0.0, 0.0, 0.0), flags, *tex)
     w = torch.randn_like(out[..., :3])
     (out[..., :3] * w).sum().backward()
-    out2, hits = vs.render(ctx, obj, cam, ws)
-    ref = vs.render_backward(ctx, obj, cam, ws, hits, w)
+    out2, hits = vs.render(ctx, obj, cam, ws, flags=flags)
+    assert torch.equal(out, out2)
+    ref = vs.render_backward(ctx, obj, cam, ws, hits, w, flags=flags)
     for t, r in zip(tex, ref):
         # same kernel, same hits: only the order of the float atomics differs
         assert (t.grad - r).abs().max().item() <= 1e-5 * r.abs().max().item()
+
+
+# ----------------------------------------------------------------------------
+# transparency attenuation (Sec. 3): alpha * (2 sigmoid(10 |v . n|) - 1)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,scale", [("c1", 1.0), ("c2", 0.01), ("c5", 0.0005)])
+def test_alpha_atten_forward_matches_oracle(vs, ctx, name, scale):
+    (scene, cams), = synth.config_scene(name, scale=scale, views=2)[:1]
+    cam = cams[-1]
+    bg = (0.3, 0.2, 0.1)
+    err, obj, ws, hits = check_forward(vs, ctx, scene, cam, bg=bg, flags=vs.VS_FLAG_ALPHA_ATTEN)
+    plain, plain_hits, *_ = gpu_render(vs, ctx, scene, cam, bg, obj=obj)
+    assert np.array_equal(plain_hits, hits)                 # visibility is unchanged
+    out, *_ = gpu_render(vs, ctx, scene, cam, bg, obj=obj, flags=vs.VS_FLAG_ALPHA_ATTEN)
+    assert np.abs(out - plain).max() > 1e-2                 # and the flag does something
+    print(f"{name} attenuated colour err {err:.2e}")
+
+
+@pytest.mark.parametrize("name,scale,rel", [("c1", 0.25, TOL_F32), ("c2", 0.005, 1e-4), ("c5", 0.0004, 1e-4)])
+def test_alpha_atten_backward_matches_oracle(vs, ctx, name, scale, rel):
+    (sc, cams), = synth.config_scene(name, scale=scale, views=1)[:1]
+    w, *_ = check_backward(vs, ctx, sc, cams[0], (0.2, 0.3, 0.4), rel, flags=vs.VS_FLAG_ALPHA_ATTEN)
+    print(f"{name} attenuated grad rel err {w:.2e}")
 
 
 # ----------------------------------------------------------------------------
@@ -314,19 +342,21 @@ def test_batch_forward_bit_identical_to_plain(vs, ctx):
         assert np.abs(it["out"].cpu().numpy() - ref).max() <= TOL_F16
 
 
-def test_batch_fused_backward_matches_plain(vs, ctx):
+@pytest.mark.parametrize("attenuate", [False, True])
+def test_batch_fused_backward_matches_plain(vs, ctx, attenuate):
+    flags = vs.VS_FLAG_ALPHA_ATTEN if attenuate else 0
     objs_cams = synth.config_scene("c4", scale=0.002, views=2)[:4]
     items, objs, ws = _batch_setup(vs, ctx, objs_cams, True)
-    vs.render_batch(ctx, items, ws, do_backward=True)
+    vs.render_batch(ctx, items, ws, do_backward=True, flags=flags)
     assert vs.read_stats(ws)["device_status"] == 0
     for obj, (sc, cams) in zip(objs, objs_cams):
         its = [it for it in items if it["obj"] is obj]
         plain = [torch.zeros_like(g) for g in its[0]["grads"]]
         for it in its:
             ws1 = vs.make_workspace(ctx, [obj], [it["cam"]])
-            out, hits = vs.render(ctx, obj, it["cam"], ws1)
+            out, hits = vs.render(ctx, obj, it["cam"], ws1, flags=flags)
             assert torch.equal(out, it["out"])
-            vs.render_backward(ctx, obj, it["cam"], ws1, hits, it["grad_rgb"], grads=plain)
+            vs.render_backward(ctx, obj, it["cam"], ws1, hits, it["grad_rgb"], grads=plain, flags=flags)
         for a, b in zip(its[0]["grads"], plain):
             assert torch.allclose(a, b, rtol=1e-4, atol=1e-6 * b.abs().max().item())
 
