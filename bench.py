@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-uneven", action="store_true", help="skip the uneven 32-object batch")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default work-unit sizes instead of autotuning them first")
     return p.parse_args()
 
 
@@ -139,7 +141,7 @@ def build_workload(args, device):
                 grads=grads, items=vs.BatchItems(items), ws=ws, H=H, W=W)
 
 
-def uneven_batch(ctx, device, stream, steps):
+def uneven_batch(ctx, device, stream, steps, autotune=True):
     """The uneven batch: 32 objects with k in {3,5,7,9}, 10k-1M faces per
     shell, 8 views each at 512^2 / 800^2 / 1024^2 / 1920x1080, 1024^2 SH1
     FP16 textures (pitch 16), fused fwd+bwd with the L2 loss -- one
@@ -176,6 +178,8 @@ def uneven_batch(ctx, device, stream, steps):
     def batched():
         vs.render_batch(ctx, bi, ws, do_backward=True, flags=flags, stream=stream)
 
+    tuning = (vs.autotune_batch(ctx, bi, ws, do_backward=True, flags=flags, stream=stream).as_dict()
+              if autotune else None)
     vs.read_stats(ws, reset=True)
     batched()
     st = vs.read_stats(ws, reset=True)
@@ -201,6 +205,7 @@ def uneven_batch(ctx, device, stream, steps):
                        "1024^2 SH1 FP16, fused fwd+bwd, L2 loss",
            "items": len(items), "triangles": int(sum(sum(s.tris.shape[0] for s in sc.shells) for sc, _ in objs)),
            "fragments_per_step": frags, "batched_ms": ms_b, "plain_ms": ms_p, "batched_vs_plain": ms_p / ms_b,
+           "tuning": tuning,
            "batched_fragments_per_s": frags / (ms_b * 1e-3), "batched_images_per_s": len(items) / (ms_b * 1e-3)}
     del ws, ws1, items, objects, bi
     torch.cuda.empty_cache()
@@ -347,6 +352,17 @@ def run_ours(args):
     def step_fwd():
         vs.render_batch(ctx, items, ws, do_backward=False, stream=stream)
 
+    # launch shapes (work-unit sizes, grid) timed on this very batch, untimed
+    # here; the tuning launches accumulate gradients and losses, so reset them
+    tuning = None
+    if not args.no_autotune:
+        tuning = {"fwd_bwd": vs.autotune_batch(ctx, items, ws, do_backward=True, flags=flags,
+                                               stream=stream).as_dict(),
+                  "fwd": vs.autotune_batch(ctx, items, ws, do_backward=False, stream=stream).as_dict()}
+        for g in wl["grads"]:
+            g.zero_()
+        wl["losses"].zero_()
+
     # fragments per step (device counter), status check
     vs.read_stats(ws, reset=True)
     step()
@@ -407,7 +423,8 @@ def run_ours(args):
                              "fwd_fragments_per_s": frags / (ms_plain_fwd * 1e-3)}
         res["batched_vs_plain"] = {"fwd_bwd": ms_plain / ms, "fwd": ms_plain_fwd / ms_fwd}
     if not args.no_uneven and rank == 0:
-        res["uneven_batch"] = uneven_batch(ctx, device, stream, max(3, args.steps // 10))
+        res["uneven_batch"] = uneven_batch(ctx, device, stream, max(3, args.steps // 10),
+                                           autotune=not args.no_autotune)
 
     if rank != 0:
         if ws_n > 1:
@@ -441,7 +458,8 @@ def run_ours(args):
                    "one persistent launch", "texel_storage": "f16", "views": n_views,
                    "image": f"{wl['W']}x{wl['H']}", "shells": wl["obj"].k,
                    "tris_per_shell": [int(s.tris.shape[0]) for s in wl["scene"].shells],
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws_n}"},
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws_n}",
+                   "tuning": tuning or "default (256 tris, 256 px, occupancy maximum)"},
         "images_per_s": n_views * ws_n / (ms * 1e-3),
         "fragments_per_step": frags,
         "fwd_only": {"fragments_per_s": frags * ws_n / (ms_fwd * 1e-3), "images_per_s": n_views * ws_n / (ms_fwd * 1e-3),

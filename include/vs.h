@@ -221,6 +221,65 @@ vs_status vs_render_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, co
                           int32_t do_backward, void* workspace, size_t ws_bytes, uint32_t flags,
                           vs_stream_t stream);
 
+/* --- batch tuning ---------------------------------------------------------------- */
+
+/* Launch shape of vs_render_batch.  The paper's renderer has no such knobs
+ * (a GL pipeline bins and tiles in fixed function); these are the work-unit
+ * ("tile") sizes of the persistent kernel and its grid. */
+typedef struct {
+  int32_t raster_tris;    /* triangles per raster work unit: a power of two in
+                             [32, 2048]                                       */
+  int32_t shade_pixels;   /* pixels per shading work unit: a power of two in
+                             [32, 4096]                                       */
+  int32_t blocks_per_sm;  /* persistent blocks per SM; 0 = the occupancy
+                             maximum, else 1 .. that maximum (larger values
+                             are clamped to it at launch)                     */
+  int32_t reserved;       /* must be 0                                        */
+} vs_tuning;
+
+/* The default: 256 triangles, 256 pixels, occupancy maximum. */
+#define VS_TUNING_DEFAULT_RASTER_TRIS 256
+#define VS_TUNING_DEFAULT_SHADE_PIXELS 256
+
+/* Sets / reads the tuning vs_render_batch uses for batches whose largest
+ * shell count is k_max (1 .. VS_MAX_SHELLS; setting also takes 0 = every
+ * k_max) and the given do_backward.  Until set, the default applies.  The tuning changes launch
+ * shape only: forward outputs stay bit-identical to vs_render.  The
+ * arguments are checked before the context (VS_ERR_INVALID_ARG), so a bad
+ * tuning is refused even with a NULL context.  The context's table is
+ * guarded by a mutex. */
+vs_status vs_set_batch_tuning(vs_ctx* ctx, int32_t do_backward, int32_t k_max, const vs_tuning* t);
+vs_status vs_get_batch_tuning(vs_ctx* ctx, int32_t do_backward, int32_t k_max, vs_tuning* t);
+
+/* Host-only coordinate-descent search over the tuning space: starting from
+ * `start`, it sweeps raster_tris over {64, 128, 256, 512, 1024},
+ * shade_pixels over {64, 128, 256, 512, 1024} and blocks_per_sm over
+ * 1 .. max_blocks_per_sm one coordinate at a time, moving to the cheapest
+ * value, until a sweep changes nothing (at most 4 sweeps).  `cost` returns
+ * the cost (e.g. milliseconds) of one configuration; each configuration is
+ * evaluated at most once.  Returns the cheapest configuration seen in *best
+ * and the number of cost calls in *evaluations (may be NULL).  A cost that
+ * is negative or NaN ends the search with VS_ERR_INVALID_ARG.  Needs no GPU;
+ * vs_autotune_batch runs it with a timed launch as the cost. */
+typedef double (*vs_cost_fn)(const vs_tuning* t, void* user);
+vs_status vs_tune_search(const vs_tuning* start, int32_t max_blocks_per_sm, vs_cost_fn cost, void* user,
+                         vs_tuning* best, int32_t* evaluations);
+
+/* Autotunes vs_render_batch for this batch: vs_tune_search from the current
+ * tuning, the cost of a configuration being the shortest of `repeats`
+ * (1 .. 16) CUDA-event-timed launches after one untimed one.  Stores the
+ * winner for (do_backward, largest k of the batch) in the context, returns
+ * it in *best (may be NULL) and synchronises the stream.  The launches are
+ * real: outputs are overwritten and, with do_backward, texel gradients and
+ * losses ACCUMULATE over all of them -- zero them before the next real step.
+ * The workspace's device counters (vs_read_stats) include these launches.
+ * Not capturable (it synchronises); tune first, then capture.
+ * Errors: as vs_render_batch; VS_ERR_INVALID_ARG for repeats out of range;
+ * a device error recorded by any launch ends the search with that status. */
+vs_status vs_autotune_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, const float* bg,
+                            int32_t do_backward, void* workspace, size_t ws_bytes, uint32_t flags,
+                            vs_stream_t stream, int32_t repeats, vs_tuning* best);
+
 /* --- allocation-free forward ------------------------------------------------- */
 
 /* vs_render for callers that cannot allocate device memory at all, and so

@@ -53,6 +53,19 @@ class vs_batch_item(ctypes.Structure):
                 ("grad_texels", ctypes.POINTER(ctypes.c_void_p)), ("loss", ctypes.c_void_p)]
 
 
+class vs_tuning(ctypes.Structure):
+    _fields_ = [("raster_tris", ctypes.c_int32), ("shade_pixels", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+VS_TUNING_DEFAULT_RASTER_TRIS = 256
+VS_TUNING_DEFAULT_SHADE_PIXELS = 256
+vs_cost_fn = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.POINTER(vs_tuning), ctypes.c_void_p)
+
+
 class vs_stats(ctypes.Structure):
     _fields_ = [("device_status", ctypes.c_int32), ("fragments", ctypes.c_uint64),
                 ("tris_front", ctypes.c_uint64), ("tris_culled_back", ctypes.c_uint64),
@@ -82,6 +95,12 @@ SIGNATURES = {
     "vs_render_batch": ([_P, ctypes.POINTER(vs_batch_item), _I, _P, _I, _P, _SZ, _U, _P], _I),
     "vs_read_stats": ([_P, _P, _I, ctypes.POINTER(vs_stats)], _I),
     "vs_render_noalloc": ([_P, _P, ctypes.POINTER(vs_camera), _P, _P, _P, _U, _P], _I),
+    "vs_set_batch_tuning": ([_P, _I, _I, ctypes.POINTER(vs_tuning)], _I),
+    "vs_get_batch_tuning": ([_P, _I, _I, ctypes.POINTER(vs_tuning)], _I),
+    "vs_tune_search": ([ctypes.POINTER(vs_tuning), _I, vs_cost_fn, _P, ctypes.POINTER(vs_tuning),
+                        ctypes.POINTER(_I)], _I),
+    "vs_autotune_batch": ([_P, ctypes.POINTER(vs_batch_item), _I, _P, _I, _P, _SZ, _U, _P, _I,
+                           ctypes.POINTER(vs_tuning)], _I),
 }
 
 _lib = None

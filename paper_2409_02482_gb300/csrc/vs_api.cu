@@ -5,12 +5,15 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "vs.h"
@@ -23,6 +26,9 @@ struct vs_ctx {
   int device;
   int num_sms;
   int persist_blocks[2][VS_MAX_SHELLS + 1];   // [backward][most shells] blocks per SM
+  std::mutex tune_mu;                          // guards tune / tune_set
+  vs_tuning tune[2][VS_MAX_SHELLS + 1];        // [backward][most shells]
+  bool tune_set[2][VS_MAX_SHELLS + 1];
 };
 
 struct vs_object {
@@ -99,6 +105,13 @@ struct ItemReq {
   float* loss;
 };
 
+// Work-unit sizes of one plan, in 32-wide rounds.  The plain launches run
+// one round per warp of a block, so they always use kWarps rounds.
+struct UnitShape {
+  int raster_rounds = kWarps;
+  int shade_rounds = kWarps;
+};
+
 struct Plan {
   size_t off_items, off_shells, off_done, off_stage, table_end, total;
   std::vector<DItem> items;
@@ -109,7 +122,9 @@ struct Plan {
 
 // Fills the plan; with ws == nullptr only sizes are computed.
 vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool clear_vis, uint32_t flags,
-                    char* ws, Plan& P) {
+                    char* ws, Plan& P, UnitShape shape = UnitShape()) {
+  const int raster_per_unit = 32 * shape.raster_rounds;
+  const int shade_per_unit = 32 * shape.shade_rounds;
   size_t off = sizeof(WsHeader);
   int S = 0;
   for (int j = 0; j < n; ++j) S += req[j].obj->k;
@@ -143,6 +158,8 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
     it.flags = (int)flags;
     it.do_bwd = do_bwd;
     it.stall = (flags & VS_FLAG_TEST_STALL) ? 1 : 0;
+    it.raster_rounds = shape.raster_rounds;
+    it.shade_rounds = shape.shade_rounds;
     it.bg[0] = bg ? bg[0] : 0.f; it.bg[1] = bg ? bg[1] : 0.f; it.bg[2] = bg ? bg[2] : 0.f;
     it.maxdeg = -1;
     const size_t HW = (size_t)c.width * c.height;
@@ -169,7 +186,7 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
       s.vsetup = reinterpret_cast<int4*>(ws ? ws + off : nullptr);
       off = align256(off + sizeof(int4) * (size_t)d.num_verts);
       it.setup_pre[i + 1] = it.setup_pre[i] + (d.num_verts + kSetupPerUnit - 1) / kSetupPerUnit;
-      it.raster_pre[i + 1] = it.raster_pre[i] + (d.num_tris + kRasterPerUnit - 1) / kRasterPerUnit;
+      it.raster_pre[i + 1] = it.raster_pre[i] + (d.num_tris + raster_per_unit - 1) / raster_per_unit;
     }
     it.vis = reinterpret_cast<unsigned long long*>(ws ? ws + off : nullptr);
     if (clear_vis) off = align256(off + sizeof(unsigned long long) * o.k * HW);
@@ -177,7 +194,7 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
     it.clear_units = clear_vis ? (int)((vis_words + kClearPerUnit - 1) / kClearPerUnit) : 0;
     it.units[PH_SETUP] = it.clear_units + it.setup_pre[o.k];
     it.units[PH_RASTER] = clear_vis ? it.raster_pre[o.k] : 0;
-    it.units[PH_SHADE] = (int)((HW + kShadePixels - 1) / kShadePixels);
+    it.units[PH_SHADE] = (int)((HW + shade_per_unit - 1) / shade_per_unit);
     sidx += o.k;
   }
   P.total = align256(off);
@@ -258,6 +275,129 @@ vs_status check_item(const vs_ctx* ctx, const vs_object* obj, const vs_camera* c
 vs_status set_device(const vs_ctx* ctx) {
   cudaError_t e = cudaSetDevice(ctx->device);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "cudaSetDevice");
+}
+
+// ---------------------------------------------------------------------------
+// batch tuning
+// ---------------------------------------------------------------------------
+bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+vs_status check_tuning(const vs_tuning* t) {
+  if (!t) return fail(VS_ERR_INVALID_ARG, "tuning is NULL");
+  if (!pow2_in(t->raster_tris, 32, 2048))
+    return fail(VS_ERR_INVALID_ARG, "raster_tris %d is not a power of two in [32, 2048]", t->raster_tris);
+  if (!pow2_in(t->shade_pixels, 32, 4096))
+    return fail(VS_ERR_INVALID_ARG, "shade_pixels %d is not a power of two in [32, 4096]", t->shade_pixels);
+  if (t->blocks_per_sm < 0 || t->blocks_per_sm > 64)
+    return fail(VS_ERR_INVALID_ARG, "blocks_per_sm %d out of [0, 64]", t->blocks_per_sm);
+  if (t->reserved != 0) return fail(VS_ERR_INVALID_ARG, "reserved field must be 0");
+  return VS_OK;
+}
+
+vs_tuning default_tuning() {
+  vs_tuning t{};
+  t.raster_tris = VS_TUNING_DEFAULT_RASTER_TRIS;
+  t.shade_pixels = VS_TUNING_DEFAULT_SHADE_PIXELS;
+  return t;
+}
+
+vs_tuning lookup_tuning(vs_ctx* ctx, int bwd, int kmax) {
+  std::lock_guard<std::mutex> g(ctx->tune_mu);
+  return ctx->tune_set[bwd][kmax] ? ctx->tune[bwd][kmax] : default_tuning();
+}
+
+UnitShape shape_of(const vs_tuning& t) {
+  UnitShape u;
+  u.raster_rounds = t.raster_tris / 32;
+  u.shade_rounds = t.shade_pixels / 32;
+  return u;
+}
+
+// Checks the batch and builds its plan (shared by vs_render_batch and the
+// autotuner).
+vs_status plan_batch(const vs_ctx* ctx, const vs_batch_item* items, int n, const float* bg, int do_backward,
+                     void* workspace, size_t ws_bytes, uint32_t flags, const vs_tuning& t, Plan& P, int* kmax) {
+  if (!ctx || !items) return fail(VS_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1) return fail(VS_ERR_INVALID_ARG, "n = %d < 1", n);
+  std::vector<ItemReq> req(n);
+  *kmax = 1;
+  for (int j = 0; j < n; ++j) {
+    const vs_batch_item& b = items[j];
+    vs_status s = check_item(ctx, b.obj, &b.cam);
+    if (s != VS_OK) return fail(s, "item %d: %s", j, g_err.c_str());
+    if (!b.out_rgba || (uintptr_t)b.out_rgba % 16) return fail(VS_ERR_INVALID_ARG, "item %d: out_rgba NULL or not 16-byte aligned", j);
+    if (do_backward) {
+      if (!b.grad_rgb || !b.grad_texels) return fail(VS_ERR_INVALID_ARG, "item %d: backward needs grad_rgb and grad_texels", j);
+      for (int i = 0; i < b.obj->k; ++i)
+        if (!b.grad_texels[i] || (uintptr_t)b.grad_texels[i] % 4) return fail(VS_ERR_INVALID_ARG, "item %d: grad_texels[%d] NULL or misaligned", j, i);
+    }
+    req[j] = ItemReq{b.obj, &b.cam, b.out_rgba, b.hits, b.grad_rgb, b.grad_texels, b.loss};
+    *kmax = std::max(*kmax, (int)b.obj->k);
+  }
+  char* ws = static_cast<char*>(workspace);
+  vs_status s = make_plan(req.data(), n, bg, do_backward ? 1 : 0, true, flags, ws, P, shape_of(t));
+  if (s != VS_OK) return s;
+  return check_ws(P, workspace, ws_bytes);
+}
+
+// Enqueues a planned batch: table upload + one persistent launch.
+vs_status launch_batch(vs_ctx* ctx, const Plan& P, void* workspace, int do_backward, int kmax, const vs_tuning& t,
+                       cudaStream_t st) {
+  char* ws = static_cast<char*>(workspace);
+  vs_status s = upload_table(P, ws, 1, st);
+  if (s != VS_OK) return s;
+  const int most = ctx->persist_blocks[do_backward ? 1 : 0][kmax];
+  const int bps = t.blocks_per_sm == 0 ? most : std::min(t.blocks_per_sm, most);
+  const long long spin_limit = 1ll << 24;   // ~ seconds with 200 ns sleeps
+  cudaError_t e = vsk::persistent(table_ref(P, ws), do_backward != 0, ctx->num_sms * bps, spin_limit, st);
+  return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_batch launch");
+}
+
+// Cost function of vs_autotune_batch: shortest of `repeats` timed launches.
+struct AutotuneJob {
+  vs_ctx* ctx;
+  const vs_batch_item* items;
+  int n;
+  const float* bg;
+  int do_backward;
+  void* ws;
+  size_t ws_bytes;
+  uint32_t flags;
+  cudaStream_t st;
+  int repeats;
+  cudaEvent_t ev[2];
+  vs_status status;       // first failure, reported after the search
+  std::string error;
+};
+
+double autotune_cost(const vs_tuning* t, void* user) {
+  AutotuneJob& J = *static_cast<AutotuneJob*>(user);
+  if (J.status != VS_OK) return NAN;
+  Plan P;
+  int kmax = 1;
+  auto bail = [&](vs_status s) {
+    J.status = s;
+    J.error = g_err;
+    return (double)NAN;
+  };
+  vs_status s = plan_batch(J.ctx, J.items, J.n, J.bg, J.do_backward, J.ws, J.ws_bytes, J.flags, *t, P, &kmax);
+  if (s != VS_OK) return bail(s);
+  float best = INFINITY;
+  for (int r = 0; r <= J.repeats; ++r) {
+    cudaError_t e = cudaEventRecord(J.ev[0], J.st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventRecord"));
+    if ((s = launch_batch(J.ctx, P, J.ws, J.do_backward, kmax, *t, J.st)) != VS_OK) return bail(s);
+    if ((e = cudaEventRecord(J.ev[1], J.st)) != cudaSuccess) return bail(cuda_fail(e, "cudaEventRecord"));
+    if ((e = cudaEventSynchronize(J.ev[1])) != cudaSuccess) return bail(cuda_fail(e, "cudaEventSynchronize"));
+    int32_t dev_status = 0;
+    if ((e = cudaMemcpy(&dev_status, J.ws, sizeof dev_status, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return bail(cuda_fail(e, "cudaMemcpy"));
+    if (dev_status != VS_OK) return bail(fail(dev_status, "a tuning launch recorded device status %d", dev_status));
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, J.ev[0], J.ev[1])) != cudaSuccess) return bail(cuda_fail(e, "cudaEventElapsedTime"));
+    if (r > 0) best = std::min(best, ms);   // launch 0 is the untimed warm-up
+  }
+  return best;
 }
 
 }  // namespace
@@ -387,33 +527,136 @@ vs_status vs_render_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, co
                           void* workspace, size_t ws_bytes, uint32_t flags, vs_stream_t stream) {
   if (!ctx || !items) return fail(VS_ERR_INVALID_ARG, "NULL argument");
   if (n < 1) return fail(VS_ERR_INVALID_ARG, "n = %d < 1", n);
-  std::vector<ItemReq> req(n);
-  for (int j = 0; j < n; ++j) {
-    const vs_batch_item& b = items[j];
-    vs_status s = check_item(ctx, b.obj, &b.cam);
-    if (s != VS_OK) return fail(s, "item %d: %s", j, g_err.c_str());
-    if (!b.out_rgba || (uintptr_t)b.out_rgba % 16) return fail(VS_ERR_INVALID_ARG, "item %d: out_rgba NULL or not 16-byte aligned", j);
-    if (do_backward) {
-      if (!b.grad_rgb || !b.grad_texels) return fail(VS_ERR_INVALID_ARG, "item %d: backward needs grad_rgb and grad_texels", j);
-      for (int i = 0; i < b.obj->k; ++i)
-        if (!b.grad_texels[i] || (uintptr_t)b.grad_texels[i] % 4) return fail(VS_ERR_INVALID_ARG, "item %d: grad_texels[%d] NULL or misaligned", j, i);
-    }
-    req[j] = ItemReq{b.obj, &b.cam, b.out_rgba, b.hits, b.grad_rgb, b.grad_texels, b.loss};
-  }
-  Plan P;
-  char* ws = static_cast<char*>(workspace);
-  vs_status s = make_plan(req.data(), n, bg, do_backward ? 1 : 0, true, flags, ws, P);
-  if (s != VS_OK) return s;
-  if ((s = check_ws(P, workspace, ws_bytes)) != VS_OK) return s;
-  if ((s = set_device(ctx)) != VS_OK) return s;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if ((s = upload_table(P, ws, 1, st)) != VS_OK) return s;
   int kmax = 1;
-  for (int j = 0; j < n; ++j) kmax = std::max(kmax, (int)items[j].obj->k);
-  const int grid = ctx->num_sms * ctx->persist_blocks[do_backward ? 1 : 0][kmax];
-  const long long spin_limit = 1ll << 24;   // ~ seconds with 200 ns sleeps
-  cudaError_t e = vsk::persistent(table_ref(P, ws), do_backward != 0, grid, spin_limit, st);
-  return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_batch launch");
+  for (int j = 0; j < n; ++j)
+    if (items[j].obj) kmax = std::max(kmax, std::min((int)items[j].obj->k, VS_MAX_SHELLS));
+  const vs_tuning t = lookup_tuning(ctx, do_backward ? 1 : 0, kmax);
+  Plan P;
+  vs_status s = plan_batch(ctx, items, n, bg, do_backward, workspace, ws_bytes, flags, t, P, &kmax);
+  if (s != VS_OK) return s;
+  if ((s = set_device(ctx)) != VS_OK) return s;
+  return launch_batch(ctx, P, workspace, do_backward, kmax, t, reinterpret_cast<cudaStream_t>(stream));
+}
+
+vs_status vs_set_batch_tuning(vs_ctx* ctx, int32_t do_backward, int32_t k_max, const vs_tuning* t) {
+  vs_status s = check_tuning(t);
+  if (s != VS_OK) return s;
+  if (k_max < 0 || k_max > VS_MAX_SHELLS) return fail(VS_ERR_INVALID_ARG, "k_max %d out of [0, %d]", k_max, VS_MAX_SHELLS);
+  if (!ctx) return fail(VS_ERR_INVALID_ARG, "ctx is NULL");
+  std::lock_guard<std::mutex> g(ctx->tune_mu);
+  const int b = do_backward ? 1 : 0;
+  for (int K = (k_max ? k_max : 1); K <= (k_max ? k_max : VS_MAX_SHELLS); ++K) {
+    ctx->tune[b][K] = *t;
+    ctx->tune_set[b][K] = true;
+  }
+  return VS_OK;
+}
+
+vs_status vs_get_batch_tuning(vs_ctx* ctx, int32_t do_backward, int32_t k_max, vs_tuning* t) {
+  if (!t) return fail(VS_ERR_INVALID_ARG, "tuning is NULL");
+  if (k_max < 1 || k_max > VS_MAX_SHELLS) return fail(VS_ERR_INVALID_ARG, "k_max %d out of [1, %d]", k_max, VS_MAX_SHELLS);
+  if (!ctx) return fail(VS_ERR_INVALID_ARG, "ctx is NULL");
+  *t = lookup_tuning(ctx, do_backward ? 1 : 0, k_max);
+  return VS_OK;
+}
+
+vs_status vs_tune_search(const vs_tuning* start, int32_t max_blocks_per_sm, vs_cost_fn cost, void* user,
+                         vs_tuning* best, int32_t* evaluations) {
+  if (!start || !cost || !best) return fail(VS_ERR_INVALID_ARG, "NULL argument");
+  vs_status s = check_tuning(start);
+  if (s != VS_OK) return s;
+  if (max_blocks_per_sm < 1 || max_blocks_per_sm > 64)
+    return fail(VS_ERR_INVALID_ARG, "max_blocks_per_sm %d out of [1, 64]", max_blocks_per_sm);
+  vs_tuning cur = *start;
+  if (cur.blocks_per_sm == 0 || cur.blocks_per_sm > max_blocks_per_sm) cur.blocks_per_sm = max_blocks_per_sm;
+  std::map<std::tuple<int, int, int>, double> seen;
+  int calls = 0;
+  bool bad = false;
+  auto eval = [&](const vs_tuning& t) -> double {
+    const auto key = std::make_tuple(t.raster_tris, t.shade_pixels, t.blocks_per_sm);
+    auto f = seen.find(key);
+    if (f != seen.end()) return f->second;
+    const double c = cost(&t, user);
+    ++calls;
+    if (!(c >= 0.0)) bad = true;
+    seen[key] = c;
+    return c;
+  };
+  double cur_cost = eval(cur);
+  static const int kSizes[] = {64, 128, 256, 512, 1024};
+  for (int sweep = 0; sweep < 4 && !bad; ++sweep) {
+    bool moved = false;
+    for (int dim = 0; dim < 3 && !bad; ++dim) {
+      const int nv = dim < 2 ? 5 : max_blocks_per_sm;
+      vs_tuning pick = cur;
+      double pick_cost = cur_cost;
+      for (int v = 0; v < nv && !bad; ++v) {
+        vs_tuning t = cur;
+        if (dim == 0) t.raster_tris = kSizes[v];
+        else if (dim == 1) t.shade_pixels = kSizes[v];
+        else t.blocks_per_sm = v + 1;
+        const double c = eval(t);
+        // a move needs a 1% gain, so timing noise does not walk the search
+        if (!bad && c < 0.99 * pick_cost) {
+          pick = t;
+          pick_cost = c;
+        }
+      }
+      if (!bad && (pick.raster_tris != cur.raster_tris || pick.shade_pixels != cur.shade_pixels ||
+                   pick.blocks_per_sm != cur.blocks_per_sm)) {
+        cur = pick;
+        cur_cost = pick_cost;
+        moved = true;
+      }
+    }
+    if (!moved) break;
+  }
+  if (evaluations) *evaluations = calls;
+  if (bad) return fail(VS_ERR_INVALID_ARG, "the cost function returned a negative or NaN cost");
+  *best = cur;
+  return VS_OK;
+}
+
+vs_status vs_autotune_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, const float* bg, int32_t do_backward,
+                            void* workspace, size_t ws_bytes, uint32_t flags, vs_stream_t stream, int32_t repeats,
+                            vs_tuning* best) {
+  if (repeats < 1 || repeats > 16) return fail(VS_ERR_INVALID_ARG, "repeats %d out of [1, 16]", repeats);
+  if (!ctx || !items) return fail(VS_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1) return fail(VS_ERR_INVALID_ARG, "n = %d < 1", n);
+  int kmax = 1;
+  for (int j = 0; j < n; ++j)
+    if (items[j].obj) kmax = std::max(kmax, std::min((int)items[j].obj->k, VS_MAX_SHELLS));
+  const int b = do_backward ? 1 : 0;
+  const vs_tuning start = lookup_tuning(ctx, b, kmax);
+  {  // validate the whole batch once before timing anything
+    Plan P;
+    int km = 1;
+    vs_status s = plan_batch(ctx, items, n, bg, do_backward, workspace, ws_bytes, flags, start, P, &km);
+    if (s != VS_OK) return s;
+  }
+  vs_status s = set_device(ctx);
+  if (s != VS_OK) return s;
+  AutotuneJob J{ctx, items, n, bg, do_backward, workspace, ws_bytes, flags & ~VS_FLAG_TEST_STALL,
+                reinterpret_cast<cudaStream_t>(stream), repeats, {nullptr, nullptr}, VS_OK, std::string()};
+  cudaError_t e = cudaEventCreate(&J.ev[0]);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  if ((e = cudaEventCreate(&J.ev[1])) != cudaSuccess) {
+    cudaEventDestroy(J.ev[0]);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  vs_tuning won{};
+  s = vs_tune_search(&start, ctx->persist_blocks[b][kmax], autotune_cost, &J, &won, nullptr);
+  cudaEventDestroy(J.ev[0]);
+  cudaEventDestroy(J.ev[1]);
+  if (J.status != VS_OK) return fail(J.status, "%s", J.error.c_str());
+  if (s != VS_OK) return s;
+  {
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    ctx->tune[b][kmax] = won;
+    ctx->tune_set[b][kmax] = true;
+  }
+  if (best) *best = won;
+  return VS_OK;
 }
 
 vs_status vs_read_stats(void* workspace, vs_stream_t stream, int32_t reset, vs_stats* out) {

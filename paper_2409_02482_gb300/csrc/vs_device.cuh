@@ -21,9 +21,13 @@ namespace vsd {
 constexpr int kThreads = 256;          // threads per block, all kernels
 constexpr int kWarps = kThreads / 32;  // a work unit is run by one warp
 constexpr int kSetupPerUnit = 1024;    // vertices per setup unit
-constexpr int kRasterPerUnit = 256;    // triangles per raster unit (rounds of 32)
+constexpr int kRasterPerUnit = 256;    // triangles per raster unit of the plain launches
 constexpr int kClearPerUnit = 16384;   // visibility words cleared per unit
-constexpr int kShadePixels = 256;      // pixels per shading unit (rounds of 32)
+constexpr int kShadePixels = 256;      // pixels per shading unit of the plain launches
+// The plain raster/shade launches run one unit per block, one 32-wide round
+// per warp, so their units are kWarps rounds; the persistent kernel takes
+// any size per item (DItem::raster_rounds, shade_rounds).
+static_assert(kRasterPerUnit == 32 * kWarps && kShadePixels == 32 * kWarps, "plain units = one round per warp");
 constexpr int kSmallMaxPixels = 64;    // bbox pixels walked by the warp's pair loop
 constexpr int kMaxShells = VS_MAX_SHELLS;
 constexpr int kTriBits = 27;           // triangle index bits in a packed fragment
@@ -79,7 +83,8 @@ struct alignas(16) DItem {
   unsigned long long* vis;     // [k, H*W] -- workspace
   int32_t k, shell0, maxdeg, clear_units;
   int32_t flags, do_bwd, stall;
-  int32_t pad1;
+  int32_t raster_rounds;       // raster unit = 32 * raster_rounds triangles
+  int32_t shade_rounds;        // shading unit = 32 * shade_rounds pixels
   int32_t units[4];            // per phase (3 used)
   int32_t setup_pre[kMaxShells + 1];
   int32_t raster_pre[kMaxShells + 1];

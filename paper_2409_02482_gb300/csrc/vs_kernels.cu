@@ -242,17 +242,17 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
   __syncwarp();   // the records are reused by the next round
 }
 
-// Raster unit: kRasterPerUnit triangles of one shell in rounds of 32; this
-// warp runs rounds [r0, r1).
-__device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* smem, int r0 = 0,
-                            int r1 = kRasterPerUnit / 32) {
+// Raster unit: 32 * it.raster_rounds triangles of one shell in rounds of 32;
+// this warp runs rounds [r0, r1).
+__device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* smem, int r0, int r1) {
   int i = 0;
   while (i + 1 < it.k && u >= it.raster_pre[i + 1]) ++i;
   const DShell& s = sh[i];
-  const int base = (u - it.raster_pre[i]) * kRasterPerUnit;
+  const int per_unit = 32 * it.raster_rounds;
+  const int base = (u - it.raster_pre[i]) * per_unit;
   unsigned long long* vis = it.vis + (size_t)i * it.cam.W * it.cam.H;
   RasterCounts rc = {0, 0, 0, 0, 0, 0};
-  const int rounds = min(r1, min(kRasterPerUnit, s.nt - base + 31) / 32);
+  const int rounds = min(r1, min(per_unit, s.nt - base + 31) / 32);
   for (int r = r0; r < rounds; ++r) raster_round(it, s, base + 32 * r, vis, smem, rc);
   warp_count(&hdr->front, rc.front);
   warp_count(&hdr->back, rc.back);
@@ -375,7 +375,7 @@ __device__ __noinline__ void atten_pass(const DCam& cam, const DShell* sh, int p
   }
 }
 
-// Shading unit: kShadePixels pixels, 32 per warp (lane = pixel).
+// Shading round: 32 consecutive pixels, one per lane.
 //  1. each lane reads its pixel's k visibility words (independent loads)
 //     and the warp compacts the hits into a fragment list in shared memory,
 //     pixel-major with shells ascending;
@@ -563,17 +563,17 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
   __syncwarp();   // the fragment list is rebuilt by the next round
 }
 
-// Shading unit: kShadePixels consecutive pixels in rounds of 32; this warp
-// runs rounds [r0, r1).  `wb` is the warp's shared-memory slice.
+// Shading unit: 32 * it.shade_rounds consecutive pixels in rounds of 32;
+// this warp runs rounds [r0, r1).  `wb` is the warp's shared-memory slice.
 template <bool BWD, bool FROM_HITS>
-__device__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* wb, int K, int r0 = 0,
-                           int r1 = kShadePixels / 32) {
+__device__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* wb, int K, int r0,
+                           int r1) {
   const unsigned FULL = 0xffffffffu;
   const int HW = it.cam.W * it.cam.H;
   unsigned nfrag = 0, bad = 0;
   float loss = 0.0f;
   for (int r = r0; r < r1; ++r) {
-    const int pbase = u * kShadePixels + 32 * r;
+    const int pbase = (u * it.shade_rounds + r) * 32;
     if (pbase >= HW) break;
     shade_round<BWD, FROM_HITS>(it, sh, pbase, wb, K, nfrag, bad, loss);
   }
@@ -696,9 +696,9 @@ __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS)
     const DShell* sh = tb.shells + it.shell0;
     switch (ph) {
       case PH_SETUP: unit_setup(it, sh, u); break;
-      case PH_RASTER: unit_raster(it, sh, u, hdr, smem); break;
+      case PH_RASTER: unit_raster(it, sh, u, hdr, smem, 0, it.raster_rounds); break;
       default:
-        unit_shade<BWD, false>(it, sh, u, hdr, smem, tb.kmax);
+        unit_shade<BWD, false>(it, sh, u, hdr, smem, tb.kmax, 0, it.shade_rounds);
     }
     __syncwarp();
     if (lane == 0) {

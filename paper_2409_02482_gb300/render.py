@@ -13,10 +13,11 @@ import torch
 
 from . import _abi
 from ._abi import (VS_FLAG_ALPHA_ATTEN, VS_FLAG_LOSS_L2, VS_TEX_RGBA_F32, VS_TEX_SH_F16, check, vs_batch_item,
-                   vs_camera, vs_shell_desc, vs_stats)
+                   vs_camera, vs_cost_fn, vs_shell_desc, vs_stats, vs_tuning)
 
 __all__ = ["Context", "ShellObject", "camera_struct", "workspace_size", "make_workspace",
            "render", "render_backward", "render_batch", "read_stats", "VSRender",
+           "tuning", "set_batch_tuning", "get_batch_tuning", "tune_search", "autotune_batch",
            "VS_FLAG_ALPHA_ATTEN", "VS_FLAG_LOSS_L2", "VS_TEX_RGBA_F32", "VS_TEX_SH_F16"]
 
 
@@ -202,6 +203,45 @@ def render_batch(ctx: Context, items, ws: torch.Tensor, bg=(0.0, 0.0, 0.0), do_b
     check(ctx.lib.vs_render_batch(ctx.handle, items.arr, items.n, bgv, int(do_backward), _ptr(ws),
                                   ws.numel(), flags, _stream(stream)))
     return items
+
+
+def tuning(raster_tris: int = 256, shade_pixels: int = 256, blocks_per_sm: int = 0) -> vs_tuning:
+    """A vs_tuning (work-unit sizes and grid of vs_render_batch)."""
+    return vs_tuning(raster_tris, shade_pixels, blocks_per_sm, 0)
+
+
+def set_batch_tuning(ctx: Context, t: vs_tuning, do_backward: bool = False, k_max: int = 0):
+    check(ctx.lib.vs_set_batch_tuning(ctx.handle, int(do_backward), k_max, ctypes.byref(t)))
+
+
+def get_batch_tuning(ctx: Context, do_backward: bool = False, k_max: int = 1) -> vs_tuning:
+    t = vs_tuning()
+    check(ctx.lib.vs_get_batch_tuning(ctx.handle, int(do_backward), k_max, ctypes.byref(t)))
+    return t
+
+
+def tune_search(start: vs_tuning, max_blocks_per_sm: int, cost) -> tuple:
+    """vs_tune_search with a Python cost(tuning) -> float; returns
+    (best vs_tuning, number of cost calls)."""
+    cb = vs_cost_fn(lambda t, _user: float(cost(t.contents)))
+    best, n = vs_tuning(), ctypes.c_int32(0)
+    check(_abi.load().vs_tune_search(ctypes.byref(start), max_blocks_per_sm, cb, None, ctypes.byref(best),
+                                     ctypes.byref(n)))
+    return best, n.value
+
+
+def autotune_batch(ctx: Context, items, ws: torch.Tensor, bg=(0.0, 0.0, 0.0), do_backward: bool = False,
+                   flags: int = 0, stream=None, repeats: int = 2) -> vs_tuning:
+    """vs_autotune_batch: times launch shapes on this batch and keeps the
+    fastest in the context.  Outputs are overwritten and gradients/losses
+    accumulate over the tuning launches."""
+    if not isinstance(items, BatchItems):
+        items = BatchItems(items)
+    bgv = (ctypes.c_float * 3)(*bg)
+    best = vs_tuning()
+    check(ctx.lib.vs_autotune_batch(ctx.handle, items.arr, items.n, bgv, int(do_backward), _ptr(ws), ws.numel(),
+                                    flags, _stream(stream), repeats, ctypes.byref(best)))
+    return best
 
 
 def read_stats(ws: torch.Tensor, reset: bool = False, stream=None) -> dict:

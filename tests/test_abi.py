@@ -37,6 +37,7 @@ def test_struct_layouts_match_header_sizes():
     assert ctypes.sizeof(_abi.vs_camera) == 76
     assert ctypes.sizeof(_abi.vs_shell_desc) == 72
     assert ctypes.sizeof(_abi.vs_stats) == 64
+    assert ctypes.sizeof(_abi.vs_tuning) == 16
 
 
 def test_create_without_gpu_reports_cuda_error(lib):
@@ -140,3 +141,74 @@ def test_workspace_size_rejects_bad_cameras(lib, w, h, znear):
     size = ctypes.c_size_t()
     assert lib.vs_workspace_size(_fake_ctx(), objs, cams, 1, 0, ctypes.byref(size)) == _abi.VS_ERR_INVALID_ARG
     lib.vs_free_shells(_fake_ctx(), obj)
+
+
+# ----------------------------------------------------------------------------
+# batch tuning: argument checks and the search itself (host logic only)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("fields", [(100, 256, 0), (256, 8192, 0), (16, 256, 0), (256, 256, -1),
+                                    (256, 256, 65), (256, 96, 0)])
+def test_set_batch_tuning_rejects_bad_values_without_a_context(lib, fields):
+    t = _abi.vs_tuning(*fields, 0)
+    assert lib.vs_set_batch_tuning(None, 0, 3, ctypes.byref(t)) == _abi.VS_ERR_INVALID_ARG
+    msg = lib.vs_last_error().decode()
+    assert "ctx" not in msg, msg                # refused for the tuning, not the context
+    good = _abi.vs_tuning(512, 128, 2, 0)
+    assert lib.vs_set_batch_tuning(None, 0, 3, ctypes.byref(good)) == _abi.VS_ERR_INVALID_ARG
+    assert "ctx" in lib.vs_last_error().decode()
+    assert lib.vs_set_batch_tuning(None, 0, 17, ctypes.byref(good)) == _abi.VS_ERR_INVALID_ARG
+    bad_reserved = _abi.vs_tuning(512, 128, 2, 7)
+    assert lib.vs_set_batch_tuning(None, 0, 3, ctypes.byref(bad_reserved)) == _abi.VS_ERR_INVALID_ARG
+
+
+def _search(lib, cost, start=(256, 256, 0), max_blocks=4):
+    from paper_2409_02482_gb300 import tune_search
+    calls = []
+
+    def f(t):
+        calls.append((t.raster_tris, t.shade_pixels, t.blocks_per_sm))
+        return cost(*calls[-1])
+    best, n = tune_search(_abi.vs_tuning(*start, 0), max_blocks, f)
+    assert n == len(calls)
+    assert len(set(calls)) == len(calls)        # no configuration costed twice
+    return (best.raster_tris, best.shade_pixels, best.blocks_per_sm), calls
+
+
+def test_tune_search_finds_separable_minimum(lib):
+    import math
+
+    def cost(r, s, b):
+        return 10 + (math.log2(r) - 9) ** 2 + 2 * (math.log2(s) - 6) ** 2 + 0.5 * (b - 3) ** 2
+    best, calls = _search(lib, cost)
+    assert best == (512, 64, 3)
+    assert len(calls) <= 3 * (5 + 5 + 4)
+
+
+def test_tune_search_follows_coupled_valley(lib):
+    # the best shade size depends on the block count: a second sweep is needed
+    def cost(r, s, b):
+        want_s = {1: 1024, 2: 512, 3: 256, 4: 128}[b]
+        return 5 + abs(s - want_s) / 256 + 3 * abs(b - 4) + (0 if r == 128 else 1)
+    best, calls = _search(lib, cost, start=(256, 1024, 1))
+    assert best == (128, 128, 4)
+
+
+def test_tune_search_ignores_gains_below_one_percent(lib):
+    # every move gains 0.5%: noise-level differences keep the start
+    def cost(r, s, b):
+        return 100.0 * (1 - 0.005 * (r != 256)) * (1 - 0.005 * (s != 256))
+    best, _ = _search(lib, cost, start=(256, 256, 2))
+    assert best == (256, 256, 2)
+
+
+def test_tune_search_stops_on_bad_cost(lib):
+    from paper_2409_02482_gb300 import tune_search
+    with pytest.raises(_abi.VSError) as e:
+        tune_search(_abi.vs_tuning(256, 256, 0, 0), 2, lambda t: float("nan"))
+    assert e.value.status == _abi.VS_ERR_INVALID_ARG
+    with pytest.raises(_abi.VSError):
+        tune_search(_abi.vs_tuning(256, 256, 0, 0), 2,
+                           lambda t: -1.0 if t.shade_pixels == 64 else 1.0)
+    with pytest.raises(_abi.VSError):
+        tune_search(_abi.vs_tuning(256, 256, 0, 0), 0, lambda t: 1.0)

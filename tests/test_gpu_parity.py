@@ -361,6 +361,70 @@ def test_batch_fused_backward_matches_plain(vs, ctx, attenuate):
             assert torch.allclose(a, b, rtol=1e-4, atol=1e-6 * b.abs().max().item())
 
 
+@pytest.mark.parametrize("raster_tris,shade_pixels,blocks", [(32, 32, 1), (2048, 4096, 0), (64, 1024, 2)])
+def test_batch_tuning_changes_launch_shape_not_results(vs, ctx, raster_tris, shade_pixels, blocks):
+    """Any unit size and grid gives the same forward bits as vs_render, and
+    the same fused gradients up to float-atomic order."""
+    objs_cams = synth.config_scene("c4", scale=0.002, views=2)[:3]
+    items, objs, ws = _batch_setup(vs, ctx, objs_cams, True)
+    kmax = max(o.k for o in objs)
+    t = vs.tuning(raster_tris, shade_pixels, blocks)
+    vs.set_batch_tuning(ctx, t, do_backward=True, k_max=kmax)
+    vs.set_batch_tuning(ctx, t, do_backward=False, k_max=kmax)
+    try:
+        got = vs.get_batch_tuning(ctx, do_backward=True, k_max=kmax)
+        assert (got.raster_tris, got.shade_pixels, got.blocks_per_sm) == (raster_tris, shade_pixels, blocks)
+        vs.render_batch(ctx, items, ws, do_backward=True)
+        assert vs.read_stats(ws)["device_status"] == 0
+        for obj in objs:
+            its = [it for it in items if it["obj"] is obj]
+            plain = [torch.zeros_like(g) for g in its[0]["grads"]]
+            for it in its:
+                ws1 = vs.make_workspace(ctx, [obj], [it["cam"]])
+                out, hits = vs.render(ctx, obj, it["cam"], ws1)
+                assert torch.equal(out, it["out"])
+                assert torch.equal(hits, it["hits"])
+                vs.render_backward(ctx, obj, it["cam"], ws1, hits, it["grad_rgb"], grads=plain)
+            for a, b in zip(its[0]["grads"], plain):
+                assert torch.allclose(a, b, rtol=1e-4, atol=1e-6 * b.abs().max().item())
+        # forward-only batch with the same shape
+        for it in items:
+            it["out"].fill_(float("nan"))
+        vs.render_batch(ctx, items, ws)
+        ref, ref_hits, _ = oracle.render(items[0]["scene"], items[0]["cam"])
+        assert np.array_equal(items[0]["hits"].cpu().numpy(), ref_hits)
+        assert np.abs(items[0]["out"].cpu().numpy() - ref).max() <= TOL_F16
+    finally:
+        vs.set_batch_tuning(ctx, vs.tuning(), do_backward=True, k_max=0)
+        vs.set_batch_tuning(ctx, vs.tuning(), do_backward=False, k_max=0)
+
+
+def test_autotune_batch_picks_and_keeps_a_valid_shape(vs, ctx):
+    objs_cams = synth.config_scene("c4", scale=0.002, views=2)[:4]
+    items, objs, ws = _batch_setup(vs, ctx, objs_cams, True)
+    kmax = max(o.k for o in objs)
+    try:
+        best = vs.autotune_batch(ctx, items, ws, do_backward=True, repeats=1)
+        assert best.raster_tris in (64, 128, 256, 512, 1024)
+        assert best.shade_pixels in (64, 128, 256, 512, 1024)
+        assert best.blocks_per_sm >= 1
+        kept = vs.get_batch_tuning(ctx, do_backward=True, k_max=kmax)
+        assert kept.as_dict() == best.as_dict()
+        assert vs.read_stats(ws, reset=True)["device_status"] == 0
+        # the tuned launch still renders what vs_render renders
+        vs.render_batch(ctx, items, ws, do_backward=True)
+        assert vs.read_stats(ws)["device_status"] == 0
+        for it in items[:3]:
+            ws1 = vs.make_workspace(ctx, [it["obj"]], [it["cam"]])
+            out, _ = vs.render(ctx, it["obj"], it["cam"], ws1)
+            assert torch.equal(out, it["out"])
+        from paper_2409_02482_gb300._abi import VSError
+        with pytest.raises(VSError):
+            vs.autotune_batch(ctx, items, ws, repeats=0)
+    finally:
+        vs.set_batch_tuning(ctx, vs.tuning(), do_backward=True, k_max=0)
+
+
 def test_batch_stall_hook_times_out_and_context_survives(vs, ctx):
     objs_cams = synth.config_scene("c4", scale=0.001, views=1)[:2]
     items, objs, ws = _batch_setup(vs, ctx, objs_cams, False)
