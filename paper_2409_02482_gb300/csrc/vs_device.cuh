@@ -34,16 +34,18 @@ constexpr int kTriBits = 27;           // triangle index bits in a packed fragme
 constexpr int kMaxTris = 1 << kTriBits;
 
 // Dynamic shared memory of a shading warp for up to K shells: N = 32 K
-// fragments; [frag float4 N][T, B float2 N][g float4 32][entry int N]
-// [alpha_w float N][lane u8 N].
-__host__ __device__ constexpr size_t shade_warp_bytes(int K) {
-  return (33 * (size_t)(32 * K) + 512 + 15) & ~(size_t)15;
+// fragments; [frag float4 N][entry u32 N][alpha_w float N][lane|shell u16 N]
+// and, for the adjoint only, [fractions float2 N][T float N] (carved in
+// shade_round).  The forward kernels reserve only the first part, which
+// keeps more of the SM's unified L1/shared storage as L1.
+__host__ __device__ constexpr size_t shade_warp_bytes(int K, bool bwd) {
+  return ((bwd ? 38 : 26) * (size_t)(32 * K) + 15) & ~(size_t)15;
 }
 constexpr size_t kRasterWarpBytes = 32 * (64 + 8 + 4);   // TriS, TriPos, start per triangle
-__host__ __device__ constexpr size_t warp_slice_bytes(int K) {
-  return shade_warp_bytes(K) > kRasterWarpBytes ? shade_warp_bytes(K) : kRasterWarpBytes;
+__host__ __device__ constexpr size_t warp_slice_bytes(int K, bool bwd) {
+  return shade_warp_bytes(K, bwd) > kRasterWarpBytes ? shade_warp_bytes(K, bwd) : kRasterWarpBytes;
 }
-__host__ __device__ constexpr size_t block_smem_bytes(int K) { return warp_slice_bytes(K) * kWarps; }
+__host__ __device__ constexpr size_t block_smem_bytes(int K, bool bwd) { return warp_slice_bytes(K, bwd) * kWarps; }
 
 // Phases of one item.  Large triangles are rasterized by the whole block
 // inside the raster unit that met them.

@@ -317,35 +317,37 @@ __device__ __forceinline__ Frag fetch_frag(const DShell& s, const Footprint& f, 
 #undef VS_CASE
 }
 
-// dL/d(values) of one fragment, scattered into its 4 texels.
+// Scatter of one fragment's adjoint.  d = (d0, d1, d2, d3) from the
+// per-pixel pass: RGBA: dL/d(r, g, b, alpha) of the texel values; SH:
+// dL/dz_r, dL/dz_g, dL/dz_b (z the pre-sigmoid colour sums) and dL/da (a
+// the alpha logit).  SH values get dz_ch * Y_m (v = unit ray direction).
 template <int DEG, int GV>
-__device__ __forceinline__ void adjoint_sh(const DShell& s, const Footprint& f, const float3 v,
-                                           const Frag& fr, float gcr, float gcg, float gcb, float ga) {
+__device__ __forceinline__ void scatter_sh(const DShell& s, const Footprint& f, const float3 v, const float4 d) {
   constexpr int NB = (DEG + 1) * (DEG + 1);
   constexpr int NCH = 1 + 3 * NB;
   float Y[16];
   sh_basis(DEG, v.x, v.y, v.z, Y);
   float dval[NCH];
-  dval[0] = ga * fr.a * (1.0f - fr.a);
-  const float dz[3] = {gcr * fr.r * (1.0f - fr.r), gcg * fr.g * (1.0f - fr.g), gcb * fr.b * (1.0f - fr.b)};
+  dval[0] = d.w;
 #pragma unroll
-  for (int m = 0; m < NB; ++m)
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) dval[1 + 3 * m + ch] = dz[ch] * Y[m];
+  for (int m = 0; m < NB; ++m) {
+    dval[1 + 3 * m] = d.x * Y[m];
+    dval[2 + 3 * m] = d.y * Y[m];
+    dval[3 + 3 * m] = d.z * Y[m];
+  }
   scatter_grad<NCH, GV>(s.grad, s.tw, s.pitch, f, dval);
 }
 
-__device__ __forceinline__ void adjoint_frag(const DShell& s, const Footprint& f, const float3 v,
-                                             const Frag& fr, float gcr, float gcg, float gcb, float ga) {
+__device__ __forceinline__ void scatter_frag(const DShell& s, const Footprint& f, const float3 v, const float4 d) {
   if (s.fmt == VS_TEX_RGBA_F32) {
-    const float dval[4] = {gcr, gcg, gcb, ga};
+    const float dval[4] = {d.x, d.y, d.z, d.w};
     if (s.gvec == 4) scatter_grad<4, 4>(s.grad, s.tw, s.pitch, f, dval);
     else if (s.gvec == 2) scatter_grad<4, 2>(s.grad, s.tw, s.pitch, f, dval);
     else scatter_grad<4, 1>(s.grad, s.tw, s.pitch, f, dval);
     return;
   }
 #define VS_CASE(D, V) \
-  case D * 16 + V: adjoint_sh<D, V>(s, f, v, fr, gcr, gcg, gcb, ga); return;
+  case D * 16 + V: scatter_sh<D, V>(s, f, v, d); return;
   switch (s.degree * 16 + s.gvec) {
     VS_CASE(0, 1) VS_CASE(0, 2) VS_CASE(0, 4)
     VS_CASE(1, 1) VS_CASE(1, 2) VS_CASE(1, 4)
@@ -356,20 +358,43 @@ __device__ __forceinline__ void adjoint_frag(const DShell& s, const Footprint& f
 #undef VS_CASE
 }
 
-// alpha_w of the fragments [0, total) of a shading round (lane-strided).
+// A footprint kept in shared memory between the fetch and the scatter:
+// x0 | y0 << 16 (texture sides <= 65536), and the fractions with the sign
+// bit set when the second tap equals the first (clamped at an edge).
+__device__ __forceinline__ void pack_footprint(const Footprint& f, unsigned& xy, float2& fr) {
+  xy = (unsigned)f.x0 | ((unsigned)f.y0 << 16);
+  fr.x = __uint_as_float(__float_as_uint(f.fx) | (f.x1 == f.x0 ? 0x80000000u : 0u));
+  fr.y = __uint_as_float(__float_as_uint(f.fy) | (f.y1 == f.y0 ? 0x80000000u : 0u));
+}
+
+__device__ __forceinline__ Footprint unpack_footprint(unsigned xy, float2 fr) {
+  Footprint f;
+  f.x0 = (int)(xy & 0xffffu);
+  f.y0 = (int)(xy >> 16);
+  const unsigned bx = __float_as_uint(fr.x), by = __float_as_uint(fr.y);
+  f.x1 = f.x0 + ((bx >> 31) ? 0 : 1);
+  f.y1 = f.y0 + ((by >> 31) ? 0 : 1);
+  f.fx = __uint_as_float(bx & 0x7fffffffu);
+  f.fy = __uint_as_float(by & 0x7fffffffu);
+  return f;
+}
+
+// alpha_w of the fragments [0, total) of a shading round (lane-strided),
+// from the packed (shell, triangle) entries.
 __device__ __noinline__ void atten_pass(const DCam& cam, const DShell* sh, int pbase, const int* sent,
-                                        const unsigned char* spl, float* saw, int total) {
+                                        const unsigned short* spl, float* saw, int total) {
   const int lane = threadIdx.x & 31;
   for (int j = lane; j < total; j += 32) {
     const int e = sent[j];
     const int i = e >> kTriBits, t = e & (kMaxTris - 1);
     const DShell& s = sh[i];
+    saw[j] = 1.0f;
     if (t >= s.nt) continue;
     const int* ip = s.tris + 3 * (size_t)t;
     const int idx[3] = {__ldg(ip), __ldg(ip + 1), __ldg(ip + 2)};
     if ((unsigned)idx[0] >= (unsigned)s.nv || (unsigned)idx[1] >= (unsigned)s.nv || (unsigned)idx[2] >= (unsigned)s.nv)
       continue;
-    const int pp = pbase + spl[j];
+    const int pp = pbase + (spl[j] & 31);
     const int y = pp / cam.W, x = pp - y * cam.W;
     saw[j] = alpha_atten(s.pos, idx, ray_dir(cam, x, y));
   }
@@ -381,16 +406,30 @@ __device__ __noinline__ void atten_pass(const DCam& cam, const DShell* sh, int p
 //     pixel-major with shells ascending;
 //  2. the warp shades the list 32 fragments at a time, every lane busy:
 //     perspective-correct UV, bilinear fetch at texel centres (Fig. 5), SH
-//     decode with the ray direction;
+//     decode with the ray direction (and, with the flag, alpha_w first);
+//     the adjoint keeps each footprint in shared memory;
 //  3. each lane composites its pixel front to back from shared memory
-//     (Eq. 6 with Eq. 1's transmittance); for the adjoint it also runs the
-//     back-to-front recurrence of B_i = A_i . g, A_i the colour seen from in
-//     front of shell i (B_i = alpha_i (c_i . g) + (1 - alpha_i) B_{i+1},
-//     B_k = bg . g);
-//  4. (adjoint) the warp scatters dL/d(texel) 32 fragments at a time:
-//     dL/dc_i = T_i alpha_i g, dL/dalpha_i = T_i (c_i . g - B_{i+1}).
+//     (Eq. 6 with Eq. 1's transmittance).  For the adjoint it then runs
+//     back to front with B_i = A_i . g, A_i the colour seen from in front of
+//     shell i (B_i = alpha_i (c_i . g) + (1 - alpha_i) B_{i+1}, B_k = bg . g):
+//     dL/dc_i = T_i alpha_i g, dL/dalpha_i = T_i (c_i . g - B_{i+1}), taken
+//     through alpha_w and the sigmoids to the texel-value space in place;
+//  4. (adjoint) the warp scatters dL/d(texel) 32 fragments at a time from
+//     the stored footprints -- no global loads, only reductions.
 // FROM_HITS: hits come from the public int32 buffer (standalone backward)
 // instead of the visibility words.
+//
+// Shared memory of the warp, N = 32 K fragments (shade_warp_bytes):
+//   frag float4 [N]  rgb + raw alpha (2 -> 3), then the adjoint d (3 -> 4)
+//   ent  u32    [N]  shell << 27 | triangle (1 -> 2), then x0 | y0 << 16
+//   aw   float  [N]  alpha_w (2 -> 3)
+//   pl   u16    [N]  lane | shell << 5 | kBadFrag for an invalid triangle
+// adjoint only:
+//   fxy  float2 [N]  footprint fractions (2 -> 4)
+//   T    float  [N]  transmittance in front of the fragment (3)
+constexpr unsigned kBadFrag = 0x8000u;
+static_assert(kMaxShells <= 16, "shell index takes 4 bits of the lane word");
+
 template <bool BWD, bool FROM_HITS>
 __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, int pbase, char* wb, int K,
                                             unsigned& nfrag, unsigned& bad, float& loss_acc) {
@@ -401,11 +440,12 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
   const int lane = threadIdx.x & 31;
   const int N = 32 * K;
   float4* sfrag = reinterpret_cast<float4*>(wb);
-  float2* stb = reinterpret_cast<float2*>(wb + 16 * (size_t)N);
-  float4* sg = reinterpret_cast<float4*>(wb + 24 * (size_t)N);
-  int* sent = reinterpret_cast<int*>(wb + 24 * (size_t)N + 512);
-  float* saw = reinterpret_cast<float*>(wb + 28 * (size_t)N + 512);
-  unsigned char* spl = reinterpret_cast<unsigned char*>(wb + 32 * (size_t)N + 512);
+  int* sent = reinterpret_cast<int*>(wb + 16 * (size_t)N);
+  unsigned* sxy = reinterpret_cast<unsigned*>(sent);
+  float* saw = reinterpret_cast<float*>(wb + 20 * (size_t)N);
+  unsigned short* spl = reinterpret_cast<unsigned short*>(wb + 24 * (size_t)N);
+  float2* sfxy = reinterpret_cast<float2*>(wb + 26 * (size_t)N);   // BWD only
+  float* sT = reinterpret_cast<float*>(wb + 34 * (size_t)N);       // BWD only
   const int p = pbase + lane;
   const bool pix_ok = p < HW;
 
@@ -451,49 +491,62 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
       const int i = __ffs(m) - 1;
       m &= m - 1;
       sent[c] = (i << kTriBits) | (scratch[i * 32 + lane] & (kMaxTris - 1));
-      spl[c] = (unsigned char)lane;
+      spl[c] = (unsigned short)(lane | (i << 5));
       ++c;
     }
   }
   __syncwarp();
 
-  // 2. fragments, 32 at a time
+  // 2a. transparency attenuation, in a pass of its own so that the fetch
+  //     loop below keeps its registers
+  const bool atten = (it.flags & VS_FLAG_ALPHA_ATTEN) != 0;
+  if (atten) {
+    atten_pass(it.cam, sh, pbase, sent, spl, saw, total);
+    __syncwarp();
+  }
+
+  // 2b. fragments, 32 at a time
   for (int j0 = 0; j0 < total; j0 += 32) {
     const int j = j0 + lane;
     if (j < total) {
       const int e = sent[j];
       const int i = e >> kTriBits, t = e & (kMaxTris - 1);
-      const int pp = pbase + spl[j];
+      const int pp = pbase + (spl[j] & 31);
       const DShell& s = sh[i];
       Frag fr = {0.f, 0.f, 0.f, 0.f};
       Tri Tr;
       int idx[3];
       if (t >= s.nt || load_tri_shade(s, t, Tr, idx) != 0) {
         bad = 1;
+        spl[j] |= (unsigned short)kBadFrag;   // invisible, and no adjoint
       } else {
         const int y = pp / W, x = pp - y * W;
         const float2 uv[3] = {__ldg(s.uv + idx[0]), __ldg(s.uv + idx[1]), __ldg(s.uv + idx[2])};
         const Footprint f = footprint(Tr, uv, s.tw, s.th, 256 * x + 128, 256 * y + 128);
+        if constexpr (BWD) {
+          unsigned xy;
+          float2 fxy;
+          pack_footprint(f, xy, fxy);
+          sxy[j] = xy;      // the entry is not read again
+          sfxy[j] = fxy;
+        }
         float3 v = make_float3(0.f, 0.f, 1.f);
         if (s.fmt == VS_TEX_SH_F16) v = ray_dir(it.cam, x, y);
         fr = fetch_frag(s, f, v);
         ++nfrag;
       }
-      // raw opacity here; the composite and the adjoint apply alpha_w
+      // raw opacity here; the composite applies alpha_w
       sfrag[j] = make_float4(fr.r, fr.g, fr.b, fr.a);
-      saw[j] = 1.0f;
+      if (!atten) saw[j] = 1.0f;
     }
   }
-  // 2b. transparency attenuation, in a pass of its own so that the fetch
-  //     loop above keeps its registers
-  if (it.flags & VS_FLAG_ALPHA_ATTEN) atten_pass(it.cam, sh, pbase, sent, spl, saw, total);
   __syncwarp();
 
   // 3. composite this pixel
   float T = 1.0f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
   for (int c = 0; c < cnt; ++c) {
     const float4 f = sfrag[start + c];
-    if constexpr (BWD) stb[start + c].x = T;
+    if constexpr (BWD) sT[start + c] = T;
     const float a = f.w * saw[start + c];
     const float ta = T * a;
     Cr = fmaf(ta, f.x, Cr);
@@ -520,42 +573,46 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
         gb = 2.0f * inv * db;
       }
     }
+    // back to front; the colour and opacity of each fragment are replaced
+    // by the adjoint in texel-value space
     float B = it.bg[0] * gr + it.bg[1] * gg + it.bg[2] * gb;
     for (int c = cnt - 1; c >= 0; --c) {
-      stb[start + c].y = B;
       const float4 f = sfrag[start + c];
-      B = fmaf(f.w * saw[start + c], f.x * gr + f.y * gg + f.z * gb - B, B);
+      const float aw = saw[start + c];
+      const float a = f.w * aw;
+      const float cg = f.x * gr + f.y * gg + f.z * gb;
+      const float Tc = sT[start + c];
+      const float ta = Tc * a;
+      // dL/d(raw alpha): alpha_w is a constant of the texels
+      const float ga = Tc * (cg - B) * aw;
+      const DShell& s = sh[(spl[start + c] >> 5) & 15];
+      float4 d;
+      if (s.fmt == VS_TEX_RGBA_F32) {
+        d = make_float4(ta * gr, ta * gg, ta * gb, ga);
+      } else {
+        d = make_float4(ta * gr * (f.x * (1.0f - f.x)), ta * gg * (f.y * (1.0f - f.y)),
+                        ta * gb * (f.z * (1.0f - f.z)), ga * (f.w * (1.0f - f.w)));
+      }
+      sfrag[start + c] = d;
+      B = fmaf(a, cg - B, B);
     }
-    sg[lane] = make_float4(gr, gg, gb, 0.0f);
     __syncwarp();
 
-    // 4. adjoint, 32 fragments at a time
+    // 4. adjoint scatter, 32 fragments at a time
     for (int j0 = 0; j0 < total; j0 += 32) {
       const int j = j0 + lane;
       if (j < total) {
-        const int e = sent[j];
-        const int i = e >> kTriBits, t = e & (kMaxTris - 1);
-        const int pl = spl[j];
-        const int pp = pbase + pl;
-        const DShell& s = sh[i];
-        Tri Tr;
-        int idx[3];
-        if (t < s.nt && load_tri_shade(s, t, Tr, idx) == 0) {
+        const unsigned pl = spl[j];
+        if (pl & kBadFrag) continue;
+        const DShell& s = sh[(pl >> 5) & 15];
+        const Footprint f = unpack_footprint(sxy[j], sfxy[j]);
+        float3 v = make_float3(0.f, 0.f, 1.f);
+        if (s.fmt == VS_TEX_SH_F16) {
+          const int pp = pbase + (int)(pl & 31);
           const int y = pp / W, x = pp - y * W;
-          const float2 uv[3] = {__ldg(s.uv + idx[0]), __ldg(s.uv + idx[1]), __ldg(s.uv + idx[2])};
-          const Footprint f = footprint(Tr, uv, s.tw, s.th, 256 * x + 128, 256 * y + 128);
-          float3 v = make_float3(0.f, 0.f, 1.f);
-          if (s.fmt == VS_TEX_SH_F16) v = ray_dir(it.cam, x, y);
-          const float4 q = sfrag[j];
-          const Frag fr = {q.x, q.y, q.z, q.w};
-          const float aw = saw[j];
-          const float2 tbv = stb[j];
-          const float4 g = sg[pl];
-          // composite opacity alpha = raw * alpha_w; alpha_w is texel-independent
-          const float ta = tbv.x * (fr.a * aw);
-          const float ga = tbv.x * (fr.r * g.x + fr.g * g.y + fr.b * g.z - tbv.y) * aw;
-          adjoint_frag(s, f, v, fr, ta * g.x, ta * g.y, ta * g.z, ga);
+          v = ray_dir(it.cam, x, y);
         }
+        scatter_frag(s, f, v, sfrag[j]);
       }
     }
   }
@@ -606,8 +663,8 @@ __global__ void __launch_bounds__(kThreads) k_upload(char* ws, const __grid_cons
 extern __shared__ __align__(16) char vs_smem[];
 
 // Shared-memory slice of the calling warp (every phase carves the same way).
-__device__ __forceinline__ char* warp_smem(int K) {
-  return vs_smem + (threadIdx.x >> 5) * warp_slice_bytes(K);
+__device__ __forceinline__ char* warp_smem(int K, bool bwd) {
+  return vs_smem + (threadIdx.x >> 5) * warp_slice_bytes(K, bwd);
 }
 
 // Plain per-phase kernels.  Setup: each warp runs one unit (8 per block).
@@ -622,14 +679,15 @@ __global__ void __launch_bounds__(kThreads) k_setup(TableRef tb, int item) {
 __global__ void __launch_bounds__(kThreads) k_raster(TableRef tb, int item) {
   const DItem& it = tb.items[item];
   const int w = threadIdx.x >> 5;
-  unit_raster(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, warp_smem(tb.kmax), w, w + 1);
+  unit_raster(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, vs_smem + w * kRasterWarpBytes, w, w + 1);
 }
 
 template <bool BWD, bool FROM_HITS>
 __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS) k_shade(TableRef tb, int item) {
   const DItem& it = tb.items[item];
   const int w = threadIdx.x >> 5;
-  unit_shade<BWD, FROM_HITS>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, warp_smem(tb.kmax), tb.kmax, w, w + 1);
+  unit_shade<BWD, FROM_HITS>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, warp_smem(tb.kmax, BWD), tb.kmax, w,
+                             w + 1);
 }
 
 // Bounded wait (one lane) for `target` completions; false on timeout or
@@ -661,7 +719,7 @@ __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS)
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   WsHeader* hdr = tb.hdr;
-  char* smem = warp_smem(tb.kmax);
+  char* smem = warp_smem(tb.kmax, BWD);
   for (;;) {
     int g = 0;
     if (lane == 0) g = *(volatile int*)&hdr->abort ? tb.total : (int)atomicAdd(&hdr->next_unit, 1u);
@@ -725,41 +783,41 @@ int plain_backward_launches(const int units[4]) { return (units[0] > 0) + (units
 
 cudaError_t plain_forward(const TableRef& tb, const int units[4], cudaStream_t st) {
   const int W = vsd::kWarps;
-  const size_t smem = vsd::block_smem_bytes(tb.kmax);
   if (units[0]) vsd::k_setup<<<(units[0] + W - 1) / W, vsd::kThreads, 0, st>>>(tb, 0);
-  if (units[1]) vsd::k_raster<<<units[1], vsd::kThreads, smem, st>>>(tb, 0);
-  if (units[2]) vsd::k_shade<false, false><<<units[2], vsd::kThreads, smem, st>>>(tb, 0);
+  if (units[1]) vsd::k_raster<<<units[1], vsd::kThreads, vsd::kRasterWarpBytes * W, st>>>(tb, 0);
+  if (units[2])
+    vsd::k_shade<false, false><<<units[2], vsd::kThreads, vsd::block_smem_bytes(tb.kmax, false), st>>>(tb, 0);
   return cudaGetLastError();
 }
 
 cudaError_t plain_backward(const TableRef& tb, const int units[4], cudaStream_t st) {
   const int W = vsd::kWarps;
   if (units[0]) vsd::k_setup<<<(units[0] + W - 1) / W, vsd::kThreads, 0, st>>>(tb, 0);
-  if (units[2]) vsd::k_shade<true, true><<<units[2], vsd::kThreads, vsd::block_smem_bytes(tb.kmax), st>>>(tb, 0);
+  if (units[2]) vsd::k_shade<true, true><<<units[2], vsd::kThreads, vsd::block_smem_bytes(tb.kmax, true), st>>>(tb, 0);
   return cudaGetLastError();
 }
 
 cudaError_t persistent(const TableRef& tb, bool bwd, int grid, long long spin_limit, cudaStream_t st) {
-  const size_t smem = vsd::block_smem_bytes(tb.kmax);
+  const size_t smem = vsd::block_smem_bytes(tb.kmax, bwd);
   if (bwd) vsd::k_persistent<true><<<grid, vsd::kThreads, smem, st>>>(tb, spin_limit);
   else vsd::k_persistent<false><<<grid, vsd::kThreads, smem, st>>>(tb, spin_limit);
   return cudaGetLastError();
 }
 
 cudaError_t persistent_occupancy(bool bwd, int kmax, int* blocks_per_sm) {
-  const size_t smem = vsd::block_smem_bytes(kmax);
+  const size_t smem = vsd::block_smem_bytes(kmax, bwd);
   if (bwd) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, vsd::k_persistent<true>, vsd::kThreads, smem);
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, vsd::k_persistent<false>, vsd::kThreads, smem);
 }
 
 cudaError_t configure_kernels() {
-  const int most = (int)vsd::block_smem_bytes(vsd::kMaxShells);
+  const int most_f = (int)vsd::block_smem_bytes(vsd::kMaxShells, false);
+  const int most_b = (int)vsd::block_smem_bytes(vsd::kMaxShells, true);
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(vsd::k_raster, cudaFuncAttributeMaxDynamicSharedMemorySize, most)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(vsd::k_shade<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(vsd::k_shade<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(vsd::k_persistent<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most)) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(vsd::k_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  if ((e = cudaFuncSetAttribute(vsd::k_shade<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_f)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(vsd::k_shade<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_b)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(vsd::k_persistent<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_f)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(vsd::k_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_b);
 }
 
 }  // namespace vsk
