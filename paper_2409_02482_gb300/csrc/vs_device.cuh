@@ -33,13 +33,26 @@ constexpr int kMaxShells = VS_MAX_SHELLS;
 constexpr int kTriBits = 27;           // triangle index bits in a packed fragment
 constexpr int kMaxTris = 1 << kTriBits;
 
-// Dynamic shared memory of a shading warp for up to K shells: N = 32 K
-// fragments; [frag float4 N][entry u32 N][alpha_w float N][lane|shell u16 N]
-// and, for the adjoint only, [fractions float2 N][T float N] (carved in
-// shade_round).  The forward kernels reserve only the first part, which
-// keeps more of the SM's unified L1/shared storage as L1.
+// Dynamic shared memory of a shading warp for up to K shells: a fragment
+// list of frag_cap(K, bwd) entries -- [frag float4][entry u32][alpha_w
+// float][lane|shell u16] and, for the adjoint only, [fractions float2][T
+// float] -- and, when the list is shorter than a round's worst case (32 K),
+// the round's hit table (32 K ints) in front of it (carved in shade_round).
+// The forward list holds the worst case (one pass per round).  The adjoint
+// list is capped at kFragCap: a round whose fragments do not fit runs in
+// several passes, and the smaller slice leaves more of the SM's unified
+// L1/shared storage to L1.
+#ifndef VS_FRAG_CAP
+#define VS_FRAG_CAP 128
+#endif
+constexpr int kFragCap = VS_FRAG_CAP;
+static_assert(kFragCap % 32 == 0, "fragment list in whole 32-wide rounds");
+__host__ __device__ constexpr int frag_cap(int K, bool bwd) {
+  return (bwd && kFragCap < 32 * K) ? kFragCap : 32 * K;
+}
 __host__ __device__ constexpr size_t shade_warp_bytes(int K, bool bwd) {
-  return ((bwd ? 38 : 26) * (size_t)(32 * K) + 15) & ~(size_t)15;
+  return ((frag_cap(K, bwd) < 32 * K ? 128 * (size_t)K : 0) + (bwd ? 38 : 26) * (size_t)frag_cap(K, bwd) + 15) &
+         ~(size_t)15;
 }
 constexpr size_t kRasterWarpBytes = 32 * (64 + 8 + 4);   // TriS, TriPos, start per triangle
 __host__ __device__ constexpr size_t warp_slice_bytes(int K, bool bwd) {

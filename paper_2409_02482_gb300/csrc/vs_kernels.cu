@@ -402,33 +402,41 @@ __device__ __noinline__ void atten_pass(const DCam& cam, const DShell* sh, int p
 
 // Shading round: 32 consecutive pixels, one per lane.
 //  1. each lane reads its pixel's k visibility words (independent loads)
-//     and the warp compacts the hits into a fragment list in shared memory,
-//     pixel-major with shells ascending;
+//     into a per-shell hit table.  The round then runs in passes over
+//     consecutive lane ranges whose fragments fit the warp's list (one
+//     pass when the list holds 32 K; kFragCap >= kMaxShells, so every pass
+//     takes at least one pixel); each pass compacts its lanes' hits into
+//     the list, pixel-major with shells ascending;
 //  2. the warp shades the list 32 fragments at a time, every lane busy:
 //     perspective-correct UV, bilinear fetch at texel centres (Fig. 5), SH
 //     decode with the ray direction (and, with the flag, alpha_w first);
 //     the adjoint keeps each footprint in shared memory;
-//  3. each lane composites its pixel front to back from shared memory
-//     (Eq. 6 with Eq. 1's transmittance).  For the adjoint it then runs
-//     back to front with B_i = A_i . g, A_i the colour seen from in front of
-//     shell i (B_i = alpha_i (c_i . g) + (1 - alpha_i) B_{i+1}, B_k = bg . g):
-//     dL/dc_i = T_i alpha_i g, dL/dalpha_i = T_i (c_i . g - B_{i+1}), taken
-//     through alpha_w and the sigmoids to the texel-value space in place;
+//  3. each lane of the pass composites its pixel front to back from shared
+//     memory (Eq. 6 with Eq. 1's transmittance).  For the adjoint it then
+//     runs back to front with B_i = A_i . g, A_i the colour seen from in
+//     front of shell i (B_i = alpha_i (c_i . g) + (1 - alpha_i) B_{i+1},
+//     B_k = bg . g): dL/dc_i = T_i alpha_i g, dL/dalpha_i = T_i (c_i . g -
+//     B_{i+1}), taken through alpha_w and the sigmoids to the texel-value
+//     space in place;
 //  4. (adjoint) the warp scatters dL/d(texel) 32 fragments at a time from
 //     the stored footprints -- no global loads, only reductions.
 // FROM_HITS: hits come from the public int32 buffer (standalone backward)
 // instead of the visibility words.
 //
-// Shared memory of the warp, N = 32 K fragments (shade_warp_bytes):
-//   frag float4 [N]  rgb + raw alpha (2 -> 3), then the adjoint d (3 -> 4)
-//   ent  u32    [N]  shell << 27 | triangle (1 -> 2), then x0 | y0 << 16
-//   aw   float  [N]  alpha_w (2 -> 3)
-//   pl   u16    [N]  lane | shell << 5 | kBadFrag for an invalid triangle
+// Shared memory of the warp (shade_warp_bytes), C = frag_cap(K, BWD):
+//   hit  int    [32 K]  triangle per (shell, lane) of the round (1); own
+//                       space only when C < 32 K, else it is the frag area,
+//                       which the single pass overwrites after the fill
+//   frag float4 [C]  rgb + raw alpha (2 -> 3), then the adjoint d (3 -> 4)
+//   ent  u32    [C]  shell << 27 | triangle (1 -> 2), then x0 | y0 << 16
+//   aw   float  [C]  alpha_w (2 -> 3)
+//   pl   u16    [C]  lane | shell << 5 | kBadFrag for an invalid triangle
 // adjoint only:
-//   fxy  float2 [N]  footprint fractions (2 -> 4)
-//   T    float  [N]  transmittance in front of the fragment (3)
+//   fxy  float2 [C]  footprint fractions (2 -> 4)
+//   T    float  [C]  transmittance in front of the fragment (3)
 constexpr unsigned kBadFrag = 0x8000u;
 static_assert(kMaxShells <= 16, "shell index takes 4 bits of the lane word");
+static_assert(kFragCap >= kMaxShells, "a pixel's fragments must fit one pass");
 
 template <bool BWD, bool FROM_HITS>
 __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, int pbase, char* wb, int K,
@@ -438,20 +446,21 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
   const int HW = W * H;
   const int k = it.k;
   const int lane = threadIdx.x & 31;
-  const int N = 32 * K;
-  float4* sfrag = reinterpret_cast<float4*>(wb);
-  int* sent = reinterpret_cast<int*>(wb + 16 * (size_t)N);
+  const int C = frag_cap(K, BWD);
+  const bool own_table = C < 32 * K;
+  int* scratch = reinterpret_cast<int*>(wb);
+  char* lb = own_table ? wb + 128 * (size_t)K : wb;
+  float4* sfrag = reinterpret_cast<float4*>(lb);
+  int* sent = reinterpret_cast<int*>(lb + 16 * C);
   unsigned* sxy = reinterpret_cast<unsigned*>(sent);
-  float* saw = reinterpret_cast<float*>(wb + 20 * (size_t)N);
-  unsigned short* spl = reinterpret_cast<unsigned short*>(wb + 24 * (size_t)N);
-  float2* sfxy = reinterpret_cast<float2*>(wb + 26 * (size_t)N);   // BWD only
-  float* sT = reinterpret_cast<float*>(wb + 34 * (size_t)N);       // BWD only
+  float* saw = reinterpret_cast<float*>(lb + 20 * C);
+  unsigned short* spl = reinterpret_cast<unsigned short*>(lb + 24 * C);
+  float2* sfxy = reinterpret_cast<float2*>(lb + 26 * C);   // BWD only
+  float* sT = reinterpret_cast<float*>(lb + 34 * C);       // BWD only
   const int p = pbase + lane;
   const bool pix_ok = p < HW;
 
-  // 1. hits of this pixel (triangle ids parked in the fragment area, which
-  //    step 2 overwrites only after the list is built)
-  int* scratch = reinterpret_cast<int*>(sfrag);
+  // 1. hits of this pixel
   unsigned mask = 0;
   // eight shells at a time: all loads of a group are in flight together
   for (int i0 = 0; i0 < k; i0 += 8) {
@@ -482,142 +491,153 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
     const int v = __shfl_up_sync(FULL, pre, o);
     if (lane >= o) pre += v;
   }
-  const int total = __shfl_sync(FULL, pre, 31);
   const int start = pre - cnt;
-  {
-    unsigned m = mask;
-    int c = start;
-    while (m) {
-      const int i = __ffs(m) - 1;
-      m &= m - 1;
-      sent[c] = (i << kTriBits) | (scratch[i * 32 + lane] & (kMaxTris - 1));
-      spl[c] = (unsigned short)(lane | (i << 5));
-      ++c;
-    }
-  }
-  __syncwarp();
-
-  // 2a. transparency attenuation, in a pass of its own so that the fetch
-  //     loop below keeps its registers
   const bool atten = (it.flags & VS_FLAG_ALPHA_ATTEN) != 0;
-  if (atten) {
-    atten_pass(it.cam, sh, pbase, sent, spl, saw, total);
-    __syncwarp();
-  }
-
-  // 2b. fragments, 32 at a time
-  for (int j0 = 0; j0 < total; j0 += 32) {
-    const int j = j0 + lane;
-    if (j < total) {
-      const int e = sent[j];
-      const int i = e >> kTriBits, t = e & (kMaxTris - 1);
-      const int pp = pbase + (spl[j] & 31);
-      const DShell& s = sh[i];
-      Frag fr = {0.f, 0.f, 0.f, 0.f};
-      Tri Tr;
-      int idx[3];
-      if (t >= s.nt || load_tri_shade(s, t, Tr, idx) != 0) {
-        bad = 1;
-        spl[j] |= (unsigned short)kBadFrag;   // invisible, and no adjoint
-      } else {
-        const int y = pp / W, x = pp - y * W;
-        const float2 uv[3] = {__ldg(s.uv + idx[0]), __ldg(s.uv + idx[1]), __ldg(s.uv + idx[2])};
-        const Footprint f = footprint(Tr, uv, s.tw, s.th, 256 * x + 128, 256 * y + 128);
-        if constexpr (BWD) {
-          unsigned xy;
-          float2 fxy;
-          pack_footprint(f, xy, fxy);
-          sxy[j] = xy;      // the entry is not read again
-          sfxy[j] = fxy;
-        }
-        float3 v = make_float3(0.f, 0.f, 1.f);
-        if (s.fmt == VS_TEX_SH_F16) v = ray_dir(it.cam, x, y);
-        fr = fetch_frag(s, f, v);
-        ++nfrag;
-      }
-      // raw opacity here; the composite applies alpha_w
-      sfrag[j] = make_float4(fr.r, fr.g, fr.b, fr.a);
-      if (!atten) saw[j] = 1.0f;
-    }
-  }
   __syncwarp();
 
-  // 3. composite this pixel
-  float T = 1.0f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
-  for (int c = 0; c < cnt; ++c) {
-    const float4 f = sfrag[start + c];
-    if constexpr (BWD) sT[start + c] = T;
-    const float a = f.w * saw[start + c];
-    const float ta = T * a;
-    Cr = fmaf(ta, f.x, Cr);
-    Cg = fmaf(ta, f.y, Cg);
-    Cb = fmaf(ta, f.z, Cb);
-    T = T * (1.0f - a);
-  }
-  const float outr = fmaf(T, it.bg[0], Cr), outg = fmaf(T, it.bg[1], Cg), outb = fmaf(T, it.bg[2], Cb);
-  if (pix_ok && it.out) it.out[p] = make_float4(outr, outg, outb, 1.0f - T);
-  float loss = 0.0f;
-  if constexpr (BWD) {
-    float gr = 0.f, gg = 0.f, gb = 0.f;
-    if (pix_ok) {
-      const float* gp = it.grad_rgb + 3 * (size_t)p;
-      gr = __ldg(gp);
-      gg = __ldg(gp + 1);
-      gb = __ldg(gp + 2);
-      if (it.flags & VS_FLAG_LOSS_L2) {
-        const float dr = outr - gr, dg = outg - gg, db = outb - gb;
-        const float inv = 1.0f / (3.0f * (float)HW);
-        loss = (dr * dr + dg * dg + db * db) * inv;
-        gr = 2.0f * inv * dr;
-        gg = 2.0f * inv * dg;
-        gb = 2.0f * inv * db;
+  for (int l0 = 0; l0 < 32;) {
+    // lanes [l0, l1) whose fragments fit the list; pre is nondecreasing
+    const int f0 = __shfl_sync(FULL, start, l0);
+    const int l1 = __popc(__ballot_sync(FULL, pre - f0 <= C));
+    const int nf = __shfl_sync(FULL, pre, l1 - 1) - f0;
+    const bool mine = lane >= l0 && lane < l1;
+    const int s0 = start - f0;          // this lane's first list slot
+    if (mine) {
+      unsigned m = mask;
+      int c = s0;
+      while (m) {
+        const int i = __ffs(m) - 1;
+        m &= m - 1;
+        sent[c] = (i << kTriBits) | (scratch[i * 32 + lane] & (kMaxTris - 1));
+        spl[c] = (unsigned short)(lane | (i << 5));
+        ++c;
       }
-    }
-    // back to front; the colour and opacity of each fragment are replaced
-    // by the adjoint in texel-value space
-    float B = it.bg[0] * gr + it.bg[1] * gg + it.bg[2] * gb;
-    for (int c = cnt - 1; c >= 0; --c) {
-      const float4 f = sfrag[start + c];
-      const float aw = saw[start + c];
-      const float a = f.w * aw;
-      const float cg = f.x * gr + f.y * gg + f.z * gb;
-      const float Tc = sT[start + c];
-      const float ta = Tc * a;
-      // dL/d(raw alpha): alpha_w is a constant of the texels
-      const float ga = Tc * (cg - B) * aw;
-      const DShell& s = sh[(spl[start + c] >> 5) & 15];
-      float4 d;
-      if (s.fmt == VS_TEX_RGBA_F32) {
-        d = make_float4(ta * gr, ta * gg, ta * gb, ga);
-      } else {
-        d = make_float4(ta * gr * (f.x * (1.0f - f.x)), ta * gg * (f.y * (1.0f - f.y)),
-                        ta * gb * (f.z * (1.0f - f.z)), ga * (f.w * (1.0f - f.w)));
-      }
-      sfrag[start + c] = d;
-      B = fmaf(a, cg - B, B);
     }
     __syncwarp();
 
-    // 4. adjoint scatter, 32 fragments at a time
-    for (int j0 = 0; j0 < total; j0 += 32) {
+    // 2a. transparency attenuation, in a pass of its own so that the fetch
+    //     loop below keeps its registers
+    if (atten) {
+      atten_pass(it.cam, sh, pbase, sent, spl, saw, nf);
+      __syncwarp();
+    }
+
+    // 2b. fragments, 32 at a time
+    for (int j0 = 0; j0 < nf; j0 += 32) {
       const int j = j0 + lane;
-      if (j < total) {
-        const unsigned pl = spl[j];
-        if (pl & kBadFrag) continue;
-        const DShell& s = sh[(pl >> 5) & 15];
-        const Footprint f = unpack_footprint(sxy[j], sfxy[j]);
-        float3 v = make_float3(0.f, 0.f, 1.f);
-        if (s.fmt == VS_TEX_SH_F16) {
-          const int pp = pbase + (int)(pl & 31);
+      if (j < nf) {
+        const int e = sent[j];
+        const int i = e >> kTriBits, t = e & (kMaxTris - 1);
+        const int pp = pbase + (spl[j] & 31);
+        const DShell& s = sh[i];
+        Frag fr = {0.f, 0.f, 0.f, 0.f};
+        Tri Tr;
+        int idx[3];
+        if (t >= s.nt || load_tri_shade(s, t, Tr, idx) != 0) {
+          bad = 1;
+          spl[j] |= (unsigned short)kBadFrag;   // invisible, and no adjoint
+        } else {
           const int y = pp / W, x = pp - y * W;
-          v = ray_dir(it.cam, x, y);
+          const float2 uv[3] = {__ldg(s.uv + idx[0]), __ldg(s.uv + idx[1]), __ldg(s.uv + idx[2])};
+          const Footprint f = footprint(Tr, uv, s.tw, s.th, 256 * x + 128, 256 * y + 128);
+          if constexpr (BWD) {
+            unsigned xy;
+            float2 fxy;
+            pack_footprint(f, xy, fxy);
+            sxy[j] = xy;      // the entry is not read again
+            sfxy[j] = fxy;
+          }
+          float3 v = make_float3(0.f, 0.f, 1.f);
+          if (s.fmt == VS_TEX_SH_F16) v = ray_dir(it.cam, x, y);
+          fr = fetch_frag(s, f, v);
+          ++nfrag;
         }
-        scatter_frag(s, f, v, sfrag[j]);
+        // raw opacity here; the composite applies alpha_w
+        sfrag[j] = make_float4(fr.r, fr.g, fr.b, fr.a);
+        if (!atten) saw[j] = 1.0f;
       }
     }
+    __syncwarp();
+
+    // 3. composite the pass's pixels
+    if (mine) {
+      float T = 1.0f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
+      for (int c = 0; c < cnt; ++c) {
+        const float4 f = sfrag[s0 + c];
+        if constexpr (BWD) sT[s0 + c] = T;
+        const float a = f.w * saw[s0 + c];
+        const float ta = T * a;
+        Cr = fmaf(ta, f.x, Cr);
+        Cg = fmaf(ta, f.y, Cg);
+        Cb = fmaf(ta, f.z, Cb);
+        T = T * (1.0f - a);
+      }
+      const float outr = fmaf(T, it.bg[0], Cr), outg = fmaf(T, it.bg[1], Cg), outb = fmaf(T, it.bg[2], Cb);
+      if (pix_ok && it.out) it.out[p] = make_float4(outr, outg, outb, 1.0f - T);
+      if constexpr (BWD) {
+        float gr = 0.f, gg = 0.f, gb = 0.f;
+        if (pix_ok) {
+          const float* gp = it.grad_rgb + 3 * (size_t)p;
+          gr = __ldg(gp);
+          gg = __ldg(gp + 1);
+          gb = __ldg(gp + 2);
+          if (it.flags & VS_FLAG_LOSS_L2) {
+            const float dr = outr - gr, dg = outg - gg, db = outb - gb;
+            const float inv = 1.0f / (3.0f * (float)HW);
+            loss_acc += (dr * dr + dg * dg + db * db) * inv;
+            gr = 2.0f * inv * dr;
+            gg = 2.0f * inv * dg;
+            gb = 2.0f * inv * db;
+          }
+        }
+        // back to front; the colour and opacity of each fragment are
+        // replaced by the adjoint in texel-value space
+        float B = it.bg[0] * gr + it.bg[1] * gg + it.bg[2] * gb;
+        for (int c = cnt - 1; c >= 0; --c) {
+          const float4 f = sfrag[s0 + c];
+          const float aw = saw[s0 + c];
+          const float a = f.w * aw;
+          const float cg = f.x * gr + f.y * gg + f.z * gb;
+          const float Tc = sT[s0 + c];
+          const float ta = Tc * a;
+          // dL/d(raw alpha): alpha_w is a constant of the texels
+          const float ga = Tc * (cg - B) * aw;
+          const DShell& s = sh[(spl[s0 + c] >> 5) & 15];
+          float4 d;
+          if (s.fmt == VS_TEX_RGBA_F32) {
+            d = make_float4(ta * gr, ta * gg, ta * gb, ga);
+          } else {
+            d = make_float4(ta * gr * (f.x * (1.0f - f.x)), ta * gg * (f.y * (1.0f - f.y)),
+                            ta * gb * (f.z * (1.0f - f.z)), ga * (f.w * (1.0f - f.w)));
+          }
+          sfrag[s0 + c] = d;
+          B = fmaf(a, cg - B, B);
+        }
+      }
+    }
+    if constexpr (BWD) {
+      __syncwarp();
+      // 4. adjoint scatter, 32 fragments at a time
+      for (int j0 = 0; j0 < nf; j0 += 32) {
+        const int j = j0 + lane;
+        if (j < nf) {
+          const unsigned pl = spl[j];
+          if (pl & kBadFrag) continue;
+          const DShell& s = sh[(pl >> 5) & 15];
+          const Footprint f = unpack_footprint(sxy[j], sfxy[j]);
+          float3 v = make_float3(0.f, 0.f, 1.f);
+          if (s.fmt == VS_TEX_SH_F16) {
+            const int pp = pbase + (int)(pl & 31);
+            const int y = pp / W, x = pp - y * W;
+            v = ray_dir(it.cam, x, y);
+          }
+          scatter_frag(s, f, v, sfrag[j]);
+        }
+      }
+    }
+    __syncwarp();   // the list is rebuilt by the next pass
+    l0 = l1;
   }
-  loss_acc += loss;
-  __syncwarp();   // the fragment list is rebuilt by the next round
 }
 
 // Shading unit: 32 * it.shade_rounds consecutive pixels in rounds of 32;
