@@ -1,6 +1,8 @@
 """Build libvs.so (the C-ABI CUDA library) in-tree for sm_103a.
 
-Two translation units compiled in parallel, then linked; no cmake.
+The translation units (the host API, the class-free kernels and one per
+texel class of the shading kernels) compile in parallel, then link; no
+cmake.
 --fmad=false: multiply-adds are fused only where the source says fmaf(), so
 the same device function computes the same bits in every kernel that
 inlines it (the batched forward is bit-identical to the per-view one).
@@ -22,7 +24,8 @@ BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
               "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["vs_kernels.cu", "vs_api.cu"]
+SOURCES = ["vs_api.cu", "vs_kernels.cu", "vs_tc_any.cu", "vs_tc_rgba.cu", "vs_tc_sh0.cu", "vs_tc_sh1.cu",
+           "vs_tc_sh2.cu", "vs_tc_sh3.cu"]
 
 
 def nvcc() -> str:

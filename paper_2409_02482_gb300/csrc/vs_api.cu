@@ -25,7 +25,7 @@ using namespace vsd;
 struct vs_ctx {
   int device;
   int num_sms;
-  int persist_blocks[2][VS_MAX_SHELLS + 1];   // [backward][most shells] blocks per SM
+  int persist_blocks[2][kNumTc][VS_MAX_SHELLS + 1];   // [backward][texel class][most shells] blocks per SM
   std::mutex tune_mu;                          // guards tune / tune_set
   vs_tuning tune[2][VS_MAX_SHELLS + 1];        // [backward][most shells]
   bool tune_set[2][VS_MAX_SHELLS + 1];
@@ -118,6 +118,7 @@ struct Plan {
   std::vector<DShell> shells;
   std::vector<int> stage_pre;    // [n + 3]
   int total_units;
+  int tc;                        // texel class of the kernels (vsd::TC_*)
 };
 
 // Fills the plan; with ws == nullptr only sizes are computed.
@@ -198,6 +199,16 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
     sidx += o.k;
   }
   P.total = align256(off);
+  // texel class: one compiled format when every shell shares it with
+  // 16-byte-aligned texels (and, for the adjoint, gradients)
+  int tc = -1;
+  for (const DShell& sh : P.shells) {
+    int c = TC_ANY;
+    if (sh.fmt == VS_TEX_RGBA_F32 && sh.vec == 4 && (!do_bwd || sh.gvec == 4)) c = TC_RGBA;
+    else if (sh.fmt == VS_TEX_SH_F16 && sh.vec == 8 && (!do_bwd || sh.gvec == 4)) c = TC_SH0 + sh.degree;
+    tc = (tc < 0 || tc == c) ? c : TC_ANY;
+  }
+  P.tc = tc < 0 ? TC_ANY : tc;
   // skewed stages: stage s = SETUP(s), RASTER(s-1), SHADE(s-2)
   long long g = 0;
   for (int st = 0; st < n + NPH - 1; ++st) {
@@ -346,10 +357,10 @@ vs_status launch_batch(vs_ctx* ctx, const Plan& P, void* workspace, int do_backw
   char* ws = static_cast<char*>(workspace);
   vs_status s = upload_table(P, ws, 1, st);
   if (s != VS_OK) return s;
-  const int most = ctx->persist_blocks[do_backward ? 1 : 0][kmax];
+  const int most = ctx->persist_blocks[do_backward ? 1 : 0][P.tc][kmax];
   const int bps = t.blocks_per_sm == 0 ? most : std::min(t.blocks_per_sm, most);
   const long long spin_limit = 1ll << 24;   // ~ seconds with 200 ns sleeps
-  cudaError_t e = vsk::persistent(table_ref(P, ws), do_backward != 0, ctx->num_sms * bps, spin_limit, st);
+  cudaError_t e = vsk::persistent(table_ref(P, ws), do_backward != 0, P.tc, ctx->num_sms * bps, spin_limit, st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_batch launch");
 }
 
@@ -427,13 +438,15 @@ vs_status vs_create(vs_ctx** ctx, int device) {
     return cuda_fail(e, "kernel configuration");
   }
   for (int b = 0; b < 2; ++b)
-    for (int K = 1; K <= VS_MAX_SHELLS; ++K) {
-      if ((e = vsk::persistent_occupancy(b == 1, K, &c->persist_blocks[b][K])) != cudaSuccess) {
-        delete c;
-        return cuda_fail(e, "occupancy query");
+    for (int tc = 0; tc < kNumTc; ++tc)
+      for (int K = 1; K <= VS_MAX_SHELLS; ++K) {
+        int& nb = c->persist_blocks[b][tc][K];
+        if ((e = vsk::persistent_occupancy(b == 1, tc, K, &nb)) != cudaSuccess) {
+          delete c;
+          return cuda_fail(e, "occupancy query");
+        }
+        if (nb < 1) nb = 1;
       }
-      if (c->persist_blocks[b][K] < 1) c->persist_blocks[b][K] = 1;
-    }
   *ctx = c;
   g_err.clear();
   return VS_OK;
@@ -499,7 +512,7 @@ vs_status vs_render(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, con
   if ((s = set_device(ctx)) != VS_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if ((s = upload_table(P, ws, vsk::plain_forward_launches(P.items[0].units), st)) != VS_OK) return s;
-  cudaError_t e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, st);
+  cudaError_t e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, P.tc, st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render launch");
 }
 
@@ -519,7 +532,7 @@ vs_status vs_render_backward(vs_ctx* ctx, const vs_object* obj, const vs_camera*
   if ((s = set_device(ctx)) != VS_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if ((s = upload_table(P, ws, vsk::plain_backward_launches(P.items[0].units), st)) != VS_OK) return s;
-  cudaError_t e = vsk::plain_backward(table_ref(P, ws), P.items[0].units, st);
+  cudaError_t e = vsk::plain_backward(table_ref(P, ws), P.items[0].units, P.tc, st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_backward launch");
 }
 
@@ -628,11 +641,13 @@ vs_status vs_autotune_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, 
     if (items[j].obj) kmax = std::max(kmax, std::min((int)items[j].obj->k, VS_MAX_SHELLS));
   const int b = do_backward ? 1 : 0;
   const vs_tuning start = lookup_tuning(ctx, b, kmax);
+  int tc = TC_ANY;
   {  // validate the whole batch once before timing anything
     Plan P;
     int km = 1;
     vs_status s = plan_batch(ctx, items, n, bg, do_backward, workspace, ws_bytes, flags, start, P, &km);
     if (s != VS_OK) return s;
+    tc = P.tc;
   }
   vs_status s = set_device(ctx);
   if (s != VS_OK) return s;
@@ -645,7 +660,7 @@ vs_status vs_autotune_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, 
     return cuda_fail(e, "cudaEventCreate");
   }
   vs_tuning won{};
-  s = vs_tune_search(&start, ctx->persist_blocks[b][kmax], autotune_cost, &J, &won, nullptr);
+  s = vs_tune_search(&start, ctx->persist_blocks[b][tc][kmax], autotune_cost, &J, &won, nullptr);
   cudaEventDestroy(J.ev[0]);
   cudaEventDestroy(J.ev[1]);
   if (J.status != VS_OK) return fail(J.status, "%s", J.error.c_str());
@@ -753,6 +768,6 @@ extern "C" vs_status vs_render_noalloc(vs_ctx* ctx, const vs_object* obj, const 
   cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-alloc header)");
   if ((s = upload_table(P, ws, vsk::plain_forward_launches(P.items[0].units), st)) != VS_OK) return s;
-  e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, st);
+  e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, P.tc, st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_noalloc launch");
 }

@@ -60,6 +60,12 @@ __host__ __device__ constexpr size_t warp_slice_bytes(int K, bool bwd) {
 }
 __host__ __device__ constexpr size_t block_smem_bytes(int K, bool bwd) { return warp_slice_bytes(K, bwd) * kWarps; }
 
+// Texel classes: a kernel compiled for TC_ANY decides the format per shell at
+// run time; the others serve batches whose shells all share one format with
+// 16-byte-aligned texels (and gradients).
+enum : int { TC_ANY = 0, TC_RGBA = 1, TC_SH0 = 2 };   // TC_SH0 + degree
+constexpr int kNumTc = TC_SH0 + 4;
+
 // Phases of one item.  Large triangles are rasterized by the whole block
 // inside the raster unit that met them.
 enum { PH_SETUP = 0, PH_RASTER = 1, PH_SHADE = 2, NPH = 3 };
