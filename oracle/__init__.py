@@ -22,6 +22,7 @@ from .build import LIB_PATH, build_oracle
 
 FMT_RGBA_F32 = 0
 FMT_SH_F16 = 1
+FMT_SH_U8 = 2
 
 _lib = None
 
@@ -36,7 +37,8 @@ class OShell(ctypes.Structure):
     _fields_ = [("pos", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("tris", ctypes.c_void_p),
                 ("nv", ctypes.c_int32), ("nt", ctypes.c_int32), ("tex", ctypes.c_void_p),
                 ("tw", ctypes.c_int32), ("th", ctypes.c_int32), ("fmt", ctypes.c_int32),
-                ("degree", ctypes.c_int32), ("pitch", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+                ("degree", ctypes.c_int32), ("pitch", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("band_shift", ctypes.c_int32), ("vmin", ctypes.c_double), ("vmax", ctypes.c_double)]
 
 
 _DTYPES = {np.dtype(np.float32): 0, np.dtype(np.float16): 1, np.dtype(np.float64): 2}
@@ -82,9 +84,28 @@ class _ShellRefs:
             o.pos, o.uv, o.tris = _ptr(pos).value, _ptr(uv).value, _ptr(tris).value
             o.nv, o.nt = pos.shape[0], tris.shape[0]
             o.tex = _ptr(tex).value
-            o.th, o.tw, o.pitch = tex.shape[0], tex.shape[1], tex.shape[2]
             o.fmt, o.degree = s.fmt, s.degree
-            o.dtype = _DTYPES[tex.dtype]
+            if s.fmt == FMT_SH_U8:
+                assert tex.dtype == np.uint8 and tex.ndim == 1
+                o.tw, o.th, o.pitch, o.dtype = s.tex_w, s.tex_h, 0, -1
+                o.band_shift, o.vmin, o.vmax = s.band_shift, s.vmin, s.vmax
+            else:
+                o.th, o.tw, o.pitch = tex.shape[0], tex.shape[1], tex.shape[2]
+                o.dtype = _DTYPES[tex.dtype]
+
+
+def sample_baked(shell, m: int, u: float, v: float) -> np.ndarray:
+    """Decoded bilinear sample of SH coefficient m (RGBA) of a FMT_SH_U8
+    shell at UV (u, v)."""
+    tex = np.ascontiguousarray(shell.tex, np.uint8)
+    out = np.zeros(4, np.float64)
+    r = lib().oracle_sample_baked(_ptr(tex), ctypes.c_int32(shell.tex_w), ctypes.c_int32(shell.tex_h),
+                                  ctypes.c_int32(shell.degree), ctypes.c_int32(shell.band_shift),
+                                  ctypes.c_double(shell.vmin), ctypes.c_double(shell.vmax), ctypes.c_int32(m),
+                                  ctypes.c_double(u), ctypes.c_double(v), _ptr(out))
+    if r != 0:
+        raise ValueError("coefficient out of range")
+    return out
 
 
 def default_threads() -> int:
@@ -196,8 +217,10 @@ def backward(scene, cam, hits: np.ndarray, grad_rgb: np.ndarray, bg=(0.0, 0.0, 0
     ptrs = (ctypes.c_void_p * scene.k)(*[gr.ctypes.data for gr in grads])
     bgv = np.ascontiguousarray(bg, np.float64)
     c = ocam(cam)
-    lib().oracle_backward(refs.arr, ctypes.c_int32(scene.k), ctypes.byref(c), _ptr(bgv), _ptr(hits),
-                          _ptr(g), ptrs, ctypes.c_int32(flags))
+    r = lib().oracle_backward(refs.arr, ctypes.c_int32(scene.k), ctypes.byref(c), _ptr(bgv), _ptr(hits),
+                              _ptr(g), ptrs, ctypes.c_int32(flags))
+    if r != 0:
+        raise ValueError("the baked byte format (FMT_SH_U8) has no gradient")
     return grads
 
 

@@ -54,6 +54,11 @@ struct OShell {
   const void* tex;         // [th, tw, pitch] texel values
   int32_t tw, th, fmt, degree, pitch;
   int32_t dtype;           // storage of tex: 0 float32, 1 float16, 2 float64
+  // FMT_SH_U8 only: tex is the byte buffer of all SH bands, band l at
+  // resolution (tw >> l*band_shift, th >> l*band_shift); decoded value =
+  // vmin + (vmax - vmin) q / 255
+  int32_t band_shift;
+  double vmin, vmax;
 };
 
 struct OCam {
@@ -62,7 +67,8 @@ struct OCam {
   int32_t width, height;
 };
 
-enum { FMT_RGBA_F32 = 0, FMT_SH_F16 = 1 };  // value meaning; storage is OShell::dtype
+// value meaning; storage is OShell::dtype except for the baked bytes of FMT_SH_U8
+enum { FMT_RGBA_F32 = 0, FMT_SH_F16 = 1, FMT_SH_U8 = 2 };
 enum { VF_NEAR = 1, VF_GUARD = 2 };
 
 struct SVert {
@@ -283,6 +289,57 @@ void sample(const OShell& s, const Footprint& f, int nch, double* out) {
   }
 }
 
+// --- the baked texel format (Sec. 3 "Mixed Resolutions", "Squeezing and
+// Quantization", "Baking Textures") ---------------------------------------------
+// SH coefficient m (band l = floor(sqrt(m))) of all four channels RGBA, one
+// byte each.  Band l is its own image of (tw >> l s) x (th >> l s) texels, s =
+// band_shift (s = 1 halves the resolution per band: the paper's 2048^2 base
+// colour down to 256^2 for band 3).  A texel of band l holds the band's 2l+1
+// coefficients as RGBA byte quadruples, padded to 4, 16, 32, 32 bytes for
+// l = 0..3; bands follow each other, each starting on a 256-byte boundary.
+// The decoded value is vmin + (vmax - vmin) q / 255 (the paper's rescale of
+// the stored q(x) = round(255 x) / 255 to [vmin, vmax]).
+struct Band {
+  int64_t w, h, stride, offset;
+};
+
+Band band_layout(const OShell& s, int l) {
+  static const int64_t kStride[4] = {4, 16, 32, 32};
+  Band b{0, 0, 0, 0};
+  for (int j = 0; j <= l; ++j) {
+    if (j > 0) b.offset += (b.w * b.h * b.stride + 255) / 256 * 256;
+    b.w = (int64_t)s.tw >> (j * s.band_shift);
+    b.h = (int64_t)s.th >> (j * s.band_shift);
+    b.stride = kStride[j];
+  }
+  return b;
+}
+
+Footprint footprint_wh(int64_t w, int64_t h, double u, double v) {
+  OShell t{};
+  t.tw = (int32_t)w;
+  t.th = (int32_t)h;
+  return footprint(t, u, v);
+}
+
+// Bilinear sample at UV (u, v) of coefficient m of every channel, decoded.
+void sample_baked(const OShell& s, int m, double u, double v, double out[4]) {
+  const int l = (int)std::floor(std::sqrt((double)m) + 1e-9);
+  const int j = m - l * l;
+  const Band b = band_layout(s, l);
+  const Footprint f = footprint_wh(b.w, b.h, u, v);
+  const uint8_t* base = (const uint8_t*)s.tex + b.offset;
+  for (int ch = 0; ch < 4; ++ch) {
+    double acc = 0.0;
+    for (int yb = 0; yb < 2; ++yb)
+      for (int xa = 0; xa < 2; ++xa) {
+        const uint8_t q = base[(f.y[yb] * b.w + f.x[xa]) * b.stride + 4 * j + ch];
+        acc += tap_weight(f, xa, yb) * (s.vmin + (s.vmax - s.vmin) * (double)q / 255.0);
+      }
+    out[ch] = acc;
+  }
+}
+
 // --- real spherical harmonics, l <= 3, orthonormal on the unit sphere ---------
 // Real forms of the complex Y_l^m without the Condon-Shortley sign; the l = 1
 // band is proportional to (y, z, x).  Index l^2 + l + m.
@@ -387,6 +444,21 @@ bool shade_fragment(const OShell& s, const OCam& c, const std::vector<SVert>& sv
   double invw[3] = {sv[idx[0]].invw, sv[idx[1]].invw, sv[idx[2]].invw};
   double uv[2];
   interp_uv(t, uvp, invw, 256 * x + 128, 256 * y + 128, uv);
+  if (s.fmt == FMT_SH_U8) {
+    // RGBA all view-dependent: channel c = sigmoid(sum_m sh_{m,c} Y_m(v))
+    const int nb = (s.degree + 1) * (s.degree + 1);
+    double z[4] = {0, 0, 0, 0};
+    for (int m = 0; m < nb; ++m) {
+      double val[4];
+      sample_baked(s, m, uv[0], uv[1], val);
+      for (int ch = 0; ch < 4; ++ch) z[ch] += val[ch] * Y[m];
+    }
+    for (int ch = 0; ch < 3; ++ch) f->rgb[ch] = sigmoid(z[ch]);
+    f->alpha_raw = sigmoid(z[3]);
+    f->atten = (flags & OFLAG_ALPHA_ATTEN) ? attenuation(s, idx, v) : 1.0;
+    f->alpha = f->alpha_raw * f->atten;
+    return true;
+  }
   f->fp = footprint(s, uv[0], uv[1]);
   int nv = num_values(s);
   sample(s, f->fp, nv, f->val);
@@ -455,7 +527,7 @@ int oracle_shade(const OShell* shells, int32_t k, const OCam* cam, const double*
   int maxdeg = 0;
   for (int i = 0; i < k; ++i) {
     sv[i] = setup_all(shells[i], *cam);
-    if (shells[i].fmt == FMT_SH_F16) maxdeg = std::max(maxdeg, (int)shells[i].degree);
+    if (shells[i].fmt != FMT_RGBA_F32) maxdeg = std::max(maxdeg, (int)shells[i].degree);
   }
   int nth = std::max(1, nthreads);
   std::vector<int64_t> cnt((size_t)nth * k, 0);
@@ -492,12 +564,16 @@ int oracle_shade(const OShell* shells, int32_t k, const OCam* cam, const double*
 // dL/d(output rgb).  grad_tex[i]: [th, tw, pitch] FP64, accumulated into.
 int oracle_backward(const OShell* shells, int32_t k, const OCam* cam, const double* bg,
                     const int32_t* hits, const double* grad_rgb, double* const* grad_tex, int32_t flags) {
+  // the baked bytes are a deployment format: no gradient (the paper fits
+  // continuous textures and quantises when baking)
+  for (int i = 0; i < k; ++i)
+    if (shells[i].fmt == FMT_SH_U8) return -3;
   const int64_t W = cam->width, H = cam->height;
   std::vector<std::vector<SVert>> sv(k);
   int maxdeg = 0;
   for (int i = 0; i < k; ++i) {
     sv[i] = setup_all(shells[i], *cam);
-    if (shells[i].fmt == FMT_SH_F16) maxdeg = std::max(maxdeg, (int)shells[i].degree);
+    if (shells[i].fmt != FMT_RGBA_F32) maxdeg = std::max(maxdeg, (int)shells[i].degree);
   }
   std::vector<Frag> fr(k);
   std::vector<char> hit(k);
@@ -596,6 +672,18 @@ int oracle_sample(const void* tex, int32_t dtype, int32_t tw, int32_t th, int32_
   s.tex = tex; s.dtype = dtype; s.tw = tw; s.th = th; s.pitch = pitch;
   Footprint f = footprint(s, u, v);
   sample(s, f, nch, out);
+  return 0;
+}
+
+// Baked format: bilinear sample of coefficient m (all four channels, decoded)
+// at UV (u, v).
+int oracle_sample_baked(const uint8_t* tex, int32_t tw, int32_t th, int32_t degree, int32_t band_shift,
+                        double vmin, double vmax, int32_t m, double u, double v, double* out) {
+  if (m < 0 || m >= (degree + 1) * (degree + 1)) return -1;
+  OShell s{};
+  s.tex = tex; s.tw = tw; s.th = th; s.degree = degree; s.fmt = FMT_SH_U8;
+  s.band_shift = band_shift; s.vmin = vmin; s.vmax = vmax;
+  sample_baked(s, m, u, v, out);
   return 0;
 }
 

@@ -15,6 +15,11 @@ Shells", Sec. 3 "Texturing Meshes", Sec. 4 Tab. 2).
 from .scenes import (  # noqa: F401
     FMT_RGBA_F32,
     FMT_SH_F16,
+    FMT_SH_U8,
+    BAKED_STRIDES,
+    baked_layout,
+    baked_values_to_bytes,
+    baked_sh_texture,
     Camera,
     Shell,
     Scene,

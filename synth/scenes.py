@@ -28,6 +28,7 @@ import numpy as np
 
 FMT_RGBA_F32 = 0
 FMT_SH_F16 = 1
+FMT_SH_U8 = 2      # baked: RGBA SH bytes, per-band resolutions (see baked_layout)
 
 
 def sh_channels(degree: int) -> int:
@@ -40,17 +41,33 @@ class Shell:
     pos: np.ndarray      # float32 [V, 3]
     uv: np.ndarray       # float32 [V, 2]
     tris: np.ndarray     # int32 [T, 3]
-    tex: np.ndarray      # float32 [Ht, Wt, pitch] or float16 [Ht, Wt, pitch]
-    fmt: int             # FMT_RGBA_F32 or FMT_SH_F16
-    degree: int = 0      # SH degree (SH_F16 only)
+    tex: np.ndarray      # float32/float16 [Ht, Wt, pitch]; FMT_SH_U8: uint8 band buffer
+    fmt: int             # FMT_RGBA_F32, FMT_SH_F16 or FMT_SH_U8
+    degree: int = 0      # SH degree (SH formats)
+    # FMT_SH_U8 only: band-0 size, resolution shift per band, decode range
+    tex_w: int = 0
+    tex_h: int = 0
+    band_shift: int = 0
+    vmin: float = -15.0
+    vmax: float = 15.0
 
     @property
     def channels(self) -> int:
+        if self.fmt == FMT_SH_U8:
+            return 4 * (self.degree + 1) ** 2
         return 4 if self.fmt == FMT_RGBA_F32 else sh_channels(self.degree)
 
     @property
     def pitch(self) -> int:
-        return int(self.tex.shape[2])
+        return 0 if self.fmt == FMT_SH_U8 else int(self.tex.shape[2])
+
+    @property
+    def width(self) -> int:
+        return self.tex_w if self.fmt == FMT_SH_U8 else int(self.tex.shape[1])
+
+    @property
+    def height(self) -> int:
+        return self.tex_h if self.fmt == FMT_SH_U8 else int(self.tex.shape[0])
 
 
 @dataclasses.dataclass
@@ -286,6 +303,46 @@ def sh_texture(h: int, w: int, degree: int, rng: np.random.Generator,
     return tex
 
 
+BAKED_STRIDES = (4, 16, 32, 32)   # bytes per texel of band l: 4 (2l + 1), padded
+
+
+def baked_layout(tex_w: int, tex_h: int, degree: int, band_shift: int):
+    """Byte layout of a FMT_SH_U8 buffer: per band l, (offset, w, h, stride)
+    with (w, h) = (tex_w, tex_h) >> l * band_shift and each band starting on
+    a 256-byte boundary; returns (bands, total bytes)."""
+    bands, off = [], 0
+    for band in range(degree + 1):
+        w, h = tex_w >> (band * band_shift), tex_h >> (band * band_shift)
+        bands.append((off, w, h, BAKED_STRIDES[band]))
+        off += -(-w * h * BAKED_STRIDES[band] // 256) * 256
+    return bands, off
+
+
+def baked_values_to_bytes(values: np.ndarray, vmin: float, vmax: float) -> np.ndarray:
+    """Quantise decoded SH values to the stored bytes: q = round(255 (x -
+    vmin) / (vmax - vmin)), clipped to [0, 255] (the inverse of the decode)."""
+    q = np.rint((values.astype(np.float64) - vmin) * (255.0 / (vmax - vmin)))
+    return np.clip(q, 0, 255).astype(np.uint8)
+
+
+def baked_sh_texture(tex_w: int, tex_h: int, degree: int, band_shift: int, rng: np.random.Generator,
+                     vmin: float = -15.0, vmax: float = 15.0, base_sigma: float = 3.5) -> np.ndarray:
+    """FMT_SH_U8 buffer of random baked texels.  Decoded values before
+    quantisation: band 0 ~ N(0, base_sigma) for all of RGBA (so that
+    sigmoid(value * Y_0) spans (0, 1)), band l >= 1 ~ N(0, base_sigma / (2 l))
+    (weaker view dependence in higher bands).  Padding bytes are zero."""
+    bands, total = baked_layout(tex_w, tex_h, degree, band_shift)
+    buf = np.zeros(total, np.uint8)
+    for band, (off, w, h, stride) in enumerate(bands):
+        n = 4 * (2 * band + 1)
+        sigma = base_sigma if band == 0 else base_sigma / (2 * band)
+        vals = rng.standard_normal((h, w, n), dtype=np.float32) * np.float32(sigma)
+        img = np.zeros((h, w, stride), np.uint8)
+        img[..., :n] = baked_values_to_bytes(vals, vmin, vmax)
+        buf[off:off + w * h * stride] = img.reshape(-1)
+    return buf
+
+
 # ----------------------------------------------------------------------------
 # cameras
 # ----------------------------------------------------------------------------
@@ -361,9 +418,22 @@ def _sh_scene(k, n_lat, tex_res, degree, seed, tex_seed, pitch=None, sigma=0.3, 
     return Scene(shells)
 
 
+def _baked_scene(k, n_lat, tex_res, degree, band_shift, seed, tex_seed):
+    geo = displaced_shells(k, n_lat, seed=seed)
+    ss = np.random.SeedSequence(tex_seed).spawn(k)
+    shells = []
+    for i, (pos, uv, tris) in enumerate(geo):
+        buf = baked_sh_texture(tex_res, tex_res, degree, band_shift, np.random.default_rng(ss[i]))
+        shells.append(Shell(pos, uv, tris, buf, FMT_SH_U8, degree, tex_w=tex_res, tex_h=tex_res,
+                            band_shift=band_shift))
+    return Scene(shells)
+
+
 def config_scene(name: str, scale: float = 1.0, views: Optional[int] = None,
                  tex_seed: int = 0, pitch: Optional[int] = None, textures: bool = True):
-    """Build workload ``name`` ('c1'..'c5').
+    """Build workload ``name`` ('c1'..'c5', or 'c2b': the C2 geometry and
+    views with the paper's deployed textures -- RGBA SH degree 3 in bytes,
+    2048^2 base halving per band down to 256^2).
 
     ``scale`` < 1 shrinks triangle counts (by scale), texture side and image
     side (by sqrt(scale)) for fast tests while keeping the structure.
@@ -390,6 +460,11 @@ def config_scene(name: str, scale: float = 1.0, views: Optional[int] = None,
     if name == "c2":
         n = 100 if views is None else views
         sc = _sh_scene(7, _n_lat_for_tris(200e3 * scale), texres(2048), 2, 0, tex_seed, pitch)
+        w = res(800)
+        return [(sc, fibonacci_cameras(n, 4.0, w, w))]
+    if name == "c2b":
+        n = 100 if views is None else views
+        sc = _baked_scene(7, _n_lat_for_tris(200e3 * scale), texres(2048), 3, 1, 0, tex_seed)
         w = res(800)
         return [(sc, fibonacci_cameras(n, 4.0, w, w))]
     if name == "c3":

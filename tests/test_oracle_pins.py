@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 import synth
-from synth import FMT_RGBA_F32, FMT_SH_F16, Camera, Scene, Shell
+from synth import FMT_RGBA_F32, FMT_SH_F16, FMT_SH_U8, Camera, Scene, Shell
 
 
 # ----------------------------------------------------------------------------
@@ -664,6 +664,129 @@ def test_attenuation_nested_shells_use_each_hit_face_normal():
                 vr = abs(dirs[y, x] @ (pt / np.linalg.norm(pt)))
                 radial_differs += abs(vr - abs(dirs[y, x] @ normals[0][hits[0, y, x]])) > 1e-3
     assert radial_differs > 100
+
+
+# ----------------------------------------------------------------------------
+# the baked format (Sec. 3 "Mixed Resolutions", "Squeezing and Quantization",
+# "Baking Textures"): RGBA SH bytes, band l at (W, H) >> l s
+# ----------------------------------------------------------------------------
+
+def _band_table(tw, th, degree, shift):
+    """The documented layout, written out independently of synth."""
+    strides = {0: 4, 1: 16, 2: 32, 3: 32}
+    out, off = [], 0
+    for band in range(degree + 1):
+        w, h = tw >> (band * shift), th >> (band * shift)
+        out.append((off, w, h, strides[band]))
+        off += ((w * h * strides[band] + 255) // 256) * 256
+    return out, off
+
+
+def _baked_shell(buf, tw, th, degree, shift, vmin=-15.0, vmax=15.0, geo=None):
+    pos, uv, tris = geo if geo is not None else synth.icosphere(1, 1.0)
+    return Shell(pos, uv, tris, buf, FMT_SH_U8, degree, tex_w=tw, tex_h=th, band_shift=shift,
+                 vmin=vmin, vmax=vmax)
+
+
+@pytest.mark.parametrize("tw,th,degree,shift", [(16, 8, 3, 1), (8, 8, 2, 0), (32, 16, 1, 2), (4, 4, 0, 1),
+                                                (12, 6, 2, 0), (20, 12, 1, 1)])
+def test_baked_texel_centres_decode_their_bytes(tw, th, degree, shift):
+    """At the centre of band-l texel (x, y) every coefficient of the band
+    decodes to vmin + (vmax - vmin) q / 255 of its own byte in the
+    documented layout (256-byte aligned bands, RGBA quadruples per
+    coefficient)."""
+    table, total = _band_table(tw, th, degree, shift)
+    assert synth.baked_layout(tw, th, degree, shift) == (table, total)
+    rng = np.random.default_rng(tw * 7 + degree)
+    buf = rng.integers(0, 256, total, dtype=np.uint8)
+    vmin, vmax = -3.0, 12.0
+    sh = _baked_shell(buf, tw, th, degree, shift, vmin, vmax)
+    for band, (off, w, h, stride) in enumerate(table):
+        for _ in range(6):
+            x, y = int(rng.integers(0, w)), int(rng.integers(0, h))
+            for j in range(2 * band + 1):
+                got = oracle.sample_baked(sh, band * band + j, (x + 0.5) / w, (y + 0.5) / h)
+                q = buf[off + (y * w + x) * stride + 4 * j: off + (y * w + x) * stride + 4 * j + 4]
+                assert np.abs(got - (vmin + (vmax - vmin) * q.astype(np.float64) / 255.0)).max() < 1e-12
+
+
+def test_baked_bands_interpolate_at_their_own_resolution():
+    """Bytes affine in each band's texel index are reproduced exactly by the
+    bilinear fetch at any interior UV, with the band's own resolution:
+    q(u, v) = b0 + gx (u w_l - 1/2) + gy (v h_l - 1/2)."""
+    tw, th, degree, shift = 32, 32, 3, 1
+    table, total = _band_table(tw, th, degree, shift)
+    buf = np.zeros(total, np.uint8)
+    coef = {}
+    for band, (off, w, h, stride) in enumerate(table):
+        for j in range(2 * band + 1):
+            for c in range(4):
+                b0, gx, gy = 10 + 3 * j + c, 1 + (j + c) % 3, 2 - (c % 2)
+                coef[(band * band + j, c)] = (b0, gx, gy, w, h)
+                ys, xs = np.mgrid[0:h, 0:w]
+                img = b0 + gx * xs + gy * ys
+                assert img.max() <= 255
+                view = buf[off: off + w * h * stride].reshape(h, w, stride)
+                view[..., 4 * j + c] = img
+    vmin, vmax = -15.0, 15.0
+    sh = _baked_shell(buf, tw, th, degree, shift, vmin, vmax)
+    rng = np.random.default_rng(3)
+    for _ in range(40):
+        u, v = rng.uniform(0.25, 0.75, 2)       # interior for every band (4x4 smallest)
+        for m in range(16):
+            got = oracle.sample_baked(sh, m, u, v)
+            for c in range(4):
+                b0, gx, gy, w, h = coef[(m, c)]
+                q = b0 + gx * (u * w - 0.5) + gy * (v * h - 0.5)
+                assert abs(got[c] - (vmin + (vmax - vmin) * q / 255.0)) < 1e-12
+
+
+def test_baked_constant_textures_closed_form_view_dependent_alpha():
+    """Constant baked bytes on concentric shells: every channel, alpha
+    included, is sigmoid(sum_m value_{m,c} Y_m(v)) with scipy's real SH and
+    the FP64 pixel ray, composited front to back."""
+    geo = synth.concentric_icospheres([1.0, 0.85], subdiv=3)
+    deg, tw = 3, 16
+    table, total = _band_table(tw, tw, deg, 1)
+    rng = np.random.default_rng(21)
+    shells, values = [], []
+    for g in geo:
+        qv = rng.integers(60, 200, (16, 4))           # per (coefficient, channel)
+        buf = np.zeros(total, np.uint8)
+        for band, (off, w, h, stride) in enumerate(table):
+            view = buf[off: off + w * h * stride].reshape(h, w, stride)
+            for j in range(2 * band + 1):
+                view[..., 4 * j: 4 * j + 4] = qv[band * band + j]
+        shells.append(_baked_shell(buf, tw, tw, deg, 1, geo=g))
+        values.append(-15.0 + 30.0 * qv.astype(np.float64) / 255.0)
+    cam = synth.look_at((-1.2, 2.5, 1.3), width=64, height=64)
+    bg = (0.05, 0.1, 0.9)
+    rgba, hits, _ = oracle.render(Scene(shells), cam, bg=bg)
+    sure = _sure_hits(cam, geo)
+    _, dirs = pixel_rays(cam)
+    valid = np.all(sure != 0, axis=0)
+    checked = 0
+    for y, x in zip(*np.nonzero(valid)):
+        Y = real_sh_scipy(deg, dirs[y, x])
+        C, T = np.zeros(3), 1.0
+        for i, val in enumerate(values):
+            if sure[i, y, x] < 0:
+                continue
+            z = Y @ val                                  # [4] = sum_m Y_m value_{m,c}
+            a = sigmoid(z[3])
+            C += T * a * sigmoid(z[:3])
+            T *= 1 - a
+        assert np.allclose(rgba[y, x, :3], C + T * np.asarray(bg), atol=1e-12)
+        assert abs(rgba[y, x, 3] - (1 - T)) < 1e-12
+        checked += 1
+    assert checked > 1000
+
+
+def test_baked_format_has_no_gradient():
+    (sc, cams), = synth.config_scene("c2b", scale=0.002, views=1)
+    hits, _, _ = oracle.raster_scene(sc, cams[0])
+    with pytest.raises(ValueError):
+        oracle.backward(sc, cams[0], hits, np.zeros((cams[0].height, cams[0].width, 3)))
 
 
 # ----------------------------------------------------------------------------
