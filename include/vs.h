@@ -79,6 +79,22 @@ typedef struct vs_object vs_object; /* opaque: k shells (non-owning views)  */
  */
 #define VS_TEX_RGBA_F32 0
 #define VS_TEX_SH_F16 1
+/* VS_TEX_SH_U8: the paper's deployed (baked) texels (Sec. 3 "Mixed
+ *   Resolutions", "Squeezing and Quantization", "Baking Textures"): SH
+ *   coefficients of degree d <= 3 for all four channels -- opacity is view
+ *   dependent too: (r, g, b, alpha) = sigmoid(sum_m sh_{m,c} Y_m(v)) -- one
+ *   byte q each, decoded as value_min + (value_max - value_min) q / 255.
+ *   Band l (coefficients l^2 .. l^2 + 2l) is its own image of
+ *   (tex_w >> l s) x (tex_h >> l s) texels, s = band_shift (s = 1: the
+ *   paper's mixed resolutions, 2048^2 base colour down to 256^2 for band 3;
+ *   s = 0: one resolution).  A texel of band l holds its 2l + 1 coefficients
+ *   as (r, g, b, alpha) byte quadruples in coefficient order, padded to 4,
+ *   16, 32, 32 bytes for l = 0..3; the bands follow each other in one buffer
+ *   (`texels`), each starting on a 256-byte boundary (vs_baked_layout).
+ *   Forward only: vs_render_backward and the backward of vs_render_batch
+ *   return VS_ERR_UNSUPPORTED for these shells (the paper fits continuous
+ *   textures and quantises when baking). */
+#define VS_TEX_SH_U8 2
 
 /* One shell.  All pointers are device memory, kept alive by the caller until
  * vs_free_shells. */
@@ -88,12 +104,27 @@ typedef struct {
   const float* uv;       /* [num_verts, 2]                                */
   const int32_t* tris;   /* [num_tris, 3] vertex indices, CCW = front    */
   int32_t num_tris;      /* 1 <= num_tris <= 2^31 - 2                    */
-  const void* texels;    /* [tex_h, tex_w, texel_pitch] of the format's type */
-  int32_t tex_w, tex_h;  /* 1 .. 65536 each                               */
+  const void* texels;    /* [tex_h, tex_w, texel_pitch] of the format's type;
+                            VS_TEX_SH_U8: the band buffer, 16-byte aligned */
+  int32_t tex_w, tex_h;  /* 1 .. 65536 each (VS_TEX_SH_U8: band 0; both
+                            divisible by 2^(d * band_shift))               */
   int32_t format;        /* VS_TEX_*                                      */
-  int32_t sh_degree;     /* 0..3 for VS_TEX_SH_F16, ignored otherwise     */
-  int32_t texel_pitch;   /* values per texel in memory, >= C (padding ok) */
+  int32_t sh_degree;     /* 0..3 for the SH formats, ignored for RGBA     */
+  int32_t texel_pitch;   /* values per texel in memory, >= C (padding ok);
+                            ignored for VS_TEX_SH_U8                        */
+  int32_t band_shift;    /* VS_TEX_SH_U8: 0..3, ignored otherwise         */
+  float value_min;       /* VS_TEX_SH_U8: decode range, value_min <      */
+  float value_max;       /*   value_max, both finite; ignored otherwise   */
 } vs_shell_desc;
+
+/* Layout of a VS_TEX_SH_U8 buffer (pure host arithmetic): for bands
+ * l = 0..sh_degree, the byte offset, width, height and bytes per texel of
+ * band l (entries past sh_degree are set to 0), and the buffer's total size.
+ * Any output pointer may be NULL.  Errors: VS_ERR_INVALID_ARG for sizes out
+ * of range or not divisible by 2^(sh_degree * band_shift). */
+vs_status vs_baked_layout(int32_t tex_w, int32_t tex_h, int32_t sh_degree, int32_t band_shift,
+                          int64_t band_offset[4], int32_t band_w[4], int32_t band_h[4],
+                          int32_t band_stride[4], int64_t* total_bytes);
 
 typedef struct {
   float world_to_cam[12]; /* row-major 3x4 [R | t]                        */
@@ -145,7 +176,9 @@ const char* vs_last_error(void);
  * descriptors (host memory only); the device arrays stay the caller's.
  * Errors: VS_ERR_INVALID_ARG for k outside [1, VS_MAX_SHELLS], NULL
  * pointers, sizes out of range, unknown format, texel_pitch < C, SH degree
- * outside [0, 3]. */
+ * outside [0, 3]; for VS_TEX_SH_U8 also band_shift outside [0, 3], band
+ * sizes not dividing, a decode range that is not finite and increasing, or
+ * a buffer not 16-byte aligned. */
 vs_status vs_load_shells(vs_ctx* ctx, const vs_shell_desc* shells, int32_t k, vs_object** out);
 vs_status vs_free_shells(vs_ctx* ctx, vs_object* obj);
 

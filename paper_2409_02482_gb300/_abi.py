@@ -27,6 +27,7 @@ STATUS_NAMES = {0: "VS_OK", -1: "VS_ERR_INVALID_ARG", -2: "VS_ERR_CUDA", -3: "VS
 
 VS_TEX_RGBA_F32 = 0
 VS_TEX_SH_F16 = 1
+VS_TEX_SH_U8 = 2
 VS_FLAG_LOSS_L2 = 1 << 0
 VS_FLAG_ALPHA_ATTEN = 1 << 1
 VS_FLAG_TEST_STALL = 1 << 30
@@ -38,7 +39,8 @@ class vs_shell_desc(ctypes.Structure):
                 ("uv", ctypes.c_void_p), ("tris", ctypes.c_void_p), ("num_tris", ctypes.c_int32),
                 ("texels", ctypes.c_void_p), ("tex_w", ctypes.c_int32), ("tex_h", ctypes.c_int32),
                 ("format", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
-                ("texel_pitch", ctypes.c_int32)]
+                ("texel_pitch", ctypes.c_int32), ("band_shift", ctypes.c_int32),
+                ("value_min", ctypes.c_float), ("value_max", ctypes.c_float)]
 
 
 class vs_camera(ctypes.Structure):
@@ -95,6 +97,8 @@ SIGNATURES = {
     "vs_render_batch": ([_P, ctypes.POINTER(vs_batch_item), _I, _P, _I, _P, _SZ, _U, _P], _I),
     "vs_read_stats": ([_P, _P, _I, ctypes.POINTER(vs_stats)], _I),
     "vs_render_noalloc": ([_P, _P, ctypes.POINTER(vs_camera), _P, _P, _P, _U, _P], _I),
+    "vs_baked_layout": ([_I, _I, _I, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                         ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64)], _I),
     "vs_set_batch_tuning": ([_P, _I, _I, ctypes.POINTER(vs_tuning)], _I),
     "vs_get_batch_tuning": ([_P, _I, _I, ctypes.POINTER(vs_tuning)], _I),
     "vs_tune_search": ([ctypes.POINTER(vs_tuning), _I, vs_cost_fn, _P, ctypes.POINTER(vs_tuning),

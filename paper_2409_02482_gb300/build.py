@@ -25,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
               "-I", INCLUDE, "-I", CSRC]
 SOURCES = ["vs_api.cu", "vs_kernels.cu", "vs_tc_any.cu", "vs_tc_rgba.cu", "vs_tc_sh0.cu", "vs_tc_sh1.cu",
-           "vs_tc_sh2.cu", "vs_tc_sh3.cu"]
+           "vs_tc_sh2.cu", "vs_tc_sh3.cu", "vs_tc_u80.cu", "vs_tc_u81.cu", "vs_tc_u82.cu", "vs_tc_u83.cu"]
 
 
 def nvcc() -> str:

@@ -55,7 +55,38 @@ vs_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 int nch_of(const vs_shell_desc& s) {
+  if (s.format == VS_TEX_SH_U8) return 4 * (s.sh_degree + 1) * (s.sh_degree + 1);
   return s.format == VS_TEX_RGBA_F32 ? 4 : 1 + 3 * (s.sh_degree + 1) * (s.sh_degree + 1);
+}
+
+// Layout of a baked (VS_TEX_SH_U8) buffer: band l at (w, h) >> l s, texels of
+// 4, 16, 32, 32 bytes, bands on 256-byte boundaries.
+struct BakedLayout {
+  int64_t offset[4];
+  int32_t w[4], h[4], stride[4];
+  int64_t total;
+};
+
+vs_status baked_layout(int32_t tw, int32_t th, int32_t degree, int32_t shift, BakedLayout& L) {
+  static const int32_t kStride[4] = {4, 16, 32, 32};
+  if (degree < 0 || degree > 3) return fail(VS_ERR_INVALID_ARG, "SH degree %d out of [0, 3]", degree);
+  if (shift < 0 || shift > 3) return fail(VS_ERR_INVALID_ARG, "band_shift %d out of [0, 3]", shift);
+  if (tw < 1 || th < 1 || tw > 65536 || th > 65536)
+    return fail(VS_ERR_INVALID_ARG, "texture %dx%d out of [1, 65536]", tw, th);
+  const int32_t div = 1 << (degree * shift);
+  if (tw % div || th % div)
+    return fail(VS_ERR_INVALID_ARG, "texture %dx%d not divisible by 2^(degree * band_shift) = %d", tw, th, div);
+  std::memset(&L, 0, sizeof L);
+  int64_t off = 0;
+  for (int l = 0; l <= degree; ++l) {
+    L.offset[l] = off;
+    L.w[l] = tw >> (l * shift);
+    L.h[l] = th >> (l * shift);
+    L.stride[l] = kStride[l];
+    off += ((int64_t)L.w[l] * L.h[l] * kStride[l] + 255) / 256 * 256;
+  }
+  L.total = off;
+  return VS_OK;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -72,7 +103,19 @@ vs_status check_shell(const vs_shell_desc& s, int i) {
   if (s.num_tris < 1 || s.num_tris >= kMaxTris) return fail(VS_ERR_INVALID_ARG, "shell %d: num_tris %d out of [1, 2^27)", i, s.num_tris);
   if (s.tex_w < 1 || s.tex_h < 1 || s.tex_w > 65536 || s.tex_h > 65536)
     return fail(VS_ERR_INVALID_ARG, "shell %d: texture %dx%d out of [1, 65536]", i, s.tex_w, s.tex_h);
-  if (s.format != VS_TEX_RGBA_F32 && s.format != VS_TEX_SH_F16) return fail(VS_ERR_INVALID_ARG, "shell %d: unknown format %d", i, s.format);
+  if (s.format != VS_TEX_RGBA_F32 && s.format != VS_TEX_SH_F16 && s.format != VS_TEX_SH_U8)
+    return fail(VS_ERR_INVALID_ARG, "shell %d: unknown format %d", i, s.format);
+  if (s.format == VS_TEX_SH_U8) {
+    BakedLayout L;
+    if (baked_layout(s.tex_w, s.tex_h, s.sh_degree, s.band_shift, L) != VS_OK)
+      return fail(VS_ERR_INVALID_ARG, "shell %d: %s", i, g_err.c_str());
+    if (!std::isfinite(s.value_min) || !std::isfinite(s.value_max) || !(s.value_min < s.value_max))
+      return fail(VS_ERR_INVALID_ARG, "shell %d: decode range [%g, %g] not finite and increasing", i,
+                  (double)s.value_min, (double)s.value_max);
+    if ((uintptr_t)s.pos % 4 || (uintptr_t)s.uv % 8 || (uintptr_t)s.tris % 4 || (uintptr_t)s.texels % 16)
+      return fail(VS_ERR_INVALID_ARG, "shell %d: misaligned array (pos 4 B, uv 8 B, tris 4 B, texels 16 B)", i);
+    return VS_OK;
+  }
   if (s.format == VS_TEX_SH_F16 && (s.sh_degree < 0 || s.sh_degree > 3)) return fail(VS_ERR_INVALID_ARG, "shell %d: SH degree %d out of [0, 3]", i, s.sh_degree);
   if (s.texel_pitch < nch_of(s)) return fail(VS_ERR_INVALID_ARG, "shell %d: texel_pitch %d < %d values", i, s.texel_pitch, nch_of(s));
   size_t esz = s.format == VS_TEX_RGBA_F32 ? 4 : 2;
@@ -172,7 +215,16 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
       s.pos = d.pos; s.uv = reinterpret_cast<const float2*>(d.uv); s.tris = d.tris; s.tex = d.texels;
       s.grad = (do_bwd && req[j].grad_tex) ? req[j].grad_tex[i] : nullptr;
       s.nv = d.num_verts; s.nt = d.num_tris; s.tw = d.tex_w; s.th = d.tex_h;
-      s.fmt = d.format; s.degree = d.format == VS_TEX_SH_F16 ? d.sh_degree : 0; s.pitch = d.texel_pitch;
+      s.fmt = d.format; s.degree = d.format != VS_TEX_RGBA_F32 ? d.sh_degree : 0; s.pitch = d.texel_pitch;
+      if (d.format == VS_TEX_SH_U8) {
+        BakedLayout L;
+        baked_layout(d.tex_w, d.tex_h, d.sh_degree, d.band_shift, L);   // checked at load
+        for (int l = 0; l < 4; ++l) s.boff[l] = L.offset[l];
+        s.bshift = d.band_shift;
+        s.vmin = d.value_min;
+        s.vscale = (d.value_max - d.value_min) / 255.0f;
+        s.pitch = 0;
+      }
       const int esz = d.format == VS_TEX_RGBA_F32 ? 4 : 2;
       const uint64_t tex_align = (uint64_t)(uintptr_t)d.texels | (uint64_t)d.texel_pitch * esz;
       s.vec = d.format == VS_TEX_RGBA_F32 ? (gcd_pow2(tex_align, 16) >= 16 ? 4 : 1) : gcd_pow2(tex_align, 16) / 2;
@@ -206,6 +258,7 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
     int c = TC_ANY;
     if (sh.fmt == VS_TEX_RGBA_F32 && sh.vec == 4 && (!do_bwd || sh.gvec == 4)) c = TC_RGBA;
     else if (sh.fmt == VS_TEX_SH_F16 && sh.vec == 8 && (!do_bwd || sh.gvec == 4)) c = TC_SH0 + sh.degree;
+    else if (sh.fmt == VS_TEX_SH_U8) c = TC_U80 + sh.degree;
     tc = (tc < 0 || tc == c) ? c : TC_ANY;
   }
   P.tc = tc < 0 ? TC_ANY : tc;
@@ -338,6 +391,9 @@ vs_status plan_batch(const vs_ctx* ctx, const vs_batch_item* items, int n, const
     if (s != VS_OK) return fail(s, "item %d: %s", j, g_err.c_str());
     if (!b.out_rgba || (uintptr_t)b.out_rgba % 16) return fail(VS_ERR_INVALID_ARG, "item %d: out_rgba NULL or not 16-byte aligned", j);
     if (do_backward) {
+      for (int i = 0; i < b.obj->k; ++i)
+        if (b.obj->shells[i].format == VS_TEX_SH_U8)
+          return fail(VS_ERR_UNSUPPORTED, "item %d, shell %d: baked bytes (VS_TEX_SH_U8) have no gradient", j, i);
       if (!b.grad_rgb || !b.grad_texels) return fail(VS_ERR_INVALID_ARG, "item %d: backward needs grad_rgb and grad_texels", j);
       for (int i = 0; i < b.obj->k; ++i)
         if (!b.grad_texels[i] || (uintptr_t)b.grad_texels[i] % 4) return fail(VS_ERR_INVALID_ARG, "item %d: grad_texels[%d] NULL or misaligned", j, i);
@@ -417,6 +473,21 @@ double autotune_cost(const vs_tuning* t, void* user) {
 extern "C" {
 
 const char* vs_last_error(void) { return g_err.c_str(); }
+
+vs_status vs_baked_layout(int32_t tex_w, int32_t tex_h, int32_t sh_degree, int32_t band_shift, int64_t band_offset[4],
+                          int32_t band_w[4], int32_t band_h[4], int32_t band_stride[4], int64_t* total_bytes) {
+  BakedLayout L;
+  vs_status s = baked_layout(tex_w, tex_h, sh_degree, band_shift, L);
+  if (s != VS_OK) return s;
+  for (int l = 0; l < 4; ++l) {
+    if (band_offset) band_offset[l] = L.offset[l];
+    if (band_w) band_w[l] = L.w[l];
+    if (band_h) band_h[l] = L.h[l];
+    if (band_stride) band_stride[l] = L.stride[l];
+  }
+  if (total_bytes) *total_bytes = L.total;
+  return VS_OK;
+}
 
 vs_status vs_create(vs_ctx** ctx, int device) {
   if (!ctx) return fail(VS_ERR_INVALID_ARG, "ctx is NULL");
@@ -521,6 +592,9 @@ vs_status vs_render_backward(vs_ctx* ctx, const vs_object* obj, const vs_camera*
                              void* workspace, size_t ws_bytes, uint32_t flags, vs_stream_t stream) {
   vs_status s = check_item(ctx, obj, cam);
   if (s != VS_OK) return s;
+  for (int i = 0; i < obj->k; ++i)
+    if (obj->shells[i].format == VS_TEX_SH_U8)
+      return fail(VS_ERR_UNSUPPORTED, "shell %d: baked bytes (VS_TEX_SH_U8) have no gradient", i);
   if (!hits || !grad_rgb || !grad_texels) return fail(VS_ERR_INVALID_ARG, "hits, grad_rgb and grad_texels are required");
   for (int i = 0; i < obj->k; ++i)
     if (!grad_texels[i] || (uintptr_t)grad_texels[i] % 4) return fail(VS_ERR_INVALID_ARG, "grad_texels[%d] NULL or misaligned", i);

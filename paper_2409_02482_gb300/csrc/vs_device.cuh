@@ -63,8 +63,8 @@ __host__ __device__ constexpr size_t block_smem_bytes(int K, bool bwd) { return 
 // Texel classes: a kernel compiled for TC_ANY decides the format per shell at
 // run time; the others serve batches whose shells all share one format with
 // 16-byte-aligned texels (and gradients).
-enum : int { TC_ANY = 0, TC_RGBA = 1, TC_SH0 = 2 };   // TC_SH0 + degree
-constexpr int kNumTc = TC_SH0 + 4;
+enum : int { TC_ANY = 0, TC_RGBA = 1, TC_SH0 = 2, TC_U80 = 6 };   // TC_SH0 / TC_U80 + degree
+constexpr int kNumTc = TC_U80 + 4;
 
 // Phases of one item.  Large triangles are rasterized by the whole block
 // inside the raster unit that met them.
@@ -93,6 +93,11 @@ struct alignas(16) DShell {
   int32_t vec;                 // texel load width in values (1, 2, 4, 8)
   int32_t gvec;                // gradient atomic width in floats (1, 2, 4)
   int32_t pad0, pad1, pad2;
+  // VS_TEX_SH_U8: byte offset of band l in tex, resolution shift per band,
+  // decode value = vmin + vscale * q
+  long long boff[4];
+  float vmin, vscale;
+  int32_t bshift, pad3;
 };
 
 struct alignas(16) DItem {
@@ -365,11 +370,12 @@ __device__ __forceinline__ void split_coord_f(float X0, float delta, int& i, flo
 }
 
 // Perspective-correct UV of pixel centre (px, py) mapped to texel space
-// (x = u W - 1/2, y = v H - 1/2), interpolated relative to vertex 0.  For
-// triangles spanning at most 8 texels plain FP32 keeps the texel-space
-// error near 1e-6 texel; wider ones go through float-float.
-__device__ __forceinline__ Footprint footprint(const Tri& t, const float2 uv[3], int tw, int th,
-                                               int px, int py) {
+// (x = u W - 1/2, y = v H - 1/2), interpolated relative to vertex 0, as an
+// integer part and a fraction (unclamped).  For triangles spanning at most 8
+// texels plain FP32 keeps the texel-space error near 1e-6 texel; wider ones
+// go through float-float.
+__device__ __forceinline__ void texel_coords(const Tri& t, const float2 uv[3], int tw, int th, int px, int py,
+                                             int& ix, float& fx, int& iy, float& fy) {
   long long e[3];
   edge_values(t, px, py, e);
   const float W = (float)tw, H = (float)th;
@@ -378,16 +384,14 @@ __device__ __forceinline__ Footprint footprint(const Tri& t, const float2 uv[3],
   const float d1x = __fsub_rn(X1, X0), d2x = __fsub_rn(X2, X0);
   const float d1y = __fsub_rn(Y1, Y0), d2y = __fsub_rn(Y2, Y0);
   const float span = fmaxf(fmaxf(fabsf(d1x), fabsf(d2x)), fmaxf(fabsf(d1y), fabsf(d2y)));
-  Footprint f;
-  int ix, iy;
   if (span <= 8.0f) {
     const float w0 = __fmul_rn((float)e[0], t.iw[0]);
     const float w1 = __fmul_rn((float)e[1], t.iw[1]);
     const float w2 = __fmul_rn((float)e[2], t.iw[2]);
     const float rD = __fdividef(1.0f, __fadd_rn(__fadd_rn(w0, w1), w2));
     const float l1 = __fmul_rn(w1, rD), l2 = __fmul_rn(w2, rD);
-    split_coord_f(X0, __fmaf_rn(l1, d1x, __fmul_rn(l2, d2x)), ix, f.fx);
-    split_coord_f(Y0, __fmaf_rn(l1, d1y, __fmul_rn(l2, d2y)), iy, f.fy);
+    split_coord_f(X0, __fmaf_rn(l1, d1x, __fmul_rn(l2, d2x)), ix, fx);
+    split_coord_f(Y0, __fmaf_rn(l1, d1y, __fmul_rn(l2, d2y)), iy, fy);
   } else {
     const ff w0 = ff_mul_f(ll_to_ff(e[0]), t.iw[0]);
     const ff w1 = ff_mul_f(ll_to_ff(e[1]), t.iw[1]);
@@ -395,14 +399,47 @@ __device__ __forceinline__ Footprint footprint(const Tri& t, const float2 uv[3],
     const ff D = ff_add(ff_add(w0, w1), w2);
     const ff ex1 = two_sum(X1, -X0), ex2 = two_sum(X2, -X0);
     const ff ey1 = two_sum(Y1, -Y0), ey2 = two_sum(Y2, -Y0);
-    split_coord(X0, ff_div(ff_add(ff_mul(w1, ex1), ff_mul(w2, ex2)), D), ix, f.fx);
-    split_coord(Y0, ff_div(ff_add(ff_mul(w1, ey1), ff_mul(w2, ey2)), D), iy, f.fy);
+    split_coord(X0, ff_div(ff_add(ff_mul(w1, ex1), ff_mul(w2, ex2)), D), ix, fx);
+    split_coord(Y0, ff_div(ff_add(ff_mul(w1, ey1), ff_mul(w2, ey2)), D), iy, fy);
   }
-  f.x0 = min(max(ix, 0), tw - 1);
-  f.x1 = min(max(ix + 1, 0), tw - 1);
-  f.y0 = min(max(iy, 0), th - 1);
-  f.y1 = min(max(iy + 1, 0), th - 1);
+}
+
+// The two taps per axis, clamped to the image (clamp-to-edge).
+__device__ __forceinline__ Footprint clamp_footprint(int ix, float fx, int iy, float fy, int w, int h) {
+  Footprint f;
+  f.fx = fx;
+  f.fy = fy;
+  f.x0 = min(max(ix, 0), w - 1);
+  f.x1 = min(max(ix + 1, 0), w - 1);
+  f.y0 = min(max(iy, 0), h - 1);
+  f.y1 = min(max(iy + 1, 0), h - 1);
   return f;
+}
+
+// Bilinear footprint (taps and weights) of pixel centre (px, py).
+__device__ __forceinline__ Footprint footprint(const Tri& t, const float2 uv[3], int tw, int th, int px, int py) {
+  int ix, iy;
+  float fx, fy;
+  texel_coords(t, uv, tw, th, px, py, ix, fx, iy, fy);
+  return clamp_footprint(ix, fx, iy, fy, tw, th);
+}
+
+// Texel coordinate of an image 2^s times smaller: from X = ix + fx at full
+// resolution, X' = (X + 1/2) / 2^s - 1/2 = q + (m + 1/2 + fx) / 2^s - 1/2 with
+// ix = q 2^s + m.  The sum m + 1/2 + fx < 2^s + 1 loses at most s bits of fx,
+// which the division by 2^s gives back: the fraction keeps about 2^-24.
+__device__ __forceinline__ void coarser_coord(int ix, float fx, int s, int& ixs, float& fxs) {
+  if (s == 0) {
+    ixs = ix;
+    fxs = fx;
+    return;
+  }
+  const int q = ix >> s;                     // floor division (arithmetic shift)
+  const int m = ix - (q << s);
+  const float t = __fmul_rn(__fadd_rn(__fadd_rn((float)m, 0.5f), fx), __int_as_float((127 - s) << 23)) - 0.5f;
+  const float fl = floorf(t);
+  ixs = q + (int)fl;
+  fxs = __fsub_rn(t, fl);
 }
 
 // ----------------------------------------------------------------------------
@@ -557,6 +594,69 @@ __device__ __forceinline__ Frag decode_sh(const float* val, const float Y[16]) {
     for (int ch = 0; ch < 3; ++ch) z[ch] = fmaf(val[1 + 3 * m + ch], Y[m], z[ch]);
   }
   return {sigmoidf_(z[0]), sigmoidf_(z[1]), sigmoidf_(z[2]), sigmoidf_(val[0])};
+}
+
+// ----------------------------------------------------------------------------
+// baked texels (VS_TEX_SH_U8): RGBA SH bytes, band l at (tw, th) >> l * bshift
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float byte_of(unsigned w, int c) { return __uint2float_rn((w >> (8 * c)) & 0xffu); }
+
+// Band L of a baked texel at full-resolution texel coordinate (ix + fx,
+// iy + fy): the band's own footprint, its 2L + 1 coefficient quadruples
+// bilinearly combined, decoded (vmin + vscale q) and added into
+// z_c += value * Y_m.
+template <int L>
+__device__ __forceinline__ void baked_band(const DShell& s, int ix, float fx, int iy, float fy, const float Y[16],
+                                           float z[4]) {
+  constexpr int NC = 2 * L + 1;
+  constexpr int STRIDE = L == 0 ? 4 : (L == 1 ? 16 : 32);
+  const int sh = L * s.bshift;
+  int bx, by;
+  float bfx, bfy;
+  coarser_coord(ix, fx, sh, bx, bfx);
+  coarser_coord(iy, fy, sh, by, bfy);
+  const int w = s.tw >> sh, h = s.th >> sh;
+  const Footprint f = clamp_footprint(bx, bfx, by, bfy, w, h);
+  const float w00 = (1.0f - f.fx) * (1.0f - f.fy), w10 = f.fx * (1.0f - f.fy);
+  const float w01 = (1.0f - f.fx) * f.fy, w11 = f.fx * f.fy;
+  const unsigned char* base = reinterpret_cast<const unsigned char*>(s.tex) + s.boff[L];
+  const unsigned char* p[4] = {base + ((size_t)f.y0 * w + f.x0) * STRIDE, base + ((size_t)f.y0 * w + f.x1) * STRIDE,
+                               base + ((size_t)f.y1 * w + f.x0) * STRIDE, base + ((size_t)f.y1 * w + f.x1) * STRIDE};
+  unsigned q[4][8];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if constexpr (L == 0) {
+      q[t][0] = __ldg(reinterpret_cast<const unsigned*>(p[t]));
+    } else {
+      const uint4 a = __ldg(reinterpret_cast<const uint4*>(p[t]));
+      q[t][0] = a.x; q[t][1] = a.y; q[t][2] = a.z; q[t][3] = a.w;
+      if constexpr (L >= 2) {
+        const uint4 b = __ldg(reinterpret_cast<const uint4*>(p[t]) + 1);
+        q[t][4] = b.x; q[t][5] = b.y; q[t][6] = b.z; q[t][7] = b.w;
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < NC; ++m)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float b = fmaf(w11, byte_of(q[3][m], c),
+                           fmaf(w01, byte_of(q[2][m], c), fmaf(w10, byte_of(q[1][m], c), w00 * byte_of(q[0][m], c))));
+      const float val = fmaf(s.vscale, b, s.vmin);
+      z[c] = fmaf(val, Y[L * L + m], z[c]);
+    }
+}
+
+// Colour and opacity of a baked fragment: every channel is
+// sigmoid(sum_m sh_{m,c} Y_m(v)) (opacity view dependent too).
+template <int DEG>
+__device__ __forceinline__ Frag fetch_baked(const DShell& s, int ix, float fx, int iy, float fy, const float Y[16]) {
+  float z[4] = {0.f, 0.f, 0.f, 0.f};
+  baked_band<0>(s, ix, fx, iy, fy, Y, z);
+  if constexpr (DEG >= 1) baked_band<1>(s, ix, fx, iy, fy, Y, z);
+  if constexpr (DEG >= 2) baked_band<2>(s, ix, fx, iy, fy, Y, z);
+  if constexpr (DEG >= 3) baked_band<3>(s, ix, fx, iy, fy, Y, z);
+  return {sigmoidf_(z[0]), sigmoidf_(z[1]), sigmoidf_(z[2]), sigmoidf_(z[3])};
 }
 
 // ----------------------------------------------------------------------------

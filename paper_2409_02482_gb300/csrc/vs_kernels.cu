@@ -46,6 +46,10 @@ const TcOps& tc_ops(int tc) {
     case vsd::TC_SH0 + 1: return kTcSh1;
     case vsd::TC_SH0 + 2: return kTcSh2;
     case vsd::TC_SH0 + 3: return kTcSh3;
+    case vsd::TC_U80: return kTcU80;
+    case vsd::TC_U80 + 1: return kTcU81;
+    case vsd::TC_U80 + 2: return kTcU82;
+    case vsd::TC_U80 + 3: return kTcU83;
     default: return kTcAny;
   }
 }

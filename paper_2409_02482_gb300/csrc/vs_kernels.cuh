@@ -301,15 +301,35 @@ __device__ __forceinline__ Frag fetch_sh(const DShell& s, const Footprint& f, co
   return decode_sh<DEG>(val, Y);
 }
 
-// Colour and opacity of one fragment; v = unit ray direction (SH only).
+template <int DEG>
+__device__ __forceinline__ Frag fetch_baked_v(const DShell& s, int ix, float fx, int iy, float fy, const float3 v) {
+  float Y[16];
+  sh_basis(DEG, v.x, v.y, v.z, Y);
+  return fetch_baked<DEG>(s, ix, fx, iy, fy, Y);
+}
+
+// Colour and opacity of one fragment; f = its clamped footprint and (ix +
+// fx, iy + fy) the unclamped texel coordinate (baked bands derive their own
+// footprints from it); v = unit ray direction (SH formats only).
 template <int TC>
-__device__ __forceinline__ Frag fetch_frag(const DShell& s, const Footprint& f, const float3 v) {
+__device__ __forceinline__ Frag fetch_frag(const DShell& s, const Footprint& f, int ix, float fx, int iy, float fy,
+                                           const float3 v) {
   if constexpr (TC == TC_RGBA) {
     float c[4];
     bilinear_rgba<4>(reinterpret_cast<const float*>(s.tex), s.tw, s.pitch, f, c);
     return {c[0], c[1], c[2], c[3]};
+  } else if constexpr (TC >= TC_U80) {
+    return fetch_baked_v<TC - TC_U80>(s, ix, fx, iy, fy, v);
   } else if constexpr (TC >= TC_SH0) {
     return fetch_sh<TC - TC_SH0, 8>(s, f, v);
+  }
+  if (s.fmt == VS_TEX_SH_U8) {
+    switch (s.degree) {
+      case 0: return fetch_baked_v<0>(s, ix, fx, iy, fy, v);
+      case 1: return fetch_baked_v<1>(s, ix, fx, iy, fy, v);
+      case 2: return fetch_baked_v<2>(s, ix, fx, iy, fy, v);
+      default: return fetch_baked_v<3>(s, ix, fx, iy, fy, v);
+    }
   }
   if (s.fmt == VS_TEX_RGBA_F32) {
     float c[4];
@@ -331,11 +351,12 @@ __device__ __forceinline__ Frag fetch_frag(const DShell& s, const Footprint& f, 
 
 // Texel class of a kernel: TC_ANY decides per shell at run time; the others
 // are compiled for one format (RGBA with 16-byte texel loads and gradient
-// reductions, or SH of one degree with 16-byte loads), which keeps the
-// kernel small (one fetch and one scatter body instead of all of them).
+// reductions, SH of one degree with 16-byte loads, or baked bytes of one
+// degree), which keeps the kernel small (one fetch and one scatter body
+// instead of all of them).  is_sh: the format needs the ray direction.
 template <int TC>
 __device__ __forceinline__ bool is_sh(const DShell& s) {
-  if constexpr (TC == TC_ANY) return s.fmt == VS_TEX_SH_F16;
+  if constexpr (TC == TC_ANY) return s.fmt != VS_TEX_RGBA_F32;
   else return TC >= TC_SH0;
 }
 
@@ -366,10 +387,13 @@ __device__ __forceinline__ void scatter_frag(const DShell& s, const Footprint& f
     const float dval[4] = {d.x, d.y, d.z, d.w};
     scatter_grad<4, 4>(s.grad, s.tw, s.pitch, f, dval);
     return;
+  } else if constexpr (TC >= TC_U80) {
+    return;   // baked shells have no adjoint (refused on the host)
   } else if constexpr (TC >= TC_SH0) {
     scatter_sh<TC - TC_SH0, 4>(s, f, v, d);
     return;
   }
+  if (s.fmt == VS_TEX_SH_U8) return;
   if (s.fmt == VS_TEX_RGBA_F32) {
     const float dval[4] = {d.x, d.y, d.z, d.w};
     if (s.gvec == 4) scatter_grad<4, 4>(s.grad, s.tw, s.pitch, f, dval);
@@ -570,7 +594,10 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
         } else {
           const int y = pp / W, x = pp - y * W;
           const float2 uv[3] = {__ldg(s.uv + idx[0]), __ldg(s.uv + idx[1]), __ldg(s.uv + idx[2])};
-          const Footprint f = footprint(Tr, uv, s.tw, s.th, 256 * x + 128, 256 * y + 128);
+          int ix, iy;
+          float fx, fy;
+          texel_coords(Tr, uv, s.tw, s.th, 256 * x + 128, 256 * y + 128, ix, fx, iy, fy);
+          const Footprint f = clamp_footprint(ix, fx, iy, fy, s.tw, s.th);
           if constexpr (BWD) {
             unsigned xy;
             float2 fxy;
@@ -580,7 +607,7 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
           }
           float3 v = make_float3(0.f, 0.f, 1.f);
           if (is_sh<TC>(s)) v = ray_dir(it.cam, x, y);
-          fr = fetch_frag<TC>(s, f, v);
+          fr = fetch_frag<TC>(s, f, ix, fx, iy, fy, v);
           ++nfrag;
         }
         // raw opacity here; the composite applies alpha_w

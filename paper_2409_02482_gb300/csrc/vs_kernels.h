@@ -44,7 +44,7 @@ struct TcOps {
   cudaError_t (*occupancy)(bool bwd, size_t smem, int* blocks_per_sm);
   cudaError_t (*configure)(int most_smem_fwd, int most_smem_bwd);
 };
-extern const TcOps kTcAny, kTcRgba, kTcSh0, kTcSh1, kTcSh2, kTcSh3;
+extern const TcOps kTcAny, kTcRgba, kTcSh0, kTcSh1, kTcSh2, kTcSh3, kTcU80, kTcU81, kTcU82, kTcU83;
 
 cudaError_t upload(char* ws, const UploadChunk& c, cudaStream_t st);
 int plain_forward_launches(const int units[4]);

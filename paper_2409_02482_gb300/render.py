@@ -12,13 +12,15 @@ from typing import List, Optional, Sequence
 import torch
 
 from . import _abi
-from ._abi import (VS_FLAG_ALPHA_ATTEN, VS_FLAG_LOSS_L2, VS_TEX_RGBA_F32, VS_TEX_SH_F16, check, vs_batch_item,
+from ._abi import (VS_FLAG_ALPHA_ATTEN, VS_FLAG_LOSS_L2, VS_TEX_RGBA_F32, VS_TEX_SH_F16, VS_TEX_SH_U8, check,
+                   vs_batch_item,
                    vs_camera, vs_cost_fn, vs_shell_desc, vs_stats, vs_tuning)
 
 __all__ = ["Context", "ShellObject", "camera_struct", "workspace_size", "make_workspace",
            "render", "render_backward", "render_batch", "read_stats", "VSRender",
            "tuning", "set_batch_tuning", "get_batch_tuning", "tune_search", "autotune_batch",
-           "VS_FLAG_ALPHA_ATTEN", "VS_FLAG_LOSS_L2", "VS_TEX_RGBA_F32", "VS_TEX_SH_F16"]
+           "VS_FLAG_ALPHA_ATTEN", "VS_FLAG_LOSS_L2", "VS_TEX_RGBA_F32", "VS_TEX_SH_F16", "VS_TEX_SH_U8",
+           "baked_layout"]
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -69,7 +71,9 @@ class ShellObject:
     """vs_load_shells over device tensors (kept alive by this object).
 
     Each shell: dict(pos=[V,3] f32, uv=[V,2] f32, tris=[T,3] i32,
-    tex=[H,W,pitch] f32 (RGBA) or f16 (SH), fmt, degree)."""
+    tex=[H,W,pitch] f32 (RGBA) or f16 (SH), fmt, degree); baked shells
+    (VS_TEX_SH_U8): tex = the u8 band buffer (vs_baked_layout) and tex_w,
+    tex_h, band_shift, vmin, vmax."""
 
     def __init__(self, ctx: Context, shells: Sequence[dict]):
         self.ctx = ctx
@@ -86,9 +90,14 @@ class ShellObject:
             d.uv = s["uv"].data_ptr()
             d.tris, d.num_tris = s["tris"].data_ptr(), s["tris"].shape[0]
             d.texels = s["tex"].data_ptr()
-            d.tex_h, d.tex_w, d.texel_pitch = s["tex"].shape
             d.format = int(s["fmt"])
             d.sh_degree = int(s.get("degree", 0))
+            if d.format == VS_TEX_SH_U8:
+                d.tex_w, d.tex_h, d.texel_pitch = int(s["tex_w"]), int(s["tex_h"]), 0
+                d.band_shift = int(s.get("band_shift", 0))
+                d.value_min, d.value_max = float(s.get("vmin", -15.0)), float(s.get("vmax", 15.0))
+            else:
+                d.tex_h, d.tex_w, d.texel_pitch = s["tex"].shape
         self.handle = ctypes.c_void_p()
         check(ctx.lib.vs_load_shells(ctx.handle, arr, k, ctypes.byref(self.handle)))
 
@@ -105,11 +114,14 @@ class ShellObject:
         """Upload a synth.Scene (numpy arrays) to the device."""
         shells = []
         for s in scene.shells:
-            shells.append(dict(pos=torch.from_numpy(s.pos).to(device).contiguous(),
-                               uv=torch.from_numpy(s.uv).to(device).contiguous(),
-                               tris=torch.from_numpy(s.tris).to(device).contiguous(),
-                               tex=torch.from_numpy(s.tex).to(device).contiguous(),
-                               fmt=s.fmt, degree=s.degree))
+            d = dict(pos=torch.from_numpy(s.pos).to(device).contiguous(),
+                     uv=torch.from_numpy(s.uv).to(device).contiguous(),
+                     tris=torch.from_numpy(s.tris).to(device).contiguous(),
+                     tex=torch.from_numpy(s.tex).to(device).contiguous(),
+                     fmt=s.fmt, degree=s.degree)
+            if s.fmt == VS_TEX_SH_U8:
+                d.update(tex_w=s.tex_w, tex_h=s.tex_h, band_shift=s.band_shift, vmin=s.vmin, vmax=s.vmax)
+            shells.append(d)
         return cls(ctx, shells)
 
     def free(self):
@@ -203,6 +215,15 @@ def render_batch(ctx: Context, items, ws: torch.Tensor, bg=(0.0, 0.0, 0.0), do_b
     check(ctx.lib.vs_render_batch(ctx.handle, items.arr, items.n, bgv, int(do_backward), _ptr(ws),
                                   ws.numel(), flags, _stream(stream)))
     return items
+
+
+def baked_layout(tex_w: int, tex_h: int, degree: int, band_shift: int):
+    """vs_baked_layout: ([(offset, w, h, stride) per band], total bytes)."""
+    off = (ctypes.c_int64 * 4)()
+    w, h, st = (ctypes.c_int32 * 4)(), (ctypes.c_int32 * 4)(), (ctypes.c_int32 * 4)()
+    total = ctypes.c_int64()
+    check(_abi.load().vs_baked_layout(tex_w, tex_h, degree, band_shift, off, w, h, st, ctypes.byref(total)))
+    return [(off[i], w[i], h[i], st[i]) for i in range(degree + 1)], total.value
 
 
 def tuning(raster_tris: int = 256, shade_pixels: int = 256, blocks_per_sm: int = 0) -> vs_tuning:

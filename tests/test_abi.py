@@ -35,7 +35,7 @@ def test_exports_every_declared_function(lib):
 def test_struct_layouts_match_header_sizes():
     # sizes implied by the C declarations on LP64
     assert ctypes.sizeof(_abi.vs_camera) == 76
-    assert ctypes.sizeof(_abi.vs_shell_desc) == 72
+    assert ctypes.sizeof(_abi.vs_shell_desc) == 80
     assert ctypes.sizeof(_abi.vs_stats) == 64
     assert ctypes.sizeof(_abi.vs_tuning) == 16
 
@@ -212,3 +212,46 @@ def test_tune_search_stops_on_bad_cost(lib):
                            lambda t: -1.0 if t.shade_pixels == 64 else 1.0)
     with pytest.raises(_abi.VSError):
         tune_search(_abi.vs_tuning(256, 256, 0, 0), 0, lambda t: 1.0)
+
+
+# ----------------------------------------------------------------------------
+# the baked byte format (VS_TEX_SH_U8): layout agreement and descriptor checks
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tw,th,deg,shift", [(2048, 2048, 3, 1), (12, 6, 2, 0), (20, 12, 1, 1), (128, 64, 3, 2),
+                                            (5, 3, 0, 3)])
+def test_baked_layout_matches_the_generators(lib, tw, th, deg, shift):
+    import synth
+    from paper_2409_02482_gb300 import baked_layout
+    assert baked_layout(tw, th, deg, shift) == synth.baked_layout(tw, th, deg, shift)
+
+
+@pytest.mark.parametrize("tw,th,deg,shift", [(12, 8, 3, 1), (16, 16, 4, 0), (16, 16, 1, 4), (0, 16, 0, 0)])
+def test_baked_layout_rejects_bad_sizes(lib, tw, th, deg, shift):
+    total = ctypes.c_int64()
+    assert lib.vs_baked_layout(tw, th, deg, shift, None, None, None, None, ctypes.byref(total)) == \
+        _abi.VS_ERR_INVALID_ARG
+
+
+def _baked_desc(**kw):
+    d = _desc(fmt=_abi.VS_TEX_SH_U8, deg=kw.pop("deg", 3), tw=kw.pop("tw", 64), th=kw.pop("th", 32), pitch=0)
+    d.band_shift = kw.pop("shift", 1)
+    d.value_min, d.value_max = kw.pop("vmin", -15.0), kw.pop("vmax", 15.0)
+    if "texels" in kw:
+        d.texels = kw.pop("texels")
+    assert not kw
+    return d
+
+
+def test_load_shells_accepts_a_baked_shell(lib):
+    st, out = _load(lib, [_baked_desc()])
+    assert st == _abi.VS_OK
+    lib.vs_free_shells(_fake_ctx(), out)
+
+
+@pytest.mark.parametrize("bad", [dict(shift=4), dict(tw=60), dict(vmin=1.0, vmax=1.0), dict(vmax=float("inf")),
+                                 dict(texels=0x40008), dict(deg=4)])
+def test_load_shells_rejects_bad_baked_descriptors(lib, bad):
+    st, out = _load(lib, [_baked_desc(**bad)])
+    assert st == _abi.VS_ERR_INVALID_ARG
+    assert not out.value

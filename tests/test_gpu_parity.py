@@ -21,6 +21,9 @@ pytestmark = pytest.mark.gpu
 
 TOL_F32 = 1e-5
 TOL_F16 = 2e-3
+# baked bytes: the oracle reads the same bytes, so only the FP32 arithmetic
+# differs (sums of up to 16 decoded values of magnitude <= 15 per channel)
+TOL_U8 = 2e-4
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +40,9 @@ def ctx(vs):
 
 
 def tol_of(scene):
-    return TOL_F32 if all(s.fmt == FMT_RGBA_F32 for s in scene.shells) else TOL_F16
+    if all(s.fmt == FMT_RGBA_F32 for s in scene.shells):
+        return TOL_F32
+    return TOL_U8 if all(s.fmt == synth.FMT_SH_U8 for s in scene.shells) else TOL_F16
 
 
 def gpu_render(vs, ctx, scene, cam, bg=(0.0, 0.0, 0.0), obj=None, flags=0):
@@ -294,6 +299,78 @@ def test_alpha_atten_backward_matches_oracle(vs, ctx, name, scale, rel):
     (sc, cams), = synth.config_scene(name, scale=scale, views=1)[:1]
     w, *_ = check_backward(vs, ctx, sc, cams[0], (0.2, 0.3, 0.4), rel, flags=vs.VS_FLAG_ALPHA_ATTEN)
     print(f"{name} attenuated grad rel err {w:.2e}")
+
+
+# ----------------------------------------------------------------------------
+# the baked format: RGBA SH bytes, per-band resolutions (Sec. 3 "Mixed
+# Resolutions", "Squeezing and Quantization", "Baking Textures")
+# ----------------------------------------------------------------------------
+
+def _baked_scene(k, n_lat, tex, degree, shift, seed=0):
+    shells = []
+    for i, (pos, uv, tris) in enumerate(synth.displaced_shells(k, n_lat, seed=seed)):
+        buf = synth.baked_sh_texture(tex, tex, degree, shift, np.random.default_rng(100 * seed + i))
+        shells.append(Shell(pos, uv, tris, buf, synth.FMT_SH_U8, degree, tex_w=tex, tex_h=tex, band_shift=shift))
+    return Scene(shells)
+
+
+@pytest.mark.parametrize("degree,shift", [(0, 0), (1, 1), (2, 0), (3, 1), (3, 2)])
+def test_baked_forward_matches_oracle(vs, ctx, degree, shift):
+    sc = _baked_scene(3, 24, 64, degree, shift, seed=degree)
+    for cam in (synth.look_at((0.3, -3.2, 1.1), width=97, height=61),
+                synth.look_at((-2.0, 1.5, 2.0), width=64, height=64)):
+        err, *_ = check_forward(vs, ctx, sc, cam, bg=(0.2, 0.1, 0.3), tol=TOL_U8)
+        print(f"baked deg {degree} shift {shift}: max colour error {err:.2e}")
+
+
+def test_baked_c2b_views_match_oracle(vs, ctx):
+    (sc, cams), = synth.config_scene("c2b", scale=0.01, views=3)
+    for cam in cams:
+        err, *_ = check_forward(vs, ctx, sc, cam, tol=TOL_U8)
+        print(f"c2b scaled view: max colour error {err:.2e}")
+
+
+def test_baked_with_attenuation_matches_oracle(vs, ctx):
+    sc = _baked_scene(2, 20, 32, 2, 1, seed=5)
+    cam = synth.look_at((2.5, -1.5, 1.0), width=80, height=72)
+    check_forward(vs, ctx, sc, cam, bg=(0.0, 0.3, 0.1), tol=TOL_U8, flags=vs.VS_FLAG_ALPHA_ATTEN)
+
+
+def test_baked_batches_bit_identical_to_plain(vs, ctx):
+    """A baked-only batch (compiled for the class) and a batch mixing baked,
+    FP16 SH and FP32 RGBA objects (decided per shell) both give vs_render's
+    bits."""
+    baked = [(_baked_scene(3, 20, 64, 3, 1, seed=s), [synth.look_at((0.5 * s, -3.0, 1.0), width=70, height=50)])
+             for s in range(3)]
+    sh = synth.config_scene("c4", scale=0.001, views=1)[:2]
+    (c1, c1cams), = synth.config_scene("c1", scale=0.25)
+    for objs_cams in (baked, baked + sh + [(c1, c1cams)]):
+        items, objs, ws = _batch_setup(vs, ctx, objs_cams, False)
+        vs.render_batch(ctx, items, ws, bg=(0.1, 0.2, 0.3))
+        assert vs.read_stats(ws)["device_status"] == 0
+        for it in items:
+            ws1 = vs.make_workspace(ctx, [it["obj"]], [it["cam"]])
+            out, hits = vs.render(ctx, it["obj"], it["cam"], ws1, bg=(0.1, 0.2, 0.3))
+            assert torch.equal(out, it["out"])
+            assert torch.equal(hits, it["hits"])
+
+
+def test_baked_shells_have_no_gradient(vs, ctx):
+    from paper_2409_02482_gb300._abi import VS_ERR_UNSUPPORTED, VSError
+    sc = _baked_scene(2, 16, 32, 1, 1)
+    cam = synth.look_at((0.0, -3.0, 0.5), width=32, height=32)
+    obj = vs.ShellObject.from_scene(ctx, sc)
+    ws = vs.make_workspace(ctx, [obj], [cam])
+    out, hits = vs.render(ctx, obj, cam, ws)
+    g = torch.zeros((32, 32, 3), device="cuda")
+    grads = [torch.zeros(1024, device="cuda") for _ in range(obj.k)]
+    with pytest.raises(VSError) as e:
+        vs.render_backward(ctx, obj, cam, ws, hits, g, grads=grads)
+    assert e.value.status == VS_ERR_UNSUPPORTED
+    items = [dict(obj=obj, cam=cam, out=out, grad_rgb=g, grads=grads)]
+    with pytest.raises(VSError) as e:
+        vs.render_batch(ctx, items, ws, do_backward=True)
+    assert e.value.status == VS_ERR_UNSUPPORTED
 
 
 # ----------------------------------------------------------------------------
