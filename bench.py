@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-uneven", action="store_true", help="skip the uneven 32-object batch")
+    p.add_argument("--no-baked", action="store_true", help="skip the baked-format forward leg")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default work-unit sizes instead of autotuning them first")
     return p.parse_args()
@@ -208,6 +209,60 @@ def uneven_batch(ctx, device, stream, steps, autotune=True):
            "tuning": tuning,
            "batched_fragments_per_s": frags / (ms_b * 1e-3), "batched_images_per_s": len(items) / (ms_b * 1e-3)}
     del ws, ws1, items, objects, bi
+    torch.cuda.empty_cache()
+    return out
+
+
+def baked_leg(ctx, device, stream, steps, peak, autotune=True):
+    """The paper's deployed path: forward rendering of baked assets (Sec. 3
+    "Baking Textures"; its Tab. 2 real-time renderer) -- the c2 geometry and
+    100 views at 800x800 with RGBA SH degree 3 bytes, 2048^2 base halving per
+    band (the paper's mixed resolutions), one persistent launch per step.
+    Roofline bytes per fragment: the distinct texels of each band (oracle
+    footprint count on views 0/49/99) times the band's real bytes per texel
+    4 (2l + 1), plus geometry and the image as for the main workload."""
+    import torch
+    import oracle
+    import synth
+    import paper_2409_02482_gb300 as vs
+    (sc, cams), = synth.config_scene("c2b", views=100)
+    obj = vs.ShellObject.from_scene(ctx, sc, device=device)
+    H, W = cams[0].height, cams[0].width
+    outs = torch.empty((len(cams), H, W, 4), device=device)
+    items = vs.BatchItems([dict(obj=obj, cam=c, out=outs[i]) for i, c in enumerate(cams)])
+    ws = vs.make_workspace(ctx, [obj] * len(cams), cams, device=device)
+
+    def step():
+        vs.render_batch(ctx, items, ws, stream=stream)
+
+    tuning = vs.autotune_batch(ctx, items, ws, stream=stream).as_dict() if autotune else None
+    vs.read_stats(ws, reset=True)
+    step()
+    st = vs.read_stats(ws, reset=True)
+    assert st["device_status"] == 0, st
+    frags = st["fragments"]
+    ms = timed(step, steps, 3, stream, lambda: None)
+    band_bytes = np.array([4 * (2 * band + 1) for band in range(4)])
+    D = F = 0
+    sampled = [0, 49, 99]
+    for i in sampled:
+        hits, _, _ = oracle.raster_scene(sc, cams[i])
+        D += float((oracle.footprint_texels_baked(sc, cams[i], hits) * band_bytes).sum())
+        F += int((hits >= 0).sum())
+    per_frag = D / max(F, 1)
+    n = len(cams)
+    geo = n * sum(20 * sh.pos.shape[0] + 12 * sh.tris.shape[0] for sh in sc.shells)
+    img = n * H * W * 16
+    b_alg = frags * per_frag + geo + img
+    achieved = b_alg / (ms * 1e-3) / 1e9
+    out = {"workload": "c2 geometry (7 shells x ~200k tris), 100 views 800x800, baked RGBA SH3 bytes, "
+                       "2048^2 base halving per band, forward only",
+           "ms_per_step": ms, "fragments_per_step": frags, "fragments_per_s": frags / (ms * 1e-3),
+           "images_per_s": n / (ms * 1e-3), "tuning": tuning,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "texel_bytes_per_fragment": per_frag,
+                        "algorithmic_bytes_per_launch": b_alg, "d_sampled_views": sampled}}
+    del ws, items, outs, obj
     torch.cuda.empty_cache()
     return out
 
@@ -425,6 +480,9 @@ def run_ours(args):
     if not args.no_uneven and rank == 0:
         res["uneven_batch"] = uneven_batch(ctx, device, stream, max(3, args.steps // 10),
                                            autotune=not args.no_autotune)
+    if not args.no_baked and rank == 0:
+        res["baked_forward"] = baked_leg(ctx, device, stream, max(5, args.steps // 3), peaks()[0],
+                                         autotune=not args.no_autotune)
 
     if rank != 0:
         if ws_n > 1:

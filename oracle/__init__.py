@@ -108,6 +108,17 @@ def sample_baked(shell, m: int, u: float, v: float) -> np.ndarray:
     return out
 
 
+def footprint_texels_baked(scene, cam, hits: np.ndarray) -> np.ndarray:
+    """Distinct texels per (shell, band) [k, 4] touched by the bilinear
+    footprints of a view's fragments (baked shells; zeros otherwise)."""
+    refs = _ShellRefs(scene.shells)
+    hits = np.ascontiguousarray(hits, np.int32)
+    out = np.zeros((scene.k, 4), np.int64)
+    c = ocam(cam)
+    lib().oracle_footprint_texels_baked(refs.arr, ctypes.c_int32(scene.k), ctypes.byref(c), _ptr(hits), _ptr(out))
+    return out
+
+
 def default_threads() -> int:
     return max(1, os.cpu_count() or 1)
 

@@ -659,6 +659,43 @@ int oracle_footprint_texels(const OShell* shells, int32_t k, const OCam* cam, co
   return 0;
 }
 
+// Baked shells: distinct texels per band (distinct[4 i + l]) touched by the
+// bilinear footprints of every fragment, each band at its own resolution.
+int oracle_footprint_texels_baked(const OShell* shells, int32_t k, const OCam* cam, const int32_t* hits,
+                                  int64_t* distinct) {
+  const int64_t W = cam->width, H = cam->height;
+  for (int i = 0; i < k; ++i) {
+    const OShell& s = shells[i];
+    for (int l = 0; l < 4; ++l) distinct[4 * i + l] = 0;
+    if (s.fmt != FMT_SH_U8) continue;
+    std::vector<SVert> sv = setup_all(s, *cam);
+    for (int l = 0; l <= s.degree; ++l) {
+      const Band b = band_layout(s, l);
+      std::vector<uint8_t> mark((size_t)(b.w * b.h), 0);
+      for (int64_t y = 0; y < H; ++y)
+        for (int64_t x = 0; x < W; ++x) {
+          int32_t h = hits[(size_t)i * H * W + y * W + x];
+          if (h < 0) continue;
+          const int32_t* idx = s.tris + 3 * h;
+          Tri t;
+          int why;
+          if (!prepare_tri(sv, idx, *cam, &t, &why)) continue;
+          const float* uvp[3] = {s.uv + 2 * idx[0], s.uv + 2 * idx[1], s.uv + 2 * idx[2]};
+          double invw[3] = {sv[idx[0]].invw, sv[idx[1]].invw, sv[idx[2]].invw};
+          double uv[2];
+          interp_uv(t, uvp, invw, 256 * x + 128, 256 * y + 128, uv);
+          const Footprint f = footprint_wh(b.w, b.h, uv[0], uv[1]);
+          for (int yb = 0; yb < 2; ++yb)
+            for (int xa = 0; xa < 2; ++xa) mark[(size_t)(f.y[yb] * b.w + f.x[xa])] = 1;
+        }
+      int64_t n = 0;
+      for (uint8_t m : mark) n += m;
+      distinct[4 * i + l] = n;
+    }
+  }
+  return 0;
+}
+
 // --- single-step entry points for the pins --------------------------------------
 int oracle_sh_basis(int32_t deg, const double* v, double* Y) {
   sh_basis(deg, v, Y);

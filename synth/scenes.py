@@ -336,9 +336,16 @@ def baked_sh_texture(tex_w: int, tex_h: int, degree: int, band_shift: int, rng: 
     for band, (off, w, h, stride) in enumerate(bands):
         n = 4 * (2 * band + 1)
         sigma = base_sigma if band == 0 else base_sigma / (2 * band)
-        vals = rng.standard_normal((h, w, n), dtype=np.float32) * np.float32(sigma)
+        # the quantisation of baked_values_to_bytes, in place in FP32 (random
+        # values: the rounding of the scale does not matter)
+        vals = rng.standard_normal((h, w, n), dtype=np.float32)
+        k = np.float32(255.0 / (vmax - vmin))
+        vals *= np.float32(sigma) * k
+        vals += np.float32(-vmin) * k
+        np.rint(vals, out=vals)
+        np.clip(vals, 0, 255, out=vals)
         img = np.zeros((h, w, stride), np.uint8)
-        img[..., :n] = baked_values_to_bytes(vals, vmin, vmax)
+        img[..., :n] = vals
         buf[off:off + w * h * stride] = img.reshape(-1)
     return buf
 
