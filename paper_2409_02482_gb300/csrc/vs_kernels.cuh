@@ -41,6 +41,7 @@ namespace vsd {
 // SETUP
 // ----------------------------------------------------------------------------
 // One warp per unit.
+template <bool HINT>
 static __device__ void unit_setup(const DItem& it, const DShell* sh, int u) {
   if (u < it.clear_units) {
     const size_t total = (size_t)it.k * it.cam.W * it.cam.H;
@@ -48,7 +49,7 @@ static __device__ void unit_setup(const DItem& it, const DShell* sh, int u) {
     const size_t end = min(total, beg + (size_t)kClearPerUnit);
     uint4* p = reinterpret_cast<uint4*>(it.vis + beg);
     const size_t n2 = (end - beg) >> 1;
-    for (size_t i = threadIdx.x & 31; i < n2; i += 32) p[i] = make_uint4(0, 0, 0, 0);
+    for (size_t i = threadIdx.x & 31; i < n2; i += 32) clear_vis2<HINT>(p + i);
     if (((end - beg) & 1) && (threadIdx.x & 31) == 0) it.vis[end - 1] = 0ull;
     return;
   }
@@ -76,10 +77,11 @@ __device__ __forceinline__ int load_tri(const DShell& s, const DCam& c, int t, T
   return make_tri(__ldcg(s.vsetup + idx[0]), __ldcg(s.vsetup + idx[1]), __ldcg(s.vsetup + idx[2]), c.W, c.H, T);
 }
 
+template <bool HINT>
 __device__ __forceinline__ void raster_pixel(const Tri& T, int t, int x, int y, int W, unsigned long long* vis) {
   long long e[3];
   edge_values(T, 256 * x + 128, 256 * y + 128, e);
-  if (covered(T, e)) red_max_u64(vis + (size_t)y * W + x, vis_key(depth_key(T, e), t));
+  if (covered(T, e)) red_max_vis<HINT>(vis + (size_t)y * W + x, vis_key(depth_key(T, e), t));
 }
 
 // Triangle record shared by the lanes of a warp during the raster walk.
@@ -128,6 +130,7 @@ struct RasterCounts {
   unsigned front, back, nearc, guard, large, bad;
 };
 
+template <bool HINT>
 __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, int t0, unsigned long long* vis,
                                              char* smem, RasterCounts& rc) {
   TriS* s_tri = reinterpret_cast<TriS*>(smem);
@@ -216,7 +219,7 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
       if ((e[0] + (q.tl_bw & 1) > 0) && (e[1] + ((q.tl_bw >> 1) & 1) > 0) && (e[2] + ((q.tl_bw >> 2) & 1) > 0)) {
         const TriPos p = s_pos[wbase + o];
         const int S = e[0] + e[1] + e[2];
-        red_max_u64(vis + (size_t)(p.ylo + dy) * W + (p.xlo + dx), vis_key(depth_key32(q.q, e, S, q.rS), q.t));
+        red_max_vis<HINT>(vis + (size_t)(p.ylo + dy) * W + (p.xlo + dx), vis_key(depth_key32(q.q, e, S, q.rS), q.t));
       }
     }
     carry += __popc(bits);
@@ -240,7 +243,7 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
     const int npq = bw * bh;
     for (int p = lane; p < npq; p += 32) {
       const int yy = p / bw;
-      raster_pixel(T, tq, T.xlo + (p - yy * bw), T.ylo + yy, W, vis);
+      raster_pixel<HINT>(T, tq, T.xlo + (p - yy * bw), T.ylo + yy, W, vis);
     }
   }
   __syncwarp();   // the records are reused by the next round
@@ -248,6 +251,7 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
 
 // Raster unit: 32 * it.raster_rounds triangles of one shell in rounds of 32;
 // this warp runs rounds [r0, r1).
+template <bool HINT>
 static __device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* smem, int r0, int r1) {
   int i = 0;
   while (i + 1 < it.k && u >= it.raster_pre[i + 1]) ++i;
@@ -257,7 +261,7 @@ static __device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsH
   unsigned long long* vis = it.vis + (size_t)i * it.cam.W * it.cam.H;
   RasterCounts rc = {0, 0, 0, 0, 0, 0};
   const int rounds = min(r1, min(per_unit, s.nt - base + 31) / 32);
-  for (int r = r0; r < rounds; ++r) raster_round(it, s, base + 32 * r, vis, smem, rc);
+  for (int r = r0; r < rounds; ++r) raster_round<HINT>(it, s, base + 32 * r, vis, smem, rc);
   warp_count(&hdr->front, rc.front);
   warp_count(&hdr->back, rc.back);
   warp_count(&hdr->nearc, rc.nearc);
@@ -526,7 +530,7 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
       tt[d] = -1;
       if (i < k && pix_ok) {
         if (FROM_HITS) tt[d] = __ldg(it.hits + (size_t)i * HW + p);
-        else tt[d] = vis_tri(__ldcg(it.vis + (size_t)i * HW + p));
+        else tt[d] = vis_tri(load_vis<BWD && !FROM_HITS>(it.vis + (size_t)i * HW + p));
       }
     }
 #pragma unroll
@@ -802,8 +806,8 @@ __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS)
     if (!ok) break;
     const DShell* sh = tb.shells + it.shell0;
     switch (ph) {
-      case PH_SETUP: unit_setup(it, sh, u); break;
-      case PH_RASTER: unit_raster(it, sh, u, hdr, smem, 0, it.raster_rounds); break;
+      case PH_SETUP: unit_setup<BWD>(it, sh, u); break;
+      case PH_RASTER: unit_raster<BWD>(it, sh, u, hdr, smem, 0, it.raster_rounds); break;
       default:
         unit_shade<BWD, false, TC>(it, sh, u, hdr, smem, tb.kmax, 0, it.shade_rounds);
     }
