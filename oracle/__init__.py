@@ -149,7 +149,9 @@ def raster(pos, tris, cam, brute: bool = False, threads: Optional[int] = None,
            coverage: bool = False):
     """Per-shell nearest-hit raster (Fig. 3c: first intersection per surface).
 
-    Returns (keys uint64 [H,W], cover int32 [H,W] or None, stats int64 [4]).
+    Returns (keys uint64 [H,W], cover int32 [H,W] or None, stats int64 [5] =
+    front, back/degenerate, behind the near plane, off the guard band,
+    clipped at the near plane).
     keys = (depth key << 32) | (2^32 - 1 - triangle); 0 = miss.
     """
     pos = np.ascontiguousarray(pos, np.float32)
@@ -157,7 +159,7 @@ def raster(pos, tris, cam, brute: bool = False, threads: Optional[int] = None,
     H, W = cam.height, cam.width
     keys = np.zeros((H, W), np.uint64)
     cover = np.zeros((H, W), np.int32) if coverage else None
-    stats = np.zeros(4, np.int64)
+    stats = np.zeros(5, np.int64)
     c = ocam(cam)
     lib().oracle_raster(_ptr(pos), ctypes.c_int32(pos.shape[0]), _ptr(tris),
                         ctypes.c_int32(tris.shape[0]), ctypes.byref(c), ctypes.c_int32(int(brute)),
@@ -172,7 +174,7 @@ def hits_from_keys(keys: np.ndarray) -> np.ndarray:
 
 
 def raster_scene(scene, cam, threads: Optional[int] = None, brute: bool = False):
-    """hits int32 [k,H,W] (-1 = miss), keys uint64 [k,H,W], stats [k,4]."""
+    """hits int32 [k,H,W] (-1 = miss), keys uint64 [k,H,W], stats [k,5]."""
     hs, ks, st = [], [], []
     for s in scene.shells:
         keys, _, stats = raster(s.pos, s.tris, cam, brute=brute, threads=threads)

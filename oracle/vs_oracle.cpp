@@ -79,7 +79,8 @@ struct SVert {
 };
 
 // --- vertex transform (pinned FP32 sequence) --------------------------------
-SVert setup_vertex(const float* p, const OCam& c) {
+// World -> camera space.
+void cam_xyz(const float* p, const OCam& c, float* out) {
   const float* m = c.w2c;
   float x = p[0], y = p[1], z = p[2];
   float xc = m[0] * x;
@@ -94,11 +95,12 @@ SVert setup_vertex(const float* p, const OCam& c) {
   zc = zc + m[9] * y;
   zc = zc + m[10] * z;
   zc = zc + m[11];
+  out[0] = xc; out[1] = yc; out[2] = zc;
+}
+
+// Camera space (zc >= znear) -> snapped screen position, 1/w, depth key.
+SVert project(float xc, float yc, float zc, const OCam& c) {
   SVert v;
-  if (!(zc >= c.znear)) {
-    v.flags = VF_NEAR;
-    return v;
-  }
   float iw = 1.0f / zc;
   float sx = c.fx * xc;
   sx = sx * iw;
@@ -120,6 +122,17 @@ SVert setup_vertex(const float* p, const OCam& c) {
   return v;
 }
 
+SVert setup_vertex(const float* p, const OCam& c) {
+  float pc[3];
+  cam_xyz(p, c, pc);
+  if (!(pc[2] >= c.znear)) {
+    SVert v;
+    v.flags = VF_NEAR;
+    return v;
+  }
+  return project(pc[0], pc[1], pc[2], c);
+}
+
 std::vector<SVert> setup_all(const OShell& s, const OCam& c) {
   std::vector<SVert> v(s.nv);
   for (int i = 0; i < s.nv; ++i) v[i] = setup_vertex(s.pos + 3 * i, c);
@@ -138,6 +151,8 @@ struct Tri {
   uint32_t q[3];
   bool tl[3];              // edge j (opposite vertex j) is a top or left edge
   int64_t xlo, xhi, ylo, yhi;
+  double iw[3];            // 1/w per vertex
+  float uv[3][2];          // texture coordinates per vertex (if the shell has UVs)
 };
 
 // orient(a, b, p) = (bx - ax)(py - ay) - (by - ay)(px - ax); for a
@@ -159,15 +174,22 @@ inline bool covered(const Tri& t, const int64_t e[3]) {
   return true;
 }
 
-// Returns 0 if culled (reason in *why: 1 back/degenerate, 2 near, 3 guard).
-bool prepare_tri(const std::vector<SVert>& sv, const int32_t* idx, const OCam& c,
-                 Tri* t, int* why) {
-  const SVert* v[3] = {&sv[idx[0]], &sv[idx[1]], &sv[idx[2]]};
-  int f = v[0]->flags | v[1]->flags | v[2]->flags;
-  if (f & VF_NEAR) { *why = 2; return false; }
-  if (f & VF_GUARD) { *why = 3; return false; }
+// A vertex of a (possibly clipped) triangle: screen data and UV.
+struct PVert {
+  SVert sv;
+  float uv[2];
+};
+
+// Orientation, fill rule and pixel box of three screen vertices; false if
+// a vertex is off the guard band (*why = 3) or the triangle is back-facing
+// or degenerate (*why = 1).
+bool finish_tri(const PVert* p0, const PVert* p1, const PVert* p2, const OCam& c, Tri* t, int* why) {
+  const PVert* v[3] = {p0, p1, p2};
+  if ((v[0]->sv.flags | v[1]->sv.flags | v[2]->sv.flags) & VF_GUARD) { *why = 3; return false; }
   for (int j = 0; j < 3; ++j) {
-    t->X[j] = v[j]->X; t->Y[j] = v[j]->Y; t->q[j] = v[j]->q;
+    t->X[j] = v[j]->sv.X; t->Y[j] = v[j]->sv.Y; t->q[j] = v[j]->sv.q;
+    t->iw[j] = v[j]->sv.invw;
+    t->uv[j][0] = v[j]->uv[0]; t->uv[j][1] = v[j]->uv[1];
   }
   int64_t a2 = (t->X[1] - t->X[0]) * (t->Y[2] - t->Y[0]) -
                (t->X[2] - t->X[0]) * (t->Y[1] - t->Y[0]);
@@ -194,6 +216,81 @@ bool prepare_tri(const std::vector<SVert>& sv, const int32_t* idx, const OCam& c
   return true;
 }
 
+// Rasterizable parts of mesh triangle `tri` (0, 1 or 2).  *why: 0 whole, 1
+// back-facing or degenerate, 2 entirely nearer than znear, 3 off the guard
+// band, 4 clipped at the near plane.
+//
+// Near-plane clipping (the paper's close-up views need it; it only says
+// the meshes are rasterized): a triangle with one or two vertices nearer
+// than znear is clipped against the plane z = znear in camera space
+// (Sutherland-Hodgman, vertices in order).  The point on a crossing edge is
+// computed from its (inside, outside) ends, t = (znear - z_out) / (z_in -
+// z_out), x = x_out + t (x_in - x_out) (same for y and the UVs), z = znear,
+// all in FP32 in this order, so two triangles sharing the edge get the same
+// point; it is projected and snapped like a vertex.  The 3- or 4-gon is
+// split into (P0, P1, P2) and (P0, P2, P3); each part is culled or
+// rasterized under the rules above and keeps the mesh triangle's id.
+int prepare_tris(const OShell& s, const std::vector<SVert>& sv, int32_t tri, const OCam& c, Tri out[2],
+                 int* why) {
+  const int32_t* idx = s.tris + 3 * tri;
+  PVert v[3];
+  int nnear = 0;
+  for (int j = 0; j < 3; ++j) {
+    v[j].sv = sv[idx[j]];
+    v[j].uv[0] = s.uv ? s.uv[2 * idx[j]] : 0.0f;
+    v[j].uv[1] = s.uv ? s.uv[2 * idx[j] + 1] : 0.0f;
+    nnear += (v[j].sv.flags & VF_NEAR) ? 1 : 0;
+  }
+  if (nnear == 3) { *why = 2; return 0; }
+  if (nnear == 0) return finish_tri(&v[0], &v[1], &v[2], c, &out[0], why) ? 1 : 0;
+  float pc[3][3];
+  for (int j = 0; j < 3; ++j) cam_xyz(s.pos + 3 * idx[j], c, pc[j]);
+  PVert poly[4];
+  int n = 0;
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a + 1) % 3;
+    const bool ina = pc[a][2] >= c.znear, inb = pc[b][2] >= c.znear;
+    if (ina) poly[n++] = v[a];
+    if (ina != inb) {
+      const int i = ina ? a : b, o = ina ? b : a;
+      float t = (c.znear - pc[o][2]) / (pc[i][2] - pc[o][2]);
+      float x = pc[o][0] + t * (pc[i][0] - pc[o][0]);
+      float y = pc[o][1] + t * (pc[i][1] - pc[o][1]);
+      float u = v[o].uv[0] + t * (v[i].uv[0] - v[o].uv[0]);
+      float w = v[o].uv[1] + t * (v[i].uv[1] - v[o].uv[1]);
+      poly[n].sv = project(x, y, c.znear, c);
+      poly[n].uv[0] = u;
+      poly[n].uv[1] = w;
+      ++n;
+    }
+  }
+  int m = 0, w;
+  if (finish_tri(&poly[0], &poly[1], &poly[2], c, &out[m], &w)) ++m;
+  if (n == 4 && finish_tri(&poly[0], &poly[2], &poly[3], c, &out[m], &w)) ++m;
+  *why = 4;
+  return m;
+}
+
+// The part of mesh triangle `tri` used to shade fixed-point pixel centre
+// (px, py): its only part, or, for a triangle clipped into two, the part
+// that covers the pixel under the fill rule (the parts do not overlap), the
+// first one if neither does.  False if nothing of the triangle is
+// rasterizable.
+bool tri_at(const OShell& s, const std::vector<SVert>& sv, int32_t tri, const OCam& c, int64_t px, int64_t py,
+            Tri* t) {
+  Tri parts[2];
+  int why;
+  const int n = prepare_tris(s, sv, tri, c, parts, &why);
+  if (n == 0) return false;
+  *t = parts[0];
+  if (n == 2) {
+    int64_t e[3];
+    edge_values(parts[1], px, py, e);
+    if (covered(parts[1], e)) *t = parts[1];
+  }
+  return true;
+}
+
 inline uint32_t depth_key(const Tri& t, const int64_t e[3]) {
   __int128 n = (__int128)e[0] * t.q[0] + (__int128)e[1] * t.q[1] + (__int128)e[2] * t.q[2];
   __int128 s = (__int128)e[0] + e[1] + e[2];
@@ -204,11 +301,12 @@ void raster_rows(const OShell& s, const OCam& c, const std::vector<SVert>& sv, i
                  int64_t y0, int64_t y1, uint64_t* keys, int32_t* cover, int64_t* stats) {
   const int64_t W = c.width;
   for (int32_t ti = 0; ti < s.nt; ++ti) {
-    Tri t;
+    Tri parts[2];
     int why;
-    bool ok = prepare_tri(sv, s.tris + 3 * ti, c, &t, &why);
+    const int np = prepare_tris(s, sv, ti, c, parts, &why);
     if (stats) stats[why] += 1;
-    if (!ok) continue;
+    for (int pi = 0; pi < np; ++pi) {
+    const Tri& t = parts[pi];
     int64_t xa = t.xlo, xb = t.xhi, ya = std::max(t.ylo, y0), yb = std::min(t.yhi, y1 - 1);
     if (brute) { xa = 0; xb = W - 1; ya = y0; yb = y1 - 1; }
     for (int64_t y = ya; y <= yb; ++y) {
@@ -223,6 +321,7 @@ void raster_rows(const OShell& s, const OCam& c, const std::vector<SVert>& sv, i
         uint64_t& slot = keys[y * W + x];
         if (key > slot) slot = key;
       }
+    }
     }
   }
 }
@@ -391,16 +490,15 @@ void ray_dir(const OCam& c, int64_t x, int64_t y, double v[3]) {
 }
 
 // Perspective-correct UV at pixel centre (px, py) (1/256 px fixed point).
-void interp_uv(const Tri& t, const float* const uv[3], const double invw[3], int64_t px, int64_t py,
-               double out[2]) {
+void interp_uv(const Tri& t, int64_t px, int64_t py, double out[2]) {
   int64_t e[3];
   edge_values(t, px, py, e);
   double w[3], sw = 0.0;
-  for (int j = 0; j < 3; ++j) { w[j] = (double)e[j] * invw[j]; sw += w[j]; }
+  for (int j = 0; j < 3; ++j) { w[j] = (double)e[j] * t.iw[j]; sw += w[j]; }
   out[0] = out[1] = 0.0;
   for (int j = 0; j < 3; ++j) {
-    out[0] += w[j] / sw * uv[j][0];
-    out[1] += w[j] / sw * uv[j][1];
+    out[0] += w[j] / sw * t.uv[j][0];
+    out[1] += w[j] / sw * t.uv[j][1];
   }
 }
 
@@ -438,12 +536,9 @@ bool shade_fragment(const OShell& s, const OCam& c, const std::vector<SVert>& sv
                     int64_t x, int64_t y, const double* Y, const double* v, int flags, Frag* f) {
   const int32_t* idx = s.tris + 3 * tri;
   Tri t;
-  int why;
-  if (!prepare_tri(sv, idx, c, &t, &why)) return false;
-  const float* uvp[3] = {s.uv + 2 * idx[0], s.uv + 2 * idx[1], s.uv + 2 * idx[2]};
-  double invw[3] = {sv[idx[0]].invw, sv[idx[1]].invw, sv[idx[2]].invw};
+  if (!tri_at(s, sv, tri, c, 256 * x + 128, 256 * y + 128, &t)) return false;
   double uv[2];
-  interp_uv(t, uvp, invw, 256 * x + 128, 256 * y + 128, uv);
+  interp_uv(t, 256 * x + 128, 256 * y + 128, uv);
   if (s.fmt == FMT_SH_U8) {
     // RGBA all view-dependent: channel c = sigmoid(sum_m sh_{m,c} Y_m(v))
     const int nb = (s.degree + 1) * (s.degree + 1);
@@ -499,21 +594,22 @@ int oracle_setup_vertices(const float* pos, int32_t nv, const OCam* cam, int64_t
 
 // keys: [H*W] zero-initialised by the caller; max of (K << 32 | ~tri).
 // cover (optional): [H*W] zero-initialised, += 1 per covering front triangle.
-// stats (optional): [4] = {front, back or zero-area, near, guard band}.
+// stats (optional): [5] = {front, back or zero-area, behind the near plane,
+// guard band, clipped at the near plane}.
 int oracle_raster(const float* pos, int32_t nv, const int32_t* tris, int32_t nt, const OCam* cam,
                   int32_t brute, int32_t nthreads, uint64_t* keys, int32_t* cover, int64_t* stats) {
   OShell s{};
   s.pos = pos; s.nv = nv; s.tris = tris; s.nt = nt;
   std::vector<SVert> sv = setup_all(s, *cam);
-  if (stats) std::memset(stats, 0, 4 * sizeof(int64_t));
+  if (stats) std::memset(stats, 0, 5 * sizeof(int64_t));
   int nth = std::max(1, nthreads);
-  std::vector<int64_t> st(4 * nth, 0);
+  std::vector<int64_t> st(5 * nth, 0);
   parallel_rows(cam->height, nth, [&](int64_t y0, int64_t y1, int i) {
-    raster_rows(s, *cam, sv, brute, y0, y1, keys, cover, st.data() + 4 * i);
+    raster_rows(s, *cam, sv, brute, y0, y1, keys, cover, st.data() + 5 * i);
   });
   if (stats) {
     // every band sees every triangle once: report the counts of band 0
-    for (int j = 0; j < 4; ++j) stats[j] = st[j];
+    for (int j = 0; j < 5; ++j) stats[j] = st[j];
   }
   return 0;
 }
@@ -640,14 +736,10 @@ int oracle_footprint_texels(const OShell* shells, int32_t k, const OCam* cam, co
       for (int64_t x = 0; x < W; ++x) {
         int32_t h = hits[(size_t)i * H * W + y * W + x];
         if (h < 0) continue;
-        const int32_t* idx = s.tris + 3 * h;
         Tri t;
-        int why;
-        if (!prepare_tri(sv, idx, *cam, &t, &why)) continue;
-        const float* uvp[3] = {s.uv + 2 * idx[0], s.uv + 2 * idx[1], s.uv + 2 * idx[2]};
-        double invw[3] = {sv[idx[0]].invw, sv[idx[1]].invw, sv[idx[2]].invw};
+        if (!tri_at(s, sv, h, *cam, 256 * x + 128, 256 * y + 128, &t)) continue;
         double uv[2];
-        interp_uv(t, uvp, invw, 256 * x + 128, 256 * y + 128, uv);
+        interp_uv(t, 256 * x + 128, 256 * y + 128, uv);
         Footprint f = footprint(s, uv[0], uv[1]);
         for (int b = 0; b < 2; ++b)
           for (int a = 0; a < 2; ++a) mark[(size_t)f.y[b] * s.tw + f.x[a]] = 1;
@@ -676,14 +768,10 @@ int oracle_footprint_texels_baked(const OShell* shells, int32_t k, const OCam* c
         for (int64_t x = 0; x < W; ++x) {
           int32_t h = hits[(size_t)i * H * W + y * W + x];
           if (h < 0) continue;
-          const int32_t* idx = s.tris + 3 * h;
           Tri t;
-          int why;
-          if (!prepare_tri(sv, idx, *cam, &t, &why)) continue;
-          const float* uvp[3] = {s.uv + 2 * idx[0], s.uv + 2 * idx[1], s.uv + 2 * idx[2]};
-          double invw[3] = {sv[idx[0]].invw, sv[idx[1]].invw, sv[idx[2]].invw};
+          if (!tri_at(s, sv, h, *cam, 256 * x + 128, 256 * y + 128, &t)) continue;
           double uv[2];
-          interp_uv(t, uvp, invw, 256 * x + 128, 256 * y + 128, uv);
+          interp_uv(t, 256 * x + 128, 256 * y + 128, uv);
           const Footprint f = footprint_wh(b.w, b.h, uv[0], uv[1]);
           for (int yb = 0; yb < 2; ++yb)
             for (int xa = 0; xa < 2; ++xa) mark[(size_t)(f.y[yb] * b.w + f.x[xa])] = 1;
@@ -729,9 +817,11 @@ int oracle_sample_baked(const uint8_t* tex, int32_t tw, int32_t th, int32_t degr
 int oracle_interp_uv(const int64_t* X, const int64_t* Y, const double* invw, const float* uv,
                      int64_t px, int64_t py, double* out) {
   Tri t{};
-  for (int j = 0; j < 3; ++j) { t.X[j] = X[j]; t.Y[j] = Y[j]; }
-  const float* uvp[3] = {uv, uv + 2, uv + 4};
-  interp_uv(t, uvp, invw, px, py, out);
+  for (int j = 0; j < 3; ++j) {
+    t.X[j] = X[j]; t.Y[j] = Y[j]; t.iw[j] = invw[j];
+    t.uv[j][0] = uv[2 * j]; t.uv[j][1] = uv[2 * j + 1];
+  }
+  interp_uv(t, px, py, out);
   return 0;
 }
 

@@ -569,6 +569,171 @@ def test_constant_sh_textures_closed_form():
 
 
 # ----------------------------------------------------------------------------
+# near-plane clipping (close-up views): triangles crossing z = znear are cut
+# there in camera space, the rest is rasterized under the same rules
+# ----------------------------------------------------------------------------
+
+def _tilted_lattice(n=14, seed=0):
+    """A planar lattice in camera space (identity pose) from z = 0.02 (bottom
+    rows, behind a near plane at 0.5) to z = 2.2 (top), jittered vertices;
+    world = camera space, so rays and depths are known exactly."""
+    rng = np.random.default_rng(seed)
+    g = np.linspace(-1.0, 1.0, n)
+    gx, gy = np.meshgrid(g, g)
+    gx = gx + rng.uniform(-0.02, 0.02, gx.shape) * (np.abs(gx) < 1)
+    gy = gy + rng.uniform(-0.02, 0.02, gy.shape) * (np.abs(gy) < 1)
+    z = 1.11 - 1.09 * gy                         # y = +1 (bottom of the image) nearest
+    pos = np.stack([0.9 * gx * z, 0.9 * gy * z * 0.7, z], -1).reshape(-1, 3).astype(np.float32)
+    uv = np.stack([(gx + 1) / 2, (gy + 1) / 2], -1).reshape(-1, 2).astype(np.float32)
+    tris = []
+    for r in range(n - 1):
+        for c in range(n - 1):
+            a, b, d, e = r * n + c, r * n + c + 1, (r + 1) * n + c, (r + 1) * n + c + 1
+            tris += [[a, b, e], [a, e, d]]
+    tris = np.array(tris, np.int32)
+    return pos, uv, tris
+
+
+def _identity_camera(w, h, f, znear):
+    return Camera(world_to_cam=np.concatenate([np.eye(3), np.zeros((3, 1))], 1).astype(np.float32),
+                  fx=f, fy=f, cx=w / 2.0, cy=h / 2.0, znear=znear, width=w, height=h)
+
+
+def _front_facing(pos, tris, cam):
+    """Orient every triangle front-facing in the camera (normals towards it)."""
+    p = pos.astype(np.float64)[tris]
+    n = np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0])
+    # front = counter-clockwise seen from the camera at the origin looking +z
+    # with y down: the normal points towards the camera, n . centroid < 0
+    flip = np.einsum("ij,ij->i", n, p.mean(1)) > 0
+    t = tris.copy()
+    t[flip] = t[flip][:, [0, 2, 1]]
+    return t
+
+
+def test_clipping_covers_the_visible_part_of_a_cut_lattice_exactly_once():
+    """A lattice cut by the near plane: every pixel whose ray meets it in
+    front of znear (by a margin) is covered exactly once -- clipped and
+    unclipped parts tile without cracks, also along mesh edges cut by the
+    plane, where both triangles must compute the same point -- and pixels
+    whose hit lies behind znear are not covered."""
+    w, h, f, znear = 96, 80, 70.0, 0.5
+    cam = _identity_camera(w, h, f, znear)
+    pos, uv, tris = _tilted_lattice()
+    tris = _front_facing(pos, tris, cam)
+    _, cover, stats = oracle.raster(pos, tris, cam, coverage=True)
+    assert stats[4] > 10 and stats[2] > 10              # clipped and fully behind
+    assert cover.max() <= 1
+    # FP64 ray against the lattice plane pieces: ray cast on the mesh
+    ys, xs = np.mgrid[0:h, 0:w]
+    d = np.stack([(xs + 0.5 - cam.cx) / f, (ys + 0.5 - cam.cy) / f, np.ones(xs.shape)], -1)
+    ids, tt, _ = raycast_front(np.zeros(3), d / np.linalg.norm(d, axis=-1, keepdims=True), pos, tris)
+    z_hit = tt.reshape(h, w) / np.linalg.norm(d, axis=-1)         # camera z of the hit
+    hit = ids.reshape(h, w) >= 0
+    # away from the mesh border, where the hit is near an edge the fill rule decides
+    scr_ok = np.ones((h, w), bool)
+    front = hit & (z_hit > znear * 1.02)
+    behind = hit & (z_hit < znear * 0.98)
+    inner = front & np.roll(front, 1, 0) & np.roll(front, -1, 0) & np.roll(front, 1, 1) & np.roll(front, -1, 1)
+    assert inner.sum() > 2000 and behind.sum() > 200
+    assert np.all(cover[inner & scr_ok] == 1)
+    assert np.all(cover[behind] == 0)
+
+
+def test_clipped_parts_interpolate_the_ray_plane_uv():
+    """UVs at the cut are interpolated along the 3D edge, and the clipped
+    parts interpolate perspective-correctly from them: the UV seen through a
+    pixel equals the UV of the FP64 ray-plane hit, on either side of a
+    lattice edge cut by the near plane."""
+    w, h, f, znear = 192, 160, 140.0, 0.5
+    cam = _identity_camera(w, h, f, znear)
+    pos, uv, tris = _tilted_lattice(seed=3)
+    tris = _front_facing(pos, tris, cam)
+    N = 16
+    tex = np.zeros((N, N, 4), np.float64)
+    tex[..., 0] = np.arange(N)[None, :]              # r = u N - 1/2 after bilinear, inside
+    tex[..., 1] = np.arange(N)[:, None]              # g = v N - 1/2
+    tex[..., 3] = 1.0
+    sc = Scene([Shell(pos, uv, tris, tex, FMT_RGBA_F32)])
+    rgba, hits, _ = oracle.render(sc, cam)
+    ys, xs = np.mgrid[0:h, 0:w]
+    d = np.stack([(xs + 0.5 - cam.cx) / f, (ys + 0.5 - cam.cy) / f, np.ones(xs.shape)], -1)
+    p64 = pos.astype(np.float64)
+    ps, _ = project64(pos, cam)
+    checked = 0
+    stats = oracle.raster(pos, tris, cam)[2]
+    assert stats[4] > 10
+    for y, x in zip(*np.nonzero(hits[0] >= 0)):
+        t = tris[hits[0, y, x]]
+        a, b, c = p64[t]
+        n = np.cross(b - a, c - a)
+        dd = d[y, x]
+        pt = dd * (n @ a) / (n @ dd)
+        A = np.stack([a - c, b - c], 1)
+        b01 = np.linalg.lstsq(A, pt - c, rcond=None)[0]
+        beta = np.array([b01[0], b01[1], 1 - b01.sum()])
+        want = beta @ uv[t].astype(np.float64)
+        if np.any((want < 0.5 / N + 1e-3) | (want > 1 - 0.5 / N - 1e-3)):
+            continue                                  # clamp-to-edge zone
+        got = (rgba[y, x, :2] + 0.5) / N
+        # vertices snap to 1/256 px: on ~14 px triangles spanning 1/13 in UV
+        # that moves the UV by up to ~2e-5
+        assert np.abs(got - want).max() < 1e-4
+        if min(p64[t][:, 2]) < znear:                # a clipped triangle
+            checked += 1
+    assert checked > 150
+
+
+def test_close_up_nested_shells_match_a_ray_cast_that_skips_the_near_zone():
+    """Camera close to nested shells with the near plane through the outer
+    one: each shell's nearest front hit is the FP64 ray cast's nearest front
+    hit with camera depth >= znear (away from edges and from the cut)."""
+    geo = synth.concentric_icospheres([1.0, 0.8], subdiv=4)
+    cam = synth.look_at((0.0, -1.45, 0.25), width=72, height=72, fov_y_deg=60.0, znear=0.6)
+    eye, dirs = pixel_rays(cam)
+    R = cam.world_to_cam[:, :3].astype(np.float64)
+    checked = 0
+    clipped_seen = 0
+    for i, (pos, uv, tris) in enumerate(geo):
+        _, cover, stats = oracle.raster(pos, tris, cam, coverage=True)
+        clipped_seen += stats[4]
+        hits = oracle.hits_from_keys(oracle.raster(pos, tris, cam)[0])
+        p = pos.astype(np.float64)
+        a, b, c = p[tris[:, 0]], p[tris[:, 1]], p[tris[:, 2]]
+        n = np.cross(b - a, c - a)
+        for y in range(0, 72, 2):
+            for x in range(0, 72, 2):
+                dd = dirs[y, x]
+                denom = n @ dd
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    tt = np.einsum("ij,ij->i", n, a - eye) / denom
+                P = eye + tt[:, None] * dd
+                zc = (P - eye) @ R[2]
+                # inside-triangle test via barycentrics
+                v0, v1, v2 = b - a, c - a, P - a
+                d00 = np.einsum("ij,ij->i", v0, v0); d01 = np.einsum("ij,ij->i", v0, v1)
+                d11 = np.einsum("ij,ij->i", v1, v1); d20 = np.einsum("ij,ij->i", v2, v0)
+                d21 = np.einsum("ij,ij->i", v2, v1)
+                den = d00 * d11 - d01 * d01
+                bv = (d11 * d20 - d01 * d21) / den
+                bw = (d00 * d21 - d01 * d20) / den
+                bu = 1 - bv - bw
+                mb = np.minimum(np.minimum(bu, bv), bw)
+                front = (denom < 0) & (tt > 0)
+                ok = front & (mb > 2e-3) & (zc >= cam.znear * 1.01)
+                # undecidable here: a front face within 2e-3 (barycentric) of
+                # its edge, or hit within 1 % of the near plane
+                edge = front & (np.abs(mb) <= 2e-3) & (zc >= cam.znear * 0.99)
+                cut = front & (mb > -2e-3) & (np.abs(zc - cam.znear) < cam.znear * 0.01)
+                if edge.any() or cut.any():
+                    continue
+                want = int(np.argmin(np.where(ok, tt, np.inf))) if ok.any() else -1
+                assert hits[y, x] == want, (i, y, x)
+                checked += 1
+    assert clipped_seen > 50 and checked > 800
+
+
+# ----------------------------------------------------------------------------
 # transparency attenuation (Sec. 3): alpha_w = 2 sigmoid(10 |v . n|) - 1
 # ----------------------------------------------------------------------------
 
