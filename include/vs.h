@@ -129,7 +129,9 @@ vs_status vs_baked_layout(int32_t tex_w, int32_t tex_h, int32_t sh_degree, int32
 typedef struct {
   float world_to_cam[12]; /* row-major 3x4 [R | t]                        */
   float fx, fy, cx, cy;   /* pinhole intrinsics in pixels                  */
-  float znear;            /* > 0; faces with a vertex nearer are culled   */
+  float znear;            /* > 0: near plane in camera space; faces crossing
+                             it are clipped there (z = znear), faces wholly
+                             nearer are culled                            */
   int32_t width, height;  /* 1 .. 8192 each                                */
 } vs_camera;
 
@@ -173,7 +175,13 @@ const char* vs_last_error(void);
 /* --- assets ---------------------------------------------------------------- */
 
 /* Wraps k shells (index 0 = outermost) into an object.  Copies the
- * descriptors (host memory only); the device arrays stay the caller's.
+ * descriptors (host memory only); the device arrays stay the caller's.  The
+ * first render with the object reads its vertex positions once (a
+ * synchronous device-to-host copy: make that call before any stream
+ * capture) to bound each shell; calls whose cameras keep every shell in
+ * front of the near plane run kernels without the clipping code, the others
+ * run the generic kernels that clip.  Reload the object if its positions
+ * change.
  * Errors: VS_ERR_INVALID_ARG for k outside [1, VS_MAX_SHELLS], NULL
  * pointers, sizes out of range, unknown format, texel_pitch < C, SH degree
  * outside [0, 3]; for VS_TEX_SH_U8 also band_shift outside [0, 3], band
@@ -344,11 +352,13 @@ typedef struct {
   uint64_t fragments;        /* (pixel, shell) pairs shaded (hits)            */
   uint64_t tris_front;       /* triangles rasterized (front-facing, valid)    */
   uint64_t tris_culled_back; /* back-facing or zero-area                       */
-  uint64_t tris_culled_near; /* a vertex nearer than znear                    */
+  uint64_t tris_culled_near; /* every vertex nearer than znear                */
   uint64_t tris_culled_guard;/* a vertex beyond +-32768 px                    */
   uint64_t tris_large;       /* rasterized cooperatively by a whole block     */
   uint64_t launches;         /* kernels enqueued by the calls (table uploads
                                 included), as declared by the host side      */
+  uint64_t tris_clipped;     /* one or two vertices nearer than znear: clipped
+                                at the near plane, the rest rasterized       */
 } vs_stats;
 
 /* Synchronizes `stream`, copies the counters accumulated in `workspace`

@@ -72,7 +72,8 @@ class vs_stats(ctypes.Structure):
     _fields_ = [("device_status", ctypes.c_int32), ("fragments", ctypes.c_uint64),
                 ("tris_front", ctypes.c_uint64), ("tris_culled_back", ctypes.c_uint64),
                 ("tris_culled_near", ctypes.c_uint64), ("tris_culled_guard", ctypes.c_uint64),
-                ("tris_large", ctypes.c_uint64), ("launches", ctypes.c_uint64)]
+                ("tris_large", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("tris_clipped", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

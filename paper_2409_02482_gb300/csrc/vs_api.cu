@@ -26,6 +26,7 @@ struct vs_ctx {
   int device;
   int num_sms;
   int persist_blocks[2][kNumTc][VS_MAX_SHELLS + 1];   // [backward][texel class][most shells] blocks per SM
+  int persist_blocks_clip[2][VS_MAX_SHELLS + 1];      // the near-plane clipping variant (generic class)
   std::mutex tune_mu;                          // guards tune / tune_set
   vs_tuning tune[2][VS_MAX_SHELLS + 1];        // [backward][most shells]
   bool tune_set[2][VS_MAX_SHELLS + 1];
@@ -34,6 +35,11 @@ struct vs_ctx {
 struct vs_object {
   int32_t k;
   vs_shell_desc shells[VS_MAX_SHELLS];
+  // bounding sphere per shell (world space), read from the positions on the
+  // first render; decides whether a camera needs the clipping kernels
+  std::mutex bounds_mu;
+  bool bounded;
+  double center[VS_MAX_SHELLS][3], radius[VS_MAX_SHELLS];
 };
 
 namespace {
@@ -156,6 +162,7 @@ struct UnitShape {
 };
 
 struct Plan {
+  bool clip = false;             // some shell may reach nearer than znear: clipping kernels
   size_t off_items, off_shells, off_done, off_stage, table_end, total;
   std::vector<DItem> items;
   std::vector<DShell> shells;
@@ -163,6 +170,55 @@ struct Plan {
   int total_units;
   int tc;                        // texel class of the kernels (vsd::TC_*)
 };
+
+// Bounding spheres of an object's shells, from one read of its positions
+// (the first render with the object; positions are not expected to change
+// afterwards -- reload the object if they do).
+vs_status ensure_bounds(const vs_object* cobj) {
+  vs_object* obj = const_cast<vs_object*>(cobj);
+  std::lock_guard<std::mutex> g(obj->bounds_mu);
+  if (obj->bounded) return VS_OK;
+  std::vector<float> p;
+  for (int i = 0; i < obj->k; ++i) {
+    const vs_shell_desc& d = obj->shells[i];
+    p.resize(3 * (size_t)d.num_verts);
+    cudaError_t e = cudaMemcpy(p.data(), d.pos, p.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading vertex positions for the shell bounds");
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (size_t v = 0; v < (size_t)d.num_verts; ++v)
+      for (int c = 0; c < 3; ++c) {
+        lo[c] = std::min(lo[c], (double)p[3 * v + c]);
+        hi[c] = std::max(hi[c], (double)p[3 * v + c]);
+      }
+    double r2 = 0.0;
+    for (int c = 0; c < 3; ++c) obj->center[i][c] = 0.5 * (lo[c] + hi[c]);
+    for (size_t v = 0; v < (size_t)d.num_verts; ++v) {
+      double q = 0.0;
+      for (int c = 0; c < 3; ++c) q += (p[3 * v + c] - obj->center[i][c]) * (p[3 * v + c] - obj->center[i][c]);
+      r2 = std::max(r2, q);
+    }
+    obj->radius[i] = std::sqrt(r2);
+  }
+  obj->bounded = true;
+  return VS_OK;
+}
+
+// Whether a shell of the object may come nearer than znear in this camera
+// (camera depth of its bounding sphere, with a margin far above the FP32
+// rounding of the vertex transform); true while the bounds are unknown.
+bool needs_clip(const vs_object& o, const vs_camera& c) {
+  if (!o.bounded) return true;
+  const float* m = c.world_to_cam;
+  const double n = std::sqrt((double)m[8] * m[8] + (double)m[9] * m[9] + (double)m[10] * m[10]);
+  for (int i = 0; i < o.k; ++i) {
+    const double* ce = o.center[i];
+    const double z = m[8] * ce[0] + m[9] * ce[1] + m[10] * ce[2] + m[11];
+    const double scale = n * (std::fabs(ce[0]) + std::fabs(ce[1]) + std::fabs(ce[2]) + o.radius[i]) +
+                         std::fabs((double)m[11]) + c.znear;
+    if (z - n * o.radius[i] < (double)c.znear + 1e-5 * scale) return true;
+  }
+  return false;
+}
 
 // Fills the plan; with ws == nullptr only sizes are computed.
 vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool clear_vis, uint32_t flags,
@@ -205,7 +261,6 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
     it.raster_rounds = shape.raster_rounds;
     it.shade_rounds = shape.shade_rounds;
     it.bg[0] = bg ? bg[0] : 0.f; it.bg[1] = bg ? bg[1] : 0.f; it.bg[2] = bg ? bg[2] : 0.f;
-    it.maxdeg = -1;
     const size_t HW = (size_t)c.width * c.height;
     it.setup_pre[0] = 0;
     it.raster_pre[0] = 0;
@@ -235,7 +290,6 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
       } else {
         s.gvec = 1;
       }
-      if (d.format == VS_TEX_SH_F16) it.maxdeg = std::max(it.maxdeg, (int)d.sh_degree);
       s.vsetup = reinterpret_cast<int4*>(ws ? ws + off : nullptr);
       off = align256(off + sizeof(int4) * (size_t)d.num_verts);
       it.setup_pre[i + 1] = it.setup_pre[i] + (d.num_verts + kSetupPerUnit - 1) / kSetupPerUnit;
@@ -262,6 +316,9 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
     tc = (tc < 0 || tc == c) ? c : TC_ANY;
   }
   P.tc = tc < 0 ? TC_ANY : tc;
+  P.clip = false;
+  for (int j = 0; j < n; ++j) P.clip = P.clip || needs_clip(*req[j].obj, *req[j].cam);
+  if (P.clip) P.tc = TC_ANY;   // the clipping kernels exist for the generic class
   // skewed stages: stage s = SETUP(s), RASTER(s-1), SHADE(s-2)
   long long g = 0;
   for (int st = 0; st < n + NPH - 1; ++st) {
@@ -402,8 +459,11 @@ vs_status plan_batch(const vs_ctx* ctx, const vs_batch_item* items, int n, const
     *kmax = std::max(*kmax, (int)b.obj->k);
   }
   char* ws = static_cast<char*>(workspace);
-  vs_status s = make_plan(req.data(), n, bg, do_backward ? 1 : 0, true, flags, ws, P, shape_of(t));
+  vs_status s = set_device(ctx);
   if (s != VS_OK) return s;
+  for (int j = 0; j < n; ++j)
+    if ((s = ensure_bounds(items[j].obj)) != VS_OK) return s;
+  if ((s = make_plan(req.data(), n, bg, do_backward ? 1 : 0, true, flags, ws, P, shape_of(t))) != VS_OK) return s;
   return check_ws(P, workspace, ws_bytes);
 }
 
@@ -413,10 +473,12 @@ vs_status launch_batch(vs_ctx* ctx, const Plan& P, void* workspace, int do_backw
   char* ws = static_cast<char*>(workspace);
   vs_status s = upload_table(P, ws, 1, st);
   if (s != VS_OK) return s;
-  const int most = ctx->persist_blocks[do_backward ? 1 : 0][P.tc][kmax];
+  const int most = P.clip ? ctx->persist_blocks_clip[do_backward ? 1 : 0][kmax]
+                         : ctx->persist_blocks[do_backward ? 1 : 0][P.tc][kmax];
   const int bps = t.blocks_per_sm == 0 ? most : std::min(t.blocks_per_sm, most);
   const long long spin_limit = 1ll << 24;   // ~ seconds with 200 ns sleeps
-  cudaError_t e = vsk::persistent(table_ref(P, ws), do_backward != 0, P.tc, ctx->num_sms * bps, spin_limit, st);
+  cudaError_t e = vsk::persistent(table_ref(P, ws), do_backward != 0, P.tc, P.clip, ctx->num_sms * bps, spin_limit,
+                                  st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_batch launch");
 }
 
@@ -512,12 +574,21 @@ vs_status vs_create(vs_ctx** ctx, int device) {
     for (int tc = 0; tc < kNumTc; ++tc)
       for (int K = 1; K <= VS_MAX_SHELLS; ++K) {
         int& nb = c->persist_blocks[b][tc][K];
-        if ((e = vsk::persistent_occupancy(b == 1, tc, K, &nb)) != cudaSuccess) {
+        if ((e = vsk::persistent_occupancy(b == 1, tc, false, K, &nb)) != cudaSuccess) {
           delete c;
           return cuda_fail(e, "occupancy query");
         }
         if (nb < 1) nb = 1;
       }
+  for (int b = 0; b < 2; ++b)
+    for (int K = 1; K <= VS_MAX_SHELLS; ++K) {
+      int& nb = c->persist_blocks_clip[b][K];
+      if ((e = vsk::persistent_occupancy(b == 1, TC_ANY, true, K, &nb)) != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "occupancy query");
+      }
+      if (nb < 1) nb = 1;
+    }
   *ctx = c;
   g_err.clear();
   return VS_OK;
@@ -578,12 +649,13 @@ vs_status vs_render(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, con
   ItemReq r{obj, cam, out_rgba, hits, nullptr, nullptr, nullptr};
   Plan P;
   char* ws = static_cast<char*>(workspace);
+  if ((s = set_device(ctx)) != VS_OK) return s;
+  if ((s = ensure_bounds(obj)) != VS_OK) return s;
   if ((s = make_plan(&r, 1, bg, 0, true, flags & ~VS_FLAG_TEST_STALL, ws, P)) != VS_OK) return s;
   if ((s = check_ws(P, workspace, ws_bytes)) != VS_OK) return s;
-  if ((s = set_device(ctx)) != VS_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if ((s = upload_table(P, ws, vsk::plain_forward_launches(P.items[0].units), st)) != VS_OK) return s;
-  cudaError_t e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, P.tc, st);
+  cudaError_t e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, P.tc, P.clip, st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render launch");
 }
 
@@ -601,12 +673,13 @@ vs_status vs_render_backward(vs_ctx* ctx, const vs_object* obj, const vs_camera*
   ItemReq r{obj, cam, nullptr, const_cast<int32_t*>(hits), grad_rgb, grad_texels, loss};
   Plan P;
   char* ws = static_cast<char*>(workspace);
+  if ((s = set_device(ctx)) != VS_OK) return s;
+  if ((s = ensure_bounds(obj)) != VS_OK) return s;
   if ((s = make_plan(&r, 1, bg, 1, false, flags & ~VS_FLAG_TEST_STALL, ws, P)) != VS_OK) return s;
   if ((s = check_ws(P, workspace, ws_bytes)) != VS_OK) return s;
-  if ((s = set_device(ctx)) != VS_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if ((s = upload_table(P, ws, vsk::plain_backward_launches(P.items[0].units), st)) != VS_OK) return s;
-  cudaError_t e = vsk::plain_backward(table_ref(P, ws), P.items[0].units, P.tc, st);
+  cudaError_t e = vsk::plain_backward(table_ref(P, ws), P.items[0].units, P.tc, P.clip, st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_backward launch");
 }
 
@@ -620,8 +693,7 @@ vs_status vs_render_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, co
   const vs_tuning t = lookup_tuning(ctx, do_backward ? 1 : 0, kmax);
   Plan P;
   vs_status s = plan_batch(ctx, items, n, bg, do_backward, workspace, ws_bytes, flags, t, P, &kmax);
-  if (s != VS_OK) return s;
-  if ((s = set_device(ctx)) != VS_OK) return s;
+  if (s != VS_OK) return s;   // plan_batch made the context's device current
   return launch_batch(ctx, P, workspace, do_backward, kmax, t, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -715,13 +787,13 @@ vs_status vs_autotune_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, 
     if (items[j].obj) kmax = std::max(kmax, std::min((int)items[j].obj->k, VS_MAX_SHELLS));
   const int b = do_backward ? 1 : 0;
   const vs_tuning start = lookup_tuning(ctx, b, kmax);
-  int tc = TC_ANY;
+  int most = 1;
   {  // validate the whole batch once before timing anything
     Plan P;
     int km = 1;
     vs_status s = plan_batch(ctx, items, n, bg, do_backward, workspace, ws_bytes, flags, start, P, &km);
     if (s != VS_OK) return s;
-    tc = P.tc;
+    most = P.clip ? ctx->persist_blocks_clip[b][kmax] : ctx->persist_blocks[b][P.tc][kmax];
   }
   vs_status s = set_device(ctx);
   if (s != VS_OK) return s;
@@ -734,7 +806,7 @@ vs_status vs_autotune_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, 
     return cuda_fail(e, "cudaEventCreate");
   }
   vs_tuning won{};
-  s = vs_tune_search(&start, ctx->persist_blocks[b][tc][kmax], autotune_cost, &J, &won, nullptr);
+  s = vs_tune_search(&start, most, autotune_cost, &J, &won, nullptr);
   cudaEventDestroy(J.ev[0]);
   cudaEventDestroy(J.ev[1]);
   if (J.status != VS_OK) return fail(J.status, "%s", J.error.c_str());
@@ -763,6 +835,7 @@ vs_status vs_read_stats(void* workspace, vs_stream_t stream, int32_t reset, vs_s
   out->tris_culled_guard = h.guard;
   out->tris_large = h.large;
   out->launches = h.launches;
+  out->tris_clipped = h.clipped;
   if (reset) {
     if ((e = cudaMemset(workspace, 0, sizeof h)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
   }
@@ -825,13 +898,14 @@ extern "C" vs_status vs_render_noalloc(vs_ctx* ctx, const vs_object* obj, const 
   ItemReq r{obj, cam, out_rgba, hits, nullptr, nullptr, nullptr};
   const uint32_t fl = flags & ~VS_FLAG_TEST_STALL;
   Plan P;
+  if ((s = set_device(ctx)) != VS_OK) return s;
+  if ((s = ensure_bounds(obj)) != VS_OK) return s;
   if ((s = make_plan(&r, 1, bg, 0, true, fl, nullptr, P)) != VS_OK) return s;
   if (P.total > kNoAllocScratchBytes)
     return fail(VS_ERR_OVERFLOW,
                 "vs_render_noalloc needs %zu bytes of scratch for this object and camera; its fixed array holds "
                 "%zu (use vs_render with a workspace)",
                 P.total, kNoAllocScratchBytes);
-  if ((s = set_device(ctx)) != VS_OK) return s;
   char* ws = nullptr;
   if ((s = noalloc_scratch(ctx->device, &ws)) != VS_OK) return s;
   if ((s = make_plan(&r, 1, bg, 0, true, fl, ws, P)) != VS_OK) return s;
@@ -842,6 +916,6 @@ extern "C" vs_status vs_render_noalloc(vs_ctx* ctx, const vs_object* obj, const 
   cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-alloc header)");
   if ((s = upload_table(P, ws, vsk::plain_forward_launches(P.items[0].units), st)) != VS_OK) return s;
-  e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, P.tc, st);
+  e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, P.tc, P.clip, st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_noalloc launch");
 }

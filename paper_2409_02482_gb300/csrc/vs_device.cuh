@@ -107,7 +107,7 @@ struct alignas(16) DItem {
   const float* grad_rgb;       // [H*W, 3] gradient or target, or null
   float* loss;                 // scalar or null
   unsigned long long* vis;     // [k, H*W] -- workspace
-  int32_t k, shell0, maxdeg, clear_units;
+  int32_t k, shell0, pad0, clear_units;
   int32_t flags, do_bwd, stall;
   int32_t raster_rounds;       // raster unit = 32 * raster_rounds triangles
   int32_t shade_rounds;        // shading unit = 32 * shade_rounds pixels
@@ -127,7 +127,8 @@ struct alignas(16) WsHeader {
   int32_t pad;
   unsigned long long frags, front, back, nearc, guard, large;
   unsigned long long launches;  // kernels enqueued by the calls (host-declared)
-  unsigned long long reserved[23];
+  unsigned long long clipped;   // triangles clipped at the near plane
+  unsigned long long reserved[22];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
@@ -215,23 +216,34 @@ __device__ __forceinline__ void warp_count(unsigned long long* ctr, unsigned v) 
 // ----------------------------------------------------------------------------
 // Each product and sum is rounded to FP32 in this order; the CPU oracle runs
 // the same sequence, so the snapped integers agree bit for bit.
-__device__ __forceinline__ int4 setup_vertex(const float* p, const DCam& c) {
+// World -> camera space (pinned FP32 sequence).
+__device__ __forceinline__ float3 cam_xyz(const float* p, const DCam& c) {
   const float x = p[0], y = p[1], z = p[2];
-  float xc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.m[0], x), __fmul_rn(c.m[1], y)),
-                                 __fmul_rn(c.m[2], z)), c.m[3]);
-  float yc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.m[4], x), __fmul_rn(c.m[5], y)),
-                                 __fmul_rn(c.m[6], z)), c.m[7]);
-  float zc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.m[8], x), __fmul_rn(c.m[9], y)),
-                                 __fmul_rn(c.m[10], z)), c.m[11]);
-  if (!(zc >= c.znear)) return make_int4(kInvalidX, 0, 0, VTX_NEAR);
+  const float xc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.m[0], x), __fmul_rn(c.m[1], y)),
+                                       __fmul_rn(c.m[2], z)), c.m[3]);
+  const float yc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.m[4], x), __fmul_rn(c.m[5], y)),
+                                       __fmul_rn(c.m[6], z)), c.m[7]);
+  const float zc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.m[8], x), __fmul_rn(c.m[9], y)),
+                                       __fmul_rn(c.m[10], z)), c.m[11]);
+  return make_float3(xc, yc, zc);
+}
+
+// Camera space (zc >= znear) -> (X, Y, bits(1/w), depth key), or the guard
+// marker off the +-32768 px band.
+__device__ __forceinline__ int4 project_cam(float xc, float yc, float zc, const DCam& c) {
   const float iw = __frcp_rn(zc);
   const float sx = __fadd_rn(__fmul_rn(__fmul_rn(c.fx, xc), iw), c.cx);
   const float sy = __fadd_rn(__fmul_rn(__fmul_rn(c.fy, yc), iw), c.cy);
   const float X = __fmul_rn(sx, 256.0f), Y = __fmul_rn(sy, 256.0f);
   if (!(fabsf(X) < 8388608.0f && fabsf(Y) < 8388608.0f)) return make_int4(kInvalidX, 0, 0, VTX_GUARD);
   const float qf = __fmul_rn(iw, __fmul_rn(c.znear, 1073741824.0f));
-  return make_int4(__float2int_rn(X), __float2int_rn(Y), __float_as_int(iw),
-                   (int)__float2uint_rn(qf));
+  return make_int4(__float2int_rn(X), __float2int_rn(Y), __float_as_int(iw), (int)__float2uint_rn(qf));
+}
+
+__device__ __forceinline__ int4 setup_vertex(const float* p, const DCam& c) {
+  const float3 pc = cam_xyz(p, c);
+  if (!(pc.z >= c.znear)) return make_int4(kInvalidX, 0, 0, VTX_NEAR);
+  return project_cam(pc.x, pc.y, pc.z, c);
 }
 
 // ----------------------------------------------------------------------------
@@ -245,13 +257,15 @@ struct Tri {
   int xlo, xhi, ylo, yhi;
 };
 
-// 0 = front-facing and valid; 1 = back-facing or zero area; 2 = near; 3 = guard.
+// 0 = front-facing and valid; 1 = back-facing or zero area; 2 = every
+// vertex nearer than znear; 3 = off the guard band; 5 = one or two vertices
+// nearer than znear (to be clipped, clip_tri).
 __device__ __forceinline__ int make_tri(const int4 v0, const int4 v1, const int4 v2, int W, int H,
                                         Tri& t) {
   if (v0.x == kInvalidX || v1.x == kInvalidX || v2.x == kInvalidX) {
-    const int f = (v0.x == kInvalidX ? v0.w : 0) | (v1.x == kInvalidX ? v1.w : 0) |
-                  (v2.x == kInvalidX ? v2.w : 0);
-    return (f & VTX_NEAR) ? 2 : 3;
+    const int nn = (v0.x == kInvalidX && (v0.w & VTX_NEAR)) + (v1.x == kInvalidX && (v1.w & VTX_NEAR)) +
+                   (v2.x == kInvalidX && (v2.w & VTX_NEAR));
+    return nn == 3 ? 2 : (nn > 0 ? 5 : 3);
   }
   t.X[0] = v0.x; t.X[1] = v1.x; t.X[2] = v2.x;
   t.Y[0] = v0.y; t.Y[1] = v1.y; t.Y[2] = v2.y;
@@ -275,6 +289,62 @@ __device__ __forceinline__ int make_tri(const int4 v0, const int4 v1, const int4
   t.ylo = max(0, -((128 - mny) >> 8));
   t.yhi = min(H - 1, (mxy - 128) >> 8);
   return 0;
+}
+
+// Near-plane clipping of a mesh triangle with one or two vertices nearer
+// than znear (the oracle's definition, same FP32 operations): in camera
+// space, Sutherland-Hodgman against z = znear with the vertices in order;
+// the point on a crossing edge comes from its (inside, outside) ends, t =
+// (znear - z_out) / (z_in - z_out), x = x_out + t (x_in - x_out) (y and the
+// UVs alike), z = znear, so triangles sharing the edge get the same point;
+// the points are projected and snapped like vertices; the 3- or 4-gon is
+// split into (P0, P1, P2) and (P0, P2, P3).  Returns the number of
+// rasterizable parts (0..2) with their per-vertex UVs.  Rare: kept out of
+// line so that the common path keeps its registers.
+static __device__ __forceinline__ int clip_tri(const float* pos, const float2* uvs, const DCam& c, const int idx[3], Tri part[2],
+                                     float2 puv[2][3]) {
+  float3 pc[3];
+  float2 uv[3];
+  bool in[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    pc[j] = cam_xyz(pos + 3 * (size_t)idx[j], c);
+    uv[j] = uvs ? __ldg(uvs + idx[j]) : make_float2(0.f, 0.f);
+    in[j] = pc[j].z >= c.znear;
+  }
+  int4 pv[4];
+  float2 pu[4];
+  int n = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a + 1) % 3;
+    if (in[a]) {
+      pv[n] = project_cam(pc[a].x, pc[a].y, pc[a].z, c);
+      pu[n] = uv[a];
+      ++n;
+    }
+    if (in[a] != in[b]) {
+      const int i = in[a] ? a : b, o = in[a] ? b : a;
+      const float t = __fdiv_rn(__fsub_rn(c.znear, pc[o].z), __fsub_rn(pc[i].z, pc[o].z));
+      const float x = __fadd_rn(pc[o].x, __fmul_rn(t, __fsub_rn(pc[i].x, pc[o].x)));
+      const float y = __fadd_rn(pc[o].y, __fmul_rn(t, __fsub_rn(pc[i].y, pc[o].y)));
+      const float u = __fadd_rn(uv[o].x, __fmul_rn(t, __fsub_rn(uv[i].x, uv[o].x)));
+      const float w = __fadd_rn(uv[o].y, __fmul_rn(t, __fsub_rn(uv[i].y, uv[o].y)));
+      pv[n] = project_cam(x, y, c.znear, c);
+      pu[n] = make_float2(u, w);
+      ++n;
+    }
+  }
+  int m = 0;
+  if (n >= 3 && make_tri(pv[0], pv[1], pv[2], c.W, c.H, part[m]) == 0) {
+    puv[m][0] = pu[0]; puv[m][1] = pu[1]; puv[m][2] = pu[2];
+    ++m;
+  }
+  if (n == 4 && make_tri(pv[0], pv[2], pv[3], c.W, c.H, part[m]) == 0) {
+    puv[m][0] = pu[0]; puv[m][1] = pu[2]; puv[m][2] = pu[3];
+    ++m;
+  }
+  return m;
 }
 
 __device__ __forceinline__ void edge_values(const Tri& t, int px, int py, long long e[3]) {

@@ -66,7 +66,8 @@ static __device__ void unit_setup(const DItem& it, const DShell* sh, int u) {
 // RASTER
 // ----------------------------------------------------------------------------
 // Loads triangle t of shell s; 0 = front-facing and rasterizable, 1..3 =
-// culled (back/zero-area, near, guard band), 4 = index out of range.
+// culled (back/zero-area, behind the near plane, guard band), 4 = index out
+// of range, 5 = to be clipped at the near plane.
 __device__ __forceinline__ int load_tri(const DShell& s, const DCam& c, int t, Tri& T, int idx[3]) {
   const int* ip = s.tris + 3 * (size_t)t;
   idx[0] = __ldg(ip);
@@ -82,6 +83,26 @@ __device__ __forceinline__ void raster_pixel(const Tri& T, int t, int x, int y, 
   long long e[3];
   edge_values(T, 256 * x + 128, 256 * y + 128, e);
   if (covered(T, e)) red_max_vis<HINT>(vis + (size_t)y * W + x, vis_key(depth_key(T, e), t));
+}
+
+// The parts of triangle t clipped at the near plane, rasterized by the whole
+// warp (each lane strides over the parts' screen boxes).  Rare: out of line.
+template <bool HINT>
+static __device__ __forceinline__ void raster_clipped(const DShell& s, const DCam& c, int t, unsigned long long* vis) {
+  const int* ip = s.tris + 3 * (size_t)t;
+  const int idx[3] = {__ldg(ip), __ldg(ip + 1), __ldg(ip + 2)};   // checked in range by load_tri
+  Tri part[2];
+  float2 puv[2][3];
+  const int np = clip_tri(s.pos, nullptr, c, idx, part, puv);
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < np; ++k) {
+    const int bw = part[k].xhi - part[k].xlo + 1, bh = part[k].yhi - part[k].ylo + 1;
+    const int npq = bw > 0 && bh > 0 ? bw * bh : 0;
+    for (int p = lane; p < npq; p += 32) {
+      const int yy = p / bw;
+      raster_pixel<HINT>(part[k], t, part[k].xlo + (p - yy * bw), part[k].ylo + yy, c.W, vis);
+    }
+  }
 }
 
 // Triangle record shared by the lanes of a warp during the raster walk.
@@ -127,10 +148,10 @@ __device__ __forceinline__ unsigned depth_key32(const unsigned q[3], const int e
 // so lanes do not idle on small or culled boxes.  Larger boxes are
 // rasterized by the whole warp, one triangle at a time.
 struct RasterCounts {
-  unsigned front, back, nearc, guard, large, bad;
+  unsigned front, back, nearc, guard, large, bad, clipped;
 };
 
-template <bool HINT>
+template <bool HINT, bool CLIP>
 __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, int t0, unsigned long long* vis,
                                              char* smem, RasterCounts& rc) {
   TriS* s_tri = reinterpret_cast<TriS*>(smem);
@@ -140,7 +161,7 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
   const int lane = threadIdx.x & 31, wbase = 0;
   const int t = t0 + lane;
   const int W = it.cam.W;
-  unsigned front = 0, back = 0, nearc = 0, guard = 0, large = 0, bad = 0;
+  unsigned front = 0, back = 0, nearc = 0, guard = 0, large = 0, bad = 0, clip = 0;
   int npx = 0;
   TriS r;
   TriPos pos;
@@ -181,6 +202,7 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
     } else if (why == 1) back = 1;
     else if (why == 2) nearc = 1;
     else if (why == 3) guard = 1;
+    else if (why == 5) clip = 1;
     else bad = 1;
   }
   // compact the non-empty boxes and take the exclusive prefix of their sizes
@@ -230,6 +252,7 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
   rc.guard += guard;
   rc.large += large;
   rc.bad |= bad;
+  rc.clipped += clip;
   // large boxes: the warp strides over each one's screen box
   unsigned lm = __ballot_sync(FULL, large);
   while (lm) {
@@ -246,27 +269,39 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
       raster_pixel<HINT>(T, tq, T.xlo + (p - yy * bw), T.ylo + yy, W, vis);
     }
   }
+  // triangles clipped at the near plane (items with a vertex nearer than
+  // znear only)
+  if constexpr (CLIP) {
+    unsigned cm = __ballot_sync(FULL, clip);
+    while (cm) {
+      const int l = __ffs(cm) - 1;
+      cm &= cm - 1;
+      raster_clipped<HINT>(s, it.cam, __shfl_sync(FULL, t, l), vis);
+    }
+  }
   __syncwarp();   // the records are reused by the next round
 }
 
 // Raster unit: 32 * it.raster_rounds triangles of one shell in rounds of 32;
 // this warp runs rounds [r0, r1).
-template <bool HINT>
-static __device__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* smem, int r0, int r1) {
+template <bool HINT, bool CLIP>
+static __device__ __forceinline__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* smem,
+                                                   int r0, int r1) {
   int i = 0;
   while (i + 1 < it.k && u >= it.raster_pre[i + 1]) ++i;
   const DShell& s = sh[i];
   const int per_unit = 32 * it.raster_rounds;
   const int base = (u - it.raster_pre[i]) * per_unit;
   unsigned long long* vis = it.vis + (size_t)i * it.cam.W * it.cam.H;
-  RasterCounts rc = {0, 0, 0, 0, 0, 0};
+  RasterCounts rc = {0, 0, 0, 0, 0, 0, 0};
   const int rounds = min(r1, min(per_unit, s.nt - base + 31) / 32);
-  for (int r = r0; r < rounds; ++r) raster_round<HINT>(it, s, base + 32 * r, vis, smem, rc);
+  for (int r = r0; r < rounds; ++r) raster_round<HINT, CLIP>(it, s, base + 32 * r, vis, smem, rc);
   warp_count(&hdr->front, rc.front);
   warp_count(&hdr->back, rc.back);
   warp_count(&hdr->nearc, rc.nearc);
   warp_count(&hdr->guard, rc.guard);
   warp_count(&hdr->large, rc.large);
+  warp_count(&hdr->clipped, rc.clipped);
   if (__any_sync(0xffffffffu, rc.bad) && (threadIdx.x & 31) == 0) record_error(hdr, VS_ERR_INVALID_ARG);
 }
 
@@ -293,6 +328,29 @@ __device__ __forceinline__ int load_tri_shade(const DShell& s, int t, Tri& T, in
   const long long a2 = (long long)(T.X[1] - T.X[0]) * (T.Y[2] - T.Y[0]) -
                        (long long)(T.X[2] - T.X[0]) * (T.Y[1] - T.Y[0]);
   return a2 < 0 ? 0 : 1;
+}
+
+// Shading a fragment of a triangle clipped at the near plane: the part used
+// for the pixel (the only part, or of two the second if it covers the pixel
+// under the fill rule, else the first) and its per-vertex UVs.  Rare: kept
+// out of line.
+static __device__ __forceinline__ bool clipped_part(const DShell& s, const DCam& c, const int idx[3], int px, int py,
+                                                 Tri& T, float2 uv[3]) {
+  Tri part[2];
+  float2 puv[2][3];
+  const int n = clip_tri(s.pos, s.uv, c, idx, part, puv);
+  if (n == 0) return false;
+  int k = 0;
+  if (n == 2) {
+    long long e[3];
+    edge_values(part[1], px, py, e);
+    if (covered(part[1], e)) k = 1;
+  }
+  T = part[k];
+  uv[0] = puv[k][0];
+  uv[1] = puv[k][1];
+  uv[2] = puv[k][2];
+  return true;
 }
 
 template <int DEG, int VEC>
@@ -459,6 +517,51 @@ static __device__ __noinline__ void atten_pass(const DCam& cam, const DShell* sh
   }
 }
 
+// Markers in the lane word of a fragment-list entry.
+constexpr unsigned kBadFrag = 0x8000u;    // unusable triangle: invisible, no adjoint
+constexpr unsigned kClipFrag = 0x4000u;   // triangle to clip at the near plane (pending)
+
+// One fragment of a triangle clipped at the near plane (list entry j): the
+// part used at its pixel, footprint, texel fetch; like the fetch loop of
+// shade_round, out of line because it is rare.
+template <bool BWD, int TC>
+static __device__ __forceinline__ void shade_clipped(const DItem& it, const DShell* sh, int pbase, int j, const int* sent,
+                                                  unsigned short* spl, float4* sfrag, unsigned* sxy, float2* sfxy,
+                                                  unsigned* nfrag, unsigned* bad) {
+  const int e = sent[j];
+  const DShell& s = sh[e >> kTriBits];
+  const int* ip = s.tris + 3 * (size_t)(e & (kMaxTris - 1));
+  const int idx[3] = {__ldg(ip), __ldg(ip + 1), __ldg(ip + 2)};   // checked in range by load_tri_shade
+  const int pp = pbase + (spl[j] & 31);
+  const int W = it.cam.W;
+  const int y = pp / W, x = pp - y * W;
+  Tri T;
+  float2 uv[3];
+  Frag fr = {0.f, 0.f, 0.f, 0.f};
+  spl[j] &= (unsigned short)~kClipFrag;
+  if (!clipped_part(s, it.cam, idx, 256 * x + 128, 256 * y + 128, T, uv)) {
+    *bad = 1;
+    spl[j] |= (unsigned short)kBadFrag;
+  } else {
+    int ix, iy;
+    float fx, fy;
+    texel_coords(T, uv, s.tw, s.th, 256 * x + 128, 256 * y + 128, ix, fx, iy, fy);
+    const Footprint f = clamp_footprint(ix, fx, iy, fy, s.tw, s.th);
+    if constexpr (BWD) {
+      unsigned xy;
+      float2 fxy;
+      pack_footprint(f, xy, fxy);
+      sxy[j] = xy;
+      sfxy[j] = fxy;
+    }
+    float3 v = make_float3(0.f, 0.f, 1.f);
+    if (is_sh<TC>(s)) v = ray_dir(it.cam, x, y);
+    fr = fetch_frag<TC>(s, f, ix, fx, iy, fy, v);
+    ++*nfrag;
+  }
+  sfrag[j] = make_float4(fr.r, fr.g, fr.b, fr.a);
+}
+
 // Shading round: 32 consecutive pixels, one per lane.
 //  1. each lane reads its pixel's k visibility words (independent loads)
 //     into a per-shell hit table.  The round then runs in passes over
@@ -489,15 +592,14 @@ static __device__ __noinline__ void atten_pass(const DCam& cam, const DShell* sh
 //   frag float4 [C]  rgb + raw alpha (2 -> 3), then the adjoint d (3 -> 4)
 //   ent  u32    [C]  shell << 27 | triangle (1 -> 2), then x0 | y0 << 16
 //   aw   float  [C]  alpha_w (2 -> 3)
-//   pl   u16    [C]  lane | shell << 5 | kBadFrag for an invalid triangle
+//   pl   u16    [C]  lane | shell << 5 | kBadFrag / kClipFrag
 // adjoint only:
 //   fxy  float2 [C]  footprint fractions (2 -> 4)
 //   T    float  [C]  transmittance in front of the fragment (3)
-constexpr unsigned kBadFrag = 0x8000u;
 static_assert(kMaxShells <= 16, "shell index takes 4 bits of the lane word");
 static_assert(kFragCap >= kMaxShells, "a pixel's fragments must fit one pass");
 
-template <bool BWD, bool FROM_HITS, int TC>
+template <bool BWD, bool FROM_HITS, int TC, bool CLIP>
 __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, int pbase, char* wb, int K,
                                             unsigned& nfrag, unsigned& bad, float& loss_acc) {
   const unsigned FULL = 0xffffffffu;
@@ -552,6 +654,7 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
   }
   const int start = pre - cnt;
   const bool atten = (it.flags & VS_FLAG_ALPHA_ATTEN) != 0;
+  int clip_pending = 0;
   __syncwarp();
 
   for (int l0 = 0; l0 < 32;) {
@@ -592,11 +695,17 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
         Frag fr = {0.f, 0.f, 0.f, 0.f};
         Tri Tr;
         int idx[3];
-        if (t >= s.nt || load_tri_shade(s, t, Tr, idx) != 0) {
+        const int y = pp / W, x = pp - y * W;
+        const int r = t < s.nt ? load_tri_shade(s, t, Tr, idx) : 4;
+        if (CLIP && r == 2) {
+          // a vertex nearer than znear (or off the guard band): the triangle
+          // is clipped; shaded by the pass below
+          clip_pending = 1;
+          spl[j] |= (unsigned short)kClipFrag;
+        } else if (r != 0) {
           bad = 1;
           spl[j] |= (unsigned short)kBadFrag;   // invisible, and no adjoint
         } else {
-          const int y = pp / W, x = pp - y * W;
           const float2 uv[3] = {__ldg(s.uv + idx[0]), __ldg(s.uv + idx[1]), __ldg(s.uv + idx[2])};
           int ix, iy;
           float fx, fy;
@@ -620,6 +729,12 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
       }
     }
     __syncwarp();
+    // 2c. fragments of triangles clipped at the near plane (rare; out of line)
+    if (CLIP && __any_sync(FULL, clip_pending)) {
+      for (int j = lane; j < nf; j += 32)
+        if (spl[j] & kClipFrag) shade_clipped<BWD, TC>(it, sh, pbase, j, sent, spl, sfrag, sxy, sfxy, &nfrag, &bad);
+      __syncwarp();
+    }
 
     // 3. composite the pass's pixels
     if (mine) {
@@ -704,9 +819,9 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
 
 // Shading unit: 32 * it.shade_rounds consecutive pixels in rounds of 32;
 // this warp runs rounds [r0, r1).  `wb` is the warp's shared-memory slice.
-template <bool BWD, bool FROM_HITS, int TC>
-__device__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* wb, int K, int r0,
-                           int r1) {
+template <bool BWD, bool FROM_HITS, int TC, bool CLIP>
+__device__ __forceinline__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* wb, int K,
+                                           int r0, int r1) {
   const unsigned FULL = 0xffffffffu;
   const int HW = it.cam.W * it.cam.H;
   unsigned nfrag = 0, bad = 0;
@@ -714,7 +829,7 @@ __device__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* h
   for (int r = r0; r < r1; ++r) {
     const int pbase = (u * it.shade_rounds + r) * 32;
     if (pbase >= HW) break;
-    shade_round<BWD, FROM_HITS, TC>(it, sh, pbase, wb, K, nfrag, bad, loss);
+    shade_round<BWD, FROM_HITS, TC, CLIP>(it, sh, pbase, wb, K, nfrag, bad, loss);
   }
   const int lane = threadIdx.x & 31;
   if (!FROM_HITS) warp_count(&hdr->frags, nfrag);
@@ -735,11 +850,11 @@ __device__ __forceinline__ char* warp_smem(int K, bool bwd) {
   return vs_smem + (threadIdx.x >> 5) * warp_slice_bytes(K, bwd);
 }
 
-template <bool BWD, bool FROM_HITS, int TC>
+template <bool BWD, bool FROM_HITS, int TC, bool CLIP>
 __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS) k_shade(TableRef tb, int item) {
   const DItem& it = tb.items[item];
   const int w = threadIdx.x >> 5;
-  unit_shade<BWD, FROM_HITS, TC>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, warp_smem(tb.kmax, BWD), tb.kmax, w,
+  unit_shade<BWD, FROM_HITS, TC, CLIP>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, warp_smem(tb.kmax, BWD), tb.kmax, w,
                              w + 1);
 }
 
@@ -767,7 +882,7 @@ static __device__ bool wait_done(const int* ctr, int target, long long limit, Ws
 // stages (while still in L2).  A unit waits only for the previous phase of
 // its own item, whose units were all dispensed in an earlier stage to warps
 // that are already running, so the wait always ends (and is bounded anyway).
-template <bool BWD, int TC>
+template <bool BWD, int TC, bool CLIP>
 __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS) k_persistent(TableRef tb, long long spin_limit) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -807,9 +922,9 @@ __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS)
     const DShell* sh = tb.shells + it.shell0;
     switch (ph) {
       case PH_SETUP: unit_setup<BWD>(it, sh, u); break;
-      case PH_RASTER: unit_raster<BWD>(it, sh, u, hdr, smem, 0, it.raster_rounds); break;
+      case PH_RASTER: unit_raster<BWD, CLIP>(it, sh, u, hdr, smem, 0, it.raster_rounds); break;
       default:
-        unit_shade<BWD, false, TC>(it, sh, u, hdr, smem, tb.kmax, 0, it.shade_rounds);
+        unit_shade<BWD, false, TC, CLIP>(it, sh, u, hdr, smem, tb.kmax, 0, it.shade_rounds);
     }
     __syncwarp();
     if (lane == 0) {
