@@ -205,8 +205,30 @@ def shade(scene, cam, hits: np.ndarray, bg=(0.0, 0.0, 0.0), threads: Optional[in
     c = ocam(cam)
     lib().oracle_shade(refs.arr, ctypes.c_int32(scene.k), ctypes.byref(c), _ptr(bgv), _ptr(hits),
                        _ptr(out), ctypes.c_int32(threads or default_threads()), _ptr(frags),
-                       ctypes.c_int32(flags))
+                       ctypes.c_int32(flags), None)
     return out, frags
+
+
+LAYER_FIELDS = ("nx", "ny", "nz", "u", "v", "alpha", "weight", "r", "g", "b", "pad0", "pad1")
+
+
+def layers(scene, cam, hits: np.ndarray, bg=(0.0, 0.0, 0.0), threads: Optional[int] = None, flags: int = 0):
+    """Per-shell render buffers of Figs. S1/S3 before blending: float64
+    [k, H, W, 12] = unit face normal, uv, opacity, blending weight T_i alpha_i
+    (the layer's contribution), rgb, 0, 0 -- zero where a shell has no
+    fragment.  Also returns the composite (rgba) like shade()."""
+    refs = _ShellRefs(scene.shells)
+    H, W = cam.height, cam.width
+    hits = np.ascontiguousarray(hits, np.int32)
+    out = np.zeros((H, W, 4), np.float64)
+    lay = np.zeros((scene.k, H, W, 12), np.float64)
+    bgv = np.ascontiguousarray(bg, np.float64)
+    frags = np.zeros(scene.k, np.int64)
+    c = ocam(cam)
+    lib().oracle_shade(refs.arr, ctypes.c_int32(scene.k), ctypes.byref(c), _ptr(bgv), _ptr(hits),
+                       _ptr(out), ctypes.c_int32(threads or default_threads()), _ptr(frags),
+                       ctypes.c_int32(flags), _ptr(lay))
+    return lay, out
 
 
 def render(scene, cam, bg=(0.0, 0.0, 0.0), threads: Optional[int] = None, flags: int = 0):

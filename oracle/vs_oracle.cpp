@@ -513,6 +513,8 @@ struct Frag {
   double atten;            // transparency attenuation (1 unless enabled)
   Footprint fp;
   double val[64];          // interpolated texel values
+  double uv[2];            // perspective-correct texture coordinates at the pixel
+  double normal[3];        // unit geometric normal of the face, (p1 - p0) x (p2 - p0)
 };
 
 // Sec. 3 "Transparency Attenuation": alpha_w = 2 sigmoid(10 |v . n|) - 1,
@@ -539,6 +541,18 @@ bool shade_fragment(const OShell& s, const OCam& c, const std::vector<SVert>& sv
   if (!tri_at(s, sv, tri, c, 256 * x + 128, 256 * y + 128, &t)) return false;
   double uv[2];
   interp_uv(t, 256 * x + 128, 256 * y + 128, uv);
+  f->uv[0] = uv[0];
+  f->uv[1] = uv[1];
+  {
+    double p[3][3];
+    for (int j = 0; j < 3; ++j)
+      for (int d = 0; d < 3; ++d) p[j][d] = s.pos[3 * idx[j] + d];
+    const double a[3] = {p[1][0] - p[0][0], p[1][1] - p[0][1], p[1][2] - p[0][2]};
+    const double b[3] = {p[2][0] - p[0][0], p[2][1] - p[0][1], p[2][2] - p[0][2]};
+    const double n[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+    const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    for (int d = 0; d < 3; ++d) f->normal[d] = n[d] / len;
+  }
   if (s.fmt == FMT_SH_U8) {
     // RGBA all view-dependent: channel c = sigmoid(sum_m sh_{m,c} Y_m(v))
     const int nb = (s.degree + 1) * (s.degree + 1);
@@ -616,8 +630,12 @@ int oracle_raster(const float* pos, int32_t nv, const int32_t* tris, int32_t nt,
 
 // Shade + composite every pixel from per-shell hits [k, H, W] (-1 = miss).
 // out: [H, W, 4] = (C + T bg, 1 - T).  stats (optional): [k] fragments per shell.
+// layers (optional): [k, H, W, 12] per-shell buffers (Figs. S1/S3): unit
+// face normal (3), uv (2), opacity, blending weight T_i alpha_i, rgb (3), 0,
+// 0; all zero where the shell has no fragment.
 int oracle_shade(const OShell* shells, int32_t k, const OCam* cam, const double* bg,
-                 const int32_t* hits, double* out, int32_t nthreads, int64_t* frags, int32_t flags) {
+                 const int32_t* hits, double* out, int32_t nthreads, int64_t* frags, int32_t flags,
+                 double* layers) {
   const int64_t W = cam->width, H = cam->height;
   std::vector<std::vector<SVert>> sv(k);
   int maxdeg = 0;
@@ -640,6 +658,15 @@ int oracle_shade(const OShell* shells, int32_t k, const OCam* cam, const double*
           Frag f;
           if (!shade_fragment(shells[i], *cam, sv[i], h, x, y, Y, v, flags, &f)) continue;
           cnt[(size_t)ti * k + i] += 1;
+          if (layers) {
+            double* L = layers + 12 * ((size_t)i * H * W + y * W + x);
+            for (int d = 0; d < 3; ++d) L[d] = f.normal[d];
+            L[3] = f.uv[0];
+            L[4] = f.uv[1];
+            L[5] = f.alpha;
+            L[6] = T * f.alpha;
+            for (int ch = 0; ch < 3; ++ch) L[7 + ch] = f.rgb[ch];
+          }
           for (int ch = 0; ch < 3; ++ch) C[ch] += T * f.alpha * f.rgb[ch];
           T *= (1.0 - f.alpha);
         }

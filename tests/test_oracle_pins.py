@@ -734,6 +734,78 @@ def test_close_up_nested_shells_match_a_ray_cast_that_skips_the_near_zone():
 
 
 # ----------------------------------------------------------------------------
+# per-layer buffers (Figs. S1/S3): each shell before blending
+# ----------------------------------------------------------------------------
+
+def test_layer_buffers_recompose_the_image():
+    """The per-shell weights T_i alpha_i sum to the composite's alpha and
+    sum_i weight_i rgb_i + (1 - alpha) bg is its colour; opacity is within
+    [0, 1], normals are unit vectors facing the camera and missed shells are
+    all zero; flag on or off."""
+    (sc, cams), = synth.config_scene("c2", scale=0.003, views=2)
+    for flags in (0, oracle.ALPHA_ATTEN):
+        cam = cams[1]
+        hits, _, _ = oracle.raster_scene(sc, cam)
+        bg = np.array([0.3, 0.1, 0.6])
+        lay, rgba = oracle.layers(sc, cam, hits, bg=tuple(bg), flags=flags)
+        w = lay[..., 6]
+        assert np.abs(w.sum(0) - rgba[..., 3]).max() < 1e-12
+        col = (w[..., None] * lay[..., 7:10]).sum(0) + (1 - rgba[..., 3:4]) * bg
+        assert np.abs(col - rgba[..., :3]).max() < 1e-12
+        hit = hits >= 0
+        assert np.all(lay[~hit] == 0)
+        n = lay[..., 0:3][hit]
+        assert np.abs(np.linalg.norm(n, axis=-1) - 1).max() < 1e-12
+        eye, dirs = pixel_rays(cam)
+        facing = np.einsum("khwc,hwc->khw", lay[..., 0:3], dirs)[hit]
+        assert np.all(facing < 0)                  # front faces turn towards the viewer
+        assert lay[..., 5][hit].min() >= 0 and lay[..., 5][hit].max() <= 1
+        # T_i alpha_i from the per-layer opacities, front to back
+        T = np.ones(hits.shape[1:])
+        for i in range(sc.k):
+            a = lay[i, ..., 5]
+            assert np.abs(lay[i, ..., 6] - T * a).max() < 1e-12
+            T = T * (1 - a)
+
+
+def test_layer_uv_and_normal_of_a_planar_quad():
+    """A slanted textured quad: every covered pixel's layer UV is the FP64
+    ray-plane intersection's UV and its normal the plane's."""
+    th = math.radians(55.0)
+    ax, az = np.array([1.0, 0.0, 0.0]), np.array([0.0, math.sin(th), math.cos(th)])
+    corners = np.array([-ax - az, ax - az, ax + az, -ax + az])
+    pos = corners.astype(np.float32)
+    uv = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], np.float32)
+    tris = np.array([[0, 1, 2], [0, 2, 3]], np.int32)
+    n = np.cross(ax, az)
+    view = 0.8 * n + 0.4 * az + 0.2 * ax
+    cam = synth.look_at(tuple(3.0 * view / np.linalg.norm(view)), width=64, height=64)
+    if oracle.raster_scene(Scene([constant_shell(pos, uv, tris, [0, 0, 0, 1])]), cam)[0][0].max() < 0:
+        tris = tris[:, ::-1].copy()
+    sc = Scene([constant_shell(pos, uv, tris, [0.2, 0.4, 0.6, 0.5])])
+    hits, _, _ = oracle.raster_scene(sc, cam)
+    lay, _ = oracle.layers(sc, cam, hits)
+    eye, dirs = pixel_rays(cam)
+    p64 = pos.astype(np.float64)
+    nn = np.cross(p64[tris[0, 1]] - p64[tris[0, 0]], p64[tris[0, 2]] - p64[tris[0, 0]])
+    nn /= np.linalg.norm(nn)
+    h = hits[0] >= 0
+    assert h.sum() > 500
+    assert np.abs(lay[0][h][:, 0:3] - nn).max() < 1e-12
+    checked = 0
+    for y, x in zip(*np.nonzero(h)):
+        d = dirs[y, x]
+        pt = eye + d * (nn @ (p64[0] - eye)) / (nn @ d)
+        a, b = p64[1] - p64[0], p64[3] - p64[0]
+        uu = (pt - p64[0]) @ a / (a @ a)
+        vv = (pt - p64[0]) @ b / (b @ b)
+        # vertices snap to 1/256 px: a ~30 px quad side moves UV by ~1e-4
+        assert abs(lay[0, y, x, 3] - uu) < 3e-4 and abs(lay[0, y, x, 4] - vv) < 3e-4
+        checked += 1
+    assert checked > 500
+
+
+# ----------------------------------------------------------------------------
 # transparency attenuation (Sec. 3): alpha_w = 2 sigmoid(10 |v . n|) - 1
 # ----------------------------------------------------------------------------
 
