@@ -235,6 +235,26 @@ vs_status vs_render_backward(vs_ctx* ctx, const vs_object* obj, const vs_camera*
                              float* const* grad_texels, float* loss, void* workspace,
                              size_t ws_bytes, uint32_t flags, vs_stream_t stream);
 
+/* --- per-layer buffers --------------------------------------------------------- */
+
+/* vs_render plus every shell's own render buffers before blending, as in the
+ * paper's render-buffer figures (Figs. S1/S3): `layers` is device float32
+ * [k, H, W, VS_LAYER_FLOATS], 16-byte aligned; record (shell i, pixel) =
+ *   [0..2] unit geometric normal of the hit face, (p1 - p0) x (p2 - p0) of
+ *          its stored world positions normalised
+ *   [3..4] texture coordinates (u, v) at the pixel (perspective-correct)
+ *   [5]    opacity alpha_i (after VS_FLAG_ALPHA_ATTEN, if set)
+ *   [6]    blending weight T_i alpha_i (the layer's contribution)
+ *   [7..9] colour (r, g, b)
+ *   [10..11] 0
+ * all zero where shell i has no fragment.  The weights sum to the output
+ * alpha, and sum_i weight_i rgb_i + (1 - alpha) bg is the output colour.  A
+ * debugging aid: it runs the generic kernels.  Errors: as vs_render. */
+#define VS_LAYER_FLOATS 12
+vs_status vs_render_layers(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, const float* bg, float* out_rgba,
+                           int32_t* hits, float* layers, void* workspace, size_t ws_bytes, uint32_t flags,
+                           vs_stream_t stream);
+
 /* --- batch ------------------------------------------------------------------------ */
 
 typedef struct {

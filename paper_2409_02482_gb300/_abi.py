@@ -32,6 +32,7 @@ VS_FLAG_LOSS_L2 = 1 << 0
 VS_FLAG_ALPHA_ATTEN = 1 << 1
 VS_FLAG_TEST_STALL = 1 << 30
 VS_MAX_SHELLS = 16
+VS_LAYER_FLOATS = 12
 
 
 class vs_shell_desc(ctypes.Structure):
@@ -93,6 +94,7 @@ SIGNATURES = {
     "vs_workspace_size": ([_P, ctypes.POINTER(_P), ctypes.POINTER(vs_camera), _I, _U,
                            ctypes.POINTER(_SZ)], _I),
     "vs_render": ([_P, _P, ctypes.POINTER(vs_camera), _P, _P, _P, _P, _SZ, _U, _P], _I),
+    "vs_render_layers": ([_P, _P, ctypes.POINTER(vs_camera), _P, _P, _P, _P, _P, _SZ, _U, _P], _I),
     "vs_render_backward": ([_P, _P, ctypes.POINTER(vs_camera), _P, _P, _P,
                             ctypes.POINTER(_P), _P, _P, _SZ, _U, _P], _I),
     "vs_render_batch": ([_P, ctypes.POINTER(vs_batch_item), _I, _P, _I, _P, _SZ, _U, _P], _I),

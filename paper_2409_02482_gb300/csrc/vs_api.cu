@@ -26,7 +26,7 @@ struct vs_ctx {
   int device;
   int num_sms;
   int persist_blocks[2][kNumTc][VS_MAX_SHELLS + 1];   // [backward][texel class][most shells] blocks per SM
-  int persist_blocks_clip[2][VS_MAX_SHELLS + 1];      // the near-plane clipping variant (generic class)
+  int persist_blocks_full[2][VS_MAX_SHELLS + 1];      // the full variant (generic class)
   std::mutex tune_mu;                          // guards tune / tune_set
   vs_tuning tune[2][VS_MAX_SHELLS + 1];        // [backward][most shells]
   bool tune_set[2][VS_MAX_SHELLS + 1];
@@ -152,6 +152,7 @@ struct ItemReq {
   const float* grad_rgb;
   float* const* grad_tex;
   float* loss;
+  float* layers = nullptr;   // per-layer buffers [k, H, W, 12] or null
 };
 
 // Work-unit sizes of one plan, in 32-wide rounds.  The plain launches run
@@ -162,7 +163,8 @@ struct UnitShape {
 };
 
 struct Plan {
-  bool clip = false;             // some shell may reach nearer than znear: clipping kernels
+  bool full = false;             // the full kernels: a shell may reach nearer than znear
+                                 // (clipping) or per-layer buffers are written
   size_t off_items, off_shells, off_done, off_stage, table_end, total;
   std::vector<DItem> items;
   std::vector<DShell> shells;
@@ -251,6 +253,7 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
     it.cam.rfx = 1.0f / c.fx; it.cam.rfy = 1.0f / c.fy;
     it.out = reinterpret_cast<float4*>(req[j].out);
     it.hits = req[j].hits;
+    it.layers = req[j].layers;
     it.grad_rgb = req[j].grad_rgb;
     it.loss = req[j].loss;
     it.k = o.k;
@@ -316,9 +319,9 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
     tc = (tc < 0 || tc == c) ? c : TC_ANY;
   }
   P.tc = tc < 0 ? TC_ANY : tc;
-  P.clip = false;
-  for (int j = 0; j < n; ++j) P.clip = P.clip || needs_clip(*req[j].obj, *req[j].cam);
-  if (P.clip) P.tc = TC_ANY;   // the clipping kernels exist for the generic class
+  P.full = false;
+  for (int j = 0; j < n; ++j) P.full = P.full || needs_clip(*req[j].obj, *req[j].cam) || req[j].layers;
+  if (P.full) P.tc = TC_ANY;   // the full kernels exist for the generic class
   // skewed stages: stage s = SETUP(s), RASTER(s-1), SHADE(s-2)
   long long g = 0;
   for (int st = 0; st < n + NPH - 1; ++st) {
@@ -473,11 +476,11 @@ vs_status launch_batch(vs_ctx* ctx, const Plan& P, void* workspace, int do_backw
   char* ws = static_cast<char*>(workspace);
   vs_status s = upload_table(P, ws, 1, st);
   if (s != VS_OK) return s;
-  const int most = P.clip ? ctx->persist_blocks_clip[do_backward ? 1 : 0][kmax]
+  const int most = P.full ? ctx->persist_blocks_full[do_backward ? 1 : 0][kmax]
                          : ctx->persist_blocks[do_backward ? 1 : 0][P.tc][kmax];
   const int bps = t.blocks_per_sm == 0 ? most : std::min(t.blocks_per_sm, most);
   const long long spin_limit = 1ll << 24;   // ~ seconds with 200 ns sleeps
-  cudaError_t e = vsk::persistent(table_ref(P, ws), do_backward != 0, P.tc, P.clip, ctx->num_sms * bps, spin_limit,
+  cudaError_t e = vsk::persistent(table_ref(P, ws), do_backward != 0, P.tc, P.full, ctx->num_sms * bps, spin_limit,
                                   st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_batch launch");
 }
@@ -582,7 +585,7 @@ vs_status vs_create(vs_ctx** ctx, int device) {
       }
   for (int b = 0; b < 2; ++b)
     for (int K = 1; K <= VS_MAX_SHELLS; ++K) {
-      int& nb = c->persist_blocks_clip[b][K];
+      int& nb = c->persist_blocks_full[b][K];
       if ((e = vsk::persistent_occupancy(b == 1, TC_ANY, true, K, &nb)) != cudaSuccess) {
         delete c;
         return cuda_fail(e, "occupancy query");
@@ -655,8 +658,29 @@ vs_status vs_render(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, con
   if ((s = check_ws(P, workspace, ws_bytes)) != VS_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if ((s = upload_table(P, ws, vsk::plain_forward_launches(P.items[0].units), st)) != VS_OK) return s;
-  cudaError_t e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, P.tc, P.clip, st);
+  cudaError_t e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, P.tc, P.full, st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render launch");
+}
+
+vs_status vs_render_layers(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, const float* bg, float* out_rgba,
+                           int32_t* hits, float* layers, void* workspace, size_t ws_bytes, uint32_t flags,
+                           vs_stream_t stream) {
+  vs_status s = check_item(ctx, obj, cam);
+  if (s != VS_OK) return s;
+  if (!out_rgba || !layers) return fail(VS_ERR_INVALID_ARG, "out_rgba and layers are required");
+  if ((uintptr_t)out_rgba % 16 || (uintptr_t)layers % 16)
+    return fail(VS_ERR_INVALID_ARG, "out_rgba and layers must be 16-byte aligned");
+  ItemReq r{obj, cam, out_rgba, hits, nullptr, nullptr, nullptr, layers};
+  Plan P;
+  char* ws = static_cast<char*>(workspace);
+  if ((s = set_device(ctx)) != VS_OK) return s;
+  if ((s = ensure_bounds(obj)) != VS_OK) return s;
+  if ((s = make_plan(&r, 1, bg, 0, true, flags & ~VS_FLAG_TEST_STALL, ws, P)) != VS_OK) return s;
+  if ((s = check_ws(P, workspace, ws_bytes)) != VS_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if ((s = upload_table(P, ws, vsk::plain_forward_launches(P.items[0].units), st)) != VS_OK) return s;
+  cudaError_t e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, P.tc, P.full, st);
+  return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_layers launch");
 }
 
 vs_status vs_render_backward(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, const float* bg,
@@ -679,7 +703,7 @@ vs_status vs_render_backward(vs_ctx* ctx, const vs_object* obj, const vs_camera*
   if ((s = check_ws(P, workspace, ws_bytes)) != VS_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if ((s = upload_table(P, ws, vsk::plain_backward_launches(P.items[0].units), st)) != VS_OK) return s;
-  cudaError_t e = vsk::plain_backward(table_ref(P, ws), P.items[0].units, P.tc, P.clip, st);
+  cudaError_t e = vsk::plain_backward(table_ref(P, ws), P.items[0].units, P.tc, P.full, st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_backward launch");
 }
 
@@ -793,7 +817,7 @@ vs_status vs_autotune_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, 
     int km = 1;
     vs_status s = plan_batch(ctx, items, n, bg, do_backward, workspace, ws_bytes, flags, start, P, &km);
     if (s != VS_OK) return s;
-    most = P.clip ? ctx->persist_blocks_clip[b][kmax] : ctx->persist_blocks[b][P.tc][kmax];
+    most = P.full ? ctx->persist_blocks_full[b][kmax] : ctx->persist_blocks[b][P.tc][kmax];
   }
   vs_status s = set_device(ctx);
   if (s != VS_OK) return s;
@@ -916,6 +940,6 @@ extern "C" vs_status vs_render_noalloc(vs_ctx* ctx, const vs_object* obj, const 
   cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-alloc header)");
   if ((s = upload_table(P, ws, vsk::plain_forward_launches(P.items[0].units), st)) != VS_OK) return s;
-  e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, P.tc, P.clip, st);
+  e = vsk::plain_forward(table_ref(P, ws), P.items[0].units, P.tc, P.full, st);
   return e == cudaSuccess ? VS_OK : cuda_fail(e, "vs_render_noalloc launch");
 }

@@ -107,6 +107,7 @@ struct alignas(16) DItem {
   const float* grad_rgb;       // [H*W, 3] gradient or target, or null
   float* loss;                 // scalar or null
   unsigned long long* vis;     // [k, H*W] -- workspace
+  float* layers;               // [k, H*W, 12] per-layer buffers or null
   int32_t k, shell0, pad0, clear_units;
   int32_t flags, do_bwd, stall;
   int32_t raster_rounds;       // raster unit = 32 * raster_rounds triangles
@@ -607,7 +608,8 @@ __device__ __forceinline__ float3 ray_dir(const DCam& c, int x, int y) {
 // unit ray direction v and the unit normal n of the hit face, taken as the
 // flat normal (p1 - p0) x (p2 - p0) of the stored triangle.  Grazing rays
 // (v . n -> 0) give alpha_w -> 0, head-on rays 2 sigmoid(10) - 1.
-__device__ __forceinline__ float alpha_atten(const float* pos, const int idx[3], const float3 v) {
+// (p1 - p0) x (p2 - p0) of the stored positions of a face (unnormalised).
+__device__ __forceinline__ float3 face_cross(const float* pos, const int idx[3]) {
   float p[3][3];
 #pragma unroll
   for (int j = 0; j < 3; ++j)
@@ -615,10 +617,14 @@ __device__ __forceinline__ float alpha_atten(const float* pos, const int idx[3],
     for (int d = 0; d < 3; ++d) p[j][d] = __ldg(pos + 3 * (size_t)idx[j] + d);
   const float ax = p[1][0] - p[0][0], ay = p[1][1] - p[0][1], az = p[1][2] - p[0][2];
   const float bx = p[2][0] - p[0][0], by = p[2][1] - p[0][1], bz = p[2][2] - p[0][2];
-  const float nx = ay * bz - az * by, ny = az * bx - ax * bz, nz = ax * by - ay * bx;
-  const float n2 = nx * nx + ny * ny + nz * nz;
+  return make_float3(ay * bz - az * by, az * bx - ax * bz, ax * by - ay * bx);
+}
+
+__device__ __forceinline__ float alpha_atten(const float* pos, const int idx[3], const float3 v) {
+  const float3 n = face_cross(pos, idx);
+  const float n2 = n.x * n.x + n.y * n.y + n.z * n.z;
   // a face with a projected area has a nonzero normal; guard the rounding case
-  const float vn = n2 > 0.0f ? fabsf(nx * v.x + ny * v.y + nz * v.z) * rsqrtf(n2) : 0.0f;
+  const float vn = n2 > 0.0f ? fabsf(n.x * v.x + n.y * v.y + n.z * v.z) * rsqrtf(n2) : 0.0f;
   return 2.0f * sigmoidf_(10.0f * vn) - 1.0f;
 }
 

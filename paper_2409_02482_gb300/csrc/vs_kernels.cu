@@ -26,11 +26,11 @@ __global__ void __launch_bounds__(kThreads) k_setup(TableRef tb, int item) {
   if (u < it.units[PH_SETUP]) unit_setup<false>(it, tb.shells + it.shell0, u);
 }
 
-template <bool CLIP>
+template <bool FULL>
 __global__ void __launch_bounds__(kThreads) k_raster(TableRef tb, int item) {
   const DItem& it = tb.items[item];
   const int w = threadIdx.x >> 5;
-  unit_raster<false, CLIP>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, vs_smem + w * kRasterWarpBytes, w, w + 1);
+  unit_raster<false, FULL>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, vs_smem + w * kRasterWarpBytes, w, w + 1);
 }
 
 }  // namespace vsd
@@ -63,33 +63,33 @@ cudaError_t upload(char* ws, const UploadChunk& c, cudaStream_t st) {
 int plain_forward_launches(const int units[4]) { return (units[0] > 0) + (units[1] > 0) + (units[2] > 0); }
 int plain_backward_launches(const int units[4]) { return (units[0] > 0) + (units[2] > 0); }
 
-cudaError_t plain_forward(const TableRef& tb, const int units[4], int tc, bool clip, cudaStream_t st) {
+cudaError_t plain_forward(const TableRef& tb, const int units[4], int tc, bool full, cudaStream_t st) {
   const int W = vsd::kWarps;
   if (units[0]) vsd::k_setup<<<(units[0] + W - 1) / W, vsd::kThreads, 0, st>>>(tb, 0);
   if (units[1]) {
-    if (clip) vsd::k_raster<true><<<units[1], vsd::kThreads, vsd::kRasterWarpBytes * W, st>>>(tb, 0);
+    if (full) vsd::k_raster<true><<<units[1], vsd::kThreads, vsd::kRasterWarpBytes * W, st>>>(tb, 0);
     else vsd::k_raster<false><<<units[1], vsd::kThreads, vsd::kRasterWarpBytes * W, st>>>(tb, 0);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !units[2]) return e;
-  return tc_ops(tc).shade(tb, false, clip, units[2], vsd::block_smem_bytes(tb.kmax, false), st);
+  return tc_ops(tc).shade(tb, false, full, units[2], vsd::block_smem_bytes(tb.kmax, false), st);
 }
 
-cudaError_t plain_backward(const TableRef& tb, const int units[4], int tc, bool clip, cudaStream_t st) {
+cudaError_t plain_backward(const TableRef& tb, const int units[4], int tc, bool full, cudaStream_t st) {
   const int W = vsd::kWarps;
   if (units[0]) vsd::k_setup<<<(units[0] + W - 1) / W, vsd::kThreads, 0, st>>>(tb, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !units[2]) return e;
-  return tc_ops(tc).shade(tb, true, clip, units[2], vsd::block_smem_bytes(tb.kmax, true), st);
+  return tc_ops(tc).shade(tb, true, full, units[2], vsd::block_smem_bytes(tb.kmax, true), st);
 }
 
-cudaError_t persistent(const TableRef& tb, bool bwd, int tc, bool clip, int grid, long long spin_limit,
+cudaError_t persistent(const TableRef& tb, bool bwd, int tc, bool full, int grid, long long spin_limit,
                        cudaStream_t st) {
-  return tc_ops(tc).persistent(tb, bwd, clip, grid, spin_limit, vsd::block_smem_bytes(tb.kmax, bwd), st);
+  return tc_ops(tc).persistent(tb, bwd, full, grid, spin_limit, vsd::block_smem_bytes(tb.kmax, bwd), st);
 }
 
-cudaError_t persistent_occupancy(bool bwd, int tc, bool clip, int kmax, int* blocks_per_sm) {
-  return tc_ops(tc).occupancy(bwd, clip, vsd::block_smem_bytes(kmax, bwd), blocks_per_sm);
+cudaError_t persistent_occupancy(bool bwd, int tc, bool full, int kmax, int* blocks_per_sm) {
+  return tc_ops(tc).occupancy(bwd, full, vsd::block_smem_bytes(kmax, bwd), blocks_per_sm);
 }
 
 cudaError_t configure_kernels() {

@@ -151,13 +151,13 @@ struct RasterCounts {
   unsigned front, back, nearc, guard, large, bad, clipped;
 };
 
-template <bool HINT, bool CLIP>
+template <bool HINT, bool FULL>
 __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, int t0, unsigned long long* vis,
                                              char* smem, RasterCounts& rc) {
   TriS* s_tri = reinterpret_cast<TriS*>(smem);
   TriPos* s_pos = reinterpret_cast<TriPos*>(smem + sizeof(TriS) * 32);
   int* s_start = reinterpret_cast<int*>(smem + (sizeof(TriS) + sizeof(TriPos)) * 32);
-  const unsigned FULL = 0xffffffffu;
+  const unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31, wbase = 0;
   const int t = t0 + lane;
   const int W = it.cam.W;
@@ -206,14 +206,14 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
     else bad = 1;
   }
   // compact the non-empty boxes and take the exclusive prefix of their sizes
-  const unsigned ne = __ballot_sync(FULL, npx > 0);
+  const unsigned ne = __ballot_sync(kAll, npx > 0);
   int pre = npx;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int v = __shfl_up_sync(FULL, pre, o);
+    const int v = __shfl_up_sync(kAll, pre, o);
     if (lane >= o) pre += v;
   }
-  const int total = __shfl_sync(FULL, pre, 31);
+  const int total = __shfl_sync(kAll, pre, 31);
   const int start = pre - npx;
   if (npx > 0) {
     const int cpos = __popc(ne & ((1u << lane) - 1u));
@@ -222,11 +222,11 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
     s_start[wbase + cpos] = start;
   }
   __syncwarp();
-  const unsigned le = (lane == 31) ? FULL : ((2u << lane) - 1u);
+  const unsigned le = (lane == 31) ? kAll : ((2u << lane) - 1u);
   int carry = 0;
   for (int w0 = 0; w0 < total; w0 += 32) {
     const unsigned b = (npx > 0 && start >= w0 && start < w0 + 32) ? (1u << (start - w0)) : 0u;
-    const unsigned bits = __reduce_or_sync(FULL, b);
+    const unsigned bits = __reduce_or_sync(kAll, b);
     const int slot = w0 + lane;
     if (slot < total) {
       const int o = carry + __popc(bits & le) - 1;
@@ -254,11 +254,11 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
   rc.bad |= bad;
   rc.clipped += clip;
   // large boxes: the warp strides over each one's screen box
-  unsigned lm = __ballot_sync(FULL, large);
+  unsigned lm = __ballot_sync(kAll, large);
   while (lm) {
     const int l = __ffs(lm) - 1;
     lm &= lm - 1;
-    const int tq = __shfl_sync(FULL, t, l);
+    const int tq = __shfl_sync(kAll, t, l);
     Tri T;
     int idx[3];
     if (load_tri(s, it.cam, tq, T, idx) != 0) continue;
@@ -271,12 +271,12 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
   }
   // triangles clipped at the near plane (items with a vertex nearer than
   // znear only)
-  if constexpr (CLIP) {
-    unsigned cm = __ballot_sync(FULL, clip);
+  if constexpr (FULL) {
+    unsigned cm = __ballot_sync(kAll, clip);
     while (cm) {
       const int l = __ffs(cm) - 1;
       cm &= cm - 1;
-      raster_clipped<HINT>(s, it.cam, __shfl_sync(FULL, t, l), vis);
+      raster_clipped<HINT>(s, it.cam, __shfl_sync(kAll, t, l), vis);
     }
   }
   __syncwarp();   // the records are reused by the next round
@@ -284,7 +284,7 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
 
 // Raster unit: 32 * it.raster_rounds triangles of one shell in rounds of 32;
 // this warp runs rounds [r0, r1).
-template <bool HINT, bool CLIP>
+template <bool HINT, bool FULL>
 static __device__ __forceinline__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* smem,
                                                    int r0, int r1) {
   int i = 0;
@@ -295,7 +295,7 @@ static __device__ __forceinline__ void unit_raster(const DItem& it, const DShell
   unsigned long long* vis = it.vis + (size_t)i * it.cam.W * it.cam.H;
   RasterCounts rc = {0, 0, 0, 0, 0, 0, 0};
   const int rounds = min(r1, min(per_unit, s.nt - base + 31) / 32);
-  for (int r = r0; r < rounds; ++r) raster_round<HINT, CLIP>(it, s, base + 32 * r, vis, smem, rc);
+  for (int r = r0; r < rounds; ++r) raster_round<HINT, FULL>(it, s, base + 32 * r, vis, smem, rc);
   warp_count(&hdr->front, rc.front);
   warp_count(&hdr->back, rc.back);
   warp_count(&hdr->nearc, rc.nearc);
@@ -517,6 +517,25 @@ static __device__ __noinline__ void atten_pass(const DCam& cam, const DShell* sh
   }
 }
 
+// Per-layer buffers (Figs. S1/S3): record of shell i at pixel p, 12 floats =
+// unit face normal, u, v | opacity, blending weight T_i alpha_i, r | g, b, 0, 0.
+__device__ __forceinline__ float* layer_rec(const DItem& it, int i, int p) {
+  return it.layers + 12 * ((size_t)i * it.cam.W * it.cam.H + p);
+}
+
+// The geometric part of a fragment's record: face normal and the UV at the
+// pixel (from the unclamped texel coordinate: u = (x + 1/2) / W).
+__device__ __forceinline__ void layer_geom(const DItem& it, const DShell& s, const int idx[3], int i, int p, int ix,
+                                           float fx, int iy, float fy) {
+  const float3 n = face_cross(s.pos, idx);
+  const float r = rsqrtf(n.x * n.x + n.y * n.y + n.z * n.z);
+  float* L = layer_rec(it, i, p);
+  const float u = __fdiv_rn(__fadd_rn(__fadd_rn((float)ix, 0.5f), fx), (float)s.tw);
+  const float v = __fdiv_rn(__fadd_rn(__fadd_rn((float)iy, 0.5f), fy), (float)s.th);
+  *reinterpret_cast<float4*>(L) = make_float4(n.x * r, n.y * r, n.z * r, u);
+  L[4] = v;
+}
+
 // Markers in the lane word of a fragment-list entry.
 constexpr unsigned kBadFrag = 0x8000u;    // unusable triangle: invisible, no adjoint
 constexpr unsigned kClipFrag = 0x4000u;   // triangle to clip at the near plane (pending)
@@ -557,6 +576,7 @@ static __device__ __forceinline__ void shade_clipped(const DItem& it, const DShe
     float3 v = make_float3(0.f, 0.f, 1.f);
     if (is_sh<TC>(s)) v = ray_dir(it.cam, x, y);
     fr = fetch_frag<TC>(s, f, ix, fx, iy, fy, v);
+    if (it.layers) layer_geom(it, s, idx, e >> kTriBits, pp, ix, fx, iy, fy);
     ++*nfrag;
   }
   sfrag[j] = make_float4(fr.r, fr.g, fr.b, fr.a);
@@ -599,10 +619,10 @@ static __device__ __forceinline__ void shade_clipped(const DItem& it, const DShe
 static_assert(kMaxShells <= 16, "shell index takes 4 bits of the lane word");
 static_assert(kFragCap >= kMaxShells, "a pixel's fragments must fit one pass");
 
-template <bool BWD, bool FROM_HITS, int TC, bool CLIP>
+template <bool BWD, bool FROM_HITS, int TC, bool FULL>
 __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, int pbase, char* wb, int K,
                                             unsigned& nfrag, unsigned& bad, float& loss_acc) {
-  const unsigned FULL = 0xffffffffu;
+  const unsigned kAll = 0xffffffffu;
   const int W = it.cam.W, H = it.cam.H;
   const int HW = W * H;
   const int k = it.k;
@@ -649,19 +669,26 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
   int pre = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int v = __shfl_up_sync(FULL, pre, o);
+    const int v = __shfl_up_sync(kAll, pre, o);
     if (lane >= o) pre += v;
   }
   const int start = pre - cnt;
   const bool atten = (it.flags & VS_FLAG_ALPHA_ATTEN) != 0;
   int clip_pending = 0;
+  if constexpr (FULL) {   // per-layer buffers: every shell's record starts at zero
+    if (it.layers && pix_ok)
+      for (int i = 0; i < k; ++i) {
+        float4* L = reinterpret_cast<float4*>(layer_rec(it, i, p));
+        L[0] = L[1] = L[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+  }
   __syncwarp();
 
   for (int l0 = 0; l0 < 32;) {
     // lanes [l0, l1) whose fragments fit the list; pre is nondecreasing
-    const int f0 = __shfl_sync(FULL, start, l0);
-    const int l1 = __popc(__ballot_sync(FULL, pre - f0 <= C));
-    const int nf = __shfl_sync(FULL, pre, l1 - 1) - f0;
+    const int f0 = __shfl_sync(kAll, start, l0);
+    const int l1 = __popc(__ballot_sync(kAll, pre - f0 <= C));
+    const int nf = __shfl_sync(kAll, pre, l1 - 1) - f0;
     const bool mine = lane >= l0 && lane < l1;
     const int s0 = start - f0;          // this lane's first list slot
     if (mine) {
@@ -697,7 +724,7 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
         int idx[3];
         const int y = pp / W, x = pp - y * W;
         const int r = t < s.nt ? load_tri_shade(s, t, Tr, idx) : 4;
-        if (CLIP && r == 2) {
+        if (FULL && r == 2) {
           // a vertex nearer than znear (or off the guard band): the triangle
           // is clipped; shaded by the pass below
           clip_pending = 1;
@@ -721,6 +748,9 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
           float3 v = make_float3(0.f, 0.f, 1.f);
           if (is_sh<TC>(s)) v = ray_dir(it.cam, x, y);
           fr = fetch_frag<TC>(s, f, ix, fx, iy, fy, v);
+          if constexpr (FULL) {
+            if (it.layers) layer_geom(it, s, idx, i, pp, ix, fx, iy, fy);
+          }
           ++nfrag;
         }
         // raw opacity here; the composite applies alpha_w
@@ -730,7 +760,7 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
     }
     __syncwarp();
     // 2c. fragments of triangles clipped at the near plane (rare; out of line)
-    if (CLIP && __any_sync(FULL, clip_pending)) {
+    if (FULL && __any_sync(kAll, clip_pending)) {
       for (int j = lane; j < nf; j += 32)
         if (spl[j] & kClipFrag) shade_clipped<BWD, TC>(it, sh, pbase, j, sent, spl, sfrag, sxy, sfxy, &nfrag, &bad);
       __syncwarp();
@@ -744,6 +774,16 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
         if constexpr (BWD) sT[s0 + c] = T;
         const float a = f.w * saw[s0 + c];
         const float ta = T * a;
+        if constexpr (FULL) {
+          if (it.layers && !(spl[s0 + c] & kBadFrag)) {
+            float* L = layer_rec(it, (spl[s0 + c] >> 5) & 15, p);
+            L[5] = a;
+            L[6] = ta;
+            L[7] = f.x;
+            L[8] = f.y;
+            L[9] = f.z;
+          }
+        }
         Cr = fmaf(ta, f.x, Cr);
         Cg = fmaf(ta, f.y, Cg);
         Cb = fmaf(ta, f.z, Cb);
@@ -819,25 +859,25 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
 
 // Shading unit: 32 * it.shade_rounds consecutive pixels in rounds of 32;
 // this warp runs rounds [r0, r1).  `wb` is the warp's shared-memory slice.
-template <bool BWD, bool FROM_HITS, int TC, bool CLIP>
+template <bool BWD, bool FROM_HITS, int TC, bool FULL>
 __device__ __forceinline__ void unit_shade(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* wb, int K,
                                            int r0, int r1) {
-  const unsigned FULL = 0xffffffffu;
+  const unsigned kAll = 0xffffffffu;
   const int HW = it.cam.W * it.cam.H;
   unsigned nfrag = 0, bad = 0;
   float loss = 0.0f;
   for (int r = r0; r < r1; ++r) {
     const int pbase = (u * it.shade_rounds + r) * 32;
     if (pbase >= HW) break;
-    shade_round<BWD, FROM_HITS, TC, CLIP>(it, sh, pbase, wb, K, nfrag, bad, loss);
+    shade_round<BWD, FROM_HITS, TC, FULL>(it, sh, pbase, wb, K, nfrag, bad, loss);
   }
   const int lane = threadIdx.x & 31;
   if (!FROM_HITS) warp_count(&hdr->frags, nfrag);
-  if (__any_sync(FULL, bad) && lane == 0) record_error(hdr, VS_ERR_INVALID_ARG);
+  if (__any_sync(kAll, bad) && lane == 0) record_error(hdr, VS_ERR_INVALID_ARG);
   if constexpr (BWD) {
     if (it.loss && (it.flags & VS_FLAG_LOSS_L2)) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(FULL, loss, o);
+      for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(kAll, loss, o);
       if (lane == 0 && loss != 0.0f) atomicAdd(it.loss, loss);
     }
   }
@@ -850,11 +890,11 @@ __device__ __forceinline__ char* warp_smem(int K, bool bwd) {
   return vs_smem + (threadIdx.x >> 5) * warp_slice_bytes(K, bwd);
 }
 
-template <bool BWD, bool FROM_HITS, int TC, bool CLIP>
+template <bool BWD, bool FROM_HITS, int TC, bool FULL>
 __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS) k_shade(TableRef tb, int item) {
   const DItem& it = tb.items[item];
   const int w = threadIdx.x >> 5;
-  unit_shade<BWD, FROM_HITS, TC, CLIP>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, warp_smem(tb.kmax, BWD), tb.kmax, w,
+  unit_shade<BWD, FROM_HITS, TC, FULL>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, warp_smem(tb.kmax, BWD), tb.kmax, w,
                              w + 1);
 }
 
@@ -882,16 +922,16 @@ static __device__ bool wait_done(const int* ctr, int target, long long limit, Ws
 // stages (while still in L2).  A unit waits only for the previous phase of
 // its own item, whose units were all dispensed in an earlier stage to warps
 // that are already running, so the wait always ends (and is bounded anyway).
-template <bool BWD, int TC, bool CLIP>
+template <bool BWD, int TC, bool FULL>
 __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS) k_persistent(TableRef tb, long long spin_limit) {
-  const unsigned FULL = 0xffffffffu;
+  const unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   WsHeader* hdr = tb.hdr;
   char* smem = warp_smem(tb.kmax, BWD);
   for (;;) {
     int g = 0;
     if (lane == 0) g = *(volatile int*)&hdr->abort ? tb.total : (int)atomicAdd(&hdr->next_unit, 1u);
-    g = __shfl_sync(FULL, g, 0);
+    g = __shfl_sync(kAll, g, 0);
     if (g >= tb.total) break;
     // stage: last s with stage_pre[s] <= g
     int lo = 0, hi = tb.n + NPH - 2;
@@ -916,15 +956,15 @@ __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS)
       if (ph == PH_SHADE && it.stall && u == 0) { target += 1; lim = 4096; }
       ok = wait_done(tb.done + j * NPH + ph - 1, target, lim, hdr) ? 1 : 0;
     }
-    ok = __shfl_sync(FULL, ok, 0);
+    ok = __shfl_sync(kAll, ok, 0);
     __syncwarp();   // orders every lane's reads after lane 0's acquire
     if (!ok) break;
     const DShell* sh = tb.shells + it.shell0;
     switch (ph) {
       case PH_SETUP: unit_setup<BWD>(it, sh, u); break;
-      case PH_RASTER: unit_raster<BWD, CLIP>(it, sh, u, hdr, smem, 0, it.raster_rounds); break;
+      case PH_RASTER: unit_raster<BWD, FULL>(it, sh, u, hdr, smem, 0, it.raster_rounds); break;
       default:
-        unit_shade<BWD, false, TC, CLIP>(it, sh, u, hdr, smem, tb.kmax, 0, it.shade_rounds);
+        unit_shade<BWD, false, TC, FULL>(it, sh, u, hdr, smem, tb.kmax, 0, it.shade_rounds);
     }
     __syncwarp();
     if (lane == 0) {

@@ -38,24 +38,24 @@ namespace vsk {
 // Launchers of the kernels compiled for one texel class (vsd::TC_*), one
 // table per translation unit vs_tc_*.cu.
 struct TcOps {
-  cudaError_t (*persistent)(const TableRef& tb, bool bwd, bool clip, int grid, long long spin_limit, size_t smem,
+  cudaError_t (*persistent)(const TableRef& tb, bool bwd, bool full, int grid, long long spin_limit, size_t smem,
                             cudaStream_t st);
-  cudaError_t (*shade)(const TableRef& tb, bool bwd, bool clip, int blocks, size_t smem, cudaStream_t st);
-  cudaError_t (*occupancy)(bool bwd, bool clip, size_t smem, int* blocks_per_sm);
+  cudaError_t (*shade)(const TableRef& tb, bool bwd, bool full, int blocks, size_t smem, cudaStream_t st);
+  cudaError_t (*occupancy)(bool bwd, bool full, size_t smem, int* blocks_per_sm);
   cudaError_t (*configure)(int most_smem_fwd, int most_smem_bwd);
 };
-// clip = the variant that clips triangles at the near plane (compiled for
-// the generic class only; the host asks for it when a shell may reach
-// nearer than znear)
+// full = the variant with the rare features -- near-plane clipping and the
+// per-layer buffers -- compiled for the generic class only; the host asks for
+// it when a shell may reach nearer than znear or layers are requested
 extern const TcOps kTcAny, kTcRgba, kTcSh0, kTcSh1, kTcSh2, kTcSh3, kTcU80, kTcU81, kTcU82, kTcU83;
 
 cudaError_t upload(char* ws, const UploadChunk& c, cudaStream_t st);
 int plain_forward_launches(const int units[4]);
 int plain_backward_launches(const int units[4]);
-cudaError_t plain_forward(const TableRef& tb, const int units[4], int tc, bool clip, cudaStream_t st);
-cudaError_t plain_backward(const TableRef& tb, const int units[4], int tc, bool clip, cudaStream_t st);
-cudaError_t persistent(const TableRef& tb, bool bwd, int tc, bool clip, int grid, long long spin_limit,
+cudaError_t plain_forward(const TableRef& tb, const int units[4], int tc, bool full, cudaStream_t st);
+cudaError_t plain_backward(const TableRef& tb, const int units[4], int tc, bool full, cudaStream_t st);
+cudaError_t persistent(const TableRef& tb, bool bwd, int tc, bool full, int grid, long long spin_limit,
                        cudaStream_t st);
-cudaError_t persistent_occupancy(bool bwd, int tc, bool clip, int kmax, int* blocks_per_sm);
+cudaError_t persistent_occupancy(bool bwd, int tc, bool full, int kmax, int* blocks_per_sm);
 cudaError_t configure_kernels();
 }  // namespace vsk

@@ -17,7 +17,7 @@ from ._abi import (VS_FLAG_ALPHA_ATTEN, VS_FLAG_LOSS_L2, VS_TEX_RGBA_F32, VS_TEX
                    vs_camera, vs_cost_fn, vs_shell_desc, vs_stats, vs_tuning)
 
 __all__ = ["Context", "ShellObject", "camera_struct", "workspace_size", "make_workspace",
-           "render", "render_backward", "render_batch", "read_stats", "VSRender",
+           "render", "render_layers", "render_backward", "render_batch", "read_stats", "VSRender",
            "tuning", "set_batch_tuning", "get_batch_tuning", "tune_search", "autotune_batch",
            "VS_FLAG_ALPHA_ATTEN", "VS_FLAG_LOSS_L2", "VS_TEX_RGBA_F32", "VS_TEX_SH_F16", "VS_TEX_SH_U8",
            "baked_layout"]
@@ -165,6 +165,22 @@ def render(ctx: Context, obj: ShellObject, cam, ws: torch.Tensor, bg=(0.0, 0.0, 
     check(ctx.lib.vs_render(ctx.handle, obj.handle, ctypes.byref(c), bgv, _ptr(out), _ptr(hits),
                             _ptr(ws), ws.numel(), flags, _stream(stream)))
     return out, hits
+
+
+def render_layers(ctx: Context, obj: ShellObject, cam, ws: torch.Tensor, bg=(0.0, 0.0, 0.0), flags: int = 0,
+                  stream=None):
+    """vs_render_layers: (rgba [H,W,4], hits [k,H,W], layers [k,H,W,12]) --
+    per shell: unit face normal, u, v, opacity, blending weight, rgb, 0, 0."""
+    H, W = int(cam.height), int(cam.width)
+    dev = ws.device
+    out = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    hits = torch.empty((obj.k, H, W), dtype=torch.int32, device=dev)
+    layers = torch.empty((obj.k, H, W, _abi.VS_LAYER_FLOATS), dtype=torch.float32, device=dev)
+    c = camera_struct(cam)
+    bgv = (ctypes.c_float * 3)(*bg)
+    check(ctx.lib.vs_render_layers(ctx.handle, obj.handle, ctypes.byref(c), bgv, _ptr(out), _ptr(hits),
+                                   _ptr(layers), _ptr(ws), ws.numel(), flags, _stream(stream)))
+    return out, hits, layers
 
 
 def render_backward(ctx: Context, obj: ShellObject, cam, ws: torch.Tensor, hits: torch.Tensor,

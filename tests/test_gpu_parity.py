@@ -338,6 +338,39 @@ def test_clipped_batch_and_backward_match(vs, ctx):
 
 
 # ----------------------------------------------------------------------------
+# per-layer buffers (Figs. S1/S3)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["c2", "baked", "closeup"])
+def test_layer_buffers_match_oracle(vs, ctx, case):
+    if case == "c2":
+        (sc, cams), = synth.config_scene("c2", scale=0.004, views=2)
+        cam, flags = cams[1], vs.VS_FLAG_ALPHA_ATTEN
+    elif case == "baked":
+        sc, cam, flags = _baked_scene(3, 24, 64, 3, 1, seed=2), synth.look_at((1.0, -2.5, 1.0), width=70, height=56), 0
+    else:
+        geo = synth.concentric_icospheres([1.0, 0.9], subdiv=3)
+        rng = np.random.default_rng(43)
+        sc = Scene([Shell(p, u, t, rng.uniform(0.1, 0.9, (16, 16, 4)).astype(np.float32), FMT_RGBA_F32)
+                    for p, u, t in geo])
+        cam, flags = _closeup_cameras()[0], 0
+    obj = vs.ShellObject.from_scene(ctx, sc)
+    ws = vs.make_workspace(ctx, [obj], [cam])
+    out, hits, lay = vs.render_layers(ctx, obj, cam, ws, bg=(0.1, 0.2, 0.3), flags=flags)
+    assert vs.read_stats(ws)["device_status"] == 0
+    plain, plain_hits = vs.render(ctx, obj, cam, ws, bg=(0.1, 0.2, 0.3), flags=flags)
+    assert torch.equal(hits, plain_hits)
+    assert (out - plain).abs().max().item() <= 1e-6
+    ref_lay, ref = oracle.layers(sc, cam, hits.cpu().numpy(), bg=(0.1, 0.2, 0.3), flags=flags)
+    lay = lay.cpu().numpy()
+    tol = tol_of(sc)
+    assert np.abs(lay[..., 0:3] - ref_lay[..., 0:3]).max() <= 1e-5      # normals
+    assert np.abs(lay[..., 3:5] - ref_lay[..., 3:5]).max() <= 1e-5      # uv
+    assert np.abs(lay[..., 5:10] - ref_lay[..., 5:10]).max() <= tol     # opacity, weight, rgb
+    assert np.all(lay[..., 10:] == 0)
+
+
+# ----------------------------------------------------------------------------
 # transparency attenuation (Sec. 3): alpha * (2 sigmoid(10 |v . n|) - 1)
 # ----------------------------------------------------------------------------
 
