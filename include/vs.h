@@ -341,6 +341,66 @@ vs_status vs_autotune_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, 
                             int32_t do_backward, void* workspace, size_t ws_bytes, uint32_t flags,
                             vs_stream_t stream, int32_t repeats, vs_tuning* best);
 
+/* --- neural texture (Sec. 3 "Texturing Meshes") -------------------------------- */
+
+/* A texture as a function: a 2D multiresolution hash encoding (the trainable
+ * positional encoding of Mueller et al. 2022) followed by an MLP of two
+ * hidden ReLU layers and a linear output (the supplement's neural texture
+ * architecture), evaluated at the texel centres ((i + 1/2)/W, (j + 1/2)/H)
+ * of the target resolution -- "grounded", so the texture the renderer
+ * samples bilinearly IS the prediction.  Definitions:
+ *   level l resolution N_l = floor(base_res * growth^l); p = x N_l; corners
+ *   floor(p) + {0,1}^2 with bilinear weights; table row of corner c: dense
+ *   c0 + c1 (N_l + 1) if (N_l + 1)^2 <= T, else (c0 XOR c1 * 2654435761)
+ *   mod T (uint32 arithmetic); feature f_l = sum w table[l, row, :];
+ *   y = W2 relu(W1 relu(W0 f + b0) + b1) + b2.
+ * Parameters: one device float32 vector, blocks in this order:
+ *   table [L, T, F], W0 [H, L F], b0 [H], W1 [H, H], b1 [H], W2 [C, H], b2 [C]
+ * (row-major).  The paper uses separate networks for colour and opacity:
+ * write them to different channel ranges of one texel array (ch0). */
+typedef struct {
+  int32_t levels;        /* L: 1 .. 16                                    */
+  int32_t features;      /* F per level: 1 .. 8                           */
+  int32_t log2_table;    /* T = 2^log2_table rows per level: 2 .. 24      */
+  int32_t base_res;      /* N_min >= 1                                     */
+  float growth;          /* b in [1, 4]; N_l <= 2^20                       */
+  int32_t hidden;        /* H: 1 .. 512                                    */
+  int32_t out_ch;        /* C: 1 .. 256                                    */
+} vs_ntex_config;
+
+/* Offsets (in floats) of the seven parameter blocks and the total count.
+ * Host only.  Errors: VS_ERR_INVALID_ARG for a config out of range. */
+vs_status vs_ntex_layout(const vs_ntex_config* cfg, int64_t offsets[7], int64_t* total);
+
+/* Workspace bytes for vs_ntex_forward / vs_ntex_backward on a tex_w x tex_h
+ * texture (activations of up to 2^18 texels at a time).  Host only. */
+vs_status vs_ntex_workspace_size(const vs_ntex_config* cfg, int32_t tex_w, int32_t tex_h, size_t* bytes);
+
+/* Evaluates the network at every texel centre and writes channels
+ * [ch0, ch0 + C) of texels [tex_h, tex_w, pitch] (dtype 0 = float32,
+ * 1 = float16, the renderer's SH storage).  FP32 arithmetic (the layers as
+ * FP32 GEMMs).  Errors: VS_ERR_INVALID_ARG (config, sizes, ch0 + C > pitch,
+ * NULL), VS_ERR_WORKSPACE, VS_ERR_CUDA. */
+vs_status vs_ntex_forward(vs_ctx* ctx, const vs_ntex_config* cfg, const float* params, int32_t tex_w, int32_t tex_h,
+                          void* texels, int32_t dtype, int32_t pitch, int32_t ch0, void* workspace, size_t ws_bytes,
+                          vs_stream_t stream);
+
+/* Adjoint: given dL/d(texel values) (float32 [tex_h, tex_w, pitch], e.g.
+ * from vs_render_backward), ADDS dL/d(params) into grads (same layout as
+ * params; zero it first).  Recomputes the activations; hash-table gradients
+ * use float atomics (summation order varies run to run).  Errors: as
+ * vs_ntex_forward. */
+vs_status vs_ntex_backward(vs_ctx* ctx, const vs_ntex_config* cfg, const float* params, int32_t tex_w, int32_t tex_h,
+                           const float* grad_texels, int32_t pitch, int32_t ch0, float* grads, void* workspace,
+                           size_t ws_bytes, vs_stream_t stream);
+
+/* One Adam step (Kingma & Ba, bias-corrected) on n parameters in place:
+ * m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * step >= 1.  Errors: VS_ERR_INVALID_ARG, VS_ERR_CUDA. */
+vs_status vs_adam_step(vs_ctx* ctx, float* params, const float* grads, float* m, float* v, int64_t n, float lr,
+                       float beta1, float beta2, float eps, int32_t step, vs_stream_t stream);
+
 /* --- allocation-free forward ------------------------------------------------- */
 
 /* vs_render for callers that cannot allocate device memory at all, and so

@@ -69,6 +69,12 @@ VS_TUNING_DEFAULT_SHADE_PIXELS = 256
 vs_cost_fn = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.POINTER(vs_tuning), ctypes.c_void_p)
 
 
+class vs_ntex_config(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("features", ctypes.c_int32), ("log2_table", ctypes.c_int32),
+                ("base_res", ctypes.c_int32), ("growth", ctypes.c_float), ("hidden", ctypes.c_int32),
+                ("out_ch", ctypes.c_int32)]
+
+
 class vs_stats(ctypes.Structure):
     _fields_ = [("device_status", ctypes.c_int32), ("fragments", ctypes.c_uint64),
                 ("tris_front", ctypes.c_uint64), ("tris_culled_back", ctypes.c_uint64),
@@ -102,6 +108,13 @@ SIGNATURES = {
     "vs_render_noalloc": ([_P, _P, ctypes.POINTER(vs_camera), _P, _P, _P, _U, _P], _I),
     "vs_baked_layout": ([_I, _I, _I, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_I), ctypes.POINTER(_I),
                          ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64)], _I),
+    "vs_ntex_layout": ([ctypes.POINTER(vs_ntex_config), ctypes.POINTER(ctypes.c_int64),
+                        ctypes.POINTER(ctypes.c_int64)], _I),
+    "vs_ntex_workspace_size": ([ctypes.POINTER(vs_ntex_config), _I, _I, ctypes.POINTER(_SZ)], _I),
+    "vs_ntex_forward": ([_P, ctypes.POINTER(vs_ntex_config), _P, _I, _I, _P, _I, _I, _I, _P, _SZ, _P], _I),
+    "vs_ntex_backward": ([_P, ctypes.POINTER(vs_ntex_config), _P, _I, _I, _P, _I, _I, _P, _P, _SZ, _P], _I),
+    "vs_adam_step": ([_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                      ctypes.c_float, _I, _P], _I),
     "vs_set_batch_tuning": ([_P, _I, _I, ctypes.POINTER(vs_tuning)], _I),
     "vs_get_batch_tuning": ([_P, _I, _I, ctypes.POINTER(vs_tuning)], _I),
     "vs_tune_search": ([ctypes.POINTER(vs_tuning), _I, vs_cost_fn, _P, ctypes.POINTER(vs_tuning),

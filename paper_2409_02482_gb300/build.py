@@ -25,7 +25,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
               "-I", INCLUDE, "-I", CSRC]
 SOURCES = ["vs_api.cu", "vs_kernels.cu", "vs_tc_any.cu", "vs_tc_rgba.cu", "vs_tc_sh0.cu", "vs_tc_sh1.cu",
-           "vs_tc_sh2.cu", "vs_tc_sh3.cu", "vs_tc_u80.cu", "vs_tc_u81.cu", "vs_tc_u82.cu", "vs_tc_u83.cu"]
+           "vs_tc_sh2.cu", "vs_tc_sh3.cu", "vs_tc_u80.cu", "vs_tc_u81.cu", "vs_tc_u82.cu", "vs_tc_u83.cu",
+           "vs_ntex.cu"]
 
 
 def nvcc() -> str:
@@ -52,7 +53,7 @@ def build(verbose_ptxas: bool = False) -> str:
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     tmp = LIB_PATH + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "--cudart", "static", "-o", tmp, *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "--cudart", "static", "-o", tmp, *objs, "-lcublas"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -19,6 +19,7 @@
 #include "vs.h"
 #include "vs_device.cuh"
 #include "vs_kernels.h"
+#include "vs_ntex.h"
 
 using namespace vsd;
 
@@ -27,6 +28,8 @@ struct vs_ctx {
   int num_sms;
   int persist_blocks[2][kNumTc][VS_MAX_SHELLS + 1];   // [backward][texel class][most shells] blocks per SM
   int persist_blocks_full[2][VS_MAX_SHELLS + 1];      // the full variant (generic class)
+  std::mutex blas_mu;                                  // guards blas
+  cublasHandle_t blas;                                 // created on the first neural-texture call
   std::mutex tune_mu;                          // guards tune / tune_set
   vs_tuning tune[2][VS_MAX_SHELLS + 1];        // [backward][most shells]
   bool tune_set[2][VS_MAX_SHELLS + 1];
@@ -598,6 +601,7 @@ vs_status vs_create(vs_ctx** ctx, int device) {
 }
 
 vs_status vs_destroy(vs_ctx* ctx) {
+  if (ctx && ctx->blas) cublasDestroy(ctx->blas);
   delete ctx;
   return VS_OK;
 }
@@ -842,6 +846,135 @@ vs_status vs_autotune_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, 
   }
   if (best) *best = won;
   return VS_OK;
+}
+
+// --- neural texture -----------------------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+vs_status check_ntex(const vs_ntex_config* c) {
+  if (!c) return fail(VS_ERR_INVALID_ARG, "config is NULL");
+  if (c->levels < 1 || c->levels > 16) return fail(VS_ERR_INVALID_ARG, "levels %d out of [1, 16]", c->levels);
+  if (c->features < 1 || c->features > 8) return fail(VS_ERR_INVALID_ARG, "features %d out of [1, 8]", c->features);
+  if (c->log2_table < 2 || c->log2_table > 24)
+    return fail(VS_ERR_INVALID_ARG, "log2_table %d out of [2, 24]", c->log2_table);
+  if (c->base_res < 1) return fail(VS_ERR_INVALID_ARG, "base_res %d < 1", c->base_res);
+  if (!(c->growth >= 1.0f && c->growth <= 4.0f)) return fail(VS_ERR_INVALID_ARG, "growth out of [1, 4]");
+  if ((double)c->base_res * std::pow((double)c->growth, c->levels - 1) > (double)(1 << 20))
+    return fail(VS_ERR_INVALID_ARG, "finest level resolution above 2^20");
+  if (c->hidden < 1 || c->hidden > 512) return fail(VS_ERR_INVALID_ARG, "hidden %d out of [1, 512]", c->hidden);
+  if (c->out_ch < 1 || c->out_ch > 256) return fail(VS_ERR_INVALID_ARG, "out_ch %d out of [1, 256]", c->out_ch);
+  return VS_OK;
+}
+
+vs_status check_ntex_call(vs_ctx* ctx, const vs_ntex_config* cfg, const void* params, int32_t W, int32_t H,
+                          const void* texels, int32_t pitch, int32_t ch0, void* ws, size_t ws_bytes) {
+  vs_status s = check_ntex(cfg);
+  if (s != VS_OK) return s;
+  if (!ctx || !params || !texels) return fail(VS_ERR_INVALID_ARG, "NULL argument");
+  if (W < 1 || H < 1 || W > 65536 || H > 65536 || (long long)W * H > (1ll << 30))
+    return fail(VS_ERR_INVALID_ARG, "texture %dx%d out of range", W, H);
+  if (ch0 < 0 || pitch < 1 || ch0 + cfg->out_ch > pitch)
+    return fail(VS_ERR_INVALID_ARG, "channels [%d, %d) do not fit pitch %d", ch0, ch0 + cfg->out_ch, pitch);
+  if ((uintptr_t)params % 4) return fail(VS_ERR_INVALID_ARG, "params must be 4-byte aligned");
+  const int rows = (long long)W * H < vsntex::kNtexChunk ? W * H : vsntex::kNtexChunk;
+  if (!ws || (uintptr_t)ws % 256) return fail(VS_ERR_WORKSPACE, "workspace NULL or not 256-byte aligned");
+  const size_t need = vsntex::ws_floats(*cfg, rows) * sizeof(float);
+  if (ws_bytes < need) return fail(VS_ERR_WORKSPACE, "workspace has %zu bytes, needs %zu", ws_bytes, need);
+  return VS_OK;
+}
+
+vs_status get_blas(vs_ctx* ctx, cudaStream_t st, cublasHandle_t* h) {
+  std::lock_guard<std::mutex> g(ctx->blas_mu);
+  if (!ctx->blas) {
+    if (cublasCreate(&ctx->blas) != CUBLAS_STATUS_SUCCESS) {
+      ctx->blas = nullptr;
+      return fail(VS_ERR_CUDA, "cublasCreate failed");
+    }
+    // FP32 arithmetic in the GEMMs: no reduced-precision tensor-core paths
+    cublasSetMathMode(ctx->blas, CUBLAS_PEDANTIC_MATH);
+  }
+  if (cublasSetStream(ctx->blas, st) != CUBLAS_STATUS_SUCCESS) return fail(VS_ERR_CUDA, "cublasSetStream failed");
+  *h = ctx->blas;
+  return VS_OK;
+}
+
+vs_status ntex_status(int r, const char* what) {
+  if (r == 0) return VS_OK;
+  if (r == -1000) return fail(VS_ERR_CUDA, "%s: a cuBLAS call failed", what);
+  return cuda_fail((cudaError_t)r, what);
+}
+
+}  // namespace
+
+extern "C" {
+
+vs_status vs_ntex_layout(const vs_ntex_config* cfg, int64_t offsets[7], int64_t* total) {
+  vs_status s = check_ntex(cfg);
+  if (s != VS_OK) return s;
+  const int64_t L = cfg->levels, T = 1ll << cfg->log2_table, F = cfg->features, H = cfg->hidden, C = cfg->out_ch;
+  const int64_t sz[7] = {L * T * F, H * L * F, H, H * H, H, C * H, C};
+  int64_t off = 0;
+  for (int i = 0; i < 7; ++i) {
+    if (offsets) offsets[i] = off;
+    off += sz[i];
+  }
+  if (total) *total = off;
+  return VS_OK;
+}
+
+vs_status vs_ntex_workspace_size(const vs_ntex_config* cfg, int32_t tex_w, int32_t tex_h, size_t* bytes) {
+  vs_status s = check_ntex(cfg);
+  if (s != VS_OK) return s;
+  if (!bytes) return fail(VS_ERR_INVALID_ARG, "bytes is NULL");
+  if (tex_w < 1 || tex_h < 1) return fail(VS_ERR_INVALID_ARG, "texture %dx%d out of range", tex_w, tex_h);
+  const long long N = (long long)tex_w * tex_h;
+  const int rows = N < vsntex::kNtexChunk ? (int)N : vsntex::kNtexChunk;
+  *bytes = vsntex::ws_floats(*cfg, rows) * sizeof(float);
+  return VS_OK;
+}
+
+vs_status vs_ntex_forward(vs_ctx* ctx, const vs_ntex_config* cfg, const float* params, int32_t tex_w, int32_t tex_h,
+                          void* texels, int32_t dtype, int32_t pitch, int32_t ch0, void* workspace, size_t ws_bytes,
+                          vs_stream_t stream) {
+  vs_status s = check_ntex_call(ctx, cfg, params, tex_w, tex_h, texels, pitch, ch0, workspace, ws_bytes);
+  if (s != VS_OK) return s;
+  if (dtype != 0 && dtype != 1) return fail(VS_ERR_INVALID_ARG, "dtype %d is neither 0 (f32) nor 1 (f16)", dtype);
+  if ((s = set_device(ctx)) != VS_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cublasHandle_t h;
+  if ((s = get_blas(ctx, st, &h)) != VS_OK) return s;
+  return ntex_status(vsntex::forward(h, *cfg, params, tex_w, tex_h, texels, dtype, pitch, ch0, workspace, st),
+                     "vs_ntex_forward");
+}
+
+vs_status vs_ntex_backward(vs_ctx* ctx, const vs_ntex_config* cfg, const float* params, int32_t tex_w, int32_t tex_h,
+                           const float* grad_texels, int32_t pitch, int32_t ch0, float* grads, void* workspace,
+                           size_t ws_bytes, vs_stream_t stream) {
+  vs_status s = check_ntex_call(ctx, cfg, params, tex_w, tex_h, grad_texels, pitch, ch0, workspace, ws_bytes);
+  if (s != VS_OK) return s;
+  if (!grads || (uintptr_t)grads % 4) return fail(VS_ERR_INVALID_ARG, "grads NULL or misaligned");
+  if ((s = set_device(ctx)) != VS_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cublasHandle_t h;
+  if ((s = get_blas(ctx, st, &h)) != VS_OK) return s;
+  return ntex_status(vsntex::backward(h, *cfg, params, tex_w, tex_h, grad_texels, pitch, ch0, grads, workspace, st),
+                     "vs_ntex_backward");
+}
+
+vs_status vs_adam_step(vs_ctx* ctx, float* params, const float* grads, float* m, float* v, int64_t n, float lr,
+                       float beta1, float beta2, float eps, int32_t step, vs_stream_t stream) {
+  if (!ctx || !params || !grads || !m || !v) return fail(VS_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1 || step < 1) return fail(VS_ERR_INVALID_ARG, "n and step must be >= 1");
+  if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps >= 0.0f))
+    return fail(VS_ERR_INVALID_ARG, "beta1, beta2 in [0, 1) and eps >= 0 required");
+  vs_status s = set_device(ctx);
+  if (s != VS_OK) return s;
+  return ntex_status(vsntex::adam(params, grads, m, v, n, lr, beta1, beta2, eps, step,
+                                  reinterpret_cast<cudaStream_t>(stream)),
+                     "vs_adam_step");
 }
 
 vs_status vs_read_stats(void* workspace, vs_stream_t stream, int32_t reset, vs_stats* out) {

@@ -13,11 +13,12 @@ import torch
 
 from . import _abi
 from ._abi import (VS_FLAG_ALPHA_ATTEN, VS_FLAG_LOSS_L2, VS_TEX_RGBA_F32, VS_TEX_SH_F16, VS_TEX_SH_U8, check,
-                   vs_batch_item,
+                   vs_batch_item, vs_ntex_config,
                    vs_camera, vs_cost_fn, vs_shell_desc, vs_stats, vs_tuning)
 
 __all__ = ["Context", "ShellObject", "camera_struct", "workspace_size", "make_workspace",
            "render", "render_layers", "render_backward", "render_batch", "read_stats", "VSRender",
+           "NeuralTexture",
            "tuning", "set_batch_tuning", "get_batch_tuning", "tune_search", "autotune_batch",
            "VS_FLAG_ALPHA_ATTEN", "VS_FLAG_LOSS_L2", "VS_TEX_RGBA_F32", "VS_TEX_SH_F16", "VS_TEX_SH_U8",
            "baked_layout"]
@@ -279,6 +280,52 @@ def autotune_batch(ctx: Context, items, ws: torch.Tensor, bg=(0.0, 0.0, 0.0), do
     check(ctx.lib.vs_autotune_batch(ctx.handle, items.arr, items.n, bgv, int(do_backward), _ptr(ws), ws.numel(),
                                     flags, _stream(stream), repeats, ctypes.byref(best)))
     return best
+
+
+class NeuralTexture:
+    """vs_ntex_*: a hash-grid + MLP texture evaluated at texel centres, its
+    adjoint and Adam, over device tensors kept here (params, grads, Adam
+    moments, workspace).  `params` may be set from a numpy vector in the
+    vs_ntex_layout order."""
+
+    def __init__(self, ctx: Context, levels=16, features=2, log2_table=19, base_res=16, growth=1.5,
+                 hidden=64, out_ch=28, tex_w=1024, tex_h=1024, device="cuda"):
+        self.ctx = ctx
+        self.cfg = vs_ntex_config(levels, features, log2_table, base_res, float(growth), hidden, out_ch)
+        self.tex_w, self.tex_h = int(tex_w), int(tex_h)
+        off = (ctypes.c_int64 * 7)()
+        total = ctypes.c_int64()
+        check(ctx.lib.vs_ntex_layout(ctypes.byref(self.cfg), off, ctypes.byref(total)))
+        self.offsets, self.count = list(off), total.value
+        self.params = torch.zeros(self.count, dtype=torch.float32, device=device)
+        self.grads = torch.zeros_like(self.params)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step = 0
+        nb = ctypes.c_size_t()
+        check(ctx.lib.vs_ntex_workspace_size(ctypes.byref(self.cfg), self.tex_w, self.tex_h, ctypes.byref(nb)))
+        self.ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device=device)
+
+    def forward(self, texels: torch.Tensor, ch0: int = 0, stream=None):
+        """Write channels [ch0, ch0 + C) of texels [H, W, pitch] (f32 or f16)."""
+        dtype = {torch.float32: 0, torch.float16: 1}[texels.dtype]
+        assert texels.is_contiguous() and texels.shape[:2] == (self.tex_h, self.tex_w)
+        check(self.ctx.lib.vs_ntex_forward(self.ctx.handle, ctypes.byref(self.cfg), _ptr(self.params), self.tex_w,
+                                           self.tex_h, _ptr(texels), dtype, texels.shape[2], ch0, _ptr(self.ws),
+                                           self.ws.numel(), _stream(stream)))
+
+    def backward(self, grad_texels: torch.Tensor, ch0: int = 0, stream=None):
+        """Add dL/d(params) for dL/d(texels) (f32 [H, W, pitch]) into grads."""
+        assert grad_texels.dtype == torch.float32 and grad_texels.is_contiguous()
+        check(self.ctx.lib.vs_ntex_backward(self.ctx.handle, ctypes.byref(self.cfg), _ptr(self.params), self.tex_w,
+                                            self.tex_h, _ptr(grad_texels), grad_texels.shape[2], ch0,
+                                            _ptr(self.grads), _ptr(self.ws), self.ws.numel(), _stream(stream)))
+
+    def adam(self, lr: float, beta1=0.9, beta2=0.99, eps=1e-15, stream=None):
+        """One Adam step with the accumulated grads (then zero them yourself)."""
+        self.step += 1
+        check(self.ctx.lib.vs_adam_step(self.ctx.handle, _ptr(self.params), _ptr(self.grads), _ptr(self.m),
+                                        _ptr(self.v), self.count, lr, beta1, beta2, eps, self.step, _stream(stream)))
 
 
 def read_stats(ws: torch.Tensor, reset: bool = False, stream=None) -> dict:

@@ -20,6 +20,7 @@ from .scenes import (  # noqa: F401
     baked_layout,
     baked_values_to_bytes,
     baked_sh_texture,
+    ntex_init,
     Camera,
     Shell,
     Scene,

@@ -350,6 +350,23 @@ def baked_sh_texture(tex_w: int, tex_h: int, degree: int, band_shift: int, rng: 
     return buf
 
 
+def ntex_init(shapes, rng: np.random.Generator) -> np.ndarray:
+    """Initial neural-texture parameters (float32, flat in the order of
+    `shapes` = [(name, shape), ...]): hash tables U(-1e-4, 1e-4) (the hash
+    encoding's usual start), weights N(0, 2 / fan_in) (for ReLU layers),
+    biases 0."""
+    out = []
+    for name, shp in shapes:
+        n = int(np.prod(shp))
+        if name == "table":
+            out.append(rng.uniform(-1e-4, 1e-4, n))
+        elif name.startswith("W"):
+            out.append(rng.normal(0.0, math.sqrt(2.0 / shp[-1]), n))
+        else:
+            out.append(np.zeros(n))
+    return np.concatenate(out).astype(np.float32)
+
+
 # ----------------------------------------------------------------------------
 # cameras
 # ----------------------------------------------------------------------------

@@ -255,3 +255,37 @@ def test_load_shells_rejects_bad_baked_descriptors(lib, bad):
     st, out = _load(lib, [_baked_desc(**bad)])
     assert st == _abi.VS_ERR_INVALID_ARG
     assert not out.value
+
+
+# ----------------------------------------------------------------------------
+# neural texture: layout agreement with the oracle, config checks (host only)
+# ----------------------------------------------------------------------------
+
+def _ntex_cfg(**kw):
+    d = dict(levels=8, features=2, log2_table=12, base_res=4, growth=1.5, hidden=64, out_ch=28)
+    d.update(kw)
+    return _abi.vs_ntex_config(d["levels"], d["features"], d["log2_table"], d["base_res"], d["growth"],
+                               d["hidden"], d["out_ch"]), d
+
+
+@pytest.mark.parametrize("kw", [{}, dict(levels=16, log2_table=19, base_res=16), dict(features=4, hidden=8, out_ch=1)])
+def test_ntex_layout_matches_the_oracle(lib, kw):
+    from oracle import ntex
+    c, d = _ntex_cfg(**kw)
+    off = (ctypes.c_int64 * 7)()
+    total = ctypes.c_int64()
+    assert lib.vs_ntex_layout(ctypes.byref(c), off, ctypes.byref(total)) == 0
+    lay, tot = ntex.NtexConfig(**d).layout()
+    assert list(off) == [o for _, o, _ in lay] and total.value == tot
+    nb = ctypes.c_size_t()
+    assert lib.vs_ntex_workspace_size(ctypes.byref(c), 2048, 2048, ctypes.byref(nb)) == 0
+    assert nb.value >= (1 << 18) * (2 * c.levels * c.features + 4 * c.hidden + 2 * c.out_ch) * 4
+
+
+@pytest.mark.parametrize("bad", [dict(levels=0), dict(levels=17), dict(features=9), dict(log2_table=25),
+                                 dict(base_res=0), dict(growth=0.5), dict(hidden=0), dict(out_ch=300),
+                                 dict(levels=16, base_res=1000, growth=4.0)])
+def test_ntex_rejects_bad_configs(lib, bad):
+    c, _ = _ntex_cfg(**bad)
+    total = ctypes.c_int64()
+    assert lib.vs_ntex_layout(ctypes.byref(c), None, ctypes.byref(total)) == _abi.VS_ERR_INVALID_ARG

@@ -1,0 +1,144 @@
+"""The neural texture on the GPU (through the C ABI) against the FP64
+oracle: forward at texel centres, adjoint into the hash tables and MLP,
+Adam; and the whole fitting loop of Sec. 3 "Texturing Meshes" -- network ->
+grounded texels -> fused render + adjoint -> network adjoint -> Adam --
+reducing an image loss."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import ntex
+from synth import FMT_SH_F16, Scene, Shell
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vs():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2409_02482_gb300 as vs
+    return vs
+
+
+@pytest.fixture(scope="module")
+def ctx(vs):
+    return vs.Context(0)
+
+
+CFG = ntex.NtexConfig(levels=8, features=2, log2_table=12, base_res=4, growth=1.6, hidden=64, out_ch=28)
+
+
+def _params(cfg, seed):
+    p = synth.ntex_init(cfg.shapes(), np.random.default_rng(seed))
+    lay, _ = cfg.layout()
+    off, shp = lay[0][1], lay[0][2]
+    n = int(np.prod(shp))
+    # tables well away from zero so that every level matters in the check
+    p[off:off + n] = np.random.default_rng(seed + 1).normal(0, 0.5, n).astype(np.float32)
+    return p
+
+
+def _net(vs, ctx, cfg, params, W, H):
+    nt = vs.NeuralTexture(ctx, cfg.levels, cfg.features, cfg.log2_table, cfg.base_res, cfg.growth, cfg.hidden,
+                          cfg.out_ch, tex_w=W, tex_h=H)
+    nt.params.copy_(torch.from_numpy(params))
+    return nt
+
+
+@pytest.mark.parametrize("W,H", [(70, 50), (600, 500)])
+def test_ntex_forward_matches_oracle(vs, ctx, W, H):
+    params = _params(CFG, 1)
+    nt = _net(vs, ctx, CFG, params, W, H)
+    ref, _ = ntex.forward(CFG, params.astype(np.float64), W, H)
+    tex = torch.full((H, W, 32), 7.0, device="cuda")
+    nt.forward(tex, ch0=2)
+    got = tex.cpu().numpy()
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(got[..., 2:30] - ref).max() <= 1e-4 * scale
+    assert np.all(got[..., :2] == 7.0) and np.all(got[..., 30:] == 7.0)
+    tex16 = torch.zeros((H, W, 28), dtype=torch.float16, device="cuda")
+    nt.forward(tex16)
+    assert np.abs(tex16.float().cpu().numpy() - ref).max() <= 2e-3 * scale
+
+
+def test_ntex_backward_matches_oracle(vs, ctx):
+    W, H = 70, 50
+    params = _params(CFG, 2)
+    nt = _net(vs, ctx, CFG, params, W, H)
+    g = torch.randn((H, W, 32), device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    nt.backward(g, ch0=2)
+    got = nt.grads.cpu().numpy()
+    ref = ntex.backward(CFG, params.astype(np.float64), W, H, g.cpu().numpy()[..., 2:30].astype(np.float64))
+    lay, _ = CFG.layout()
+    for name, off, shp in lay:
+        n = int(np.prod(shp))
+        r, q = ref[off:off + n], got[off:off + n]
+        assert np.abs(q - r).max() <= 1e-4 * max(np.abs(r).max(), 1e-30), name
+
+
+def test_adam_matches_oracle(vs, ctx):
+    W, H = 8, 8
+    params = _params(CFG, 4)
+    nt = _net(vs, ctx, CFG, params, W, H)
+    rng = np.random.default_rng(5)
+    g = rng.normal(size=params.size).astype(np.float32)
+    p, m, v = params.astype(np.float64), np.zeros(params.size), np.zeros(params.size)
+    for step in (1, 2, 3):
+        nt.grads.copy_(torch.from_numpy(g * step))
+        nt.adam(lr=1e-2)
+        p, m, v = ntex.adam(p, (g * step).astype(np.float64), m, v, step, lr=1e-2)
+    assert np.abs(nt.params.cpu().numpy() - p).max() <= 1e-5
+    assert np.abs(nt.m.cpu().numpy() - m).max() <= 1e-5
+
+
+def test_fitting_through_the_renderer_reduces_the_loss(vs, ctx):
+    """Two SH-degree-1 shells, four views: each shell's texture is a neural
+    texture (one network, 13 channels: alpha logit + 12 SH coefficients)
+    grounded at its 64 x 64 texel centres; 60 steps of fused render + adjoint
+    against targets rendered from a random texture set, the texel gradients
+    taken back through the networks, Adam."""
+    geo = synth.concentric_icospheres([1.0, 0.85], subdiv=3)
+    rng = np.random.default_rng(6)
+    deg, tw, pitch = 1, 64, 16
+    target = Scene([Shell(p, u, t, synth.sh_texture(tw, tw, deg, rng, sigma=0.8, pitch=pitch), FMT_SH_F16, deg)
+                    for p, u, t in geo])
+    cams = [synth.look_at(e, width=96, height=96) for e in [(0.3, -3.0, 0.8), (2.5, 1.5, 0.5),
+                                                              (-2.0, 1.0, 2.0), (0.0, 2.5, -1.5)]]
+    tobj = vs.ShellObject.from_scene(ctx, target)
+    tws = vs.make_workspace(ctx, [tobj], cams[:1])
+    targets = [vs.render(ctx, tobj, c, tws)[0][..., :3].contiguous() for c in cams]
+    cfg = ntex.NtexConfig(levels=8, features=2, log2_table=12, base_res=4, growth=1.5, hidden=32, out_ch=13)
+    nets, shells = [], []
+    for i, (p, u, t) in enumerate(geo):
+        nt = _net(vs, ctx, cfg, synth.ntex_init(cfg.shapes(), np.random.default_rng(10 + i)), tw, tw)
+        tex = torch.zeros((tw, tw, pitch), dtype=torch.float16, device="cuda")
+        nets.append(nt)
+        shells.append(dict(pos=torch.from_numpy(p).cuda(), uv=torch.from_numpy(u).cuda(),
+                           tris=torch.from_numpy(t).cuda(), tex=tex, fmt=FMT_SH_F16, degree=deg))
+    obj = vs.ShellObject(ctx, shells)
+    grads = [torch.zeros((tw, tw, pitch), device="cuda") for _ in shells]
+    loss = torch.zeros(len(cams), device="cuda")
+    items = [dict(obj=obj, cam=c, out=torch.empty((96, 96, 4), device="cuda"), grad_rgb=targets[j], grads=grads,
+                  loss=loss[j:j + 1]) for j, c in enumerate(cams)]
+    bi = vs.BatchItems(items)
+    ws = vs.make_workspace(ctx, [obj] * len(cams), cams)
+    history = []
+    for step in range(60):
+        for nt, sh in zip(nets, shells):
+            nt.forward(sh["tex"])
+        for g in grads:
+            g.zero_()
+        loss.zero_()
+        vs.render_batch(ctx, bi, ws, do_backward=True, flags=vs.VS_FLAG_LOSS_L2)
+        for nt, g in zip(nets, grads):
+            nt.grads.zero_()
+            nt.backward(g)
+            nt.adam(lr=1e-2)
+        history.append(loss.sum().item())
+    assert vs.read_stats(ws)["device_status"] == 0
+    assert all(np.isfinite(history))
+    assert history[-1] < 0.5 * history[0], history[::10]
