@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-uneven", action="store_true", help="skip the uneven 32-object batch")
     p.add_argument("--no-baked", action="store_true", help="skip the baked-format forward leg")
+    p.add_argument("--no-ntex", action="store_true", help="skip the neural-texture fitting leg")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default work-unit sizes instead of autotuning them first")
     return p.parse_args()
@@ -263,6 +264,78 @@ def baked_leg(ctx, device, stream, steps, peak, autotune=True):
                         "frac": achieved / peak, "texel_bytes_per_fragment": per_frag,
                         "algorithmic_bytes_per_launch": b_alg, "d_sampled_views": sampled}}
     del ws, items, outs, obj
+    torch.cuda.empty_cache()
+    return out
+
+
+def ntex_leg(wl, device, stream, steps):
+    """Texture fitting with neural textures on the main workload (Sec. 3
+    "Texturing Meshes"): per shell two networks (opacity: 1 output; colour:
+    27 SH-2 outputs), 16-level hash grids with 2^19 rows and 2 features, two
+    64-wide ReLU layers (the supplement's sizes), evaluated at all 2048^2
+    texel centres into the FP16 texture, then the fused render + adjoint of
+    the 100 views, the networks' adjoints and Adam -- one fitting step.
+    Times each part with CUDA events; random initial parameters."""
+    import torch
+    import synth
+    import paper_2409_02482_gb300 as vs
+    ctx, obj, items, ws = wl["ctx"], wl["obj"], wl["items"], wl["ws"]
+    nets = []
+    for i, tex in enumerate(obj.textures):
+        h, w, _ = tex.shape
+        pair = []
+        for j, (ch0, c) in enumerate(((0, 1), (1, 27))):
+            nt = vs.NeuralTexture(ctx, levels=16, features=2, log2_table=19, base_res=16, growth=1.447,
+                                  hidden=64, out_ch=c, tex_w=w, tex_h=h, device=device)
+            shapes = [("table", (16, 1 << 19, 2)), ("W0", (64, 32)), ("b0", (64,)), ("W1", (64, 64)),
+                      ("b1", (64,)), ("W2", (c, 64)), ("b2", (c,))]
+            nt.params.copy_(torch.from_numpy(synth.ntex_init(shapes, np.random.default_rng(100 * i + j))))
+            pair.append((nt, ch0))
+        nets.append(pair)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    parts = np.zeros(4)
+
+    def step(record):
+        if record:
+            ev[0].record(stream)
+        for pair, tex in zip(nets, obj.textures):
+            for nt, ch0 in pair:
+                nt.forward(tex, ch0=ch0, stream=stream)
+        if record:
+            ev[1].record(stream)
+        for g in wl["grads"]:
+            g.zero_()
+        vs.render_batch(ctx, items, ws, do_backward=True, flags=vs.VS_FLAG_LOSS_L2, stream=stream)
+        if record:
+            ev[2].record(stream)
+        for pair, g in zip(nets, wl["grads"]):
+            for nt, ch0 in pair:
+                nt.grads.zero_()
+                nt.backward(g, ch0=ch0, stream=stream)
+        if record:
+            ev[3].record(stream)
+        for pair in nets:
+            for nt, _ in pair:
+                nt.adam(1e-2, stream=stream)
+        if record:
+            ev[4].record(stream)
+
+    for _ in range(2):
+        step(False)
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        step(True)
+        torch.cuda.synchronize()
+        parts += [ev[k].elapsed_time(ev[k + 1]) for k in range(4)]
+    parts /= steps
+    n_tex = sum(t.shape[0] * t.shape[1] for t in obj.textures)
+    out = {"workload": "main workload with neural textures: 7 shells x 2 networks (1 + 27 outputs), "
+                       "16 levels x 2^19 x 2 hash grids, 2 x 64 ReLU MLP, 2048^2 grounded texels",
+           "ms_per_step": float(parts.sum()), "ms_network_forward": float(parts[0]),
+           "ms_render_fwd_bwd": float(parts[1]), "ms_network_backward": float(parts[2]),
+           "ms_adam": float(parts[3]), "texels_per_step": n_tex,
+           "network_evaluations_per_s": 2 * n_tex / (parts[0] * 1e-3)}
+    del nets
     torch.cuda.empty_cache()
     return out
 
@@ -480,6 +553,8 @@ def run_ours(args):
     if not args.no_uneven and rank == 0:
         res["uneven_batch"] = uneven_batch(ctx, device, stream, max(3, args.steps // 10),
                                            autotune=not args.no_autotune)
+    if not args.no_ntex and rank == 0:
+        res["neural_texture_fitting"] = ntex_leg(wl, device, stream, max(3, args.steps // 10))
     if not args.no_baked and rank == 0:
         res["baked_forward"] = baked_leg(ctx, device, stream, max(5, args.steps // 3), peaks()[0],
                                          autotune=not args.no_autotune)

@@ -82,21 +82,62 @@ __global__ void __launch_bounds__(kThreads) k_encode(Enc e, const float* table, 
   for (int f = 0; f < e.F; ++f) x[f] = acc[f];
 }
 
-// dtable[l, row, f] += w dX[i, l F + f]  (the encoding's adjoint).
+// dtable[l, row, f] += w dX[i, l F + f]  (the encoding's adjoint), level
+// blockIdx.y.  Texels are row-major, so a segment of kSeg consecutive texels
+// touches only a band of two or three vertex rows of a dense level: the
+// block accumulates the segment's contributions to that band in shared
+// memory and adds the band to the table once (a coarse level would
+// otherwise receive millions of float atomics on a few hundred rows).
+// Hashed levels (and bands too large for the buffer) scatter straight to
+// the table, where rows are spread out.
+constexpr int kSmemAcc = 12288;   // floats of band buffer (48 KB)
+constexpr int kSeg = 4096;        // texels per segment
+
+__device__ __forceinline__ int cell_row(const Enc& e, int l, int ty, int H) {
+  return (int)floorf((ty + 0.5f) / (float)H * (float)e.res[l]);
+}
+
 __global__ void __launch_bounds__(kThreads) k_encode_bwd(Enc e, const float* dX, int W, int H, int n0, int count,
                                                           float* dtable) {
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= (long long)count * e.L) return;
-  const int i = (int)(id / e.L), l = (int)(id - (long long)i * e.L);
-  const int n = n0 + i, tx = n % W, ty = n / W;
+  extern __shared__ float acc[];
+  const int l = blockIdx.y;
+  const int n = e.res[l];
+  const bool dense = (long long)(n + 1) * (n + 1) <= (1ll << e.logT);
   const size_t lt = (size_t)l << e.logT;
-  const float* d = dX + (size_t)i * e.L * e.F + l * e.F;
-  for (int c = 0; c < 4; ++c) {
-    uint32_t row;
-    float w;
-    corner(e, l, tx, ty, W, H, c, row, w);
-    float* t = dtable + (lt + row) * e.F;
-    for (int f = 0; f < e.F; ++f) atomicAdd(t + f, w * d[f]);
+  const int nseg = (count + kSeg - 1) / kSeg;
+  for (int seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
+    const int i0 = seg * kSeg, i1 = min(count, i0 + kSeg);
+    int vb = 0, band = 0;
+    if (dense) {
+      const int cy0 = cell_row(e, l, (n0 + i0) / W, H), cy1 = cell_row(e, l, (n0 + i1 - 1) / W, H);
+      vb = cy0 * (n + 1);
+      band = (cy1 - cy0 + 2) * (n + 1);
+    }
+    const bool local = dense && band * e.F <= kSmemAcc;   // block-uniform
+    if (local) {
+      for (int r = threadIdx.x; r < band * e.F; r += blockDim.x) acc[r] = 0.0f;
+      __syncthreads();
+    }
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const int t = n0 + i, tx = t % W, ty = t / W;
+      const float* d = dX + (size_t)i * e.L * e.F + l * e.F;
+      for (int c = 0; c < 4; ++c) {
+        uint32_t row;
+        float w;
+        corner(e, l, tx, ty, W, H, c, row, w);
+        for (int f = 0; f < e.F; ++f) {
+          if (local) atomicAdd(acc + ((int)row - vb) * e.F + f, w * d[f]);
+          else atomicAdd(dtable + (lt + row) * e.F + f, w * d[f]);
+        }
+      }
+    }
+    if (local) {
+      __syncthreads();
+      float* t = dtable + (lt + vb) * e.F;
+      for (int r = threadIdx.x; r < band * e.F; r += blockDim.x)
+        if (acc[r] != 0.0f) atomicAdd(t + r, acc[r]);
+      __syncthreads();   // the buffer is reused by the next segment
+    }
   }
 }
 
@@ -318,7 +359,11 @@ int backward(cublasHandle_t h, const vs_ntex_config& c, const float* params, int
     VS_TRY_BLAS(gemm_atb_acc(h, rows, Hd, LF, w.dH1, w.X, g[1]));
     k_colsum<<<dim3(64, Hd), kThreads, 0, st>>>(w.dH1, rows, Hd, g[2]);
     VS_TRY_BLAS(gemm_ab(h, rows, LF, Hd, w.dH1, P.W0, w.dX));
-    k_encode_bwd<<<blocks_for((long long)rows * c.levels), kThreads, 0, st>>>(e, w.dX, W, H, n0, rows, g[0]);
+    {
+      const unsigned nseg = (unsigned)((rows + kSeg - 1) / kSeg);
+      const unsigned gx = nseg < 256u ? nseg : 256u;
+      k_encode_bwd<<<dim3(gx, c.levels), kThreads, kSmemAcc * sizeof(float), st>>>(e, w.dX, W, H, n0, rows, g[0]);
+    }
     VS_TRY_CUDA(cudaGetLastError());
   }
   return 0;
