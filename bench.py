@@ -268,7 +268,7 @@ def baked_leg(ctx, device, stream, steps, peak, autotune=True):
     return out
 
 
-def ntex_leg(wl, device, stream, steps):
+def ntex_leg(wl, device, stream, steps, tensor_cores=False):
     """Texture fitting with neural textures on the main workload (Sec. 3
     "Texturing Meshes"): per shell two networks (opacity: 1 output; colour:
     27 SH-2 outputs), 16-level hash grids with 2^19 rows and 2 features, two
@@ -286,7 +286,8 @@ def ntex_leg(wl, device, stream, steps):
         pair = []
         for j, (ch0, c) in enumerate(((0, 1), (1, 27))):
             nt = vs.NeuralTexture(ctx, levels=16, features=2, log2_table=19, base_res=16, growth=1.447,
-                                  hidden=64, out_ch=c, tex_w=w, tex_h=h, device=device)
+                                  hidden=64, out_ch=c, tex_w=w, tex_h=h, device=device,
+                                  tensor_cores=tensor_cores)
             shapes = [("table", (16, 1 << 19, 2)), ("W0", (64, 32)), ("b0", (64,)), ("W1", (64, 64)),
                       ("b1", (64,)), ("W2", (c, 64)), ("b2", (c,))]
             nt.params.copy_(torch.from_numpy(synth.ntex_init(shapes, np.random.default_rng(100 * i + j))))
@@ -331,6 +332,7 @@ def ntex_leg(wl, device, stream, steps):
     n_tex = sum(t.shape[0] * t.shape[1] for t in obj.textures)
     out = {"workload": "main workload with neural textures: 7 shells x 2 networks (1 + 27 outputs), "
                        "16 levels x 2^19 x 2 hash grids, 2 x 64 ReLU MLP, 2048^2 grounded texels",
+           "layers": "TF32 tensor cores" if tensor_cores else "FP32",
            "ms_per_step": float(parts.sum()), "ms_network_forward": float(parts[0]),
            "ms_render_fwd_bwd": float(parts[1]), "ms_network_backward": float(parts[2]),
            "ms_adam": float(parts[3]), "texels_per_step": n_tex,
@@ -358,13 +360,15 @@ def timed(fn, steps, warmup, stream, barrier):
 
 
 def kernel_source_hash():
-    """sha256 over the CUDA sources; a stored ncu traffic figure is used only
-    while it matches (the kernels have not changed since the capture)."""
+    """sha256 over the renderer's CUDA sources (kernels and the host code that
+    shapes their launches; the neural-texture files take no part in them); a
+    stored ncu traffic figure is used only while it matches (the kernels have
+    not changed since the capture)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2409_02482_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name.endswith((".cu", ".cuh", ".h")) and not name.startswith("vs_ntex"):
             h.update(name.encode())
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(f.read())
@@ -555,6 +559,8 @@ def run_ours(args):
                                            autotune=not args.no_autotune)
     if not args.no_ntex and rank == 0:
         res["neural_texture_fitting"] = ntex_leg(wl, device, stream, max(3, args.steps // 10))
+        res["neural_texture_fitting_tf32"] = ntex_leg(wl, device, stream, max(3, args.steps // 10),
+                                                      tensor_cores=True)
     if not args.no_baked and rank == 0:
         res["baked_forward"] = baked_leg(ctx, device, stream, max(5, args.steps // 3), peaks()[0],
                                          autotune=not args.no_autotune)

@@ -366,6 +366,9 @@ typedef struct {
   float growth;          /* b in [1, 4]; N_l <= 2^20                       */
   int32_t hidden;        /* H: 1 .. 512                                    */
   int32_t out_ch;        /* C: 1 .. 256                                    */
+  int32_t tensor_cores;  /* 0: FP32 layers (exact FP32 GEMMs, the default);
+                            1: the layers on the tensor cores in TF32 (10-bit
+                            mantissa inputs, FP32 accumulation)            */
 } vs_ntex_config;
 
 /* Offsets (in floats) of the seven parameter blocks and the total count.
@@ -378,9 +381,10 @@ vs_status vs_ntex_workspace_size(const vs_ntex_config* cfg, int32_t tex_w, int32
 
 /* Evaluates the network at every texel centre and writes channels
  * [ch0, ch0 + C) of texels [tex_h, tex_w, pitch] (dtype 0 = float32,
- * 1 = float16, the renderer's SH storage).  FP32 arithmetic (the layers as
- * FP32 GEMMs).  Errors: VS_ERR_INVALID_ARG (config, sizes, ch0 + C > pitch,
- * NULL), VS_ERR_WORKSPACE, VS_ERR_CUDA. */
+ * 1 = float16, the renderer's SH storage).  FP32 arithmetic: the layers as
+ * FP32 GEMMs, or as TF32 tensor-core GEMMs when cfg->tensor_cores = 1.
+ * Errors: VS_ERR_INVALID_ARG (config, sizes, ch0 + C > pitch, NULL),
+ * VS_ERR_WORKSPACE, VS_ERR_CUDA. */
 vs_status vs_ntex_forward(vs_ctx* ctx, const vs_ntex_config* cfg, const float* params, int32_t tex_w, int32_t tex_h,
                           void* texels, int32_t dtype, int32_t pitch, int32_t ch0, void* workspace, size_t ws_bytes,
                           vs_stream_t stream);

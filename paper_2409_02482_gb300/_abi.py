@@ -72,7 +72,7 @@ vs_cost_fn = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.POINTER(vs_tuning), ctypes
 class vs_ntex_config(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int32), ("features", ctypes.c_int32), ("log2_table", ctypes.c_int32),
                 ("base_res", ctypes.c_int32), ("growth", ctypes.c_float), ("hidden", ctypes.c_int32),
-                ("out_ch", ctypes.c_int32)]
+                ("out_ch", ctypes.c_int32), ("tensor_cores", ctypes.c_int32)]
 
 
 class vs_stats(ctypes.Structure):

@@ -866,6 +866,7 @@ vs_status check_ntex(const vs_ntex_config* c) {
     return fail(VS_ERR_INVALID_ARG, "finest level resolution above 2^20");
   if (c->hidden < 1 || c->hidden > 512) return fail(VS_ERR_INVALID_ARG, "hidden %d out of [1, 512]", c->hidden);
   if (c->out_ch < 1 || c->out_ch > 256) return fail(VS_ERR_INVALID_ARG, "out_ch %d out of [1, 256]", c->out_ch);
+  if (c->tensor_cores != 0 && c->tensor_cores != 1) return fail(VS_ERR_INVALID_ARG, "tensor_cores must be 0 or 1");
   return VS_OK;
 }
 
@@ -886,16 +887,19 @@ vs_status check_ntex_call(vs_ctx* ctx, const vs_ntex_config* cfg, const void* pa
   return VS_OK;
 }
 
-vs_status get_blas(vs_ctx* ctx, cudaStream_t st, cublasHandle_t* h) {
-  std::lock_guard<std::mutex> g(ctx->blas_mu);
+// The context's cuBLAS handle, on `st`, in the math mode the config asks
+// for: exact FP32 (no reduced-precision tensor-core paths) or TF32 tensor
+// cores.  Holds the handle's mutex until the caller's lock goes out of scope.
+vs_status get_blas(vs_ctx* ctx, cudaStream_t st, int tensor_cores, cublasHandle_t* h) {
   if (!ctx->blas) {
     if (cublasCreate(&ctx->blas) != CUBLAS_STATUS_SUCCESS) {
       ctx->blas = nullptr;
       return fail(VS_ERR_CUDA, "cublasCreate failed");
     }
-    // FP32 arithmetic in the GEMMs: no reduced-precision tensor-core paths
-    cublasSetMathMode(ctx->blas, CUBLAS_PEDANTIC_MATH);
   }
+  if (cublasSetMathMode(ctx->blas, tensor_cores ? CUBLAS_TF32_TENSOR_OP_MATH : CUBLAS_PEDANTIC_MATH) !=
+      CUBLAS_STATUS_SUCCESS)
+    return fail(VS_ERR_CUDA, "cublasSetMathMode failed");
   if (cublasSetStream(ctx->blas, st) != CUBLAS_STATUS_SUCCESS) return fail(VS_ERR_CUDA, "cublasSetStream failed");
   *h = ctx->blas;
   return VS_OK;
@@ -944,8 +948,9 @@ vs_status vs_ntex_forward(vs_ctx* ctx, const vs_ntex_config* cfg, const float* p
   if (dtype != 0 && dtype != 1) return fail(VS_ERR_INVALID_ARG, "dtype %d is neither 0 (f32) nor 1 (f16)", dtype);
   if ((s = set_device(ctx)) != VS_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(ctx->blas_mu);   // the handle's stream and mode are per call
   cublasHandle_t h;
-  if ((s = get_blas(ctx, st, &h)) != VS_OK) return s;
+  if ((s = get_blas(ctx, st, cfg->tensor_cores, &h)) != VS_OK) return s;
   return ntex_status(vsntex::forward(h, *cfg, params, tex_w, tex_h, texels, dtype, pitch, ch0, workspace, st),
                      "vs_ntex_forward");
 }
@@ -958,8 +963,9 @@ vs_status vs_ntex_backward(vs_ctx* ctx, const vs_ntex_config* cfg, const float* 
   if (!grads || (uintptr_t)grads % 4) return fail(VS_ERR_INVALID_ARG, "grads NULL or misaligned");
   if ((s = set_device(ctx)) != VS_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(ctx->blas_mu);
   cublasHandle_t h;
-  if ((s = get_blas(ctx, st, &h)) != VS_OK) return s;
+  if ((s = get_blas(ctx, st, cfg->tensor_cores, &h)) != VS_OK) return s;
   return ntex_status(vsntex::backward(h, *cfg, params, tex_w, tex_h, grad_texels, pitch, ch0, grads, workspace, st),
                      "vs_ntex_backward");
 }

@@ -289,9 +289,10 @@ class NeuralTexture:
     vs_ntex_layout order."""
 
     def __init__(self, ctx: Context, levels=16, features=2, log2_table=19, base_res=16, growth=1.5,
-                 hidden=64, out_ch=28, tex_w=1024, tex_h=1024, device="cuda"):
+                 hidden=64, out_ch=28, tex_w=1024, tex_h=1024, device="cuda", tensor_cores=False):
         self.ctx = ctx
-        self.cfg = vs_ntex_config(levels, features, log2_table, base_res, float(growth), hidden, out_ch)
+        self.cfg = vs_ntex_config(levels, features, log2_table, base_res, float(growth), hidden, out_ch,
+                                  int(tensor_cores))
         self.tex_w, self.tex_h = int(tex_w), int(tex_h)
         off = (ctypes.c_int64 * 7)()
         total = ctypes.c_int64()

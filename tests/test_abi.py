@@ -265,7 +265,7 @@ def _ntex_cfg(**kw):
     d = dict(levels=8, features=2, log2_table=12, base_res=4, growth=1.5, hidden=64, out_ch=28)
     d.update(kw)
     return _abi.vs_ntex_config(d["levels"], d["features"], d["log2_table"], d["base_res"], d["growth"],
-                               d["hidden"], d["out_ch"]), d
+                               d["hidden"], d["out_ch"], d.pop("tensor_cores", 0)), d
 
 
 @pytest.mark.parametrize("kw", [{}, dict(levels=16, log2_table=19, base_res=16), dict(features=4, hidden=8, out_ch=1)])
@@ -284,7 +284,7 @@ def test_ntex_layout_matches_the_oracle(lib, kw):
 
 @pytest.mark.parametrize("bad", [dict(levels=0), dict(levels=17), dict(features=9), dict(log2_table=25),
                                  dict(base_res=0), dict(growth=0.5), dict(hidden=0), dict(out_ch=300),
-                                 dict(levels=16, base_res=1000, growth=4.0)])
+                                 dict(levels=16, base_res=1000, growth=4.0), dict(tensor_cores=2)])
 def test_ntex_rejects_bad_configs(lib, bad):
     c, _ = _ntex_cfg(**bad)
     total = ctypes.c_int64()
