@@ -228,6 +228,11 @@ bool needs_clip(const vs_object& o, const vs_camera& c) {
 // Fills the plan; with ws == nullptr only sizes are computed.
 vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool clear_vis, uint32_t flags,
                     char* ws, Plan& P, UnitShape shape = UnitShape()) {
+  P.full = false;
+  for (int j = 0; j < n; ++j) P.full = P.full || needs_clip(*req[j].obj, *req[j].cam) || req[j].layers;
+  // triangle records for the fused adjoint; reserved whatever kernels run,
+  // so that the size does not depend on bounds read on a later call
+  const bool records = clear_vis && do_bwd;
   const int raster_per_unit = 32 * shape.raster_rounds;
   const int shade_per_unit = 32 * shape.shade_rounds;
   size_t off = sizeof(WsHeader);
@@ -289,6 +294,7 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
       const int esz = d.format == VS_TEX_RGBA_F32 ? 4 : 2;
       const uint64_t tex_align = (uint64_t)(uintptr_t)d.texels | (uint64_t)d.texel_pitch * esz;
       s.vec = d.format == VS_TEX_RGBA_F32 ? (gcd_pow2(tex_align, 16) >= 16 ? 4 : 1) : gcd_pow2(tex_align, 16) / 2;
+      s.wide = gcd_pow2(tex_align, 32) >= 32;
       if (s.grad) {
         const uint64_t ga = (uint64_t)(uintptr_t)s.grad | (uint64_t)d.texel_pitch * 4;
         s.gvec = gcd_pow2(ga, 16) / 4;
@@ -298,6 +304,8 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
       }
       s.vsetup = reinterpret_cast<int4*>(ws ? ws + off : nullptr);
       off = align256(off + sizeof(int4) * (size_t)d.num_verts);
+      s.trec = (records && ws && !P.full) ? reinterpret_cast<int4*>(ws + off) : nullptr;
+      if (records) off = align256(off + 4 * sizeof(int4) * (size_t)d.num_tris);
       it.setup_pre[i + 1] = it.setup_pre[i] + (d.num_verts + kSetupPerUnit - 1) / kSetupPerUnit;
       it.raster_pre[i + 1] = it.raster_pre[i] + (d.num_tris + raster_per_unit - 1) / raster_per_unit;
     }
@@ -312,18 +320,18 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
   }
   P.total = align256(off);
   // texel class: one compiled format when every shell shares it with
-  // 16-byte-aligned texels (and, for the adjoint, gradients)
+  // 16-byte-aligned texels (and, for the adjoint, gradients); SH of degree
+  // >= 1 also with 32-byte-aligned texels (256-bit loads)
   int tc = -1;
   for (const DShell& sh : P.shells) {
     int c = TC_ANY;
     if (sh.fmt == VS_TEX_RGBA_F32 && sh.vec == 4 && (!do_bwd || sh.gvec == 4)) c = TC_RGBA;
-    else if (sh.fmt == VS_TEX_SH_F16 && sh.vec == 8 && (!do_bwd || sh.gvec == 4)) c = TC_SH0 + sh.degree;
+    else if (sh.fmt == VS_TEX_SH_F16 && sh.vec == 8 && (!do_bwd || sh.gvec == 4) && (sh.degree == 0 || sh.wide))
+      c = TC_SH0 + sh.degree;
     else if (sh.fmt == VS_TEX_SH_U8) c = TC_U80 + sh.degree;
     tc = (tc < 0 || tc == c) ? c : TC_ANY;
   }
   P.tc = tc < 0 ? TC_ANY : tc;
-  P.full = false;
-  for (int j = 0; j < n; ++j) P.full = P.full || needs_clip(*req[j].obj, *req[j].cam) || req[j].layers;
   if (P.full) P.tc = TC_ANY;   // the full kernels exist for the generic class
   // skewed stages: stage s = SETUP(s), RASTER(s-1), SHADE(s-2)
   long long g = 0;

@@ -33,11 +33,30 @@ constexpr int kMaxShells = VS_MAX_SHELLS;
 constexpr int kTriBits = 27;           // triangle index bits in a packed fragment
 constexpr int kMaxTris = 1 << kTriBits;
 
+// Texel classes: a kernel compiled for TC_ANY decides the format per shell at
+// run time; the others serve batches whose shells all share one format with
+// 16-byte-aligned texels (and gradients); SH classes of degree >= 1 also want
+// 32-byte-aligned texels for their 256-bit loads.
+enum : int { TC_ANY = 0, TC_RGBA = 1, TC_SH0 = 2, TC_U80 = 6 };   // TC_SH0 / TC_U80 + degree
+constexpr int kNumTc = TC_U80 + 4;
+
+// SH basis values per pixel that an adjoint shading warp keeps for the
+// round's fragments (compiled SH classes of degree 1-3: evaluated once per
+// pixel instead of once per fragment in the fetch, and read again by the
+// cooperative scatter), else 0.  The forward kernels evaluate it per
+// fragment: measured faster there, the larger slice costing more L1 than the
+// evaluation.
+__host__ __device__ constexpr int pixel_basis(int tc, bool bwd) {
+  return (bwd && tc >= TC_SH0 + 1 && tc <= TC_SH0 + 3) ? (tc - TC_SH0 + 1) * (tc - TC_SH0 + 1) : 0;
+}
+
 // Dynamic shared memory of a shading warp for up to K shells: a fragment
 // list of frag_cap(K, bwd) entries -- [frag float4][entry u32][alpha_w
 // float][lane|shell u16] and, for the adjoint only, [fractions float2][T
 // float] -- and, when the list is shorter than a round's worst case (32 K),
-// the round's hit table (32 K ints) in front of it (carved in shade_round).
+// the round's hit table (32 K ints) in front of it, and behind it, for the
+// adjoint, the SH basis of the round's 32 pixels (pixel_basis values each;
+// carved in shade_round).
 // The forward list holds the worst case (one pass per round).  The adjoint
 // list is capped at kFragCap: a round whose fragments do not fit runs in
 // several passes, and the smaller slice leaves more of the SM's unified
@@ -50,21 +69,19 @@ static_assert(kFragCap % 32 == 0, "fragment list in whole 32-wide rounds");
 __host__ __device__ constexpr int frag_cap(int K, bool bwd) {
   return (bwd && kFragCap < 32 * K) ? kFragCap : 32 * K;
 }
-__host__ __device__ constexpr size_t shade_warp_bytes(int K, bool bwd) {
-  return ((frag_cap(K, bwd) < 32 * K ? 128 * (size_t)K : 0) + (bwd ? 38 : 26) * (size_t)frag_cap(K, bwd) + 15) &
+__host__ __device__ constexpr size_t shade_warp_bytes(int K, bool bwd, int tc) {
+  return ((frag_cap(K, bwd) < 32 * K ? 128 * (size_t)K : 0) + (bwd ? 38 : 26) * (size_t)frag_cap(K, bwd) +
+          128 * (size_t)pixel_basis(tc, bwd) + 15) &
          ~(size_t)15;
 }
 constexpr size_t kRasterWarpBytes = 32 * (64 + 8 + 4);   // TriS, TriPos, start per triangle
-__host__ __device__ constexpr size_t warp_slice_bytes(int K, bool bwd) {
-  return shade_warp_bytes(K, bwd) > kRasterWarpBytes ? shade_warp_bytes(K, bwd) : kRasterWarpBytes;
+__host__ __device__ constexpr size_t warp_slice_bytes(int K, bool bwd, int tc) {
+  return shade_warp_bytes(K, bwd, tc) > kRasterWarpBytes ? shade_warp_bytes(K, bwd, tc) : kRasterWarpBytes;
 }
-__host__ __device__ constexpr size_t block_smem_bytes(int K, bool bwd) { return warp_slice_bytes(K, bwd) * kWarps; }
+__host__ __device__ constexpr size_t block_smem_bytes(int K, bool bwd, int tc) {
+  return warp_slice_bytes(K, bwd, tc) * kWarps;
+}
 
-// Texel classes: a kernel compiled for TC_ANY decides the format per shell at
-// run time; the others serve batches whose shells all share one format with
-// 16-byte-aligned texels (and gradients).
-enum : int { TC_ANY = 0, TC_RGBA = 1, TC_SH0 = 2, TC_U80 = 6 };   // TC_SH0 / TC_U80 + degree
-constexpr int kNumTc = TC_U80 + 4;
 
 // Phases of one item.  Large triangles are rasterized by the whole block
 // inside the raster unit that met them.
@@ -92,7 +109,8 @@ struct alignas(16) DShell {
   int32_t fmt, degree, pitch;
   int32_t vec;                 // texel load width in values (1, 2, 4, 8)
   int32_t gvec;                // gradient atomic width in floats (1, 2, 4)
-  int32_t pad0, pad1, pad2;
+  int32_t wide;                // texels 32-byte aligned (base and pitch): 256-bit loads
+  int4* trec;                  // [nt][4] this view's triangle records for shading (workspace), or null
   // VS_TEX_SH_U8: byte offset of band l in tex, resolution shift per band,
   // decode value = vmin + vscale * q
   long long boff[4];
@@ -633,7 +651,18 @@ __device__ __forceinline__ float alpha_atten(const float* pos, const int idx[3],
 // ----------------------------------------------------------------------------
 template <int VEC>
 __device__ __forceinline__ void load_halves(const __half* p, float* out) {
-  if constexpr (VEC == 8) {
+  if constexpr (VEC == 16) {   // one 256-bit load (32-byte aligned)
+    unsigned r[8];
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "l"(p));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&r[i]));
+      out[2 * i] = f.x;
+      out[2 * i + 1] = f.y;
+    }
+  } else if constexpr (VEC == 8) {
     const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
     const __half2* h = reinterpret_cast<const __half2*>(&r);
 #pragma unroll

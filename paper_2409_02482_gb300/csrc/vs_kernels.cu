@@ -72,7 +72,7 @@ cudaError_t plain_forward(const TableRef& tb, const int units[4], int tc, bool f
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !units[2]) return e;
-  return tc_ops(tc).shade(tb, false, full, units[2], vsd::block_smem_bytes(tb.kmax, false), st);
+  return tc_ops(tc).shade(tb, false, full, units[2], vsd::block_smem_bytes(tb.kmax, false, tc), st);
 }
 
 cudaError_t plain_backward(const TableRef& tb, const int units[4], int tc, bool full, cudaStream_t st) {
@@ -80,22 +80,22 @@ cudaError_t plain_backward(const TableRef& tb, const int units[4], int tc, bool 
   if (units[0]) vsd::k_setup<<<(units[0] + W - 1) / W, vsd::kThreads, 0, st>>>(tb, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !units[2]) return e;
-  return tc_ops(tc).shade(tb, true, full, units[2], vsd::block_smem_bytes(tb.kmax, true), st);
+  return tc_ops(tc).shade(tb, true, full, units[2], vsd::block_smem_bytes(tb.kmax, true, tc), st);
 }
 
 cudaError_t persistent(const TableRef& tb, bool bwd, int tc, bool full, int grid, long long spin_limit,
                        cudaStream_t st) {
-  return tc_ops(tc).persistent(tb, bwd, full, grid, spin_limit, vsd::block_smem_bytes(tb.kmax, bwd), st);
+  return tc_ops(tc).persistent(tb, bwd, full, grid, spin_limit, vsd::block_smem_bytes(tb.kmax, bwd, tc), st);
 }
 
 cudaError_t persistent_occupancy(bool bwd, int tc, bool full, int kmax, int* blocks_per_sm) {
-  return tc_ops(tc).occupancy(bwd, full, vsd::block_smem_bytes(kmax, bwd), blocks_per_sm);
+  return tc_ops(tc).occupancy(bwd, full, vsd::block_smem_bytes(kmax, bwd, tc), blocks_per_sm);
 }
 
 cudaError_t configure_kernels() {
-  const int most_f = (int)vsd::block_smem_bytes(vsd::kMaxShells, false);
-  const int most_b = (int)vsd::block_smem_bytes(vsd::kMaxShells, true);
   for (int tc = 0; tc < vsd::kNumTc; ++tc) {
+    const int most_f = (int)vsd::block_smem_bytes(vsd::kMaxShells, false, tc);
+    const int most_b = (int)vsd::block_smem_bytes(vsd::kMaxShells, true, tc);
     cudaError_t e = tc_ops(tc).configure(most_f, most_b);
     if (e != cudaSuccess) return e;
   }

@@ -78,6 +78,20 @@ __device__ __forceinline__ int load_tri(const DShell& s, const DCam& c, int t, T
   return make_tri(__ldcg(s.vsetup + idx[0]), __ldcg(s.vsetup + idx[1]), __ldcg(s.vsetup + idx[2]), c.W, c.H, T);
 }
 
+// Shading record of a triangle the raster accepted, for this view: snapped
+// positions, 1/w and UVs of its vertices in one 64-byte entry, so that the
+// adjoint's shading reaches a fragment's geometry with one dependent load
+// instead of two (indices, then vertices).  Bit copies: shading computes the
+// same values as from the vertex arrays.
+__device__ __forceinline__ void store_tri_rec(const DShell& s, int t, const Tri& T, const int idx[3]) {
+  const float2 a = __ldg(s.uv + idx[0]), b = __ldg(s.uv + idx[1]), c = __ldg(s.uv + idx[2]);
+  int4* rp = s.trec + 4 * (size_t)t;
+  rp[0] = make_int4(T.X[0], T.Y[0], T.X[1], T.Y[1]);
+  rp[1] = make_int4(T.X[2], T.Y[2], __float_as_int(T.iw[0]), __float_as_int(T.iw[1]));
+  rp[2] = make_int4(__float_as_int(T.iw[2]), __float_as_int(a.x), __float_as_int(a.y), __float_as_int(b.x));
+  rp[3] = make_int4(__float_as_int(b.y), __float_as_int(c.x), __float_as_int(c.y), 0);
+}
+
 template <bool HINT>
 __device__ __forceinline__ void raster_pixel(const Tri& T, int t, int x, int y, int W, unsigned long long* vis) {
   long long e[3];
@@ -173,6 +187,9 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
       front = 1;
       const int bw = T.xhi - T.xlo + 1, bh = T.yhi - T.ylo + 1;
       if (bw > 0 && bh > 0) {
+        if constexpr (HINT && !FULL) {   // the fused adjoint's raster
+          if (s.trec) store_tri_rec(s, t, T, idx);   // every fragment of t comes from this raster
+        }
         if (bw * bh <= kSmallMaxPixels) {
           npx = bw * bh;
           const int ox = 256 * T.xlo + 128, oy = 256 * T.ylo + 128;
@@ -330,6 +347,28 @@ __device__ __forceinline__ int load_tri_shade(const DShell& s, int t, Tri& T, in
   return a2 < 0 ? 0 : 1;
 }
 
+// The same from the triangle's record (written by this item's raster, which
+// produced every hit that refers to it).
+__device__ __forceinline__ int load_tri_rec(const DShell& s, int t, Tri& T, float2 uv[3]) {
+  const int4* rp = s.trec + 4 * (size_t)t;
+  const int4 a = __ldcg(rp), b = __ldcg(rp + 1), c = __ldcg(rp + 2), d = __ldcg(rp + 3);
+  T.X[0] = a.x;
+  T.Y[0] = a.y;
+  T.X[1] = a.z;
+  T.Y[1] = a.w;
+  T.X[2] = b.x;
+  T.Y[2] = b.y;
+  T.iw[0] = __int_as_float(b.z);
+  T.iw[1] = __int_as_float(b.w);
+  T.iw[2] = __int_as_float(c.x);
+  uv[0] = make_float2(__int_as_float(c.y), __int_as_float(c.z));
+  uv[1] = make_float2(__int_as_float(c.w), __int_as_float(d.x));
+  uv[2] = make_float2(__int_as_float(d.y), __int_as_float(d.z));
+  const long long a2 = (long long)(T.X[1] - T.X[0]) * (T.Y[2] - T.Y[0]) -
+                       (long long)(T.X[2] - T.X[0]) * (T.Y[1] - T.Y[0]);
+  return a2 < 0 ? 0 : 1;
+}
+
 // Shading a fragment of a triangle clipped at the near plane: the part used
 // for the pixel (the only part, or of two the second if it covers the pixel
 // under the fill rule, else the first) and its per-vertex UVs.  Rare: kept
@@ -363,6 +402,25 @@ __device__ __forceinline__ Frag fetch_sh(const DShell& s, const Footprint& f, co
   return decode_sh<DEG>(val, Y);
 }
 
+// The same with the basis already evaluated (sY: the pixel's NB values).
+template <int DEG, int VEC>
+__device__ __forceinline__ Frag fetch_sh_basis(const DShell& s, const Footprint& f, const float* sY) {
+  constexpr int NB = (DEG + 1) * (DEG + 1), NCH = 1 + 3 * NB;
+  float Y[16];
+#pragma unroll
+  for (int m = 0; m < NB; ++m) Y[m] = sY[m];
+  float val[NCH];
+  bilinear_f16<NCH, VEC>(reinterpret_cast<const __half*>(s.tex), s.tw, s.pitch, f, val);
+  return decode_sh<DEG>(val, Y);
+}
+
+// Texel load width of the compiled SH classes: 256-bit loads from degree 1
+// (texels of 16 or more channels), 128-bit for degree 0.
+template <int TC>
+__host__ __device__ constexpr int sh_vec() {
+  return TC == TC_SH0 ? 8 : 16;
+}
+
 template <int DEG>
 __device__ __forceinline__ Frag fetch_baked_v(const DShell& s, int ix, float fx, int iy, float fy, const float3 v) {
   float Y[16];
@@ -383,7 +441,7 @@ __device__ __forceinline__ Frag fetch_frag(const DShell& s, const Footprint& f, 
   } else if constexpr (TC >= TC_U80) {
     return fetch_baked_v<TC - TC_U80>(s, ix, fx, iy, fy, v);
   } else if constexpr (TC >= TC_SH0) {
-    return fetch_sh<TC - TC_SH0, 8>(s, f, v);
+    return fetch_sh<TC - TC_SH0, sh_vec<TC>()>(s, f, v);
   }
   if (s.fmt == VS_TEX_SH_U8) {
     switch (s.degree) {
@@ -600,10 +658,15 @@ static __device__ __forceinline__ void shade_clipped(const DItem& it, const DShe
 //     B_k = bg . g): dL/dc_i = T_i alpha_i g, dL/dalpha_i = T_i (c_i . g -
 //     B_{i+1}), taken through alpha_w and the sigmoids to the texel-value
 //     space in place;
-//  4. (adjoint) the warp scatters dL/d(texel) 32 fragments at a time from
-//     the stored footprints -- no global loads, only reductions.
+//  4. (adjoint) the warp scatters dL/d(texel) from the stored footprints --
+//     no global loads, only reductions.  SH classes of degree 1-3 scatter
+//     cooperatively: each lane owns one 16-byte chunk of one tap's texel, so
+//     one reduction instruction writes whole contiguous texel rows of a
+//     fragment (4 taps x up to 8 chunks); the other classes give each lane
+//     a fragment.
 // FROM_HITS: hits come from the public int32 buffer (standalone backward)
-// instead of the visibility words.
+// instead of the visibility words.  The fused adjoint (!FROM_HITS, !FULL)
+// reads each fragment's geometry from the raster's triangle records.
 //
 // Shared memory of the warp (shade_warp_bytes), C = frag_cap(K, BWD):
 //   hit  int    [32 K]  triangle per (shell, lane) of the round (1); own
@@ -616,6 +679,8 @@ static __device__ __forceinline__ void shade_clipped(const DItem& it, const DShe
 // adjoint only:
 //   fxy  float2 [C]  footprint fractions (2 -> 4)
 //   T    float  [C]  transmittance in front of the fragment (3)
+//   Y    float  [32 NB]  SH basis of the round's pixels, NB = pixel_basis
+//                    (SH classes of degree 1-3; 1 -> 2, 4)
 static_assert(kMaxShells <= 16, "shell index takes 4 bits of the lane word");
 static_assert(kFragCap >= kMaxShells, "a pixel's fragments must fit one pass");
 
@@ -638,8 +703,20 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
   unsigned short* spl = reinterpret_cast<unsigned short*>(lb + 24 * C);
   float2* sfxy = reinterpret_cast<float2*>(lb + 26 * C);   // BWD only
   float* sT = reinterpret_cast<float*>(lb + 34 * C);       // BWD only
+  constexpr int NB = pixel_basis(TC, BWD);
+  float* sY = reinterpret_cast<float*>(lb + 38 * C);       // NB > 0 only
   const int p = pbase + lane;
   const bool pix_ok = p < HW;
+  if constexpr (NB > 0) {   // SH basis of this lane's pixel, shared by its fragments
+    if (pix_ok) {
+      const int y = p / W, x = p - y * W;
+      const float3 v = ray_dir(it.cam, x, y);
+      float Yb[16];
+      sh_basis(TC - TC_SH0, v.x, v.y, v.z, Yb);
+#pragma unroll
+      for (int m = 0; m < NB; ++m) sY[lane * NB + m] = Yb[m];
+    }
+  }
 
   // 1. hits of this pixel
   unsigned mask = 0;
@@ -723,7 +800,18 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
         Tri Tr;
         int idx[3];
         const int y = pp / W, x = pp - y * W;
-        const int r = t < s.nt ? load_tri_shade(s, t, Tr, idx) : 4;
+        float2 uv[3];
+        int r;
+        if (BWD && !FULL && !FROM_HITS && s.trec) {
+          r = t < s.nt ? load_tri_rec(s, t, Tr, uv) : 4;
+        } else {
+          r = t < s.nt ? load_tri_shade(s, t, Tr, idx) : 4;
+          if (r == 0) {
+            uv[0] = __ldg(s.uv + idx[0]);
+            uv[1] = __ldg(s.uv + idx[1]);
+            uv[2] = __ldg(s.uv + idx[2]);
+          }
+        }
         if (FULL && r == 2) {
           // a vertex nearer than znear (or off the guard band): the triangle
           // is clipped; shaded by the pass below
@@ -733,7 +821,6 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
           bad = 1;
           spl[j] |= (unsigned short)kBadFrag;   // invisible, and no adjoint
         } else {
-          const float2 uv[3] = {__ldg(s.uv + idx[0]), __ldg(s.uv + idx[1]), __ldg(s.uv + idx[2])};
           int ix, iy;
           float fx, fy;
           texel_coords(Tr, uv, s.tw, s.th, 256 * x + 128, 256 * y + 128, ix, fx, iy, fy);
@@ -745,9 +832,13 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
             sxy[j] = xy;      // the entry is not read again
             sfxy[j] = fxy;
           }
-          float3 v = make_float3(0.f, 0.f, 1.f);
-          if (is_sh<TC>(s)) v = ray_dir(it.cam, x, y);
-          fr = fetch_frag<TC>(s, f, ix, fx, iy, fy, v);
+          if constexpr (NB > 0) {
+            fr = fetch_sh_basis<TC - TC_SH0, sh_vec<TC>()>(s, f, sY + (spl[j] & 31) * NB);
+          } else {
+            float3 v = make_float3(0.f, 0.f, 1.f);
+            if (is_sh<TC>(s)) v = ray_dir(it.cam, x, y);
+            fr = fetch_frag<TC>(s, f, ix, fx, iy, fy, v);
+          }
           if constexpr (FULL) {
             if (it.layers) layer_geom(it, s, idx, i, pp, ix, fx, iy, fy);
           }
@@ -832,7 +923,50 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
         }
       }
     }
-    if constexpr (BWD) {
+    if constexpr (NB > 0) {
+      __syncwarp();
+      // 4. adjoint scatter, cooperative: lane = (fragment, tap, 16-byte
+      //    chunk l of the texel's NCH values); degree 3 (13 chunks) takes
+      //    two taps per lane.  Each value is w_q * (d_c * Y_m), as in
+      //    scatter_sh.
+      constexpr int NCH = 1 + 3 * NB, NL = (NCH + 3) / 4;
+      constexpr int CPT = NL <= 4 ? 4 : (NL <= 8 ? 8 : 16);   // lanes per texel
+      constexpr int TPL = CPT == 16 ? 2 : 1;                   // taps per lane
+      constexpr int LPF = 4 * CPT / TPL, FPI = 32 / LPF;       // lanes per fragment, fragments per step
+      const int l = lane % CPT, q0 = (lane / CPT) % (4 / TPL), fs = lane / LPF;
+      int ym[4], col[4];   // channel 4 l + e: colour (3 = alpha, 4 = padding) and basis index
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = 4 * l + e;
+        col[e] = c == 0 ? 3 : (c >= NCH ? 4 : (c - 1) % 3);
+        ym[e] = (c == 0 || c >= NCH) ? 0 : (c - 1) / 3;
+      }
+      if (l < NL) {
+        for (int j = fs; j < nf; j += FPI) {
+          const unsigned pl = spl[j];
+          if (pl & kBadFrag) continue;
+          const DShell& s = sh[(pl >> 5) & 15];
+          const Footprint f = unpack_footprint(sxy[j], sfxy[j]);
+          const float4 d = sfrag[j];
+          const float* Y = sY + (pl & 31) * NB;
+          float dv[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float dc = col[e] == 0 ? d.x : (col[e] == 1 ? d.y : (col[e] == 2 ? d.z : d.w));
+            dv[e] = col[e] == 3 ? dc : dc * Y[ym[e]];
+          }
+#pragma unroll
+          for (int tq = 0; tq < TPL; ++tq) {
+            const int q = q0 + 2 * tq;
+            const int xq = (q & 1) ? f.x1 : f.x0, yq = (q & 2) ? f.y1 : f.y0;
+            const float w = ((q & 1) ? f.fx : 1.0f - f.fx) * ((q & 2) ? f.fy : 1.0f - f.fy);
+            red_add_v4f32(s.grad + ((size_t)yq * s.tw + xq) * s.pitch + 4 * l, col[0] == 4 ? 0.0f : w * dv[0],
+                          col[1] == 4 ? 0.0f : w * dv[1], col[2] == 4 ? 0.0f : w * dv[2],
+                          col[3] == 4 ? 0.0f : w * dv[3]);
+          }
+        }
+      }
+    } else if constexpr (BWD) {
       __syncwarp();
       // 4. adjoint scatter, 32 fragments at a time
       for (int j0 = 0; j0 < nf; j0 += 32) {
@@ -886,15 +1020,15 @@ __device__ __forceinline__ void unit_shade(const DItem& it, const DShell* sh, in
 extern __shared__ __align__(16) char vs_smem[];
 
 // Shared-memory slice of the calling warp (every phase carves the same way).
-__device__ __forceinline__ char* warp_smem(int K, bool bwd) {
-  return vs_smem + (threadIdx.x >> 5) * warp_slice_bytes(K, bwd);
+__device__ __forceinline__ char* warp_smem(int K, bool bwd, int tc) {
+  return vs_smem + (threadIdx.x >> 5) * warp_slice_bytes(K, bwd, tc);
 }
 
 template <bool BWD, bool FROM_HITS, int TC, bool FULL>
 __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS) k_shade(TableRef tb, int item) {
   const DItem& it = tb.items[item];
   const int w = threadIdx.x >> 5;
-  unit_shade<BWD, FROM_HITS, TC, FULL>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, warp_smem(tb.kmax, BWD), tb.kmax, w,
+  unit_shade<BWD, FROM_HITS, TC, FULL>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, warp_smem(tb.kmax, BWD, TC), tb.kmax, w,
                              w + 1);
 }
 
@@ -927,7 +1061,7 @@ __global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS)
   const unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   WsHeader* hdr = tb.hdr;
-  char* smem = warp_smem(tb.kmax, BWD);
+  char* smem = warp_smem(tb.kmax, BWD, TC);
   for (;;) {
     int g = 0;
     if (lane == 0) g = *(volatile int*)&hdr->abort ? tb.total : (int)atomicAdd(&hdr->next_unit, 1u);

@@ -196,9 +196,9 @@ def test_host_side_errors(vs, ctx):
     from paper_2409_02482_gb300._abi import VSError
     (scene, cams), = synth.config_scene("c1", scale=0.1)
     obj = vs.ShellObject.from_scene(ctx, scene)
-    ws = vs.make_workspace(ctx, [obj], cams)
-    with pytest.raises(VSError, match="WORKSPACE"):
-        vs.render(ctx, obj, cams[0], ws[: ws.numel() // 2])
+    ws = vs.make_workspace(ctx, [obj], cams[:1])
+    with pytest.raises(VSError, match="WORKSPACE"):   # below the visibility words alone
+        vs.render(ctx, obj, cams[0], ws[: 8 * obj.k * int(cams[0].width) * int(cams[0].height) // 2])
     with pytest.raises(VSError, match="WORKSPACE"):
         vs.render(ctx, obj, cams[0], ws[1:])
 
