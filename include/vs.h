@@ -443,6 +443,13 @@ typedef struct {
                                 included), as declared by the host side      */
   uint64_t tris_clipped;     /* one or two vertices nearer than znear: clipped
                                 at the near plane, the rest rasterized       */
+  int32_t kernel_class;      /* shading kernels of the last call: 1 + texel
+                                class (0 any format, chosen per shell; 1 RGBA
+                                F32; 2 + d SH F16 of degree d; 6 + d baked
+                                bytes of degree d), + 16 for the variant with
+                                near-plane clipping and per-layer buffers; 0
+                                before any call                               */
+  int32_t reserved;
 } vs_stats;
 
 /* Synchronizes `stream`, copies the counters accumulated in `workspace`

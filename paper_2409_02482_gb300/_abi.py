@@ -80,11 +80,14 @@ class vs_stats(ctypes.Structure):
                 ("tris_front", ctypes.c_uint64), ("tris_culled_back", ctypes.c_uint64),
                 ("tris_culled_near", ctypes.c_uint64), ("tris_culled_guard", ctypes.c_uint64),
                 ("tris_large", ctypes.c_uint64), ("launches", ctypes.c_uint64),
-                ("tris_clipped", ctypes.c_uint64)]
+                ("tris_clipped", ctypes.c_uint64), ("kernel_class", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
+
+# vs_stats.kernel_class: 1 + texel class (+ 16 for the clipping / layers variant)
+KCLASS_ANY, KCLASS_RGBA, KCLASS_SH0, KCLASS_U80, KCLASS_FULL = 1, 2, 3, 7, 16
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int32

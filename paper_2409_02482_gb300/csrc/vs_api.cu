@@ -384,6 +384,7 @@ vs_status upload_table(const Plan& P, char* ws, int kernels, cudaStream_t st) {
     chunk.nbytes = (uint32_t)nb;
     chunk.reset = c == 0 ? 1 : 0;
     chunk.launches = c == 0 ? (int32_t)(nchunks + kernels) : 0;
+    chunk.kernel_class = 1 + P.tc + (P.full ? 16 : 0);
     std::memcpy(chunk.data, blob.data() + pos, nb);
     cudaError_t e = vsk::upload(ws, chunk, st);
     if (e != cudaSuccess) return cuda_fail(e, "table upload launch");
@@ -1007,6 +1008,8 @@ vs_status vs_read_stats(void* workspace, vs_stream_t stream, int32_t reset, vs_s
   out->tris_large = h.large;
   out->launches = h.launches;
   out->tris_clipped = h.clipped;
+  out->kernel_class = h.kernel_class;
+  out->reserved = 0;
   if (reset) {
     if ((e = cudaMemset(workspace, 0, sizeof h)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
   }

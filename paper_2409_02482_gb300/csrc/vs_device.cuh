@@ -147,7 +147,9 @@ struct alignas(16) WsHeader {
   unsigned long long frags, front, back, nearc, guard, large;
   unsigned long long launches;  // kernels enqueued by the calls (host-declared)
   unsigned long long clipped;   // triangles clipped at the near plane
-  unsigned long long reserved[22];
+  int32_t kernel_class;         // shading kernels of the last call (host-declared)
+  int32_t pad1;
+  unsigned long long reserved[21];
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 

@@ -14,6 +14,7 @@ __global__ void __launch_bounds__(kThreads) k_upload(char* ws, const __grid_cons
     h->next_unit = 0;
     h->abort = 0;
     h->launches += (unsigned long long)c.launches;
+    h->kernel_class = c.kernel_class;
   }
 }
 

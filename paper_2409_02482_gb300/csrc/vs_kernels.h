@@ -31,6 +31,8 @@ struct UploadChunk {
   uint32_t nbytes;          // multiple of 16
   int32_t reset;            // first chunk: reset next_unit / abort, count launches
   int32_t launches;         // kernels this call enqueues (added to the header)
+  int32_t kernel_class;     // first chunk: the call's shading kernels (vs_stats::kernel_class)
+  int32_t pad[3];
   uint4 data[kUploadBytes / 16];
 };
 

@@ -36,7 +36,7 @@ def test_struct_layouts_match_header_sizes():
     # sizes implied by the C declarations on LP64
     assert ctypes.sizeof(_abi.vs_camera) == 76
     assert ctypes.sizeof(_abi.vs_shell_desc) == 80
-    assert ctypes.sizeof(_abi.vs_stats) == 72
+    assert ctypes.sizeof(_abi.vs_stats) == 80
     assert ctypes.sizeof(_abi.vs_tuning) == 16
 
 

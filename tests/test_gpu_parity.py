@@ -636,6 +636,76 @@ def test_batch_graph_capture_replays(vs, ctx):
 # full-size workloads (the launch configuration the benchmark times)
 # ----------------------------------------------------------------------------
 
+# ----------------------------------------------------------------------------
+# compiled texel classes: the kernels the fused step runs on aligned texels
+# (256-bit SH loads, per-pixel SH basis, triangle records, cooperative
+# scatter), checked against the oracle and shown to be the ones that ran
+# ----------------------------------------------------------------------------
+
+def _class_scene(fmt, deg, pitch, k=3, n_lat=20, tex=64, seed=0):
+    rng = np.random.default_rng(50 + deg)
+    shells = []
+    for pos, uv, tris in synth.displaced_shells(k, n_lat, seed=seed):
+        if fmt == FMT_RGBA_F32:
+            shells.append(Shell(pos, uv, tris, synth.rgba_texture(tex, tex, rng), FMT_RGBA_F32))
+        else:
+            shells.append(Shell(pos, uv, tris, synth.sh_texture(tex, tex, deg, rng, sigma=0.4, pitch=pitch),
+                                FMT_SH_F16, deg))
+    return Scene(shells)
+
+
+# (format, SH degree, texel pitch with 32-byte-aligned texels, kernel class)
+CLASS_CASES = [(FMT_RGBA_F32, 0, 4, 2), (FMT_SH_F16, 0, 8, 3), (FMT_SH_F16, 1, 16, 4), (FMT_SH_F16, 2, 32, 5),
+               (FMT_SH_F16, 3, 64, 6)]
+
+
+@pytest.mark.parametrize("fmt,deg,pitch,kclass", CLASS_CASES)
+def test_class_kernels_match_oracle(vs, ctx, fmt, deg, pitch, kclass):
+    """Fused batch (forward + adjoint of two views into shared gradients) and
+    the plain render / render_backward pair, both on the class kernels,
+    against the oracle: hits exact, colours and gradients to FP32 rounding."""
+    sc = _class_scene(fmt, deg, pitch)
+    cams = [synth.look_at((0.3, -2.6, 0.9), width=96, height=72),
+            synth.look_at((-1.9, -1.2, -0.7), width=80, height=88)]
+    bg = (0.1, 0.2, 0.3)
+    items, objs, ws = _batch_setup(vs, ctx, [(sc, cams)], True)
+    vs.render_batch(ctx, items, ws, bg=bg, do_backward=True)
+    st = vs.read_stats(ws, reset=True)
+    assert st["device_status"] == 0
+    assert st["kernel_class"] == kclass
+    nch = 4 if fmt == FMT_RGBA_F32 else 1 + 3 * (deg + 1) ** 2
+    ref_sum = None
+    for it in items:
+        ref, ref_hits, _ = oracle.render(sc, it["cam"], bg=bg)
+        assert np.array_equal(it["hits"].cpu().numpy(), ref_hits)
+        assert np.abs(it["out"].cpu().numpy() - ref).max() <= 2e-5
+        rg = oracle.backward(sc, it["cam"], ref_hits, it["grad_rgb"].cpu().numpy().astype(np.float64), bg=bg)
+        ref_sum = rg if ref_sum is None else [a + b for a, b in zip(ref_sum, rg)]
+        # plain pair on the same class kernels, this view alone
+        ws1 = vs.make_workspace(ctx, [objs[0]], [it["cam"]])
+        out1, hits1 = vs.render(ctx, objs[0], it["cam"], ws1, bg=bg)
+        assert torch.equal(out1, it["out"]) and torch.equal(hits1, it["hits"])
+        g1 = vs.render_backward(ctx, objs[0], it["cam"], ws1, hits1, it["grad_rgb"], bg=bg)
+        assert vs.read_stats(ws1)["kernel_class"] == kclass
+        for gg, r in zip(g1, rg):
+            got = gg.cpu().numpy()
+            assert np.abs(got[..., :nch] - r[..., :nch]).max() <= 1e-4 * max(np.abs(r).max(), 1e-30)
+            assert not got[..., nch:].any()
+    for gg, r in zip(items[0]["grads"], ref_sum):
+        got = gg.cpu().numpy()
+        assert np.abs(got[..., :nch] - r[..., :nch]).max() <= 1e-4 * max(np.abs(r).max(), 1e-30)
+        assert not got[..., nch:].any()
+
+
+def test_unaligned_texels_take_the_generic_kernels(vs, ctx):
+    """A pitch that breaks 32-byte alignment keeps SH degree 2 on the generic
+    kernels, with the same results."""
+    sc = _class_scene(FMT_SH_F16, 2, 28)
+    cam = synth.look_at((0.3, -2.6, 0.9), width=64, height=48)
+    w, obj, ws, hits, grads = check_backward(vs, ctx, sc, cam, (0.1, 0.2, 0.3), 1e-4)
+    assert vs.read_stats(ws)["kernel_class"] == 1
+
+
 def test_c2_full_size_views(vs, ctx):
     (scene, cams), = synth.config_scene("c2", views=100)
     obj = vs.ShellObject.from_scene(ctx, scene)
