@@ -925,44 +925,47 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
     }
     if constexpr (NB > 0) {
       __syncwarp();
-      // 4. adjoint scatter, cooperative: lane = (fragment, tap, 16-byte
-      //    chunk l of the texel's NCH values); degree 3 (13 chunks) takes
-      //    two taps per lane.  Each value is w_q * (d_c * Y_m), as in
+      // 4. adjoint scatter, cooperative: lane = (fragment, 16-byte chunk l
+      //    of the texel's NCH values), looping over the 4 taps, so one
+      //    reduction instruction writes FPI fragments' texel rows as
+      //    contiguous chunks.  Each value is w_q * (d_c * Y_m), as in
       //    scatter_sh.
       constexpr int NCH = 1 + 3 * NB, NL = (NCH + 3) / 4;
-      constexpr int CPT = NL <= 4 ? 4 : (NL <= 8 ? 8 : 16);   // lanes per texel
-      constexpr int TPL = CPT == 16 ? 2 : 1;                   // taps per lane
-      constexpr int LPF = 4 * CPT / TPL, FPI = 32 / LPF;       // lanes per fragment, fragments per step
-      const int l = lane % CPT, q0 = (lane / CPT) % (4 / TPL), fs = lane / LPF;
-      int ym[4], col[4];   // channel 4 l + e: colour (3 = alpha, 4 = padding) and basis index
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int c = 4 * l + e;
-        col[e] = c == 0 ? 3 : (c >= NCH ? 4 : (c - 1) % 3);
-        ym[e] = (c == 0 || c >= NCH) ? 0 : (c - 1) / 3;
-      }
+      constexpr int CPT = NL <= 4 ? 4 : (NL <= 8 ? 8 : 16);   // lanes per fragment
+      constexpr int FPI = 32 / CPT;                            // fragments per step
+      const int l = lane % CPT, fs = lane / CPT;
+      // Channel c = 4 l + e >= 1 holds colour (c - 1) % 3 of basis function
+      // (c - 1) / 3: with rot = (4 l - 1) mod 3 (2 for l = 0), channel e has
+      // colour (rot + e) % 3 and basis mA while rot + e < 3, else mB.
+      // Channel 0 is the alpha logit; channels >= NCH are padding (0).
+      const int rot = (4 * l + 2) % 3;
+      const int mA = l == 0 ? 0 : (4 * l - 1) / 3;
+      const int mB = l == 0 ? 0 : min(mA + 1, NB - 1);
+      const bool k1 = 4 * l + 1 < NCH, k2 = 4 * l + 2 < NCH, k3 = 4 * l + 3 < NCH;
       if (l < NL) {
         for (int j = fs; j < nf; j += FPI) {
           const unsigned pl = spl[j];
           if (pl & kBadFrag) continue;
           const DShell& s = sh[(pl >> 5) & 15];
-          const Footprint f = unpack_footprint(sxy[j], sfxy[j]);
           const float4 d = sfrag[j];
           const float* Y = sY + (pl & 31) * NB;
-          float dv[4];
+          const float yA = Y[mA], yB = Y[mB];
+          const float c0 = rot == 0 ? d.x : (rot == 1 ? d.y : d.z);
+          const float c1 = rot == 0 ? d.y : (rot == 1 ? d.z : d.x);
+          const float c2 = rot == 0 ? d.z : (rot == 1 ? d.x : d.y);
+          const float dv0 = l == 0 ? d.w : c0 * yA;
+          const float dv1 = c1 * (rot < 2 ? yA : yB);
+          const float dv2 = c2 * (rot < 1 ? yA : yB);
+          const float dv3 = c0 * yB;
+          const Footprint f = unpack_footprint(sxy[j], sfxy[j]);
+          const size_t r0 = (size_t)f.y0 * s.tw, r1 = (size_t)f.y1 * s.tw;
+          float* g = s.grad + 4 * l;
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float dc = col[e] == 0 ? d.x : (col[e] == 1 ? d.y : (col[e] == 2 ? d.z : d.w));
-            dv[e] = col[e] == 3 ? dc : dc * Y[ym[e]];
-          }
-#pragma unroll
-          for (int tq = 0; tq < TPL; ++tq) {
-            const int q = q0 + 2 * tq;
-            const int xq = (q & 1) ? f.x1 : f.x0, yq = (q & 2) ? f.y1 : f.y0;
+          for (int q = 0; q < 4; ++q) {
+            const int xq = (q & 1) ? f.x1 : f.x0;
             const float w = ((q & 1) ? f.fx : 1.0f - f.fx) * ((q & 2) ? f.fy : 1.0f - f.fy);
-            red_add_v4f32(s.grad + ((size_t)yq * s.tw + xq) * s.pitch + 4 * l, col[0] == 4 ? 0.0f : w * dv[0],
-                          col[1] == 4 ? 0.0f : w * dv[1], col[2] == 4 ? 0.0f : w * dv[2],
-                          col[3] == 4 ? 0.0f : w * dv[3]);
+            red_add_v4f32(g + (((q & 2) ? r1 : r0) + xq) * s.pitch, w * dv0, k1 ? w * dv1 : 0.0f,
+                          k2 ? w * dv2 : 0.0f, k3 ? w * dv3 : 0.0f);
           }
         }
       }
