@@ -266,6 +266,16 @@ def l2_loss_grad(rgba: np.ndarray, target_rgb: np.ndarray):
     return float((d * d).sum() / n), 2.0 * d / n
 
 
+def l1_loss_grad(rgba: np.ndarray, target_rgb: np.ndarray):
+    """The pixel-wise L1 colour loss the textures are fitted with (Sec. 3
+    "Texturing Meshes"): L = mean over pixels and RGB channels of
+    |C - target|; returns (L, dL/dC) with the subgradient 0 where C equals
+    the target."""
+    d = rgba[..., :3] - target_rgb
+    n = d.size
+    return float(np.abs(d).sum() / n), np.sign(d) / n
+
+
 def footprint_texels(scene, cam, hits: np.ndarray) -> np.ndarray:
     """Distinct texels read by each shell's bilinear footprints."""
     refs = _ShellRefs(scene.shells)

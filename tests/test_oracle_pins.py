@@ -1123,3 +1123,59 @@ def test_workloads_cull_nothing_at_near_plane_or_guard_band(name):
             for s in sc.shells:
                 xy, invw, q, flags = oracle.setup_vertices(s.pos, cam)
                 assert np.all(flags == 0)
+
+
+# ----------------------------------------------------------------------------
+# image losses (the L1 colour loss of Sec. 3 "Texturing Meshes"; the L2 one of
+# the fitting benchmark)
+# ----------------------------------------------------------------------------
+
+def _loss_case():
+    rgba = np.zeros((1, 2, 4))
+    rgba[0, 0, :3] = (0.5, 0.25, 1.0)
+    rgba[0, 1, :3] = (0.0, 0.75, 0.5)
+    target = np.array([[[0.25, 0.25, 0.0], [0.5, 0.5, 0.5]]])
+    return rgba, target
+
+
+def test_l1_loss_closed_form():
+    rgba, target = _loss_case()
+    L, g = oracle.l1_loss_grad(rgba, target)
+    # |d| = 0.25, 0, 1, 0.5, 0.25, 0 over 6 values
+    assert L == pytest.approx(2.0 / 6.0, abs=1e-15)
+    assert np.array_equal(g * 6.0, np.array([[[1.0, 0.0, 1.0], [-1.0, 1.0, 0.0]]]))
+
+
+def test_l2_loss_closed_form():
+    rgba, target = _loss_case()
+    L, g = oracle.l2_loss_grad(rgba, target)
+    assert L == pytest.approx((0.0625 + 1.0 + 0.25 + 0.0625) / 6.0, abs=1e-15)
+    assert np.allclose(g * 6.0, 2.0 * np.array([[[0.25, 0.0, 1.0], [-0.5, 0.25, 0.0]]]), atol=1e-15)
+
+
+@pytest.mark.parametrize("which", ["l1", "l2"])
+def test_loss_gradients_match_finite_differences(which):
+    rng = np.random.default_rng(11)
+    rgba = rng.random((5, 7, 4))
+    target = rng.random((5, 7, 3))
+    fn = oracle.l1_loss_grad if which == "l1" else oracle.l2_loss_grad
+    _, g = fn(rgba, target)
+    h = 1e-7
+    for idx in [(0, 0, 0), (2, 3, 1), (4, 6, 2), (1, 5, 0)]:
+        assert abs(rgba[idx] - target[idx]) > 10 * h   # away from the L1 kink
+        p, m = rgba.copy(), rgba.copy()
+        p[idx] += h
+        m[idx] -= h
+        fd = (fn(p, target)[0] - fn(m, target)[0]) / (2 * h)
+        assert fd == pytest.approx(g[idx], rel=1e-6, abs=1e-9)
+
+
+def test_l1_at_most_root_l2():
+    """mean |d| <= sqrt(mean d^2), equality for constant |d|."""
+    rng = np.random.default_rng(12)
+    rgba, target = rng.random((6, 5, 4)), rng.random((6, 5, 3))
+    assert oracle.l1_loss_grad(rgba, target)[0] <= math.sqrt(oracle.l2_loss_grad(rgba, target)[0])
+    flat = np.zeros((2, 2, 4))
+    tgt = np.full((2, 2, 3), 0.5)
+    flat[..., :3] = tgt + np.where(rng.random((2, 2, 3)) < 0.5, -0.25, 0.25)
+    assert oracle.l1_loss_grad(flat, tgt)[0] == pytest.approx(math.sqrt(oracle.l2_loss_grad(flat, tgt)[0]))
