@@ -141,6 +141,11 @@ typedef struct {
  * gradient; the kernel uses dL/dC = 2 (C - target) / (3 H W), i.e. the
  * gradient of the mean squared error over pixels and RGB channels, computing
  * C itself from the hits, and adds L to `loss` when that pointer is set. */
+#define VS_FLAG_LOSS_L1 (1u << 2)
+/* Backward only, like VS_FLAG_LOSS_L2 with the pixel-wise L1 colour loss the
+ * textures are fitted with (Sec. 3 "Texturing Meshes"): L = mean over pixels
+ * and RGB channels of |C - target|, dL/dC = sign(C - target) / (3 H W) with
+ * sign(0) = 0.  Setting both loss flags is VS_ERR_INVALID_ARG. */
 #define VS_FLAG_ALPHA_ATTEN (1u << 1)
 /* Transparency attenuation (Sec. 3 "Transparency Attenuation"): every
  * fragment's opacity is multiplied by alpha_w = 2 sigmoid(10 |v . n|) - 1,
@@ -222,11 +227,11 @@ vs_status vs_render(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, con
  *   hits         device int32 [k, H, W] as written by vs_render for the same
  *                object, camera and texels
  *   grad_rgb     device float32 [H, W, 3] (or the target image with
- *                VS_FLAG_LOSS_L2)
+ *                VS_FLAG_LOSS_L2 / VS_FLAG_LOSS_L1)
  *   grad_texels  host array of k device pointers, each float32
  *                [tex_h, tex_w, texel_pitch]; ADDED to (zero them first);
  *                padding values receive nothing
- *   loss         device float32 scalar, L added (VS_FLAG_LOSS_L2 only; may
+ *   loss         device float32 scalar, L added (with a loss flag only; may
  *                be NULL)
  * Transmittance is recomputed from the hits, not stored.  Gradients use
  * float atomics: summation order, hence the last bits, vary run to run. */
@@ -264,7 +269,7 @@ typedef struct {
   int32_t* hits;              /* device [k, H, W] or NULL                 */
   const float* grad_rgb;      /* device [H, W, 3] (do_backward only)      */
   float* const* grad_texels;  /* host array of k device pointers (bwd)    */
-  float* loss;                /* device scalar or NULL (VS_FLAG_LOSS_L2)  */
+  float* loss;                /* device scalar or NULL (loss flags)       */
 } vs_batch_item;
 
 /* Renders n items -- any mix of objects, shell counts, triangle counts and
@@ -274,7 +279,7 @@ typedef struct {
  * item s-1, shading of item s-2); a unit waits, with a bounded spin, only
  * for units handed out before it, so the launch cannot deadlock.  With do_backward, each pixel's forward result is
  * differentiated in the same unit (fused forward + backward) using
- * grad_rgb -- with VS_FLAG_LOSS_L2, the target image.  Forward outputs are
+ * grad_rgb -- with a loss flag, the target image.  Forward outputs are
  * bit-identical to vs_render of each item.  All enqueued work is
  * capturable in a CUDA graph (the item table travels in kernel parameters).
  * Errors: as vs_render; VS_ERR_INVALID_ARG for n < 1. */

@@ -29,6 +29,7 @@ VS_TEX_RGBA_F32 = 0
 VS_TEX_SH_F16 = 1
 VS_TEX_SH_U8 = 2
 VS_FLAG_LOSS_L2 = 1 << 0
+VS_FLAG_LOSS_L1 = 1 << 2
 VS_FLAG_ALPHA_ATTEN = 1 << 1
 VS_FLAG_TEST_STALL = 1 << 30
 VS_MAX_SHELLS = 16

@@ -228,6 +228,8 @@ bool needs_clip(const vs_object& o, const vs_camera& c) {
 // Fills the plan; with ws == nullptr only sizes are computed.
 vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool clear_vis, uint32_t flags,
                     char* ws, Plan& P, UnitShape shape = UnitShape()) {
+  if ((flags & VS_FLAG_LOSS_L1) && (flags & VS_FLAG_LOSS_L2))
+    return fail(VS_ERR_INVALID_ARG, "VS_FLAG_LOSS_L1 and VS_FLAG_LOSS_L2 are exclusive");
   P.full = false;
   for (int j = 0; j < n; ++j) P.full = P.full || needs_clip(*req[j].obj, *req[j].cam) || req[j].layers;
   // triangle records for the fused adjoint; reserved whatever kernels run,

@@ -896,6 +896,13 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
             gr = 2.0f * inv * dr;
             gg = 2.0f * inv * dg;
             gb = 2.0f * inv * db;
+          } else if (it.flags & VS_FLAG_LOSS_L1) {
+            const float dr = outr - gr, dg = outg - gg, db = outb - gb;
+            const float inv = 1.0f / (3.0f * (float)HW);
+            loss_acc += (fabsf(dr) + fabsf(dg) + fabsf(db)) * inv;
+            gr = dr > 0.0f ? inv : (dr < 0.0f ? -inv : 0.0f);
+            gg = dg > 0.0f ? inv : (dg < 0.0f ? -inv : 0.0f);
+            gb = db > 0.0f ? inv : (db < 0.0f ? -inv : 0.0f);
           }
         }
         // back to front; the colour and opacity of each fragment are
@@ -1012,7 +1019,7 @@ __device__ __forceinline__ void unit_shade(const DItem& it, const DShell* sh, in
   if (!FROM_HITS) warp_count(&hdr->frags, nfrag);
   if (__any_sync(kAll, bad) && lane == 0) record_error(hdr, VS_ERR_INVALID_ARG);
   if constexpr (BWD) {
-    if (it.loss && (it.flags & VS_FLAG_LOSS_L2)) {
+    if (it.loss && (it.flags & (VS_FLAG_LOSS_L2 | VS_FLAG_LOSS_L1))) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(kAll, loss, o);
       if (lane == 0 && loss != 0.0f) atomicAdd(it.loss, loss);

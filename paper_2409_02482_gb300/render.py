@@ -12,7 +12,7 @@ from typing import List, Optional, Sequence
 import torch
 
 from . import _abi
-from ._abi import (VS_FLAG_ALPHA_ATTEN, VS_FLAG_LOSS_L2, VS_TEX_RGBA_F32, VS_TEX_SH_F16, VS_TEX_SH_U8, check,
+from ._abi import (VS_FLAG_ALPHA_ATTEN, VS_FLAG_LOSS_L1, VS_FLAG_LOSS_L2, VS_TEX_RGBA_F32, VS_TEX_SH_F16, VS_TEX_SH_U8, check,
                    vs_batch_item, vs_ntex_config,
                    vs_camera, vs_cost_fn, vs_shell_desc, vs_stats, vs_tuning)
 
@@ -20,7 +20,7 @@ __all__ = ["Context", "ShellObject", "camera_struct", "workspace_size", "make_wo
            "render", "render_layers", "render_backward", "render_batch", "read_stats", "VSRender",
            "NeuralTexture",
            "tuning", "set_batch_tuning", "get_batch_tuning", "tune_search", "autotune_batch",
-           "VS_FLAG_ALPHA_ATTEN", "VS_FLAG_LOSS_L2", "VS_TEX_RGBA_F32", "VS_TEX_SH_F16", "VS_TEX_SH_U8",
+           "VS_FLAG_ALPHA_ATTEN", "VS_FLAG_LOSS_L1", "VS_FLAG_LOSS_L2", "VS_TEX_RGBA_F32", "VS_TEX_SH_F16", "VS_TEX_SH_U8",
            "baked_layout"]
 
 

@@ -132,6 +132,18 @@ def test_workspace_size_covers_the_dominant_terms(lib):
     lib.vs_free_shells(_fake_ctx(), obj)
 
 
+def test_loss_flags_are_exclusive(lib):
+    st, obj = _load(lib, [_desc()])
+    assert st == 0
+    objs = (ctypes.c_void_p * 1)(obj.value)
+    cams = (_abi.vs_camera * 1)(_cam())
+    size = ctypes.c_size_t()
+    for fl, want in [(_abi.VS_FLAG_LOSS_L1, 0), (_abi.VS_FLAG_LOSS_L2, 0),
+                     (_abi.VS_FLAG_LOSS_L1 | _abi.VS_FLAG_LOSS_L2, _abi.VS_ERR_INVALID_ARG)]:
+        assert lib.vs_workspace_size(_fake_ctx(), objs, cams, 1, fl, ctypes.byref(size)) == want
+    lib.vs_free_shells(_fake_ctx(), obj)
+
+
 @pytest.mark.parametrize("w,h,znear", [(0, 10, 0.1), (10, 9000, 0.1), (64, 64, 0.0), (64, 64, -1.0)])
 def test_workspace_size_rejects_bad_cameras(lib, w, h, znear):
     st, obj = _load(lib, [_desc()])

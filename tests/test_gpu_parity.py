@@ -257,6 +257,35 @@ def test_backward_l2_loss_flag(vs, ctx):
         assert np.abs(gg.cpu().numpy() - rg).max() <= 1e-4 * np.abs(rg).max()
 
 
+def test_backward_l1_loss_flag(vs, ctx):
+    """The L1 colour loss of Sec. 3 "Texturing Meshes": loss value and
+    gradients against the oracle."""
+    BG_EXACT = (0.25, 0.5, 0.75)   # exact in FP32: background residuals are 0 on both sides
+    (scene, cams), = synth.config_scene("c3", scale=0.002, views=1)
+    cam = cams[0]
+    (target_scene, _), = synth.config_scene("c3", scale=0.002, views=1, tex_seed=5)
+    target, _, _ = oracle.render(target_scene, cam, bg=BG_EXACT)
+    tgt64 = target[..., :3].astype(np.float32).astype(np.float64)
+    ref_rgba, ref_hits, _ = oracle.render(scene, cam, bg=BG_EXACT)
+    # no residual so close to zero that FP32 and FP64 could disagree on its
+    # sign (the colours agree to ~2e-7; target seed 5 keeps them >= 3e-5)
+    d = np.abs(ref_rgba[..., :3] - tgt64)
+    assert not np.any((d > 0) & (d < 1e-5))
+    obj = vs.ShellObject.from_scene(ctx, scene)
+    ws = vs.make_workspace(ctx, [obj], [cam])
+    out, hits = vs.render(ctx, obj, cam, ws, bg=BG_EXACT)
+    tgt = torch.from_numpy(target[..., :3].astype(np.float32)).cuda()
+    loss = torch.zeros(1, device="cuda")
+    grads = vs.render_backward(ctx, obj, cam, ws, hits, tgt, bg=BG_EXACT, loss=loss,
+                               flags=vs.VS_FLAG_LOSS_L1)
+    L, dL = oracle.l1_loss_grad(ref_rgba, tgt64)
+    ref = oracle.backward(scene, cam, ref_hits, dL, bg=BG_EXACT)
+    assert abs(loss.item() - L) <= 1e-5 * L + 1e-9
+    for gg, rg in zip(grads, ref):
+        assert np.abs(gg.cpu().numpy() - rg).max() <= 1e-4 * np.abs(rg).max()
+    assert vs.read_stats(ws)["device_status"] == 0
+
+
 @pytest.mark.parametrize("attenuate", [False, True])
 def test_autograd_function(vs, ctx, attenuate):
     flags = vs.VS_FLAG_ALPHA_ATTEN if attenuate else 0
@@ -512,9 +541,9 @@ def test_batch_forward_bit_identical_to_plain(vs, ctx):
         assert np.abs(it["out"].cpu().numpy() - ref).max() <= TOL_F16
 
 
-@pytest.mark.parametrize("attenuate", [False, True])
-def test_batch_fused_backward_matches_plain(vs, ctx, attenuate):
-    flags = vs.VS_FLAG_ALPHA_ATTEN if attenuate else 0
+@pytest.mark.parametrize("mode", ["plain", "attenuate", "l1"])
+def test_batch_fused_backward_matches_plain(vs, ctx, mode):
+    flags = {"plain": 0, "attenuate": vs.VS_FLAG_ALPHA_ATTEN, "l1": vs.VS_FLAG_LOSS_L1}[mode]
     objs_cams = synth.config_scene("c4", scale=0.002, views=2)[:4]
     items, objs, ws = _batch_setup(vs, ctx, objs_cams, True)
     vs.render_batch(ctx, items, ws, do_backward=True, flags=flags)
