@@ -97,11 +97,35 @@ __device__ __forceinline__ int cell_row(const Enc& e, int l, int ty, int H) {
   return (int)floorf((ty + 0.5f) / (float)H * (float)e.res[l]);
 }
 
+// Run of consecutive lanes holding the same key: `start` = lane of the run's
+// first member, `tail` = this lane ends the run.  The sentinel 0xffffffff
+// (idle lanes) never matches a table row.
+__device__ __forceinline__ void lane_run(uint32_t key, int lane, int& start, bool& tail) {
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1), next = __shfl_down_sync(0xffffffffu, key, 1);
+  const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+  start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+  tail = lane == 31 || next != key;
+}
+// Sum of v over the lanes [start, lane] (inclusive segmented scan).
+__device__ __forceinline__ float run_scan(float v, int lane, int start) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane - o >= start) v += u;
+  }
+  return v;
+}
+
 __global__ void __launch_bounds__(kThreads) k_encode_bwd(Enc e, const float* dX, int W, int H, int n0, int count,
                                                           float* dtable) {
   extern __shared__ float acc[];
   const int l = blockIdx.y;
   const int n = e.res[l];
+  const int lane = threadIdx.x & 31;
+  // neighbouring texels share a cell (two or more texels per cell): a warp's
+  // contributions to one row are added up across its lanes first, so that a
+  // row takes one atomic per run instead of one per texel
+  const bool runs = 2 * n <= W;                              // block-uniform
   const bool dense = (long long)(n + 1) * (n + 1) <= (1ll << e.logT);
   const size_t lt = (size_t)l << e.logT;
   const int nseg = (count + kSeg - 1) / kSeg;
@@ -118,16 +142,41 @@ __global__ void __launch_bounds__(kThreads) k_encode_bwd(Enc e, const float* dX,
       for (int r = threadIdx.x; r < band * e.F; r += blockDim.x) acc[r] = 0.0f;
       __syncthreads();
     }
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const int t = n0 + i, tx = t % W, ty = t / W;
-      const float* d = dX + (size_t)i * e.L * e.F + l * e.F;
-      for (int c = 0; c < 4; ++c) {
-        uint32_t row;
-        float w;
-        corner(e, l, tx, ty, W, H, c, row, w);
-        for (int f = 0; f < e.F; ++f) {
-          if (local) atomicAdd(acc + ((int)row - vb) * e.F + f, w * d[f]);
-          else atomicAdd(dtable + (lt + row) * e.F + f, w * d[f]);
+    if (runs) {
+      // whole warps step together (shuffles); idle lanes carry the sentinel
+      for (int ib = i0 + (threadIdx.x & ~31); ib < i1; ib += blockDim.x) {
+        const int i = ib + lane;
+        const bool ok = i < i1;
+        const int t = n0 + (ok ? i : i0), tx = t % W, ty = t / W;
+        const float* d = dX + (size_t)(ok ? i : i0) * e.L * e.F + l * e.F;
+        for (int c = 0; c < 4; ++c) {
+          uint32_t row;
+          float w;
+          corner(e, l, tx, ty, W, H, c, row, w);
+          int start;
+          bool tail;
+          lane_run(ok ? row : 0xffffffffu, lane, start, tail);
+          for (int f = 0; f < e.F; ++f) {
+            const float v = run_scan(ok ? w * d[f] : 0.0f, lane, start);
+            if (ok && tail) {
+              if (local) atomicAdd(acc + ((int)row - vb) * e.F + f, v);
+              else atomicAdd(dtable + (lt + row) * e.F + f, v);
+            }
+          }
+        }
+      }
+    } else {
+      for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int t = n0 + i, tx = t % W, ty = t / W;
+        const float* d = dX + (size_t)i * e.L * e.F + l * e.F;
+        for (int c = 0; c < 4; ++c) {
+          uint32_t row;
+          float w;
+          corner(e, l, tx, ty, W, H, c, row, w);
+          for (int f = 0; f < e.F; ++f) {
+            if (local) atomicAdd(acc + ((int)row - vb) * e.F + f, w * d[f]);
+            else atomicAdd(dtable + (lt + row) * e.F + f, w * d[f]);
+          }
         }
       }
     }
@@ -149,6 +198,25 @@ __global__ void __launch_bounds__(kThreads) k_bias_act(float* Z, const float* b,
   const float v = Z[id] + __ldg(b + j);
   Z[id] = relu ? fmaxf(v, 0.0f) : v;
 }
+// The same four values at a time (cols a multiple of 4; Z and b 16-byte aligned).
+__global__ void __launch_bounds__(kThreads) k_bias_act4(float4* Z, const float* b, long long n4, int cols, int relu) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= n4) return;
+  const int j = (int)((4 * id) % cols);
+  const float4 bb = __ldg(reinterpret_cast<const float4*>(b + j));
+  float4 v = Z[id];
+  v.x += bb.x;
+  v.y += bb.y;
+  v.z += bb.z;
+  v.w += bb.w;
+  if (relu) {
+    v.x = fmaxf(v.x, 0.0f);
+    v.y = fmaxf(v.y, 0.0f);
+    v.z = fmaxf(v.z, 0.0f);
+    v.w = fmaxf(v.w, 0.0f);
+  }
+  Z[id] = v;
+}
 
 // dZ = dH * (H > 0) for H the ReLU output (in place on dH).
 __global__ void __launch_bounds__(kThreads) k_relu_bwd(float* dH, const float* H, long long n) {
@@ -169,6 +237,36 @@ __global__ void __launch_bounds__(kThreads) k_colsum(const float* dZ, int rows, 
     float t = 0.0f;
     for (int w = 0; w < kThreads / 32; ++w) t += part[w];
     atomicAdd(db + j, t);
+  }
+}
+
+// db[j] += sum_r dZ[r, j] with dZ = dH * (H > 0) written back in place
+// (H = null: dZ = dH, no write).  Row-major and coalesced: thread t of a
+// block owns column t % cols of rows t / cols + RS k, RS = 256 / cols rows
+// per step (cols <= 256); the block adds its per-column partials once.
+__global__ void __launch_bounds__(kThreads) k_relu_colsum(float* dH, const float* H, int rows, int cols, float* db) {
+  __shared__ float part[kThreads];
+  const int RS = kThreads / cols;
+  const int t = threadIdx.x;
+  float s = 0.0f;
+  if (t < RS * cols) {
+    const int j = t % cols;
+    for (long long r = (long long)blockIdx.x * RS + t / cols; r < rows; r += (long long)gridDim.x * RS) {
+      const size_t o = (size_t)r * cols + j;
+      float v = dH[o];
+      if (H && !(H[o] > 0.0f)) {
+        v = 0.0f;
+        dH[o] = 0.0f;
+      }
+      s += v;
+    }
+  }
+  part[t] = s;
+  __syncthreads();
+  if (t < cols) {
+    float u = 0.0f;
+    for (int k = 0; k < RS; ++k) u += part[t + k * cols];
+    atomicAdd(db + t, u);
   }
 }
 
@@ -205,6 +303,27 @@ __global__ void __launch_bounds__(kThreads) k_adam(float* p, const float* g, flo
 }
 
 unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+void bias_act(float* Z, const float* b, int rows, int cols, int relu, cudaStream_t st) {
+  if (cols % 4 == 0 && ((uintptr_t)Z | (uintptr_t)b) % 16 == 0) {
+    const long long n4 = (long long)rows * cols / 4;
+    k_bias_act4<<<blocks_for(n4), kThreads, 0, st>>>(reinterpret_cast<float4*>(Z), b, n4, cols, relu);
+  } else {
+    k_bias_act<<<blocks_for((long long)rows * cols), kThreads, 0, st>>>(Z, b, rows, cols, relu);
+  }
+}
+
+// db += column sums of dZ, dZ = dH * (H > 0) in place (H may be null).
+void relu_colsum(float* dH, const float* H, int rows, int cols, float* db, cudaStream_t st) {
+  if (cols <= kThreads) {
+    const long long steps = (rows + kThreads / cols - 1) / (kThreads / cols);
+    const unsigned grid = (unsigned)(steps < 1216 ? steps : 1216);
+    k_relu_colsum<<<grid, kThreads, 0, st>>>(dH, H, rows, cols, db);
+  } else {
+    if (H) k_relu_bwd<<<blocks_for((long long)rows * cols), kThreads, 0, st>>>(dH, H, (long long)rows * cols);
+    k_colsum<<<dim3(64, cols), kThreads, 0, st>>>(dH, rows, cols, db);
+  }
+}
 
 }  // namespace vsn
 
@@ -298,11 +417,11 @@ int chunk_forward(cublasHandle_t h, const vs_ntex_config& c, const Enc& e, const
   k_encode<<<blocks_for((long long)rows * c.levels), kThreads, 0, st>>>(e, P.table, W, H, n0, rows, w.X);
   VS_TRY_CUDA(cudaGetLastError());
   VS_TRY_BLAS(gemm_abt(h, rows, Hd, LF, w.X, P.W0, w.H1, 0.0f));
-  k_bias_act<<<blocks_for((long long)rows * Hd), kThreads, 0, st>>>(w.H1, P.b0, rows, Hd, 1);
+  bias_act(w.H1, P.b0, rows, Hd, 1, st);
   VS_TRY_BLAS(gemm_abt(h, rows, Hd, Hd, w.H1, P.W1, w.H2, 0.0f));
-  k_bias_act<<<blocks_for((long long)rows * Hd), kThreads, 0, st>>>(w.H2, P.b1, rows, Hd, 1);
+  bias_act(w.H2, P.b1, rows, Hd, 1, st);
   VS_TRY_BLAS(gemm_abt(h, rows, C, Hd, w.H2, P.W2, w.Y, 0.0f));
-  k_bias_act<<<blocks_for((long long)rows * C), kThreads, 0, st>>>(w.Y, P.b2, rows, C, 0);
+  bias_act(w.Y, P.b2, rows, C, 0, st);
   VS_TRY_CUDA(cudaGetLastError());
   return 0;
 }
@@ -347,17 +466,15 @@ int backward(cublasHandle_t h, const vs_ntex_config& c, const float* params, int
     VS_TRY_CUDA(cudaGetLastError());
     // output layer
     VS_TRY_BLAS(gemm_atb_acc(h, rows, C, Hd, w.dY, w.H2, g[5]));
-    k_colsum<<<dim3(64, C), kThreads, 0, st>>>(w.dY, rows, C, g[6]);
+    relu_colsum(w.dY, nullptr, rows, C, g[6], st);
     VS_TRY_BLAS(gemm_ab(h, rows, Hd, C, w.dY, P.W2, w.dH2));
-    k_relu_bwd<<<blocks_for((long long)rows * Hd), kThreads, 0, st>>>(w.dH2, w.H2, (long long)rows * Hd);
+    relu_colsum(w.dH2, w.H2, rows, Hd, g[4], st);
     // second hidden layer
     VS_TRY_BLAS(gemm_atb_acc(h, rows, Hd, Hd, w.dH2, w.H1, g[3]));
-    k_colsum<<<dim3(64, Hd), kThreads, 0, st>>>(w.dH2, rows, Hd, g[4]);
     VS_TRY_BLAS(gemm_ab(h, rows, Hd, Hd, w.dH2, P.W1, w.dH1));
-    k_relu_bwd<<<blocks_for((long long)rows * Hd), kThreads, 0, st>>>(w.dH1, w.H1, (long long)rows * Hd);
+    relu_colsum(w.dH1, w.H1, rows, Hd, g[2], st);
     // first hidden layer and the encoding
     VS_TRY_BLAS(gemm_atb_acc(h, rows, Hd, LF, w.dH1, w.X, g[1]));
-    k_colsum<<<dim3(64, Hd), kThreads, 0, st>>>(w.dH1, rows, Hd, g[2]);
     VS_TRY_BLAS(gemm_ab(h, rows, LF, Hd, w.dH1, P.W0, w.dX));
     {
       const unsigned nseg = (unsigned)((rows + kSeg - 1) / kSeg);
