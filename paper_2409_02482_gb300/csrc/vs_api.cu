@@ -12,6 +12,8 @@
 #include <map>
 #include <mutex>
 #include <new>
+
+#include <nvtx3/nvToolsExt.h>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -48,6 +50,15 @@ struct vs_object {
 namespace {
 
 thread_local std::string g_err;
+
+// NVTX range named after a public call (header-only NVTX3: without a tool
+// attached -- nsys, ncu --nvtx -- the push and pop cost a few nanoseconds).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 vs_status fail(vs_status code, const char* fmt, ...) {
   char buf[512];
@@ -660,6 +671,7 @@ vs_status vs_workspace_size(vs_ctx* ctx, const vs_object* const* objs, const vs_
 
 vs_status vs_render(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, const float* bg, float* out_rgba,
                     int32_t* hits, void* workspace, size_t ws_bytes, uint32_t flags, vs_stream_t stream) {
+  NvtxRange nvtx_range("vs_render");
   vs_status s = check_item(ctx, obj, cam);
   if (s != VS_OK) return s;
   if (!out_rgba) return fail(VS_ERR_INVALID_ARG, "out_rgba is NULL");
@@ -680,6 +692,7 @@ vs_status vs_render(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, con
 vs_status vs_render_layers(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, const float* bg, float* out_rgba,
                            int32_t* hits, float* layers, void* workspace, size_t ws_bytes, uint32_t flags,
                            vs_stream_t stream) {
+  NvtxRange nvtx_range("vs_render_layers");
   vs_status s = check_item(ctx, obj, cam);
   if (s != VS_OK) return s;
   if (!out_rgba || !layers) return fail(VS_ERR_INVALID_ARG, "out_rgba and layers are required");
@@ -701,6 +714,7 @@ vs_status vs_render_layers(vs_ctx* ctx, const vs_object* obj, const vs_camera* c
 vs_status vs_render_backward(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, const float* bg,
                              const int32_t* hits, const float* grad_rgb, float* const* grad_texels, float* loss,
                              void* workspace, size_t ws_bytes, uint32_t flags, vs_stream_t stream) {
+  NvtxRange nvtx_range("vs_render_backward");
   vs_status s = check_item(ctx, obj, cam);
   if (s != VS_OK) return s;
   for (int i = 0; i < obj->k; ++i)
@@ -724,6 +738,7 @@ vs_status vs_render_backward(vs_ctx* ctx, const vs_object* obj, const vs_camera*
 
 vs_status vs_render_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, const float* bg, int32_t do_backward,
                           void* workspace, size_t ws_bytes, uint32_t flags, vs_stream_t stream) {
+  NvtxRange nvtx_range("vs_render_batch");
   if (!ctx || !items) return fail(VS_ERR_INVALID_ARG, "NULL argument");
   if (n < 1) return fail(VS_ERR_INVALID_ARG, "n = %d < 1", n);
   int kmax = 1;
@@ -818,6 +833,7 @@ vs_status vs_tune_search(const vs_tuning* start, int32_t max_blocks_per_sm, vs_c
 vs_status vs_autotune_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, const float* bg, int32_t do_backward,
                             void* workspace, size_t ws_bytes, uint32_t flags, vs_stream_t stream, int32_t repeats,
                             vs_tuning* best) {
+  NvtxRange nvtx_range("vs_autotune_batch");
   if (repeats < 1 || repeats > 16) return fail(VS_ERR_INVALID_ARG, "repeats %d out of [1, 16]", repeats);
   if (!ctx || !items) return fail(VS_ERR_INVALID_ARG, "NULL argument");
   if (n < 1) return fail(VS_ERR_INVALID_ARG, "n = %d < 1", n);
@@ -954,6 +970,7 @@ vs_status vs_ntex_workspace_size(const vs_ntex_config* cfg, int32_t tex_w, int32
 vs_status vs_ntex_forward(vs_ctx* ctx, const vs_ntex_config* cfg, const float* params, int32_t tex_w, int32_t tex_h,
                           void* texels, int32_t dtype, int32_t pitch, int32_t ch0, void* workspace, size_t ws_bytes,
                           vs_stream_t stream) {
+  NvtxRange nvtx_range("vs_ntex_forward");
   vs_status s = check_ntex_call(ctx, cfg, params, tex_w, tex_h, texels, pitch, ch0, workspace, ws_bytes);
   if (s != VS_OK) return s;
   if (dtype != 0 && dtype != 1) return fail(VS_ERR_INVALID_ARG, "dtype %d is neither 0 (f32) nor 1 (f16)", dtype);
@@ -969,6 +986,7 @@ vs_status vs_ntex_forward(vs_ctx* ctx, const vs_ntex_config* cfg, const float* p
 vs_status vs_ntex_backward(vs_ctx* ctx, const vs_ntex_config* cfg, const float* params, int32_t tex_w, int32_t tex_h,
                            const float* grad_texels, int32_t pitch, int32_t ch0, float* grads, void* workspace,
                            size_t ws_bytes, vs_stream_t stream) {
+  NvtxRange nvtx_range("vs_ntex_backward");
   vs_status s = check_ntex_call(ctx, cfg, params, tex_w, tex_h, grad_texels, pitch, ch0, workspace, ws_bytes);
   if (s != VS_OK) return s;
   if (!grads || (uintptr_t)grads % 4) return fail(VS_ERR_INVALID_ARG, "grads NULL or misaligned");
@@ -983,6 +1001,7 @@ vs_status vs_ntex_backward(vs_ctx* ctx, const vs_ntex_config* cfg, const float* 
 
 vs_status vs_adam_step(vs_ctx* ctx, float* params, const float* grads, float* m, float* v, int64_t n, float lr,
                        float beta1, float beta2, float eps, int32_t step, vs_stream_t stream) {
+  NvtxRange nvtx_range("vs_adam_step");
   if (!ctx || !params || !grads || !m || !v) return fail(VS_ERR_INVALID_ARG, "NULL argument");
   if (n < 1 || step < 1) return fail(VS_ERR_INVALID_ARG, "n and step must be >= 1");
   if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps >= 0.0f))
@@ -1067,6 +1086,7 @@ vs_status noalloc_scratch(int device, char** out) {
 
 extern "C" vs_status vs_render_noalloc(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, const float* bg,
                                        float* out_rgba, int32_t* hits, uint32_t flags, vs_stream_t stream) {
+  NvtxRange nvtx_range("vs_render_noalloc");
   vs_status s = check_item(ctx, obj, cam);
   if (s != VS_OK) return s;
   if (!out_rgba) return fail(VS_ERR_INVALID_ARG, "out_rgba is NULL");
