@@ -59,6 +59,9 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-uneven", action="store_true", help="skip the uneven 32-object batch")
     p.add_argument("--no-baked", action="store_true", help="skip the baked-format forward leg")
+    p.add_argument("--baked-scale", type=float, default=1.0, help="shrink the baked leg (profiling only)")
+    p.add_argument("--baked-views", type=int, default=100)
+    p.add_argument("--no-latency", action="store_true", help="skip the single-view latency leg")
     p.add_argument("--no-ntex", action="store_true", help="skip the neural-texture fitting leg")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default work-unit sizes instead of autotuning them first")
@@ -123,11 +126,16 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # workload
 # ----------------------------------------------------------------------------
-def build_workload(args, device):
+def build_workload(args, device, rank=0, world=1):
+    """The C2 fitting workload of this rank: with N ranks the step's view
+    list has N x args.views views, dealt round-robin (shard.view_shard), so
+    every rank renders args.views views (weak scaling)."""
     import torch
     import synth
     import paper_2409_02482_gb300 as vs
-    (scene, cams), = synth.config_scene("c2", scale=args.scale, views=args.views, pitch=args.pitch)
+    from paper_2409_02482_gb300.shard import view_shard
+    (scene, cams), = synth.config_scene("c2", scale=args.scale, views=args.views * world, pitch=args.pitch)
+    cams = [cams[v] for v in view_shard(len(cams), rank, world)]
     ctx = vs.Context(device.index or 0)
     obj = vs.ShellObject.from_scene(ctx, scene, device=device)
     H, W = cams[0].height, cams[0].width
@@ -214,7 +222,7 @@ def uneven_batch(ctx, device, stream, steps, autotune=True):
     return out
 
 
-def baked_leg(ctx, device, stream, steps, peak, autotune=True):
+def baked_leg(ctx, device, stream, steps, peak, autotune=True, scale=1.0, views=100):
     """The paper's deployed path: forward rendering of baked assets (Sec. 3
     "Baking Textures"; its Tab. 2 real-time renderer) -- the c2 geometry and
     100 views at 800x800 with RGBA SH degree 3 bytes, 2048^2 base halving per
@@ -226,7 +234,7 @@ def baked_leg(ctx, device, stream, steps, peak, autotune=True):
     import oracle
     import synth
     import paper_2409_02482_gb300 as vs
-    (sc, cams), = synth.config_scene("c2b", views=100)
+    (sc, cams), = synth.config_scene("c2b", scale=scale, views=views)
     obj = vs.ShellObject.from_scene(ctx, sc, device=device)
     H, W = cams[0].height, cams[0].width
     outs = torch.empty((len(cams), H, W, 4), device=device)
@@ -245,7 +253,7 @@ def baked_leg(ctx, device, stream, steps, peak, autotune=True):
     ms = timed(step, steps, 3, stream, lambda: None)
     band_bytes = np.array([4 * (2 * band + 1) for band in range(4)])
     D = F = 0
-    sampled = [0, 49, 99]
+    sampled = sorted({0, len(cams) // 2, len(cams) - 1})
     for i in sampled:
         hits, _, _ = oracle.raster_scene(sc, cams[i])
         D += float((oracle.footprint_texels_baked(sc, cams[i], hits) * band_bytes).sum())
@@ -435,26 +443,90 @@ def texels_per_fragment(wl, n_views=3, threads=None):
 def cpu_baseline(wl, budget_s=20.0):
     """The oracle, as it stands, on a bounded sample of the workload: full
     fused step (raster, shade, L2 loss gradient, adjoint) for as many views
-    as fit in ~budget_s."""
+    as fit in ~budget_s.  Only the oracle's work is timed: each view's
+    target image is copied to the host and widened to FP64 outside the
+    clock."""
     import oracle
     threads = os.cpu_count() or 1
-    t_start = time.perf_counter()
+    dt = 0.0
     frags = 0
     views = 0
-    targets = wl["targets"].cpu().numpy().astype(np.float64)
     for i, cam in enumerate(wl["cams"]):
+        target = wl["targets"][i].cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
         rgba, hits, fr = oracle.render(wl["scene"], cam, threads=threads)
-        _, dL = oracle.l2_loss_grad(rgba, targets[i])
+        _, dL = oracle.l2_loss_grad(rgba, target)
         oracle.backward(wl["scene"], cam, hits, dL)
+        dt += time.perf_counter() - t0
         frags += int(fr.sum())
         views += 1
-        if time.perf_counter() - t_start > budget_s:
+        if dt > budget_s:
             break
-    dt = time.perf_counter() - t_start
     return {"value": frags / dt, "unit": "fragments/s", "cores": threads, "kind": "oracle",
             "sample": f"{views} of {len(wl['cams'])} views, full fused step (raster+shade on {threads} "
-                      f"threads, adjoint on 1), {dt:.1f} s",
+                      f"threads, adjoint on 1), {dt:.1f} s of oracle time",
             "images_per_s": views / dt}
+
+
+def single_view_latency(wl, stream, reps=50):
+    """Frame latency of ONE view (the paper's real-time figures are per
+    frame): vs_render of view 0 (forward, no hit buffer) and the fused
+    forward + backward of that view as a one-item vs_render_batch, each
+    timed alone with CUDA events around the call, the L2 flushed (a 256 MB
+    write) before every call; median over `reps`.  Also the same forward
+    replayed from a captured CUDA graph (launch overhead removed)."""
+    import torch
+    import paper_2409_02482_gb300 as vs
+    ctx, obj, cam = wl["ctx"], wl["obj"], wl["cams"][0]
+    dev = wl["targets"].device
+    ws1 = vs.make_workspace(ctx, [obj], [cam], device=dev)
+    out = torch.empty((wl["H"], wl["W"], 4), device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    one = vs.BatchItems([dict(obj=obj, cam=cam, out=out, grad_rgb=wl["targets"][0], grads=wl["grads"],
+                              loss=wl["losses"][0:1])])
+
+    def fwd():
+        vs.render(ctx, obj, cam, ws1, out=out, want_hits=False, stream=stream)
+
+    def fused():
+        vs.render_batch(ctx, one, ws1, do_backward=True, flags=vs.VS_FLAG_LOSS_L2, stream=stream)
+
+    def med(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(reps):
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    ms_fwd = med(fwd)
+    ms_fused = med(fused)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        fwd_side = lambda: vs.render(ctx, obj, cam, ws1, out=out, want_hits=False, stream=side)  # noqa: E731
+        fwd_side()
+        side.synchronize()
+        with torch.cuda.graph(g, stream=side):
+            fwd_side()
+    stream.wait_stream(side)
+    ms_graph = med(g.replay)
+    for t in wl["grads"]:
+        t.zero_()
+    wl["losses"].zero_()
+    del ws1, flush
+    return {"view": f"view 0 of the workload ({wl['W']}x{wl['H']}, k = {obj.k})",
+            "forward_ms": ms_fwd, "forward_frames_per_s": 1e3 / ms_fwd,
+            "forward_graph_ms": ms_graph, "forward_graph_frames_per_s": 1e3 / ms_graph,
+            "fused_fwd_bwd_ms": ms_fused, "fused_fwd_bwd_frames_per_s": 1e3 / ms_fused,
+            "timing": "CUDA events around each call, L2 flushed before each, median of %d" % reps}
 
 
 # ----------------------------------------------------------------------------
@@ -474,12 +546,25 @@ def run_ours(args):
         def barrier():
             pass
     stream = torch.cuda.current_stream()
-    wl = build_workload(args, device)
+    wl = build_workload(args, device, rank, ws_n)
     ctx, ws, items = wl["ctx"], wl["ws"], wl["items"]
     flags = vs.VS_FLAG_LOSS_L2
 
-    def step():
+    def render_views(views):
+        assert len(views) == len(wl["cams"])
         vs.render_batch(ctx, items, ws, do_backward=True, flags=flags, stream=stream)
+
+    if ws_n > 1:
+        # the view-sharded fitting step: this rank's views in one fused
+        # launch, then one all-reduce (sum) of the FP32 texel gradients
+        from paper_2409_02482_gb300.shard import ShardedFittingStep
+        sharded = ShardedFittingStep(wl["grads"], render_views, args.views * ws_n)
+
+        def step():
+            sharded()
+    else:
+        def step():
+            render_views(list(range(len(wl["cams"]))))
 
     def step_fwd():
         vs.render_batch(ctx, items, ws, do_backward=False, stream=stream)
@@ -541,6 +626,10 @@ def run_ours(args):
         stream.wait_event(ready[b])
         los[b].zero_()
         vs.render_batch(ctx, bufs[b], ws, do_backward=True, flags=flags, stream=stream)
+        if ws_n > 1:   # the sharded step's gradient exchange
+            import torch.distributed as dist
+            for g in wl["grads"]:
+                dist.all_reduce(g)
         host_loss[b].copy_(los[b], non_blocking=True)
         done[b].record(stream)
 
@@ -593,6 +682,8 @@ def run_ours(args):
                              "fwd_bwd_fragments_per_s": frags / (ms_plain * 1e-3),
                              "fwd_fragments_per_s": frags / (ms_plain_fwd * 1e-3)}
         res["batched_vs_plain"] = {"fwd_bwd": ms_plain / ms, "fwd": ms_plain_fwd / ms_fwd}
+    if not args.no_latency and rank == 0:
+        res["single_view_latency"] = single_view_latency(wl, stream)
     if not args.no_uneven and rank == 0:
         res["uneven_batch"] = uneven_batch(ctx, device, stream, max(3, args.steps // 10),
                                            autotune=not args.no_autotune)
@@ -602,7 +693,8 @@ def run_ours(args):
                                                       tensor_cores=True)
     if not args.no_baked and rank == 0:
         res["baked_forward"] = baked_leg(ctx, device, stream, max(5, args.steps // 3), peaks()[0],
-                                         autotune=not args.no_autotune)
+                                         autotune=not args.no_autotune, scale=args.baked_scale,
+                                         views=args.baked_views)
 
     if rank != 0:
         if ws_n > 1:
@@ -636,7 +728,9 @@ def run_ours(args):
                    "one persistent launch", "texel_storage": "f16", "views": n_views,
                    "image": f"{wl['W']}x{wl['H']}", "shells": wl["obj"].k,
                    "tris_per_shell": [int(s.tris.shape[0]) for s in wl["scene"].shells],
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws_n}",
+                   "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": (f"views sharded over {ws_n} ranks ({n_views} each), one gradient "
+                                   f"all-reduce per step" if ws_n > 1 else "1 GPU"),
                    "tuning": tuning or "default (256 tris, 256 px, occupancy maximum)"},
         "images_per_s": n_views * ws_n / (ms * 1e-3),
         "fragments_per_step": frags,

@@ -413,18 +413,22 @@ vs_status vs_adam_step(vs_ctx* ctx, float* params, const float* grads, float* m,
 /* --- allocation-free forward ------------------------------------------------- */
 
 /* vs_render for callers that cannot allocate device memory at all, and so
- * cannot pass a workspace: code running where cudaMalloc is not allowed (a
- * host callback, a real-time loop under a no-allocation rule) or inside a
- * framework that owns all device memory and lends none out.  The paper has no
- * counterpart; this is a deployment convenience.
+ * cannot pass a workspace: a render loop that must not allocate once it is
+ * running (allocation can block the loop and fragment memory), or a plug-in
+ * inside a host framework that owns and pools every byte of device memory
+ * and lends none out.  The paper has no counterpart; this is a deployment
+ * convenience.
  *   Scratch: a fixed 16 MiB array in device memory that every GPU loading the
  *   library holds until the process exits.  One call needs about
  *   8 k H W + 16 sum(V) bytes plus a few KB (e.g. k = 3 shells at 512x512
  *   with up to 300k vertices); larger requests return VS_ERR_OVERFLOW with the
  *   needed size in vs_last_error(), before anything is enqueued.
- *   First call: the first call on each device looks up the array's device
- *   address (cudaGetSymbolAddress); make that first call before any stream
- *   capture.
+ *   First calls: the first call on each device looks up the array's device
+ *   address (cudaGetSymbolAddress), and the first render of each object --
+ *   through this call or any other -- reads its vertex positions once with a
+ *   blocking device-to-host copy (vs_load_shells).  Make both first calls
+ *   before any stream capture, from ordinary host code (no CUDA call is
+ *   allowed inside a stream callback).
  *   Sharing: every call uses the same array and leaves its contents there;
  *   each call re-initialises what must start at zero.  Calls that overlap on
  *   the GPU (e.g. on two streams of one device) race and corrupt each

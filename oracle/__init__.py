@@ -239,10 +239,23 @@ def render(scene, cam, bg=(0.0, 0.0, 0.0), threads: Optional[int] = None, flags:
 
 
 def backward(scene, cam, hits: np.ndarray, grad_rgb: np.ndarray, bg=(0.0, 0.0, 0.0),
-             flags: int = 0) -> List[np.ndarray]:
+             flags: int = 0, with_scale: bool = False, gmag: Optional[np.ndarray] = None,
+             aw_err: float = 0.0):
     """dL/d(texel values) given dL/d(output rgb) -- the texture-fitting
     gradient of Sec. 3 "Texturing Meshes".  Returns one FP64 array per shell,
-    shaped like its texture."""
+    shaped like its texture.
+
+    with_scale: also return the gradient's per-texel error scales as
+    (grads, (S_w, S_1)): over the (fragment, tap) terms that reach a texel
+    value, S_w sums |w| M and S_1 sums M, M being the term's product without
+    the tap weight w, with every factor taken by absolute value and every
+    difference as the sum of its terms' absolute values (see
+    oracle_backward).  An FP32 evaluation errs by a small multiple of
+    epsilon times S_w plus its tap-weight error times S_1.  gmag [H, W, 3]:
+    the size of each pixel's output gradient before cancellation (default
+    |grad_rgb|; l2_loss_scale for the L2 loss).  aw_err: with ALPHA_ATTEN,
+    an absolute error of each alpha_w that the scales allow for.  The
+    scales do not change the gradient."""
     refs = _ShellRefs(scene.shells)
     H, W = cam.height, cam.width
     hits = np.ascontiguousarray(hits, np.int32)
@@ -250,13 +263,23 @@ def backward(scene, cam, hits: np.ndarray, grad_rgb: np.ndarray, bg=(0.0, 0.0, 0
     assert g.shape == (H, W, 3)
     grads = [np.zeros(s.tex.shape, np.float64) for s in scene.shells]
     ptrs = (ctypes.c_void_p * scene.k)(*[gr.ctypes.data for gr in grads])
+    scales = [np.zeros(s.tex.shape, np.float64) for s in scene.shells] if with_scale else None
+    reach = [np.zeros(s.tex.shape, np.float64) for s in scene.shells] if with_scale else None
+    sptrs = (ctypes.c_void_p * scene.k)(*[a.ctypes.data for a in scales]) if with_scale else None
+    rptrs = (ctypes.c_void_p * scene.k)(*[a.ctypes.data for a in reach]) if with_scale else None
+    gm = None
+    if gmag is not None:
+        gm = np.ascontiguousarray(gmag, np.float64)
+        assert gm.shape == (H, W, 3)
     bgv = np.ascontiguousarray(bg, np.float64)
     c = ocam(cam)
     r = lib().oracle_backward(refs.arr, ctypes.c_int32(scene.k), ctypes.byref(c), _ptr(bgv), _ptr(hits),
-                              _ptr(g), ptrs, ctypes.c_int32(flags))
+                              _ptr(g), ptrs, ctypes.c_int32(flags),
+                              _ptr(gm) if gm is not None else ctypes.c_void_p(0), sptrs, rptrs,
+                              ctypes.c_double(aw_err))
     if r != 0:
         raise ValueError("the baked byte format (FMT_SH_U8) has no gradient")
-    return grads
+    return (grads, (scales, reach)) if with_scale else grads
 
 
 def l2_loss_grad(rgba: np.ndarray, target_rgb: np.ndarray):
@@ -264,6 +287,13 @@ def l2_loss_grad(rgba: np.ndarray, target_rgb: np.ndarray):
     d = rgba[..., :3] - target_rgb
     n = d.size
     return float((d * d).sum() / n), 2.0 * d / n
+
+
+def l2_loss_scale(rgba: np.ndarray, target_rgb: np.ndarray):
+    """Size of each pixel's L2-loss gradient before cancellation,
+    2 (|C| + |target|) / n: the gmag of backward's error scale when the
+    gradient is formed from a computed colour and a target."""
+    return 2.0 * (np.abs(rgba[..., :3]) + np.abs(target_rgb)) / (rgba[..., :3].size)
 
 
 def l1_loss_grad(rgba: np.ndarray, target_rgb: np.ndarray):

@@ -685,8 +685,28 @@ int oracle_shade(const OShell* shells, int32_t k, const OCam* cam, const double*
 
 // Adjoint of oracle_shade w.r.t. the texel values.  grad_rgb: [H, W, 3] =
 // dL/d(output rgb).  grad_tex[i]: [th, tw, pitch] FP64, accumulated into.
+//
+// Optional error scales (abs_tex, reach_tex non-NULL, same layout as
+// grad_tex), a yardstick for comparing gradients, not part of the method.
+// For every texel value and every (fragment, tap) that reaches it, let M be
+// the SAME product as the gradient term with every factor replaced by its
+// absolute value and every difference by the sum of the absolute values of
+// its terms (c_i . g - A_{i+1} . g -> |c_i| . |g| + |A_{i+1}| . |g|, the
+// colour seen behind counted with |bg|), without the tap weight.
+// abs_tex accumulates |w| M and reach_tex accumulates M.  A floating-point
+// evaluation of the adjoint in any order errs per texel value by a small
+// multiple of machine epsilon times the first sum, also where terms cancel,
+// plus the error of its tap weights times the second.  gmag [H, W, 3]
+// (NULL = |grad_rgb|) gives the size of each pixel's output gradient before
+// cancellation (e.g. (|C| + |target|) 2 / n for the L2 loss).  With the
+// transparency attenuation on, aw_err is an absolute error of each alpha_w
+// that the scales allow for: every term of a fragment's adjoint scales with
+// its alpha_w, and the transmittances with the (1 - alpha_j) of the pixel's
+// other fragments, so the fragment's M is multiplied by
+// 1 + aw_err (1 / alpha_w + sum_j 1 / (1 - alpha_j)).
 int oracle_backward(const OShell* shells, int32_t k, const OCam* cam, const double* bg,
-                    const int32_t* hits, const double* grad_rgb, double* const* grad_tex, int32_t flags) {
+                    const int32_t* hits, const double* grad_rgb, double* const* grad_tex, int32_t flags,
+                    const double* gmag, double* const* abs_tex, double* const* reach_tex, double aw_err) {
   // the baked bytes are a deployment format: no gradient (the paper fits
   // continuous textures and quantises when baking)
   for (int i = 0; i < k; ++i)
@@ -707,43 +727,76 @@ int oracle_backward(const OShell* shells, int32_t k, const OCam* cam, const doub
       double v[3], Y[16];
       ray_dir(*cam, x, y, v);
       sh_basis(maxdeg, v, Y);
-      double T = 1.0;
+      double T = 1.0, sens = 0.0;   // sens: error scale only
       for (int i = 0; i < k; ++i) {
         int32_t h = hits[(size_t)i * H * W + y * W + x];
         hit[i] = h >= 0 && shade_fragment(shells[i], *cam, sv[i], h, x, y, Y, v, flags, &fr[i]);
         Tin[i] = T;
-        if (hit[i]) T *= (1.0 - fr[i].alpha);
+        if (hit[i]) {
+          T *= (1.0 - fr[i].alpha);
+          sens += 1.0 / std::max(1.0 - fr[i].alpha, 1e-300);
+        }
       }
       // back to front: A = colour seen behind shell i (bg behind the last)
       double A[3] = {bg[0], bg[1], bg[2]};
+      double gm[3], Am[3];   // error scale only
+      for (int ch = 0; ch < 3; ++ch) {
+        gm[ch] = gmag ? gmag[3 * (y * W + x) + ch] : std::fabs(g[ch]);
+        Am[ch] = std::fabs(bg[ch]);
+      }
       for (int i = k - 1; i >= 0; --i) {
         if (!hit[i]) continue;
         const Frag& f = fr[i];
         const OShell& s = shells[i];
-        double gc[3], ga = 0.0;
+        double gc[3], ga = 0.0, gcm[3], gam = 0.0;
         for (int ch = 0; ch < 3; ++ch) {
           gc[ch] = Tin[i] * f.alpha * g[ch];                 // dL/dc_i
           ga += Tin[i] * (f.rgb[ch] - A[ch]) * g[ch];         // dL/dalpha_i
+          gcm[ch] = Tin[i] * f.alpha * gm[ch];
+          gam += Tin[i] * (std::fabs(f.rgb[ch]) + Am[ch]) * gm[ch];
         }
-        for (int ch = 0; ch < 3; ++ch) A[ch] = f.alpha * f.rgb[ch] + (1.0 - f.alpha) * A[ch];
+        for (int ch = 0; ch < 3; ++ch) {
+          A[ch] = f.alpha * f.rgb[ch] + (1.0 - f.alpha) * A[ch];
+          Am[ch] = f.alpha * std::fabs(f.rgb[ch]) + (1.0 - f.alpha) * Am[ch];
+        }
         int nv = num_values(s);
-        double dval[64];
+        double dval[64], dmag[64];
         // alpha = alpha_raw * atten, atten independent of the texels
         if (s.fmt == FMT_RGBA_F32) {
           dval[0] = gc[0]; dval[1] = gc[1]; dval[2] = gc[2]; dval[3] = ga * f.atten;
+          dmag[0] = gcm[0]; dmag[1] = gcm[1]; dmag[2] = gcm[2]; dmag[3] = gam * f.atten;
         } else {
           int nb = (s.degree + 1) * (s.degree + 1);
-          dval[0] = ga * f.atten * f.alpha_raw * (1.0 - f.alpha_raw);
+          const double sa = f.alpha_raw * (1.0 - f.alpha_raw);
+          dval[0] = ga * f.atten * sa;
+          dmag[0] = gam * f.atten * sa;
           for (int ch = 0; ch < 3; ++ch) {
-            double dz = gc[ch] * f.rgb[ch] * (1.0 - f.rgb[ch]);
-            for (int m = 0; m < nb; ++m) dval[1 + 3 * m + ch] = dz * Y[m];
+            const double sc = f.rgb[ch] * (1.0 - f.rgb[ch]);
+            double dz = gc[ch] * sc;
+            for (int m = 0; m < nb; ++m) {
+              dval[1 + 3 * m + ch] = dz * Y[m];
+              dmag[1 + 3 * m + ch] = gcm[ch] * sc * std::fabs(Y[m]);
+            }
           }
+        }
+        if ((flags & OFLAG_ALPHA_ATTEN) && aw_err > 0.0) {
+          const double grow = 1.0 + aw_err * (1.0 / std::max(f.atten, 1e-300) + sens);
+          for (int ch = 0; ch < nv; ++ch) dmag[ch] *= grow;
         }
         for (int b = 0; b < 2; ++b)
           for (int a = 0; a < 2; ++a) {
             double w = tap_weight(f.fp, a, b);
-            double* gt = grad_tex[i] + ((size_t)f.fp.y[b] * s.tw + (size_t)f.fp.x[a]) * s.pitch;
+            const size_t off = ((size_t)f.fp.y[b] * s.tw + (size_t)f.fp.x[a]) * s.pitch;
+            double* gt = grad_tex[i] + off;
             for (int ch = 0; ch < nv; ++ch) gt[ch] += w * dval[ch];
+            if (abs_tex) {
+              double* at = abs_tex[i] + off;
+              for (int ch = 0; ch < nv; ++ch) at[ch] += std::fabs(w) * dmag[ch];
+            }
+            if (reach_tex) {
+              double* rt = reach_tex[i] + off;
+              for (int ch = 0; ch < nv; ++ch) rt[ch] += dmag[ch];
+            }
           }
       }
     }

@@ -1042,10 +1042,9 @@ vs_status vs_read_stats(void* workspace, vs_stream_t stream, int32_t reset, vs_s
 // ===========================================================================
 // Allocation-free forward (vs_render_noalloc).
 //
-// Some callers cannot allocate device memory: code that runs where
-// cudaMalloc is not allowed (a host callback, a real-time loop under a
-// no-allocation rule) or inside a framework that owns every byte of device
-// memory and lends none out.  They cannot hand vs_render a workspace, so this
+// Some callers cannot allocate device memory: a render loop that must not
+// allocate once it is running, or a plug-in inside a framework that owns and
+// pools every byte of device memory and lends none out.  They cannot hand vs_render a workspace, so this
 // entry point keeps its scratch in a fixed device array instead.  The array
 // exists once per GPU that loads the library and stays until the process
 // exits; its size is the limit on what one call may render.

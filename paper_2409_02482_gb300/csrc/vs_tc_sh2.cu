@@ -1,4 +1,4 @@
-// Shading kernels for batches whose shells all hold SH degree 2 FP16 texels, 16-byte loads.
+// Shading kernels for batches whose shells all hold SH degree 2 FP16 texels (32-byte aligned: 256-bit loads).
 #define VS_TC (vsd::TC_SH0 + 2)
 #define VS_TC_OPS kTcSh2
 #include "vs_tc_impl.cuh"

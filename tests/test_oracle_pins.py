@@ -1179,3 +1179,64 @@ def test_l1_at_most_root_l2():
     tgt = np.full((2, 2, 3), 0.5)
     flat[..., :3] = tgt + np.where(rng.random((2, 2, 3)) < 0.5, -0.25, 0.25)
     assert oracle.l1_loss_grad(flat, tgt)[0] == pytest.approx(math.sqrt(oracle.l2_loss_grad(flat, tgt)[0]))
+
+
+def test_backward_error_scales():
+    """The per-texel error scales of the adjoint (the yardstick of the GPU
+    gradient bars; no part of the method): they leave the gradient unchanged,
+    bound it (|grad| <= S_w <= S_1, zero exactly where nothing reaches), equal
+    |grad| where no term can cancel (colour values of RGBA textures and the
+    Y_0 coefficients of SH textures under a nonnegative output gradient), sum
+    over a constant texture to the per-fragment magnitudes -- the alpha one
+    T_i (|c_i| + |A_{i+1}|) . |g| -- and count four taps per fragment."""
+    bg = np.array([0.3, 0.1, 0.5])
+    # (1) random textures, signed gradient
+    for fmt, degree in ((FMT_RGBA_F32, 0), (FMT_SH_F16, 2)):
+        sc = _tiny_scene(fmt, degree, seed=40 + degree)
+        cam = synth.look_at((0.7, -2.8, 0.9), width=24, height=20)
+        hits, _, _ = oracle.raster_scene(sc, cam)
+        g = np.random.default_rng(41).normal(size=(cam.height, cam.width, 3))
+        plain = oracle.backward(sc, cam, hits, g, bg=bg)
+        grads, (sw, s1) = oracle.backward(sc, cam, hits, g, bg=bg, with_scale=True)
+        same, _ = oracle.backward(sc, cam, hits, g, bg=bg, with_scale=True, gmag=np.abs(g))
+        for a, b, c, w, r in zip(plain, grads, same, sw, s1):
+            assert np.array_equal(a, b) and np.array_equal(a, c)
+            assert np.all(np.abs(a) <= w * (1 + 1e-12)) and np.all(w <= r * (1 + 1e-12))
+            assert np.array_equal(w == 0, r == 0) and np.all(a[w == 0] == 0)
+        assert max(float(w.max()) for w in sw) > 0
+        # (2) nonnegative output gradient: no cancellation in the colour terms
+        gp = np.abs(g)
+        grads, (sw, _) = oracle.backward(sc, cam, hits, gp, bg=bg, with_scale=True)
+        cols = slice(0, 3) if fmt == FMT_RGBA_F32 else slice(1, 4)
+        for a, w in zip(grads, sw):
+            assert np.allclose(np.abs(a[..., cols]), w[..., cols], rtol=1e-12, atol=0)
+        # the alpha terms do cancel somewhere: strictly larger scale there
+        assert any(np.any(w[..., 3 if fmt == FMT_RGBA_F32 else 0] > np.abs(a[..., 3 if fmt == FMT_RGBA_F32 else 0]) * 1.01)
+                   for a, w in zip(grads, sw))
+    # (3) constant RGBA textures: closed forms of the sums
+    geo = synth.concentric_icospheres([1.0, 0.9, 0.8], subdiv=2)
+    colors = [np.array([0.9, 0.2, 0.1]), np.array([0.1, 0.8, 0.3]), np.array([0.2, 0.3, 0.95])]
+    alphas = [0.35, 0.6, 0.8]
+    sc = Scene([constant_shell(p, u, t, list(c) + [a], dtype=np.float64)
+                for (p, u, t), c, a in zip(geo, colors, alphas)])
+    cam = synth.look_at((1.1, -2.6, 0.7), width=32, height=32)
+    hits, _, _ = oracle.raster_scene(sc, cam)
+    g = np.random.default_rng(13).normal(size=(32, 32, 3))
+    _, (sw, s1) = oracle.backward(sc, cam, hits, g, bg=bg, with_scale=True)
+    want_rgb, want_a = np.zeros((3, 3)), np.zeros(3)
+    for y in range(32):
+        for x in range(32):
+            on = [i for i in range(3) if hits[i, y, x] >= 0]
+            T, Ts = 1.0, {}
+            for i in on:
+                Ts[i] = T
+                T *= 1 - alphas[i]
+            A = bg.copy()
+            for i in reversed(on):
+                want_rgb[i] += Ts[i] * alphas[i] * np.abs(g[y, x])
+                want_a[i] += Ts[i] * (np.abs(colors[i]) + np.abs(A)) @ np.abs(g[y, x])
+                A = alphas[i] * colors[i] + (1 - alphas[i]) * A
+    for i in range(3):
+        assert np.allclose(sw[i][..., :3].sum((0, 1)), want_rgb[i], rtol=1e-10)
+        assert abs(sw[i][..., 3].sum() - want_a[i]) < 1e-10 * want_a[i]
+        assert np.allclose(s1[i].sum((0, 1)), 4 * sw[i].sum((0, 1)), rtol=1e-10)

@@ -1,10 +1,14 @@
 """vs_render_noalloc: the forward entry point for callers that cannot allocate
-device memory (code where cudaMalloc is not allowed, or a framework that owns
-all device memory), so cannot pass a workspace.  It keeps its scratch in a
-fixed device array shared by every call.  These checks call it through the
-C ABI and compare it with vs_render on two calls in a row -- the second call
-must not see the first call's leftovers -- and check that a request larger
-than the fixed array is refused before anything runs.
+device memory -- a render loop that must not allocate once it is running, or
+a host framework that owns and pools every byte of device memory and lends
+none out -- and so cannot pass a workspace.  It keeps its scratch in a fixed
+device array shared by every call.  These checks call it through the C ABI
+and compare it with vs_render on two calls in a row: the second call must not
+see the first call's leftovers.  Both entry points run the same kernels on the
+same inputs, so colours must agree bit for bit, not just to a tolerance.  The
+calls cover a hit buffer and none, and a close-up whose near plane cuts the
+shells (the generic kernels with clipping).  A request larger than the fixed
+array is refused before anything runs.
 
 This file is collected last on purpose: it must pass on its own in a fresh
 process and after every other test.
@@ -40,21 +44,31 @@ def test_noalloc_matches_vs_render_on_consecutive_calls():
     ctx = vs.Context(0)
     (scene, cams), = synth.config_scene("c1")
     obj = vs.ShellObject.from_scene(ctx, scene)
-    # two different views in a row: different sizes, so stale scratch from the
-    # first call would show up in the second
-    views = [cams[0], synth.look_at((1.0, 2.5, 1.2), width=200, height=150)]
+    # views in a row with different sizes, so stale scratch from one call
+    # would show up in the next; the last is a close-up with the near plane
+    # through the shells (clipping kernels), rendered without a hit buffer
+    views = [(cams[0], True),
+             (synth.look_at((1.0, 2.5, 1.2), width=200, height=150), True),
+             (synth.look_at((0.0, -1.45, 0.25), width=96, height=80, fov_y_deg=60.0, znear=0.6), True),
+             (synth.look_at((0.9, -0.9, 0.6), width=77, height=64, fov_y_deg=70.0, znear=0.55), False),
+             (cams[0], False)]
     bg = (0.3, 0.2, 0.1)
-    for cam in views:
+    clipped = 0
+    for cam, with_hits in views:
         ws = vs.make_workspace(ctx, [obj], [cam])
         ref_out, ref_hits = vs.render(ctx, obj, cam, ws, bg=bg)
+        clipped += vs.read_stats(ws)["tris_clipped"]
         out = torch.full((cam.height, cam.width, 4), float("nan"), device="cuda")
-        hits = torch.full((obj.k, cam.height, cam.width), -7, dtype=torch.int32, device="cuda")
+        hits = (torch.full((obj.k, cam.height, cam.width), -7, dtype=torch.int32, device="cuda")
+                if with_hits else None)
         assert _call_noalloc(lib, ctx, obj, cam, bg, out, hits) == _abi.VS_OK, lib.vs_last_error()
         torch.cuda.synchronize()
-        assert torch.equal(hits, ref_hits)
-        # same kernels on the same inputs: agreement to the colour bar (1e-5)
-        assert (out - ref_out).abs().max().item() <= 1e-5
-        assert (hits >= 0).any()
+        if with_hits:
+            assert torch.equal(hits, ref_hits)
+        # same kernels, same inputs, same arithmetic: identical bits
+        assert torch.equal(out, ref_out), (out - ref_out).abs().max().item()
+        assert (ref_hits >= 0).any()
+    assert clipped > 0, "the close-ups must exercise near-plane clipping"
 
 
 def test_noalloc_refuses_requests_beyond_its_fixed_scratch():
