@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--scale", type=float, default=1.0, help="shrink the workload (testing only)")
     p.add_argument("--pitch", type=int, default=32,
                    help="FP16 values per texel in memory (28 used; 32 = 64-byte texels)")
+    p.add_argument("--grad-pitch", type=int, default=0,
+                   help="FP32 values per gradient texel (0 = the texel pitch; 28 = no padding)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-uneven", action="store_true", help="skip the uneven 32-object batch")
@@ -62,6 +64,11 @@ def parse():
     p.add_argument("--baked-scale", type=float, default=1.0, help="shrink the baked leg (profiling only)")
     p.add_argument("--baked-views", type=int, default=100)
     p.add_argument("--no-latency", action="store_true", help="skip the single-view latency leg")
+    p.add_argument("--no-c3", action="store_true", help="skip the full-size k=9 / 1024^2 fitting leg")
+    p.add_argument("--no-c5", action="store_true", help="skip the full-size k=9 / 4K / SH3 leg")
+    p.add_argument("--c5-views", type=int, default=256)
+    p.add_argument("--c5-ws-gb", type=float, default=48.0,
+                   help="workspace budget of the 4K leg (its batch runs in workspace-sized runs)")
     p.add_argument("--no-ntex", action="store_true", help="skip the neural-texture fitting leg")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default work-unit sizes instead of autotuning them first")
@@ -137,13 +144,13 @@ def build_workload(args, device, rank=0, world=1):
     (scene, cams), = synth.config_scene("c2", scale=args.scale, views=args.views * world, pitch=args.pitch)
     cams = [cams[v] for v in view_shard(len(cams), rank, world)]
     ctx = vs.Context(device.index or 0)
-    obj = vs.ShellObject.from_scene(ctx, scene, device=device)
+    obj = vs.ShellObject.from_scene(ctx, scene, device=device, grad_pitch=args.grad_pitch or None)
     H, W = cams[0].height, cams[0].width
     g = torch.Generator(device=device).manual_seed(1)
     targets = torch.rand((len(cams), H, W, 3), device=device, generator=g)
     outs = torch.empty((len(cams), H, W, 4), device=device)
     losses = torch.zeros(len(cams), device=device)
-    grads = [torch.zeros(t.shape, dtype=torch.float32, device=device) for t in obj.textures]
+    grads = obj.zero_grads()
     items = [dict(obj=obj, cam=c, out=outs[i], grad_rgb=targets[i], grads=grads, loss=losses[i:i + 1])
              for i, c in enumerate(cams)]
     ws = vs.make_workspace(ctx, [obj] * len(cams), cams, device=device)
@@ -272,6 +279,117 @@ def baked_leg(ctx, device, stream, steps, peak, autotune=True, scale=1.0, views=
                         "frac": achieved / peak, "texel_bytes_per_fragment": per_frag,
                         "algorithmic_bytes_per_launch": b_alg, "d_sampled_views": sampled}}
     del ws, items, outs, obj
+    torch.cuda.empty_cache()
+    return out
+
+
+def device_textures(scene, device, seed, sigma=0.3):
+    """FP16 texel arrays shaped like the scene's, every real value drawn
+    N(0, sigma) on the device (the generator's distribution; only shape and
+    distribution matter for timing), padding zero."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(seed)
+    out = []
+    for s_ in scene.shells:
+        h, w, pitch = s_.tex.shape
+        t = torch.zeros((h, w, pitch), dtype=torch.float16, device=device)
+        for r0 in range(0, h, 1024):   # bounded FP32 temporaries
+            r1 = min(h, r0 + 1024)
+            t[r0:r1, :, :s_.channels] = (sigma * torch.randn((r1 - r0, w, s_.channels), device=device,
+                                                              generator=g)).half()
+        out.append(t)
+    return out
+
+
+def config_leg(name, ctx, device, stream, steps, peak, autotune=True, views=None, ws_gb=None):
+    """A full-size fitting configuration besides the main one, forward + adjoint
+    and forward only, as batched persistent launches:
+      c3: 9 shells x ~500k faces, 2048^2 SH2 FP16 (texel pitch 32, gradient
+          pitch 28), 64 views at 1024^2 on the hemisphere at 4, L2 loss
+          against targets rendered from a second seeded texture set;
+      c5: 9 shells x ~2M faces, 4096^2 SH3 FP16 (texel pitch 64, gradient
+          pitch 52), 256 views at 3840x2160 on the sphere at 3.5, L2 loss
+          against random targets; the batch runs in workspace-sized runs
+          (ws_gb) -- 256 views at 4K would need ~600 MB of visibility words
+          and ~1.2 GB of triangle records per view at once.
+    Texel values are drawn on the device.  Roofline bytes as for the main
+    workload with D from the oracle's footprint count on the middle view."""
+    import torch
+    import oracle
+    import synth
+    import paper_2409_02482_gb300 as vs
+    pitch, gpitch = {"c3": (32, 28), "c5": (64, 52)}[name]
+    (sc, cams), = synth.config_scene(name, views=views, pitch=pitch, textures=False)
+    texs = device_textures(sc, device, seed=10)
+    shells = [dict(pos=torch.from_numpy(s_.pos).to(device), uv=torch.from_numpy(s_.uv).to(device),
+                   tris=torch.from_numpy(s_.tris).to(device), tex=t, fmt=s_.fmt, degree=s_.degree,
+                   grad_pitch=gpitch) for s_, t in zip(sc.shells, texs)]
+    obj = vs.ShellObject(ctx, shells)
+    n, H, W = len(cams), cams[0].height, cams[0].width
+    per_item = vs.workspace_size(ctx, [obj], cams[:1])
+    full = vs.workspace_size(ctx, [obj] * n, cams)
+    budget = full if ws_gb is None else min(full, max(int(ws_gb * 2 ** 30), 2 * per_item))
+    ws = torch.zeros(budget, dtype=torch.uint8, device=device)
+    if name == "c3":   # targets: the same views rendered from a second seeded texture set
+        tex2 = device_textures(sc, device, seed=11)
+        obj2 = vs.ShellObject(ctx, [dict(s_, tex=t) for s_, t in zip(shells, tex2)])
+        t4 = torch.empty((n, H, W, 4), device=device)
+        vs.render_batch(ctx, [dict(obj=obj2, cam=c, out=t4[i]) for i, c in enumerate(cams)], ws, stream=stream)
+        targets = t4[..., :3].contiguous()
+        del t4, tex2, obj2
+    else:
+        targets = torch.rand((n, H, W, 3), device=device, generator=torch.Generator(device=device).manual_seed(12))
+    outs = torch.empty((n, H, W, 4), device=device)
+    grads = obj.zero_grads()
+    losses = torch.zeros(n, device=device)
+    items = vs.BatchItems([dict(obj=obj, cam=c, out=outs[i], grad_rgb=targets[i], grads=grads,
+                                loss=losses[i:i + 1]) for i, c in enumerate(cams)])
+    fwd_items = vs.BatchItems([dict(obj=obj, cam=c, out=outs[i]) for i, c in enumerate(cams)])
+    flags = vs.VS_FLAG_LOSS_L2
+    tuning = None
+    if autotune:   # on the items of one run (the shape carries over to every run)
+        m = max(1, min(n, budget // per_item - 1))
+        sub = vs.BatchItems([dict(obj=obj, cam=c, out=outs[i], grad_rgb=targets[i], grads=grads,
+                                  loss=losses[i:i + 1]) for i, c in enumerate(cams[:m])])
+        sub_f = vs.BatchItems([dict(obj=obj, cam=c, out=outs[i]) for i, c in enumerate(cams[:m])])
+        tuning = {"fwd_bwd": vs.autotune_batch(ctx, sub, ws, do_backward=True, flags=flags,
+                                               stream=stream).as_dict(),
+                  "fwd": vs.autotune_batch(ctx, sub_f, ws, stream=stream).as_dict(), "tuned_on_views": m}
+        for g_ in grads:
+            g_.zero_()
+
+    def step():
+        vs.render_batch(ctx, items, ws, do_backward=True, flags=flags, stream=stream)
+
+    def step_fwd():
+        vs.render_batch(ctx, fwd_items, ws, stream=stream)
+
+    vs.read_stats(ws, reset=True)
+    step()
+    st = vs.read_stats(ws, reset=True)
+    assert st["device_status"] == 0, st
+    frags, launches = st["fragments"], st["launches"]
+    ms = timed(step, steps, 1, stream, lambda: None)
+    ms_f = timed(step_fwd, steps, 1, stream, lambda: None)
+    mid = n // 2
+    hits, _, _ = oracle.raster_scene(sc, cams[mid])
+    d_per_frag = float(oracle.footprint_texels(sc, cams[mid], hits).sum()) / max(int((hits >= 0).sum()), 1)
+    wl = {"scene": sc, "cams": cams, "H": H, "W": W}
+    b_alg, parts = algorithmic_bytes(wl, frags / n, d_per_frag, True)
+    b_fwd, _ = algorithmic_bytes(wl, frags / n, d_per_frag, False)
+    out = {"workload": synth.CONFIGS[name], "views": n, "image": f"{W}x{H}", "shells": obj.k,
+           "tris_per_shell": int(sc.shells[0].tris.shape[0]), "texture": f"{sc.shells[0].tex.shape[1]}^2 SH"
+           f"{sc.shells[0].degree} FP16, texel pitch {pitch}, gradient pitch {gpitch}",
+           "workspace_bytes": budget, "workspace_bytes_one_launch": full, "launches_per_step": launches,
+           "tuning": tuning, "fragments_per_step": frags,
+           "fwd_bwd": {"ms_per_step": ms, "fragments_per_s": frags / (ms * 1e-3), "images_per_s": n / (ms * 1e-3),
+                       "roofline": {"bound": "hbm", "achieved": b_alg / (ms * 1e-3) / 1e9, "peak": peak,
+                                    "unit": "GB/s", "frac": b_alg / (ms * 1e-3) / 1e9 / peak,
+                                    "algorithmic_bytes_per_step": b_alg, "bytes_breakdown": parts}},
+           "fwd": {"ms_per_step": ms_f, "fragments_per_s": frags / (ms_f * 1e-3), "images_per_s": n / (ms_f * 1e-3),
+                   "roofline_frac": b_fwd / (ms_f * 1e-3) / 1e9 / peak},
+           "distinct_texels_per_fragment": d_per_frag, "d_sampled_views": [mid]}
+    del items, fwd_items, ws, outs, targets, grads, obj, texs, shells
     torch.cuda.empty_cache()
     return out
 
@@ -691,6 +809,12 @@ def run_ours(args):
         res["neural_texture_fitting"] = ntex_leg(wl, device, stream, max(3, args.steps // 10))
         res["neural_texture_fitting_tf32"] = ntex_leg(wl, device, stream, max(3, args.steps // 10),
                                                       tensor_cores=True)
+    if not args.no_c3 and rank == 0:
+        res["c3_fitting"] = config_leg("c3", ctx, device, stream, max(3, args.steps // 6), peaks()[0],
+                                       autotune=not args.no_autotune)
+    if not args.no_c5 and rank == 0:
+        res["c5_4k"] = config_leg("c5", ctx, device, stream, 2, peaks()[0], autotune=not args.no_autotune,
+                                  views=args.c5_views, ws_gb=args.c5_ws_gb)
     if not args.no_baked and rank == 0:
         res["baked_forward"] = baked_leg(ctx, device, stream, max(5, args.steps // 3), peaks()[0],
                                          autotune=not args.no_autotune, scale=args.baked_scale,

@@ -115,6 +115,12 @@ typedef struct {
   int32_t band_shift;    /* VS_TEX_SH_U8: 0..3, ignored otherwise         */
   float value_min;       /* VS_TEX_SH_U8: decode range, value_min <      */
   float value_max;       /*   value_max, both finite; ignored otherwise   */
+  int32_t grad_pitch;    /* FP32 values per texel of this shell's gradient
+                            arrays (vs_render_backward, vs_render_batch):
+                            0 = texel_pitch, else >= C; lets the gradient
+                            drop the texels' alignment padding (e.g. 28 for
+                            SH degree 2 stored at texel_pitch 32).  Ignored
+                            for VS_TEX_SH_U8                              */
 } vs_shell_desc;
 
 /* Layout of a VS_TEX_SH_U8 buffer (pure host arithmetic): for bands
@@ -229,7 +235,8 @@ vs_status vs_render(vs_ctx* ctx, const vs_object* obj, const vs_camera* cam, con
  *   grad_rgb     device float32 [H, W, 3] (or the target image with
  *                VS_FLAG_LOSS_L2 / VS_FLAG_LOSS_L1)
  *   grad_texels  host array of k device pointers, each float32
- *                [tex_h, tex_w, texel_pitch]; ADDED to (zero them first);
+ *                [tex_h, tex_w, grad_pitch] (grad_pitch = texel_pitch
+ *                unless the shell sets it); ADDED to (zero them first);
  *                padding values receive nothing
  *   loss         device float32 scalar, L added (with a loss flag only; may
  *                be NULL)
@@ -282,7 +289,14 @@ typedef struct {
  * grad_rgb -- with a loss flag, the target image.  Forward outputs are
  * bit-identical to vs_render of each item.  All enqueued work is
  * capturable in a CUDA graph (the item table travels in kernel parameters).
- * Errors: as vs_render; VS_ERR_INVALID_ARG for n < 1. */
+ * Workspace: vs_workspace_size of all n items runs them in one launch.  A
+ * smaller workspace runs them as consecutive launches over runs of items,
+ * each run the longest that fits (e.g. hundreds of 4K views whose per-shell
+ * visibility words and triangle records would not all fit); results are
+ * the same, the runs do not overlap.  Every item is checked before anything
+ * is enqueued.
+ * Errors: as vs_render; VS_ERR_INVALID_ARG for n < 1; VS_ERR_WORKSPACE when
+ * a single item does not fit. */
 vs_status vs_render_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, const float* bg,
                           int32_t do_backward, void* workspace, size_t ws_bytes, uint32_t flags,
                           vs_stream_t stream);

@@ -71,19 +71,22 @@ def ocam(cam) -> OCam:
 class _ShellRefs:
     """Keeps contiguous copies alive while the C side holds pointers."""
 
-    def __init__(self, shells):
+    def __init__(self, shells, shape_only: bool = False):
+        # shape_only: the texel values are not passed (NULL): for the calls
+        # that never read them (raster statistics, footprint counts), so a
+        # shape-only texture (e.g. a broadcast array) is not materialised
         self.keep = []
         self.arr = (OShell * len(shells))()
         for i, s in enumerate(shells):
             pos = np.ascontiguousarray(s.pos, np.float32)
             uv = np.ascontiguousarray(s.uv, np.float32)
             tris = np.ascontiguousarray(s.tris, np.int32)
-            tex = np.ascontiguousarray(s.tex)
+            tex = s.tex if shape_only else np.ascontiguousarray(s.tex)
             self.keep += [pos, uv, tris, tex]
             o = self.arr[i]
             o.pos, o.uv, o.tris = _ptr(pos).value, _ptr(uv).value, _ptr(tris).value
             o.nv, o.nt = pos.shape[0], tris.shape[0]
-            o.tex = _ptr(tex).value
+            o.tex = None if shape_only else _ptr(tex).value
             o.fmt, o.degree = s.fmt, s.degree
             if s.fmt == FMT_SH_U8:
                 assert tex.dtype == np.uint8 and tex.ndim == 1
@@ -240,7 +243,7 @@ def render(scene, cam, bg=(0.0, 0.0, 0.0), threads: Optional[int] = None, flags:
 
 def backward(scene, cam, hits: np.ndarray, grad_rgb: np.ndarray, bg=(0.0, 0.0, 0.0),
              flags: int = 0, with_scale: bool = False, gmag: Optional[np.ndarray] = None,
-             aw_err: float = 0.0):
+             aw_err: float = 0.0, only: Optional[int] = None, weight_err: float = 0.0):
     """dL/d(texel values) given dL/d(output rgb) -- the texture-fitting
     gradient of Sec. 3 "Texturing Meshes".  Returns one FP64 array per shell,
     shaped like its texture.
@@ -254,19 +257,33 @@ def backward(scene, cam, hits: np.ndarray, grad_rgb: np.ndarray, bg=(0.0, 0.0, 0
     epsilon times S_w plus its tap-weight error times S_1.  gmag [H, W, 3]:
     the size of each pixel's output gradient before cancellation (default
     |grad_rgb|; l2_loss_scale for the L2 loss).  aw_err: with ALPHA_ATTEN,
-    an absolute error of each alpha_w that the scales allow for.  The
-    scales do not change the gradient."""
+    an absolute error of each alpha_w that the scales allow for.
+    weight_err: a tap-weight error the scales allow for; S_1 then also
+    reaches the texels beside a footprint whose texel coordinate lies
+    within weight_err of a texel-centre line (where a lower-precision
+    evaluation may shift the footprint by one texel).  only:
+    compute shell `only`'s arrays alone (the others are None), which bounds
+    the host memory of large textures.  The scales do not change the
+    gradient."""
     refs = _ShellRefs(scene.shells)
     H, W = cam.height, cam.width
     hits = np.ascontiguousarray(hits, np.int32)
     g = np.ascontiguousarray(grad_rgb, np.float64)
     assert g.shape == (H, W, 3)
-    grads = [np.zeros(s.tex.shape, np.float64) for s in scene.shells]
-    ptrs = (ctypes.c_void_p * scene.k)(*[gr.ctypes.data for gr in grads])
-    scales = [np.zeros(s.tex.shape, np.float64) for s in scene.shells] if with_scale else None
-    reach = [np.zeros(s.tex.shape, np.float64) for s in scene.shells] if with_scale else None
-    sptrs = (ctypes.c_void_p * scene.k)(*[a.ctypes.data for a in scales]) if with_scale else None
-    rptrs = (ctypes.c_void_p * scene.k)(*[a.ctypes.data for a in reach]) if with_scale else None
+    want = [only is None or i == only for i in range(scene.k)]
+
+    def arrays():
+        return [np.zeros(s.tex.shape, np.float64) if w else None for s, w in zip(scene.shells, want)]
+
+    def pointers(arrs):
+        return (ctypes.c_void_p * scene.k)(*[a.ctypes.data if a is not None else None for a in arrs])
+
+    grads = arrays()
+    ptrs = pointers(grads)
+    scales = arrays() if with_scale else None
+    reach = arrays() if with_scale else None
+    sptrs = pointers(scales) if with_scale else None
+    rptrs = pointers(reach) if with_scale else None
     gm = None
     if gmag is not None:
         gm = np.ascontiguousarray(gmag, np.float64)
@@ -276,7 +293,7 @@ def backward(scene, cam, hits: np.ndarray, grad_rgb: np.ndarray, bg=(0.0, 0.0, 0
     r = lib().oracle_backward(refs.arr, ctypes.c_int32(scene.k), ctypes.byref(c), _ptr(bgv), _ptr(hits),
                               _ptr(g), ptrs, ctypes.c_int32(flags),
                               _ptr(gm) if gm is not None else ctypes.c_void_p(0), sptrs, rptrs,
-                              ctypes.c_double(aw_err))
+                              ctypes.c_double(aw_err), ctypes.c_double(weight_err))
     if r != 0:
         raise ValueError("the baked byte format (FMT_SH_U8) has no gradient")
     return (grads, (scales, reach)) if with_scale else grads
@@ -308,7 +325,7 @@ def l1_loss_grad(rgba: np.ndarray, target_rgb: np.ndarray):
 
 def footprint_texels(scene, cam, hits: np.ndarray) -> np.ndarray:
     """Distinct texels read by each shell's bilinear footprints."""
-    refs = _ShellRefs(scene.shells)
+    refs = _ShellRefs(scene.shells, shape_only=True)
     hits = np.ascontiguousarray(hits, np.int32)
     out = np.zeros(scene.k, np.int64)
     c = ocam(cam)

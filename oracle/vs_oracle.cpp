@@ -684,7 +684,9 @@ int oracle_shade(const OShell* shells, int32_t k, const OCam* cam, const double*
 }
 
 // Adjoint of oracle_shade w.r.t. the texel values.  grad_rgb: [H, W, 3] =
-// dL/d(output rgb).  grad_tex[i]: [th, tw, pitch] FP64, accumulated into.
+// dL/d(output rgb).  grad_tex[i]: [th, tw, pitch] FP64, accumulated into
+// (NULL: shell i's gradient is not wanted; its scales are then not
+// written either).
 //
 // Optional error scales (abs_tex, reach_tex non-NULL, same layout as
 // grad_tex), a yardstick for comparing gradients, not part of the method.
@@ -703,10 +705,15 @@ int oracle_shade(const OShell* shells, int32_t k, const OCam* cam, const double*
 // that the scales allow for: every term of a fragment's adjoint scales with
 // its alpha_w, and the transmittances with the (1 - alpha_j) of the pixel's
 // other fragments, so the fragment's M is multiplied by
-// 1 + aw_err (1 / alpha_w + sum_j 1 / (1 - alpha_j)).
+// 1 + aw_err (1 / alpha_w + sum_j 1 / (1 - alpha_j)).  weight_err: where
+// a fragment's texel coordinate lies within weight_err of a texel centre
+// line, an evaluation in lower precision may place its footprint one texel
+// over, giving the texel beyond a tap weight of at most weight_err: M is
+// then also added to reach_tex at those texels.
 int oracle_backward(const OShell* shells, int32_t k, const OCam* cam, const double* bg,
                     const int32_t* hits, const double* grad_rgb, double* const* grad_tex, int32_t flags,
-                    const double* gmag, double* const* abs_tex, double* const* reach_tex, double aw_err) {
+                    const double* gmag, double* const* abs_tex, double* const* reach_tex, double aw_err,
+                    double weight_err) {
   // the baked bytes are a deployment format: no gradient (the paper fits
   // continuous textures and quantises when baking)
   for (int i = 0; i < k; ++i)
@@ -724,6 +731,11 @@ int oracle_backward(const OShell* shells, int32_t k, const OCam* cam, const doub
   for (int64_t y = 0; y < H; ++y)
     for (int64_t x = 0; x < W; ++x) {
       const double* g = grad_rgb + 3 * (y * W + x);
+      // a pixel with a zero output gradient (and error scale) adds nothing
+      if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0 &&
+          (!gmag || (gmag[3 * (y * W + x)] == 0.0 && gmag[3 * (y * W + x) + 1] == 0.0 &&
+                     gmag[3 * (y * W + x) + 2] == 0.0)))
+        continue;
       double v[3], Y[16];
       ray_dir(*cam, x, y, v);
       sh_basis(maxdeg, v, Y);
@@ -787,6 +799,7 @@ int oracle_backward(const OShell* shells, int32_t k, const OCam* cam, const doub
           for (int a = 0; a < 2; ++a) {
             double w = tap_weight(f.fp, a, b);
             const size_t off = ((size_t)f.fp.y[b] * s.tw + (size_t)f.fp.x[a]) * s.pitch;
+            if (!grad_tex[i]) continue;   // shell not asked for
             double* gt = grad_tex[i] + off;
             for (int ch = 0; ch < nv; ++ch) gt[ch] += w * dval[ch];
             if (abs_tex) {
@@ -798,6 +811,28 @@ int oracle_backward(const OShell* shells, int32_t k, const OCam* cam, const doub
               for (int ch = 0; ch < nv; ++ch) rt[ch] += dmag[ch];
             }
           }
+        if (reach_tex && grad_tex[i] && weight_err > 0.0) {
+          const double X = f.uv[0] * s.tw - 0.5, Yc = f.uv[1] * s.th - 0.5;
+          const int64_t ix = (int64_t)std::floor(X), iy = (int64_t)std::floor(Yc);
+          const double ex = X - (double)ix, ey = Yc - (double)iy;
+          int64_t xs[3], ys[3];
+          int nx = 0, ny = 0;
+          xs[nx++] = ix;
+          xs[nx++] = ix + 1;
+          if (ex < weight_err) xs[nx++] = ix - 1;
+          else if (ex > 1.0 - weight_err) xs[nx++] = ix + 2;
+          ys[ny++] = iy;
+          ys[ny++] = iy + 1;
+          if (ey < weight_err) ys[ny++] = iy - 1;
+          else if (ey > 1.0 - weight_err) ys[ny++] = iy + 2;
+          for (int b = 0; b < ny; ++b)
+            for (int a = 0; a < nx; ++a) {
+              if (a < 2 && b < 2) continue;   // the footprint's own taps, added above
+              const int64_t cx = std::clamp<int64_t>(xs[a], 0, s.tw - 1), cy = std::clamp<int64_t>(ys[b], 0, s.th - 1);
+              double* rt = reach_tex[i] + ((size_t)cy * s.tw + (size_t)cx) * s.pitch;
+              for (int ch = 0; ch < nv; ++ch) rt[ch] += dmag[ch];
+            }
+        }
       }
     }
   return 0;

@@ -42,7 +42,8 @@ class vs_shell_desc(ctypes.Structure):
                 ("texels", ctypes.c_void_p), ("tex_w", ctypes.c_int32), ("tex_h", ctypes.c_int32),
                 ("format", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
                 ("texel_pitch", ctypes.c_int32), ("band_shift", ctypes.c_int32),
-                ("value_min", ctypes.c_float), ("value_max", ctypes.c_float)]
+                ("value_min", ctypes.c_float), ("value_max", ctypes.c_float),
+                ("grad_pitch", ctypes.c_int32)]
 
 
 class vs_camera(ctypes.Structure):

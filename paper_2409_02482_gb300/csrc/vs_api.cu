@@ -117,6 +117,10 @@ int gcd_pow2(uint64_t a, int cap) {  // largest power of two <= cap dividing a
   return g;
 }
 
+// The binding (_abi.py) mirrors these layouts field by field.
+static_assert(sizeof(vs_shell_desc) == 88 && offsetof(vs_shell_desc, grad_pitch) == 80, "vs_shell_desc layout");
+static_assert(sizeof(vs_camera) == 76, "vs_camera layout");
+
 vs_status check_shell(const vs_shell_desc& s, int i) {
   if (!s.pos || !s.uv || !s.tris || !s.texels) return fail(VS_ERR_INVALID_ARG, "shell %d: NULL array", i);
   if (s.num_verts < 3 || s.num_verts > (1 << 30)) return fail(VS_ERR_INVALID_ARG, "shell %d: num_verts %d out of [3, 2^30]", i, s.num_verts);
@@ -138,6 +142,8 @@ vs_status check_shell(const vs_shell_desc& s, int i) {
   }
   if (s.format == VS_TEX_SH_F16 && (s.sh_degree < 0 || s.sh_degree > 3)) return fail(VS_ERR_INVALID_ARG, "shell %d: SH degree %d out of [0, 3]", i, s.sh_degree);
   if (s.texel_pitch < nch_of(s)) return fail(VS_ERR_INVALID_ARG, "shell %d: texel_pitch %d < %d values", i, s.texel_pitch, nch_of(s));
+  if (s.grad_pitch != 0 && s.grad_pitch < nch_of(s))
+    return fail(VS_ERR_INVALID_ARG, "shell %d: grad_pitch %d < %d values", i, s.grad_pitch, nch_of(s));
   size_t esz = s.format == VS_TEX_RGBA_F32 ? 4 : 2;
   if ((uintptr_t)s.pos % 4 || (uintptr_t)s.uv % 8 || (uintptr_t)s.tris % 4 || (uintptr_t)s.texels % esz)
     return fail(VS_ERR_INVALID_ARG, "shell %d: misaligned array (pos 4 B, uv 8 B, tris 4 B, texels %zu B)", i, esz);
@@ -308,8 +314,9 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
       const uint64_t tex_align = (uint64_t)(uintptr_t)d.texels | (uint64_t)d.texel_pitch * esz;
       s.vec = d.format == VS_TEX_RGBA_F32 ? (gcd_pow2(tex_align, 16) >= 16 ? 4 : 1) : gcd_pow2(tex_align, 16) / 2;
       s.wide = gcd_pow2(tex_align, 32) >= 32;
+      s.gpitch = d.grad_pitch > 0 ? d.grad_pitch : d.texel_pitch;
       if (s.grad) {
-        const uint64_t ga = (uint64_t)(uintptr_t)s.grad | (uint64_t)d.texel_pitch * 4;
+        const uint64_t ga = (uint64_t)(uintptr_t)s.grad | (uint64_t)s.gpitch * 4;
         s.gvec = gcd_pow2(ga, 16) / 4;
         if (s.gvec < 1) s.gvec = 1;
       } else {
@@ -462,13 +469,13 @@ UnitShape shape_of(const vs_tuning& t) {
   return u;
 }
 
-// Checks the batch and builds its plan (shared by vs_render_batch and the
-// autotuner).
-vs_status plan_batch(const vs_ctx* ctx, const vs_batch_item* items, int n, const float* bg, int do_backward,
-                     void* workspace, size_t ws_bytes, uint32_t flags, const vs_tuning& t, Plan& P, int* kmax) {
+// Checks every item of a batch (before anything is enqueued) and fills the
+// plan requests; makes the context's device current and bounds the objects.
+vs_status check_batch(const vs_ctx* ctx, const vs_batch_item* items, int n, int do_backward,
+                      std::vector<ItemReq>& req, int* kmax) {
   if (!ctx || !items) return fail(VS_ERR_INVALID_ARG, "NULL argument");
   if (n < 1) return fail(VS_ERR_INVALID_ARG, "n = %d < 1", n);
-  std::vector<ItemReq> req(n);
+  req.assign(n, ItemReq{});
   *kmax = 1;
   for (int j = 0; j < n; ++j) {
     const vs_batch_item& b = items[j];
@@ -486,12 +493,23 @@ vs_status plan_batch(const vs_ctx* ctx, const vs_batch_item* items, int n, const
     req[j] = ItemReq{b.obj, &b.cam, b.out_rgba, b.hits, b.grad_rgb, b.grad_texels, b.loss};
     *kmax = std::max(*kmax, (int)b.obj->k);
   }
-  char* ws = static_cast<char*>(workspace);
   vs_status s = set_device(ctx);
   if (s != VS_OK) return s;
   for (int j = 0; j < n; ++j)
     if ((s = ensure_bounds(items[j].obj)) != VS_OK) return s;
-  if ((s = make_plan(req.data(), n, bg, do_backward ? 1 : 0, true, flags, ws, P, shape_of(t))) != VS_OK) return s;
+  return VS_OK;
+}
+
+// Checks the batch and builds its plan (shared by vs_render_batch and the
+// autotuner).
+vs_status plan_batch(const vs_ctx* ctx, const vs_batch_item* items, int n, const float* bg, int do_backward,
+                     void* workspace, size_t ws_bytes, uint32_t flags, const vs_tuning& t, Plan& P, int* kmax) {
+  std::vector<ItemReq> req;
+  vs_status s = check_batch(ctx, items, n, do_backward, req, kmax);
+  if (s != VS_OK) return s;
+  if ((s = make_plan(req.data(), n, bg, do_backward ? 1 : 0, true, flags, static_cast<char*>(workspace), P,
+                     shape_of(t))) != VS_OK)
+    return s;
   return check_ws(P, workspace, ws_bytes);
 }
 
@@ -745,10 +763,55 @@ vs_status vs_render_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, co
   for (int j = 0; j < n; ++j)
     if (items[j].obj) kmax = std::max(kmax, std::min((int)items[j].obj->k, VS_MAX_SHELLS));
   const vs_tuning t = lookup_tuning(ctx, do_backward ? 1 : 0, kmax);
-  Plan P;
-  vs_status s = plan_batch(ctx, items, n, bg, do_backward, workspace, ws_bytes, flags, t, P, &kmax);
-  if (s != VS_OK) return s;   // plan_batch made the context's device current
-  return launch_batch(ctx, P, workspace, do_backward, kmax, t, reinterpret_cast<cudaStream_t>(stream));
+  std::vector<ItemReq> req;
+  vs_status s = check_batch(ctx, items, n, do_backward, req, &kmax);   // makes the device current
+  if (s != VS_OK) return s;
+  const int bwd = do_backward ? 1 : 0;
+  const UnitShape shape = shape_of(t);
+  // bytes of the runs [j, j + m): the plan's layout without a workspace
+  auto run_bytes = [&](int j, int m, size_t* bytes) {
+    Plan Q;
+    vs_status r = make_plan(req.data() + j, m, bg, bwd, true, flags, nullptr, Q, shape);
+    *bytes = Q.total;
+    return r;
+  };
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  size_t all = 0;
+  if ((s = run_bytes(0, n, &all)) != VS_OK) return s;
+  // consecutive runs of items, each the longest that fits the workspace (the
+  // whole batch in one launch when it fits)
+  int runs = 0;
+  for (int j = 0; j < n;) {
+    int m = n - j;
+    size_t bytes = j == 0 ? all : 0;
+    if (j > 0 && (s = run_bytes(j, m, &bytes)) != VS_OK) return s;
+    if (bytes > ws_bytes) {
+      size_t one = 0;
+      if ((s = run_bytes(j, 1, &one)) != VS_OK) return s;
+      if (one > ws_bytes || !workspace)
+        return fail(VS_ERR_WORKSPACE, "workspace has %zu bytes; item %d alone needs %zu (the batch %zu)", ws_bytes,
+                    j, one, all);
+      int lo = 1, hi = m - 1;   // largest m' in [lo, hi] that fits; lo fits
+      while (lo < hi) {
+        const int mid = lo + (hi - lo + 1) / 2;
+        size_t b = 0;
+        if ((s = run_bytes(j, mid, &b)) != VS_OK) return s;
+        if (b <= ws_bytes) lo = mid; else hi = mid - 1;
+      }
+      m = lo;
+    }
+    Plan P;
+    if ((s = make_plan(req.data() + j, m, bg, bwd, true, flags, static_cast<char*>(workspace), P, shape)) != VS_OK)
+      return s;
+    if ((s = check_ws(P, workspace, ws_bytes)) != VS_OK) return s;
+    int km = 1;
+    for (int q = j; q < j + m; ++q) km = std::max(km, (int)items[q].obj->k);
+    if ((s = launch_batch(ctx, P, workspace, do_backward, km, t, st)) != VS_OK)
+      return runs ? fail(s, "run %d of the batch (items %d..%d): %s", runs, j, j + m - 1, g_err.c_str()) : s;
+    ++runs;
+    j += m;
+  }
+  return VS_OK;
 }
 
 vs_status vs_set_batch_tuning(vs_ctx* ctx, int32_t do_backward, int32_t k_max, const vs_tuning* t) {

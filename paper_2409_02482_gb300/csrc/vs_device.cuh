@@ -103,7 +103,7 @@ struct alignas(16) DShell {
   const float2* uv;            // [nv]
   const int32_t* tris;         // [nt, 3]
   const void* tex;             // [th, tw, pitch]
-  float* grad;                 // [th, tw, pitch] FP32 (backward) or null
+  float* grad;                 // [th, tw, gpitch] FP32 (backward) or null
   int4* vsetup;                // [nv] (X, Y, bits(1/w), q) -- workspace
   int32_t nv, nt, tw, th;
   int32_t fmt, degree, pitch;
@@ -115,7 +115,8 @@ struct alignas(16) DShell {
   // decode value = vmin + vscale * q
   long long boff[4];
   float vmin, vscale;
-  int32_t bshift, pad3;
+  int32_t bshift;
+  int32_t gpitch;              // FP32 values per gradient texel (>= the value count)
 };
 
 struct alignas(16) DItem {

@@ -498,14 +498,14 @@ __device__ __forceinline__ void scatter_sh(const DShell& s, const Footprint& f, 
     dval[2 + 3 * m] = d.y * Y[m];
     dval[3 + 3 * m] = d.z * Y[m];
   }
-  scatter_grad<NCH, GV>(s.grad, s.tw, s.pitch, f, dval);
+  scatter_grad<NCH, GV>(s.grad, s.tw, s.gpitch, f, dval);
 }
 
 template <int TC>
 __device__ __forceinline__ void scatter_frag(const DShell& s, const Footprint& f, const float3 v, const float4 d) {
   if constexpr (TC == TC_RGBA) {
     const float dval[4] = {d.x, d.y, d.z, d.w};
-    scatter_grad<4, 4>(s.grad, s.tw, s.pitch, f, dval);
+    scatter_grad<4, 4>(s.grad, s.tw, s.gpitch, f, dval);
     return;
   } else if constexpr (TC >= TC_U80) {
     return;   // baked shells have no adjoint (refused on the host)
@@ -516,9 +516,9 @@ __device__ __forceinline__ void scatter_frag(const DShell& s, const Footprint& f
   if (s.fmt == VS_TEX_SH_U8) return;
   if (s.fmt == VS_TEX_RGBA_F32) {
     const float dval[4] = {d.x, d.y, d.z, d.w};
-    if (s.gvec == 4) scatter_grad<4, 4>(s.grad, s.tw, s.pitch, f, dval);
-    else if (s.gvec == 2) scatter_grad<4, 2>(s.grad, s.tw, s.pitch, f, dval);
-    else scatter_grad<4, 1>(s.grad, s.tw, s.pitch, f, dval);
+    if (s.gvec == 4) scatter_grad<4, 4>(s.grad, s.tw, s.gpitch, f, dval);
+    else if (s.gvec == 2) scatter_grad<4, 2>(s.grad, s.tw, s.gpitch, f, dval);
+    else scatter_grad<4, 1>(s.grad, s.tw, s.gpitch, f, dval);
     return;
   }
 #define VS_CASE(D, V) \
@@ -971,7 +971,7 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
           for (int q = 0; q < 4; ++q) {
             const int xq = (q & 1) ? f.x1 : f.x0;
             const float w = ((q & 1) ? f.fx : 1.0f - f.fx) * ((q & 2) ? f.fy : 1.0f - f.fy);
-            red_add_v4f32(g + (((q & 2) ? r1 : r0) + xq) * s.pitch, w * dv0, k1 ? w * dv1 : 0.0f,
+            red_add_v4f32(g + (((q & 2) ? r1 : r0) + xq) * s.gpitch, w * dv0, k1 ? w * dv1 : 0.0f,
                           k2 ? w * dv2 : 0.0f, k3 ? w * dv3 : 0.0f);
           }
         }

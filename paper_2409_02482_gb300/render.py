@@ -72,7 +72,9 @@ class ShellObject:
     """vs_load_shells over device tensors (kept alive by this object).
 
     Each shell: dict(pos=[V,3] f32, uv=[V,2] f32, tris=[T,3] i32,
-    tex=[H,W,pitch] f32 (RGBA) or f16 (SH), fmt, degree); baked shells
+    tex=[H,W,pitch] f32 (RGBA) or f16 (SH), fmt, degree, and optionally
+    grad_pitch: FP32 values per texel of its gradient arrays, default the
+    texel pitch); baked shells
     (VS_TEX_SH_U8): tex = the u8 band buffer (vs_baked_layout) and tex_w,
     tex_h, band_shift, vmin, vmax."""
 
@@ -99,6 +101,7 @@ class ShellObject:
                 d.value_min, d.value_max = float(s.get("vmin", -15.0)), float(s.get("vmax", 15.0))
             else:
                 d.tex_h, d.tex_w, d.texel_pitch = s["tex"].shape
+                d.grad_pitch = int(s.get("grad_pitch", 0))
         self.handle = ctypes.c_void_p()
         check(ctx.lib.vs_load_shells(ctx.handle, arr, k, ctypes.byref(self.handle)))
 
@@ -110,9 +113,24 @@ class ShellObject:
     def textures(self) -> List[torch.Tensor]:
         return [s["tex"] for s in self.shells]
 
+    def grad_shapes(self) -> List[tuple]:
+        """Shape of each shell's FP32 gradient array: [H, W, grad_pitch]."""
+        out = []
+        for s in self.shells:
+            h, w, p = s["tex"].shape
+            out.append((h, w, int(s.get("grad_pitch", 0)) or p))
+        return out
+
+    def zero_grads(self) -> List[torch.Tensor]:
+        """Zeroed FP32 gradient arrays, one per shell."""
+        return [torch.zeros(sh, dtype=torch.float32, device=s["tex"].device)
+                for sh, s in zip(self.grad_shapes(), self.shells)]
+
     @classmethod
-    def from_scene(cls, ctx: Context, scene, device="cuda") -> "ShellObject":
-        """Upload a synth.Scene (numpy arrays) to the device."""
+    def from_scene(cls, ctx: Context, scene, device="cuda", grad_pitch: Optional[int] = None) -> "ShellObject":
+        """Upload a synth.Scene (numpy arrays) to the device.  grad_pitch: the
+        gradient arrays' values per texel for the FP16/FP32 shells (None =
+        the texel pitch; "tight" = the format's value count)."""
         shells = []
         for s in scene.shells:
             d = dict(pos=torch.from_numpy(s.pos).to(device).contiguous(),
@@ -122,6 +140,8 @@ class ShellObject:
                      fmt=s.fmt, degree=s.degree)
             if s.fmt == VS_TEX_SH_U8:
                 d.update(tex_w=s.tex_w, tex_h=s.tex_h, band_shift=s.band_shift, vmin=s.vmin, vmax=s.vmax)
+            elif grad_pitch is not None:
+                d["grad_pitch"] = s.channels if grad_pitch == "tight" else int(grad_pitch)
             shells.append(d)
         return cls(ctx, shells)
 
@@ -190,7 +210,7 @@ def render_backward(ctx: Context, obj: ShellObject, cam, ws: torch.Tensor, hits:
                     stream=None) -> List[torch.Tensor]:
     """vs_render_backward: accumulates into (and returns) FP32 texel grads."""
     if grads is None:
-        grads = [torch.zeros(t.shape, dtype=torch.float32, device=t.device) for t in obj.textures]
+        grads = obj.zero_grads()
     c = camera_struct(cam)
     bgv = (ctypes.c_float * 3)(*bg)
     gptrs = (ctypes.c_void_p * obj.k)(*[g.data_ptr() for g in grads])
@@ -357,4 +377,8 @@ class VSRender(torch.autograd.Function):
         g = grad_out[..., :3].contiguous().float()
         grads = render_backward(fctx.vctx, fctx.obj, fctx.cam, fctx.ws, hits, g, bg=fctx.bg,
                                 flags=fctx.flags)
-        return (None, None, None, None, None, None, *grads)
+        out = []
+        for gr, t in zip(grads, fctx.obj.textures):   # gradient pitch -> texel pitch
+            p, gp = t.shape[2], gr.shape[2]
+            out.append(gr if gp == p else (gr[..., :p] if gp > p else torch.nn.functional.pad(gr, (0, p - gp))))
+        return (None, None, None, None, None, None, *out)

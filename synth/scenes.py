@@ -294,12 +294,26 @@ def sh_texture(h: int, w: int, degree: int, rng: np.random.Generator,
     """
     c = sh_channels(degree)
     pitch = c if pitch is None else pitch
-    vals = rng.standard_normal((h, w, c), dtype=np.float32)
-    vals *= np.float32(sigma)
-    if pitch == c:
-        return vals.astype(np.float16)
     tex = np.zeros((h, w, pitch), dtype=np.float16)
-    tex[..., :c] = vals
+    # blocks of rows, each from its own generator seeded by `rng`, filled by
+    # a thread pool (numpy releases the GIL): large textures (4096^2 x 49)
+    # generate in seconds, deterministically for a given rng state
+    rows = 128
+    seeds = rng.integers(0, 2 ** 63 - 1, size=(h + rows - 1) // rows)
+
+    def fill(b):
+        r0, r1 = b * rows, min(h, (b + 1) * rows)
+        vals = np.random.default_rng(int(seeds[b])).standard_normal((r1 - r0, w, c), dtype=np.float32)
+        vals *= np.float32(sigma)
+        tex[r0:r1, :, :c] = vals
+
+    if len(seeds) == 1:
+        fill(0)
+    else:
+        from concurrent.futures import ThreadPoolExecutor
+        import os
+        with ThreadPoolExecutor(min(len(seeds), os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, range(len(seeds))))
     return tex
 
 
@@ -483,7 +497,7 @@ def config_scene(name: str, scale: float = 1.0, views: Optional[int] = None,
         return [(Scene(shells), [cam])]
     if name == "c2":
         n = 100 if views is None else views
-        sc = _sh_scene(7, _n_lat_for_tris(200e3 * scale), texres(2048), 2, 0, tex_seed, pitch)
+        sc = _sh_scene(7, _n_lat_for_tris(200e3 * scale), texres(2048), 2, 0, tex_seed, pitch, textures=textures)
         w = res(800)
         return [(sc, fibonacci_cameras(n, 4.0, w, w))]
     if name == "c2b":
@@ -493,7 +507,7 @@ def config_scene(name: str, scale: float = 1.0, views: Optional[int] = None,
         return [(sc, fibonacci_cameras(n, 4.0, w, w))]
     if name == "c3":
         n = 64 if views is None else views
-        sc = _sh_scene(9, _n_lat_for_tris(500e3 * scale), texres(2048), 2, 0, tex_seed, pitch)
+        sc = _sh_scene(9, _n_lat_for_tris(500e3 * scale), texres(2048), 2, 0, tex_seed, pitch, textures=textures)
         w = res(1024)
         return [(sc, fibonacci_cameras(n, 4.0, w, w))]
     if name == "c4":
@@ -516,7 +530,7 @@ def config_scene(name: str, scale: float = 1.0, views: Optional[int] = None,
         return out
     if name == "c5":
         n = 256 if views is None else views
-        sc = _sh_scene(9, _n_lat_for_tris(2e6 * scale), texres(4096), 3, 0, tex_seed, pitch)
+        sc = _sh_scene(9, _n_lat_for_tris(2e6 * scale), texres(4096), 3, 0, tex_seed, pitch, textures=textures)
         return [(sc, fibonacci_cameras(n, 3.5, res(3840), res(2160),
                                        elev_range=(-80.0, 80.0)))]
     raise KeyError(name)

@@ -35,7 +35,8 @@ def test_exports_every_declared_function(lib):
 def test_struct_layouts_match_header_sizes():
     # sizes implied by the C declarations on LP64
     assert ctypes.sizeof(_abi.vs_camera) == 76
-    assert ctypes.sizeof(_abi.vs_shell_desc) == 80
+    assert ctypes.sizeof(_abi.vs_shell_desc) == 88
+    assert _abi.vs_shell_desc.grad_pitch.offset == 80   # static_assert in vs_api.cu
     assert ctypes.sizeof(_abi.vs_stats) == 80
     assert ctypes.sizeof(_abi.vs_tuning) == 16
 

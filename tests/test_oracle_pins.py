@@ -1204,6 +1204,12 @@ def test_backward_error_scales():
             assert np.all(np.abs(a) <= w * (1 + 1e-12)) and np.all(w <= r * (1 + 1e-12))
             assert np.array_equal(w == 0, r == 0) and np.all(a[w == 0] == 0)
         assert max(float(w.max()) for w in sw) > 0
+        # a tap-weight allowance widens S_1 beside footprints near texel
+        # lines and changes neither the gradient nor S_w
+        g2, (sw2, s12) = oracle.backward(sc, cam, hits, g, bg=bg, with_scale=True, weight_err=0.25)
+        for a, b, w, w2, r, r2 in zip(grads, g2, sw, sw2, s1, s12):
+            assert np.array_equal(a, b) and np.array_equal(w, w2) and np.all(r2 >= r)
+        assert any(np.any((r2 > 0) & (r == 0)) for r, r2 in zip(s1, s12))
         # (2) nonnegative output gradient: no cancellation in the colour terms
         gp = np.abs(g)
         grads, (sw, _) = oracle.backward(sc, cam, hits, gp, bg=bg, with_scale=True)
