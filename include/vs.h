@@ -385,9 +385,14 @@ typedef struct {
   float growth;          /* b in [1, 4]; N_l <= 2^20                       */
   int32_t hidden;        /* H: 1 .. 512                                    */
   int32_t out_ch;        /* C: 1 .. 256                                    */
-  int32_t tensor_cores;  /* 0: FP32 layers (exact FP32 GEMMs, the default);
-                            1: the layers on the tensor cores in TF32 (10-bit
-                            mantissa inputs, FP32 accumulation)            */
+  int32_t tensor_cores;  /* 0: FP32 layers (FP32 FMAs on the FP32 pipes, the
+                            default); 1: the layer products shaped like the
+                            forward (the three layers, and the adjoint's
+                            activation gradients) on the tensor cores
+                            (tcgen05, inputs rounded to TF32 -- 10-bit
+                            mantissa, to nearest -- FP32 accumulation in
+                            tensor memory, N <= 256); the weight gradients
+                            stay FP32                                      */
 } vs_ntex_config;
 
 /* Offsets (in floats) of the seven parameter blocks and the total count.
@@ -395,13 +400,17 @@ typedef struct {
 vs_status vs_ntex_layout(const vs_ntex_config* cfg, int64_t offsets[7], int64_t* total);
 
 /* Workspace bytes for vs_ntex_forward / vs_ntex_backward on a tex_w x tex_h
- * texture (activations of up to 2^18 texels at a time).  Host only. */
+ * texture (activations of up to 2^18 texels at a time).  Host only.  Its
+ * first 4 bytes are a status word: zero the workspace once; with
+ * tensor_cores = 1 a bounded wait that ran out writes 1 there (the layer's
+ * outputs are then zero) and the call still returns. */
 vs_status vs_ntex_workspace_size(const vs_ntex_config* cfg, int32_t tex_w, int32_t tex_h, size_t* bytes);
 
 /* Evaluates the network at every texel centre and writes channels
  * [ch0, ch0 + C) of texels [tex_h, tex_w, pitch] (dtype 0 = float32,
  * 1 = float16, the renderer's SH storage).  FP32 arithmetic: the layers as
- * FP32 GEMMs, or as TF32 tensor-core GEMMs when cfg->tensor_cores = 1.
+ * hand-written FP32 GEMMs with bias and ReLU fused, or on the tensor cores
+ * in TF32 when cfg->tensor_cores = 1.
  * Errors: VS_ERR_INVALID_ARG (config, sizes, ch0 + C > pitch, NULL),
  * VS_ERR_WORKSPACE, VS_ERR_CUDA. */
 vs_status vs_ntex_forward(vs_ctx* ctx, const vs_ntex_config* cfg, const float* params, int32_t tex_w, int32_t tex_h,

@@ -249,12 +249,14 @@ def backward(scene, cam, hits: np.ndarray, grad_rgb: np.ndarray, bg=(0.0, 0.0, 0
     shaped like its texture.
 
     with_scale: also return the gradient's per-texel error scales as
-    (grads, (S_w, S_1)): over the (fragment, tap) terms that reach a texel
-    value, S_w sums |w| M and S_1 sums M, M being the term's product without
-    the tap weight w, with every factor taken by absolute value and every
-    difference as the sum of its terms' absolute values (see
+    (grads, (S_w, S_1, S_y)): over the (fragment, tap) terms that reach a
+    texel value, S_w sums |w| M and S_1 sums M, M being the term's product
+    without the tap weight w, with every factor taken by absolute value and
+    every difference as the sum of its terms' absolute values; S_y sums
+    |w| M with the SH basis value left out (SH coefficient values only; see
     oracle_backward).  An FP32 evaluation errs by a small multiple of
-    epsilon times S_w plus its tap-weight error times S_1.  gmag [H, W, 3]:
+    epsilon times S_w, plus its tap-weight error times S_1, plus its
+    absolute SH-basis error times S_y.  gmag [H, W, 3]:
     the size of each pixel's output gradient before cancellation (default
     |grad_rgb|; l2_loss_scale for the L2 loss).  aw_err: with ALPHA_ATTEN,
     an absolute error of each alpha_w that the scales allow for.
@@ -284,6 +286,8 @@ def backward(scene, cam, hits: np.ndarray, grad_rgb: np.ndarray, bg=(0.0, 0.0, 0
     reach = arrays() if with_scale else None
     sptrs = pointers(scales) if with_scale else None
     rptrs = pointers(reach) if with_scale else None
+    ysc = arrays() if with_scale else None
+    yptrs = pointers(ysc) if with_scale else None
     gm = None
     if gmag is not None:
         gm = np.ascontiguousarray(gmag, np.float64)
@@ -293,10 +297,10 @@ def backward(scene, cam, hits: np.ndarray, grad_rgb: np.ndarray, bg=(0.0, 0.0, 0
     r = lib().oracle_backward(refs.arr, ctypes.c_int32(scene.k), ctypes.byref(c), _ptr(bgv), _ptr(hits),
                               _ptr(g), ptrs, ctypes.c_int32(flags),
                               _ptr(gm) if gm is not None else ctypes.c_void_p(0), sptrs, rptrs,
-                              ctypes.c_double(aw_err), ctypes.c_double(weight_err))
+                              ctypes.c_double(aw_err), ctypes.c_double(weight_err), yptrs)
     if r != 0:
         raise ValueError("the baked byte format (FMT_SH_U8) has no gradient")
-    return (grads, (scales, reach)) if with_scale else grads
+    return (grads, (scales, reach, ysc)) if with_scale else grads
 
 
 def l2_loss_grad(rgba: np.ndarray, target_rgb: np.ndarray):

@@ -101,23 +101,40 @@ def encode(cfg: NtexConfig, P, x: np.ndarray) -> np.ndarray:
     return np.concatenate(feats, 1)
 
 
-def forward(cfg: NtexConfig, params: np.ndarray, tex_w: int, tex_h: int):
-    """Texel values [tex_h, tex_w, C] and the activations (for the adjoint)."""
-    P = unpack(cfg, params.astype(np.float64))
-    x = texel_centres(tex_w, tex_h)
+def _mlp(cfg: NtexConfig, P, x: np.ndarray):
     f = encode(cfg, P, x)
     z1 = f @ P["W0"].T + P["b0"]
     h1 = np.maximum(z1, 0)
     z2 = h1 @ P["W1"].T + P["b1"]
     h2 = np.maximum(z2, 0)
     y = h2 @ P["W2"].T + P["b2"]
-    return y.reshape(tex_h, tex_w, cfg.out_ch), dict(x=x, f=f, z1=z1, h1=h1, z2=z2, h2=h2)
+    return y, dict(x=x, f=f, z1=z1, h1=h1, z2=z2, h2=h2)
 
 
-def backward(cfg: NtexConfig, params: np.ndarray, tex_w: int, tex_h: int, grad_y: np.ndarray) -> np.ndarray:
-    """dL/d(params) (flat, FP64) given dL/d(texel values) [tex_h, tex_w, C]."""
+def forward(cfg: NtexConfig, params: np.ndarray, tex_w: int, tex_h: int):
+    """Texel values [tex_h, tex_w, C] and the activations (for the adjoint)."""
     P = unpack(cfg, params.astype(np.float64))
-    _, a = forward(cfg, params, tex_w, tex_h)
+    y, a = _mlp(cfg, P, texel_centres(tex_w, tex_h))
+    return y.reshape(tex_h, tex_w, cfg.out_ch), a
+
+
+def forward_at(cfg: NtexConfig, params: np.ndarray, tex_w: int, tex_h: int, texels: np.ndarray) -> np.ndarray:
+    """The values [n, C] of the texels with row-major indices `texels` only
+    (the same definition as forward, for spot checks of large textures)."""
+    P = unpack(cfg, params.astype(np.float64))
+    return _mlp(cfg, P, texel_centres(tex_w, tex_h)[np.asarray(texels)])[0]
+
+
+def backward(cfg: NtexConfig, params: np.ndarray, tex_w: int, tex_h: int, grad_y: np.ndarray,
+             texels: np.ndarray = None) -> np.ndarray:
+    """dL/d(params) (flat, FP64) given dL/d(texel values) [tex_h, tex_w, C];
+    with `texels` (row-major indices), grad_y is [n, C] for those texels
+    and the rest of the texture has a zero gradient."""
+    P = unpack(cfg, params.astype(np.float64))
+    if texels is None:
+        _, a = forward(cfg, params, tex_w, tex_h)
+    else:
+        _, a = _mlp(cfg, P, texel_centres(tex_w, tex_h)[np.asarray(texels)])
     g = grad_y.reshape(-1, cfg.out_ch).astype(np.float64)
     G = {name: np.zeros(shp) for name, shp in cfg.shapes()}
     G["W2"] = g.T @ a["h2"]

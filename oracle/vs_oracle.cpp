@@ -709,11 +709,15 @@ int oracle_shade(const OShell* shells, int32_t k, const OCam* cam, const double*
 // a fragment's texel coordinate lies within weight_err of a texel centre
 // line, an evaluation in lower precision may place its footprint one texel
 // over, giving the texel beyond a tap weight of at most weight_err: M is
-// then also added to reach_tex at those texels.
+// then also added to reach_tex at those texels.  ysc_tex (optional, like
+// abs_tex): for the SH coefficient values, the sum of |w| M with the SH
+// basis value left out of M -- the scale of an absolute error in the basis
+// values (a basis value near zero is a difference of terms of the ray
+// direction, so its error does not shrink with it).
 int oracle_backward(const OShell* shells, int32_t k, const OCam* cam, const double* bg,
                     const int32_t* hits, const double* grad_rgb, double* const* grad_tex, int32_t flags,
                     const double* gmag, double* const* abs_tex, double* const* reach_tex, double aw_err,
-                    double weight_err) {
+                    double weight_err, double* const* ysc_tex) {
   // the baked bytes are a deployment format: no gradient (the paper fits
   // continuous textures and quantises when baking)
   for (int i = 0; i < k; ++i)
@@ -772,28 +776,34 @@ int oracle_backward(const OShell* shells, int32_t k, const OCam* cam, const doub
           Am[ch] = f.alpha * std::fabs(f.rgb[ch]) + (1.0 - f.alpha) * Am[ch];
         }
         int nv = num_values(s);
-        double dval[64], dmag[64];
+        double dval[64], dmag[64], ymag[64];
         // alpha = alpha_raw * atten, atten independent of the texels
         if (s.fmt == FMT_RGBA_F32) {
           dval[0] = gc[0]; dval[1] = gc[1]; dval[2] = gc[2]; dval[3] = ga * f.atten;
           dmag[0] = gcm[0]; dmag[1] = gcm[1]; dmag[2] = gcm[2]; dmag[3] = gam * f.atten;
+          for (int ch = 0; ch < 4; ++ch) ymag[ch] = 0.0;
         } else {
           int nb = (s.degree + 1) * (s.degree + 1);
           const double sa = f.alpha_raw * (1.0 - f.alpha_raw);
           dval[0] = ga * f.atten * sa;
           dmag[0] = gam * f.atten * sa;
+          ymag[0] = 0.0;
           for (int ch = 0; ch < 3; ++ch) {
             const double sc = f.rgb[ch] * (1.0 - f.rgb[ch]);
             double dz = gc[ch] * sc;
             for (int m = 0; m < nb; ++m) {
               dval[1 + 3 * m + ch] = dz * Y[m];
               dmag[1 + 3 * m + ch] = gcm[ch] * sc * std::fabs(Y[m]);
+              ymag[1 + 3 * m + ch] = gcm[ch] * sc;
             }
           }
         }
         if ((flags & OFLAG_ALPHA_ATTEN) && aw_err > 0.0) {
           const double grow = 1.0 + aw_err * (1.0 / std::max(f.atten, 1e-300) + sens);
-          for (int ch = 0; ch < nv; ++ch) dmag[ch] *= grow;
+          for (int ch = 0; ch < nv; ++ch) {
+            dmag[ch] *= grow;
+            ymag[ch] *= grow;
+          }
         }
         for (int b = 0; b < 2; ++b)
           for (int a = 0; a < 2; ++a) {
@@ -809,6 +819,10 @@ int oracle_backward(const OShell* shells, int32_t k, const OCam* cam, const doub
             if (reach_tex) {
               double* rt = reach_tex[i] + off;
               for (int ch = 0; ch < nv; ++ch) rt[ch] += dmag[ch];
+            }
+            if (ysc_tex) {
+              double* yt = ysc_tex[i] + off;
+              for (int ch = 0; ch < nv; ++ch) yt[ch] += std::fabs(w) * ymag[ch];
             }
           }
         if (reach_tex && grad_tex[i] && weight_err > 0.0) {

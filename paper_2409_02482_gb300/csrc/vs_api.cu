@@ -30,8 +30,6 @@ struct vs_ctx {
   int num_sms;
   int persist_blocks[2][kNumTc][VS_MAX_SHELLS + 1];   // [backward][texel class][most shells] blocks per SM
   int persist_blocks_full[2][VS_MAX_SHELLS + 1];      // the full variant (generic class)
-  std::mutex blas_mu;                                  // guards blas
-  cublasHandle_t blas;                                 // created on the first neural-texture call
   std::mutex tune_mu;                          // guards tune / tune_set
   vs_tuning tune[2][VS_MAX_SHELLS + 1];        // [backward][most shells]
   bool tune_set[2][VS_MAX_SHELLS + 1];
@@ -641,7 +639,6 @@ vs_status vs_create(vs_ctx** ctx, int device) {
 }
 
 vs_status vs_destroy(vs_ctx* ctx) {
-  if (ctx && ctx->blas) cublasDestroy(ctx->blas);
   delete ctx;
   return VS_OK;
 }
@@ -977,27 +974,8 @@ vs_status check_ntex_call(vs_ctx* ctx, const vs_ntex_config* cfg, const void* pa
   return VS_OK;
 }
 
-// The context's cuBLAS handle, on `st`, in the math mode the config asks
-// for: exact FP32 (no reduced-precision tensor-core paths) or TF32 tensor
-// cores.  Holds the handle's mutex until the caller's lock goes out of scope.
-vs_status get_blas(vs_ctx* ctx, cudaStream_t st, int tensor_cores, cublasHandle_t* h) {
-  if (!ctx->blas) {
-    if (cublasCreate(&ctx->blas) != CUBLAS_STATUS_SUCCESS) {
-      ctx->blas = nullptr;
-      return fail(VS_ERR_CUDA, "cublasCreate failed");
-    }
-  }
-  if (cublasSetMathMode(ctx->blas, tensor_cores ? CUBLAS_TF32_TENSOR_OP_MATH : CUBLAS_PEDANTIC_MATH) !=
-      CUBLAS_STATUS_SUCCESS)
-    return fail(VS_ERR_CUDA, "cublasSetMathMode failed");
-  if (cublasSetStream(ctx->blas, st) != CUBLAS_STATUS_SUCCESS) return fail(VS_ERR_CUDA, "cublasSetStream failed");
-  *h = ctx->blas;
-  return VS_OK;
-}
-
 vs_status ntex_status(int r, const char* what) {
   if (r == 0) return VS_OK;
-  if (r == -1000) return fail(VS_ERR_CUDA, "%s: a cuBLAS call failed", what);
   return cuda_fail((cudaError_t)r, what);
 }
 
@@ -1039,10 +1017,7 @@ vs_status vs_ntex_forward(vs_ctx* ctx, const vs_ntex_config* cfg, const float* p
   if (dtype != 0 && dtype != 1) return fail(VS_ERR_INVALID_ARG, "dtype %d is neither 0 (f32) nor 1 (f16)", dtype);
   if ((s = set_device(ctx)) != VS_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  std::lock_guard<std::mutex> g(ctx->blas_mu);   // the handle's stream and mode are per call
-  cublasHandle_t h;
-  if ((s = get_blas(ctx, st, cfg->tensor_cores, &h)) != VS_OK) return s;
-  return ntex_status(vsntex::forward(h, *cfg, params, tex_w, tex_h, texels, dtype, pitch, ch0, workspace, st),
+  return ntex_status(vsntex::forward(*cfg, params, tex_w, tex_h, texels, dtype, pitch, ch0, workspace, st),
                      "vs_ntex_forward");
 }
 
@@ -1055,10 +1030,7 @@ vs_status vs_ntex_backward(vs_ctx* ctx, const vs_ntex_config* cfg, const float* 
   if (!grads || (uintptr_t)grads % 4) return fail(VS_ERR_INVALID_ARG, "grads NULL or misaligned");
   if ((s = set_device(ctx)) != VS_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  std::lock_guard<std::mutex> g(ctx->blas_mu);
-  cublasHandle_t h;
-  if ((s = get_blas(ctx, st, cfg->tensor_cores, &h)) != VS_OK) return s;
-  return ntex_status(vsntex::backward(h, *cfg, params, tex_w, tex_h, grad_texels, pitch, ch0, grads, workspace, st),
+  return ntex_status(vsntex::backward(*cfg, params, tex_w, tex_h, grad_texels, pitch, ch0, grads, workspace, st),
                      "vs_ntex_backward");
 }
 

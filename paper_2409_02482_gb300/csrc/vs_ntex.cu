@@ -9,12 +9,16 @@
 //
 // GB300 mapping: the encoding (a 4-corner gather per level) and its adjoint
 // (a scatter with float atomics) are hand-written kernels, one thread per
-// (texel, level); the three layers are dense contractions over the texels
-// -- plain FP32 GEMMs through cuBLAS -- with bias/ReLU, texel writes and
-// gradient gathers as small elementwise kernels.  Texels run in chunks of
-// kChunk so that the activations fit a bounded workspace.
+// (texel, level); the three layers are dense contractions over the texels,
+// run as hand-written GEMM kernels with their elementwise work fused in:
+// bias and ReLU in the forward's epilogue, the ReLU mask and the bias
+// gradient's column sums in the adjoint's.  FP32 layers (the default) run on
+// the FP32 pipes; with cfg.tensor_cores the forward-shaped products run on
+// the tensor cores (tcgen05, TF32 inputs, FP32 accumulators in tensor
+// memory; see vs_ntex_tc.cuh).  Texels run in chunks of kChunk so that the
+// activations (64 MB per layer at 2^18 texels) stay within L2 between
+// layers and in a bounded workspace.
 
-#include <cublas_v2.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -190,34 +194,6 @@ __global__ void __launch_bounds__(kThreads) k_encode_bwd(Enc e, const float* dX,
   }
 }
 
-// Z[r, j] = act(Z[r, j] + b[j]); act = ReLU or identity.
-__global__ void __launch_bounds__(kThreads) k_bias_act(float* Z, const float* b, int rows, int cols, int relu) {
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= (long long)rows * cols) return;
-  const int j = (int)(id % cols);
-  const float v = Z[id] + __ldg(b + j);
-  Z[id] = relu ? fmaxf(v, 0.0f) : v;
-}
-// The same four values at a time (cols a multiple of 4; Z and b 16-byte aligned).
-__global__ void __launch_bounds__(kThreads) k_bias_act4(float4* Z, const float* b, long long n4, int cols, int relu) {
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= n4) return;
-  const int j = (int)((4 * id) % cols);
-  const float4 bb = __ldg(reinterpret_cast<const float4*>(b + j));
-  float4 v = Z[id];
-  v.x += bb.x;
-  v.y += bb.y;
-  v.z += bb.z;
-  v.w += bb.w;
-  if (relu) {
-    v.x = fmaxf(v.x, 0.0f);
-    v.y = fmaxf(v.y, 0.0f);
-    v.z = fmaxf(v.z, 0.0f);
-    v.w = fmaxf(v.w, 0.0f);
-  }
-  Z[id] = v;
-}
-
 // dZ = dH * (H > 0) for H the ReLU output (in place on dH).
 __global__ void __launch_bounds__(kThreads) k_relu_bwd(float* dH, const float* H, long long n) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -302,16 +278,170 @@ __global__ void __launch_bounds__(kThreads) k_adam(float* p, const float* g, flo
   p[id] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+// ----------------------------------------------------------------------------
+// GEMMs of the layers (FP32 pipes).  Row-major throughout; "rows" are texels.
+// ----------------------------------------------------------------------------
+// Epilogues of Y = A B^T: store, + bias, + bias and ReLU, or (adjoint) the
+// ReLU mask of the forward activation H applied and the masked column sums
+// added into db (the bias gradient).
+enum { EPI_NONE = 0, EPI_BIAS = 1, EPI_BIAS_RELU = 2, EPI_MASK_COLSUM = 3 };
 
-void bias_act(float* Z, const float* b, int rows, int cols, int relu, cudaStream_t st) {
-  if (cols % 4 == 0 && ((uintptr_t)Z | (uintptr_t)b) % 16 == 0) {
-    const long long n4 = (long long)rows * cols / 4;
-    k_bias_act4<<<blocks_for(n4), kThreads, 0, st>>>(reinterpret_cast<float4*>(Z), b, n4, cols, relu);
-  } else {
-    k_bias_act<<<blocks_for((long long)rows * cols), kThreads, 0, st>>>(Z, b, rows, cols, relu);
+constexpr int kGM = 128, kGN = 64, kGK = 16;   // block tile of k_gemm_abt
+
+// Y[r, n] = sum_k A[r, k] B[n, k] (A rows x K, B N x K) with epilogue EPI.
+// 256 threads, each 8 rows x 4 columns of the 128 x 64 tile; k in slices of
+// 16 staged through shared memory (A and B transposed there, so the inner
+// loop reads broadcast float4s).  FMAs in k order: exact FP32 products and
+// sums, no reduced-precision path.
+template <int EPI>
+__global__ void __launch_bounds__(kThreads) k_gemm_abt(const float* __restrict__ A, const float* __restrict__ B,
+                                                        float* __restrict__ Y, int rows, int N, int K,
+                                                        const float* __restrict__ bias, const float* __restrict__ H,
+                                                        float* __restrict__ db) {
+  __shared__ __align__(16) float As[kGK][kGM];
+  __shared__ __align__(16) float Bs[kGK][kGN];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;          // 4 columns tx * 4.., 8 rows ty * 8..
+  const long long r0 = (long long)blockIdx.x * kGM;
+  const int n0 = blockIdx.y * kGN;
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+  for (int k0 = 0; k0 < K; k0 += kGK) {
+    // A tile: 128 rows x 16 k, 8 values per thread (k fastest: coalesced)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + q * kThreads, rr = e >> 4, kk = e & 15;
+      const long long r = r0 + rr;
+      As[kk][rr] = (r < rows && k0 + kk < K) ? __ldg(A + r * K + k0 + kk) : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * kThreads, nn = e >> 4, kk = e & 15;
+      Bs[kk][nn] = (n0 + nn < N && k0 + kk < K) ? __ldg(B + (size_t)(n0 + nn) * K + k0 + kk) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float csum[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const long long r = r0 + ty * 8 + i;
+    if (r >= rows) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx * 4 + j;
+      if (n >= N) continue;
+      float v = acc[i][j];
+      if constexpr (EPI == EPI_BIAS || EPI == EPI_BIAS_RELU) v += __ldg(bias + n);
+      if constexpr (EPI == EPI_BIAS_RELU) v = fmaxf(v, 0.0f);
+      if constexpr (EPI == EPI_MASK_COLSUM) {
+        if (!(__ldg(H + r * N + n) > 0.0f)) v = 0.0f;
+        csum[j] += v;
+      }
+      Y[r * N + n] = v;
+    }
+  }
+  if constexpr (EPI == EPI_MASK_COLSUM) {
+    // column sums over the block's 128 rows: 16 row groups per column
+    __syncthreads();
+    float* part = &As[0][0];   // 16 x 64 floats
+#pragma unroll
+    for (int j = 0; j < 4; ++j) part[ty * kGN + tx * 4 + j] = csum[j];
+    __syncthreads();
+    if (tid < kGN && n0 + tid < N) {
+      float t = 0.0f;
+      for (int g = 0; g < 16; ++g) t += part[g * kGN + tid];
+      atomicAdd(db + n0 + tid, t);
+    }
   }
 }
+
+}  // namespace vsn
+
+#include "vs_ntex_tc.cuh"
+
+namespace vsn {
+
+constexpr int kWN = 64, kWK = 64, kWR = 16;   // output tile and row slice of k_gemm_atb
+constexpr int kWRows = 1024;                  // rows per block (split of the reduction)
+
+// dW[n, k] += sum_r D[r, n] A[r, k] (D rows x N, A rows x K): the weight
+// gradient, a reduction over the texels.  Block = one 64 x 64 tile of dW
+// over kWRows rows, 4 x 4 outputs per thread; the partial tile is added
+// into dW with one atomic per value.
+__global__ void __launch_bounds__(kThreads) k_gemm_atb(const float* __restrict__ D, const float* __restrict__ A,
+                                                        float* __restrict__ dW, int rows, int N, int K) {
+  __shared__ __align__(16) float Ds[kWR][kWN];
+  __shared__ __align__(16) float Xs[kWR][kWK];
+  const int tid = threadIdx.x;
+  const int tn = tid >> 4, tk = tid & 15;          // 4 n (tn * 4..), 4 k (tk * 4..)
+  const int tiles_k = (K + kWK - 1) / kWK;
+  const int n0 = (blockIdx.x / tiles_k) * kWN, k0 = (blockIdx.x % tiles_k) * kWK;
+  const long long rb = (long long)blockIdx.y * kWRows;
+  const long long re = rb + kWRows < rows ? rb + kWRows : rows;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+  for (long long s0 = rb; s0 < re; s0 += kWR) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * kThreads, rr = e >> 6, cc = e & 63;
+      const long long r = s0 + rr;
+      Ds[rr][cc] = (r < re && n0 + cc < N) ? __ldg(D + r * N + n0 + cc) : 0.0f;
+      Xs[rr][cc] = (r < re && k0 + cc < K) ? __ldg(A + r * K + k0 + cc) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < kWR; ++rr) {
+      const float4 d = *reinterpret_cast<const float4*>(&Ds[rr][tn * 4]);
+      const float4 x = *reinterpret_cast<const float4*>(&Xs[rr][tk * 4]);
+      const float dv[4] = {d.x, d.y, d.z, d.w}, xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(dv[i], xv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int n = n0 + tn * 4 + i;
+    if (n >= N) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = k0 + tk * 4 + j;
+      if (k < K && acc[i][j] != 0.0f) atomicAdd(dW + (size_t)n * K + k, acc[i][j]);
+    }
+  }
+}
+
+// Wt[k, n] = W[n, k] (W N x K): the adjoint's B operands.
+__global__ void __launch_bounds__(kThreads) k_transpose(const float* __restrict__ W, float* __restrict__ Wt, int N,
+                                                         int K) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)N * K) return;
+  const int n = (int)(id / K), k = (int)(id - (long long)n * K);
+  Wt[(size_t)k * N + n] = W[id];
+}
+
+unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 // db += column sums of dZ, dZ = dH * (H > 0) in place (H may be null).
 void relu_colsum(float* dH, const float* H, int rows, int cols, float* db, cudaStream_t st) {
@@ -349,15 +479,20 @@ void views(const vs_ntex_config& c, P* base, P* out[7]) {
   }
 }
 
-// Workspace carve for a chunk of `rows` texels.
+// Workspace carve for a chunk of `rows` texels, plus the transposed weights
+// of the adjoint; the first 256 bytes hold the status word (0, or
+// kNtexTimeout when a tensor-core wait ran out).
 struct Ws {
-  float *X, *H1, *H2, *Y, *dY, *dH2, *dH1, *dX;
+  int* status;
+  float *X, *H1, *H2, *Y, *dY, *dH2, *dH1, *dX, *W2t, *W1t, *W0t;
 };
 
 Ws carve(const vs_ntex_config& c, int rows, void* ws) {
   const size_t LF = (size_t)c.levels * c.features, H = c.hidden, C = c.out_ch;
   float* p = static_cast<float*>(ws);
   Ws w;
+  w.status = reinterpret_cast<int*>(p);
+  p += 64;
   auto take = [&](size_t n) {
     float* q = p;
     p += (n + 63) & ~(size_t)63;   // 256-byte steps
@@ -371,33 +506,16 @@ Ws carve(const vs_ntex_config& c, int rows, void* ws) {
   w.dH2 = take(rows * H);
   w.dH1 = take(rows * H);
   w.dX = take(rows * LF);
+  w.W2t = take(H * C);
+  w.W1t = take(H * H);
+  w.W0t = take(H * LF);
   return w;
 }
 
 size_t ws_floats(const vs_ntex_config& c, int rows) {
   const size_t LF = (size_t)c.levels * c.features, H = c.hidden, C = c.out_ch;
   auto r = [](size_t n) { return (n + 63) & ~(size_t)63; };
-  return 2 * r(rows * LF) + 4 * r(rows * H) + 2 * r(rows * C);
-}
-
-// Row-major Y[rows, m] = A[rows, k] B[m, k]^T (+ beta Y), as column-major
-// Y^T = B A^T.
-cublasStatus_t gemm_abt(cublasHandle_t h, int rows, int m, int k, const float* A, const float* B, float* Y,
-                        float beta) {
-  const float one = 1.0f;
-  return cublasSgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, m, rows, k, &one, B, k, A, k, &beta, Y, m);
-}
-
-// Row-major Y[rows, k] = A[rows, m] B[m, k], as column-major Y^T = B^T A^T.
-cublasStatus_t gemm_ab(cublasHandle_t h, int rows, int k, int m, const float* A, const float* B, float* Y) {
-  const float one = 1.0f, zero = 0.0f;
-  return cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, k, rows, m, &one, B, k, A, m, &zero, Y, k);
-}
-
-// Row-major dW[m, k] += D[rows, m]^T A[rows, k], as column-major dW^T += A^T D.
-cublasStatus_t gemm_atb_acc(cublasHandle_t h, int rows, int m, int k, const float* D, const float* A, float* dW) {
-  const float one = 1.0f;
-  return cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, k, m, rows, &one, A, k, D, m, &one, dW, k);
+  return 64 + 2 * r(rows * LF) + 4 * r(rows * H) + 2 * r(rows * C) + r(H * C) + r(H * H) + r(H * LF);
 }
 
 #define VS_TRY_CUDA(x)                          \
@@ -405,29 +523,92 @@ cublasStatus_t gemm_atb_acc(cublasHandle_t h, int rows, int m, int k, const floa
     cudaError_t e_ = (x);                       \
     if (e_ != cudaSuccess) return (int)e_;      \
   } while (0)
-#define VS_TRY_BLAS(x)                                   \
-  do {                                                   \
-    if ((x) != CUBLAS_STATUS_SUCCESS) return -1000;      \
+
+// Dynamic shared memory of k_gemm_abt_tc for N x K operands, and the
+// tensor-memory columns of its accumulator; the request also keeps the CTAs
+// per SM within the 512 tensor-memory columns, so an allocation never waits.
+struct TcShape {
+  size_t smem;
+  int cols;
+};
+TcShape tc_shape(int N, int K) {
+  const int Kp = (K + 7) & ~7, Np = (N + 15) & ~15;
+  int cols = 32;
+  while (cols < Np) cols *= 2;
+  size_t smem = sizeof(float) * (size_t)Kp * (kTcRows + Np) + 16;
+  const size_t per_sm = 228 * 1024, floor_smem = per_sm / (512 / cols) + 1024;
+  return {smem > floor_smem ? smem : floor_smem, cols};
+}
+constexpr size_t kTcMaxSmem = 200 * 1024;
+
+template <int EPI>
+int launch_tc(const float* A, const float* B, float* Y, int rows, int N, int K, const float* bias, const float* H,
+              float* db, int* status, cudaStream_t st) {
+  static bool configured = false;   // idempotent; a race only repeats the call
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_abt_tc<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTcMaxSmem);
+    if (e != cudaSuccess) return (int)e;
+    configured = true;
+  }
+  const TcShape s = tc_shape(N, K);
+  k_gemm_abt_tc<EPI><<<(unsigned)((rows + kTcRows - 1) / kTcRows), kTcThreads, s.smem, st>>>(
+      A, B, Y, rows, N, K, bias, H, db, status, s.cols, 1ll << 22);
+  return (int)cudaGetLastError();
+}
+
+// Y = A B^T with epilogue epi (rows x N outputs, K inner): FP32 pipes, or
+// the tensor cores in TF32 when tc and the operands fit (N <= 256).
+int gemm_abt(bool tc, int epi, const float* A, const float* B, float* Y, int rows, int N, int K, const float* bias,
+             const float* H, float* db, int* status, cudaStream_t st) {
+  if (tc && N <= 256 && tc_shape(N, K).smem <= kTcMaxSmem) {
+    switch (epi) {
+      case EPI_BIAS: return launch_tc<EPI_BIAS>(A, B, Y, rows, N, K, bias, H, db, status, st);
+      case EPI_BIAS_RELU: return launch_tc<EPI_BIAS_RELU>(A, B, Y, rows, N, K, bias, H, db, status, st);
+      case EPI_MASK_COLSUM: return launch_tc<EPI_MASK_COLSUM>(A, B, Y, rows, N, K, bias, H, db, status, st);
+      default: return launch_tc<EPI_NONE>(A, B, Y, rows, N, K, bias, H, db, status, st);
+    }
+  }
+  const dim3 grid((unsigned)((rows + kGM - 1) / kGM), (unsigned)((N + kGN - 1) / kGN));
+  switch (epi) {
+    case EPI_BIAS: k_gemm_abt<EPI_BIAS><<<grid, kThreads, 0, st>>>(A, B, Y, rows, N, K, bias, H, db); break;
+    case EPI_BIAS_RELU: k_gemm_abt<EPI_BIAS_RELU><<<grid, kThreads, 0, st>>>(A, B, Y, rows, N, K, bias, H, db); break;
+    case EPI_MASK_COLSUM:
+      k_gemm_abt<EPI_MASK_COLSUM><<<grid, kThreads, 0, st>>>(A, B, Y, rows, N, K, bias, H, db);
+      break;
+    default: k_gemm_abt<EPI_NONE><<<grid, kThreads, 0, st>>>(A, B, Y, rows, N, K, bias, H, db);
+  }
+  return (int)cudaGetLastError();
+}
+
+// dW += D^T A over `rows` texels.
+int gemm_atb(const float* D, const float* A, float* dW, int rows, int N, int K, cudaStream_t st) {
+  const dim3 grid((unsigned)(((N + kWN - 1) / kWN) * ((K + kWK - 1) / kWK)), (unsigned)((rows + kWRows - 1) / kWRows));
+  k_gemm_atb<<<grid, kThreads, 0, st>>>(D, A, dW, rows, N, K);
+  return (int)cudaGetLastError();
+}
+
+#define VS_TRY(x)            \
+  do {                       \
+    int r_ = (x);            \
+    if (r_) return r_;       \
   } while (0)
 
 // Forward of one chunk: activations X, H1, H2, Y in the workspace.
-int chunk_forward(cublasHandle_t h, const vs_ntex_config& c, const Enc& e, const Views& P, int W, int H, int n0,
-                  int rows, const Ws& w, cudaStream_t st) {
+int chunk_forward(const vs_ntex_config& c, const Enc& e, const Views& P, int W, int H, int n0, int rows, const Ws& w,
+                  cudaStream_t st) {
   const int LF = c.levels * c.features, Hd = c.hidden, C = c.out_ch;
+  const bool tc = c.tensor_cores != 0;
   k_encode<<<blocks_for((long long)rows * c.levels), kThreads, 0, st>>>(e, P.table, W, H, n0, rows, w.X);
   VS_TRY_CUDA(cudaGetLastError());
-  VS_TRY_BLAS(gemm_abt(h, rows, Hd, LF, w.X, P.W0, w.H1, 0.0f));
-  bias_act(w.H1, P.b0, rows, Hd, 1, st);
-  VS_TRY_BLAS(gemm_abt(h, rows, Hd, Hd, w.H1, P.W1, w.H2, 0.0f));
-  bias_act(w.H2, P.b1, rows, Hd, 1, st);
-  VS_TRY_BLAS(gemm_abt(h, rows, C, Hd, w.H2, P.W2, w.Y, 0.0f));
-  bias_act(w.Y, P.b2, rows, C, 0, st);
-  VS_TRY_CUDA(cudaGetLastError());
+  VS_TRY(gemm_abt(tc, EPI_BIAS_RELU, w.X, P.W0, w.H1, rows, Hd, LF, P.b0, nullptr, nullptr, w.status, st));
+  VS_TRY(gemm_abt(tc, EPI_BIAS_RELU, w.H1, P.W1, w.H2, rows, Hd, Hd, P.b1, nullptr, nullptr, w.status, st));
+  VS_TRY(gemm_abt(tc, EPI_BIAS, w.H2, P.W2, w.Y, rows, C, Hd, P.b2, nullptr, nullptr, w.status, st));
   return 0;
 }
 
-int forward(cublasHandle_t h, const vs_ntex_config& c, const float* params, int W, int H, void* texels, int dtype,
-            int pitch, int ch0, void* ws, cudaStream_t st) {
+int forward(const vs_ntex_config& c, const float* params, int W, int H, void* texels, int dtype, int pitch, int ch0,
+            void* ws, cudaStream_t st) {
   const float* v[7];
   views(c, params, v);
   const Views P{v[0], v[1], v[2], v[3], v[4], v[5], v[6]};
@@ -437,8 +618,7 @@ int forward(cublasHandle_t h, const vs_ntex_config& c, const float* params, int 
   const Ws w = carve(c, chunk, ws);
   for (int n0 = 0; n0 < N; n0 += chunk) {
     const int rows = N - n0 < chunk ? N - n0 : chunk;
-    int r = chunk_forward(h, c, e, P, W, H, n0, rows, w, st);
-    if (r) return r;
+    VS_TRY(chunk_forward(c, e, P, W, H, n0, rows, w, st));
     k_write_texels<<<blocks_for((long long)rows * c.out_ch), kThreads, 0, st>>>(w.Y, c.out_ch, n0, rows, texels, dtype,
                                                                                  pitch, ch0);
     VS_TRY_CUDA(cudaGetLastError());
@@ -446,8 +626,8 @@ int forward(cublasHandle_t h, const vs_ntex_config& c, const float* params, int 
   return 0;
 }
 
-int backward(cublasHandle_t h, const vs_ntex_config& c, const float* params, int W, int H, const float* grad_texels,
-             int pitch, int ch0, float* grads, void* ws, cudaStream_t st) {
+int backward(const vs_ntex_config& c, const float* params, int W, int H, const float* grad_texels, int pitch, int ch0,
+             float* grads, void* ws, cudaStream_t st) {
   const float* v[7];
   views(c, params, v);
   const Views P{v[0], v[1], v[2], v[3], v[4], v[5], v[6]};
@@ -456,26 +636,29 @@ int backward(cublasHandle_t h, const vs_ntex_config& c, const float* params, int
   const Enc e = make_enc(c);
   const int N = W * H;
   const int LF = c.levels * c.features, Hd = c.hidden, C = c.out_ch;
+  const bool tc = c.tensor_cores != 0;
   const int chunk = N < kNtexChunk ? N : kNtexChunk;
   const Ws w = carve(c, chunk, ws);
+  // the adjoint's B operands: W2^T, W1^T, W0^T
+  k_transpose<<<blocks_for((long long)C * Hd), kThreads, 0, st>>>(P.W2, w.W2t, C, Hd);
+  k_transpose<<<blocks_for((long long)Hd * Hd), kThreads, 0, st>>>(P.W1, w.W1t, Hd, Hd);
+  k_transpose<<<blocks_for((long long)Hd * LF), kThreads, 0, st>>>(P.W0, w.W0t, Hd, LF);
+  VS_TRY_CUDA(cudaGetLastError());
   for (int n0 = 0; n0 < N; n0 += chunk) {
     const int rows = N - n0 < chunk ? N - n0 : chunk;
-    int r = chunk_forward(h, c, e, P, W, H, n0, rows, w, st);   // recompute the activations
-    if (r) return r;
+    VS_TRY(chunk_forward(c, e, P, W, H, n0, rows, w, st));   // recompute the activations
     k_gather_grad<<<blocks_for((long long)rows * C), kThreads, 0, st>>>(grad_texels, C, n0, rows, pitch, ch0, w.dY);
     VS_TRY_CUDA(cudaGetLastError());
-    // output layer
-    VS_TRY_BLAS(gemm_atb_acc(h, rows, C, Hd, w.dY, w.H2, g[5]));
+    // output layer: dW2 += dY^T H2, db2 += column sums of dY, dH2 = (dY W2) * (H2 > 0), db1 += its sums
+    VS_TRY(gemm_atb(w.dY, w.H2, g[5], rows, C, Hd, st));
     relu_colsum(w.dY, nullptr, rows, C, g[6], st);
-    VS_TRY_BLAS(gemm_ab(h, rows, Hd, C, w.dY, P.W2, w.dH2));
-    relu_colsum(w.dH2, w.H2, rows, Hd, g[4], st);
-    // second hidden layer
-    VS_TRY_BLAS(gemm_atb_acc(h, rows, Hd, Hd, w.dH2, w.H1, g[3]));
-    VS_TRY_BLAS(gemm_ab(h, rows, Hd, Hd, w.dH2, P.W1, w.dH1));
-    relu_colsum(w.dH1, w.H1, rows, Hd, g[2], st);
-    // first hidden layer and the encoding
-    VS_TRY_BLAS(gemm_atb_acc(h, rows, Hd, LF, w.dH1, w.X, g[1]));
-    VS_TRY_BLAS(gemm_ab(h, rows, LF, Hd, w.dH1, P.W0, w.dX));
+    VS_TRY(gemm_abt(tc, EPI_MASK_COLSUM, w.dY, w.W2t, w.dH2, rows, Hd, C, nullptr, w.H2, g[4], w.status, st));
+    // second hidden layer: dW1 += dH2^T H1, dH1 = (dH2 W1) * (H1 > 0), db0 += its sums
+    VS_TRY(gemm_atb(w.dH2, w.H1, g[3], rows, Hd, Hd, st));
+    VS_TRY(gemm_abt(tc, EPI_MASK_COLSUM, w.dH2, w.W1t, w.dH1, rows, Hd, Hd, nullptr, w.H1, g[2], w.status, st));
+    // first layer and the encoding: dW0 += dH1^T X, dX = dH1 W0
+    VS_TRY(gemm_atb(w.dH1, w.X, g[1], rows, Hd, LF, st));
+    VS_TRY(gemm_abt(tc, EPI_NONE, w.dH1, w.W0t, w.dX, rows, LF, Hd, nullptr, nullptr, nullptr, w.status, st));
     {
       const unsigned nseg = (unsigned)((rows + kSeg - 1) / kSeg);
       const unsigned gx = nseg < 256u ? nseg : 256u;

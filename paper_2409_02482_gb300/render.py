@@ -325,7 +325,12 @@ class NeuralTexture:
         self.step = 0
         nb = ctypes.c_size_t()
         check(ctx.lib.vs_ntex_workspace_size(ctypes.byref(self.cfg), self.tex_w, self.tex_h, ctypes.byref(nb)))
-        self.ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device=device)
+        self.ws = torch.zeros(max(nb.value, 256), dtype=torch.uint8, device=device)
+
+    def status(self) -> int:
+        """The workspace's status word (synchronises): 0, or 1 when a
+        bounded wait of the tensor-core layers ran out."""
+        return int(self.ws[:4].view(torch.int32).item())
 
     def forward(self, texels: torch.Tensor, ch0: int = 0, stream=None):
         """Write channels [ch0, ch0 + C) of texels [H, W, pitch] (f32 or f16)."""

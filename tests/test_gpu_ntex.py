@@ -97,6 +97,60 @@ def test_ntex_tensor_core_mode_is_close(vs, ctx):
         r, q = nt.grads[off:off + n], tc.grads[off:off + n]
         bar = 1e-5 if name == "b2" else 8e-2
         assert (q - r).norm().item() <= bar * r.norm().item(), name
+    assert tc.status() == 0 and nt.status() == 0
+
+
+# the benchmark's networks: 16 levels x 2 features, 2^19-row tables, two
+# 64-wide hidden layers, 1 (opacity) or 27 (SH-2 colour) outputs, 2048^2 texels
+BENCH_CFG = dict(levels=16, features=2, log2_table=19, base_res=16, growth=1.447, hidden=64)
+
+
+@pytest.mark.parametrize("tensor_cores", [False, True])
+@pytest.mark.parametrize("out_ch", [1, 27])
+def test_ntex_bench_configuration_matches_oracle(vs, ctx, out_ch, tensor_cores):
+    """The benchmark's neural texture at full size (one 2048^2 texture),
+    forward into FP32 texels and the adjoint of a gradient on 4096 sampled
+    texels, against the oracle evaluated on those texels.  FP32 layers: the
+    texels within 1e-4 and every parameter block's gradient within 1e-4 of
+    its largest entry.  TF32 layers (tcgen05): within the bars derived for
+    TF32 (see test_ntex_tensor_core_mode_is_close), and the status word
+    clear (no bounded wait ran out)."""
+    cfg = ntex.NtexConfig(out_ch=out_ch, **BENCH_CFG)
+    W = H = 2048
+    params = synth.ntex_init(cfg.shapes(), np.random.default_rng(40 + out_ch))
+    lay, _ = cfg.layout()
+    off, shp = lay[0][1], lay[0][2]
+    n = int(np.prod(shp))
+    params[off:off + n] = np.random.default_rng(41).normal(0, 0.5, n).astype(np.float32)
+    nt = vs.NeuralTexture(ctx, cfg.levels, cfg.features, cfg.log2_table, cfg.base_res, cfg.growth, cfg.hidden,
+                          cfg.out_ch, tex_w=W, tex_h=H, tensor_cores=tensor_cores)
+    nt.params.copy_(torch.from_numpy(params))
+    tex = torch.zeros((H, W, out_ch), device="cuda")
+    nt.forward(tex)
+    idx = np.sort(np.random.default_rng(42).choice(W * H, 4096, replace=False))
+    ref = ntex.forward_at(cfg, params.astype(np.float64), W, H, idx)
+    got = tex.reshape(-1, out_ch).cpu().numpy()[idx].astype(np.float64)
+    scale = max(1.0, np.abs(ref).max())
+    if tensor_cores:
+        assert np.abs(got - ref).max() <= 1e-2 * scale
+        assert np.linalg.norm(got - ref) <= 2e-3 * np.linalg.norm(ref)
+    else:
+        assert np.abs(got - ref).max() <= 1e-4 * scale
+    g = np.random.default_rng(43).normal(size=(len(idx), out_ch)).astype(np.float32)
+    dense = torch.zeros((H * W, out_ch), device="cuda")
+    dense[torch.from_numpy(idx).cuda()] = torch.from_numpy(g).cuda()
+    nt.backward(dense.reshape(H, W, out_ch))
+    rg = ntex.backward(cfg, params.astype(np.float64), W, H, g.astype(np.float64), texels=idx)
+    q = nt.grads.cpu().numpy().astype(np.float64)
+    for name, o, sh in lay:
+        k = int(np.prod(sh))
+        r, v = rg[o:o + k], q[o:o + k]
+        if tensor_cores:
+            bar = 1e-5 if name == "b2" else 8e-2
+            assert np.linalg.norm(v - r) <= bar * np.linalg.norm(r) + 1e-30, name
+        else:
+            assert np.abs(v - r).max() <= 1e-4 * max(np.abs(r).max(), 1e-30), name
+    assert nt.status() == 0
 
 
 def test_ntex_backward_matches_oracle(vs, ctx):

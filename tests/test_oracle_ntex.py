@@ -9,6 +9,7 @@ geometry, weights, dense vs hashed levels -- not its constant."""
 import numpy as np
 import pytest
 
+import synth
 from oracle import ntex
 
 
@@ -99,3 +100,21 @@ def test_adam_first_step_closed_form():
     p1, m, v = ntex.adam(p, g, z, z, 1, lr=0.01, eps=1e-15)
     assert np.allclose(p1, p - 0.01 * np.sign(g))
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.01 * g * g)
+
+
+def test_sampled_texels_equal_the_full_texture():
+    """forward_at / backward(texels=...) evaluate the same definition on a
+    subset of texels: the subset of the full forward, and the full adjoint
+    of a gradient that is zero outside the subset."""
+    cfg = ntex.NtexConfig(levels=4, features=2, log2_table=8, base_res=3, growth=1.7, hidden=8, out_ch=5)
+    params = synth.ntex_init(cfg.shapes(), np.random.default_rng(3)).astype(np.float64)
+    W, H = 13, 11
+    idx = np.array([0, 5, 17, 60, 142])
+    full, _ = ntex.forward(cfg, params, W, H)
+    assert np.array_equal(ntex.forward_at(cfg, params, W, H, idx), full.reshape(-1, cfg.out_ch)[idx])
+    g = np.random.default_rng(4).normal(size=(len(idx), cfg.out_ch))
+    dense = np.zeros((H * W, cfg.out_ch))
+    dense[idx] = g
+    a = ntex.backward(cfg, params, W, H, dense.reshape(H, W, cfg.out_ch))
+    b = ntex.backward(cfg, params, W, H, g, texels=idx)
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-15)

@@ -1197,7 +1197,7 @@ def test_backward_error_scales():
         hits, _, _ = oracle.raster_scene(sc, cam)
         g = np.random.default_rng(41).normal(size=(cam.height, cam.width, 3))
         plain = oracle.backward(sc, cam, hits, g, bg=bg)
-        grads, (sw, s1) = oracle.backward(sc, cam, hits, g, bg=bg, with_scale=True)
+        grads, (sw, s1, sy) = oracle.backward(sc, cam, hits, g, bg=bg, with_scale=True)
         same, _ = oracle.backward(sc, cam, hits, g, bg=bg, with_scale=True, gmag=np.abs(g))
         for a, b, c, w, r in zip(plain, grads, same, sw, s1):
             assert np.array_equal(a, b) and np.array_equal(a, c)
@@ -1206,16 +1206,24 @@ def test_backward_error_scales():
         assert max(float(w.max()) for w in sw) > 0
         # a tap-weight allowance widens S_1 beside footprints near texel
         # lines and changes neither the gradient nor S_w
-        g2, (sw2, s12) = oracle.backward(sc, cam, hits, g, bg=bg, with_scale=True, weight_err=0.25)
+        g2, (sw2, s12, _) = oracle.backward(sc, cam, hits, g, bg=bg, with_scale=True, weight_err=0.25)
         for a, b, w, w2, r, r2 in zip(grads, g2, sw, sw2, s1, s12):
             assert np.array_equal(a, b) and np.array_equal(w, w2) and np.all(r2 >= r)
         assert any(np.any((r2 > 0) & (r == 0)) for r, r2 in zip(s1, s12))
         # (2) nonnegative output gradient: no cancellation in the colour terms
         gp = np.abs(g)
-        grads, (sw, _) = oracle.backward(sc, cam, hits, gp, bg=bg, with_scale=True)
+        grads, (sw, _, sy) = oracle.backward(sc, cam, hits, gp, bg=bg, with_scale=True)
         cols = slice(0, 3) if fmt == FMT_RGBA_F32 else slice(1, 4)
         for a, w in zip(grads, sw):
             assert np.allclose(np.abs(a[..., cols]), w[..., cols], rtol=1e-12, atol=0)
+        # S_y: the coefficient terms without their basis value -- none for
+        # RGBA and the alpha logit; for Y_0 (a constant) S_w = Y_0 S_y
+        for w, y in zip(sw, sy):
+            if fmt == FMT_RGBA_F32:
+                assert not y.any()
+            else:
+                assert not y[..., 0].any()
+                assert np.allclose(w[..., 1:4], oracle.sh_basis(0, [0.0, 0.0, 1.0])[0] * y[..., 1:4], rtol=1e-12)
         # the alpha terms do cancel somewhere: strictly larger scale there
         assert any(np.any(w[..., 3 if fmt == FMT_RGBA_F32 else 0] > np.abs(a[..., 3 if fmt == FMT_RGBA_F32 else 0]) * 1.01)
                    for a, w in zip(grads, sw))
@@ -1228,7 +1236,7 @@ def test_backward_error_scales():
     cam = synth.look_at((1.1, -2.6, 0.7), width=32, height=32)
     hits, _, _ = oracle.raster_scene(sc, cam)
     g = np.random.default_rng(13).normal(size=(32, 32, 3))
-    _, (sw, s1) = oracle.backward(sc, cam, hits, g, bg=bg, with_scale=True)
+    _, (sw, s1, sy) = oracle.backward(sc, cam, hits, g, bg=bg, with_scale=True)
     want_rgb, want_a = np.zeros((3, 3)), np.zeros(3)
     for y in range(32):
         for x in range(32):
