@@ -292,7 +292,7 @@ typedef struct {
  * Workspace: vs_workspace_size of all n items runs them in one launch.  A
  * smaller workspace runs them as consecutive launches over runs of items,
  * each run the longest that fits (e.g. hundreds of 4K views whose per-shell
- * visibility words and triangle records would not all fit); results are
+ * visibility words would not all fit); results are
  * the same, the runs do not overlap.  Every item is checked before anything
  * is enqueued.
  * Errors: as vs_render; VS_ERR_INVALID_ARG for n < 1; VS_ERR_WORKSPACE when

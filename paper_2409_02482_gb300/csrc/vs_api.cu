@@ -247,9 +247,6 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
     return fail(VS_ERR_INVALID_ARG, "VS_FLAG_LOSS_L1 and VS_FLAG_LOSS_L2 are exclusive");
   P.full = false;
   for (int j = 0; j < n; ++j) P.full = P.full || needs_clip(*req[j].obj, *req[j].cam) || req[j].layers;
-  // triangle records for the fused adjoint; reserved whatever kernels run,
-  // so that the size does not depend on bounds read on a later call
-  const bool records = clear_vis && do_bwd;
   const int raster_per_unit = 32 * shape.raster_rounds;
   const int shade_per_unit = 32 * shape.shade_rounds;
   size_t off = sizeof(WsHeader);
@@ -322,8 +319,6 @@ vs_status make_plan(const ItemReq* req, int n, const float* bg, int do_bwd, bool
       }
       s.vsetup = reinterpret_cast<int4*>(ws ? ws + off : nullptr);
       off = align256(off + sizeof(int4) * (size_t)d.num_verts);
-      s.trec = (records && ws && !P.full) ? reinterpret_cast<int4*>(ws + off) : nullptr;
-      if (records) off = align256(off + 4 * sizeof(int4) * (size_t)d.num_tris);
       it.setup_pre[i + 1] = it.setup_pre[i] + (d.num_verts + kSetupPerUnit - 1) / kSetupPerUnit;
       it.raster_pre[i + 1] = it.raster_pre[i] + (d.num_tris + raster_per_unit - 1) / raster_per_unit;
     }

@@ -110,7 +110,7 @@ struct alignas(16) DShell {
   int32_t vec;                 // texel load width in values (1, 2, 4, 8)
   int32_t gvec;                // gradient atomic width in floats (1, 2, 4)
   int32_t wide;                // texels 32-byte aligned (base and pitch): 256-bit loads
-  int4* trec;                  // [nt][4] this view's triangle records for shading (workspace), or null
+  int4* pad5;                  // unused
   // VS_TEX_SH_U8: byte offset of band l in tex, resolution shift per band,
   // decode value = vmin + vscale * q
   long long boff[4];

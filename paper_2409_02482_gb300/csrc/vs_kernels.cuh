@@ -78,20 +78,6 @@ __device__ __forceinline__ int load_tri(const DShell& s, const DCam& c, int t, T
   return make_tri(__ldcg(s.vsetup + idx[0]), __ldcg(s.vsetup + idx[1]), __ldcg(s.vsetup + idx[2]), c.W, c.H, T);
 }
 
-// Shading record of a triangle the raster accepted, for this view: snapped
-// positions, 1/w and UVs of its vertices in one 64-byte entry, so that the
-// adjoint's shading reaches a fragment's geometry with one dependent load
-// instead of two (indices, then vertices).  Bit copies: shading computes the
-// same values as from the vertex arrays.
-__device__ __forceinline__ void store_tri_rec(const DShell& s, int t, const Tri& T, const int idx[3]) {
-  const float2 a = __ldg(s.uv + idx[0]), b = __ldg(s.uv + idx[1]), c = __ldg(s.uv + idx[2]);
-  int4* rp = s.trec + 4 * (size_t)t;
-  rp[0] = make_int4(T.X[0], T.Y[0], T.X[1], T.Y[1]);
-  rp[1] = make_int4(T.X[2], T.Y[2], __float_as_int(T.iw[0]), __float_as_int(T.iw[1]));
-  rp[2] = make_int4(__float_as_int(T.iw[2]), __float_as_int(a.x), __float_as_int(a.y), __float_as_int(b.x));
-  rp[3] = make_int4(__float_as_int(b.y), __float_as_int(c.x), __float_as_int(c.y), 0);
-}
-
 template <bool HINT>
 __device__ __forceinline__ void raster_pixel(const Tri& T, int t, int x, int y, int W, unsigned long long* vis) {
   long long e[3];
@@ -187,9 +173,6 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
       front = 1;
       const int bw = T.xhi - T.xlo + 1, bh = T.yhi - T.ylo + 1;
       if (bw > 0 && bh > 0) {
-        if constexpr (HINT && !FULL) {   // the fused adjoint's raster
-          if (s.trec) store_tri_rec(s, t, T, idx);   // every fragment of t comes from this raster
-        }
         if (bw * bh <= kSmallMaxPixels) {
           npx = bw * bh;
           const int ox = 256 * T.xlo + 128, oy = 256 * T.ylo + 128;
@@ -342,28 +325,6 @@ __device__ __forceinline__ int load_tri_shade(const DShell& s, int t, Tri& T, in
     T.Y[j] = v.y;
     T.iw[j] = __int_as_float(v.z);
   }
-  const long long a2 = (long long)(T.X[1] - T.X[0]) * (T.Y[2] - T.Y[0]) -
-                       (long long)(T.X[2] - T.X[0]) * (T.Y[1] - T.Y[0]);
-  return a2 < 0 ? 0 : 1;
-}
-
-// The same from the triangle's record (written by this item's raster, which
-// produced every hit that refers to it).
-__device__ __forceinline__ int load_tri_rec(const DShell& s, int t, Tri& T, float2 uv[3]) {
-  const int4* rp = s.trec + 4 * (size_t)t;
-  const int4 a = __ldcg(rp), b = __ldcg(rp + 1), c = __ldcg(rp + 2), d = __ldcg(rp + 3);
-  T.X[0] = a.x;
-  T.Y[0] = a.y;
-  T.X[1] = a.z;
-  T.Y[1] = a.w;
-  T.X[2] = b.x;
-  T.Y[2] = b.y;
-  T.iw[0] = __int_as_float(b.z);
-  T.iw[1] = __int_as_float(b.w);
-  T.iw[2] = __int_as_float(c.x);
-  uv[0] = make_float2(__int_as_float(c.y), __int_as_float(c.z));
-  uv[1] = make_float2(__int_as_float(c.w), __int_as_float(d.x));
-  uv[2] = make_float2(__int_as_float(d.y), __int_as_float(d.z));
   const long long a2 = (long long)(T.X[1] - T.X[0]) * (T.Y[2] - T.Y[0]) -
                        (long long)(T.X[2] - T.X[0]) * (T.Y[1] - T.Y[0]);
   return a2 < 0 ? 0 : 1;
@@ -665,8 +626,7 @@ static __device__ __forceinline__ void shade_clipped(const DItem& it, const DShe
 //     fragment (4 taps x up to 8 chunks); the other classes give each lane
 //     a fragment.
 // FROM_HITS: hits come from the public int32 buffer (standalone backward)
-// instead of the visibility words.  The fused adjoint (!FROM_HITS, !FULL)
-// reads each fragment's geometry from the raster's triangle records.
+// instead of the visibility words.
 //
 // Shared memory of the warp (shade_warp_bytes), C = frag_cap(K, BWD):
 //   hit  int    [32 K]  triangle per (shell, lane) of the round (1); own
@@ -801,16 +761,11 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
         int idx[3];
         const int y = pp / W, x = pp - y * W;
         float2 uv[3];
-        int r;
-        if (BWD && !FULL && !FROM_HITS && s.trec) {
-          r = t < s.nt ? load_tri_rec(s, t, Tr, uv) : 4;
-        } else {
-          r = t < s.nt ? load_tri_shade(s, t, Tr, idx) : 4;
-          if (r == 0) {
-            uv[0] = __ldg(s.uv + idx[0]);
-            uv[1] = __ldg(s.uv + idx[1]);
-            uv[2] = __ldg(s.uv + idx[2]);
-          }
+        const int r = t < s.nt ? load_tri_shade(s, t, Tr, idx) : 4;
+        if (r == 0) {
+          uv[0] = __ldg(s.uv + idx[0]);
+          uv[1] = __ldg(s.uv + idx[1]);
+          uv[2] = __ldg(s.uv + idx[2]);
         }
         if (FULL && r == 2) {
           // a vertex nearer than znear (or off the guard band): the triangle

@@ -607,6 +607,32 @@ int chunk_forward(const vs_ntex_config& c, const Enc& e, const Views& P, int W, 
   return 0;
 }
 
+// The fused tensor-core forward (TF32 mode) for networks of 64-wide hidden
+// layers with at most 64 encoding values and outputs; one persistent launch
+// over the whole texture.  Returns -1 when the shape is not covered.
+int fused_forward_tc(const vs_ntex_config& c, const Views& P, const Enc& e, int W, int H, void* texels, int dtype,
+                     int pitch, int ch0, int* status, cudaStream_t st) {
+  const int LF = c.levels * c.features;
+  if (!c.tensor_cores || c.hidden != kMlpH || LF > 64 || c.out_ch > 64) return -1;
+  const int smem = mlp_fwd_smem(LF, c.out_ch);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t err = cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (err != cudaSuccess) return (int)err;
+    configured = true;
+  }
+  int dev = 0, sms = 0;
+  VS_TRY_CUDA(cudaGetDevice(&dev));
+  VS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // two CTAs per SM at most: 2 x 256 tensor-memory columns, and the shared
+  // memory of a third would not fit
+  const int per_sm = 2 * (smem + 1024) <= 228 * 1024 ? 2 : 1;
+  MlpFwdArgs a{P.table, P.W0, P.b0, P.W1, P.b1, P.W2, P.b2, texels, W, H, W * H, c.out_ch, LF, dtype, pitch, ch0,
+               status, 1ll << 22};
+  k_mlp_fwd_tc<<<sms * per_sm, kTcThreads, smem, st>>>(a, e);
+  return (int)cudaGetLastError();
+}
+
 int forward(const vs_ntex_config& c, const float* params, int W, int H, void* texels, int dtype, int pitch, int ch0,
             void* ws, cudaStream_t st) {
   const float* v[7];
@@ -614,6 +640,10 @@ int forward(const vs_ntex_config& c, const float* params, int W, int H, void* te
   const Views P{v[0], v[1], v[2], v[3], v[4], v[5], v[6]};
   const Enc e = make_enc(c);
   const int N = W * H;
+  {
+    const int r = fused_forward_tc(c, P, e, W, H, texels, dtype, pitch, ch0, carve(c, 1, ws).status, st);
+    if (r >= 0) return r;
+  }
   const int chunk = N < kNtexChunk ? N : kNtexChunk;
   const Ws w = carve(c, chunk, ws);
   for (int n0 = 0; n0 < N; n0 += chunk) {

@@ -120,9 +120,8 @@ def test_workspace_size_covers_the_dominant_terms(lib):
     cams = (_abi.vs_camera * 1)(_cam())
     size = ctypes.c_size_t()
     assert lib.vs_workspace_size(_fake_ctx(), objs, cams, 1, 0, ctypes.byref(size)) == 0
-    # visibility words, snapped vertices and the fused adjoint's 64-byte
-    # triangle records (the size covers every call, the adjoint included)
-    need = 8 * 5 * 800 * 600 + sum(16 * d.num_verts + 64 * d.num_tris for d in descs)
+    # visibility words and snapped vertices
+    need = 8 * 5 * 800 * 600 + sum(16 * d.num_verts for d in descs)
     assert need <= size.value <= need + 64 * 1024
     # batch of 3 items ~ three times one item
     objs3 = (ctypes.c_void_p * 3)(obj.value, obj.value, obj.value)
