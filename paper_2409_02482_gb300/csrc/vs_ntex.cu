@@ -656,6 +656,30 @@ int forward(const vs_ntex_config& c, const float* params, int W, int H, void* te
   return 0;
 }
 
+// The fused tensor-core adjoint (TF32 mode) for 64-wide hidden layers, at
+// most 32 encoding values with F dividing 16, and at most 32 outputs; one
+// persistent launch over the whole texture.  -1 when not covered.
+int fused_backward_tc(const vs_ntex_config& c, const Views& P, float* const g[7], const Enc& e, int W, int H,
+                      const float* grad, int pitch, int ch0, int* status, cudaStream_t st) {
+  const int LF = c.levels * c.features;
+  if (!c.tensor_cores || c.hidden != kMlpH || LF > 32 || c.out_ch > 32 || 16 % c.features != 0) return -1;
+  const int smem = mlp_bwd_smem(LF, c.out_ch);
+  if (smem > 227 * 1024) return -1;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t err = cudaFuncSetAttribute(k_mlp_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return (int)err;
+    configured = true;
+  }
+  int dev = 0, sms = 0;
+  VS_TRY_CUDA(cudaGetDevice(&dev));
+  VS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  MlpBwdArgs a{P.table, P.W0, P.b0, P.W1, P.b1, P.W2, grad, g[0], g[1], g[2], g[3], g[4], g[5], g[6],
+               W, H, W * H, c.out_ch, LF, pitch, ch0, status, 1ll << 22};
+  k_mlp_bwd_tc<<<sms, kTcThreads, smem, st>>>(a, e);   // one CTA per SM (shared memory)
+  return (int)cudaGetLastError();
+}
+
 int backward(const vs_ntex_config& c, const float* params, int W, int H, const float* grad_texels, int pitch, int ch0,
              float* grads, void* ws, cudaStream_t st) {
   const float* v[7];
@@ -664,6 +688,10 @@ int backward(const vs_ntex_config& c, const float* params, int W, int H, const f
   float* g[7];
   views(c, grads, g);
   const Enc e = make_enc(c);
+  {
+    const int r = fused_backward_tc(c, P, g, e, W, H, grad_texels, pitch, ch0, carve(c, 1, ws).status, st);
+    if (r >= 0) return r;
+  }
   const int N = W * H;
   const int LF = c.levels * c.features, Hd = c.hidden, C = c.out_ch;
   const bool tc = c.tensor_cores != 0;

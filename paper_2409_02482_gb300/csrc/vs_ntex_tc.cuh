@@ -251,10 +251,11 @@ __device__ __forceinline__ void stage_op(float* dst, const float* src, int n_row
   }
 }
 
-// Issues the MMAs of D[128 x Np] = A[128 x Kp] B[Np x Kp]^T (one thread) and
-// commits them to the mbarrier.
+// Issues the MMAs of D[128 x Np] = A[128 x Kp] B[Np x Kp]^T (one thread)
+// and, with commit, commits every MMA this thread issued so far to the
+// mbarrier (one phase).
 __device__ __forceinline__ void mma_tile(uint32_t d_tmem, const float* A, const float* B, int Kp, int Np,
-                                         uint64_t* bar) {
+                                         uint64_t* bar, bool commit = true) {
   const uint32_t a0 = smem_u32(A), b0 = smem_u32(B), sbo = (uint32_t)(Kp / 4) * 128u;
   const uint32_t id = idesc_tf32(Np);
   for (int s = 0; s < Kp / 8; ++s) {
@@ -266,8 +267,9 @@ __device__ __forceinline__ void mma_tile(uint32_t d_tmem, const float* A, const 
         "l"(da), "l"(dbd), "r"(id), "r"(acc)
         : "memory");
   }
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
+  if (commit)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
@@ -300,6 +302,19 @@ __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase, int* st
 }
 
 constexpr int kMlpTmemCols = 256;   // D0 [0, 64), D1 [64, 128), D2 [128, 128 + Cp)
+
+// Four consecutive values k .. k + 3 (k % 4 == 0) of row m: one 16-byte
+// access (a warp's 32 rows then cover 512 contiguous-in-groups bytes:
+// 4 wavefronts, the least for 16-byte accesses).
+__device__ __forceinline__ void st4(float* base, int m, int k, int Kp, float4 v) {
+  *reinterpret_cast<float4*>(op_at(base, m, k, Kp)) = v;
+}
+// TF32(max(v + b, 0)) of four values (live: else zeros).
+__device__ __forceinline__ float4 relu_tf32(const float* v, const float* b, bool live) {
+  if (!live) return make_float4(0.f, 0.f, 0.f, 0.f);
+  return make_float4(tf32_rna(fmaxf(v[0] + __ldg(b), 0.0f)), tf32_rna(fmaxf(v[1] + __ldg(b + 1), 0.0f)),
+                     tf32_rna(fmaxf(v[2] + __ldg(b + 2), 0.0f)), tf32_rna(fmaxf(v[3] + __ldg(b + 3), 0.0f)));
+}
 
 // Dynamic shared memory of k_mlp_fwd_tc for LF inputs and C outputs.
 __host__ __device__ constexpr int mlp_fwd_smem(int LF, int C) {
@@ -372,7 +387,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(const MlpFwdArgs a
       float v[16];
       tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) *op_at(H1s, tid, c0 + j, kMlpH) = tf32_rna(fmaxf(v[j] + __ldg(a.b0 + c0 + j), 0.0f));
+      for (int j = 0; j < 16; j += 4)
+        st4(H1s, tid, c0 + j, kMlpH, relu_tf32(v + j, a.b0 + c0 + j, true));
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -385,7 +401,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(const MlpFwdArgs a
       float v[16];
       tmem_ld16(tmem + lane_base + 64u + (uint32_t)c0, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) *op_at(H2s, tid, c0 + j, kMlpH) = tf32_rna(fmaxf(v[j] + __ldg(a.b1 + c0 + j), 0.0f));
+      for (int j = 0; j < 16; j += 4)
+        st4(H2s, tid, c0 + j, kMlpH, relu_tf32(v + j, a.b1 + c0 + j, true));
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -412,6 +429,281 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(const MlpFwdArgs a
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();   // X, H1, H2 and the accumulators are reused by the next tile
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMlpTmemCols) : "memory");
+}
+
+}  // namespace vsn
+
+namespace vsn {
+
+// ----------------------------------------------------------------------------
+// Fused adjoint of the network on the tensor cores (TF32 mode), for tiles of
+// 128 texels: the forward's hidden layers again (encoding, layer 0, layer 1),
+// then dH2 = (dY W2) * (H2 > 0), dH1 = (dH2 W1) * (H1 > 0), dX = dH1 W0 on
+// the tensor cores (the transposed weights staged once per CTA, K-major),
+// the encoding's adjoint scattered into the tables (runs of lanes on one
+// table row added first), and the weight and bias gradients accumulated in
+// registers over the CTA's tiles (FP32 FMAs on the staged tiles) and added
+// into the gradient vector once at the end.  Shapes: LF <= 32 encoding
+// values, hidden 64, C <= 32 outputs.
+// ----------------------------------------------------------------------------
+struct MlpBwdArgs {
+  const float *table, *W0, *b0, *W1, *b1, *W2;
+  const float* grad;   // dL/d(texels) [N, pitch], channels ch0 .. ch0 + C
+  float *dtable, *dW0, *db0, *dW1, *db1, *dW2, *db2;
+  int W, H, N, C, LF, pitch, ch0;
+  int* status;
+  long long spin_limit;
+};
+
+// dst (m, k) = src[k * src_cols + m]: the transpose of a row-major matrix as
+// a canonical operand (TF32), zero outside rows x K.
+__device__ __forceinline__ void stage_op_tr(float* dst, const float* src, int rows, int rows_p, int K, int src_cols) {
+  const int Kp = (K + 7) & ~7;
+  for (int i = threadIdx.x; i < rows_p * Kp; i += blockDim.x) {
+    const int m = i / Kp, k = i - m * Kp;
+    *op_at(dst, m, k, Kp) = (m < rows && k < K) ? tf32_rna(__ldg(src + (size_t)k * src_cols + m)) : 0.0f;
+  }
+}
+
+__host__ __device__ constexpr int mlp_bwd_smem(int LF, int C) {
+  return op_bytes(kMlpH, LF) + op_bytes(kMlpH, kMlpH) + op_bytes(kMlpH, C) + op_bytes(kMlpH, kMlpH) +
+         op_bytes((LF + 15) & ~15, kMlpH) + op_bytes(128, LF) + 2 * op_bytes(128, kMlpH) + op_bytes(128, C) +
+         2 * op_bytes(128, kMlpH) + 256;
+}
+
+__device__ __forceinline__ float4 ld4(const float* base, int m, int k, int Kp) {
+  return *reinterpret_cast<const float4*>(op_at(const_cast<float*>(base), m, k, Kp));
+}
+
+// Writes the block barrier sequence around a phase whose shared-memory
+// results feed the tensor cores.
+__device__ __forceinline__ void sync_for_mma() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs a, const Enc e) {
+  extern __shared__ __align__(128) char msm[];
+  const int LF = a.LF, LFp = (LF + 7) & ~7, LF16 = (LF + 15) & ~15, Cp = (a.C + 7) & ~7;
+  float* W0s = reinterpret_cast<float*>(msm);      // [64 x LF]   layer 0 B
+  float* W1s = W0s + kMlpH * LFp;                  // [64 x 64]   layer 1 B
+  float* W2Ts = W1s + kMlpH * kMlpH;               // [64 x C]    W2^T: B of dH2
+  float* W1Ts = W2Ts + kMlpH * Cp;                 // [64 x 64]   W1^T: B of dH1
+  float* W0Ts = W1Ts + kMlpH * kMlpH;              // [LF16 x 64] W0^T: B of dX
+  float* Xs = W0Ts + LF16 * kMlpH;                 // [128 x LF]
+  float* H1s = Xs + 128 * LFp;                     // [128 x 64]
+  float* H2s = H1s + 128 * kMlpH;
+  float* dYs = H2s + 128 * kMlpH;                  // [128 x C]
+  float* dH2s = dYs + 128 * Cp;                    // [128 x 64]
+  float* dH1s = dH2s + 128 * kMlpH;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(dH1s + 128 * kMlpH);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kMlpTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  stage_op(W0s, a.W0, kMlpH, kMlpH, LF);
+  stage_op(W1s, a.W1, kMlpH, kMlpH, kMlpH);
+  stage_op_tr(W2Ts, a.W2, kMlpH, kMlpH, a.C, kMlpH);
+  stage_op_tr(W1Ts, a.W1, kMlpH, kMlpH, kMlpH, kMlpH);
+  stage_op_tr(W0Ts, a.W0, LF, LF16, kMlpH, LF);
+  sync_for_mma();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  uint32_t phase = 0;
+  bool ok = true;
+
+  // register accumulators of the weight and bias gradients:
+  //   dW1 rows 4 ib .. +3, columns 8 jb .. +7;   dW0 rows 4 ib .. +3, columns 4 fb .. +3;
+  //   dW2 rows 4 cb .. +3, columns 4 hb .. +3;   db1 / db0 rows of ib (jb == 0 / fb == 0), db2 of cb (hb == 0)
+  const int ib = tid >> 3, jb = tid & 7, fb = tid & 7, cb = tid >> 4, hb = tid & 15;
+  float gW1[4][8], gW0[4][4], gW2[4][4], gb1[4], gb0[4], gb2[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    gb1[i] = gb0[i] = gb2[i] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) gW1[i][j] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) gW0[i][j] = gW2[i][j] = 0.0f;
+  }
+
+  const int tiles = (a.N + 127) / 128;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int n = tile * 128 + tid;
+    const bool live = n < a.N;
+    const int tx = live ? n % a.W : 0, ty = live ? n / a.W : 0;
+    // encoding (row tid of X) and the output gradient (row tid of dY)
+    for (int l = 0; l < e.L; ++l) {
+      float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (live) {
+        const size_t lt = (size_t)l << e.logT;
+        for (int c = 0; c < 4; ++c) {
+          uint32_t row;
+          float w;
+          corner(e, l, tx, ty, a.W, a.H, c, row, w);
+          const float* t = a.table + (lt + row) * e.F;
+          for (int f = 0; f < e.F; ++f) acc[f] = fmaf(w, __ldg(t + f), acc[f]);
+        }
+      }
+      for (int f = 0; f < e.F; ++f) *op_at(Xs, tid, l * e.F + f, LFp) = tf32_rna(acc[f]);
+    }
+    for (int k = LF; k < LFp; ++k) *op_at(Xs, tid, k, LFp) = 0.0f;
+    // dY kept in FP32 (the tensor cores read its TF32 part; the bias and
+    // weight gradients of the output layer use all of it)
+    for (int c = 0; c < Cp; ++c)
+      *op_at(dYs, tid, c, Cp) = (live && c < a.C) ? __ldg(a.grad + (size_t)n * a.pitch + a.ch0 + c) : 0.0f;
+    sync_for_mma();
+    // layer 0 -> H1
+    if (tid == 0) mma_tile(tmem, Xs, W0s, LFp, kMlpH, bar);
+    ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
+    for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 16; j += 4) st4(H1s, tid, c0 + j, kMlpH, relu_tf32(v + j, a.b0 + c0 + j, live));
+    }
+    sync_for_mma();
+    // layer 1 -> H2; dH2 = dY W2 (independent: issued together, one commit)
+    if (tid == 0) {
+      mma_tile(tmem + 64u, H1s, W1s, kMlpH, kMlpH, bar, false);
+      mma_tile(tmem + 128u, dYs, W2Ts, Cp, kMlpH, bar);
+    }
+    ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
+    for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+      float v[16], u[16];
+      tmem_ld16(tmem + lane_base + 64u + (uint32_t)c0, v);
+      tmem_ld16(tmem + lane_base + 128u + (uint32_t)c0, u);
+#pragma unroll
+      for (int j = 0; j < 16; j += 4) {
+        const float4 h2 = relu_tf32(v + j, a.b1 + c0 + j, live);
+        st4(H2s, tid, c0 + j, kMlpH, h2);
+        st4(dH2s, tid, c0 + j, kMlpH,
+            make_float4(h2.x > 0.0f ? tf32_rna(u[j]) : 0.0f, h2.y > 0.0f ? tf32_rna(u[j + 1]) : 0.0f,
+                        h2.z > 0.0f ? tf32_rna(u[j + 2]) : 0.0f, h2.w > 0.0f ? tf32_rna(u[j + 3]) : 0.0f));
+      }
+    }
+    sync_for_mma();
+    // dH1 = (dH2 W1) * (H1 > 0)
+    if (tid == 0) mma_tile(tmem, dH2s, W1Ts, kMlpH, kMlpH, bar);
+    ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
+    for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 16; j += 4) {
+        const float4 h1 = ld4(H1s, tid, c0 + j, kMlpH);
+        st4(dH1s, tid, c0 + j, kMlpH,
+            make_float4(h1.x > 0.0f ? tf32_rna(v[j]) : 0.0f, h1.y > 0.0f ? tf32_rna(v[j + 1]) : 0.0f,
+                        h1.z > 0.0f ? tf32_rna(v[j + 2]) : 0.0f, h1.w > 0.0f ? tf32_rna(v[j + 3]) : 0.0f));
+      }
+    }
+    sync_for_mma();
+    // dX = dH1 W0 -> the encoding's adjoint
+    if (tid == 0) mma_tile(tmem + 64u, dH1s, W0Ts, kMlpH, LF16, bar);
+    ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
+    for (int c0 = 0; c0 < LF16; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + lane_base + 64u + (uint32_t)c0, v);
+      // levels of these 16 values: l = (c0 + j) / F
+      for (int l = c0 / e.F; l < e.L && l * e.F < c0 + 16; ++l) {
+        const size_t lt = (size_t)l << e.logT;
+        for (int c = 0; c < 4; ++c) {
+          uint32_t row = 0xffffffffu;
+          float w = 0.0f;
+          if (live) corner(e, l, tx, ty, a.W, a.H, c, row, w);
+          int start;
+          bool tail;
+          lane_run(live ? row : 0xffffffffu, lane, start, tail);
+          for (int f = 0; f < e.F; ++f) {
+            const float d = (ok && live) ? w * v[l * e.F + f - c0] : 0.0f;
+            const float s = run_scan(d, lane, start);
+            if (live && tail && s != 0.0f) atomicAdd(a.dtable + (lt + row) * e.F + f, s);
+          }
+        }
+      }
+    }
+    // weight and bias gradients of this tile (FP32 FMAs on the staged
+    // tiles).  Each thread visits the rows in its own rotated order (start =
+    // its column block): the lanes of a warp then read different rows of one
+    // 8-row core matrix, 16 bytes apart, instead of one row's blocks 256
+    // bytes apart in the same banks.
+    __syncthreads();
+    for (int s = 0; s < 128; ++s) {
+      const int t = (s + jb) & 127;
+      const float4 d2 = ld4(dH2s, t, 4 * ib, kMlpH);
+      const float4 h1a = ld4(H1s, t, 8 * jb, kMlpH), h1b = ld4(H1s, t, 8 * jb + 4, kMlpH);
+      const float dv[4] = {d2.x, d2.y, d2.z, d2.w};
+      const float hv[8] = {h1a.x, h1a.y, h1a.z, h1a.w, h1b.x, h1b.y, h1b.z, h1b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) gW1[i][j] = fmaf(dv[i], hv[j], gW1[i][j]);
+        if (jb == 0) gb1[i] += dv[i];
+      }
+      const float4 d1 = ld4(dH1s, t, 4 * ib, kMlpH);
+      const float d1v[4] = {d1.x, d1.y, d1.z, d1.w};
+      if (4 * fb < LF) {
+        const float4 x = ld4(Xs, t, 4 * fb, LFp);
+        const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) gW0[i][j] = fmaf(d1v[i], xv[j], gW0[i][j]);
+      }
+      if (fb == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) gb0[i] += d1v[i];
+      }
+    }
+    if (4 * cb < Cp) {
+      for (int s = 0; s < 128; ++s) {
+        const int t = (s + hb) & 127;
+        const float4 y = ld4(dYs, t, 4 * cb, Cp);
+        const float4 h2 = ld4(H2s, t, 4 * hb, kMlpH);
+        const float yv[4] = {y.x, y.y, y.z, y.w}, h2v[4] = {h2.x, h2.y, h2.z, h2.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) gW2[i][j] = fmaf(yv[i], h2v[j], gW2[i][j]);
+          if (hb == 0) gb2[i] += yv[i];
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();   // the tiles and accumulators are reused
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  // the CTA's gradient sums into the gradient vector
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = 4 * ib + i;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) atomicAdd(a.dW1 + r * kMlpH + 8 * jb + j, gW1[i][j]);
+    if (jb == 0) atomicAdd(a.db1 + r, gb1[i]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (4 * fb + j < LF) atomicAdd(a.dW0 + r * LF + 4 * fb + j, gW0[i][j]);
+    if (fb == 0) atomicAdd(a.db0 + r, gb0[i]);
+    const int c = 4 * cb + i;
+    if (c < a.C) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) atomicAdd(a.dW2 + c * kMlpH + 4 * hb + j, gW2[i][j]);
+      if (hb == 0) atomicAdd(a.db2 + c, gb2[i]);
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
