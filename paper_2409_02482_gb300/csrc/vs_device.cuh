@@ -752,7 +752,12 @@ __device__ __forceinline__ Frag decode_sh(const float* val, const float Y[16]) {
 // ----------------------------------------------------------------------------
 // baked texels (VS_TEX_SH_U8): RGBA SH bytes, band l at (tw, th) >> l * bshift
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ float byte_of(unsigned w, int c) { return __uint2float_rn((w >> (8 * c)) & 0xffu); }
+// Byte c of w as a float, exactly: the byte placed under the exponent of
+// 2^23 (one byte permute: 0x4B0000bb is 2^23 + bb) minus 2^23 -- no
+// integer-to-float conversion (a quarter-rate instruction) per byte.
+__device__ __forceinline__ float byte_of(unsigned w, int c) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (unsigned)c)) - 8388608.0f;
+}
 
 // Band L of a baked texel at full-resolution texel coordinate (ix + fx,
 // iy + fy): the band's own footprint, its 2L + 1 coefficient quadruples
