@@ -311,9 +311,10 @@ typedef struct {
                              [32, 2048]                                       */
   int32_t shade_pixels;   /* pixels per shading work unit: a power of two in
                              [32, 4096]                                       */
-  int32_t blocks_per_sm;  /* persistent blocks per SM; 0 = the occupancy
-                             maximum, else 1 .. that maximum (larger values
-                             are clamped to it at launch)                     */
+  int32_t blocks_per_sm;  /* persistent blocks per SM (blocks of 160
+                             threads with do_backward, else 256); 0 = the
+                             occupancy maximum, else 1 .. that maximum
+                             (larger values are clamped to it at launch)      */
   int32_t reserved;       /* must be 0                                        */
 } vs_tuning;
 

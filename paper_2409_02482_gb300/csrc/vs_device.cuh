@@ -82,6 +82,26 @@ __host__ __device__ constexpr size_t block_smem_bytes(int K, bool bwd, int tc) {
   return warp_slice_bytes(K, bwd, tc) * kWarps;
 }
 
+// Block shape of the persistent kernel, per direction.  Its warps take units
+// on their own, so the block size only sets the register budget: the SM's
+// 64K registers are shared by (warps per block) x (resident blocks) warps.
+// The fused forward + adjoint runs 5-warp blocks, 4 per SM: 20 warps at 96
+// registers (measured 0.7 % faster on the C2 fitting step than 24 warps at
+// 80 registers, which spill ~2x more; 16 warps at 128 registers, no spill,
+// 4 % slower).  The forward keeps 8-warp blocks, 3 per SM (24 warps at 80
+// registers: 7 % faster than 20 warps at 96).
+#ifndef VS_PERS_BWD_WARPS
+#define VS_PERS_BWD_WARPS 5
+#endif
+#ifndef VS_PERS_FWD_WARPS
+#define VS_PERS_FWD_WARPS 8
+#endif
+__host__ __device__ constexpr int pers_warps(bool bwd) { return bwd ? VS_PERS_BWD_WARPS : VS_PERS_FWD_WARPS; }
+__host__ __device__ constexpr int pers_threads(bool bwd) { return 32 * pers_warps(bwd); }
+__host__ __device__ constexpr size_t pers_smem_bytes(int K, bool bwd, int tc) {
+  return warp_slice_bytes(K, bwd, tc) * pers_warps(bwd);
+}
+
 
 // Phases of one item.  Large triangles are rasterized by the whole block
 // inside the raster unit that met them.
@@ -417,6 +437,20 @@ __device__ __forceinline__ unsigned long long vis_key(unsigned K, int tri) {
 
 __device__ __forceinline__ int vis_tri(unsigned long long key) {
   return key ? (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull)) : -1;
+}
+
+// The triangle of a visibility word from its low 32 bits alone (the word is
+// little-endian, so they sit at its address): an empty word is 0, and a
+// written one holds ~triangle there, which is never 0 because triangle ids
+// stay below 2^31.  Half the registers of loading the whole word.
+template <bool HINT>
+__device__ __forceinline__ int load_vis_tri(const unsigned long long* p) {
+  unsigned lo;
+  if constexpr (HINT)
+    asm volatile("ld.global.cg.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(lo) : "l"(p), "l"(l2_evict_first()) : "memory");
+  else
+    lo = __ldcg(reinterpret_cast<const unsigned*>(p));
+  return lo ? (int)(0xFFFFFFFFu - lo) : -1;
 }
 
 // ----------------------------------------------------------------------------

@@ -86,17 +86,19 @@ cudaError_t plain_backward(const TableRef& tb, const int units[4], int tc, bool 
 
 cudaError_t persistent(const TableRef& tb, bool bwd, int tc, bool full, int grid, long long spin_limit,
                        cudaStream_t st) {
-  return tc_ops(tc).persistent(tb, bwd, full, grid, spin_limit, vsd::block_smem_bytes(tb.kmax, bwd, tc), st);
+  return tc_ops(tc).persistent(tb, bwd, full, grid, spin_limit, vsd::pers_smem_bytes(tb.kmax, bwd, tc), st);
 }
 
 cudaError_t persistent_occupancy(bool bwd, int tc, bool full, int kmax, int* blocks_per_sm) {
-  return tc_ops(tc).occupancy(bwd, full, vsd::block_smem_bytes(kmax, bwd, tc), blocks_per_sm);
+  return tc_ops(tc).occupancy(bwd, full, vsd::pers_smem_bytes(kmax, bwd, tc), blocks_per_sm);
 }
 
 cudaError_t configure_kernels() {
   for (int tc = 0; tc < vsd::kNumTc; ++tc) {
-    const int most_f = (int)vsd::block_smem_bytes(vsd::kMaxShells, false, tc);
-    const int most_b = (int)vsd::block_smem_bytes(vsd::kMaxShells, true, tc);
+    const int most_f = (int)std::max(vsd::block_smem_bytes(vsd::kMaxShells, false, tc),
+                                     vsd::pers_smem_bytes(vsd::kMaxShells, false, tc));
+    const int most_b = (int)std::max(vsd::block_smem_bytes(vsd::kMaxShells, true, tc),
+                                     vsd::pers_smem_bytes(vsd::kMaxShells, true, tc));
     cudaError_t e = tc_ops(tc).configure(most_f, most_b);
     if (e != cudaSuccess) return e;
   }

@@ -34,6 +34,12 @@
 #ifndef VS_FWD_BLOCKS
 #define VS_FWD_BLOCKS 3   // ... and for forward-only kernels
 #endif
+#ifndef VS_PERS_BWD_BLOCKS
+#define VS_PERS_BWD_BLOCKS 4   // resident blocks per SM of the persistent kernel with the adjoint (pers_threads(true) each)
+#endif
+#ifndef VS_PERS_FWD_BLOCKS
+#define VS_PERS_FWD_BLOCKS 3   // ... and of the forward-only persistent kernel
+#endif
 
 namespace vsd {
 
@@ -147,8 +153,12 @@ __device__ __forceinline__ unsigned depth_key32(const unsigned q[3], const int e
 // the triangles' start bits tells every lane which triangle owns its pair,
 // so lanes do not idle on small or culled boxes.  Larger boxes are
 // rasterized by the whole warp, one triangle at a time.
+// Per-lane triangle counts of a raster unit, two 16-bit fields per word (a
+// lane sees one triangle per round and a unit has at most kMaxRasterRounds
+// rounds, so no field overflows): fb = front | back << 16, ng = near plane |
+// guard band << 16, lc = large box | clipped << 16, plus an error bit.
 struct RasterCounts {
-  unsigned front, back, nearc, guard, large, bad, clipped;
+  unsigned fb, ng, lc, bad;
 };
 
 template <bool HINT, bool FULL>
@@ -246,13 +256,10 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
     }
     carry += __popc(bits);
   }
-  rc.front += front;
-  rc.back += back;
-  rc.nearc += nearc;
-  rc.guard += guard;
-  rc.large += large;
+  rc.fb += front | (back << 16);
+  rc.ng += nearc | (guard << 16);
+  rc.lc += large | (clip << 16);
   rc.bad |= bad;
-  rc.clipped += clip;
   // large boxes: the warp strides over each one's screen box
   unsigned lm = __ballot_sync(kAll, large);
   while (lm) {
@@ -293,15 +300,15 @@ static __device__ __forceinline__ void unit_raster(const DItem& it, const DShell
   const int per_unit = 32 * it.raster_rounds;
   const int base = (u - it.raster_pre[i]) * per_unit;
   unsigned long long* vis = it.vis + (size_t)i * it.cam.W * it.cam.H;
-  RasterCounts rc = {0, 0, 0, 0, 0, 0, 0};
+  RasterCounts rc = {0, 0, 0, 0};
   const int rounds = min(r1, min(per_unit, s.nt - base + 31) / 32);
   for (int r = r0; r < rounds; ++r) raster_round<HINT, FULL>(it, s, base + 32 * r, vis, smem, rc);
-  warp_count(&hdr->front, rc.front);
-  warp_count(&hdr->back, rc.back);
-  warp_count(&hdr->nearc, rc.nearc);
-  warp_count(&hdr->guard, rc.guard);
-  warp_count(&hdr->large, rc.large);
-  warp_count(&hdr->clipped, rc.clipped);
+  warp_count(&hdr->front, rc.fb & 0xFFFFu);
+  warp_count(&hdr->back, rc.fb >> 16);
+  warp_count(&hdr->nearc, rc.ng & 0xFFFFu);
+  warp_count(&hdr->guard, rc.ng >> 16);
+  warp_count(&hdr->large, rc.lc & 0xFFFFu);
+  warp_count(&hdr->clipped, rc.lc >> 16);
   if (__any_sync(0xffffffffu, rc.bad) && (threadIdx.x & 31) == 0) record_error(hdr, VS_ERR_INVALID_ARG);
 }
 
@@ -689,7 +696,7 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
       tt[d] = -1;
       if (i < k && pix_ok) {
         if (FROM_HITS) tt[d] = __ldg(it.hits + (size_t)i * HW + p);
-        else tt[d] = vis_tri(load_vis<BWD && !FROM_HITS>(it.vis + (size_t)i * HW + p));
+        else tt[d] = load_vis_tri<BWD && !FROM_HITS>(it.vis + (size_t)i * HW + p);
       }
     }
 #pragma unroll
@@ -1022,7 +1029,7 @@ static __device__ bool wait_done(const int* ctr, int target, long long limit, Ws
 // its own item, whose units were all dispensed in an earlier stage to warps
 // that are already running, so the wait always ends (and is bounded anyway).
 template <bool BWD, int TC, bool FULL>
-__global__ void __launch_bounds__(kThreads, BWD ? VS_BWD_BLOCKS : VS_FWD_BLOCKS) k_persistent(TableRef tb, long long spin_limit) {
+__global__ void __launch_bounds__(pers_threads(BWD), BWD ? VS_PERS_BWD_BLOCKS : VS_PERS_FWD_BLOCKS) k_persistent(TableRef tb, long long spin_limit) {
   const unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   WsHeader* hdr = tb.hdr;

@@ -16,7 +16,7 @@ constexpr bool kHasFull = (VS_TC) == vsd::TC_ANY;
 
 template <bool BWD, bool FULL>
 cudaError_t launch_persistent(const TableRef& tb, int grid, long long spin_limit, size_t smem, cudaStream_t st) {
-  vsd::k_persistent<BWD, VS_TC, FULL><<<grid, vsd::kThreads, smem, st>>>(tb, spin_limit);
+  vsd::k_persistent<BWD, VS_TC, FULL><<<grid, vsd::pers_threads(BWD), smem, st>>>(tb, spin_limit);
   return cudaGetLastError();
 }
 
@@ -54,7 +54,7 @@ cudaError_t tc_shade(const TableRef& tb, bool bwd, bool full, int blocks, size_t
 template <bool BWD, bool FULL>
 cudaError_t occupancy_of(size_t smem, int* blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, vsd::k_persistent<BWD, VS_TC, FULL>,
-                                                       vsd::kThreads, smem);
+                                                       vsd::pers_threads(BWD), smem);
 }
 
 cudaError_t tc_occupancy(bool bwd, bool full, size_t smem, int* blocks_per_sm) {
