@@ -51,18 +51,32 @@ Enc make_enc(const vs_ntex_config& c) {
   return e;
 }
 
+// Table row of lattice vertex (c0, c1) of level l: dense indexing while the
+// level's (N_l + 1)^2 vertices fit the table, else the spatial hash.
+__device__ __forceinline__ uint32_t table_row(const Enc& e, int l, uint32_t c0, uint32_t c1) {
+  const int n = e.res[l];
+  const uint32_t T = 1u << e.logT;
+  if ((uint64_t)(n + 1) * (uint64_t)(n + 1) <= T) return c0 + c1 * (uint32_t)(n + 1);
+  return (c0 ^ (c1 * kPrime)) & (T - 1u);
+}
+
+// Lattice cell of texel coordinate v (of `ext` texels) at resolution n, and
+// the fractional position r inside it.
+__device__ __forceinline__ int lattice_cell(int v, int ext, int n, float& r) {
+  const float p = (v + 0.5f) / (float)ext * (float)n;
+  const float f = floorf(p);
+  r = p - f;
+  return (int)f;
+}
+
 // Corner c (dx = c & 1, dy = c >> 1) of level l at texel n: table row and weight.
 __device__ __forceinline__ void corner(const Enc& e, int l, int tx, int ty, int W, int H, int c, uint32_t& row,
                                        float& w) {
   const int n = e.res[l];
-  const float px = (tx + 0.5f) / (float)W * (float)n, py = (ty + 0.5f) / (float)H * (float)n;
-  const float fx = floorf(px), fy = floorf(py);
-  const float rx = px - fx, ry = py - fy;
+  float rx, ry;
+  const int fx = lattice_cell(tx, W, n, rx), fy = lattice_cell(ty, H, n, ry);
   const int dx = c & 1, dy = c >> 1;
-  const uint32_t c0 = (uint32_t)((int)fx + dx), c1 = (uint32_t)((int)fy + dy);
-  const uint32_t T = 1u << e.logT;
-  if ((uint64_t)(n + 1) * (uint64_t)(n + 1) <= T) row = c0 + c1 * (uint32_t)(n + 1);
-  else row = (c0 ^ (c1 * kPrime)) & (T - 1u);
+  row = table_row(e, l, (uint32_t)(fx + dx), (uint32_t)(fy + dy));
   w = (dx ? rx : 1.0f - rx) * (dy ? ry : 1.0f - ry);
 }
 
@@ -86,110 +100,135 @@ __global__ void __launch_bounds__(kThreads) k_encode(Enc e, const float* table, 
   for (int f = 0; f < e.F; ++f) x[f] = acc[f];
 }
 
-// dtable[l, row, f] += w dX[i, l F + f]  (the encoding's adjoint), level
-// blockIdx.y.  Texels are row-major, so a segment of kSeg consecutive texels
-// touches only a band of two or three vertex rows of a dense level: the
-// block accumulates the segment's contributions to that band in shared
-// memory and adds the band to the table once (a coarse level would
-// otherwise receive millions of float atomics on a few hundred rows).
-// Hashed levels (and bands too large for the buffer) scatter straight to
-// the table, where rows are spread out.
-constexpr int kSmemAcc = 12288;   // floats of band buffer (48 KB)
-constexpr int kSeg = 4096;        // texels per segment
+// The encoding's adjoint, dtable[l, row, f] += w dX[i, l F + f], by 2D
+// tiles of texels: a block takes one tile of one level, 256 texel columns
+// (one per thread) by the level's tile height.  Down its column a thread
+// sums, in registers, the contributions of consecutive texels in the same
+// lattice cell row (the x weights are constant down a column) and adds the
+// cell's four corners when the cell row changes: into a shared-memory copy
+// of the tile's vertex box, which is added to the table once per tile, or,
+// at levels where a vertex meets few texels (the box would take more
+// atomics than the texels' corners), straight into the table.  A coarse
+// level thus takes a few atomics per tile instead of four per texel.
+// Element (l, i, f) of dX (texel n0 + i) sits at dX[l sl + i si + f].
+constexpr int kTgThreads = 256;
+constexpr int kTgSmem = 12288;   // floats of the vertex box (48 KB)
 
-__device__ __forceinline__ int cell_row(const Enc& e, int l, int ty, int H) {
-  return (int)floorf((ty + 0.5f) / (float)H * (float)e.res[l]);
-}
+struct TgPlan {
+  int L, tiles_x, y_first, nrows;
+  int ty[16];       // tile rows of level l
+  int direct[16];   // 1: corners straight into the table
+  int pre[17];      // first block of level l
+};
 
-// Run of consecutive lanes holding the same key: `start` = lane of the run's
-// first member, `tail` = this lane ends the run.  The sentinel 0xffffffff
-// (idle lanes) never matches a table row.
-__device__ __forceinline__ void lane_run(uint32_t key, int lane, int& start, bool& tail) {
-  const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1), next = __shfl_down_sync(0xffffffffu, key, 1);
-  const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
-  start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-  tail = lane == 31 || next != key;
-}
-// Sum of v over the lanes [start, lane] (inclusive segmented scan).
-__device__ __forceinline__ float run_scan(float v, int lane, int start) {
+// dst[0 .. F) += v[0 .. F) with vector reductions where F allows (8- and
+// 16-byte aligned rows).
+template <int F>
+__device__ __forceinline__ void red_row(float* dst, const float* v) {
+  if constexpr (F == 2) {
+    asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(dst), "f"(v[0]), "f"(v[1]) : "memory");
+  } else if constexpr (F % 4 == 0) {
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const float u = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane - o >= start) v += u;
+    for (int f = 0; f < F; f += 4)
+      asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + f), "f"(v[f]),
+                   "f"(v[f + 1]), "f"(v[f + 2]), "f"(v[f + 3])
+                   : "memory");
+  } else {
+#pragma unroll
+    for (int f = 0; f < F; ++f) atomicAdd(dst + f, v[f]);
   }
-  return v;
 }
 
-__global__ void __launch_bounds__(kThreads) k_encode_bwd(Enc e, const float* dX, int W, int H, int n0, int count,
-                                                          float* dtable) {
-  extern __shared__ float acc[];
-  const int l = blockIdx.y;
+template <int F>
+__global__ void __launch_bounds__(kTgThreads) k_table_grad(const __grid_constant__ Enc e,
+                                                           const __grid_constant__ TgPlan p, const float* __restrict__ dX,
+                                                           long long sl, int si, int W, int H, int n0, int count,
+                                                           float* dtable) {
+  extern __shared__ float box[];
+  const int b = blockIdx.x;
+  int l = 0;
+  while (l + 1 < p.L && b >= p.pre[l + 1]) ++l;
+  const int t = b - p.pre[l];
   const int n = e.res[l];
-  const int lane = threadIdx.x & 31;
-  // neighbouring texels share a cell (two or more texels per cell): a warp's
-  // contributions to one row are added up across its lanes first, so that a
-  // row takes one atomic per run instead of one per texel
-  const bool runs = 2 * n <= W;                              // block-uniform
-  const bool dense = (long long)(n + 1) * (n + 1) <= (1ll << e.logT);
-  const size_t lt = (size_t)l << e.logT;
-  const int nseg = (count + kSeg - 1) / kSeg;
-  for (int seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
-    const int i0 = seg * kSeg, i1 = min(count, i0 + kSeg);
-    int vb = 0, band = 0;
-    if (dense) {
-      const int cy0 = cell_row(e, l, (n0 + i0) / W, H), cy1 = cell_row(e, l, (n0 + i1 - 1) / W, H);
-      vb = cy0 * (n + 1);
-      band = (cy1 - cy0 + 2) * (n + 1);
-    }
-    const bool local = dense && band * e.F <= kSmemAcc;   // block-uniform
-    if (local) {
-      for (int r = threadIdx.x; r < band * e.F; r += blockDim.x) acc[r] = 0.0f;
-      __syncthreads();
-    }
-    if (runs) {
-      // whole warps step together (shuffles); idle lanes carry the sentinel
-      for (int ib = i0 + (threadIdx.x & ~31); ib < i1; ib += blockDim.x) {
-        const int i = ib + lane;
-        const bool ok = i < i1;
-        const int t = n0 + (ok ? i : i0), tx = t % W, ty = t / W;
-        const float* d = dX + (size_t)(ok ? i : i0) * e.L * e.F + l * e.F;
-        for (int c = 0; c < 4; ++c) {
-          uint32_t row;
-          float w;
-          corner(e, l, tx, ty, W, H, c, row, w);
-          int start;
-          bool tail;
-          lane_run(ok ? row : 0xffffffffu, lane, start, tail);
-          for (int f = 0; f < e.F; ++f) {
-            const float v = run_scan(ok ? w * d[f] : 0.0f, lane, start);
-            if (ok && tail) {
-              if (local) atomicAdd(acc + ((int)row - vb) * e.F + f, v);
-              else atomicAdd(dtable + (lt + row) * e.F + f, v);
-            }
+  const int x0 = (t % p.tiles_x) * kTgThreads;
+  const int y0 = p.y_first + (t / p.tiles_x) * p.ty[l], y1 = min(y0 + p.ty[l], p.y_first + p.nrows);
+  float r;
+  const int bx0 = lattice_cell(x0, W, n, r), by0 = lattice_cell(y0, H, n, r);
+  const int bxn = lattice_cell(min(x0 + kTgThreads - 1, W - 1), W, n, r) + 2 - bx0;
+  const int byn = lattice_cell(y1 - 1, H, n, r) + 2 - by0;
+  const int nbox = bxn * byn * F;
+  const bool direct = p.direct[l] || nbox > kTgSmem;   // block-uniform
+  float* tl = dtable + ((size_t)l << e.logT) * F;
+  if (!direct) {
+    for (int i = threadIdx.x; i < nbox; i += blockDim.x) box[i] = 0.0f;
+    __syncthreads();
+  }
+  const int x = x0 + threadIdx.x;
+  if (x < W) {
+    float rx;
+    const int cx = lattice_cell(x, W, n, rx);
+    const float wx[2] = {1.0f - rx, rx};
+    float acc[2][F];
+    int cur = -1;
+    // the four corners of cell row `cur` from the column's sums
+    auto flush = [&]() {
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+          if (wx[dx] == 0.0f) continue;
+          float v[F];
+          bool any = false;
+#pragma unroll
+          for (int f = 0; f < F; ++f) {
+            v[f] = wx[dx] * acc[dy][f];
+            any = any || v[f] != 0.0f;
+          }
+          if (!any) continue;
+          const int vx = cx + dx, vy = cur + dy;
+          if (direct) {
+            red_row<F>(tl + (size_t)table_row(e, l, (uint32_t)vx, (uint32_t)vy) * F, v);
+          } else {
+            float* q = box + ((vy - by0) * bxn + (vx - bx0)) * F;
+#pragma unroll
+            for (int f = 0; f < F; ++f) atomicAdd(q + f, v[f]);
           }
         }
+    };
+    for (int y = y0; y < y1; ++y) {
+      const long long nn = (long long)y * W + x;
+      if (nn < n0 || nn >= (long long)n0 + count) continue;   // outside this chunk
+      float ry;
+      const int cy = lattice_cell(y, H, n, ry);
+      if (cy != cur) {
+        if (cur >= 0) flush();
+        cur = cy;
+#pragma unroll
+        for (int f = 0; f < F; ++f) acc[0][f] = acc[1][f] = 0.0f;
       }
-    } else {
-      for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        const int t = n0 + i, tx = t % W, ty = t / W;
-        const float* d = dX + (size_t)i * e.L * e.F + l * e.F;
-        for (int c = 0; c < 4; ++c) {
-          uint32_t row;
-          float w;
-          corner(e, l, tx, ty, W, H, c, row, w);
-          for (int f = 0; f < e.F; ++f) {
-            if (local) atomicAdd(acc + ((int)row - vb) * e.F + f, w * d[f]);
-            else atomicAdd(dtable + (lt + row) * e.F + f, w * d[f]);
-          }
-        }
+      const float* d = dX + l * sl + (nn - n0) * si;
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        const float v = __ldg(d + f);
+        acc[0][f] += (1.0f - ry) * v;
+        acc[1][f] += ry * v;
       }
     }
-    if (local) {
-      __syncthreads();
-      float* t = dtable + (lt + vb) * e.F;
-      for (int r = threadIdx.x; r < band * e.F; r += blockDim.x)
-        if (acc[r] != 0.0f) atomicAdd(t + r, acc[r]);
-      __syncthreads();   // the buffer is reused by the next segment
+    if (cur >= 0) flush();
+  }
+  if (!direct) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < bxn * byn; i += blockDim.x) {
+      float v[F];
+      bool any = false;
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        v[f] = box[i * F + f];
+        any = any || v[f] != 0.0f;
+      }
+      if (!any) continue;
+      const int vy = by0 + i / bxn, vx = bx0 + i % bxn;
+      red_row<F>(tl + (size_t)table_row(e, l, (uint32_t)vx, (uint32_t)vy) * F, v);
     }
   }
 }
@@ -595,6 +634,61 @@ int gemm_atb(const float* D, const float* A, float* dW, int rows, int N, int K, 
   } while (0)
 
 // Forward of one chunk: activations X, H1, H2, Y in the workspace.
+// Tile plan of k_table_grad for texels n0 .. n0 + count of a W x H texture.
+// Per level: the tallest power-of-two tile (at most 128 rows) whose vertex
+// box fits the shared buffer, and the route with fewer atomics -- the box
+// (every box vertex once per tile) or direct (the four corners of every run
+// of texels down a column inside one cell row).
+TgPlan tg_plan(const Enc& e, int W, int H, int n0, int count) {
+  TgPlan p{};
+  p.L = e.L;
+  p.tiles_x = (W + kTgThreads - 1) / kTgThreads;
+  p.y_first = n0 / W;
+  p.nrows = (int)(((long long)n0 + count - 1) / W) - p.y_first + 1;
+  const long long cols = W < kTgThreads ? W : kTgThreads;
+  p.pre[0] = 0;
+  for (int l = 0; l < e.L; ++l) {
+    const long long n = e.res[l];
+    const long long bx = ((cols - 1) * n + W - 1) / W + 3;   // box width bound (vertices)
+    auto by = [&](long long ty) { return ((ty - 1) * n + H - 1) / H + 3; };
+    int ty = 0;
+    for (int c = 128; c >= 1 && ty == 0; c >>= 1)
+      if (bx * by(c) * e.F <= kTgSmem) ty = c;
+    bool direct = ty == 0;
+    if (!direct) {
+      const long long tiles = (long long)p.tiles_x * ((p.nrows + ty - 1) / ty);
+      const long long runs = (long long)count * (n < H ? n : H) / H + W;
+      direct = 4 * runs < tiles * bx * by(ty);
+    }
+    if (direct) ty = 16;
+    p.ty[l] = ty;
+    p.direct[l] = direct ? 1 : 0;
+    p.pre[l + 1] = p.pre[l] + p.tiles_x * ((p.nrows + ty - 1) / ty);
+  }
+  return p;
+}
+
+// dtable += the encoding's adjoint of dX (element (l, i, f) at
+// dX[l sl + i si + f]) for texels n0 .. n0 + count.
+int table_grad(const Enc& e, const float* dX, long long sl, int si, int W, int H, int n0, int count, float* dtable,
+               cudaStream_t st) {
+  if (count <= 0) return 0;
+  const TgPlan p = tg_plan(e, W, H, n0, count);
+  const unsigned grid = (unsigned)p.pre[e.L];
+  const size_t smem = kTgSmem * sizeof(float);
+  switch (e.F) {
+    case 1: k_table_grad<1><<<grid, kTgThreads, smem, st>>>(e, p, dX, sl, si, W, H, n0, count, dtable); break;
+    case 2: k_table_grad<2><<<grid, kTgThreads, smem, st>>>(e, p, dX, sl, si, W, H, n0, count, dtable); break;
+    case 3: k_table_grad<3><<<grid, kTgThreads, smem, st>>>(e, p, dX, sl, si, W, H, n0, count, dtable); break;
+    case 4: k_table_grad<4><<<grid, kTgThreads, smem, st>>>(e, p, dX, sl, si, W, H, n0, count, dtable); break;
+    case 5: k_table_grad<5><<<grid, kTgThreads, smem, st>>>(e, p, dX, sl, si, W, H, n0, count, dtable); break;
+    case 6: k_table_grad<6><<<grid, kTgThreads, smem, st>>>(e, p, dX, sl, si, W, H, n0, count, dtable); break;
+    case 7: k_table_grad<7><<<grid, kTgThreads, smem, st>>>(e, p, dX, sl, si, W, H, n0, count, dtable); break;
+    default: k_table_grad<8><<<grid, kTgThreads, smem, st>>>(e, p, dX, sl, si, W, H, n0, count, dtable); break;
+  }
+  return (int)cudaGetLastError();
+}
+
 int chunk_forward(const vs_ntex_config& c, const Enc& e, const Views& P, int W, int H, int n0, int rows, const Ws& w,
                   cudaStream_t st) {
   const int LF = c.levels * c.features, Hd = c.hidden, C = c.out_ch;
@@ -660,7 +754,7 @@ int forward(const vs_ntex_config& c, const float* params, int W, int H, void* te
 // most 32 encoding values with F dividing 16, and at most 32 outputs; one
 // persistent launch over the whole texture.  -1 when not covered.
 int fused_backward_tc(const vs_ntex_config& c, const Views& P, float* const g[7], const Enc& e, int W, int H,
-                      const float* grad, int pitch, int ch0, int* status, cudaStream_t st) {
+                      const float* grad, int pitch, int ch0, void* ws, cudaStream_t st) {
   const int LF = c.levels * c.features;
   if (!c.tensor_cores || c.hidden != kMlpH || LF > 32 || c.out_ch > 32 || 16 % c.features != 0) return -1;
   const int smem = mlp_bwd_smem(LF, c.out_ch);
@@ -674,10 +768,22 @@ int fused_backward_tc(const vs_ntex_config& c, const Views& P, float* const g[7]
   int dev = 0, sms = 0;
   VS_TRY_CUDA(cudaGetDevice(&dev));
   VS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  MlpBwdArgs a{P.table, P.W0, P.b0, P.W1, P.b1, P.W2, grad, g[0], g[1], g[2], g[3], g[4], g[5], g[6],
-               W, H, W * H, c.out_ch, LF, pitch, ch0, status, 1ll << 22};
-  k_mlp_bwd_tc<<<sms, kTcThreads, smem, st>>>(a, e);   // one CTA per SM (shared memory)
-  return (int)cudaGetLastError();
+  // chunks of texels whose level-major dX fits the workspace (sized for
+  // kNtexChunk texels of every activation: at least four times this)
+  const int N = W * H;
+  const int rows_ws = N < kNtexChunk ? N : kNtexChunk;
+  const int chunk = N < 4 * rows_ws ? N : 4 * rows_ws;
+  const Ws w = carve(c, 1, ws);
+  float* dX = reinterpret_cast<float*>(ws) + 64;
+  for (int n0 = 0; n0 < N; n0 += chunk) {
+    const int count = N - n0 < chunk ? N - n0 : chunk;
+    MlpBwdArgs a{P.table, P.W0, P.b0, P.W1, P.b1, P.W2, grad, g[1], g[2], g[3], g[4], g[5], g[6], dX,
+                 W, H, n0, count, c.out_ch, LF, c.features, pitch, ch0, w.status, 1ll << 22};
+    k_mlp_bwd_tc<<<sms, kTcThreads, smem, st>>>(a, e);   // one CTA per SM (shared memory)
+    VS_TRY_CUDA(cudaGetLastError());
+    VS_TRY(table_grad(e, dX, (long long)count * c.features, c.features, W, H, n0, count, g[0], st));
+  }
+  return 0;
 }
 
 int backward(const vs_ntex_config& c, const float* params, int W, int H, const float* grad_texels, int pitch, int ch0,
@@ -689,7 +795,7 @@ int backward(const vs_ntex_config& c, const float* params, int W, int H, const f
   views(c, grads, g);
   const Enc e = make_enc(c);
   {
-    const int r = fused_backward_tc(c, P, g, e, W, H, grad_texels, pitch, ch0, carve(c, 1, ws).status, st);
+    const int r = fused_backward_tc(c, P, g, e, W, H, grad_texels, pitch, ch0, ws, st);
     if (r >= 0) return r;
   }
   const int N = W * H;
@@ -717,12 +823,7 @@ int backward(const vs_ntex_config& c, const float* params, int W, int H, const f
     // first layer and the encoding: dW0 += dH1^T X, dX = dH1 W0
     VS_TRY(gemm_atb(w.dH1, w.X, g[1], rows, Hd, LF, st));
     VS_TRY(gemm_abt(tc, EPI_NONE, w.dH1, w.W0t, w.dX, rows, LF, Hd, nullptr, nullptr, nullptr, w.status, st));
-    {
-      const unsigned nseg = (unsigned)((rows + kSeg - 1) / kSeg);
-      const unsigned gx = nseg < 256u ? nseg : 256u;
-      k_encode_bwd<<<dim3(gx, c.levels), kThreads, kSmemAcc * sizeof(float), st>>>(e, w.dX, W, H, n0, rows, g[0]);
-    }
-    VS_TRY_CUDA(cudaGetLastError());
+    VS_TRY(table_grad(e, w.dX, c.features, (int)LF, W, H, n0, rows, g[0], st));
   }
   return 0;
 }

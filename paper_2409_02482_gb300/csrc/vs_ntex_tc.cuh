@@ -454,8 +454,9 @@ namespace vsn {
 struct MlpBwdArgs {
   const float *table, *W0, *b0, *W1, *b1, *W2;
   const float* grad;   // dL/d(texels) [N, pitch], channels ch0 .. ch0 + C
-  float *dtable, *dW0, *db0, *dW1, *db1, *dW2, *db2;
-  int W, H, N, C, LF, pitch, ch0;
+  float *dW0, *db0, *dW1, *db1, *dW2, *db2;
+  float* dX;           // dL/d(encoding) of texels n0 .. n0 + count, level-major [L][count][F]
+  int W, H, n0, count, C, LF, F, pitch, ch0;
   int* status;
   long long spin_limit;
 };
@@ -505,7 +506,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs a
   float* dH1s = dH2s + 128 * kMlpH;
   uint64_t* bar = reinterpret_cast<uint64_t*>(dH1s + 128 * kMlpH);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kMlpTmemCols)
@@ -541,10 +542,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs a
     for (int j = 0; j < 4; ++j) gW0[i][j] = gW2[i][j] = 0.0f;
   }
 
-  const int tiles = (a.N + 127) / 128;
+  const int tiles = (a.count + 127) / 128;
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int n = tile * 128 + tid;
-    const bool live = n < a.N;
+    const int i = tile * 128 + tid, n = a.n0 + i;
+    const bool live = i < a.count;
     const int tx = live ? n % a.W : 0, ty = live ? n / a.W : 0;
     // encoding (row tid of X) and the output gradient (row tid of dY)
     for (int l = 0; l < e.L; ++l) {
@@ -612,26 +613,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs a
       }
     }
     sync_for_mma();
-    // dX = dH1 W0 -> the encoding's adjoint
+    // dX = dH1 W0, stored level-major for the encoding's adjoint (a
+    // separate tiled kernel: k_table_grad)
     if (tid == 0) mma_tile(tmem + 64u, dH1s, W0Ts, kMlpH, LF16, bar);
     ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
     for (int c0 = 0; c0 < LF16; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + lane_base + 64u + (uint32_t)c0, v);
-      // levels of these 16 values: l = (c0 + j) / F
-      for (int l = c0 / e.F; l < e.L && l * e.F < c0 + 16; ++l) {
-        const size_t lt = (size_t)l << e.logT;
-        for (int c = 0; c < 4; ++c) {
-          uint32_t row = 0xffffffffu;
-          float w = 0.0f;
-          if (live) corner(e, l, tx, ty, a.W, a.H, c, row, w);
-          int start;
-          bool tail;
-          lane_run(live ? row : 0xffffffffu, lane, start, tail);
-          for (int f = 0; f < e.F; ++f) {
-            const float d = (ok && live) ? w * v[l * e.F + f - c0] : 0.0f;
-            const float s = run_scan(d, lane, start);
-            if (live && tail && s != 0.0f) atomicAdd(a.dtable + (lt + row) * e.F + f, s);
+      if (live) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if (c0 + j < LF) {
+            const int l = (c0 + j) / a.F, f = (c0 + j) - l * a.F;
+            a.dX[((size_t)l * a.count + i) * a.F + f] = ok ? v[j] : 0.0f;
           }
         }
       }

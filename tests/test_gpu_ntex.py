@@ -153,6 +153,39 @@ def test_ntex_bench_configuration_matches_oracle(vs, ctx, out_ch, tensor_cores):
     assert nt.status() == 0
 
 
+@pytest.mark.parametrize("tensor_cores", [False, True])
+def test_ntex_backward_across_chunk_boundaries(vs, ctx, tensor_cores):
+    """A 1500 x 800 texture: the adjoint runs in chunks of texels (2^18 for
+    FP32 layers, 2^20 for the fused TF32 kernel) that end inside a texel
+    row, so the tiles of the encoding's adjoint are cut by a chunk boundary.
+    A gradient on sampled texels, among them every texel within 3 of a chunk
+    boundary, against the oracle on those texels."""
+    W, H = 1500, 800
+    params = _params(CFG, 5)
+    nt = vs.NeuralTexture(ctx, CFG.levels, CFG.features, CFG.log2_table, CFG.base_res, CFG.growth, CFG.hidden,
+                          CFG.out_ch, tex_w=W, tex_h=H, tensor_cores=tensor_cores)
+    nt.params.copy_(torch.from_numpy(params))
+    rng = np.random.default_rng(6)
+    edges = [b + d for b in (1 << 18, 2 << 18, 3 << 18, 4 << 18) for d in range(-3, 3)]
+    idx = np.unique(np.concatenate([rng.choice(W * H, 3000, replace=False), edges]))
+    g = rng.normal(size=(len(idx), CFG.out_ch)).astype(np.float32)
+    dense = torch.zeros((H * W, CFG.out_ch), device="cuda")
+    dense[torch.from_numpy(idx).cuda()] = torch.from_numpy(g).cuda()
+    nt.backward(dense.reshape(H, W, CFG.out_ch))
+    ref = ntex.backward(CFG, params.astype(np.float64), W, H, g.astype(np.float64), texels=idx)
+    got = nt.grads.cpu().numpy().astype(np.float64)
+    lay, _ = CFG.layout()
+    for name, off, shp in lay:
+        n = int(np.prod(shp))
+        r, q = ref[off:off + n], got[off:off + n]
+        if tensor_cores:   # the TF32 bars of test_ntex_bench_configuration_matches_oracle
+            bar = 1e-5 if name == "b2" else 8e-2
+            assert np.linalg.norm(q - r) <= bar * np.linalg.norm(r) + 1e-30, name
+        else:
+            assert np.abs(q - r).max() <= 1e-4 * max(np.abs(r).max(), 1e-30), name
+    assert nt.status() == 0
+
+
 def test_ntex_backward_matches_oracle(vs, ctx):
     W, H = 70, 50
     params = _params(CFG, 2)
