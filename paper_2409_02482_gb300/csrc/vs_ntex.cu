@@ -779,7 +779,7 @@ int fused_backward_tc(const vs_ntex_config& c, const Views& P, float* const g[7]
     const int count = N - n0 < chunk ? N - n0 : chunk;
     MlpBwdArgs a{P.table, P.W0, P.b0, P.W1, P.b1, P.W2, grad, g[1], g[2], g[3], g[4], g[5], g[6], dX,
                  W, H, n0, count, c.out_ch, LF, c.features, pitch, ch0, w.status, 1ll << 22};
-    k_mlp_bwd_tc<<<sms, kTcThreads, smem, st>>>(a, e);   // one CTA per SM (shared memory)
+    k_mlp_bwd_tc<<<sms, kBwdThreads, smem, st>>>(a, e);   // one CTA per SM (shared memory)
     VS_TRY_CUDA(cudaGetLastError());
     VS_TRY(table_grad(e, dX, (long long)count * c.features, c.features, W, H, n0, count, g[0], st));
   }

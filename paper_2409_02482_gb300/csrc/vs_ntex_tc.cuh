@@ -445,11 +445,11 @@ namespace vsn {
 // 128 texels: the forward's hidden layers again (encoding, layer 0, layer 1),
 // then dH2 = (dY W2) * (H2 > 0), dH1 = (dH2 W1) * (H1 > 0), dX = dH1 W0 on
 // the tensor cores (the transposed weights staged once per CTA, K-major),
-// the encoding's adjoint scattered into the tables (runs of lanes on one
-// table row added first), and the weight and bias gradients accumulated in
-// registers over the CTA's tiles (FP32 FMAs on the staged tiles) and added
-// into the gradient vector once at the end.  Shapes: LF <= 32 encoding
-// values, hidden 64, C <= 32 outputs.
+// dX written level-major for the encoding's adjoint (k_table_grad), and the
+// weight and bias gradients accumulated in registers over the CTA's tiles
+// (FP32 FMAs on the staged tiles, overlapping the tensor-core products) and
+// added into the gradient vector once at the end.  Shapes: LF <= 32
+// encoding values, hidden 64, C <= 32 outputs.
 // ----------------------------------------------------------------------------
 struct MlpBwdArgs {
   const float *table, *W0, *b0, *W1, *b1, *W2;
@@ -490,7 +490,13 @@ __device__ __forceinline__ void sync_for_mma() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs a, const Enc e) {
+// 8 warps per CTA: warps w and w + 4 share the tensor-memory lane quarter
+// (texel rows 32 (w % 4) ..) and split the columns (and the encoding's
+// levels) between them; the weight gradients of a tile are summed on the
+// FP32 pipes while the tensor cores run the next product.
+constexpr int kBwdThreads = 256;
+
+__global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs a, const Enc e) {
   extern __shared__ __align__(128) char msm[];
   const int LF = a.LF, LFp = (LF + 7) & ~7, LF16 = (LF + 15) & ~15, Cp = (a.C + 7) & ~7;
   float* W0s = reinterpret_cast<float*>(msm);      // [64 x LF]   layer 0 B
@@ -506,7 +512,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs a
   float* dH1s = dH2s + 128 * kMlpH;
   uint64_t* bar = reinterpret_cast<uint64_t*>(dH1s + 128 * kMlpH);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int half = tid >> 7, r = tid & 127;        // column half, texel row of the tile
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kMlpTmemCols)
@@ -524,31 +531,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs a
   stage_op_tr(W0Ts, a.W0, LF, LF16, kMlpH, LF);
   sync_for_mma();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   uint32_t phase = 0;
   bool ok = true;
 
-  // register accumulators of the weight and bias gradients:
-  //   dW1 rows 4 ib .. +3, columns 8 jb .. +7;   dW0 rows 4 ib .. +3, columns 4 fb .. +3;
-  //   dW2 rows 4 cb .. +3, columns 4 hb .. +3;   db1 / db0 rows of ib (jb == 0 / fb == 0), db2 of cb (hb == 0)
-  const int ib = tid >> 3, jb = tid & 7, fb = tid & 7, cb = tid >> 4, hb = tid & 15;
-  float gW1[4][8], gW0[4][4], gW2[4][4], gb1[4], gb0[4], gb2[4];
+  // register accumulators of the weight and bias gradients (thread tid):
+  //   dW1 rows 4 ib .. +3, columns 4 jb .. +3   (ib = tid >> 4, jb = tid & 15)
+  //   dW2 rows 2 cb .. +1, columns 4 jb .. +3   (cb = tid >> 4)
+  //   dW0 rows 2 ob .. +1, columns 4 fb .. +3   (ob = tid >> 3, fb = tid & 7)
+  //   db1 rows of ib, db2 rows of cb (jb == 0); db0 rows of ob (fb == 0)
+  // Each thread walks the tile's rows from its own offset rot = lane & 7, so
+  // that the eight lanes of a quarter-warp read eight different rows (eight
+  // different 16-byte bank groups of the canonical layout).
+  const int ib = tid >> 4, jb = tid & 15, cb = tid >> 4, ob = tid >> 3, fb = tid & 7, rot = lane & 7;
+  float gW1[4][4], gW2[2][4], gW0[2][4], gb1[4], gb2[2], gb0[2];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    gb1[i] = gb0[i] = gb2[i] = 0.0f;
+    gb1[i] = 0.0f;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) gW1[i][j] = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) gW0[i][j] = gW2[i][j] = 0.0f;
+    for (int j = 0; j < 4; ++j) gW1[i][j] = 0.0f;
   }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    gb2[i] = gb0[i] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) gW2[i][j] = gW0[i][j] = 0.0f;
+  }
+  const bool do_w2 = 2 * cb < Cp, do_w0 = 4 * fb < LF;
+  const int l_lo = half ? (e.L + 1) / 2 : 0, l_hi = half ? e.L : (e.L + 1) / 2;
 
   const int tiles = (a.count + 127) / 128;
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int i = tile * 128 + tid, n = a.n0 + i;
+    const int i = tile * 128 + r, n = a.n0 + i;
     const bool live = i < a.count;
     const int tx = live ? n % a.W : 0, ty = live ? n / a.W : 0;
-    // encoding (row tid of X) and the output gradient (row tid of dY)
-    for (int l = 0; l < e.L; ++l) {
+    // encoding of row r (this half's levels) and the output gradient (this
+    // half's columns)
+    for (int l = l_lo; l < l_hi; ++l) {
       float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (live) {
         const size_t lt = (size_t)l << e.logT;
@@ -560,22 +579,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs a
           for (int f = 0; f < e.F; ++f) acc[f] = fmaf(w, __ldg(t + f), acc[f]);
         }
       }
-      for (int f = 0; f < e.F; ++f) *op_at(Xs, tid, l * e.F + f, LFp) = tf32_rna(acc[f]);
+      for (int f = 0; f < e.F; ++f) *op_at(Xs, r, l * e.F + f, LFp) = tf32_rna(acc[f]);
     }
-    for (int k = LF; k < LFp; ++k) *op_at(Xs, tid, k, LFp) = 0.0f;
+    if (half == 0)
+      for (int k = LF; k < LFp; ++k) *op_at(Xs, r, k, LFp) = 0.0f;
     // dY kept in FP32 (the tensor cores read its TF32 part; the bias and
     // weight gradients of the output layer use all of it)
-    for (int c = 0; c < Cp; ++c)
-      *op_at(dYs, tid, c, Cp) = (live && c < a.C) ? __ldg(a.grad + (size_t)n * a.pitch + a.ch0 + c) : 0.0f;
+    for (int c = half * (Cp / 2); c < (half + 1) * (Cp / 2); ++c)
+      *op_at(dYs, r, c, Cp) = (live && c < a.C) ? __ldg(a.grad + (size_t)n * a.pitch + a.ch0 + c) : 0.0f;
     sync_for_mma();
     // layer 0 -> H1
     if (tid == 0) mma_tile(tmem, Xs, W0s, LFp, kMlpH, bar);
     ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
-    for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+    for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
-      for (int j = 0; j < 16; j += 4) st4(H1s, tid, c0 + j, kMlpH, relu_tf32(v + j, a.b0 + c0 + j, live));
+      for (int j = 0; j < 16; j += 4) st4(H1s, r, c0 + j, kMlpH, relu_tf32(v + j, a.b0 + c0 + j, live));
     }
     sync_for_mma();
     // layer 1 -> H2; dH2 = dY W2 (independent: issued together, one commit)
@@ -584,40 +604,78 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs a
       mma_tile(tmem + 128u, dYs, W2Ts, Cp, kMlpH, bar);
     }
     ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
-    for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+    for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 16) {
       float v[16], u[16];
       tmem_ld16(tmem + lane_base + 64u + (uint32_t)c0, v);
       tmem_ld16(tmem + lane_base + 128u + (uint32_t)c0, u);
 #pragma unroll
       for (int j = 0; j < 16; j += 4) {
         const float4 h2 = relu_tf32(v + j, a.b1 + c0 + j, live);
-        st4(H2s, tid, c0 + j, kMlpH, h2);
-        st4(dH2s, tid, c0 + j, kMlpH,
+        st4(H2s, r, c0 + j, kMlpH, h2);
+        st4(dH2s, r, c0 + j, kMlpH,
             make_float4(h2.x > 0.0f ? tf32_rna(u[j]) : 0.0f, h2.y > 0.0f ? tf32_rna(u[j + 1]) : 0.0f,
                         h2.z > 0.0f ? tf32_rna(u[j + 2]) : 0.0f, h2.w > 0.0f ? tf32_rna(u[j + 3]) : 0.0f));
       }
     }
     sync_for_mma();
-    // dH1 = (dH2 W1) * (H1 > 0)
+    // dH1 = (dH2 W1) * (H1 > 0) on the tensor cores; meanwhile the FP32
+    // pipes add dW1 += dH2^T H1 and dW2 += dY^T H2 over the tile's rows
     if (tid == 0) mma_tile(tmem, dH2s, W1Ts, kMlpH, kMlpH, bar);
+    for (int s = 0; s < 128; ++s) {
+      const int t = (s + rot) & 127;
+      const float4 d2 = ld4(dH2s, t, 4 * ib, kMlpH), h1 = ld4(H1s, t, 4 * jb, kMlpH);
+      const float dv[4] = {d2.x, d2.y, d2.z, d2.w}, hv[4] = {h1.x, h1.y, h1.z, h1.w};
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) gW1[p][q] = fmaf(dv[p], hv[q], gW1[p][q]);
+        if (jb == 0) gb1[p] += dv[p];
+      }
+      if (do_w2) {
+        const float4 h2 = ld4(H2s, t, 4 * jb, kMlpH);
+        const float2 y = *reinterpret_cast<const float2*>(op_at(dYs, t, 2 * cb, Cp));
+        const float yv[2] = {y.x, y.y}, h2v[4] = {h2.x, h2.y, h2.z, h2.w};
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) gW2[p][q] = fmaf(yv[p], h2v[q], gW2[p][q]);
+          if (jb == 0) gb2[p] += yv[p];
+        }
+      }
+    }
     ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
-    for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+    for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
       for (int j = 0; j < 16; j += 4) {
-        const float4 h1 = ld4(H1s, tid, c0 + j, kMlpH);
-        st4(dH1s, tid, c0 + j, kMlpH,
+        const float4 h1 = ld4(H1s, r, c0 + j, kMlpH);
+        st4(dH1s, r, c0 + j, kMlpH,
             make_float4(h1.x > 0.0f ? tf32_rna(v[j]) : 0.0f, h1.y > 0.0f ? tf32_rna(v[j + 1]) : 0.0f,
                         h1.z > 0.0f ? tf32_rna(v[j + 2]) : 0.0f, h1.w > 0.0f ? tf32_rna(v[j + 3]) : 0.0f));
       }
     }
     sync_for_mma();
-    // dX = dH1 W0, stored level-major for the encoding's adjoint (a
-    // separate tiled kernel: k_table_grad)
+    // dX = dH1 W0 on the tensor cores; meanwhile dW0 += dH1^T X
     if (tid == 0) mma_tile(tmem + 64u, dH1s, W0Ts, kMlpH, LF16, bar);
+    if (do_w0) {
+      for (int s = 0; s < 128; ++s) {
+        const int t = (s + rot) & 127;
+        const float2 d1 = *reinterpret_cast<const float2*>(op_at(dH1s, t, 2 * ob, kMlpH));
+        const float4 x = ld4(Xs, t, 4 * fb, LFp);
+        const float dv[2] = {d1.x, d1.y}, xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) gW0[p][q] = fmaf(dv[p], xv[q], gW0[p][q]);
+          if (fb == 0) gb0[p] += dv[p];
+        }
+      }
+    }
     ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
-    for (int c0 = 0; c0 < LF16; c0 += 16) {
+    // dX stored level-major for the encoding's adjoint (a separate tiled
+    // kernel: k_table_grad)
+    for (int c0 = 16 * half; c0 < LF16; c0 += 32) {
       float v[16];
       tmem_ld16(tmem + lane_base + 64u + (uint32_t)c0, v);
       if (live) {
@@ -630,73 +688,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs a
         }
       }
     }
-    // weight and bias gradients of this tile (FP32 FMAs on the staged
-    // tiles).  Each thread visits the rows in its own rotated order (start =
-    // its column block): the lanes of a warp then read different rows of one
-    // 8-row core matrix, 16 bytes apart, instead of one row's blocks 256
-    // bytes apart in the same banks.
-    __syncthreads();
-    for (int s = 0; s < 128; ++s) {
-      const int t = (s + jb) & 127;
-      const float4 d2 = ld4(dH2s, t, 4 * ib, kMlpH);
-      const float4 h1a = ld4(H1s, t, 8 * jb, kMlpH), h1b = ld4(H1s, t, 8 * jb + 4, kMlpH);
-      const float dv[4] = {d2.x, d2.y, d2.z, d2.w};
-      const float hv[8] = {h1a.x, h1a.y, h1a.z, h1a.w, h1b.x, h1b.y, h1b.z, h1b.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) gW1[i][j] = fmaf(dv[i], hv[j], gW1[i][j]);
-        if (jb == 0) gb1[i] += dv[i];
-      }
-      const float4 d1 = ld4(dH1s, t, 4 * ib, kMlpH);
-      const float d1v[4] = {d1.x, d1.y, d1.z, d1.w};
-      if (4 * fb < LF) {
-        const float4 x = ld4(Xs, t, 4 * fb, LFp);
-        const float xv[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) gW0[i][j] = fmaf(d1v[i], xv[j], gW0[i][j]);
-      }
-      if (fb == 0) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) gb0[i] += d1v[i];
-      }
-    }
-    if (4 * cb < Cp) {
-      for (int s = 0; s < 128; ++s) {
-        const int t = (s + hb) & 127;
-        const float4 y = ld4(dYs, t, 4 * cb, Cp);
-        const float4 h2 = ld4(H2s, t, 4 * hb, kMlpH);
-        const float yv[4] = {y.x, y.y, y.z, y.w}, h2v[4] = {h2.x, h2.y, h2.z, h2.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) gW2[i][j] = fmaf(yv[i], h2v[j], gW2[i][j]);
-          if (hb == 0) gb2[i] += yv[i];
-        }
-      }
-    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();   // the tiles and accumulators are reused
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
   // the CTA's gradient sums into the gradient vector
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = 4 * ib + i;
+  for (int p = 0; p < 4; ++p) {
+    const int o = 4 * ib + p;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) atomicAdd(a.dW1 + r * kMlpH + 8 * jb + j, gW1[i][j]);
-    if (jb == 0) atomicAdd(a.db1 + r, gb1[i]);
+    for (int q = 0; q < 4; ++q) atomicAdd(a.dW1 + o * kMlpH + 4 * jb + q, gW1[p][q]);
+    if (jb == 0) atomicAdd(a.db1 + o, gb1[p]);
+  }
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (4 * fb + j < LF) atomicAdd(a.dW0 + r * LF + 4 * fb + j, gW0[i][j]);
-    if (fb == 0) atomicAdd(a.db0 + r, gb0[i]);
-    const int c = 4 * cb + i;
-    if (c < a.C) {
+  for (int p = 0; p < 2; ++p) {
+    const int c = 2 * cb + p;
+    if (do_w2 && c < a.C) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) atomicAdd(a.dW2 + c * kMlpH + 4 * hb + j, gW2[i][j]);
-      if (hb == 0) atomicAdd(a.db2 + c, gb2[i]);
+      for (int q = 0; q < 4; ++q) atomicAdd(a.dW2 + c * kMlpH + 4 * jb + q, gW2[p][q]);
+      if (jb == 0) atomicAdd(a.db2 + c, gb2[p]);
+    }
+    const int o = 2 * ob + p;
+    if (do_w0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (4 * fb + q < LF) atomicAdd(a.dW0 + o * LF + 4 * fb + q, gW0[p][q]);
+      if (fb == 0) atomicAdd(a.db0 + o, gb0[p]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
