@@ -496,6 +496,19 @@ __device__ __forceinline__ void sync_for_mma() {
 // FP32 pipes while the tensor cores run the next product.
 constexpr int kBwdThreads = 256;
 
+// Element (m, k) of a canonical operand tile as raw bits (an MMA fragment).
+__device__ __forceinline__ uint32_t lds_u(const float* base, int m, int k, int Kp) {
+  return __float_as_uint(*op_at(const_cast<float*>(base), m, k, Kp));
+}
+// D[16 x 8] += A[16 x 8] B[8 x 8], TF32 inputs, FP32 accumulators (one warp).
+__device__ __forceinline__ void mma_tf32(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs a, const Enc e) {
   extern __shared__ __align__(128) char msm[];
   const int LF = a.LF, LFp = (LF + 7) & ~7, LF16 = (LF + 15) & ~15, Cp = (a.C + 7) & ~7;
@@ -535,29 +548,34 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
   uint32_t phase = 0;
   bool ok = true;
 
-  // register accumulators of the weight and bias gradients (thread tid):
-  //   dW1 rows 4 ib .. +3, columns 4 jb .. +3   (ib = tid >> 4, jb = tid & 15)
-  //   dW2 rows 2 cb .. +1, columns 4 jb .. +3   (cb = tid >> 4)
-  //   dW0 rows 2 ob .. +1, columns 4 fb .. +3   (ob = tid >> 3, fb = tid & 7)
-  //   db1 rows of ib, db2 rows of cb (jb == 0); db0 rows of ob (fb == 0)
-  // Each thread walks the tile's rows from its own offset rot = lane & 7, so
-  // that the eight lanes of a quarter-warp read eight different rows (eight
-  // different 16-byte bank groups of the canonical layout).
-  const int ib = tid >> 4, jb = tid & 15, cb = tid >> 4, ob = tid >> 3, fb = tid & 7, rot = lane & 7;
-  float gW1[4][4], gW2[2][4], gW0[2][4], gb1[4], gb2[2], gb0[2];
+  // Weight and bias gradients of the tile, summed over its 128 texels with
+  // warp-level TF32 MMAs (mma.sync m16n8k8) whose fragments are read
+  // straight from the texel-major tiles: as a product over texels they want
+  // texel-contiguous (transposed) operands, which tcgen05's TF32 K-major
+  // descriptors would need as extra copies that do not fit shared memory.
+  // FP32 accumulators in registers over the CTA's tiles.  Warp w:
+  //   dW1 = dH2^T H1: rows 16 (w & 3) .. +15, columns 32 (w >> 2) .. +31
+  //   dW2 = dY^T H2:  rows 16 (w & 1) .. +15, columns 16 (w >> 1) .. +15
+  //   dW0 = dH1^T X:  rows 16 (w & 3) .. +15, columns 16 (w >> 2) .. +15
+  //   db1, db0 (warps 0-3): the same A fragments times a matrix of ones
+  //   db2: FP32 sums of dY per thread (kept exact: a plain sum)
+  const int g = lane >> 2, tig = lane & 3;
+  const int m1 = 16 * (warp & 3), n1 = 32 * (warp >> 2);
+  const int m2 = 16 * (warp & 1), n2 = 16 * (warp >> 1);
+  const int n0c = 16 * (warp >> 2);
+  const bool do_w2 = m2 < Cp, bias = warp < 4;
+  float acc1[4][4], acc2[2][4], acc0[2][4], accb1[4], accb0[4], gb2[16];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    gb1[i] = 0.0f;
+  for (int q = 0; q < 4; ++q) {
+    accb1[q] = accb0[q] = 0.0f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) gW1[i][j] = 0.0f;
+    for (int j = 0; j < 4; ++j) acc1[j][q] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc2[j][q] = acc0[j][q] = 0.0f;
   }
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    gb2[i] = gb0[i] = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) gW2[i][j] = gW0[i][j] = 0.0f;
-  }
-  const bool do_w2 = 2 * cb < Cp, do_w0 = 4 * fb < LF;
+  for (int q = 0; q < 16; ++q) gb2[q] = 0.0f;
+  const uint32_t one = __float_as_uint(1.0f);
   const int l_lo = half ? (e.L + 1) / 2 : 0, l_hi = half ? e.L : (e.L + 1) / 2;
 
   const int tiles = (a.count + 127) / 128;
@@ -585,8 +603,15 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
       for (int k = LF; k < LFp; ++k) *op_at(Xs, r, k, LFp) = 0.0f;
     // dY kept in FP32 (the tensor cores read its TF32 part; the bias and
     // weight gradients of the output layer use all of it)
-    for (int c = half * (Cp / 2); c < (half + 1) * (Cp / 2); ++c)
-      *op_at(dYs, r, c, Cp) = (live && c < a.C) ? __ldg(a.grad + (size_t)n * a.pitch + a.ch0 + c) : 0.0f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int c = half * (Cp / 2) + q;
+      if (q < Cp / 2) {
+        const float v = (live && c < a.C) ? __ldg(a.grad + (size_t)n * a.pitch + a.ch0 + c) : 0.0f;
+        *op_at(dYs, r, c, Cp) = v;
+        gb2[q] += v;
+      }
+    }
     sync_for_mma();
     // layer 0 -> H1
     if (tid == 0) mma_tile(tmem, Xs, W0s, LFp, kMlpH, bar);
@@ -618,29 +643,24 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
       }
     }
     sync_for_mma();
-    // dH1 = (dH2 W1) * (H1 > 0) on the tensor cores; meanwhile the FP32
-    // pipes add dW1 += dH2^T H1 and dW2 += dY^T H2 over the tile's rows
+    // dH1 = (dH2 W1) * (H1 > 0) on the tensor cores; meanwhile dW1 += dH2^T H1
+    // (and db1) and dW2 += dY^T H2
     if (tid == 0) mma_tile(tmem, dH2s, W1Ts, kMlpH, kMlpH, bar);
-    for (int s = 0; s < 128; ++s) {
-      const int t = (s + rot) & 127;
-      const float4 d2 = ld4(dH2s, t, 4 * ib, kMlpH), h1 = ld4(H1s, t, 4 * jb, kMlpH);
-      const float dv[4] = {d2.x, d2.y, d2.z, d2.w}, hv[4] = {h1.x, h1.y, h1.z, h1.w};
+    for (int k0 = 0; k0 < 128; k0 += 8) {
+      const int ka = k0 + tig, kb = ka + 4;
+      const uint32_t A[4] = {lds_u(dH2s, ka, m1 + g, kMlpH), lds_u(dH2s, ka, m1 + g + 8, kMlpH),
+                             lds_u(dH2s, kb, m1 + g, kMlpH), lds_u(dH2s, kb, m1 + g + 8, kMlpH)};
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) gW1[p][q] = fmaf(dv[p], hv[q], gW1[p][q]);
-        if (jb == 0) gb1[p] += dv[p];
-      }
+      for (int j = 0; j < 4; ++j)
+        mma_tf32(acc1[j], A, lds_u(H1s, ka, n1 + 8 * j + g, kMlpH), lds_u(H1s, kb, n1 + 8 * j + g, kMlpH));
+      if (bias) mma_tf32(accb1, A, one, one);
       if (do_w2) {
-        const float4 h2 = ld4(H2s, t, 4 * jb, kMlpH);
-        const float2 y = *reinterpret_cast<const float2*>(op_at(dYs, t, 2 * cb, Cp));
-        const float yv[2] = {y.x, y.y}, h2v[4] = {h2.x, h2.y, h2.z, h2.w};
+        // dY holds FP32 values: rounded to TF32 here (rows beyond Cp are zero)
+        auto dy = [&](int t, int c) { return c < Cp ? __float_as_uint(tf32_rna(*op_at(dYs, t, c, Cp))) : 0u; };
+        const uint32_t A2[4] = {dy(ka, m2 + g), dy(ka, m2 + g + 8), dy(kb, m2 + g), dy(kb, m2 + g + 8)};
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) gW2[p][q] = fmaf(yv[p], h2v[q], gW2[p][q]);
-          if (jb == 0) gb2[p] += yv[p];
-        }
+        for (int j = 0; j < 2; ++j)
+          mma_tf32(acc2[j], A2, lds_u(H2s, ka, n2 + 8 * j + g, kMlpH), lds_u(H2s, kb, n2 + 8 * j + g, kMlpH));
       }
     }
     ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
@@ -656,21 +676,17 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
       }
     }
     sync_for_mma();
-    // dX = dH1 W0 on the tensor cores; meanwhile dW0 += dH1^T X
+    // dX = dH1 W0 on the tensor cores; meanwhile dW0 += dH1^T X (and db0)
     if (tid == 0) mma_tile(tmem + 64u, dH1s, W0Ts, kMlpH, LF16, bar);
-    if (do_w0) {
-      for (int s = 0; s < 128; ++s) {
-        const int t = (s + rot) & 127;
-        const float2 d1 = *reinterpret_cast<const float2*>(op_at(dH1s, t, 2 * ob, kMlpH));
-        const float4 x = ld4(Xs, t, 4 * fb, LFp);
-        const float dv[2] = {d1.x, d1.y}, xv[4] = {x.x, x.y, x.z, x.w};
+    for (int k0 = 0; k0 < 128; k0 += 8) {
+      const int ka = k0 + tig, kb = ka + 4;
+      const uint32_t A[4] = {lds_u(dH1s, ka, m1 + g, kMlpH), lds_u(dH1s, ka, m1 + g + 8, kMlpH),
+                             lds_u(dH1s, kb, m1 + g, kMlpH), lds_u(dH1s, kb, m1 + g + 8, kMlpH)};
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) gW0[p][q] = fmaf(dv[p], xv[q], gW0[p][q]);
-          if (fb == 0) gb0[p] += dv[p];
-        }
-      }
+      for (int j = 0; j < 2; ++j)
+        if (n0c + 8 * j < LFp)
+          mma_tf32(acc0[j], A, lds_u(Xs, ka, n0c + 8 * j + g, LFp), lds_u(Xs, kb, n0c + 8 * j + g, LFp));
+      if (bias) mma_tf32(accb0, A, one, one);
     }
     ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
     // dX stored level-major for the encoding's adjoint (a separate tiled
@@ -692,29 +708,30 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
     __syncthreads();   // the tiles and accumulators are reused
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
-  // the CTA's gradient sums into the gradient vector
+  // the CTA's gradient sums into the gradient vector (accumulator fragment
+  // q of an m16n8 tile: row g + 8 (q >> 1), column 2 tig + (q & 1))
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    const int o = 4 * ib + p;
+  for (int q = 0; q < 4; ++q) {
+    const int row = g + 8 * (q >> 1), col = 2 * tig + (q & 1);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) atomicAdd(a.dW1 + o * kMlpH + 4 * jb + q, gW1[p][q]);
-    if (jb == 0) atomicAdd(a.db1 + o, gb1[p]);
+    for (int j = 0; j < 4; ++j) atomicAdd(a.dW1 + (m1 + row) * kMlpH + n1 + 8 * j + col, acc1[j][q]);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (do_w2 && m2 + row < a.C) atomicAdd(a.dW2 + (m2 + row) * kMlpH + n2 + 8 * j + col, acc2[j][q]);
+      if (n0c + 8 * j + col < LF) atomicAdd(a.dW0 + (m1 + row) * LF + n0c + 8 * j + col, acc0[j][q]);
+    }
+    if (bias && tig == 0 && (q & 1) == 0) {   // every column of a bias tile holds the same sums
+      atomicAdd(a.db1 + m1 + row, accb1[q]);
+      atomicAdd(a.db0 + m1 + row, accb0[q]);
+    }
   }
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    const int c = 2 * cb + p;
-    if (do_w2 && c < a.C) {
+  for (int q = 0; q < 16; ++q) {
+    float v = gb2[q];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) atomicAdd(a.dW2 + c * kMlpH + 4 * jb + q, gW2[p][q]);
-      if (jb == 0) atomicAdd(a.db2 + c, gb2[p]);
-    }
-    const int o = 2 * ob + p;
-    if (do_w0) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (4 * fb + q < LF) atomicAdd(a.dW0 + o * LF + 4 * fb + q, gW0[p][q]);
-      if (fb == 0) atomicAdd(a.db0 + o, gb0[p]);
-    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int c = half * (Cp / 2) + q;
+    if (lane == 0 && q < Cp / 2 && c < a.C) atomicAdd(a.db2 + c, v);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
