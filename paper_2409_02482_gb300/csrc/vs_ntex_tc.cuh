@@ -251,6 +251,58 @@ __device__ __forceinline__ void stage_op(float* dst, const float* src, int n_row
   }
 }
 
+// Encoding of texel (tx, ty), levels [l0, l1), into row m of the canonical
+// operand X (TF32).  With two features per level the levels go four at a
+// time, all sixteen corner rows (8 bytes each) loaded before any is used;
+// the sums run in the same order as the generic loop.
+__device__ __forceinline__ void encode_row(const Enc& e, const float* table, int tx, int ty, int W, int H, int l0,
+                                           int l1, float* X, int m, int Kp) {
+  if (e.F == 2) {
+    const float2* t2 = reinterpret_cast<const float2*>(table);
+    for (int lb = l0; lb < l1; lb += 4) {
+      float2 v[4][4];
+      float w[4][4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        const int l = lb + d < l1 ? lb + d : lb;
+        const size_t lt = (size_t)l << e.logT;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          uint32_t row;
+          corner(e, l, tx, ty, W, H, c, row, w[d][c]);
+          v[d][c] = __ldg(t2 + lt + row);
+        }
+      }
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        if (lb + d < l1) {
+          float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            a0 = fmaf(w[d][c], v[d][c].x, a0);
+            a1 = fmaf(w[d][c], v[d][c].y, a1);
+          }
+          *op_at(X, m, 2 * (lb + d), Kp) = tf32_rna(a0);
+          *op_at(X, m, 2 * (lb + d) + 1, Kp) = tf32_rna(a1);
+        }
+      }
+    }
+    return;
+  }
+  for (int l = l0; l < l1; ++l) {
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const size_t lt = (size_t)l << e.logT;
+    for (int c = 0; c < 4; ++c) {
+      uint32_t row;
+      float w;
+      corner(e, l, tx, ty, W, H, c, row, w);
+      const float* t = table + (lt + row) * e.F;
+      for (int f = 0; f < e.F; ++f) acc[f] = fmaf(w, __ldg(t + f), acc[f]);
+    }
+    for (int f = 0; f < e.F; ++f) *op_at(X, m, l * e.F + f, Kp) = tf32_rna(acc[f]);
+  }
+}
+
 // Issues the MMAs of D[128 x Np] = A[128 x Kp] B[Np x Kp]^T (one thread)
 // and, with commit, commits every MMA this thread issued so far to the
 // mbarrier (one phase).
@@ -322,7 +374,7 @@ __host__ __device__ constexpr int mlp_fwd_smem(int LF, int C) {
          2 * op_bytes(128, kMlpH) + 256;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(const MlpFwdArgs a, const Enc e) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(const MlpFwdArgs a, const __grid_constant__ Enc e) {
   extern __shared__ __align__(128) char msm[];
   const int LFp = (a.LF + 7) & ~7, Cp = (a.C + 15) & ~15;
   float* W0s = reinterpret_cast<float*>(msm);
@@ -359,19 +411,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(const MlpFwdArgs a
     // encoding of texel n = 128 tile + tid into row tid of X
     const int n = tile * 128 + tid;
     if (n < a.N) {
-      const int tx = n % a.W, ty = n / a.W;
-      for (int l = 0; l < e.L; ++l) {
-        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const size_t lt = (size_t)l << e.logT;
-        for (int c = 0; c < 4; ++c) {
-          uint32_t row;
-          float w;
-          corner(e, l, tx, ty, a.W, a.H, c, row, w);
-          const float* t = a.table + (lt + row) * e.F;
-          for (int f = 0; f < e.F; ++f) acc[f] = fmaf(w, __ldg(t + f), acc[f]);
-        }
-        for (int f = 0; f < e.F; ++f) *op_at(Xs, tid, l * e.F + f, LFp) = tf32_rna(acc[f]);
-      }
+      encode_row(e, a.table, n % a.W, n / a.W, a.W, a.H, 0, e.L, Xs, tid, LFp);
       for (int k = a.LF; k < LFp; ++k) *op_at(Xs, tid, k, LFp) = 0.0f;
     } else {
       for (int k = 0; k < LFp; ++k) *op_at(Xs, tid, k, LFp) = 0.0f;
@@ -509,7 +549,7 @@ __device__ __forceinline__ void mma_tf32(float d[4], const uint32_t a[4], uint32
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs a, const Enc e) {
+__global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs a, const __grid_constant__ Enc e) {
   extern __shared__ __align__(128) char msm[];
   const int LF = a.LF, LFp = (LF + 7) & ~7, LF16 = (LF + 15) & ~15, Cp = (a.C + 7) & ~7;
   float* W0s = reinterpret_cast<float*>(msm);      // [64 x LF]   layer 0 B
@@ -585,20 +625,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
     const int tx = live ? n % a.W : 0, ty = live ? n / a.W : 0;
     // encoding of row r (this half's levels) and the output gradient (this
     // half's columns)
-    for (int l = l_lo; l < l_hi; ++l) {
-      float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (live) {
-        const size_t lt = (size_t)l << e.logT;
-        for (int c = 0; c < 4; ++c) {
-          uint32_t row;
-          float w;
-          corner(e, l, tx, ty, a.W, a.H, c, row, w);
-          const float* t = a.table + (lt + row) * e.F;
-          for (int f = 0; f < e.F; ++f) acc[f] = fmaf(w, __ldg(t + f), acc[f]);
-        }
-      }
-      for (int f = 0; f < e.F; ++f) *op_at(Xs, r, l * e.F + f, LFp) = tf32_rna(acc[f]);
-    }
+    if (live) encode_row(e, a.table, tx, ty, a.W, a.H, l_lo, l_hi, Xs, r, LFp);
+    else
+      for (int k = l_lo * e.F; k < l_hi * e.F; ++k) *op_at(Xs, r, k, LFp) = 0.0f;
     if (half == 0)
       for (int k = LF; k < LFp; ++k) *op_at(Xs, r, k, LFp) = 0.0f;
     // dY kept in FP32 (the tensor cores read its TF32 part; the bias and
