@@ -7,17 +7,17 @@
 // gradients (vs_render_backward / the fused batch) back to the hash tables
 // and MLP parameters; vs_adam_step updates them.
 //
-// GB300 mapping: the encoding (a 4-corner gather per level) and its adjoint
-// (a scatter with float atomics) are hand-written kernels, one thread per
-// (texel, level); the three layers are dense contractions over the texels,
-// run as hand-written GEMM kernels with their elementwise work fused in:
-// bias and ReLU in the forward's epilogue, the ReLU mask and the bias
-// gradient's column sums in the adjoint's.  FP32 layers (the default) run on
-// the FP32 pipes; with cfg.tensor_cores the forward-shaped products run on
-// the tensor cores (tcgen05, TF32 inputs, FP32 accumulators in tensor
-// memory; see vs_ntex_tc.cuh).  Texels run in chunks of kChunk so that the
-// activations (64 MB per layer at 2^18 texels) stay within L2 between
-// layers and in a bounded workspace.
+// GB300 mapping.  FP32 layers (the default): per chunk of kNtexChunk texels
+// the encoding (a 4-corner gather per level, one thread per (texel, level)),
+// the three layers as hand-written GEMM kernels on the FP32 pipes with their
+// elementwise work fused in (bias and ReLU in the forward's epilogue, the
+// ReLU mask and the bias gradient's column sums in the adjoint's), so that
+// the activations (64 MB per layer at 2^18 texels) stay within L2 between
+// layers and in a bounded workspace.  TF32 layers (cfg.tensor_cores): one
+// fused persistent kernel each way, the layers on the tensor cores (tcgen05,
+// FP32 accumulators in tensor memory; vs_ntex_tc.cuh).  Both modes take the
+// encoding's adjoint in k_table_grad, by 2D tiles of texels (register runs
+// down columns, a shared vertex box per tile).
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
