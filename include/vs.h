@@ -281,7 +281,12 @@ typedef struct {
 
 /* Renders n items -- any mix of objects, shell counts, triangle counts and
  * resolutions -- in ONE persistent kernel launch (after small launches that
- * copy the item table into the workspace).  Work units are handed out in a
+ * copy the item table into the workspace).  The items run in an order of
+ * the library's choosing, for cache locality: grouped by object, and within
+ * an object a nearest-neighbour chain of camera centres from its first item
+ * (up to 4096 items per object; larger groups keep the given order).
+ * Outputs do not depend on the order, gradient sums only through the
+ * rounding order of their FP32 atomics.  Work units are handed out in a
  * fixed, skewed global order (stage s: vertex setup of item s, raster of
  * item s-1, shading of item s-2); a unit waits, with a bounded spin, only
  * for units handed out before it, so the launch cannot deadlock.  With do_backward, each pixel's forward result is

@@ -171,7 +171,66 @@ struct ItemReq {
   float* const* grad_tex;
   float* loss;
   float* layers = nullptr;   // per-layer buffers [k, H, W, 12] or null
+  int index = 0;             // the item's position in the caller's array
 };
+
+// Dispatch order of a batch, for L2 locality: items grouped by object (in
+// the order objects first appear), and within an object a greedy
+// nearest-neighbour chain of camera centres from its first item, so that
+// consecutive items -- shaded at overlapping times by the persistent
+// kernel's skewed stages -- see nearby surface and share gradient and texel
+// lines in L2.  Outputs do not depend on the order (each item writes its
+// own buffers); gradient sums only through the FP32 rounding order of their
+// atomics, which is unordered anyway.  Groups larger than kChainMax keep the
+// caller's order (the chain costs O(n^2) on the host).
+constexpr int kChainMax = 4096;
+
+void order_for_locality(std::vector<ItemReq>& req) {
+  const int n = (int)req.size();
+  std::vector<ItemReq> out;
+  out.reserve(n);
+  std::vector<char> taken(n, 0);
+  auto eye = [](const vs_camera& c, double e[3]) {   // -R^T t
+    for (int a = 0; a < 3; ++a)
+      e[a] = -(c.world_to_cam[0 * 4 + a] * (double)c.world_to_cam[0 * 4 + 3] +
+               c.world_to_cam[1 * 4 + a] * (double)c.world_to_cam[1 * 4 + 3] +
+               c.world_to_cam[2 * 4 + a] * (double)c.world_to_cam[2 * 4 + 3]);
+  };
+  for (int j0 = 0; j0 < n; ++j0) {
+    if (taken[j0]) continue;
+    std::vector<int> grp;
+    for (int j = j0; j < n; ++j)
+      if (!taken[j] && req[j].obj == req[j0].obj) grp.push_back(j);
+    for (int j : grp) taken[j] = 1;
+    if ((int)grp.size() > kChainMax) {
+      for (int j : grp) out.push_back(req[j]);
+      continue;
+    }
+    std::vector<double> E(3 * grp.size());
+    for (size_t q = 0; q < grp.size(); ++q) eye(*req[grp[q]].cam, &E[3 * q]);
+    std::vector<char> used(grp.size(), 0);
+    size_t cur = 0;
+    used[0] = 1;
+    out.push_back(req[grp[0]]);
+    for (size_t step = 1; step < grp.size(); ++step) {
+      size_t best = 0;
+      double bd = -1.0;
+      for (size_t q = 0; q < grp.size(); ++q) {
+        if (used[q]) continue;
+        const double dx = E[3 * q] - E[3 * cur], dy = E[3 * q + 1] - E[3 * cur + 1], dz = E[3 * q + 2] - E[3 * cur + 2];
+        const double d = dx * dx + dy * dy + dz * dz;
+        if (bd < 0.0 || d < bd) {
+          bd = d;
+          best = q;
+        }
+      }
+      used[best] = 1;
+      cur = best;
+      out.push_back(req[grp[best]]);
+    }
+  }
+  req.swap(out);
+}
 
 // Work-unit sizes of one plan, in 32-wide rounds.  The plain launches run
 // one round per warp of a block, so they always use kWarps rounds.
@@ -483,13 +542,14 @@ vs_status check_batch(const vs_ctx* ctx, const vs_batch_item* items, int n, int 
       for (int i = 0; i < b.obj->k; ++i)
         if (!b.grad_texels[i] || (uintptr_t)b.grad_texels[i] % 4) return fail(VS_ERR_INVALID_ARG, "item %d: grad_texels[%d] NULL or misaligned", j, i);
     }
-    req[j] = ItemReq{b.obj, &b.cam, b.out_rgba, b.hits, b.grad_rgb, b.grad_texels, b.loss};
+    req[j] = ItemReq{b.obj, &b.cam, b.out_rgba, b.hits, b.grad_rgb, b.grad_texels, b.loss, nullptr, j};
     *kmax = std::max(*kmax, (int)b.obj->k);
   }
   vs_status s = set_device(ctx);
   if (s != VS_OK) return s;
   for (int j = 0; j < n; ++j)
     if ((s = ensure_bounds(items[j].obj)) != VS_OK) return s;
+  order_for_locality(req);
   return VS_OK;
 }
 
@@ -782,7 +842,7 @@ vs_status vs_render_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, co
       if ((s = run_bytes(j, 1, &one)) != VS_OK) return s;
       if (one > ws_bytes || !workspace)
         return fail(VS_ERR_WORKSPACE, "workspace has %zu bytes; item %d alone needs %zu (the batch %zu)", ws_bytes,
-                    j, one, all);
+                    req[j].index, one, all);
       int lo = 1, hi = m - 1;   // largest m' in [lo, hi] that fits; lo fits
       while (lo < hi) {
         const int mid = lo + (hi - lo + 1) / 2;
@@ -797,9 +857,9 @@ vs_status vs_render_batch(vs_ctx* ctx, const vs_batch_item* items, int32_t n, co
       return s;
     if ((s = check_ws(P, workspace, ws_bytes)) != VS_OK) return s;
     int km = 1;
-    for (int q = j; q < j + m; ++q) km = std::max(km, (int)items[q].obj->k);
+    for (int q = j; q < j + m; ++q) km = std::max(km, (int)req[q].obj->k);
     if ((s = launch_batch(ctx, P, workspace, do_backward, km, t, st)) != VS_OK)
-      return runs ? fail(s, "run %d of the batch (items %d..%d): %s", runs, j, j + m - 1, g_err.c_str()) : s;
+      return runs ? fail(s, "run %d of the batch (%d items): %s", runs, m, g_err.c_str()) : s;
     ++runs;
     j += m;
   }
