@@ -61,23 +61,49 @@ __device__ __forceinline__ uint32_t table_row(const Enc& e, int l, uint32_t c0, 
 }
 
 // Lattice cell of texel coordinate v (of `ext` texels) at resolution n, and
-// the fractional position r inside it.
+// the fractional position r inside it.  The position p = (v + 1/2) n / ext
+// is the fraction (2v + 1) n / (2 ext) of integers, so the cell is an exact
+// integer quotient and r = remainder / (2 ext) carries one rounding (two
+// with the reciprocal): the encoding's weights do not lose the ~n 2^-24 of
+// a cell that a float evaluation of p would at fine levels.  Numerators
+// below 2^24 (every texture up to 4096 texels a side with levels up to 2048
+// cells) take the quotient from a float estimate corrected by one step.
 __device__ __forceinline__ int lattice_cell(int v, int ext, int n, float& r) {
-  const float p = (v + 0.5f) / (float)ext * (float)n;
-  const float f = floorf(p);
-  r = p - f;
-  return (int)f;
+  const unsigned long long num = (unsigned long long)(2 * v + 1) * (unsigned)n;
+  const unsigned den = 2u * (unsigned)ext;
+  const float rcp = __frcp_rn((float)den);
+  int q, rem;
+  if (num < (1ull << 24)) {
+    q = (int)__fmul_rz((float)num, rcp);
+    rem = (int)num - q * (int)den;
+    if (rem < 0) {
+      --q;
+      rem += (int)den;
+    } else if (rem >= (int)den) {
+      ++q;
+      rem -= (int)den;
+    }
+  } else {
+    q = (int)(num / den);
+    rem = (int)(num - (unsigned long long)q * den);
+  }
+  r = __fmul_rn((float)rem, rcp);
+  return q;
 }
 
-// Corner c (dx = c & 1, dy = c >> 1) of level l at texel n: table row and weight.
-__device__ __forceinline__ void corner(const Enc& e, int l, int tx, int ty, int W, int H, int c, uint32_t& row,
-                                       float& w) {
+// The four corners of level l at texel (tx, ty): corner c (dx = c & 1,
+// dy = c >> 1) has table row row[c] and weight w[c].
+__device__ __forceinline__ void corners4(const Enc& e, int l, int tx, int ty, int W, int H, uint32_t row[4],
+                                         float w[4]) {
   const int n = e.res[l];
   float rx, ry;
   const int fx = lattice_cell(tx, W, n, rx), fy = lattice_cell(ty, H, n, ry);
-  const int dx = c & 1, dy = c >> 1;
-  row = table_row(e, l, (uint32_t)(fx + dx), (uint32_t)(fy + dy));
-  w = (dx ? rx : 1.0f - rx) * (dy ? ry : 1.0f - ry);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int dx = c & 1, dy = c >> 1;
+    row[c] = table_row(e, l, (uint32_t)(fx + dx), (uint32_t)(fy + dy));
+    w[c] = (dx ? rx : 1.0f - rx) * (dy ? ry : 1.0f - ry);
+  }
 }
 
 // X[i, l F + f] = sum_corners w table[l, row, f] for texels n0 + i.
@@ -89,12 +115,12 @@ __global__ void __launch_bounds__(kThreads) k_encode(Enc e, const float* table, 
   const int n = n0 + i, tx = n % W, ty = n / W;
   const size_t lt = (size_t)l << e.logT;
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  uint32_t row[4];
+  float w[4];
+  corners4(e, l, tx, ty, W, H, row, w);
   for (int c = 0; c < 4; ++c) {
-    uint32_t row;
-    float w;
-    corner(e, l, tx, ty, W, H, c, row, w);
-    const float* t = table + (lt + row) * e.F;
-    for (int f = 0; f < e.F; ++f) acc[f] = fmaf(w, __ldg(t + f), acc[f]);
+    const float* t = table + (lt + row[c]) * e.F;
+    for (int f = 0; f < e.F; ++f) acc[f] = fmaf(w[c], __ldg(t + f), acc[f]);
   }
   float* x = X + (size_t)i * e.L * e.F + l * e.F;
   for (int f = 0; f < e.F; ++f) x[f] = acc[f];

@@ -266,12 +266,10 @@ __device__ __forceinline__ void encode_row(const Enc& e, const float* table, int
       for (int d = 0; d < 4; ++d) {
         const int l = lb + d < l1 ? lb + d : lb;
         const size_t lt = (size_t)l << e.logT;
+        uint32_t row[4];
+        corners4(e, l, tx, ty, W, H, row, w[d]);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          uint32_t row;
-          corner(e, l, tx, ty, W, H, c, row, w[d][c]);
-          v[d][c] = __ldg(t2 + lt + row);
-        }
+        for (int c = 0; c < 4; ++c) v[d][c] = __ldg(t2 + lt + row[c]);
       }
 #pragma unroll
       for (int d = 0; d < 4; ++d) {
@@ -292,12 +290,12 @@ __device__ __forceinline__ void encode_row(const Enc& e, const float* table, int
   for (int l = l0; l < l1; ++l) {
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const size_t lt = (size_t)l << e.logT;
+    uint32_t row[4];
+    float w[4];
+    corners4(e, l, tx, ty, W, H, row, w);
     for (int c = 0; c < 4; ++c) {
-      uint32_t row;
-      float w;
-      corner(e, l, tx, ty, W, H, c, row, w);
-      const float* t = table + (lt + row) * e.F;
-      for (int f = 0; f < e.F; ++f) acc[f] = fmaf(w, __ldg(t + f), acc[f]);
+      const float* t = table + (lt + row[c]) * e.F;
+      for (int f = 0; f < e.F; ++f) acc[f] = fmaf(w[c], __ldg(t + f), acc[f]);
     }
     for (int f = 0; f < e.F; ++f) *op_at(X, m, l * e.F + f, Kp) = tf32_rna(acc[f]);
   }
