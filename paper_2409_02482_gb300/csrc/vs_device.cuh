@@ -491,19 +491,23 @@ __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
   p.lo = __fadd_rn(p.lo, __fmul_rn(a.lo, b));
   return quick_two_sum(p.hi, p.lo);
 }
-__device__ __forceinline__ ff ff_div(ff a, ff b) {
-  const float q1 = __fdiv_rn(a.hi, b.hi);
-  ff r = ff_add(a, ff_mul_f({-b.hi, -b.lo}, q1));
-  const float q2 = __fdiv_rn(r.hi, b.hi);
-  r = ff_add(r, ff_mul_f({-b.hi, -b.lo}, q2));
-  const float q3 = __fdiv_rn(r.hi, b.hi);
-  ff q = quick_two_sum(q1, q2);
-  return ff_add(q, {q3, 0.0f});
-}
 __device__ __forceinline__ ff ll_to_ff(long long v) {
   const float hi = __ll2float_rn(v);
   const float lo = __ll2float_rn(v - __float2ll_rn(hi));
   return {hi, lo};
+}
+__device__ __forceinline__ ff int_to_ff(int v) {   // the same split for |v| < 2^31
+  const float hi = __int2float_rn(v);
+  const float lo = __int2float_rn(v - __float2int_rn(hi));
+  return {hi, lo};
+}
+// a / b with rb = 1/b.hi rounded: the quotient estimate and one correction
+// step on the float-float remainder (relative error near 2^-44).
+__device__ __forceinline__ ff ff_div_r(ff a, ff b, float rb) {
+  const float q1 = __fmul_rn(a.hi, rb);
+  const ff r = ff_add(a, ff_mul_f({-b.hi, -b.lo}, q1));
+  const float q2 = __fmul_rn(r.hi, rb);
+  return quick_two_sum(q1, q2);
 }
 
 // ----------------------------------------------------------------------------
@@ -547,8 +551,25 @@ __device__ __forceinline__ void split_coord_f(float X0, float delta, int& i, flo
 // go through float-float.
 __device__ __forceinline__ void texel_coords(const Tri& t, const float2 uv[3], int tw, int th, int px, int py,
                                              int& ix, float& fx, int& iy, float& fy) {
+  // exact edge values at the pixel: 32-bit arithmetic when every vertex lies
+  // within 2^14 units (64 px) of it (products below 2^29), else 64-bit; the
+  // same integers either way
+  bool near = true;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+    near = near && abs(t.X[j] - px) < (1 << 14) && abs(t.Y[j] - py) < (1 << 14);
+  int e32[3];
   long long e[3];
-  edge_values(t, px, py, e);
+  if (near) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int a = (j + 2) % 3, b = (j + 1) % 3;
+      e32[j] = (t.X[b] - t.X[a]) * (py - t.Y[a]) - (t.Y[b] - t.Y[a]) * (px - t.X[a]);
+      e[j] = e32[j];
+    }
+  } else {
+    edge_values(t, px, py, e);
+  }
   const float W = (float)tw, H = (float)th;
   const float X0 = __fmul_rn(uv[0].x, W), X1 = __fmul_rn(uv[1].x, W), X2 = __fmul_rn(uv[2].x, W);
   const float Y0 = __fmul_rn(uv[0].y, H), Y1 = __fmul_rn(uv[1].y, H), Y2 = __fmul_rn(uv[2].y, H);
@@ -556,22 +577,29 @@ __device__ __forceinline__ void texel_coords(const Tri& t, const float2 uv[3], i
   const float d1y = __fsub_rn(Y1, Y0), d2y = __fsub_rn(Y2, Y0);
   const float span = fmaxf(fmaxf(fabsf(d1x), fabsf(d2x)), fmaxf(fabsf(d1y), fabsf(d2y)));
   if (span <= 8.0f) {
-    const float w0 = __fmul_rn((float)e[0], t.iw[0]);
-    const float w1 = __fmul_rn((float)e[1], t.iw[1]);
-    const float w2 = __fmul_rn((float)e[2], t.iw[2]);
+    float ef[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) ef[j] = near ? __int2float_rn(e32[j]) : __ll2float_rn(e[j]);
+    const float w0 = __fmul_rn(ef[0], t.iw[0]);
+    const float w1 = __fmul_rn(ef[1], t.iw[1]);
+    const float w2 = __fmul_rn(ef[2], t.iw[2]);
     const float rD = __fdividef(1.0f, __fadd_rn(__fadd_rn(w0, w1), w2));
     const float l1 = __fmul_rn(w1, rD), l2 = __fmul_rn(w2, rD);
     split_coord_f(X0, __fmaf_rn(l1, d1x, __fmul_rn(l2, d2x)), ix, fx);
     split_coord_f(Y0, __fmaf_rn(l1, d1y, __fmul_rn(l2, d2y)), iy, fy);
   } else {
-    const ff w0 = ff_mul_f(ll_to_ff(e[0]), t.iw[0]);
-    const ff w1 = ff_mul_f(ll_to_ff(e[1]), t.iw[1]);
-    const ff w2 = ff_mul_f(ll_to_ff(e[2]), t.iw[2]);
+    ff ee[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) ee[j] = near ? int_to_ff(e32[j]) : ll_to_ff(e[j]);
+    const ff w0 = ff_mul_f(ee[0], t.iw[0]);
+    const ff w1 = ff_mul_f(ee[1], t.iw[1]);
+    const ff w2 = ff_mul_f(ee[2], t.iw[2]);
     const ff D = ff_add(ff_add(w0, w1), w2);
+    const float rD = __frcp_rn(D.hi);
     const ff ex1 = two_sum(X1, -X0), ex2 = two_sum(X2, -X0);
     const ff ey1 = two_sum(Y1, -Y0), ey2 = two_sum(Y2, -Y0);
-    split_coord(X0, ff_div(ff_add(ff_mul(w1, ex1), ff_mul(w2, ex2)), D), ix, fx);
-    split_coord(Y0, ff_div(ff_add(ff_mul(w1, ey1), ff_mul(w2, ey2)), D), iy, fy);
+    split_coord(X0, ff_div_r(ff_add(ff_mul(w1, ex1), ff_mul(w2, ex2)), D, rD), ix, fx);
+    split_coord(Y0, ff_div_r(ff_add(ff_mul(w1, ey1), ff_mul(w2, ey2)), D, rD), iy, fy);
   }
 }
 
