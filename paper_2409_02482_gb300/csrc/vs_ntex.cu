@@ -107,17 +107,31 @@ __device__ __forceinline__ void corners4(const Enc& e, int l, int tx, int ty, in
 }
 
 // X[i, l F + f] = sum_corners w table[l, row, f] for texels n0 + i.
-__global__ void __launch_bounds__(kThreads) k_encode(Enc e, const float* table, int W, int H, int n0, int count,
-                                                      float* X) {
+__global__ void __launch_bounds__(kThreads) k_encode(const __grid_constant__ Enc e, const float* table, int W, int H,
+                                                      int n0, int count, float* X) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= (long long)count * e.L) return;
   const int i = (int)(id / e.L), l = (int)(id - (long long)i * e.L);
   const int n = n0 + i, tx = n % W, ty = n / W;
   const size_t lt = (size_t)l << e.logT;
-  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   uint32_t row[4];
   float w[4];
   corners4(e, l, tx, ty, W, H, row, w);
+  if (e.F == 2) {   // four 8-byte rows, all in flight; the same sums as below
+    const float2* t2 = reinterpret_cast<const float2*>(table) + lt;
+    float2 v[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = __ldg(t2 + row[c]);
+    float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      a0 = fmaf(w[c], v[c].x, a0);
+      a1 = fmaf(w[c], v[c].y, a1);
+    }
+    *reinterpret_cast<float2*>(X + (size_t)i * e.L * 2 + l * 2) = make_float2(a0, a1);
+    return;
+  }
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int c = 0; c < 4; ++c) {
     const float* t = table + (lt + row[c]) * e.F;
     for (int f = 0; f < e.F; ++f) acc[f] = fmaf(w[c], __ldg(t + f), acc[f]);
