@@ -1022,6 +1022,50 @@ def test_c3_full_size_fused_view_matches_oracle(vs, ctx):
     print(f"c3 full-size view: {frags.sum()} fragments, grad worst err / per-texel 1e-5 bar {w:.2e}")
 
 
+def test_c4_full_size_uneven_items_match_oracle(vs, ctx):
+    """The uneven multi-object configuration at full size (32 objects, k in
+    {3, 5, 7, 9}, 10k-1M faces per shell, 1024^2 SH1 FP16 texels at pitch
+    16, the SH1 class): the two objects with the most faces, one view each
+    at different resolutions, in ONE fused forward + adjoint batch with the
+    L2 loss against uniform targets.  Per item: hits exact, colours within
+    the FP16 bar, the loss against the oracle's, every texel value of the
+    gradient within its own bar."""
+    objs_cams = synth.config_scene("c4", views=8, pitch=16)
+    order = sorted(range(len(objs_cams)), key=lambda o: -sum(s.tris.shape[0] for s in objs_cams[o][0].shells))
+    picks = []
+    for o in order[:2]:
+        sc, cams = objs_cams[o]
+        cam = max(cams, key=lambda c: c.width * c.height) if not picks else min(cams, key=lambda c: c.width * c.height)
+        picks.append((sc, cam))
+    del objs_cams
+    rng = np.random.default_rng(21)
+    items = []
+    for sc, cam in picks:
+        obj = vs.ShellObject.from_scene(ctx, sc)
+        H, W = cam.height, cam.width
+        tgt = rng.random((H, W, 3), dtype=np.float32)
+        items.append(dict(obj=obj, cam=cam, scene=sc, tgt=tgt, out=torch.empty((H, W, 4), device="cuda"),
+                          hits=torch.empty((obj.k, H, W), dtype=torch.int32, device="cuda"),
+                          grad_rgb=torch.from_numpy(tgt).cuda(), grads=obj.zero_grads(),
+                          loss=torch.zeros(1, device="cuda")))
+    ws = vs.make_workspace(ctx, [it["obj"] for it in items], [it["cam"] for it in items])
+    vs.render_batch(ctx, items, ws, do_backward=True, flags=vs.VS_FLAG_LOSS_L2)
+    st = vs.read_stats(ws)
+    assert st["device_status"] == 0 and st["kernel_class"] == 1 + 2 + 1
+    for it in items:
+        sc, cam = it["scene"], it["cam"]
+        ref, ref_hits, frags = oracle.render(sc, cam)
+        assert np.array_equal(it["hits"].cpu().numpy(), ref_hits)
+        assert np.abs(it["out"].cpu().numpy() - ref).max() <= TOL_F16
+        t64 = it["tgt"].astype(np.float64)
+        L, dL = oracle.l2_loss_grad(ref, t64)
+        assert abs(it["loss"].item() - L) <= 1e-5 * L
+        w = assert_grad_bar_by_shell(sc, [(cam, ref_hits, dL, oracle.l2_loss_scale(ref, t64))], it["grads"],
+                                     TOL_F16, nch=13)
+        print(f"c4 full-size item k={sc.k} {cam.width}x{cam.height}: "
+              f"{frags.sum()} fragments, grad worst err / per-texel bar {w:.2e}")
+
+
 def test_c5_full_size_view_matches_oracle(vs, ctx):
     """The large configuration at full size: 9 shells x ~2M faces, 4096^2
     SH3 FP16 texels (pitch 64, the SH3 class; ~19 GB), one 3840x2160 view.
