@@ -763,7 +763,7 @@ int fused_forward_tc(const vs_ntex_config& c, const Views& P, const Enc& e, int 
   const int per_sm = 2 * (smem + 1024) <= 228 * 1024 ? 2 : 1;
   MlpFwdArgs a{P.table, P.W0, P.b0, P.W1, P.b1, P.W2, P.b2, texels, W, H, W * H, c.out_ch, LF, dtype, pitch, ch0,
                status, 1ll << 22};
-  k_mlp_fwd_tc<<<sms * per_sm, kTcThreads, smem, st>>>(a, e);
+  k_mlp_fwd_tc<<<sms * per_sm, kFwdThreads, smem, st>>>(a, e);
   return (int)cudaGetLastError();
 }
 

@@ -372,7 +372,11 @@ __host__ __device__ constexpr int mlp_fwd_smem(int LF, int C) {
          2 * op_bytes(128, kMlpH) + 256;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(const MlpFwdArgs a, const __grid_constant__ Enc e) {
+// 8 warps per CTA, as in the adjoint: warps w and w + 4 share a tensor-memory
+// lane quarter (texel rows) and split the columns and the encoding's levels.
+constexpr int kFwdThreads = 256;
+
+__global__ void __launch_bounds__(kFwdThreads, 2) k_mlp_fwd_tc(const MlpFwdArgs a, const __grid_constant__ Enc e) {
   extern __shared__ __align__(128) char msm[];
   const int LFp = (a.LF + 7) & ~7, Cp = (a.C + 15) & ~15;
   float* W0s = reinterpret_cast<float*>(msm);
@@ -384,6 +388,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(const MlpFwdArgs a
   uint64_t* bar = reinterpret_cast<uint64_t*>(H2s + 128 * kMlpH);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int half = tid >> 7, r = tid & 127;        // column half, texel row of the tile
+  const int l_lo = half ? (e.L + 1) / 2 : 0, l_hi = half ? e.L : (e.L + 1) / 2;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kMlpTmemCols)
@@ -401,19 +407,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(const MlpFwdArgs a
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   uint32_t phase = 0;
   bool ok = true;
   const int tiles = (a.N + 127) / 128;
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    // encoding of texel n = 128 tile + tid into row tid of X
-    const int n = tile * 128 + tid;
-    if (n < a.N) {
-      encode_row(e, a.table, n % a.W, n / a.W, a.W, a.H, 0, e.L, Xs, tid, LFp);
-      for (int k = a.LF; k < LFp; ++k) *op_at(Xs, tid, k, LFp) = 0.0f;
-    } else {
-      for (int k = 0; k < LFp; ++k) *op_at(Xs, tid, k, LFp) = 0.0f;
-    }
+    // encoding of texel n = 128 tile + r into row r of X (this half's levels)
+    const int n = tile * 128 + r;
+    if (n < a.N) encode_row(e, a.table, n % a.W, n / a.W, a.W, a.H, l_lo, l_hi, Xs, r, LFp);
+    else
+      for (int k = l_lo * e.F; k < l_hi * e.F; ++k) *op_at(Xs, r, k, LFp) = 0.0f;
+    if (half == 0)
+      for (int k = a.LF; k < LFp; ++k) *op_at(Xs, r, k, LFp) = 0.0f;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -421,12 +426,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(const MlpFwdArgs a
     // layer 0
     if (tid == 0) mma_tile(tmem, Xs, W0s, LFp, kMlpH, bar);
     ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
-    for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+    for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
       for (int j = 0; j < 16; j += 4)
-        st4(H1s, tid, c0 + j, kMlpH, relu_tf32(v + j, a.b0 + c0 + j, true));
+        st4(H1s, r, c0 + j, kMlpH, relu_tf32(v + j, a.b0 + c0 + j, true));
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -435,12 +440,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(const MlpFwdArgs a
     // layer 1
     if (tid == 0) mma_tile(tmem + 64u, H1s, W1s, kMlpH, kMlpH, bar);
     ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
-    for (int c0 = 0; c0 < kMlpH; c0 += 16) {
+    for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + lane_base + 64u + (uint32_t)c0, v);
 #pragma unroll
       for (int j = 0; j < 16; j += 4)
-        st4(H2s, tid, c0 + j, kMlpH, relu_tf32(v + j, a.b1 + c0 + j, true));
+        st4(H2s, r, c0 + j, kMlpH, relu_tf32(v + j, a.b1 + c0 + j, true));
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -449,7 +454,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_fwd_tc(const MlpFwdArgs a
     // output layer -> texels
     if (tid == 0) mma_tile(tmem + 128u, H2s, W2s, kMlpH, Cp, bar);
     ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
-    for (int c0 = 0; c0 < Cp; c0 += 16) {
+    for (int c0 = 16 * half; c0 < Cp; c0 += 32) {
       float v[16];
       tmem_ld16(tmem + lane_base + 128u + (uint32_t)c0, v);
       if (n < a.N) {
