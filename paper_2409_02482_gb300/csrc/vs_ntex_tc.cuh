@@ -533,11 +533,17 @@ __device__ __forceinline__ void sync_for_mma() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 8 warps per CTA: warps w and w + 4 share the tensor-memory lane quarter
-// (texel rows 32 (w % 4) ..) and split the columns (and the encoding's
-// levels) between them; the weight gradients of a tile are summed on the
-// FP32 pipes while the tensor cores run the next product.
-constexpr int kBwdThreads = 256;
+// kBwdWarps warps per CTA: warps w, w + 4, ... share the tensor-memory lane
+// quarter (texel rows 32 (w % 4) ..) and split the columns (and the
+// encoding's levels) between them; the weight gradients of a tile are summed
+// by warp-level MMAs while the tensor cores run the next product.  16 warps
+// (125 registers) hide more of the gathers' and products' latency than 8.
+#ifndef VS_NTEX_BWD_WARPS
+#define VS_NTEX_BWD_WARPS 16
+#endif
+constexpr int kBwdWarps = VS_NTEX_BWD_WARPS;   // 8 or 16: 2 or 4 warps per tensor-memory lane quarter
+constexpr int kBwdThreads = 32 * kBwdWarps;
+static_assert(kBwdWarps == 8 || kBwdWarps == 16, "column groups of 32 or 16 hidden units");
 
 // Element (m, k) of a canonical operand tile as raw bits (an MMA fragment).
 __device__ __forceinline__ uint32_t lds_u(const float* base, int m, int k, int Kp) {
@@ -569,7 +575,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
   uint64_t* bar = reinterpret_cast<uint64_t*>(dH1s + 128 * kMlpH);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int half = tid >> 7, r = tid & 127;        // column half, texel row of the tile
+  const int quad = tid >> 7, r = tid & 127;        // column group, texel row of the tile
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kMlpTmemCols)
@@ -597,48 +603,53 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
   // texel-contiguous (transposed) operands, which tcgen05's TF32 K-major
   // descriptors would need as extra copies that do not fit shared memory.
   // FP32 accumulators in registers over the CTA's tiles.  Warp w:
-  //   dW1 = dH2^T H1: rows 16 (w & 3) .. +15, columns 32 (w >> 2) .. +31
-  //   dW2 = dY^T H2:  rows 16 (w & 1) .. +15, columns 16 (w >> 1) .. +15
-  //   dW0 = dH1^T X:  rows 16 (w & 3) .. +15, columns 16 (w >> 2) .. +15
+  //   dW1 = dH2^T H1: rows 16 (w & 3) .. +15, J1 n8-tiles of columns from 8 J1 (w >> 2)
+  //   dW2 = dY^T H2:  rows 16 (w & 1) .. +15, J2 n8-tiles from 8 J2 (w >> 1)
+  //   dW0 = dH1^T X:  rows 16 (w & 3) .. +15, J0 n8-tiles from 8 J0 (w >> 2)
   //   db1, db0 (warps 0-3): the same A fragments times a matrix of ones
   //   db2: FP32 sums of dY per thread (kept exact: a plain sum)
+  constexpr int J1 = 32 / kBwdWarps, J2 = 16 / kBwdWarps, J0 = 16 / kBwdWarps, NG = kBwdWarps / 4;
+  constexpr int kDy = 32 / NG;                      // dY columns per thread at most (Cp <= 32)
   const int g = lane >> 2, tig = lane & 3;
-  const int m1 = 16 * (warp & 3), n1 = 32 * (warp >> 2);
-  const int m2 = 16 * (warp & 1), n2 = 16 * (warp >> 1);
-  const int n0c = 16 * (warp >> 2);
+  const int m1 = 16 * (warp & 3), n1 = 8 * J1 * (warp >> 2);
+  const int m2 = 16 * (warp & 1), n2 = 8 * J2 * (warp >> 1);
+  const int n0c = 8 * J0 * (warp >> 2);
   const bool do_w2 = m2 < Cp, bias = warp < 4;
-  float acc1[4][4], acc2[2][4], acc0[2][4], accb1[4], accb0[4], gb2[16];
+  float acc1[J1][4], acc2[J2][4], acc0[J0][4], accb1[4], accb0[4], gb2[kDy];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     accb1[q] = accb0[q] = 0.0f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc1[j][q] = 0.0f;
+    for (int j = 0; j < J1; ++j) acc1[j][q] = 0.0f;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) acc2[j][q] = acc0[j][q] = 0.0f;
+    for (int j = 0; j < J2; ++j) acc2[j][q] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < J0; ++j) acc0[j][q] = 0.0f;
   }
 #pragma unroll
-  for (int q = 0; q < 16; ++q) gb2[q] = 0.0f;
+  for (int q = 0; q < kDy; ++q) gb2[q] = 0.0f;
   const uint32_t one = __float_as_uint(1.0f);
-  const int l_lo = half ? (e.L + 1) / 2 : 0, l_hi = half ? e.L : (e.L + 1) / 2;
+  const int l_lo = quad * e.L / NG, l_hi = (quad + 1) * e.L / NG;   // this group's levels
+  const int cw = kMlpH / NG;                                        // hidden columns per group
 
   const int tiles = (a.count + 127) / 128;
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int i = tile * 128 + r, n = a.n0 + i;
     const bool live = i < a.count;
     const int tx = live ? n % a.W : 0, ty = live ? n / a.W : 0;
-    // encoding of row r (this half's levels) and the output gradient (this
-    // half's columns)
+    // encoding of row r (this group's levels) and the output gradient (this
+    // group's columns)
     if (live) encode_row(e, a.table, tx, ty, a.W, a.H, l_lo, l_hi, Xs, r, LFp);
     else
       for (int k = l_lo * e.F; k < l_hi * e.F; ++k) *op_at(Xs, r, k, LFp) = 0.0f;
-    if (half == 0)
+    if (quad == 0)
       for (int k = LF; k < LFp; ++k) *op_at(Xs, r, k, LFp) = 0.0f;
     // dY kept in FP32 (the tensor cores read its TF32 part; the bias and
     // weight gradients of the output layer use all of it)
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int c = half * (Cp / 2) + q;
-      if (q < Cp / 2) {
+    for (int q = 0; q < kDy; ++q) {
+      const int c = quad * (Cp / NG) + q;
+      if (q < Cp / NG) {
         const float v = (live && c < a.C) ? __ldg(a.grad + (size_t)n * a.pitch + a.ch0 + c) : 0.0f;
         *op_at(dYs, r, c, Cp) = v;
         gb2[q] += v;
@@ -648,7 +659,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
     // layer 0 -> H1
     if (tid == 0) mma_tile(tmem, Xs, W0s, LFp, kMlpH, bar);
     ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
-    for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 16) {
+    for (int c0 = cw * quad; c0 < cw * quad + cw; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
@@ -661,7 +672,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
       mma_tile(tmem + 128u, dYs, W2Ts, Cp, kMlpH, bar);
     }
     ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
-    for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 16) {
+    for (int c0 = cw * quad; c0 < cw * quad + cw; c0 += 16) {
       float v[16], u[16];
       tmem_ld16(tmem + lane_base + 64u + (uint32_t)c0, v);
       tmem_ld16(tmem + lane_base + 128u + (uint32_t)c0, u);
@@ -683,7 +694,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
       const uint32_t A[4] = {lds_u(dH2s, ka, m1 + g, kMlpH), lds_u(dH2s, ka, m1 + g + 8, kMlpH),
                              lds_u(dH2s, kb, m1 + g, kMlpH), lds_u(dH2s, kb, m1 + g + 8, kMlpH)};
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < J1; ++j)
         mma_tf32(acc1[j], A, lds_u(H1s, ka, n1 + 8 * j + g, kMlpH), lds_u(H1s, kb, n1 + 8 * j + g, kMlpH));
       if (bias) mma_tf32(accb1, A, one, one);
       if (do_w2) {
@@ -691,12 +702,12 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
         auto dy = [&](int t, int c) { return c < Cp ? __float_as_uint(tf32_rna(*op_at(dYs, t, c, Cp))) : 0u; };
         const uint32_t A2[4] = {dy(ka, m2 + g), dy(ka, m2 + g + 8), dy(kb, m2 + g), dy(kb, m2 + g + 8)};
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
+        for (int j = 0; j < J2; ++j)
           mma_tf32(acc2[j], A2, lds_u(H2s, ka, n2 + 8 * j + g, kMlpH), lds_u(H2s, kb, n2 + 8 * j + g, kMlpH));
       }
     }
     ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
-    for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 16) {
+    for (int c0 = cw * quad; c0 < cw * quad + cw; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
@@ -715,7 +726,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
       const uint32_t A[4] = {lds_u(dH1s, ka, m1 + g, kMlpH), lds_u(dH1s, ka, m1 + g + 8, kMlpH),
                              lds_u(dH1s, kb, m1 + g, kMlpH), lds_u(dH1s, kb, m1 + g + 8, kMlpH)};
 #pragma unroll
-      for (int j = 0; j < 2; ++j)
+      for (int j = 0; j < J0; ++j)
         if (n0c + 8 * j < LFp)
           mma_tf32(acc0[j], A, lds_u(Xs, ka, n0c + 8 * j + g, LFp), lds_u(Xs, kb, n0c + 8 * j + g, LFp));
       if (bias) mma_tf32(accb0, A, one, one);
@@ -723,7 +734,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
     ok = wait_mma(bar, phase, a.status, a.spin_limit) && ok;
     // dX stored level-major for the encoding's adjoint (a separate tiled
     // kernel: k_table_grad)
-    for (int c0 = 16 * half; c0 < LF16; c0 += 32) {
+    for (int c0 = 16 * quad; c0 < LF16; c0 += 16 * NG) {
       float v[16];
       tmem_ld16(tmem + lane_base + 64u + (uint32_t)c0, v);
       if (live) {
@@ -746,24 +757,25 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_mlp_bwd_tc(const MlpBwdArgs 
   for (int q = 0; q < 4; ++q) {
     const int row = g + 8 * (q >> 1), col = 2 * tig + (q & 1);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) atomicAdd(a.dW1 + (m1 + row) * kMlpH + n1 + 8 * j + col, acc1[j][q]);
+    for (int j = 0; j < J1; ++j) atomicAdd(a.dW1 + (m1 + row) * kMlpH + n1 + 8 * j + col, acc1[j][q]);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < J2; ++j)
       if (do_w2 && m2 + row < a.C) atomicAdd(a.dW2 + (m2 + row) * kMlpH + n2 + 8 * j + col, acc2[j][q]);
+#pragma unroll
+    for (int j = 0; j < J0; ++j)
       if (n0c + 8 * j + col < LF) atomicAdd(a.dW0 + (m1 + row) * LF + n0c + 8 * j + col, acc0[j][q]);
-    }
     if (bias && tig == 0 && (q & 1) == 0) {   // every column of a bias tile holds the same sums
       atomicAdd(a.db1 + m1 + row, accb1[q]);
       atomicAdd(a.db0 + m1 + row, accb0[q]);
     }
   }
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
+  for (int q = 0; q < kDy; ++q) {
     float v = gb2[q];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int c = half * (Cp / 2) + q;
-    if (lane == 0 && q < Cp / 2 && c < a.C) atomicAdd(a.db2 + c, v);
+    const int c = quad * (Cp / NG) + q;
+    if (lane == 0 && q < Cp / NG && c < a.C) atomicAdd(a.db2 + c, v);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
