@@ -587,6 +587,32 @@ __device__ __forceinline__ void texel_coords(const Tri& t, const float2 uv[3], i
     const float l1 = __fmul_rn(w1, rD), l2 = __fmul_rn(w2, rD);
     split_coord_f(X0, __fmaf_rn(l1, d1x, __fmul_rn(l2, d2x)), ix, fx);
     split_coord_f(Y0, __fmaf_rn(l1, d1y, __fmul_rn(l2, d2y)), iy, fy);
+  } else if (span <= 32.0f && near && abs(e32[0]) < (1 << 24) && abs(e32[1]) < (1 << 24) &&
+             abs(e32[2]) < (1 << 24)) {
+    // Edge values below 2^24 convert to float exactly, so each weight
+    // w_j = e_j (1/w_j) carries one rounding (relative 2^-24); everything
+    // after it -- the sum of the weights, the vertex differences, the
+    // numerators and the quotient with one correction step -- is kept to
+    // ~2^-44 by error-free transformations.  The weights' roundings move
+    // the offset by at most 2 * 2^-24 * span: 2^-18 texel at span 32.
+    const float w0 = __fmul_rn(__int2float_rn(e32[0]), t.iw[0]);
+    const float w1 = __fmul_rn(__int2float_rn(e32[1]), t.iw[1]);
+    const float w2 = __fmul_rn(__int2float_rn(e32[2]), t.iw[2]);
+    const ff s01 = two_sum(w0, w1);
+    const ff s012 = two_sum(s01.hi, w2);
+    const float Sh = s012.hi, Sl = __fadd_rn(s012.lo, s01.lo);
+    const float r = __frcp_rn(Sh);
+    auto offset = [&](float A0, float A1, float A2) {
+      const ff d1 = two_sum(A1, -A0), d2 = two_sum(A2, -A0);
+      const ff p1 = two_prod(w1, d1.hi), p2 = two_prod(w2, d2.hi);
+      const ff nh = two_sum(p1.hi, p2.hi);
+      const float nl = __fmaf_rn(w2, d2.lo, __fmaf_rn(w1, d1.lo, __fadd_rn(__fadd_rn(nh.lo, p1.lo), p2.lo)));
+      const float q = __fmul_rn(nh.hi, r);
+      const float rem = __fadd_rn(__fmaf_rn(-q, Sh, nh.hi), __fsub_rn(nl, __fmul_rn(q, Sl)));
+      return quick_two_sum(q, __fmul_rn(rem, r));
+    };
+    split_coord(X0, offset(X0, X1, X2), ix, fx);
+    split_coord(Y0, offset(Y0, Y1, Y2), iy, fy);
   } else {
     ff ee[3];
 #pragma unroll
