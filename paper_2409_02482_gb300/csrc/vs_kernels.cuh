@@ -147,20 +147,20 @@ __device__ __forceinline__ unsigned depth_key32(const unsigned q[3], const int e
   return Q;
 }
 
-// One round of a raster unit: 32 triangles t0 + lane of one shell.  Each
-// lane sets up one triangle; then the warp walks all (triangle, box pixel)
-// pairs of the 32 triangles together: window by window, a warp-wide OR of
-// the triangles' start bits tells every lane which triangle owns its pair,
-// so lanes do not idle on small or culled boxes.  Larger boxes are
-// rasterized by the whole warp, one triangle at a time.
 // Per-lane triangle counts of a raster unit, two 16-bit fields per word (a
-// lane sees one triangle per round and a unit has at most kMaxRasterRounds
+// lane sees one triangle per round and a unit has at most 2048 / 32 = 64
 // rounds, so no field overflows): fb = front | back << 16, ng = near plane |
 // guard band << 16, lc = large box | clipped << 16, plus an error bit.
 struct RasterCounts {
   unsigned fb, ng, lc, bad;
 };
 
+// One round of a raster unit: 32 triangles t0 + lane of one shell.  Each
+// lane sets up one triangle; then the warp walks all (triangle, box pixel)
+// pairs of the 32 triangles together: window by window, a warp-wide OR of
+// the triangles' start bits tells every lane which triangle owns its pair,
+// so lanes do not idle on small or culled boxes.  Larger boxes are
+// rasterized by the whole warp, one triangle at a time.
 template <bool HINT, bool FULL>
 __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, int t0, unsigned long long* vis,
                                              char* smem, RasterCounts& rc) {
@@ -317,20 +317,27 @@ static __device__ __forceinline__ void unit_raster(const DItem& it, const DShell
 // ----------------------------------------------------------------------------
 // The part of triangle setup shading needs: snapped positions and 1/w,
 // after the same validity checks as the raster (0 = usable).
-__device__ __forceinline__ int load_tri_shade(const DShell& s, int t, Tri& T, int idx[3]) {
+// The vertices' UVs are loaded alongside their snapped positions (both
+// need only the indices), so the two loads overlap instead of chaining.
+__device__ __forceinline__ int load_tri_shade(const DShell& s, int t, Tri& T, int idx[3], float2 uv[3]) {
   const int* ip = s.tris + 3 * (size_t)t;
   idx[0] = __ldg(ip);
   idx[1] = __ldg(ip + 1);
   idx[2] = __ldg(ip + 2);
   if ((unsigned)idx[0] >= (unsigned)s.nv || (unsigned)idx[1] >= (unsigned)s.nv || (unsigned)idx[2] >= (unsigned)s.nv)
     return 4;
+  int4 v[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    const int4 v = __ldcg(s.vsetup + idx[j]);
-    if (v.x == kInvalidX) return 2;
-    T.X[j] = v.x;
-    T.Y[j] = v.y;
-    T.iw[j] = __int_as_float(v.z);
+    v[j] = __ldcg(s.vsetup + idx[j]);
+    uv[j] = __ldg(s.uv + idx[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    if (v[j].x == kInvalidX) return 2;
+    T.X[j] = v[j].x;
+    T.Y[j] = v[j].y;
+    T.iw[j] = __int_as_float(v[j].z);
   }
   const long long a2 = (long long)(T.X[1] - T.X[0]) * (T.Y[2] - T.Y[0]) -
                        (long long)(T.X[2] - T.X[0]) * (T.Y[1] - T.Y[0]);
@@ -768,12 +775,7 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
         int idx[3];
         const int y = pp / W, x = pp - y * W;
         float2 uv[3];
-        const int r = t < s.nt ? load_tri_shade(s, t, Tr, idx) : 4;
-        if (r == 0) {
-          uv[0] = __ldg(s.uv + idx[0]);
-          uv[1] = __ldg(s.uv + idx[1]);
-          uv[2] = __ldg(s.uv + idx[2]);
-        }
+        const int r = t < s.nt ? load_tri_shade(s, t, Tr, idx, uv) : 4;
         if (FULL && r == 2) {
           // a vertex nearer than znear (or off the guard band): the triangle
           // is clipped; shaded by the pass below
