@@ -546,9 +546,10 @@ __device__ __forceinline__ void split_coord_f(float X0, float delta, int& i, flo
 
 // Perspective-correct UV of pixel centre (px, py) mapped to texel space
 // (x = u W - 1/2, y = v H - 1/2), interpolated relative to vertex 0, as an
-// integer part and a fraction (unclamped).  For triangles spanning at most 8
-// texels plain FP32 keeps the texel-space error near 1e-6 texel; wider ones
-// go through float-float.
+// integer part and a fraction (unclamped).  Three paths by the triangle's
+// span in texels: up to 8, plain FP32 (error ~10 2^-24 span); up to 32 with
+// edge values below 2^24, one rounding per weight and error-free
+// transformations after it (error <= 2 2^-24 span); beyond, float-float.
 __device__ __forceinline__ void texel_coords(const Tri& t, const float2 uv[3], int tw, int th, int px, int py,
                                              int& ix, float& fx, int& iy, float& fy) {
   // exact edge values at the pixel: 32-bit arithmetic when every vertex lies
