@@ -188,59 +188,37 @@ __device__ __forceinline__ void red_max_u64(unsigned long long* p, unsigned long
   asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// L2 eviction priority of the per-shell visibility words in the fused
-// forward + adjoint kernel: an item's words (36 MB for k = 7 at 800^2) are
-// cleared and max-reduced a few stages before its shading reads them once,
-// while ~2 GB of texel reads and gradient reductions per view stream through
-// the 129 MB L2.  HINT keeps them with evict_last until that read, which is
-// evict_first.  (Measured on the C2 step: 2.7 % faster fused; the
-// forward-only kernel, with less L2 pressure, is faster without, and texel
-// reads marked evict_first are slower everywhere, so neither is used.)
+// L2 eviction priority.  The fused forward + adjoint kernel streams, per
+// view, ~2 GB of texel reads and FP32 gradient reductions and 36 MB of
+// per-shell visibility words (k = 7 at 800^2) through the 129 MB L2.  A
+// gradient texel's 128-byte line is reduced into by the neighbouring
+// fragments of several shading rounds; the reductions mark it evict_last so
+// that it stays in L2 between them instead of making another DRAM round trip.
+// The visibility words and the texel reads of the adjoint keep the default
+// priority.  (Measured on the C2 step against other assignments: words
+// evict_last until an evict_first read, gradients normal -- 0.8 % slower;
+// texel reads evict_first -- 11 % slower, evict_last -- 0.6 % slower.  The
+// forward-only kernels keep texel lines evict_last: there they are the
+// lines that neighbouring fragments reuse.)
 __device__ __forceinline__ unsigned long long l2_evict_last() {
   unsigned long long p;
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
-__device__ __forceinline__ unsigned long long l2_evict_first() {
-  unsigned long long p;
-  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-template <bool HINT>
 __device__ __forceinline__ void red_max_vis(unsigned long long* p, unsigned long long v) {
-  if constexpr (HINT)
-    asm volatile("red.relaxed.gpu.global.max.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(l2_evict_last())
-                 : "memory");
-  else
-    asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+  asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-template <bool HINT>
-__device__ __forceinline__ void clear_vis2(uint4* p) {
-  if constexpr (HINT)
-    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %1, %1, %1}, %2;" ::"l"(p), "r"(0u), "l"(l2_evict_last())
-                 : "memory");
-  else
-    *p = make_uint4(0, 0, 0, 0);
-}
-template <bool HINT>
-__device__ __forceinline__ unsigned long long load_vis(const unsigned long long* p) {
-  if constexpr (HINT) {
-    unsigned long long v;
-    asm volatile("ld.global.cg.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(l2_evict_first()) : "memory");
-    return v;
-  } else {
-    return __ldcg(p);
-  }
-}
+__device__ __forceinline__ void clear_vis2(uint4* p) { *p = make_uint4(0, 0, 0, 0); }
 __device__ __forceinline__ void red_add_f32(float* p, float v) {
   asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 __device__ __forceinline__ void red_add_v2f32(float* p, float a, float b) {
   asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
 }
+// Gradient reductions (16 bytes of a gradient texel), evict_last (above).
 __device__ __forceinline__ void red_add_v4f32(float* p, float a, float b, float c, float d) {
-  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
-               "f"(d)
+  asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(a),
+               "f"(b), "f"(c), "f"(d), "l"(l2_evict_last())
                : "memory");
 }
 
@@ -443,13 +421,8 @@ __device__ __forceinline__ int vis_tri(unsigned long long key) {
 // little-endian, so they sit at its address): an empty word is 0, and a
 // written one holds ~triangle there, which is never 0 because triangle ids
 // stay below 2^31.  Half the registers of loading the whole word.
-template <bool HINT>
 __device__ __forceinline__ int load_vis_tri(const unsigned long long* p) {
-  unsigned lo;
-  if constexpr (HINT)
-    asm volatile("ld.global.cg.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(lo) : "l"(p), "l"(l2_evict_first()) : "memory");
-  else
-    lo = __ldcg(reinterpret_cast<const unsigned*>(p));
+  const unsigned lo = __ldcg(reinterpret_cast<const unsigned*>(p));
   return lo ? (int)(0xFFFFFFFFu - lo) : -1;
 }
 
@@ -741,13 +714,21 @@ __device__ __forceinline__ float alpha_atten(const float* pos, const int idx[3],
 // ----------------------------------------------------------------------------
 // texel fetch + decode.  NCH values per texel, loaded VEC at a time.
 // ----------------------------------------------------------------------------
-template <int VEC>
+// KEEP: the load marks its L2 line evict_last (the forward-only kernels,
+// where texel lines are what neighbouring fragments reuse; measured on the
+// C2 forward batch: 2 % faster).
+template <int VEC, bool KEEP = false>
 __device__ __forceinline__ void load_halves(const __half* p, float* out) {
   if constexpr (VEC == 16) {   // one 256-bit load (32-byte aligned)
     unsigned r[8];
-    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-        : "l"(p));
+    if constexpr (KEEP)
+      asm("ld.global.nc.L2::cache_hint.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+          : "l"(p), "l"(l2_evict_last()));
+    else
+      asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+          : "l"(p));
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&r[i]));
@@ -755,7 +736,13 @@ __device__ __forceinline__ void load_halves(const __half* p, float* out) {
       out[2 * i + 1] = f.y;
     }
   } else if constexpr (VEC == 8) {
-    const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
+    uint4 r;
+    if constexpr (KEEP)
+      asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+          : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+          : "l"(p), "l"(l2_evict_last()));
+    else
+      r = __ldg(reinterpret_cast<const uint4*>(p));
     const __half2* h = reinterpret_cast<const __half2*>(&r);
 #pragma unroll
     for (int i = 0; i < 4; ++i) { float2 f = __half22float2(h[i]); out[2 * i] = f.x; out[2 * i + 1] = f.y; }
@@ -774,7 +761,7 @@ __device__ __forceinline__ void load_halves(const __half* p, float* out) {
 }
 
 // Bilinear mix of the 4 taps' NCH values (fp16 storage), FP32 accumulate.
-template <int NCH, int VEC>
+template <int NCH, int VEC, bool KEEP = false>
 __device__ __forceinline__ void bilinear_f16(const __half* tex, int tw, int pitch, const Footprint& f,
                                              float val[NCH]) {
   const float w00 = (1.0f - f.fx) * (1.0f - f.fy), w10 = f.fx * (1.0f - f.fy);
@@ -787,10 +774,10 @@ __device__ __forceinline__ void bilinear_f16(const __half* tex, int tw, int pitc
 #pragma unroll
   for (int l = 0; l < NL; ++l) {
     float a[VEC], b[VEC], c[VEC], d[VEC];
-    load_halves<VEC>(p00 + l * VEC, a);
-    load_halves<VEC>(p10 + l * VEC, b);
-    load_halves<VEC>(p01 + l * VEC, c);
-    load_halves<VEC>(p11 + l * VEC, d);
+    load_halves<VEC, KEEP>(p00 + l * VEC, a);
+    load_halves<VEC, KEEP>(p10 + l * VEC, b);
+    load_halves<VEC, KEEP>(p01 + l * VEC, c);
+    load_halves<VEC, KEEP>(p11 + l * VEC, d);
 #pragma unroll
     for (int i = 0; i < VEC; ++i) {
       const int ch = l * VEC + i;

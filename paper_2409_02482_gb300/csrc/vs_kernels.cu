@@ -24,14 +24,14 @@ __global__ void __launch_bounds__(kThreads) k_upload(char* ws, const __grid_cons
 __global__ void __launch_bounds__(kThreads) k_setup(TableRef tb, int item) {
   const DItem& it = tb.items[item];
   const int u = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  if (u < it.units[PH_SETUP]) unit_setup<false>(it, tb.shells + it.shell0, u);
+  if (u < it.units[PH_SETUP]) unit_setup(it, tb.shells + it.shell0, u);
 }
 
 template <bool FULL>
 __global__ void __launch_bounds__(kThreads) k_raster(TableRef tb, int item) {
   const DItem& it = tb.items[item];
   const int w = threadIdx.x >> 5;
-  unit_raster<false, FULL>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, vs_smem + w * kRasterWarpBytes, w, w + 1);
+  unit_raster<FULL>(it, tb.shells + it.shell0, blockIdx.x, tb.hdr, vs_smem + w * kRasterWarpBytes, w, w + 1);
 }
 
 }  // namespace vsd

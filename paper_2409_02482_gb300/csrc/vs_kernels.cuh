@@ -47,7 +47,6 @@ namespace vsd {
 // SETUP
 // ----------------------------------------------------------------------------
 // One warp per unit.
-template <bool HINT>
 static __device__ void unit_setup(const DItem& it, const DShell* sh, int u) {
   if (u < it.clear_units) {
     const size_t total = (size_t)it.k * it.cam.W * it.cam.H;
@@ -55,7 +54,7 @@ static __device__ void unit_setup(const DItem& it, const DShell* sh, int u) {
     const size_t end = min(total, beg + (size_t)kClearPerUnit);
     uint4* p = reinterpret_cast<uint4*>(it.vis + beg);
     const size_t n2 = (end - beg) >> 1;
-    for (size_t i = threadIdx.x & 31; i < n2; i += 32) clear_vis2<HINT>(p + i);
+    for (size_t i = threadIdx.x & 31; i < n2; i += 32) clear_vis2(p + i);
     if (((end - beg) & 1) && (threadIdx.x & 31) == 0) it.vis[end - 1] = 0ull;
     return;
   }
@@ -84,16 +83,14 @@ __device__ __forceinline__ int load_tri(const DShell& s, const DCam& c, int t, T
   return make_tri(__ldcg(s.vsetup + idx[0]), __ldcg(s.vsetup + idx[1]), __ldcg(s.vsetup + idx[2]), c.W, c.H, T);
 }
 
-template <bool HINT>
 __device__ __forceinline__ void raster_pixel(const Tri& T, int t, int x, int y, int W, unsigned long long* vis) {
   long long e[3];
   edge_values(T, 256 * x + 128, 256 * y + 128, e);
-  if (covered(T, e)) red_max_vis<HINT>(vis + (size_t)y * W + x, vis_key(depth_key(T, e), t));
+  if (covered(T, e)) red_max_vis(vis + (size_t)y * W + x, vis_key(depth_key(T, e), t));
 }
 
 // The parts of triangle t clipped at the near plane, rasterized by the whole
 // warp (each lane strides over the parts' screen boxes).  Rare: out of line.
-template <bool HINT>
 static __device__ __forceinline__ void raster_clipped(const DShell& s, const DCam& c, int t, unsigned long long* vis) {
   const int* ip = s.tris + 3 * (size_t)t;
   const int idx[3] = {__ldg(ip), __ldg(ip + 1), __ldg(ip + 2)};   // checked in range by load_tri
@@ -106,7 +103,7 @@ static __device__ __forceinline__ void raster_clipped(const DShell& s, const DCa
     const int npq = bw > 0 && bh > 0 ? bw * bh : 0;
     for (int p = lane; p < npq; p += 32) {
       const int yy = p / bw;
-      raster_pixel<HINT>(part[k], t, part[k].xlo + (p - yy * bw), part[k].ylo + yy, c.W, vis);
+      raster_pixel(part[k], t, part[k].xlo + (p - yy * bw), part[k].ylo + yy, c.W, vis);
     }
   }
 }
@@ -161,7 +158,7 @@ struct RasterCounts {
 // the triangles' start bits tells every lane which triangle owns its pair,
 // so lanes do not idle on small or culled boxes.  Larger boxes are
 // rasterized by the whole warp, one triangle at a time.
-template <bool HINT, bool FULL>
+template <bool FULL>
 __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, int t0, unsigned long long* vis,
                                              char* smem, RasterCounts& rc) {
   TriS* s_tri = reinterpret_cast<TriS*>(smem);
@@ -251,7 +248,7 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
       if ((e[0] + (q.tl_bw & 1) > 0) && (e[1] + ((q.tl_bw >> 1) & 1) > 0) && (e[2] + ((q.tl_bw >> 2) & 1) > 0)) {
         const TriPos p = s_pos[wbase + o];
         const int S = e[0] + e[1] + e[2];
-        red_max_vis<HINT>(vis + (size_t)(p.ylo + dy) * W + (p.xlo + dx), vis_key(depth_key32(q.q, e, S, q.rS), q.t));
+        red_max_vis(vis + (size_t)(p.ylo + dy) * W + (p.xlo + dx), vis_key(depth_key32(q.q, e, S, q.rS), q.t));
       }
     }
     carry += __popc(bits);
@@ -273,7 +270,7 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
     const int npq = bw * bh;
     for (int p = lane; p < npq; p += 32) {
       const int yy = p / bw;
-      raster_pixel<HINT>(T, tq, T.xlo + (p - yy * bw), T.ylo + yy, W, vis);
+      raster_pixel(T, tq, T.xlo + (p - yy * bw), T.ylo + yy, W, vis);
     }
   }
   // triangles clipped at the near plane (items with a vertex nearer than
@@ -283,7 +280,7 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
     while (cm) {
       const int l = __ffs(cm) - 1;
       cm &= cm - 1;
-      raster_clipped<HINT>(s, it.cam, __shfl_sync(kAll, t, l), vis);
+      raster_clipped(s, it.cam, __shfl_sync(kAll, t, l), vis);
     }
   }
   __syncwarp();   // the records are reused by the next round
@@ -291,7 +288,7 @@ __device__ __forceinline__ void raster_round(const DItem& it, const DShell& s, i
 
 // Raster unit: 32 * it.raster_rounds triangles of one shell in rounds of 32;
 // this warp runs rounds [r0, r1).
-template <bool HINT, bool FULL>
+template <bool FULL>
 static __device__ __forceinline__ void unit_raster(const DItem& it, const DShell* sh, int u, WsHeader* hdr, char* smem,
                                                    int r0, int r1) {
   int i = 0;
@@ -302,7 +299,7 @@ static __device__ __forceinline__ void unit_raster(const DItem& it, const DShell
   unsigned long long* vis = it.vis + (size_t)i * it.cam.W * it.cam.H;
   RasterCounts rc = {0, 0, 0, 0};
   const int rounds = min(r1, min(per_unit, s.nt - base + 31) / 32);
-  for (int r = r0; r < rounds; ++r) raster_round<HINT, FULL>(it, s, base + 32 * r, vis, smem, rc);
+  for (int r = r0; r < rounds; ++r) raster_round<FULL>(it, s, base + 32 * r, vis, smem, rc);
   warp_count(&hdr->front, rc.fb & 0xFFFFu);
   warp_count(&hdr->back, rc.fb >> 16);
   warp_count(&hdr->nearc, rc.ng & 0xFFFFu);
@@ -367,13 +364,13 @@ static __device__ __forceinline__ bool clipped_part(const DShell& s, const DCam&
   return true;
 }
 
-template <int DEG, int VEC>
+template <int DEG, int VEC, bool KEEP = false>
 __device__ __forceinline__ Frag fetch_sh(const DShell& s, const Footprint& f, const float3 v) {
   constexpr int NCH = 1 + 3 * (DEG + 1) * (DEG + 1);
   float Y[16];
   sh_basis(DEG, v.x, v.y, v.z, Y);
   float val[NCH];
-  bilinear_f16<NCH, VEC>(reinterpret_cast<const __half*>(s.tex), s.tw, s.pitch, f, val);
+  bilinear_f16<NCH, VEC, KEEP>(reinterpret_cast<const __half*>(s.tex), s.tw, s.pitch, f, val);
   return decode_sh<DEG>(val, Y);
 }
 
@@ -405,8 +402,9 @@ __device__ __forceinline__ Frag fetch_baked_v(const DShell& s, int ix, float fx,
 
 // Colour and opacity of one fragment; f = its clamped footprint and (ix +
 // fx, iy + fy) the unclamped texel coordinate (baked bands derive their own
-// footprints from it); v = unit ray direction (SH formats only).
-template <int TC>
+// footprints from it); v = unit ray direction (SH formats only).  KEEP: FP16
+// texel loads mark their lines evict_last (forward-only kernels).
+template <int TC, bool KEEP = false>
 __device__ __forceinline__ Frag fetch_frag(const DShell& s, const Footprint& f, int ix, float fx, int iy, float fy,
                                            const float3 v) {
   if constexpr (TC == TC_RGBA) {
@@ -416,7 +414,7 @@ __device__ __forceinline__ Frag fetch_frag(const DShell& s, const Footprint& f, 
   } else if constexpr (TC >= TC_U80) {
     return fetch_baked_v<TC - TC_U80>(s, ix, fx, iy, fy, v);
   } else if constexpr (TC >= TC_SH0) {
-    return fetch_sh<TC - TC_SH0, sh_vec<TC>()>(s, f, v);
+    return fetch_sh<TC - TC_SH0, sh_vec<TC>(), KEEP>(s, f, v);
   }
   if (s.fmt == VS_TEX_SH_U8) {
     switch (s.degree) {
@@ -433,7 +431,7 @@ __device__ __forceinline__ Frag fetch_frag(const DShell& s, const Footprint& f, 
     return {c[0], c[1], c[2], c[3]};
   }
 #define VS_CASE(D, V) \
-  case D * 16 + V: return fetch_sh<D, V>(s, f, v);
+  case D * 16 + V: return fetch_sh<D, V, KEEP>(s, f, v);
   switch (s.degree * 16 + s.vec) {
     VS_CASE(0, 1) VS_CASE(0, 2) VS_CASE(0, 4) VS_CASE(0, 8)
     VS_CASE(1, 1) VS_CASE(1, 2) VS_CASE(1, 4) VS_CASE(1, 8)
@@ -608,7 +606,7 @@ static __device__ __forceinline__ void shade_clipped(const DItem& it, const DShe
     }
     float3 v = make_float3(0.f, 0.f, 1.f);
     if (is_sh<TC>(s)) v = ray_dir(it.cam, x, y);
-    fr = fetch_frag<TC>(s, f, ix, fx, iy, fy, v);
+    fr = fetch_frag<TC, !BWD>(s, f, ix, fx, iy, fy, v);
     if (it.layers) layer_geom(it, s, idx, e >> kTriBits, pp, ix, fx, iy, fy);
     ++*nfrag;
   }
@@ -703,7 +701,7 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
       tt[d] = -1;
       if (i < k && pix_ok) {
         if (FROM_HITS) tt[d] = __ldg(it.hits + (size_t)i * HW + p);
-        else tt[d] = load_vis_tri<BWD && !FROM_HITS>(it.vis + (size_t)i * HW + p);
+        else tt[d] = load_vis_tri(it.vis + (size_t)i * HW + p);
       }
     }
 #pragma unroll
@@ -801,7 +799,7 @@ __device__ __forceinline__ void shade_round(const DItem& it, const DShell* sh, i
           } else {
             float3 v = make_float3(0.f, 0.f, 1.f);
             if (is_sh<TC>(s)) v = ray_dir(it.cam, x, y);
-            fr = fetch_frag<TC>(s, f, ix, fx, iy, fy, v);
+            fr = fetch_frag<TC, !BWD>(s, f, ix, fx, iy, fy, v);
           }
           if constexpr (FULL) {
             if (it.layers) layer_geom(it, s, idx, i, pp, ix, fx, iy, fy);
@@ -1069,8 +1067,8 @@ __global__ void __launch_bounds__(pers_threads(BWD), BWD ? VS_PERS_BWD_BLOCKS : 
     if (!ok) break;
     const DShell* sh = tb.shells + it.shell0;
     switch (ph) {
-      case PH_SETUP: unit_setup<BWD>(it, sh, u); break;
-      case PH_RASTER: unit_raster<BWD, FULL>(it, sh, u, hdr, smem, 0, it.raster_rounds); break;
+      case PH_SETUP: unit_setup(it, sh, u); break;
+      case PH_RASTER: unit_raster<FULL>(it, sh, u, hdr, smem, 0, it.raster_rounds); break;
       default:
         unit_shade<BWD, false, TC, FULL>(it, sh, u, hdr, smem, tb.kmax, 0, it.shade_rounds);
     }

@@ -44,6 +44,18 @@ def test_algorithmic_bytes_count_real_channels_not_padding():
     assert fparts["grads"] == 0 and fparts["image"] == 2 * wl["H"] * wl["W"] * 16
 
 
+def test_step_lower_bound_moves_each_touched_texel_once():
+    (scene, cams), = synth.config_scene("c2", scale=0.002, views=3, pitch=32)
+    wl = dict(scene=scene, cams=cams, H=cams[0].height, W=cams[0].width)
+    touched = 12345
+    b = bench.step_lower_bound_bytes(wl, touched)
+    geo = sum(20 * s.pos.shape[0] + 12 * s.tris.shape[0] for s in scene.shells)   # once per step
+    assert b == pytest.approx(touched * (28 * 2 + 28 * 8) + geo + 3 * wl["H"] * wl["W"] * 28)
+    # never above the per-view bytes when every view touches every texel it counts
+    per_view, _ = bench.algorithmic_bytes(wl, touched / 3.0, 1.0, with_bwd=True)
+    assert b <= per_view
+
+
 def test_stored_traffic_only_for_the_captured_sources(monkeypatch):
     with open(os.path.join(bench.ROOT, "profiles", "k_persistent_fwdbwd_c2_traffic.json")) as f:
         d = json.load(f)
