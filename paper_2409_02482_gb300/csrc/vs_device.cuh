@@ -196,7 +196,7 @@ __device__ __forceinline__ void red_max_u64(unsigned long long* p, unsigned long
 // that it stays in L2 between them instead of making another DRAM round trip.
 // The visibility words and the texel reads of the adjoint keep the default
 // priority.  (Measured on the C2 step against other assignments: words
-// evict_last until an evict_first read, gradients normal -- 0.8 % slower;
+// evict_last until an evict_first read, gradients normal -- 1.7 % slower;
 // texel reads evict_first -- 11 % slower, evict_last -- 0.6 % slower.  The
 // forward-only kernels keep texel lines evict_last: there they are the
 // lines that neighbouring fragments reuse.)
